@@ -1,0 +1,199 @@
+/*
+ * libpfire — GB300 (sm_103a) library for the wildfire cellular automaton of
+ * arXiv 2502.18738 (PyTorchFire): the per-step 8-neighbour stencil in its discrete
+ * stochastic form and its differentiable (mean-field) form, and the reverse-time
+ * adjoint of the differentiable form.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grid H x W, row-major, row r grows southward, column c grows eastward. Every
+ *   per-cell array passed in or out is dense: element (r, c) at offset r*W + c, and a
+ *   batch of R realisations is R consecutive H*W planes.
+ * - Unless stated otherwise, array pointers are DEVICE pointers owned by the caller
+ *   and valid for the duration of the call (inputs are copied into library-owned
+ *   buffers before the call returns to the stream, so the caller may reuse them once
+ *   the stream has passed the call). Outputs are caller-allocated device memory.
+ * - All work is enqueued on the CUDA stream given to pf_create; calls return before
+ *   the work finishes unless stated otherwise ("synchronous").
+ * - Discrete states are uint8: 0 non-burnable, 1 unburned (burnable), 2 burning,
+ *   3 burned (Sec. 2.2, "State and transition rules"; the paper's non-burnable
+ *   "no forest fuel" state is kept as its own code).
+ * - Directions: the burning neighbour i of a receiving cell j sits at offset
+ *   (dr, dc) in the fixed order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1).
+ * - Every entry point returns a pf_status; on failure pf_last_error(ctx) holds a
+ *   one-line message. A failed call leaves the context usable unless it returns
+ *   PF_ECUDA, after which the CUDA context itself may be unusable.
+ */
+#ifndef PFIRE_H
+#define PFIRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_ctx pf_ctx;
+
+typedef enum pf_status {
+    PF_OK = 0,
+    PF_EINVAL = -1,   /* bad argument: sizes, NULL where required, out-of-range values */
+    PF_ENOMEM = -2,   /* device allocation failed */
+    PF_ECUDA = -3,    /* a CUDA call or kernel launch failed */
+    PF_ESTATE = -4,   /* call not valid in the context's current state */
+    PF_ETIMEOUT = -5  /* a bounded device wait ran out (batched kernel) */
+} pf_status;
+
+typedef enum pf_form {
+    PF_DISCRETE = 0,  /* stochastic uint8 automaton with Philox draws */
+    PF_DIFF = 1       /* differentiable continuous-state form, FP32 (a, b) */
+} pf_form;
+
+/* Create a context for an H x W grid.
+ *   form          PF_DISCRETE or PF_DIFF.
+ *   realisations  R >= 1 independent stochastic runs sharing one landscape (discrete
+ *                 form); must be 1 for PF_DIFF, which is deterministic.
+ *   seed          64-bit Philox key (Sec. 2.2 data flow: "two random matrices").
+ *   cuda_stream   cudaStream_t to run on (NULL = legacy default stream).
+ * Limits: 1 <= H, W <= 65536, H*W*R < 2^32. Allocates the state and q buffers; the
+ * landscape defaults to flat, calm, p_veg = p_den = 0, parameters to the paper's
+ * calibration start values (p_h 0.58, c1 0.045, c2 0.131, a 0.078, p_continue 0.3,
+ * l 30 m). Returns PF_EINVAL / PF_ENOMEM / PF_ECUDA; *out is NULL on failure. */
+int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t seed, void* cuda_stream);
+
+/* Release every buffer of the context (synchronises its stream first). NULL is a no-op. */
+void pf_destroy(pf_ctx* ctx);
+
+/* Static landscape (Sec. 2.1 inputs): elevation E (m; the slope of Eq. 1 is derived
+ * from it), vegetation p_veg and density p_den (Eq. 2), and the first wind epoch
+ * (V_w m/s, theta_w degrees counter-clockwise from East, Eq. 3), which applies from
+ * step 0. Each is an H*W FP32 device array; NULL selects the neutral factor, as the
+ * paper's "empty tensor" rule does (flat terrain, p_veg = p_den = 0, no wind).
+ * Returns PF_EINVAL if any p_veg or p_den is below -1 or any value is NaN or infinite.
+ * Replaces all wind epochs. Synchronous validation (one device reduction). */
+int pf_set_env(pf_ctx* ctx, const float* E, const float* p_veg, const float* p_den,
+               const float* V_w, const float* theta_w_deg);
+
+/* Add a wind epoch (Eq. 3 inputs) that applies from global step from_step onwards,
+ * until the next epoch. from_step must be > 0 and larger than every earlier epoch's;
+ * NULL V_w means calm. The data is copied into the context (8 bytes per cell per
+ * epoch). Used to resample the wind during a run and replayed by pf_backward. */
+int pf_set_wind(pf_ctx* ctx, const float* V_w, const float* theta_w_deg, int from_step);
+
+/* Model parameters (Sec. 2.1 list; Eq. 2-4): p_h base probability, c1 wind-speed
+ * factor, c2 wind-direction factor, a slope factor (per degree), p_continue
+ * probability that a burning cell keeps burning, l cell side in metres (Eq. 1).
+ * Requires finite values, p_h >= 0, 0 <= p_continue <= 1 and l > 0 (else PF_EINVAL). */
+int pf_set_params(pf_ctx* ctx, float p_h, float c1, float c2, float a, float p_continue, float l_m);
+
+/* Run T >= 0 steps from S_init (uint8 [R][H][W], device), starting at global step 0.
+ *   Discrete form: S_out is uint8 [R][H][W]. Realisation r draws with run index r.
+ *   Differentiable form: S_init's codes map to a = [S in {2,3}], b = [S == 2]; code 0
+ *   cells are non-burnable for the whole run. S_out is FP32 [2][H][W]: a_T (probability
+ *   of having ignited by step T, the burn probability) then b_T (probability of burning).
+ *   The run is recorded for pf_backward: (a, b) checkpoints every K steps (K chosen to
+ *   fit free HBM, see pf_tuning) and the wind epochs it used.
+ * S_out may be NULL (the state is kept in the context; see pf_get_state).
+ * Sec. 2.2 transition rules and Eq. 9 for the discrete form; Eq. 9 with burning
+ * probabilities in place of the burning indicator for the differentiable form. */
+int pf_forward(pf_ctx* ctx, const uint8_t* S_init, int T, void* S_out);
+
+/* Continue the current state for T more steps (same output layout as pf_forward).
+ * Global step numbering continues, so pf_forward(T1) then pf_advance(T2) draws the
+ * same numbers as pf_forward(T1 + T2). In the differentiable form the recorded run
+ * is extended as well. */
+int pf_advance(pf_ctx* ctx, int T, void* S_out);
+
+/* Reverse-time adjoint of the last recorded differentiable run (PF_DIFF only; else,
+ * or before any pf_forward, PF_ESTATE).
+ *   dL_da_T, dL_db_T  FP32 [H][W] device gradients of the loss w.r.t. a_T and b_T
+ *                     (either may be NULL = zero).
+ *   grad_params       HOST double[4], overwritten with dL/d(p_h, c1, c2, a): the
+ *                     parameter gradients summed over all cells and steps in FP64,
+ *                     in a fixed order (bit-reproducible run to run).
+ *   grad_pveg, grad_pden  FP32 [H][W] device outputs (nullable): dL/dp_veg, dL/dp_den
+ *                     per cell (0 at non-burnable cells).
+ * Recomputes each checkpoint segment, newest first, then sweeps it backwards.
+ * Synchronous (grad_params is on the host when it returns). */
+int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double grad_params[4],
+                float* grad_pveg, float* grad_pden);
+
+/* Current state and its global step number. S: discrete uint8 [R][H][W]; differentiable
+ * FP32 [2][H][W] (a then b). step may be NULL. */
+int pf_get_state(pf_ctx* ctx, int* step, void* S);
+
+/* Overwrite the current state and set the global step counter (resume, and the
+ * paper's in-place edits for spotting, Sec. 2.2). Discrete: uint8 [R][H][W] with codes
+ * 0-3. Differentiable: FP32 [2][H][W] with 0 <= b <= a <= 1 (not validated); cells with
+ * a == b == 0 remain burnable. Discards the recorded run. */
+int pf_set_state(pf_ctx* ctx, int step, const void* S);
+
+/* Ignition probability map p_ignite (Eq. 9) of the current state: FP32 [R][H][W]
+ * (discrete: over burning neighbours, for every cell; differentiable: with burning
+ * probabilities b, R = 1). The paper's real-time ignition-map accessor (Sec. 2.1). */
+int pf_ignition_map(pf_ctx* ctx, float* P_out);
+
+/* Binary cross-entropy of a burn-probability map against a 0/1 target, and its
+ * gradient: yhat = clamp(a, 1e-7, 1 - 1e-7), L = -mean(y log yhat + (1-y) log(1-yhat)),
+ * dL_da = (yhat - y) / (yhat (1 - yhat)) / n inside the clamp range, else 0.
+ * a, y: FP32 [n] device; dL_da: FP32 [n] device (nullable); loss: HOST double
+ * (nullable; if given the call is synchronous). Context-free; runs on cuda_stream. */
+int pf_loss_bce(const float* a, const float* y, int64_t n, float* dL_da, double* loss, void* cuda_stream);
+
+/* Kernel selection and checkpoint interval. Zero fields mean "choose automatically".
+ *   kernel  1 = plain one-launch-per-step kernels, 2 = temporal-blocked TMA kernels.
+ *   k       steps per launch of the temporal-blocked kernels (1..16).
+ *   K       checkpoint interval of the differentiable form (>= 1; 1 keeps every state).
+ *   profile 1 = time every kernel launch with CUDA events on the context's stream
+ *           (read with pf_profile_read). */
+typedef struct pf_tuning {
+    int kernel;
+    int k;
+    int K;
+    int profile;
+} pf_tuning;
+
+int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t);
+int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t);
+
+/* Per-kernel-kind launch counts and (if profiling) summed device milliseconds since
+ * the last reset. kinds[i] is a static name string. Synchronous. Returns the number of
+ * kinds written (<= max_kinds) or a negative pf_status. */
+int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* launches, double* ms, int reset);
+
+/* ----------------------------------------------------------- batched fires */
+
+/* One independent fire for pf_batch_submit. All pointers are device pointers; the
+ * per-cell arrays are dense H*W FP32 (NULL = neutral factor, as in pf_set_env).
+ *   form        PF_DISCRETE (S_out uint8 [H][W]) or PF_DIFF (S_out FP32 [2][H][W];
+ *               the adjoint is not part of the batch).
+ *   fire_id     Philox counter word 3, so fires draw disjoint streams.
+ *   run         Philox counter word 1 (realisation index). */
+typedef struct pf_job {
+    int H, W, T, form;
+    uint64_t seed;
+    uint32_t run, fire_id;
+    const float *E, *p_veg, *p_den, *V_w, *theta_w;
+    float p_h, c1, c2, a, p_continue, l;
+    const uint8_t* S_init;
+    void* S_out;
+} pf_job;
+
+/* Run n independent fires of uneven sizes and step counts (each as pf_forward would,
+ * bit-identically for the discrete form) from one device work queue in a persistent
+ * kernel. Synchronous. Returns PF_ETIMEOUT if a bounded device-side wait ran out. */
+int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream);
+
+/* Message of the last failure on ctx (or of the last context-free call when ctx is
+ * NULL). Never NULL; valid until the next call on the same context. */
+const char* pf_last_error(const pf_ctx* ctx);
+
+/* Library version string. */
+const char* pf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFIRE_H */

@@ -1,0 +1,335 @@
+"""Python binding of libpfire, the GB300 (sm_103a) library for the differentiable
+wildfire cellular automaton of arXiv 2502.18738 (PyTorchFire).
+
+Argument marshalling only: every step of the automaton runs in the library's CUDA
+kernels. PyTorch supplies device memory and streams. The functions ``pf_*`` mirror the
+C ABI of ``include/pfire.h`` one to one (tensors in place of device pointers);
+``FireModel`` and ``DiffFire`` are thin conveniences on top of them.
+
+There is no CPU path: if ``libpfire.so`` is missing or cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "PFireError", "build", "load", "PF_DISCRETE", "PF_DIFF",
+    "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward",
+    "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
+    "pf_set_tuning", "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error",
+    "pf_version", "FireModel", "DiffFire", "PfJob", "EXPORTED_SYMBOLS",
+]
+
+PF_DISCRETE, PF_DIFF = 0, 1
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ESTATE, PF_ETIMEOUT = 0, -1, -2, -3, -4, -5
+_STATUS = {PF_EINVAL: "PF_EINVAL", PF_ENOMEM: "PF_ENOMEM", PF_ECUDA: "PF_ECUDA",
+           PF_ESTATE: "PF_ESTATE", PF_ETIMEOUT: "PF_ETIMEOUT"}
+
+LIB_PATH = _build.LIB
+
+# every extern "C" entry point declared in include/pfire.h
+EXPORTED_SYMBOLS = [
+    "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
+    "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
+    "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
+]
+
+
+class PFireError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class PfTuning(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("k", ctypes.c_int), ("K", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class PfJob(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("T", ctypes.c_int), ("form", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("run", ctypes.c_uint32), ("fire_id", ctypes.c_uint32),
+                ("E", ctypes.c_void_p), ("p_veg", ctypes.c_void_p), ("p_den", ctypes.c_void_p),
+                ("V_w", ctypes.c_void_p), ("theta_w", ctypes.c_void_p),
+                ("p_h", ctypes.c_float), ("c1", ctypes.c_float), ("c2", ctypes.c_float), ("a", ctypes.c_float),
+                ("p_continue", ctypes.c_float), ("l", ctypes.c_float),
+                ("S_init", ctypes.c_void_p), ("S_out", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile libpfire.so for sm_103a (no-op when up to date)."""
+    return _build.build(force=force)
+
+
+def load():
+    """Load libpfire.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpfire.so is not built ({LIB_PATH}); call paper_2502_18738_gb300.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i, f, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_uint64
+        sig = {
+            "pf_create": ([ctypes.POINTER(vp), i, i, i, i, u64, vp], i),
+            "pf_destroy": ([vp], None),
+            "pf_set_env": ([vp, vp, vp, vp, vp, vp], i),
+            "pf_set_wind": ([vp, vp, vp, i], i),
+            "pf_set_params": ([vp, f, f, f, f, f, f], i),
+            "pf_forward": ([vp, vp, i, vp], i),
+            "pf_advance": ([vp, i, vp], i),
+            "pf_backward": ([vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp], i),
+            "pf_get_state": ([vp, ctypes.POINTER(i), vp], i),
+            "pf_set_state": ([vp, i, vp], i),
+            "pf_ignition_map": ([vp, vp], i),
+            "pf_loss_bce": ([vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double), vp], i),
+            "pf_set_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
+            "pf_get_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
+            "pf_profile_read": ([vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_double), i], i),
+            "pf_batch_submit": ([ctypes.POINTER(PfJob), i, vp], i),
+            "pf_last_error": ([vp], ctypes.c_char_p),
+            "pf_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, h=None):
+    if rc != PF_OK:
+        msg = load().pf_last_error(h).decode()
+        raise PFireError(rc, msg)
+
+
+def _ptr(t, dtype=None, numel=None, what="tensor"):
+    """Device pointer of a CUDA tensor (None -> NULL), after shape/dtype checks."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------ raw ABI
+
+def pf_version() -> str:
+    return load().pf_version().decode()
+
+
+def pf_last_error(h=None) -> str:
+    return load().pf_last_error(h).decode()
+
+
+def pf_create(H, W, form=PF_DISCRETE, realisations=1, seed=0, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().pf_create(ctypes.byref(h), int(H), int(W), int(form), int(realisations),
+                            int(seed) & 0xFFFFFFFFFFFFFFFF, _stream(stream)))
+    return h
+
+
+def pf_destroy(h):
+    if h:
+        load().pf_destroy(h)
+
+
+def pf_set_env(h, H, W, E=None, p_veg=None, p_den=None, V_w=None, theta_w=None):
+    n = H * W
+    f = torch.float32
+    _check(load().pf_set_env(h, _ptr(E, f, n, "E"), _ptr(p_veg, f, n, "p_veg"), _ptr(p_den, f, n, "p_den"),
+                             _ptr(V_w, f, n, "V_w"), _ptr(theta_w, f, n, "theta_w")), h)
+
+
+def pf_set_wind(h, H, W, V_w, theta_w, from_step):
+    n = H * W
+    _check(load().pf_set_wind(h, _ptr(V_w, torch.float32, n, "V_w"), _ptr(theta_w, torch.float32, n, "theta_w"),
+                              int(from_step)), h)
+
+
+def pf_set_params(h, p_h, c1, c2, a, p_continue, l=30.0):
+    _check(load().pf_set_params(h, p_h, c1, c2, a, p_continue, l), h)
+
+
+def pf_forward(h, S_init, T, S_out=None):
+    _check(load().pf_forward(h, _ptr(S_init, torch.uint8, None, "S_init"), int(T), _ptr(S_out, None, None, "S_out")), h)
+    return S_out
+
+
+def pf_advance(h, T, S_out=None):
+    _check(load().pf_advance(h, int(T), _ptr(S_out, None, None, "S_out")), h)
+    return S_out
+
+
+def pf_backward(h, dL_da=None, dL_db=None, grad_pveg=None, grad_pden=None):
+    g = (ctypes.c_double * 4)()
+    f = torch.float32
+    _check(load().pf_backward(h, _ptr(dL_da, f, None, "dL_da"), _ptr(dL_db, f, None, "dL_db"), g,
+                              _ptr(grad_pveg, f, None, "grad_pveg"), _ptr(grad_pden, f, None, "grad_pden")), h)
+    return [g[0], g[1], g[2], g[3]]
+
+
+def pf_get_state(h, S=None) -> int:
+    step = ctypes.c_int()
+    _check(load().pf_get_state(h, ctypes.byref(step), _ptr(S, None, None, "S")), h)
+    return step.value
+
+
+def pf_set_state(h, step, S):
+    _check(load().pf_set_state(h, int(step), _ptr(S, None, None, "S")), h)
+
+
+def pf_ignition_map(h, P_out):
+    _check(load().pf_ignition_map(h, _ptr(P_out, torch.float32, None, "P_out")), h)
+    return P_out
+
+
+def pf_loss_bce(a, y, dL_da=None, want_loss=True, stream=None):
+    n = a.numel()
+    loss = ctypes.c_double()
+    _check(load().pf_loss_bce(_ptr(a, torch.float32, n, "a"), _ptr(y, torch.float32, n, "y"), n,
+                              _ptr(dL_da, torch.float32, n, "dL_da"),
+                              ctypes.byref(loss) if want_loss else None, _stream(stream)))
+    return loss.value if want_loss else None
+
+
+def pf_set_tuning(h, kernel=0, k=0, K=0, profile=0):
+    t = PfTuning(kernel, k, K, profile)
+    _check(load().pf_set_tuning(h, ctypes.byref(t)), h)
+
+
+def pf_get_tuning(h) -> dict:
+    t = PfTuning()
+    _check(load().pf_get_tuning(h, ctypes.byref(t)), h)
+    return dict(kernel=t.kernel, k=t.k, K=t.K, profile=t.profile)
+
+
+def pf_profile_read(h, reset=False) -> dict:
+    n = 16
+    kinds = (ctypes.c_char_p * n)()
+    launches = (ctypes.c_longlong * n)()
+    ms = (ctypes.c_double * n)()
+    m = load().pf_profile_read(h, n, kinds, launches, ms, int(bool(reset)))
+    if m < 0:
+        _check(m, h)
+    return {kinds[i].decode(): (int(launches[i]), float(ms[i])) for i in range(m)}
+
+
+def pf_batch_submit(jobs, stream=None):
+    arr = (PfJob * len(jobs))(*jobs)
+    _check(load().pf_batch_submit(arr, len(jobs), _stream(stream)))
+
+
+# ------------------------------------------------------------- conveniences
+
+class FireModel:
+    """One libpfire context (an H x W grid, one form) on the current CUDA stream."""
+
+    def __init__(self, H, W, form=PF_DISCRETE, realisations=1, seed=0, stream=None):
+        self.H, self.W, self.form, self.R = int(H), int(W), int(form), int(realisations)
+        self.h = pf_create(H, W, form, realisations, seed, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pf_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_env(self, E=None, p_veg=None, p_den=None, V_w=None, theta_w=None):
+        pf_set_env(self.h, self.H, self.W, E, p_veg, p_den, V_w, theta_w)
+
+    def set_wind(self, V_w, theta_w, from_step):
+        pf_set_wind(self.h, self.H, self.W, V_w, theta_w, from_step)
+
+    def set_params(self, p_h, c1, c2, a, p_continue, l=30.0):
+        pf_set_params(self.h, p_h, c1, c2, a, p_continue, l)
+
+    def set_tuning(self, **kw):
+        pf_set_tuning(self.h, **kw)
+
+    def _out(self):
+        if self.form == PF_DISCRETE:
+            return torch.empty((self.R, self.H, self.W), dtype=torch.uint8, device="cuda")
+        return torch.empty((2, self.H, self.W), dtype=torch.float32, device="cuda")
+
+    def forward(self, S_init, T, out=None):
+        out = self._out() if out is None else out
+        return pf_forward(self.h, S_init, T, out)
+
+    def advance(self, T, out=None):
+        out = self._out() if out is None else out
+        return pf_advance(self.h, T, out)
+
+    def backward(self, dL_da=None, dL_db=None, per_cell=True):
+        gpv = gpd = None
+        if per_cell:
+            gpv = torch.empty((self.H, self.W), dtype=torch.float32, device="cuda")
+            gpd = torch.empty_like(gpv)
+        g = pf_backward(self.h, dL_da, dL_db, gpv, gpd)
+        return g, gpv, gpd
+
+    def state(self):
+        out = self._out()
+        step = pf_get_state(self.h, out)
+        return step, out
+
+    def set_state(self, step, S):
+        pf_set_state(self.h, step, S)
+
+    def ignition_map(self):
+        P = torch.empty((self.R if self.form == PF_DISCRETE else 1, self.H, self.W), dtype=torch.float32,
+                        device="cuda")
+        return pf_ignition_map(self.h, P)
+
+
+class DiffFire(torch.autograd.Function):
+    """Differentiable forward through pf_forward and adjoint through pf_backward.
+
+    ``a_T, b_T = DiffFire.apply(model, S_init, T, params4, p_veg, p_den)`` where params4 =
+    (p_h, c1, c2, a) as a float64 tensor (CPU or CUDA) and p_veg / p_den are H x W float32
+    CUDA tensors. The model's other inputs (E, wind epochs, p_continue, l) are held
+    fixed."""
+
+    @staticmethod
+    def forward(ctx, model: FireModel, S_init, T, params4, p_veg, p_den, p_continue=0.3, l=30.0,
+                E=None, V_w=None, theta_w=None):
+        p = [float(x) for x in params4.detach().cpu().tolist()]
+        model.set_env(E, p_veg.detach().contiguous(), p_den.detach().contiguous(), V_w, theta_w)
+        model.set_params(p[0], p[1], p[2], p[3], p_continue, l)
+        out = model.forward(S_init, T)
+        ctx.model = model
+        ctx.params_dtype, ctx.params_device = params4.dtype, params4.device
+        return out[0].clone(), out[1].clone()
+
+    @staticmethod
+    def backward(ctx, ga, gb):
+        ga = None if ga is None else ga.contiguous().float()
+        gb = None if gb is None else gb.contiguous().float()
+        g, gpv, gpd = ctx.model.backward(ga, gb, per_cell=True)
+        g4 = torch.tensor(g, dtype=ctx.params_dtype, device=ctx.params_device)
+        return None, None, None, g4, gpv, gpd, None, None, None, None, None

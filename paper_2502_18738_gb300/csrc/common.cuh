@@ -1,0 +1,96 @@
+// Internal declarations shared by the libpfire translation units (not installed).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pf {
+
+// f_p(x) = tanh(C x) (Eq. 5/8), the paper's constant rounded to FP32.
+constexpr float kC = 1.1486328125f;
+
+// Neighbour offsets (dr, dc) from the receiving cell to the burning neighbour, fixed
+// direction order d = 0..7.
+__host__ __device__ constexpr int dir_dr(int d) { return d < 3 ? -1 : (d < 5 ? 0 : 1); }
+__host__ __device__ constexpr int dir_dc(int d) {
+    return (d == 0 || d == 3 || d == 5) ? -1 : ((d == 1 || d == 6) ? 0 : 1);
+}
+
+// Pitched layouts: every internal per-cell plane has H rows of `pitch` elements,
+// pitch = W rounded up to 16 (16-byte rows for uint8, 64-byte rows for FP32), so that
+// rows are valid TMA strides and 16-byte vector accesses. Columns [W, pitch) hold the
+// neutral value (state 0 / a = b = q = 0) and behave as cells outside the grid.
+inline int pitch_of(int W) { return (W + 15) & ~15; }
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): per round, the two multipliers act on words 0
+// and 2; their high halves are xored with the odd words and the key; the key advances
+// by the two Weyl increments between rounds.
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                       uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// Uniform in [0, 1) from the top 24 bits: exact in FP32.
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// Byte-lane helpers for uint8 states packed 4 per 32-bit word (states are 0..3, so
+// only bits 0-1 of each byte are ever set).
+__device__ __forceinline__ uint32_t lanes_eq2(uint32_t x) { return (x >> 1) & ~x & 0x01010101u; }
+__device__ __forceinline__ uint32_t lanes_eq1(uint32_t x) { return x & ~(x >> 1) & 0x01010101u; }
+
+// ---------------------------------------------------------------- launchers
+struct PrepArgs {
+    int H, W, pitch;
+    const float *E, *pveg, *pden, *V, *th;  // dense H*W, nullable
+    const uint8_t* burnable;                 // dense H*W, nullable
+    float p_h, c1, c2, a, l;
+};
+
+void launch_prep(const PrepArgs& g, float* q, cudaStream_t s);
+// dL/dq -> per-block FP64 partials of dL/d(p_h, c1, c2, a) (partials[nblk][4]) and
+// accumulation of per-cell gradients (dense H*W, nullable).
+int prep_adjoint_blocks(int H, int W);
+void launch_prep_adjoint(const PrepArgs& g, const float* Gq, double* partials, float* gpveg,
+                         float* gpden, cudaStream_t s);
+// acc[0..3] += fixed-order FP64 sum of partials[nblk][4]
+void launch_reduce_partials(const double* partials, int nblk, double* acc, cudaStream_t s);
+
+struct DiscreteArgs {
+    int H, W, pitch, R;
+    float p_continue;
+    uint32_t key0, key1, fire, run0;
+};
+void launch_discrete_step(const DiscreteArgs& g, const uint8_t* S, uint8_t* Sn, const float* q,
+                          uint32_t step, cudaStream_t s);
+// temporal-blocked: k <= KH steps per launch from global step `step`; `tin` is a 3-D
+// tensor map over the [R][H][pitch] uint8 input buffer with box {160, TH + 2 KH, 1}.
+int discrete_blocked_tile_rows();
+size_t discrete_blocked_smem(int TH, int KH);
+void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin, int TH, int KH, uint8_t* Sn,
+                                  const float* q, uint32_t step, int k, int* err, cudaStream_t s);
+
+void launch_diff_step(int H, int W, int pitch, float p_continue, const float* ab, float* ab_next,
+                      const float* q, cudaStream_t s);
+void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float* ab, const float* q,
+                         const float* lam1, float* lam0, float* Gq, cudaStream_t s);
+void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,
+                                  cudaStream_t s);
+void launch_ignition_map_diff(int H, int W, int pitch, const float* ab, const float* q, float* P,
+                              cudaStream_t s);
+
+}  // namespace pf

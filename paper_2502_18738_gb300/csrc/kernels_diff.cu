@@ -1,0 +1,157 @@
+// Differentiable (mean-field) step and its reverse-time adjoint.
+// State (a, b) = (P[ever ignited], P[burning]) as two FP32 planes [2][H][pitch]:
+//   P_j  = 1 - prod_d (1 - b_{j+d} q_dj)     (Eq. 9 with burning probabilities)
+//   n_j  = (1 - a_j) P_j,  a'_j = a_j + n_j,  b'_j = n_j + p_continue b_j
+// P is accumulated as P <- P + x (1 - P), which keeps small probabilities accurate in FP32.
+#include "common.cuh"
+
+namespace pf {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_diff_step(int H, int W, int pitch, float pc, const float* __restrict__ ab,
+                                                   float* __restrict__ abn, const float* __restrict__ q) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= H || c >= pitch) return;
+    const size_t plane = (size_t)H * pitch;
+    const size_t j = (size_t)r * pitch + c;
+    if (c >= W) {
+        abn[j] = 0.0f;
+        abn[plane + j] = 0.0f;
+        return;
+    }
+    const float* b = ab + plane;
+    float P = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int ri = r + dir_dr(d), ci = c + dir_dc(d);
+        if (ri < 0 || ri >= H || ci < 0 || ci >= W) continue;
+        const float x = __ldg(b + (size_t)ri * pitch + ci) * __ldg(q + d * plane + j);
+        P = fmaf(x, 1.0f - P, P);
+    }
+    const float a = ab[j];
+    const float n = (1.0f - a) * P;
+    abn[j] = a + n;
+    abn[plane + j] = fmaf(pc, b[j], n);
+}
+
+__global__ void k_ignition_map_diff(int H, int W, int pitch, const float* __restrict__ ab,
+                                    const float* __restrict__ q, float* __restrict__ Pout) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)H * W) return;
+    const int r = (int)(idx / W), c = (int)(idx % W);
+    const size_t plane = (size_t)H * pitch;
+    const size_t j = (size_t)r * pitch + c;
+    const float* b = ab + plane;
+    float P = 0.0f;
+    for (int d = 0; d < 8; ++d) {
+        const int ri = r + dir_dr(d), ci = c + dir_dc(d);
+        if (ri < 0 || ri >= H || ci < 0 || ci >= W) continue;
+        const float x = b[(size_t)ri * pitch + ci] * q[d * plane + j];
+        P = fmaf(x, 1.0f - P, P);
+    }
+    Pout[idx] = P;
+}
+
+// ---------------------------------------------------------------- adjoint
+// Reverse-mode transpose of k_diff_step for one step. With lambda' = dL/d(a', b'):
+//   l_n = l_a'_j + l_b'_j,  l_a_j = l_a'_j - l_n P_j,  l_P_j = l_n (1 - a_j)
+//   l_b_i = p_c l_b'_i + sum_{targets j of i} l_P_j q_dj prod_{e != d} (1 - b_e q_ej)
+//   Gq_dj += l_P_j b_{j+d} prod_{e != d} (1 - b_e q_ej)
+// The leave-one-out products come from prefix / suffix products (no division, since a
+// factor 1 - b q can be exactly 0). Each block computes the per-target contributions of
+// its tile plus a one-cell ring into shared memory, then gathers them per source cell.
+constexpr int kAX = 32, kAY = 8;
+
+__global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pitch, float pc,
+                                                            const float* __restrict__ ab,
+                                                            const float* __restrict__ q,
+                                                            const float* __restrict__ lam1,
+                                                            float* __restrict__ lam0, float* __restrict__ Gq) {
+    __shared__ float sb[kAY + 4][kAX + 4];          // b, rows r0-2 .. r0+kAY+1
+    __shared__ float sc[8][kAY + 2][kAX + 2];       // contributions of targets j
+    const int c0 = blockIdx.x * kAX, r0 = blockIdx.y * kAY;
+    const int tid = threadIdx.y * kAX + threadIdx.x;
+    const size_t plane = (size_t)H * pitch;
+    const float* a = ab;
+    const float* b = ab + plane;
+    const float* la1 = lam1;
+    const float* lb1 = lam1 + plane;
+    for (int i = tid; i < (kAY + 4) * (kAX + 4); i += kAX * kAY) {
+        const int y = i / (kAX + 4), x = i % (kAX + 4);
+        const int r = r0 - 2 + y, c = c0 - 2 + x;
+        sb[y][x] = (r >= 0 && r < H && c >= 0 && c < W) ? b[(size_t)r * pitch + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = tid; i < (kAY + 2) * (kAX + 2); i += kAX * kAY) {
+        const int y = i / (kAX + 2), x = i % (kAX + 2);
+        const int r = r0 - 1 + y, c = c0 - 1 + x;
+        if (r < 0 || r >= H || c < 0 || c >= W) {
+#pragma unroll
+            for (int d = 0; d < 8; ++d) sc[d][y][x] = 0.0f;
+            continue;
+        }
+        const size_t j = (size_t)r * pitch + c;
+        float qd[8], bi[8], f[8];
+        float P = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            qd[d] = __ldg(q + d * plane + j);
+            bi[d] = sb[y + 1 + dir_dr(d)][x + 1 + dir_dc(d)];
+            const float xx = bi[d] * qd[d];
+            f[d] = 1.0f - xx;
+            P = fmaf(xx, 1.0f - P, P);
+        }
+        float pre[8], suf[8];
+        pre[0] = 1.0f;
+#pragma unroll
+        for (int d = 1; d < 8; ++d) pre[d] = pre[d - 1] * f[d - 1];
+        suf[7] = 1.0f;
+#pragma unroll
+        for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
+        const float la = __ldg(la1 + j), lb = __ldg(lb1 + j);
+        const float ln = la + lb;
+        const float lP = ln * (1.0f - __ldg(a + j));
+        const bool interior = (y >= 1 && y <= kAY && x >= 1 && x <= kAX);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const float loo = pre[d] * suf[d];
+            sc[d][y][x] = lP * qd[d] * loo;
+            if (interior) Gq[d * plane + j] += lP * bi[d] * loo;
+        }
+        if (interior) lam0[j] = la - ln * P;
+    }
+    __syncthreads();
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int r = r0 + y, c = c0 + x;
+    if (r >= H || c >= W) return;
+    const size_t j = (size_t)r * pitch + c;
+    float acc = pc * __ldg(lb1 + j);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) acc += sc[d][y + 1 - dir_dr(d)][x + 1 - dir_dc(d)];  // target j = i - offset
+    lam0[plane + j] = acc;
+}
+
+}  // namespace
+
+void launch_diff_step(int H, int W, int pitch, float pc, const float* ab, float* abn, const float* q,
+                      cudaStream_t s) {
+    dim3 blk(64, 4);
+    dim3 grd((pitch + 63) / 64, (H + 3) / 4);
+    k_diff_step<<<grd, blk, 0, s>>>(H, W, pitch, pc, ab, abn, q);
+}
+
+void launch_ignition_map_diff(int H, int W, int pitch, const float* ab, const float* q, float* P, cudaStream_t s) {
+    const size_t n = (size_t)H * W;
+    k_ignition_map_diff<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(H, W, pitch, ab, q, P);
+}
+
+void launch_adjoint_step(int H, int W, int pitch, float pc, const float* ab, const float* q, const float* lam1,
+                         float* lam0, float* Gq, cudaStream_t s) {
+    dim3 blk(kAX, kAY);
+    dim3 grd((W + kAX - 1) / kAX, (H + kAY - 1) / kAY);
+    k_adjoint_step<<<grd, blk, 0, s>>>(H, W, pitch, pc, ab, q, lam1, lam0, Gq);
+}
+
+}  // namespace pf

@@ -1,0 +1,245 @@
+// Discrete stochastic step (Sec. 2.2 transition rules, Eq. 9): uint8 states packed
+// four per 32-bit word, SWAR "any neighbour burning" tests, Philox draws taken only
+// for cells that can change.
+//   - k_discrete_step: the plain one-launch-per-step kernel (global memory only).
+//   - k_discrete_blocked: TMA-staged tile + halo, k steps per launch in shared memory.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace pf {
+
+namespace {
+
+// Burning flags (bit 0 of each byte) of cells c-1 .. c+4 of one row, as bytes 0..5 of
+// a 64-bit word, from the word at c..c+3 and its left / right neighbour words.
+__device__ __forceinline__ uint64_t row_burning(uint32_t left, uint32_t mid, uint32_t right) {
+    const uint64_t ext = (uint64_t)(left >> 24) | ((uint64_t)mid << 8) | ((uint64_t)(right & 0xffu) << 40);
+    return (ext >> 1) & ~ext & 0x0101010101010101ull;
+}
+
+// New value of the 4 cells of word `mid` (row r, columns col0..col0+3 of the grid).
+// U/C/D are the burning flags of the rows above / at / below (row_burning layout).
+__device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64_t C, uint64_t D, int r,
+                                                int col0, size_t qoff, size_t qplane, const float* __restrict__ q,
+                                                const DiscreteArgs& g, uint32_t run, uint32_t step) {
+    const uint64_t all3 = U | C | D;
+    const uint64_t nb64 = (all3 << 8) | (all3 >> 8) | U | D;  // neighbours of byte positions 1..4
+    const uint32_t nb = (uint32_t)(nb64 >> 8) & 0x01010101u;
+    const uint32_t burning = lanes_eq2(mid);
+    const uint32_t active = burning | (nb & lanes_eq1(mid));
+    if (active == 0u) return mid;
+    uint32_t out = mid;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (((active >> (8 * k)) & 1u) == 0u) continue;
+        const uint32_t s = (mid >> (8 * k)) & 0xffu;
+        const int col = col0 + k;
+        const uint32_t cell = (uint32_t)r * (uint32_t)g.W + (uint32_t)col;
+        uint32_t ns;
+        if (s == 1u) {
+            // Eq. 9 over the burning neighbours, as P <- P + x (1 - P)
+            float P = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const uint64_t row = dir_dr(d) < 0 ? U : (dir_dr(d) == 0 ? C : D);
+                if ((row >> (8 * (k + 1 + dir_dc(d)))) & 1ull) {
+                    const float x = __ldg(q + (size_t)d * qplane + qoff + k);
+                    P = fmaf(x, 1.0f - P, P);
+                }
+            }
+            const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
+            ns = (u24(x.x) < P) ? 2u : 1u;
+        } else {
+            const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
+            ns = (u24(x.y) < g.p_continue) ? 2u : 3u;
+        }
+        out = (out & ~(0xffu << (8 * k))) | (ns << (8 * k));
+    }
+    return out;
+}
+
+__global__ void __launch_bounds__(256) k_discrete_step(DiscreteArgs g, const uint8_t* __restrict__ S,
+                                                       uint8_t* __restrict__ Sn, const float* __restrict__ q,
+                                                       uint32_t step) {
+    const int wpr = g.pitch >> 2;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)g.R * g.H * wpr;
+    if (idx >= total) return;
+    const int w = (int)(idx % wpr);
+    const size_t rowid = idx / wpr;
+    const int r = (int)(rowid % g.H);
+    const int rr = (int)(rowid / g.H);
+    const uint32_t* base = reinterpret_cast<const uint32_t*>(S + (size_t)rr * g.H * g.pitch);
+    auto ld = [&](int y, int x) -> uint32_t {
+        return (y >= 0 && y < g.H && x >= 0 && x < wpr) ? __ldg(base + (size_t)y * wpr + x) : 0u;
+    };
+    const uint32_t mid = ld(r, w);
+    const uint64_t U = row_burning(ld(r - 1, w - 1), ld(r - 1, w), ld(r - 1, w + 1));
+    const uint64_t C = row_burning(ld(r, w - 1), mid, ld(r, w + 1));
+    const uint64_t D = row_burning(ld(r + 1, w - 1), ld(r + 1, w), ld(r + 1, w + 1));
+    const uint32_t out = update_word(mid, U, C, D, r, 4 * w, (size_t)r * g.pitch + 4 * w, (size_t)g.H * g.pitch,
+                                     q, g, g.run0 + (uint32_t)rr, step);
+    reinterpret_cast<uint32_t*>(Sn + (size_t)rr * g.H * g.pitch)[(size_t)r * wpr + w] = out;
+}
+
+// ------------------------------------------------------------ temporal-blocked
+// Tile: kTW interior bytes x TH interior rows; the TMA box adds 16 bytes left and right
+// (TMA x offsets must be 16-byte multiples, so k <= 16) and k rows above and below.
+constexpr int kTW = 128;
+constexpr int kXH = 16;
+constexpr int kCT = kTW + 2 * kXH;  // 160 bytes per tile row
+constexpr int kCW = kCT / 4;        // 40 words per tile row
+constexpr int kBlkThreads = 256;
+
+__global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_constant__ CUtensorMap tin,
+                                                                  DiscreteArgs g, int TH, int KH,
+                                                                  uint8_t* __restrict__ Sn,
+                                                                  const float* __restrict__ q, uint32_t step0,
+                                                                  int k, int* __restrict__ err) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    // TMA destinations: round the dynamic shared-memory base up to 128 bytes (the
+    // allocation carries 128 bytes of slack for this)
+    uint8_t* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    __shared__ int any_burning;
+    const int RT = TH + 2 * KH;
+    const int tile_bytes = RT * kCT;
+    uint32_t* A = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* B = reinterpret_cast<uint32_t*>(smem + ((tile_bytes + 127) & ~127));
+    const int c0 = blockIdx.x * kTW;
+    const int r0 = blockIdx.y * TH;
+    const int rr = blockIdx.z;
+    if (threadIdx.x == 0) {
+        any_burning = 0;
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, (uint32_t)tile_bytes);
+        tma_load_3d(A, &tin, &bar, c0 - kXH, r0 - KH, rr);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, kErrTmaTimeout);
+            mbar_wait_bounded(&bar, 0);  // give the copy in flight one more budget
+        }
+        return;
+    }
+    // Copy A -> B so the ring the steps never write holds defined states, and find
+    // whether anything burns in the tile at all.
+    const int nwords = tile_bytes / 4;
+    int local_burn = 0;
+    for (int i = threadIdx.x; i < nwords; i += kBlkThreads) {
+        const uint32_t v = A[i];
+        B[i] = v;
+        local_burn |= (lanes_eq2(v) != 0u);
+    }
+    if (local_burn) any_burning = 1;
+    __syncthreads();
+    const size_t qplane = (size_t)g.H * g.pitch;
+    uint32_t* src = A;
+    uint32_t* dst = B;
+    if (any_burning) {
+        const int y_off = r0 - KH, x_off = c0 - kXH;
+        for (int s = 0; s < k; ++s) {
+            // rows / words that can still influence the interior after step s
+            const int y_lo = KH - k + 1 + s, y_hi = RT - y_lo;  // rows [y_lo, y_hi)
+            const int b_lo = kXH - k + 1 + s;                                   // first byte needed
+            int m_lo = b_lo >> 2, m_hi = (kCT - 1 - b_lo) >> 2;
+            m_lo = m_lo < 1 ? 1 : m_lo;
+            m_hi = m_hi > kCW - 2 ? kCW - 2 : m_hi;
+            const int nm = m_hi - m_lo + 1, ny = y_hi - y_lo;
+            const uint32_t step = step0 + (uint32_t)s;
+            for (int i = threadIdx.x; i < nm * ny; i += kBlkThreads) {
+                const int y = y_lo + i / nm, m = m_lo + i % nm;
+                const uint32_t* ru = src + (y - 1) * kCW;
+                const uint32_t* rc = src + y * kCW;
+                const uint32_t* rd = src + (y + 1) * kCW;
+                const uint32_t mid = rc[m];
+                const uint64_t U = row_burning(ru[m - 1], ru[m], ru[m + 1]);
+                const uint64_t C = row_burning(rc[m - 1], mid, rc[m + 1]);
+                const uint64_t D = row_burning(rd[m - 1], rd[m], rd[m + 1]);
+                const int gr = y_off + y, gc = x_off + 4 * m;
+                // states 1/2 exist only inside the grid, so gr/gc are valid whenever a
+                // cell is active; the q offset is formed but only read for such cells
+                const size_t qoff = (size_t)gr * g.pitch + gc;
+                dst[y * kCW + m] = update_word(mid, U, C, D, gr, gc, qoff, qplane, q, g, g.run0 + (uint32_t)rr, step);
+            }
+            __syncthreads();
+            uint32_t* t = src; src = dst; dst = t;
+        }
+    }
+    // store the interior rows [KH, KH + TH), bytes [16, 144) with 16-byte vectors
+    uint8_t* out = Sn + (size_t)rr * g.H * g.pitch;
+    const int vec_per_row = kTW / 16;
+    for (int i = threadIdx.x; i < TH * vec_per_row; i += kBlkThreads) {
+        const int y = i / vec_per_row, v = i % vec_per_row;
+        const int gr = r0 + y, gc = c0 + 16 * v;
+        if (gr >= g.H || gc >= g.pitch) continue;
+        const uint4 val = *reinterpret_cast<const uint4*>(reinterpret_cast<const uint8_t*>(src) + (KH + y) * kCT + kXH + 16 * v);
+        *reinterpret_cast<uint4*>(out + (size_t)gr * g.pitch + gc) = val;
+    }
+}
+
+__global__ void k_ignition_map_discrete(DiscreteArgs g, const uint8_t* __restrict__ S, const float* __restrict__ q,
+                                        float* __restrict__ P) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t HW = (size_t)g.H * g.W;
+    if (idx >= HW * g.R) return;
+    const int rr = (int)(idx / HW);
+    const size_t j = idx % HW;
+    const int r = (int)(j / g.W), c = (int)(j % g.W);
+    const uint8_t* s = S + (size_t)rr * g.H * g.pitch;
+    float p = 0.0f;
+    if (s[(size_t)r * g.pitch + c] == 1) {
+        for (int d = 0; d < 8; ++d) {
+            const int ri = r + dir_dr(d), ci = c + dir_dc(d);
+            if (ri < 0 || ri >= g.H || ci < 0 || ci >= g.W) continue;
+            if (s[(size_t)ri * g.pitch + ci] == 2) {
+                const float x = q[(size_t)d * g.H * g.pitch + (size_t)r * g.pitch + c];
+                p = fmaf(x, 1.0f - p, p);
+            }
+        }
+    }
+    P[idx] = p;
+}
+
+}  // namespace
+
+void launch_discrete_step(const DiscreteArgs& g, const uint8_t* S, uint8_t* Sn, const float* q, uint32_t step,
+                          cudaStream_t s) {
+    const size_t total = (size_t)g.R * g.H * (g.pitch >> 2);
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    k_discrete_step<<<blocks, 256, 0, s>>>(g, S, Sn, q, step);
+}
+
+int discrete_blocked_tile_rows() { return 64; }
+
+size_t discrete_blocked_smem(int TH, int KH) {
+    const int tile_bytes = (TH + 2 * KH) * kCT;
+    return 2 * (size_t)((tile_bytes + 127) & ~127) + 128;
+}
+
+void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin, int TH, int KH, uint8_t* Sn,
+                                  const float* q, uint32_t step, int k, int* err, cudaStream_t s) {
+    const size_t smem = discrete_blocked_smem(TH, KH);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_discrete_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        attr_set = true;
+    }
+    dim3 grd((g.pitch + kTW - 1) / kTW, (g.H + TH - 1) / TH, g.R);
+    k_discrete_blocked<<<grd, kBlkThreads, smem, s>>>(*tin, g, TH, KH, Sn, q, step, k, err);
+}
+
+void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,
+                                  cudaStream_t s) {
+    const size_t total = (size_t)g.R * g.H * g.W;
+    k_ignition_map_discrete<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(g, S, q, P);
+}
+
+}  // namespace pf

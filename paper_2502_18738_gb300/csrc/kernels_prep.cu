@@ -1,0 +1,186 @@
+// Prep (Eq. 1-5): fold the static landscape, the wind epoch and the parameters into
+// eight per-cell directional ignition factors q[d][r][c] = f_p(p_propagate), and the
+// chain rule of that fold for the adjoint.
+#include "common.cuh"
+
+namespace pf {
+
+namespace {
+
+// Direction of travel from the burning neighbour to the receiving cell, counter-
+// clockwise from East (north = decreasing row): phi_d = atan2(dr, -dc). Stored as
+// (cos phi_d, sin phi_d) so that cos(theta_w - phi_d) needs one sincos per cell.
+__constant__ float kCosPhi[8] = {0.70710678118654752f, 0.0f, -0.70710678118654752f, 1.0f,
+                                 -1.0f, 0.70710678118654752f, 0.0f, -0.70710678118654752f};
+__constant__ float kSinPhi[8] = {-0.70710678118654752f, -1.0f, -0.70710678118654752f, 0.0f,
+                                 0.0f, 0.70710678118654752f, 1.0f, 0.70710678118654752f};
+
+constexpr float kRadToDeg = 57.295779513082320876f;
+
+struct CellFactors {
+    float G;      // (1 + p_veg)(1 + p_den)
+    float V;      // wind speed
+    float cw, sw; // cos / sin of the wind direction
+    float pv, pd;
+    float Ej;
+};
+
+__device__ __forceinline__ CellFactors load_cell(const PrepArgs& g, int r, int c) {
+    const size_t j = (size_t)r * g.W + c;
+    CellFactors f;
+    f.pv = g.pveg ? g.pveg[j] : 0.0f;
+    f.pd = g.pden ? g.pden[j] : 0.0f;
+    f.G = (1.0f + f.pv) * (1.0f + f.pd);
+    f.V = g.V ? g.V[j] : 0.0f;
+    float th = g.th ? g.th[j] : 0.0f;
+    sincospif(th * (1.0f / 180.0f), &f.sw, &f.cw);
+    f.Ej = g.E ? g.E[j] : 0.0f;
+    return f;
+}
+
+// Exponent of p_w * p_s (Eq. 3 and 4 combined) for direction d; returns false when the
+// neighbour lies outside the grid. Also returns theta_s (deg) and cos(theta) - 1.
+__device__ __forceinline__ bool dir_exponent(const PrepArgs& g, const CellFactors& f, int r, int c, int d,
+                                             float& expo, float& theta_s, float& cosm1) {
+    const int ri = r + dir_dr(d), ci = c + dir_dc(d);
+    if (ri < 0 || ri >= g.H || ci < 0 || ci >= g.W) return false;
+    float dE = 0.0f;
+    if (g.E) dE = f.Ej - g.E[(size_t)ri * g.W + ci];
+    const bool diag = (dir_dr(d) != 0) && (dir_dc(d) != 0);
+    const float kl = diag ? g.l * 1.41421356237309505f : g.l;
+    theta_s = atanf(dE / kl) * kRadToDeg;                              // Eq. 1 (degrees)
+    cosm1 = (f.cw * kCosPhi[d] + f.sw * kSinPhi[d]) - 1.0f;            // cos(theta_w - phi_d) - 1
+    expo = g.c1 * f.V + g.c2 * f.V * cosm1 + g.a * theta_s;            // Eq. 3 x Eq. 4
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_prep(PrepArgs g, float* __restrict__ q) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= g.H || c >= g.pitch) return;
+    const size_t plane = (size_t)g.H * g.pitch;
+    float* qo = q + (size_t)r * g.pitch + c;
+    if (c >= g.W || (g.burnable && g.burnable[(size_t)r * g.W + c] == 0)) {
+#pragma unroll
+        for (int d = 0; d < 8; ++d) qo[d * plane] = 0.0f;
+        return;
+    }
+    const CellFactors f = load_cell(g, r, c);
+    const float Gp = g.p_h * f.G;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        float expo, ts, cm1, v = 0.0f;
+        if (dir_exponent(g, f, r, c, d, expo, ts, cm1)) v = tanhf(kC * (Gp * expf(expo)));  // Eq. 2, 5
+        qo[d * plane] = v;
+    }
+}
+
+constexpr int kAdjThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One thread per cell (grid-stride, fixed assignment): the parameter partials are
+// accumulated per thread in FP32 over the 8 directions of a cell and in FP64 across
+// cells, reduced by warp shuffles and then across the block, and written as one FP64
+// row per block. Per-cell gradients are accumulated into gpveg / gpden.
+__global__ void __launch_bounds__(kAdjThreads) k_prep_adjoint(PrepArgs g, const float* __restrict__ Gq,
+                                                              double* __restrict__ partials,
+                                                              float* __restrict__ gpveg,
+                                                              float* __restrict__ gpden) {
+    const size_t plane = (size_t)g.H * g.pitch;
+    const size_t HW = (size_t)g.H * g.W;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (size_t j = (size_t)blockIdx.x * kAdjThreads + threadIdx.x; j < HW; j += (size_t)gridDim.x * kAdjThreads) {
+        const int r = (int)(j / g.W), c = (int)(j % g.W);
+        if (g.burnable && g.burnable[j] == 0) continue;
+        const CellFactors f = load_cell(g, r, c);
+        const float* gq = Gq + (size_t)r * g.pitch + c;
+        float sh = 0.f, s1 = 0.f, s2 = 0.f, sa = 0.f, se = 0.f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            float expo, ts, cm1;
+            if (!dir_exponent(g, f, r, c, d, expo, ts, cm1)) continue;
+            const float e = expf(expo);
+            const float pp = g.p_h * f.G * e;
+            const float qq = tanhf(kC * pp);
+            const float gpp = gq[d * plane] * kC * ((1.0f - qq) * (1.0f + qq));  // tanh'
+            se += gpp * e;              // d pp / d(p_h (1+pv)(1+pd)) summed over d
+            sh += gpp * f.G * e;        // d pp / d p_h
+            s1 += gpp * pp * f.V;       // d pp / d c1
+            s2 += gpp * pp * f.V * cm1; // d pp / d c2
+            sa += gpp * pp * ts;        // d pp / d a
+        }
+        acc[0] += sh; acc[1] += s1; acc[2] += s2; acc[3] += sa;
+        if (gpveg) gpveg[j] += se * g.p_h * (1.0f + f.pd);
+        if (gpden) gpden[j] += se * g.p_h * (1.0f + f.pv);
+    }
+    __shared__ double red[kAdjThreads / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double v = warp_sum(acc[k]);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < kAdjThreads / 32; ++w) s += red[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+constexpr int kRedThreads = 512;
+
+// Fixed-order FP64 sum of the block partials: thread t sums rows t, t+512, ... in order,
+// then a fixed shuffle/shared-memory tree; bit-reproducible for a given nblk.
+__global__ void __launch_bounds__(kRedThreads) k_reduce_partials(const double* __restrict__ partials, int nblk,
+                                                                 double* __restrict__ acc) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblk; b += kRedThreads)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s[k] += partials[(size_t)b * 4 + k];
+    __shared__ double red[kRedThreads / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double v = warp_sum(s[k]);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) t += red[w][threadIdx.x];
+        acc[threadIdx.x] += t;
+    }
+}
+
+}  // namespace
+
+void launch_prep(const PrepArgs& g, float* q, cudaStream_t s) {
+    dim3 blk(64, 4);
+    dim3 grd((g.pitch + blk.x - 1) / blk.x, (g.H + blk.y - 1) / blk.y);
+    k_prep<<<grd, blk, 0, s>>>(g, q);
+}
+
+int prep_adjoint_blocks(int H, int W) {
+    const size_t HW = (size_t)H * W;
+    size_t want = (HW + kAdjThreads - 1) / kAdjThreads;
+    const size_t cap = 152 * 8;  // 8 resident blocks per SM on 152 SMs
+    return (int)(want < cap ? (want ? want : 1) : cap);
+}
+
+void launch_prep_adjoint(const PrepArgs& g, const float* Gq, double* partials, float* gpveg, float* gpden,
+                         cudaStream_t s) {
+    const int nblk = prep_adjoint_blocks(g.H, g.W);
+    k_prep_adjoint<<<nblk, kAdjThreads, 0, s>>>(g, Gq, partials, gpveg, gpden);
+}
+
+void launch_reduce_partials(const double* partials, int nblk, double* acc, cudaStream_t s) {
+    k_reduce_partials<<<1, kRedThreads, 0, s>>>(partials, nblk, acc);
+}
+
+}  // namespace pf

@@ -1,0 +1,910 @@
+// libpfire C ABI: context, buffers, wind epochs, checkpointed reverse sweep, dispatch.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "pfire.h"
+#include "tma.cuh"
+
+namespace pf {
+// small helper kernels (kernels_misc.cu)
+void launch_validate_fields(const float* x, size_t n, float lo, int bit, int* flags, cudaStream_t s);
+void launch_validate_states(const uint8_t* S, size_t n, int* flags, cudaStream_t s);
+void launch_diff_init(const uint8_t* S, int H, int W, int pitch, float* ab, uint8_t* burn, cudaStream_t s);
+void launch_bce(const float* a, const float* y, int64_t n, float* g, double* partials, int nblk, cudaStream_t s);
+int bce_blocks(int64_t n);
+}  // namespace pf
+
+using namespace pf;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+enum Kind { K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_PADJ, K_RED, K_MISC, K_NKINDS };
+const char* kKindNames[K_NKINDS] = {"prep",         "discrete_step", "discrete_blocked",
+                                    "diff_step",    "diff_blocked",  "adjoint_step",
+                                    "prep_adjoint", "reduce_fp64",   "misc"};
+
+struct Epoch {
+    int from;
+    float* V;   // dense H*W or nullptr (calm)
+    float* th;  // dense H*W or nullptr
+};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t e0, e1;
+};
+
+// Host-side allocation-failure injector: PF_FAULT_ALLOC=n makes the n-th device
+// allocation of the process fail with PF_ENOMEM (n >= 1).
+long g_alloc_count = 0;
+long fault_alloc_at() {
+    static long at = -2;
+    if (at == -2) {
+        const char* s = getenv("PF_FAULT_ALLOC");
+        at = s ? atol(s) : -1;
+    }
+    return at;
+}
+
+}  // namespace
+
+struct pf_ctx {
+    int H = 0, W = 0, P = 0, form = 0, R = 1;
+    uint64_t seed = 0;
+    cudaStream_t st = nullptr;
+    float p_h = 0.58f, c1 = 0.045f, c2 = 0.131f, a = 0.078f, pc = 0.3f, l = 30.0f;
+    float *E = nullptr, *pveg = nullptr, *pden = nullptr;
+    std::vector<Epoch> winds;
+    // q cache
+    float* q = nullptr;
+    long q_key_epoch = -1;
+    long q_key_version = -1;
+    long version = 0;  // bumped whenever params / env / wind / mask change
+    // state
+    int step = 0;
+    uint8_t* S[2] = {nullptr, nullptr};  // discrete [R][H][P]
+    int scur = 0;
+    float* work[2] = {nullptr, nullptr};  // diff [2][H][P]
+    float* cur_ab = nullptr;              // where the current diff state lives
+    uint8_t* burn = nullptr;              // diff burnable mask, dense H*W
+    // tape (diff)
+    bool tape_valid = false;
+    int tape_start = 0;
+    int K = 1;
+    std::vector<std::pair<int, float*>> ckpts;  // (step, slot)
+    std::vector<float*> slot_pool;              // allocated slots, reused
+    size_t slots_used = 0;
+    float* tape_params[1] = {nullptr};
+    float t_p_h = 0, t_c1 = 0, t_c2 = 0, t_a = 0, t_pc = 0, t_l = 0;
+    long t_version = -1;
+    // adjoint
+    float* lam[2] = {nullptr, nullptr};
+    float* Gq = nullptr;
+    std::vector<float*> seg;
+    double* partials = nullptr;
+    double* gacc = nullptr;
+    // misc
+    int* dflags = nullptr;  // [0] device error word, [1..] validation flags
+    int* hflags = nullptr;  // pinned mirror
+    CUtensorMap tmapS[2];
+    bool tmap_ok = false;
+    int TH = 64, KH = 16;
+    pf_tuning tun{0, 0, 0, 0};
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    long long launches[K_NKINDS] = {0};
+    double prof_ms[K_NKINDS] = {0};
+    std::vector<void*> allocs;
+    std::string err = "no error";
+};
+
+namespace {
+
+int fail(pf_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    g_last_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, PF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+int dalloc(pf_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    ++g_alloc_count;
+    const long at = fault_alloc_at();
+    if (at > 0 && g_alloc_count == at)
+        return fail(ctx, PF_ENOMEM, "injected allocation failure (PF_FAULT_ALLOC=%ld)", at);
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, PF_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(*p);
+    return PF_OK;
+}
+
+void dfree(pf_ctx* ctx, void* p) {
+    if (!p) return;
+    auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+    if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+    cudaFree(p);
+}
+
+size_t plane_elems(const pf_ctx* c) { return (size_t)c->H * c->P; }
+size_t diff_state_bytes(const pf_ctx* c) { return 2 * plane_elems(c) * sizeof(float); }
+
+// ------------------------------------------------------------- profiling
+struct LaunchScope {
+    pf_ctx* c;
+    int kind;
+    cudaEvent_t e1 = nullptr;
+    LaunchScope(pf_ctx* c_, int k) : c(c_), kind(k) {
+        c->launches[k] += 1;
+        if (!c->tun.profile) return;
+        cudaEvent_t e0 = take();
+        e1 = take();
+        cudaEventRecord(e0, c->st);
+        c->prof.push_back({k, e0, e1});
+    }
+    ~LaunchScope() {
+        if (e1) cudaEventRecord(e1, c->st);
+    }
+    cudaEvent_t take() {
+        if (!c->ev_pool.empty()) {
+            cudaEvent_t e = c->ev_pool.back();
+            c->ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
+void prof_collect(pf_ctx* c) {
+    for (auto& r : c->prof) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) c->prof_ms[r.kind] += ms;
+        c->ev_pool.push_back(r.e0);
+        c->ev_pool.push_back(r.e1);
+    }
+    c->prof.clear();
+    cudaGetLastError();
+}
+
+int check_launch(pf_ctx* ctx, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, PF_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+    return PF_OK;
+}
+
+// ------------------------------------------------------------- TMA maps
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+bool encode_state_map(pf_ctx* c, CUtensorMap* m, uint8_t* base) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)c->P, (cuuint64_t)c->H, (cuuint64_t)c->R};
+    cuuint64_t strides[2] = {(cuuint64_t)c->P, (cuuint64_t)c->P * c->H};
+    cuuint32_t box[3] = {160u, (cuuint32_t)(c->TH + 2 * c->KH), 1u};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------- q cache
+int epoch_of(const pf_ctx* c, int t) {
+    int e = 0;
+    for (size_t i = 0; i < c->winds.size(); ++i)
+        if (t >= c->winds[i].from) e = (int)i;
+    return e;
+}
+
+int next_epoch_start(const pf_ctx* c, int t) {
+    for (auto& w : c->winds)
+        if (w.from > t) return w.from;
+    return 0x7fffffff;
+}
+
+PrepArgs prep_args(const pf_ctx* c, int e, bool use_tape_params) {
+    PrepArgs g;
+    g.H = c->H; g.W = c->W; g.pitch = c->P;
+    g.E = c->E; g.pveg = c->pveg; g.pden = c->pden;
+    g.V = c->winds[e].V; g.th = c->winds[e].th;
+    g.burnable = (c->form == PF_DIFF) ? c->burn : nullptr;
+    if (use_tape_params) {
+        g.p_h = c->t_p_h; g.c1 = c->t_c1; g.c2 = c->t_c2; g.a = c->t_a; g.l = c->t_l;
+    } else {
+        g.p_h = c->p_h; g.c1 = c->c1; g.c2 = c->c2; g.a = c->a; g.l = c->l;
+    }
+    return g;
+}
+
+int ensure_q(pf_ctx* ctx, int e) {
+    if (ctx->q_key_epoch == e && ctx->q_key_version == ctx->version) return PF_OK;
+    {
+        LaunchScope ls(ctx, K_PREP);
+        launch_prep(prep_args(ctx, e, false), ctx->q, ctx->st);
+    }
+    int rc = check_launch(ctx, "prep");
+    if (rc) return rc;
+    ctx->q_key_epoch = e;
+    ctx->q_key_version = ctx->version;
+    return PF_OK;
+}
+
+int sync_flags(pf_ctx* ctx, int n) {
+    CK(cudaMemcpyAsync(ctx->hflags, ctx->dflags, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return PF_OK;
+}
+
+int device_error(pf_ctx* ctx) {
+    int rc = sync_flags(ctx, 1);
+    if (rc) return rc;
+    if (ctx->hflags[0] != 0) {
+        const int code = ctx->hflags[0];
+        CK(cudaMemsetAsync(ctx->dflags, 0, sizeof(int), ctx->st));
+        return fail(ctx, PF_ETIMEOUT, "a bounded device wait ran out (device code %d)", code);
+    }
+    return PF_OK;
+}
+
+// ------------------------------------------------------------- kernel choice
+int choose_kernel(const pf_ctx* c) {
+    if (c->tun.kernel == 1) return 1;
+    if (c->tun.kernel == 2) return (c->form == PF_DISCRETE && c->tmap_ok) ? 2 : 1;
+    // automatic: the blocked kernel when its tensor maps exist
+    return (c->form == PF_DISCRETE && c->tmap_ok) ? 2 : 1;
+}
+
+int blocked_k(const pf_ctx* c) {
+    int k = c->tun.k > 0 ? c->tun.k : 8;
+    return std::min(k, c->KH);
+}
+
+// ------------------------------------------------------------- discrete runs
+DiscreteArgs dargs(const pf_ctx* c) {
+    DiscreteArgs g;
+    g.H = c->H; g.W = c->W; g.pitch = c->P; g.R = c->R;
+    g.p_continue = c->pc;
+    g.key0 = (uint32_t)c->seed; g.key1 = (uint32_t)(c->seed >> 32);
+    g.fire = 0; g.run0 = 0;
+    return g;
+}
+
+int run_discrete(pf_ctx* ctx, int T) {
+    const DiscreteArgs g = dargs(ctx);
+    const int kern = choose_kernel(ctx);
+    int t = ctx->step;
+    const int end = ctx->step + T;
+    while (t < end) {
+        const int e = epoch_of(ctx, t);
+        int rc = ensure_q(ctx, e);
+        if (rc) return rc;
+        int n = std::min(end - t, next_epoch_start(ctx, t) - t);
+        const int src = ctx->scur, dst = 1 - ctx->scur;
+        if (kern == 2) {
+            n = std::min(n, blocked_k(ctx));
+            LaunchScope ls(ctx, K_DBLK);
+            launch_discrete_blocked_impl(g, &ctx->tmapS[src], ctx->TH, ctx->KH, ctx->S[dst], ctx->q, (uint32_t)t, n,
+                                         ctx->dflags, ctx->st);
+        } else {
+            n = 1;
+            LaunchScope ls(ctx, K_DSTEP);
+            launch_discrete_step(g, ctx->S[src], ctx->S[dst], ctx->q, (uint32_t)t, ctx->st);
+        }
+        rc = check_launch(ctx, "discrete step");
+        if (rc) return rc;
+        ctx->scur = dst;
+        t += n;
+    }
+    ctx->step = end;
+    return PF_OK;
+}
+
+// ------------------------------------------------------------- diff runs
+float* take_slot(pf_ctx* ctx, int* rc) {
+    *rc = PF_OK;
+    if (ctx->slots_used < ctx->slot_pool.size()) return ctx->slot_pool[ctx->slots_used++];
+    void* p = nullptr;
+    *rc = dalloc(ctx, &p, diff_state_bytes(ctx));
+    if (*rc) return nullptr;
+    ctx->slot_pool.push_back((float*)p);
+    ctx->slots_used++;
+    return (float*)p;
+}
+
+bool is_ckpt_step(const pf_ctx* c, int t) {
+    if ((t - c->tape_start) % c->K == 0) return true;
+    for (auto& w : c->winds)
+        if (w.from == t) return true;
+    return false;
+}
+
+int choose_K(pf_ctx* ctx, int T) {
+    if (ctx->tun.K > 0) return ctx->tun.K;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    const double budget = 0.6 * (double)(free_b + ctx->slot_pool.size() * diff_state_bytes(ctx));
+    const double sb = (double)diff_state_bytes(ctx);
+    const int ne = (int)ctx->winds.size();
+    if ((double)(T + 1 + ne) * sb <= budget) return 1;  // keep every state: no recomputation
+    int K = std::max(2, (int)std::ceil(std::sqrt((double)T)));
+    return K;
+}
+
+int diff_steps(pf_ctx* ctx, int T) {
+    const int end = ctx->step + T;
+    while (ctx->step < end) {
+        const int t = ctx->step;
+        int rc = ensure_q(ctx, epoch_of(ctx, t));
+        if (rc) return rc;
+        float* out;
+        if (ctx->tape_valid && is_ckpt_step(ctx, t + 1)) {
+            out = take_slot(ctx, &rc);
+            if (rc) return rc;
+            ctx->ckpts.push_back({t + 1, out});
+        } else {
+            out = (ctx->cur_ab == ctx->work[0]) ? ctx->work[1] : ctx->work[0];
+        }
+        {
+            LaunchScope ls(ctx, K_FSTEP);
+            launch_diff_step(ctx->H, ctx->W, ctx->P, ctx->pc, ctx->cur_ab, out, ctx->q, ctx->st);
+        }
+        rc = check_launch(ctx, "diff step");
+        if (rc) return rc;
+        ctx->cur_ab = out;
+        ctx->step = t + 1;
+    }
+    return PF_OK;
+}
+
+void tape_reset(pf_ctx* ctx) {
+    ctx->tape_valid = false;
+    ctx->ckpts.clear();
+    ctx->slots_used = 0;
+}
+
+// Start a fresh tape at the current step with the current state as checkpoint 0.
+int tape_begin(pf_ctx* ctx, int T) {
+    tape_reset(ctx);
+    ctx->K = choose_K(ctx, T);
+    ctx->tape_start = ctx->step;
+    ctx->t_p_h = ctx->p_h; ctx->t_c1 = ctx->c1; ctx->t_c2 = ctx->c2; ctx->t_a = ctx->a;
+    ctx->t_pc = ctx->pc; ctx->t_l = ctx->l;
+    ctx->t_version = ctx->version;
+    int rc;
+    float* s0 = take_slot(ctx, &rc);
+    if (rc) return rc;
+    if (ctx->cur_ab != s0)
+        CK(cudaMemcpyAsync(s0, ctx->cur_ab, diff_state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->st));
+    ctx->cur_ab = s0;
+    ctx->ckpts.push_back({ctx->step, s0});
+    ctx->tape_valid = true;
+    return PF_OK;
+}
+
+int write_diff_out(pf_ctx* ctx, void* out) {
+    if (!out) return PF_OK;
+    CK(cudaMemcpy2DAsync(out, sizeof(float) * ctx->W, ctx->cur_ab, sizeof(float) * ctx->P, sizeof(float) * ctx->W,
+                         2 * (size_t)ctx->H, cudaMemcpyDeviceToDevice, ctx->st));
+    return PF_OK;
+}
+
+int write_discrete_out(pf_ctx* ctx, void* out) {
+    if (!out) return PF_OK;
+    CK(cudaMemcpy2DAsync(out, ctx->W, ctx->S[ctx->scur], ctx->P, ctx->W, (size_t)ctx->R * ctx->H,
+                         cudaMemcpyDeviceToDevice, ctx->st));
+    return PF_OK;
+}
+
+int validate_states(pf_ctx* ctx, const uint8_t* S, size_t n) {
+    CK(cudaMemsetAsync(ctx->dflags + 1, 0, sizeof(int), ctx->st));
+    {
+        LaunchScope ls(ctx, K_MISC);
+        launch_validate_states(S, n, ctx->dflags + 1, ctx->st);
+    }
+    int rc = check_launch(ctx, "validate states");
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->hflags + 1, ctx->dflags + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (ctx->hflags[1]) return fail(ctx, PF_EINVAL, "state array holds codes other than 0..3");
+    return PF_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* pf_version(void) { return "libpfire 0.1 (sm_103a)"; }
+
+const char* pf_last_error(const pf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
+
+int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t seed, void* cuda_stream) {
+    if (!out) return fail(nullptr, PF_EINVAL, "pf_create: out is NULL");
+    *out = nullptr;
+    if (H < 1 || W < 1 || H > 65536 || W > 65536)
+        return fail(nullptr, PF_EINVAL, "pf_create: grid %dx%d outside 1..65536", H, W);
+    if (form != PF_DISCRETE && form != PF_DIFF) return fail(nullptr, PF_EINVAL, "pf_create: unknown form %d", form);
+    if (realisations < 1) return fail(nullptr, PF_EINVAL, "pf_create: realisations must be >= 1");
+    if (form == PF_DIFF && realisations != 1)
+        return fail(nullptr, PF_EINVAL, "pf_create: the differentiable form takes realisations = 1");
+    if ((uint64_t)H * (uint64_t)W * (uint64_t)realisations >= (1ull << 32))
+        return fail(nullptr, PF_EINVAL, "pf_create: H*W*R must be below 2^32");
+    pf_ctx* ctx = new pf_ctx();
+    ctx->H = H; ctx->W = W; ctx->P = pitch_of(W); ctx->form = form; ctx->R = realisations;
+    ctx->seed = seed;
+    ctx->st = (cudaStream_t)cuda_stream;
+    ctx->winds.push_back({0, nullptr, nullptr});
+    int rc = PF_OK;
+    const size_t pe = plane_elems(ctx);
+#define ALLOC(ptr, bytes)                                         \
+    do {                                                          \
+        void* p_ = nullptr;                                       \
+        rc = dalloc(ctx, &p_, (bytes));                           \
+        if (rc) goto failed;                                      \
+        ptr = (decltype(ptr))p_;                                  \
+    } while (0)
+    ALLOC(ctx->q, 8 * pe * sizeof(float));
+    ALLOC(ctx->dflags, 16 * sizeof(int));
+    if (cudaMallocHost((void**)&ctx->hflags, 16 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(ctx, PF_ENOMEM, "pinned flag allocation failed");
+        goto failed;
+    }
+    if (cudaMemsetAsync(ctx->dflags, 0, 16 * sizeof(int), ctx->st) != cudaSuccess) goto cuda_failed;
+    if (form == PF_DISCRETE) {
+        const size_t sb = (size_t)realisations * pe;
+        ALLOC(ctx->S[0], sb);
+        ALLOC(ctx->S[1], sb);
+        if (cudaMemsetAsync(ctx->S[0], 0, sb, ctx->st) != cudaSuccess) goto cuda_failed;
+        if (cudaMemsetAsync(ctx->S[1], 0, sb, ctx->st) != cudaSuccess) goto cuda_failed;
+        ctx->tmap_ok = encode_state_map(ctx, &ctx->tmapS[0], ctx->S[0]) &&
+                       encode_state_map(ctx, &ctx->tmapS[1], ctx->S[1]);
+    } else {
+        ALLOC(ctx->work[0], diff_state_bytes(ctx));
+        ALLOC(ctx->work[1], diff_state_bytes(ctx));
+        ALLOC(ctx->burn, (size_t)H * W);
+        if (cudaMemsetAsync(ctx->work[0], 0, diff_state_bytes(ctx), ctx->st) != cudaSuccess) goto cuda_failed;
+        if (cudaMemsetAsync(ctx->work[1], 0, diff_state_bytes(ctx), ctx->st) != cudaSuccess) goto cuda_failed;
+        if (cudaMemsetAsync(ctx->burn, 1, (size_t)H * W, ctx->st) != cudaSuccess) goto cuda_failed;
+        ctx->cur_ab = ctx->work[0];
+    }
+    if (cudaStreamSynchronize(ctx->st) != cudaSuccess) goto cuda_failed;
+    *out = ctx;
+    return PF_OK;
+cuda_failed:
+    rc = fail(ctx, PF_ECUDA, "pf_create: %s", cudaGetErrorString(cudaGetLastError()));
+failed : {
+    std::string msg = ctx->err;
+    pf_destroy(ctx);
+    g_last_error = msg;
+    return rc;
+}
+#undef ALLOC
+}
+
+void pf_destroy(pf_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->st);
+    for (auto& r : ctx->prof) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->hflags) cudaFreeHost(ctx->hflags);
+    cudaGetLastError();
+    delete ctx;
+}
+
+int pf_set_params(pf_ctx* ctx, float p_h, float c1, float c2, float a, float p_continue, float l_m) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_set_params: ctx is NULL");
+    const float v[6] = {p_h, c1, c2, a, p_continue, l_m};
+    for (float x : v)
+        if (!std::isfinite(x)) return fail(ctx, PF_EINVAL, "pf_set_params: non-finite parameter");
+    if (p_h < 0.f) return fail(ctx, PF_EINVAL, "pf_set_params: p_h must be >= 0");
+    if (p_continue < 0.f || p_continue > 1.f) return fail(ctx, PF_EINVAL, "pf_set_params: p_continue outside [0,1]");
+    if (!(l_m > 0.f)) return fail(ctx, PF_EINVAL, "pf_set_params: l must be > 0");
+    ctx->p_h = p_h; ctx->c1 = c1; ctx->c2 = c2; ctx->a = a; ctx->pc = p_continue; ctx->l = l_m;
+    ctx->version++;
+    tape_reset(ctx);
+    return PF_OK;
+}
+
+static int copy_field(pf_ctx* ctx, float** dst, const float* src) {
+    const size_t bytes = (size_t)ctx->H * ctx->W * sizeof(float);
+    if (!src) {
+        if (*dst) dfree(ctx, *dst);
+        *dst = nullptr;
+        return PF_OK;
+    }
+    if (!*dst) {
+        void* p;
+        int rc = dalloc(ctx, &p, bytes);
+        if (rc) return rc;
+        *dst = (float*)p;
+    }
+    CK(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->st));
+    return PF_OK;
+}
+
+static int validate_fields(pf_ctx* ctx, const float* const* f, const float* lo, int n) {
+    const size_t cells = (size_t)ctx->H * ctx->W;
+    CK(cudaMemsetAsync(ctx->dflags + 1, 0, sizeof(int), ctx->st));
+    for (int i = 0; i < n; ++i) {
+        if (!f[i]) continue;
+        LaunchScope ls(ctx, K_MISC);
+        launch_validate_fields(f[i], cells, lo[i], i, ctx->dflags + 1, ctx->st);
+    }
+    int rc = check_launch(ctx, "validate fields");
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ctx->hflags + 1, ctx->dflags + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return ctx->hflags[1];
+}
+
+int pf_set_env(pf_ctx* ctx, const float* E, const float* p_veg, const float* p_den, const float* V_w,
+               const float* theta_w_deg) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_set_env: ctx is NULL");
+    const float* f[5] = {E, p_veg, p_den, V_w, theta_w_deg};
+    const float lo[5] = {-INFINITY, -1.0f, -1.0f, -INFINITY, -INFINITY};
+    const char* names[5] = {"E", "p_veg", "p_den", "V_w", "theta_w"};
+    int bad = validate_fields(ctx, f, lo, 5);
+    if (bad < 0) return bad;
+    if (bad) {
+        std::string which;
+        for (int i = 0; i < 5; ++i)
+            if (bad & (1 << i)) which += std::string(which.empty() ? "" : ", ") + names[i];
+        return fail(ctx, PF_EINVAL, "pf_set_env: invalid values (NaN/inf, or p_veg/p_den < -1) in %s", which.c_str());
+    }
+    int rc;
+    if ((rc = copy_field(ctx, &ctx->E, E))) return rc;
+    if ((rc = copy_field(ctx, &ctx->pveg, p_veg))) return rc;
+    if ((rc = copy_field(ctx, &ctx->pden, p_den))) return rc;
+    for (size_t i = 1; i < ctx->winds.size(); ++i) {
+        dfree(ctx, ctx->winds[i].V);
+        dfree(ctx, ctx->winds[i].th);
+    }
+    ctx->winds.resize(1);
+    if ((rc = copy_field(ctx, &ctx->winds[0].V, V_w))) return rc;
+    if ((rc = copy_field(ctx, &ctx->winds[0].th, theta_w_deg))) return rc;
+    ctx->version++;
+    tape_reset(ctx);
+    return PF_OK;
+}
+
+int pf_set_wind(pf_ctx* ctx, const float* V_w, const float* theta_w_deg, int from_step) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_set_wind: ctx is NULL");
+    if (from_step <= ctx->winds.back().from)
+        return fail(ctx, PF_EINVAL, "pf_set_wind: from_step %d must exceed the last epoch's start %d", from_step,
+                    ctx->winds.back().from);
+    const float* f[2] = {V_w, theta_w_deg};
+    const float lo[2] = {-INFINITY, -INFINITY};
+    int bad = validate_fields(ctx, f, lo, 2);
+    if (bad < 0) return bad;
+    if (bad) return fail(ctx, PF_EINVAL, "pf_set_wind: NaN or infinite wind values");
+    Epoch e{from_step, nullptr, nullptr};
+    int rc;
+    if ((rc = copy_field(ctx, &e.V, V_w))) return rc;
+    if ((rc = copy_field(ctx, &e.th, theta_w_deg))) return rc;
+    ctx->winds.push_back(e);
+    if (ctx->tape_valid && from_step <= ctx->step) tape_reset(ctx);
+    return PF_OK;
+}
+
+int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t) {
+    if (!ctx || !t) return fail(ctx, PF_EINVAL, "pf_set_tuning: NULL argument");
+    if (t->kernel < 0 || t->kernel > 2) return fail(ctx, PF_EINVAL, "pf_set_tuning: kernel must be 0, 1 or 2");
+    if (t->k < 0 || t->k > 16) return fail(ctx, PF_EINVAL, "pf_set_tuning: k must be in 0..16");
+    if (t->K < 0) return fail(ctx, PF_EINVAL, "pf_set_tuning: K must be >= 0");
+    ctx->tun = *t;
+    return PF_OK;
+}
+
+int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t) {
+    if (!ctx || !t) return fail(nullptr, PF_EINVAL, "pf_get_tuning: NULL argument");
+    *t = ctx->tun;
+    t->kernel = choose_kernel(ctx);
+    if (t->k == 0) t->k = blocked_k(ctx);
+    if (t->K == 0) t->K = ctx->K;
+    return PF_OK;
+}
+
+int pf_forward(pf_ctx* ctx, const uint8_t* S_init, int T, void* S_out) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_forward: ctx is NULL");
+    if (!S_init) return fail(ctx, PF_EINVAL, "pf_forward: S_init is NULL");
+    if (T < 0) return fail(ctx, PF_EINVAL, "pf_forward: T must be >= 0");
+    const size_t n = (size_t)ctx->R * ctx->H * ctx->W;
+    int rc = validate_states(ctx, S_init, n);
+    if (rc) return rc;
+    ctx->step = 0;
+    if (ctx->form == PF_DISCRETE) {
+        ctx->scur = 0;
+        CK(cudaMemcpy2DAsync(ctx->S[0], ctx->P, S_init, ctx->W, ctx->W, (size_t)ctx->R * ctx->H,
+                             cudaMemcpyDeviceToDevice, ctx->st));
+        rc = run_discrete(ctx, T);
+        if (rc) return rc;
+        return write_discrete_out(ctx, S_out);
+    }
+    {
+        LaunchScope ls(ctx, K_MISC);
+        launch_diff_init(S_init, ctx->H, ctx->W, ctx->P, ctx->work[0], ctx->burn, ctx->st);
+    }
+    if ((rc = check_launch(ctx, "diff init"))) return rc;
+    ctx->cur_ab = ctx->work[0];
+    ctx->version++;  // the burnable mask is part of q
+    if ((rc = tape_begin(ctx, T))) return rc;
+    if ((rc = diff_steps(ctx, T))) return rc;
+    return write_diff_out(ctx, S_out);
+}
+
+int pf_advance(pf_ctx* ctx, int T, void* S_out) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_advance: ctx is NULL");
+    if (T < 0) return fail(ctx, PF_EINVAL, "pf_advance: T must be >= 0");
+    int rc;
+    if (ctx->form == PF_DISCRETE) {
+        if ((rc = run_discrete(ctx, T))) return rc;
+        return write_discrete_out(ctx, S_out);
+    }
+    if (!ctx->tape_valid || ctx->t_version != ctx->version) {
+        if ((rc = tape_begin(ctx, T))) return rc;
+    }
+    if ((rc = diff_steps(ctx, T))) return rc;
+    return write_diff_out(ctx, S_out);
+}
+
+int pf_get_state(pf_ctx* ctx, int* step, void* S) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_get_state: ctx is NULL");
+    if (step) *step = ctx->step;
+    if (!S) return PF_OK;
+    return ctx->form == PF_DISCRETE ? write_discrete_out(ctx, S) : write_diff_out(ctx, S);
+}
+
+int pf_set_state(pf_ctx* ctx, int step, const void* S) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_set_state: ctx is NULL");
+    if (!S || step < 0) return fail(ctx, PF_EINVAL, "pf_set_state: NULL state or negative step");
+    tape_reset(ctx);
+    if (ctx->form == PF_DISCRETE) {
+        int rc = validate_states(ctx, (const uint8_t*)S, (size_t)ctx->R * ctx->H * ctx->W);
+        if (rc) return rc;
+        CK(cudaMemcpy2DAsync(ctx->S[ctx->scur], ctx->P, S, ctx->W, ctx->W, (size_t)ctx->R * ctx->H,
+                             cudaMemcpyDeviceToDevice, ctx->st));
+    } else {
+        float* dst = (ctx->cur_ab == ctx->work[0]) ? ctx->work[1] : ctx->work[0];
+        CK(cudaMemcpy2DAsync(dst, sizeof(float) * ctx->P, S, sizeof(float) * ctx->W, sizeof(float) * ctx->W,
+                             2 * (size_t)ctx->H, cudaMemcpyDeviceToDevice, ctx->st));
+        ctx->cur_ab = dst;
+    }
+    ctx->step = step;
+    return PF_OK;
+}
+
+int pf_ignition_map(pf_ctx* ctx, float* P_out) {
+    if (!ctx || !P_out) return fail(ctx, PF_EINVAL, "pf_ignition_map: NULL argument");
+    int rc = ensure_q(ctx, epoch_of(ctx, ctx->step));
+    if (rc) return rc;
+    {
+        LaunchScope ls(ctx, K_MISC);
+        if (ctx->form == PF_DISCRETE)
+            launch_ignition_map_discrete(dargs(ctx), ctx->S[ctx->scur], ctx->q, P_out, ctx->st);
+        else
+            launch_ignition_map_diff(ctx->H, ctx->W, ctx->P, ctx->cur_ab, ctx->q, P_out, ctx->st);
+    }
+    return check_launch(ctx, "ignition map");
+}
+
+int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double grad_params[4], float* grad_pveg,
+                float* grad_pden) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_backward: ctx is NULL");
+    if (!grad_params) return fail(ctx, PF_EINVAL, "pf_backward: grad_params is NULL");
+    if (ctx->form != PF_DIFF) return fail(ctx, PF_ESTATE, "pf_backward: only the differentiable form has an adjoint");
+    if (!ctx->tape_valid || ctx->t_version != ctx->version)
+        return fail(ctx, PF_ESTATE, "pf_backward: no recorded differentiable run (call pf_forward first)");
+    const size_t pe = plane_elems(ctx);
+    const size_t sbytes = diff_state_bytes(ctx);
+    int rc;
+    // lazily allocated adjoint buffers
+    for (int i = 0; i < 2; ++i)
+        if (!ctx->lam[i]) {
+            void* p;
+            if ((rc = dalloc(ctx, &p, sbytes))) return rc;
+            ctx->lam[i] = (float*)p;
+        }
+    if (!ctx->Gq) {
+        void* p;
+        if ((rc = dalloc(ctx, &p, 8 * pe * sizeof(float)))) return rc;
+        ctx->Gq = (float*)p;
+    }
+    const int nblk = prep_adjoint_blocks(ctx->H, ctx->W);
+    if (!ctx->partials) {
+        void* p;
+        if ((rc = dalloc(ctx, &p, (size_t)nblk * 4 * sizeof(double) + 4 * sizeof(double)))) return rc;
+        ctx->partials = (double*)p;
+        ctx->gacc = ctx->partials + (size_t)nblk * 4;
+    }
+    const int segmax = ctx->K - 1;
+    while ((int)ctx->seg.size() < segmax) {
+        void* p;
+        if ((rc = dalloc(ctx, &p, sbytes))) return rc;
+        ctx->seg.push_back((float*)p);
+    }
+    // terminal adjoint
+    CK(cudaMemsetAsync(ctx->lam[0], 0, sbytes, ctx->st));
+    if (dL_da_T)
+        CK(cudaMemcpy2DAsync(ctx->lam[0], sizeof(float) * ctx->P, dL_da_T, sizeof(float) * ctx->W,
+                             sizeof(float) * ctx->W, ctx->H, cudaMemcpyDeviceToDevice, ctx->st));
+    if (dL_db_T)
+        CK(cudaMemcpy2DAsync(ctx->lam[0] + pe, sizeof(float) * ctx->P, dL_db_T, sizeof(float) * ctx->W,
+                             sizeof(float) * ctx->W, ctx->H, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemsetAsync(ctx->gacc, 0, 4 * sizeof(double), ctx->st));
+    const size_t cell_bytes = (size_t)ctx->H * ctx->W * sizeof(float);
+    if (grad_pveg) CK(cudaMemsetAsync(grad_pveg, 0, cell_bytes, ctx->st));
+    if (grad_pden) CK(cudaMemsetAsync(grad_pden, 0, cell_bytes, ctx->st));
+    CK(cudaMemsetAsync(ctx->Gq, 0, 8 * pe * sizeof(float), ctx->st));
+
+    const int T_end = ctx->step;
+    int lcur = 0;
+    int cur_e = -1;
+    auto flush = [&](int e) -> int {
+        {
+            LaunchScope ls(ctx, K_PADJ);
+            launch_prep_adjoint(prep_args(ctx, e, true), ctx->Gq, ctx->partials, grad_pveg, grad_pden, ctx->st);
+        }
+        int r = check_launch(ctx, "prep adjoint");
+        if (r) return r;
+        {
+            LaunchScope ls(ctx, K_RED);
+            launch_reduce_partials(ctx->partials, nblk, ctx->gacc, ctx->st);
+        }
+        if ((r = check_launch(ctx, "fp64 reduction"))) return r;
+        if (cudaMemsetAsync(ctx->Gq, 0, 8 * pe * sizeof(float), ctx->st) != cudaSuccess)
+            return fail(ctx, PF_ECUDA, "memset Gq failed");
+        return PF_OK;
+    };
+    const float pc = ctx->t_pc;
+    for (int si = (int)ctx->ckpts.size() - 1; si >= 0; --si) {
+        const int s0 = ctx->ckpts[si].first;
+        const int s1 = (si + 1 < (int)ctx->ckpts.size()) ? ctx->ckpts[si + 1].first : T_end;
+        if (s1 <= s0) continue;
+        const int e = epoch_of(ctx, s0);
+        if (e != cur_e) {
+            if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
+            cur_e = e;
+            // q of epoch e with the recorded parameters (the cache may hold another epoch)
+            {
+                LaunchScope ls(ctx, K_PREP);
+                launch_prep(prep_args(ctx, e, true), ctx->q, ctx->st);
+            }
+            if ((rc = check_launch(ctx, "prep"))) return rc;
+            ctx->q_key_epoch = -1;
+        }
+        // recompute states s0+1 .. s1-1 of the segment
+        std::vector<const float*> states;
+        states.push_back(ctx->ckpts[si].second);
+        for (int t = s0 + 1; t < s1; ++t) {
+            float* out = ctx->seg[t - s0 - 1];
+            {
+                LaunchScope ls(ctx, K_FSTEP);
+                launch_diff_step(ctx->H, ctx->W, ctx->P, pc, states.back(), out, ctx->q, ctx->st);
+            }
+            if ((rc = check_launch(ctx, "diff step (recompute)"))) return rc;
+            states.push_back(out);
+        }
+        for (int t = s1 - 1; t >= s0; --t) {
+            {
+                LaunchScope ls(ctx, K_ADJ);
+                launch_adjoint_step(ctx->H, ctx->W, ctx->P, pc, states[t - s0], ctx->q, ctx->lam[lcur],
+                                    ctx->lam[1 - lcur], ctx->Gq, ctx->st);
+            }
+            if ((rc = check_launch(ctx, "adjoint step"))) return rc;
+            lcur = 1 - lcur;
+        }
+    }
+    if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
+    CK(cudaMemcpyAsync(ctx->hflags + 4, ctx->gacc, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    if ((rc = device_error(ctx))) return rc;  // synchronises the stream
+    memcpy(grad_params, ctx->hflags + 4, 4 * sizeof(double));
+    return PF_OK;
+}
+
+int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* launches, double* ms, int reset) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_profile_read: ctx is NULL");
+    CK(cudaStreamSynchronize(ctx->st));
+    prof_collect(ctx);
+    int n = std::min(max_kinds, (int)K_NKINDS);
+    for (int i = 0; i < n; ++i) {
+        if (kinds) kinds[i] = kKindNames[i];
+        if (launches) launches[i] = ctx->launches[i];
+        if (ms) ms[i] = ctx->prof_ms[i];
+    }
+    if (reset)
+        for (int i = 0; i < K_NKINDS; ++i) {
+            ctx->launches[i] = 0;
+            ctx->prof_ms[i] = 0.0;
+        }
+    return n;
+}
+
+int pf_loss_bce(const float* a, const float* y, int64_t n, float* dL_da, double* loss, void* cuda_stream) {
+    if (!a || !y || n <= 0) return fail(nullptr, PF_EINVAL, "pf_loss_bce: NULL input or n <= 0");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int nblk = bce_blocks(n);
+    double* partials = nullptr;
+    static thread_local double* cached = nullptr;
+    static thread_local int cached_n = 0;
+    if (cached_n < nblk + 1) {
+        if (cached) cudaFree(cached);
+        if (cudaMalloc((void**)&cached, sizeof(double) * (nblk + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            cached = nullptr;
+            cached_n = 0;
+            return fail(nullptr, PF_ENOMEM, "pf_loss_bce: scratch allocation failed");
+        }
+        cached_n = nblk + 1;
+    }
+    partials = cached;
+    launch_bce(a, y, n, dL_da, partials, nblk, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, "pf_loss_bce: %s", cudaGetErrorString(e));
+    if (loss) {
+        double h = 0.0;
+        e = cudaMemcpyAsync(&h, partials + nblk, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, "pf_loss_bce: %s", cudaGetErrorString(e));
+        *loss = h;
+    }
+    return PF_OK;
+}
+
+int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
+    (void)jobs;
+    (void)n;
+    (void)cuda_stream;
+    return fail(nullptr, PF_ESTATE, "pf_batch_submit: not built yet");
+}
+
+}  // extern "C"

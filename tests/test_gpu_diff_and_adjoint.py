@@ -1,0 +1,143 @@
+"""GPU parity of the differentiable form and its adjoint against the oracle, through
+the C ABI: single steps on random states (1e-5 relative), trajectories (1e-4 relative
+after T), and gradients (1e-3 relative) for several checkpoint intervals."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from tests._util import PRM, cuda, set_landscape
+
+pytestmark = pytest.mark.gpu
+
+STEP_RTOL, STEP_ATOL = 1e-5, 1e-7
+RUN_RTOL, RUN_ATOL = 1e-4, 1e-6
+GRAD_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import paper_2502_18738_gb300 as pf
+    pf.build()
+    pf.load()
+    return pf
+
+
+def _close(got, want, rtol, atol):
+    err = np.abs(got - want)
+    ok = err <= rtol * np.abs(want) + atol
+    assert ok.all(), f"max err {err.max():.3g} at {np.unravel_index(np.argmax(err - rtol * np.abs(want)), err.shape)}"
+
+
+def _model(pf, orc, land, V, th, H, W, **kw):
+    p = {**PRM, **kw}
+    m = pf.FireModel(H, W, pf.PF_DIFF)
+    set_landscape(m, land, V, th)
+    m.set_params(**p)
+    return m, orc.Params(**p)
+
+
+@pytest.mark.parametrize("H,W", [(33, 47), (64, 64), (1, 50), (50, 1), (150, 260)])
+def test_single_step_random_states(pf, orc, H, W):
+    land = syn.make_landscape(H, W, 2)
+    V, th = syn.smooth_wind(H, W, 2, 0, sigma=6.0)
+    m, prm = _model(pf, orc, land, V, th, H, W)
+    S0 = np.where(land.burnable != 0, 1, 0).astype(np.uint8)
+    m.forward(cuda(S0), 0)  # sets the burnable mask
+    q = orc.prep(H, W, land.E, land.p_veg, land.p_den, V, th, prm, burnable=land.burnable)
+    a, b = syn.random_diff_state(H, W, 4, land.burnable)
+    m.set_state(3, cuda(np.stack([a, b])))
+    out = m.advance(1).cpu().numpy()
+    a1, b1 = orc.step_diff(a, b, q, prm.p_continue)
+    _close(out[0], a1, STEP_RTOL, STEP_ATOL)
+    _close(out[1], b1, STEP_RTOL, STEP_ATOL)
+    Pg = m.ignition_map()[0].cpu().numpy()
+    _, _, P = orc.step_diff(a, b, q, prm.p_continue, return_P=True)
+    _close(Pg, P, STEP_RTOL, STEP_ATOL)
+
+
+def _problem(H, W, T, seed, n_epochs=2):
+    land = syn.make_landscape(H, W, seed)
+    winds = [syn.smooth_wind(H, W, seed, e, sigma=8.0) for e in range(n_epochs)]
+    starts = [int(round(e * T / n_epochs)) for e in range(n_epochs)]
+    S0 = syn.initial_state(land, [(H // 2, W // 2), (H // 4, W // 3)])
+    return land, winds, starts, S0
+
+
+def _set_winds(m, winds, starts):
+    for (V, th), s in list(zip(winds, starts))[1:]:
+        m.set_wind(cuda(V), cuda(th), s)
+
+
+@pytest.mark.parametrize("H,W,T", [(96, 80, 60), (200, 170, 120)])
+def test_trajectory(pf, orc, H, W, T):
+    land, winds, starts, S0 = _problem(H, W, T, 6)
+    m, prm = _model(pf, orc, land, *winds[0], H, W)
+    _set_winds(m, winds, starts)
+    out = m.forward(cuda(S0), T).cpu().numpy()
+    a, b, _ = orc.diff_forward(land, winds, starts, prm, S0, T, keep_states=False)
+    _close(out[0], a, RUN_RTOL, RUN_ATOL)
+    _close(out[1], b, RUN_RTOL, RUN_ATOL)
+    assert a.max() > 0.9 and (a > 0.01).sum() > 100
+
+
+@pytest.mark.parametrize("K", [1, 7, 0])
+def test_gradients_match_oracle(pf, orc, K):
+    import torch
+    H, W, T = 72, 64, 48
+    land, winds, starts, S0 = _problem(H, W, T, 13)
+    m, prm = _model(pf, orc, land, *winds[0], H, W)
+    _set_winds(m, winds, starts)
+    m.set_tuning(K=K)
+    y = (orc.forward_discrete(S0, orc.prep(H, W, land.E, land.p_veg, land.p_den, *winds[0],
+                                            orc.Params(0.5, 0.05, 0.12, 0.08, 0.3)),
+                              0.3, seed=2, T=T) >= 2).astype(np.float32)
+    out = m.forward(cuda(S0), T)
+    a_T = out[0].contiguous()
+    g_a = torch.empty_like(a_T)
+    loss = pf.pf_loss_bce(a_T, cuda(y), g_a)
+    g_b = cuda(np.random.default_rng(0).standard_normal((H, W)).astype(np.float32) * 1e-3)
+    g4, gpv, gpd = m.backward(g_a, g_b)
+    # oracle
+    a, b, tape = orc.diff_forward(land, winds, starts, prm, S0, T)
+    L, gA = orc.bce(a, y)
+    assert loss == pytest.approx(L, rel=1e-5)
+    want4, wpv, wpd = orc.diff_backward(land, winds, starts, prm, S0, tape, gA, g_b.cpu().numpy().astype(np.float64))
+    for k in range(4):
+        assert g4[k] == pytest.approx(want4[k], rel=GRAD_RTOL), k
+    for got, want in ((gpv.cpu().numpy(), wpv), (gpd.cpu().numpy(), wpd)):
+        scale = np.abs(want).max()
+        assert np.all(np.abs(got - want) <= GRAD_RTOL * np.abs(want) + 1e-6 * scale)
+
+
+def test_gradient_reduction_is_deterministic(pf, orc):
+    import torch
+    H, W, T = 60, 70, 30
+    land, winds, starts, S0 = _problem(H, W, T, 17)
+    m, prm = _model(pf, orc, land, *winds[0], H, W)
+    _set_winds(m, winds, starts)
+    m.set_tuning(K=5)
+    res = []
+    for _ in range(2):
+        out = m.forward(cuda(S0), T)
+        g = torch.ones((H, W), device="cuda") * 1e-3
+        res.append(m.backward(g, None)[0])
+    assert res[0] == res[1]
+
+
+def test_autograd_function(pf, orc):
+    import torch
+    H, W, T = 40, 44, 20
+    land, winds, starts, S0 = _problem(H, W, T, 19, n_epochs=1)
+    m = pf.FireModel(H, W, pf.PF_DIFF)
+    V, th = winds[0]
+    params = torch.tensor([PRM["p_h"], PRM["c1"], PRM["c2"], PRM["a"]], dtype=torch.float64, requires_grad=True)
+    pv = cuda(land.p_veg).requires_grad_(True)
+    pd = cuda(land.p_den).requires_grad_(True)
+    a_T, b_T = pf.DiffFire.apply(m, cuda(S0), T, params, pv, pd, PRM["p_continue"], PRM["l"],
+                                 cuda(land.E), cuda(V), cuda(th))
+    (a_T.sum() + 0.5 * b_T.sum()).backward()
+    prm = orc.Params(**PRM)
+    a, b, tape = orc.diff_forward(land, winds, starts, prm, S0, T)
+    g4, gpv, gpd = orc.diff_backward(land, winds, starts, prm, S0, tape, np.ones((H, W)), 0.5 * np.ones((H, W)))
+    assert np.allclose(params.grad.numpy(), g4, rtol=GRAD_RTOL)
+    assert np.allclose(pv.grad.cpu().numpy(), gpv, rtol=GRAD_RTOL, atol=1e-5 * np.abs(gpv).max())

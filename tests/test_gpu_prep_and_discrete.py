@@ -1,0 +1,167 @@
+"""GPU parity of prep (Eq. 1-5, read through the ignition map on lattice states) and
+of the discrete step (Sec. 2.2, Eq. 9) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from tests._util import PRM, cuda, lattice_direction, lattice_state, set_landscape
+
+pytestmark = pytest.mark.gpu
+
+NEAR = 1e-6  # a draw within this distance of p_ignite may legitimately decide differently
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import paper_2502_18738_gb300 as pf
+    pf.build()
+    pf.load()
+    return pf
+
+
+def _setup(pf, orc, H, W, seed, R=1, form=0, wind="smooth", rng_seed=0, **kw):
+    land = syn.make_landscape(H, W, seed)
+    if wind == "smooth":
+        V, th = syn.smooth_wind(H, W, seed, 0, sigma=6.0)
+    else:
+        V, th = syn.uniform_wind(H, W, 5.0, 45.0)
+    p = {**PRM, **kw}
+    m = pf.FireModel(H, W, form, R, seed=rng_seed)
+    set_landscape(m, land, V, th)
+    m.set_params(**p)
+    prm = orc.Params(**p)
+    q = orc.prep(H, W, land.E, land.p_veg, land.p_den, V, th, prm)
+    return m, land, V, th, prm, q
+
+
+@pytest.mark.parametrize("H,W", [(37, 53), (16, 16), (1, 40), (40, 1), (130, 200)])
+def test_prep_matches_oracle_via_lattice_ignition_maps(pf, orc, H, W):
+    m, land, V, th, prm, q = _setup(pf, orc, H, W, seed=3)
+    worst = 0.0
+    for rho in range(3):
+        for gam in range(3):
+            S, on = lattice_state(H, W, rho, gam)
+            m.set_state(0, cuda(S))
+            P = m.ignition_map()[0].cpu().numpy().astype(np.float64)
+            d = lattice_direction(H, W, rho, gam)
+            rr, cc = np.nonzero(~on)
+            want = q[d[rr, cc], rr, cc]
+            got = P[rr, cc]
+            assert np.all(np.abs(got - want) <= 2e-6 * np.abs(want) + 1e-7), (rho, gam)
+            worst = max(worst, float(np.max(np.abs(got - want) / np.maximum(np.abs(want), 1e-30), initial=0)))
+    assert worst < 2e-6
+
+
+def _compare_step(S_in, gpu, ora, P, u, burning_pc_exact=True):
+    """Cells may differ only where the oracle flags a near-tie; returns (#diff, #flagged)."""
+    diff = gpu != ora
+    near = (S_in == 1) & (np.abs(u - P) < NEAR)
+    bad = diff & ~near
+    assert not bad.any(), f"{bad.sum()} cells differ without a near-tie, first at {np.argwhere(bad)[:3]}"
+    return int(diff.sum()), int(near.sum())
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("H,W,R", [(45, 77, 1), (64, 128, 3), (1, 33, 2), (29, 1, 1), (200, 300, 2)])
+def test_single_step_on_random_states(pf, orc, kernel, H, W, R):
+    seed = 0x5EEDF00D12345678
+    m, land, V, th, prm, q = _setup(pf, orc, H, W, seed=7, R=R, rng_seed=seed)
+    m.set_tuning(kernel=kernel, k=1)
+    flagged = 0
+    for step in (0, 5, 123456):
+        S = syn.random_state(H, W, seed=step + H, R=R)
+        m.set_state(step, cuda(S))
+        out = m.advance(1).cpu().numpy()
+        ora, P, u = orc.step_discrete(S, q, prm.p_continue, seed=seed, step=step, return_P=True)
+        _, f = _compare_step(S, out, ora, P, u)
+        flagged += f
+    assert flagged < 5
+
+
+@pytest.mark.parametrize("kernel,k", [(1, 1), (2, 1), (2, 3), (2, 8), (2, 16)])
+def test_small_plain_workload_trajectory(pf, orc, kernel, k):
+    """128 x 128, T = 200, uniform wind 5 m/s at 45 deg, one ignited centre cell,
+    Philox seed 0: the whole trajectory bit-exact (checked step by step against the
+    oracle's own trajectory)."""
+    c = syn.CONFIG1
+    H, W, T = c["H"], c["W"], c["T"]
+    land = syn.make_landscape(H, W, c["field_seed"])
+    V, th = syn.uniform_wind(H, W, c["V"], c["theta"])
+    S0 = syn.initial_state(land, [(H // 2, W // 2)])
+    p = {k_: c[k_] for k_ in ("p_h", "c1", "c2", "a", "p_continue", "l")}
+    prm = orc.Params(**p)
+    q = orc.prep(H, W, land.E, land.p_veg, land.p_den, V, th, prm)
+    states, Ps, us = orc.trajectory_discrete(S0, q, prm.p_continue, seed=c["seed"], T=T)
+    m = pf.FireModel(H, W, 0, 1, seed=c["seed"])
+    set_landscape(m, land, V, th)
+    m.set_params(**p)
+    m.set_tuning(kernel=kernel, k=k)
+    out = m.forward(cuda(S0), T).cpu().numpy()[0]
+    if not np.array_equal(out, states[T]):
+        # find the first step where a run from the oracle's state departs from it
+        for t in range(T):
+            m.set_state(t, cuda(states[t]))
+            g = m.advance(1).cpu().numpy()[0]
+            _compare_step(states[t], g, states[t + 1], Ps[t], us[t])
+        pytest.fail("trajectories differ although every single step agrees")
+    assert (out == 3).sum() + (out == 2).sum() > 50  # the fire did spread
+
+
+def test_forward_then_advance_equals_one_forward(pf, orc):
+    H, W, R = 70, 90, 4
+    m, land, V, th, prm, q = _setup(pf, orc, H, W, seed=9, R=R, rng_seed=77)
+    S0 = np.stack([syn.initial_state(land, [(35, 45), (10, 10 + r)]) for r in range(R)])
+    a = m.forward(cuda(S0), 37).cpu().numpy()
+    m.forward(cuda(S0), 20)
+    b = m.advance(17).cpu().numpy()
+    assert np.array_equal(a, b)
+    m.set_tuning(kernel=1)
+    c = m.forward(cuda(S0), 37).cpu().numpy()
+    assert np.array_equal(a, c)
+
+
+def test_realisations_use_their_run_index(pf, orc):
+    H, W, R = 40, 48, 3
+    m, land, V, th, prm, q = _setup(pf, orc, H, W, seed=4, R=R, rng_seed=11)
+    S0 = np.broadcast_to(syn.initial_state(land, [(20, 24)]), (R, H, W)).copy()
+    out = m.forward(cuda(S0), 15).cpu().numpy()
+    ref = orc.forward_discrete(S0, q, prm.p_continue, seed=11, T=15)
+    assert np.array_equal(out, ref)
+    assert not np.array_equal(out[0], out[1])
+
+
+def test_wind_epochs(pf, orc):
+    H, W = 50, 60
+    m, land, V, th, prm, q0 = _setup(pf, orc, H, W, seed=5, rng_seed=3)
+    V1, th1 = syn.smooth_wind(H, W, 5, 1, sigma=6.0)
+    m.set_wind(cuda(V1), cuda(th1), 6)
+    q1 = orc.prep(H, W, land.E, land.p_veg, land.p_den, V1, th1, prm)
+    S0 = syn.initial_state(land, [(25, 30)])
+    out = m.forward(cuda(S0), 14).cpu().numpy()[0]
+    s = orc.forward_discrete(S0, q0, prm.p_continue, seed=3, T=6)
+    s = orc.forward_discrete(s, q1, prm.p_continue, seed=3, T=8, step0=6)
+    assert np.array_equal(out, s)
+
+
+def test_invalid_inputs_are_rejected(pf, orc):
+    import torch
+    H, W = 8, 8
+    m = pf.FireModel(H, W, 0, 1)
+    bad = torch.full((H, W), -1.5, device="cuda")
+    with pytest.raises(pf.PFireError) as e:
+        m.set_env(p_veg=bad)
+    assert e.value.code == pf.PF_EINVAL
+    nan = torch.full((H, W), float("nan"), device="cuda")
+    with pytest.raises(pf.PFireError):
+        m.set_env(E=nan)
+    with pytest.raises(pf.PFireError):
+        m.set_params(0.5, 0.1, 0.1, 0.1, 1.5)
+    S = torch.full((1, H, W), 7, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pf.PFireError):
+        m.forward(S, 3)
+    with pytest.raises(pf.PFireError) as e:
+        pf.pf_create(0, 5)
+    assert e.value.code == pf.PF_EINVAL
+    with pytest.raises(pf.PFireError) as e:
+        m.backward()
+    assert e.value.code == pf.PF_ESTATE
