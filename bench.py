@@ -1,0 +1,340 @@
+"""Throughput benchmark of libpfire on one GB300 (or N replicas under torchrun).
+
+Workload (the 8192 x 8192 large-scale configuration): 67M-cell grid, l = 30 m, T = 2000
+steps, differentiable (continuous-state, FP32) form, per-cell wind resampled every 100
+steps (20 epochs), one ignited centre cell plus 4 random ones, BCE of the final burn
+probability against a synthetic target, forward + adjoint with checkpointing, FP64
+parameter-gradient reduction. One bench step = pf_forward + pf_loss_bce + pf_backward.
+
+metric: cell-updates/s of forward + adjoint (H * W * T per step, every cell counted).
+Also reported: forward-only cell-updates/s, the plain one-launch-per-step kernels as
+the comparator, the roofline of the dominant kernel, the oracle on the host cores,
+clocks during the timed region, and the end-to-end rate through the C ABI with host
+buffers (inputs copied in and gradients copied out inside the timed region).
+
+--impl reference times the FP64 CPU oracle (the reference arm: there is no reference
+implementation to install) on a bounded crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+H = W = 8192
+T = 2000
+EPOCH_STEPS = 100
+FIELD_SEED = 5
+PHILOX_SEED = 5
+PARAMS = dict(p_h=0.58, c1=0.045, c2=0.131, a=0.078, p_continue=0.3, l=30.0)
+HIDDEN = dict(p_h=0.5, c1=0.05, c2=0.12, a=0.08)
+METRIC = "cell-updates/s fwd+adjoint (8192^2 diff form, T=2000)"
+WORKLOAD = "8192x8192 differentiable fwd+adjoint, T=2000, wind resampled every 100 steps"
+B_FWD, B_ADJ = 16, 24  # algorithmic bytes per cell-step: (a, b) in + out; state, lambda in, lambda out
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_inputs(H, W, T, seed):
+    land = syn.make_landscape(H, W, seed)
+    n_ep = (T + EPOCH_STEPS - 1) // EPOCH_STEPS
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        winds = list(ex.map(lambda e: syn.smooth_wind(H, W, seed, e), range(n_ep)))
+    ign = [(H // 2, W // 2)] + syn.random_ignitions(land, seed, 4, 4)
+    S0 = syn.initial_state(land, ign)
+    # synthetic observed burn map: a disc around the ignitions, the size of the fire
+    # the hidden parameters reach (stands in for the oracle-generated target of the
+    # small calibration case, which is too slow to produce at 67M cells)
+    rr, cc = np.ogrid[:H, :W]
+    y = np.zeros((H, W), np.float32)
+    for (r, c) in ign:
+        y[(rr - r) ** 2 + (cc - c) ** 2 < (0.35 * T) ** 2] = 1.0
+    y *= land.burnable
+    return land, winds, S0, y
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", os.environ.get("LOCAL_RANK", "0")],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            self.p.wait()
+            self.f.close()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except Exception:
+            pass
+        if not sm:
+            return None
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(land, winds, S0, y, T_s, crop):
+    """Oracle fwd + BCE + adjoint on the top-left crop x crop of the workload for T_s
+    steps (bounded CPU work). Returns (cell-updates/s, seconds, threads)."""
+    import oracle as orc
+    orc.build()
+    sl = (slice(0, crop), slice(0, crop))
+    l2 = syn.Landscape(land.E[sl].copy(), land.p_veg[sl].copy(), land.p_den[sl].copy(), land.burnable[sl].copy())
+    w2 = [(V[sl].copy(), th[sl].copy()) for (V, th) in winds[:1]]
+    S2 = S0[sl].copy()
+    S2[crop // 2, crop // 2] = 2
+    prm = orc.Params(**PARAMS)
+    t0 = time.perf_counter()
+    a, b, tape = orc.diff_forward(l2, w2, [0], prm, S2, T_s)
+    _, g = orc.bce(a, y[sl])
+    orc.diff_backward(l2, w2, [0], prm, S2, tape, g, np.zeros_like(g))
+    dt = time.perf_counter() - t0
+    return crop * crop * T_s / dt, dt, orc.num_threads()
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on a bounded sample, rank 0 only."""
+    if rank != 0:
+        return
+    crop, T_s = 1024, 60
+    land, winds, S0, y = make_inputs(crop, crop, EPOCH_STEPS, FIELD_SEED)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, dt, thr = oracle_sample(land, winds, S0, y, T_s, crop)
+        if i >= args.warmup:
+            vals.append((v, dt))
+    value = statistics.median(v for v, _ in vals)
+    ms = 1000 * statistics.median(dt for _, dt in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{crop}x{crop} crop, {T_s} steps, one wind epoch"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": thr, "kind": "oracle",
+                             "sample": f"{crop}x{crop} crop of the workload, T={T_s} fwd+adjoint, FP64 C oracle"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=H, help="grid side (default 8192, the workload)")
+    ap.add_argument("--T", type=int, default=T)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2502_18738_gb300 as pf
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    pf.build()
+    Hs = Ws = args.size
+    Ts = args.T
+    land, winds, S0, y = make_inputs(Hs, Ws, Ts, FIELD_SEED + rank)
+    c = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    dev = dict(E=c(land.E), pv=c(land.p_veg), pd=c(land.p_den), S0=c(S0), y=c(y),
+               winds=[(c(V), c(th)) for V, th in winds])
+    stream = torch.cuda.current_stream()
+
+    def setup(model):
+        model.set_env(dev["E"], dev["pv"], dev["pd"], *dev["winds"][0])
+        for e, (V, th) in enumerate(dev["winds"][1:], start=1):
+            model.set_wind(V, th, e * EPOCH_STEPS)
+        model.set_params(**PARAMS)
+
+    m = pf.FireModel(Hs, Ws, pf.PF_DIFF, seed=PHILOX_SEED + rank)
+    setup(m)
+    g_a = torch.empty((Hs, Ws), dtype=torch.float32, device="cuda")
+    gpv = torch.empty_like(g_a)
+    gpd = torch.empty_like(g_a)
+    out = torch.empty((2, Hs, Ws), dtype=torch.float32, device="cuda")
+
+    def step():
+        pf.pf_forward(m.h, dev["S0"], Ts, out)
+        pf.pf_loss_bce(out[0], dev["y"], g_a, want_loss=False)
+        return pf.pf_backward(m.h, g_a, None, gpv, gpd)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, n):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / n
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pf.pf_set_tuning(m.h, profile=1)
+    pf.pf_profile_read(m.h, reset=True)
+    with Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/pfire_clocks_{rank}.csv") as clk:
+        ms = timed(step, args.steps)
+    prof = pf.pf_profile_read(m.h, reset=True)
+    pf.pf_set_tuning(m.h, profile=0)
+    tun = pf.pf_get_tuning(m.h)
+    cells = Hs * Ws * Ts
+    value = cells * world / (ms / 1000.0)
+    gpu_launches = sum(n for n, _ in prof.values())
+    # forward only
+    ms_fwd = timed(lambda: pf.pf_forward(m.h, dev["S0"], Ts, out), max(1, args.steps))
+    # plain one-launch-per-step comparator (forward)
+    ms_fwd_plain = None
+    if not args.no_plain:
+        pf.pf_set_tuning(m.h, kernel=1, K=tun["K"])
+        ms_fwd_plain = timed(lambda: pf.pf_forward(m.h, dev["S0"], Ts, out), 1)
+        pf.pf_set_tuning(m.h, kernel=0)
+
+    # roofline of the dominant kernel (largest share of device time in the timed region)
+    hbm, how = peaks()
+    kind, (n_l, t_l) = max(prof.items(), key=lambda kv: kv[1][1])
+    per_launch_cells = Hs * Ws
+    alg = {"adjoint_step": B_ADJ, "diff_step": B_FWD, "diff_blocked": B_FWD}.get(kind, B_FWD)
+    steps_per_launch = 1
+    achieved = alg * per_launch_cells * steps_per_launch / (t_l / n_l / 1000.0) / 1e9
+    roof = {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": how,
+            "launches": n_l, "ms_per_launch": t_l / n_l,
+            "share": t_l / max(1e-9, sum(t for _, t in prof.values()))}
+
+    # end to end through the C ABI with host buffers: inputs H2D, gradients D2H each step
+    e2e = None
+    if not args.no_e2e:
+        hp = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        host = dict(E=hp(land.E), pv=hp(land.p_veg), pd=hp(land.p_den), S0=hp(S0), y=hp(y),
+                    winds=[(hp(V), hp(th)) for V, th in winds])
+        hgpv = torch.empty((Hs, Ws), dtype=torch.float32).pin_memory()
+        hgpd = torch.empty_like(hgpv)
+        hout = torch.empty((2, Hs, Ws), dtype=torch.float32).pin_memory()
+        d2 = {k: torch.empty_like(v, device="cuda") for k, v in host.items() if k != "winds"}
+        dw = [(torch.empty_like(V, device="cuda"), torch.empty_like(th, device="cuda")) for V, th in host["winds"]]
+        h2d = sum(v.numel() * v.element_size() for k, v in host.items() if k != "winds")
+        h2d += sum(V.numel() * 4 + th.numel() * 4 for V, th in host["winds"])
+        d2h = hgpv.numel() * 4 * 2 + hout.numel() * 4 + 4 * 8
+
+        def e2e_step():
+            for k in d2:
+                d2[k].copy_(host[k], non_blocking=True)
+            for (dV, dth), (V, th) in zip(dw, host["winds"]):
+                dV.copy_(V, non_blocking=True)
+                dth.copy_(th, non_blocking=True)
+            m.set_env(d2["E"], d2["pv"], d2["pd"], *dw[0])
+            for e, (V, th) in enumerate(dw[1:], start=1):
+                m.set_wind(V, th, e * EPOCH_STEPS)
+            m.set_params(**PARAMS)
+            pf.pf_forward(m.h, d2["S0"], Ts, out)
+            pf.pf_loss_bce(out[0], d2["y"], g_a, want_loss=False)
+            g = pf.pf_backward(m.h, g_a, None, gpv, gpd)
+            hgpv.copy_(gpv, non_blocking=True)
+            hgpd.copy_(gpd, non_blocking=True)
+            hout.copy_(out, non_blocking=True)
+            return g
+
+        ms_e2e = timed(e2e_step, max(1, args.steps))
+        e2e = {"value": cells * world / (ms_e2e / 1000.0), "unit": "cell-updates/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt, thr = oracle_sample(land, winds, S0, y, 60, 1024)
+        cpu = {"value": v, "unit": "cell-updates/s", "cores": thr, "kind": "oracle", "seconds": dt,
+               "sample": "1024x1024 top-left crop of the workload, T=60 fwd+adjoint, FP64 C oracle"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD if (Hs == H and Ts == T) else f"{Hs}x{Ws} diff fwd+adjoint T={Ts}",
+                           "H": Hs, "W": Ws, "T": Ts, "wind_epochs": len(winds),
+                           "checkpoint_K": tun["K"], "kernel": tun["kernel"], "k": tun["k"],
+                           "l2": "inputs larger than L2 (state 0.5 GB, q 2.1 GB per epoch)"},
+                "fwd": {"value": cells * world / (ms_fwd / 1000.0), "unit": "cell-updates/s", "ms": ms_fwd,
+                        "frac_hbm_alg": B_FWD * cells / (ms_fwd / 1000.0) / 1e9 / hbm},
+                "fwd_plain": None if ms_fwd_plain is None else
+                {"value": cells / (ms_fwd_plain / 1000.0), "unit": "cell-updates/s", "ms": ms_fwd_plain},
+                "fwd_adj_frac_hbm_alg": (B_FWD + B_ADJ) * cells / (ms / 1000.0) / 1e9 / hbm,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "kernels": {k: {"launches": n, "ms": t} for k, (n, t) in prof.items() if n},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -59,7 +59,12 @@ struct PrepArgs {
     const float *E, *pveg, *pden, *V, *th;  // dense H*W, nullable
     const uint8_t* burnable;                 // dense H*W, nullable
     float p_h, c1, c2, a, l;
+    // derived on the host in FP64 and split into hi + lo floats:
+    // a * 180/pi, 1/l and 1/(sqrt(2) l)
+    float adeg_hi, adeg_lo, ikl_e_hi, ikl_e_lo, ikl_d_hi, ikl_d_lo;
 };
+// fill the derived hi/lo fields of PrepArgs from p_h, c1, c2, a, l
+void prep_derive(PrepArgs& g);
 
 void launch_prep(const PrepArgs& g, float* q, cudaStream_t s);
 // dL/dq -> per-block FP64 partials of dL/d(p_h, c1, c2, a) (partials[nblk][4]) and

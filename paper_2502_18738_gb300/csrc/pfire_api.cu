@@ -255,6 +255,7 @@ PrepArgs prep_args(const pf_ctx* c, int e, bool use_tape_params) {
     } else {
         g.p_h = c->p_h; g.c1 = c->c1; g.c2 = c->c2; g.a = c->a; g.l = c->l;
     }
+    prep_derive(g);
     return g;
 }
 

@@ -59,19 +59,27 @@ def _gauss_filter_fft(x: np.ndarray, sigma: float) -> np.ndarray:
 
 
 def _bilinear_upsample(x: np.ndarray, H: int, W: int, f: int) -> np.ndarray:
-    """Upsample a coarse periodic field by integer factor f (cell-centred, wraps)."""
+    """Upsample a coarse periodic field by integer factor f (cell-centred, wraps);
+    separable: along columns on the coarse rows first, then along rows. Uses torch's
+    multi-threaded CPU ops when available (same arithmetic as the numpy fallback)."""
     h, w = x.shape
     ry = (np.arange(H) + 0.5) / f - 0.5
     rx = (np.arange(W) + 0.5) / f - 0.5
     y0 = np.floor(ry).astype(np.int64)
     x0 = np.floor(rx).astype(np.int64)
-    fy = (ry - y0).astype(x.dtype)[:, None]
-    fx = (rx - x0).astype(x.dtype)[None, :]
-    y0m, y1m = y0 % h, (y0 + 1) % h
-    x0m, x1m = x0 % w, (x0 + 1) % w
-    top = x[y0m][:, x0m] * (1 - fx) + x[y0m][:, x1m] * fx
-    bot = x[y1m][:, x0m] * (1 - fx) + x[y1m][:, x1m] * fx
-    return top * (1 - fy) + bot * fy
+    fy = (ry - y0).astype(np.float32)[:, None]
+    fx = (rx - x0).astype(np.float32)[None, :]
+    try:
+        import torch
+        xt = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+        cols = torch.lerp(xt[:, torch.from_numpy(x0 % w)], xt[:, torch.from_numpy((x0 + 1) % w)],
+                          torch.from_numpy(fx))
+        out = torch.lerp(cols[torch.from_numpy(y0 % h)], cols[torch.from_numpy((y0 + 1) % h)],
+                         torch.from_numpy(fy))
+        return out.numpy()
+    except ImportError:  # pragma: no cover
+        cols = x[:, x0 % w] * (1 - fx) + x[:, (x0 + 1) % w] * fx          # h x W
+        return cols[y0 % h] * (1 - fy) + cols[(y0 + 1) % h] * fy           # H x W
 
 
 def smooth_field(H: int, W: int, sigma: float, seed: int, stream: int = 0) -> np.ndarray:
@@ -121,11 +129,15 @@ def uniform_wind(H: int, W: int, V: float, theta_deg: float):
 
 
 def _rescale(g: np.ndarray, lo: float, hi: float) -> np.ndarray:
-    g = g.astype(np.float64)
-    mn, mx = g.min(), g.max()
+    """lo + (hi - lo) (g - min)/(max - min), computed in float32."""
+    g = np.asarray(g, dtype=np.float32)
+    mn, mx = float(g.min()), float(g.max())
     if mx <= mn:
         return np.full(g.shape, lo, dtype=np.float32)
-    return (lo + (hi - lo) * (g - mn) / (mx - mn)).astype(np.float32)
+    out = g - np.float32(mn)
+    out *= np.float32((hi - lo) / (mx - mn))
+    out += np.float32(lo)
+    return out
 
 
 def smooth_wind(H: int, W: int, seed: int, epoch: int = 0, sigma: float = 32.0,
