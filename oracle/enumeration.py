@@ -10,6 +10,7 @@ cells, so only for grids of a few cells and a few steps.
 from __future__ import annotations
 
 import itertools
+import math
 
 import numpy as np
 
@@ -18,12 +19,12 @@ OFFSETS = [(-1, -1), (-1, 0), (-1, 1), (0, -1), (0, 1), (1, -1), (1, 0), (1, 1)]
 
 def _ignite_prob(S, q, r, c):
     H, W = S.shape
-    prod = 1.0
+    logprod = 0.0  # Eq. 9 as -expm1(sum log1p(-q)), free of cancellation
     for d, (dr, dc) in enumerate(OFFSETS):
         ri, ci = r + dr, c + dc
         if 0 <= ri < H and 0 <= ci < W and S[ri, ci] == 2:
-            prod *= 1.0 - float(q[d, r, c])
-    return 1.0 - prod
+            logprod += math.log1p(-float(q[d, r, c]))
+    return -math.expm1(logprod)
 
 
 def step_distribution(S, q, p_continue):

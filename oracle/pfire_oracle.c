@@ -137,6 +137,12 @@ void orc_prep(int H, int W, const float* E, const float* p_veg, const float* p_d
 
 /* ---------------------------------------------------------- discrete step */
 
+/* Eq. 9, p_ignite = 1 - prod_i (1 - p_i), is evaluated as -expm1(sum_i log1p(-p_i)):
+ * the same quantity, without the cancellation of 1 - prod in floating point, which
+ * would round every contribution below ~1e-16 to zero (those tiny probabilities at the
+ * leading edge of the fire are what later grows into the front). */
+static double orc_one_minus_exp(double logprod) { return -expm1(logprod); }
+
 /* One synchronous step of R realisations (Sec. 2.2 rules, Eq. 9). States:
  * 0 non-burnable, 1 unburned, 2 burning, 3 burned. Realisation r uses Philox run
  * index run0 + r. P_out (nullable, R*H*W) receives the FP64 ignition probability of
@@ -157,13 +163,13 @@ void orc_step_discrete(int H, int W, int R, const uint8_t* S, uint8_t* S_next, c
                 uint8_t st = s[j], out = st;
                 double P = 0.0, u = -1.0;
                 if (st == 1) {
-                    double prod = 1.0;
+                    double logprod = 0.0;   /* log of prod (1 - q) over burning neighbours */
                     for (int d = 0; d < 8; ++d) {
                         int ri = r + ORC_DR[d], ci = c + ORC_DC[d];
                         if (ri < 0 || ri >= H || ci < 0 || ci >= W) continue;
-                        if (s[(size_t)ri * W + ci] == 2) prod *= (1.0 - q[(size_t)d * HW + j]);
+                        if (s[(size_t)ri * W + ci] == 2) logprod += log1p(-q[(size_t)d * HW + j]);
                     }
-                    P = 1.0 - prod;                                              /* Eq. 9 */
+                    P = orc_one_minus_exp(logprod);                              /* Eq. 9 */
                     double u0, u1;
                     orc_cell_draws(seed, run0 + (uint32_t)rr, step, fire, (uint32_t)j, &u0, &u1);
                     u = u0;
@@ -213,13 +219,13 @@ void orc_step_diff(int H, int W, const double* a, const double* b, const double*
     for (int r = 0; r < H; ++r) {
         for (int c = 0; c < W; ++c) {
             size_t j = (size_t)r * W + c;
-            double prod = 1.0;
+            double logprod = 0.0;
             for (int d = 0; d < 8; ++d) {
                 int ri = r + ORC_DR[d], ci = c + ORC_DC[d];
                 if (ri < 0 || ri >= H || ci < 0 || ci >= W) continue;
-                prod *= 1.0 - b[(size_t)ri * W + ci] * q[(size_t)d * HW + j];
+                logprod += log1p(-b[(size_t)ri * W + ci] * q[(size_t)d * HW + j]);
             }
-            double P = 1.0 - prod;
+            double P = orc_one_minus_exp(logprod);                               /* Eq. 9 */
             double n = (1.0 - a[j]) * P;
             a_next[j] = a[j] + n;
             b_next[j] = n + p_continue * b[j];
@@ -241,14 +247,14 @@ void orc_adjoint_step(int H, int W, const double* a, const double* b, const doub
             size_t j = (size_t)r * W + c;
             int inside[8];
             size_t src[8];
-            double prod = 1.0;
+            double logprod = 0.0;
             for (int d = 0; d < 8; ++d) {
                 int ri = r + ORC_DR[d], ci = c + ORC_DC[d];
                 inside[d] = !(ri < 0 || ri >= H || ci < 0 || ci >= W);
                 src[d] = inside[d] ? (size_t)ri * W + ci : 0;
-                if (inside[d]) prod *= 1.0 - b[src[d]] * q[(size_t)d * HW + j];
+                if (inside[d]) logprod += log1p(-b[src[d]] * q[(size_t)d * HW + j]);
             }
-            double P = 1.0 - prod;
+            double P = orc_one_minus_exp(logprod);
             double ln = la1[j] + lb1[j];                 /* n feeds both a' and b' */
             la0[j] += la1[j] - ln * P;                   /* a' = a + (1-a) P */
             lb0[j] += p_continue * lb1[j];               /* b' = n + p_c b */

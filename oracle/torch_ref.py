@@ -51,10 +51,11 @@ def q_planes(E, p_veg, p_den, V, theta, p_h, c1, c2, a, l, burnable=None):
 
 
 def step(a, b, qs, p_continue):
-    prod = torch.ones_like(a)
+    # Eq. 9 as -expm1(sum log1p(-x)): 1 - prod(1 - x) without floating-point cancellation
+    logprod = torch.zeros_like(a)
     for (dr, dc), q in zip(OFFSETS, qs):
-        prod = prod * (1.0 - _shift(b, dr, dc, 0.0) * q)
-    P = 1.0 - prod
+        logprod = logprod + torch.log1p(-_shift(b, dr, dc, 0.0) * q)
+    P = -torch.expm1(logprod)
     n = (1.0 - a) * P
     return a + n, n + p_continue * b
 

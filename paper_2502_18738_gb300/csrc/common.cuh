@@ -53,6 +53,15 @@ __device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * (1.0
 __device__ __forceinline__ uint32_t lanes_eq2(uint32_t x) { return (x >> 1) & ~x & 0x01010101u; }
 __device__ __forceinline__ uint32_t lanes_eq1(uint32_t x) { return x & ~(x >> 1) & 0x01010101u; }
 
+// Continuous-state encoding of a = P[ever ignited]: A = a when a < 1/2, A = -(1 - a)
+// otherwise (the sign bit selects the complement; -0.0 is a = 1). FP32 keeps both a
+// near 0 and 1 - a near 0 accurate this way, which the update n = (1 - a) P needs in
+// cells that have almost surely ignited.
+__device__ __forceinline__ void a_decode(float A, float& a, float& ua) {
+    if (signbit(A)) { a = 1.0f + A; ua = -A; } else { a = A; ua = 1.0f - A; }
+}
+__device__ __forceinline__ float a_encode(float a, float ua) { return a < 0.5f ? a : -ua; }
+
 // ---------------------------------------------------------------- launchers
 struct PrepArgs {
     int H, W, pitch;
@@ -97,5 +106,8 @@ void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const
                                   cudaStream_t s);
 void launch_ignition_map_diff(int H, int W, int pitch, const float* ab, const float* q, float* P,
                               cudaStream_t s);
+// dense FP32 (a, b) [2][H][W]  <->  pitched encoded (A, b) [2][H][pitch]
+void launch_diff_pack(const float* dense, int H, int W, int pitch, float* ab, cudaStream_t s);
+void launch_diff_unpack(const float* ab, int H, int W, int pitch, float* dense, cudaStream_t s);
 
 }  // namespace pf

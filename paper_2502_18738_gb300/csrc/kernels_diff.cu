@@ -1,8 +1,11 @@
 // Differentiable (mean-field) step and its reverse-time adjoint.
-// State (a, b) = (P[ever ignited], P[burning]) as two FP32 planes [2][H][pitch]:
+// State (a, b) = (P[ever ignited], P[burning]) as two FP32 planes [2][H][pitch], a held
+// in the complement-aware encoding A (common.cuh):
 //   P_j  = 1 - prod_d (1 - b_{j+d} q_dj)     (Eq. 9 with burning probabilities)
 //   n_j  = (1 - a_j) P_j,  a'_j = a_j + n_j,  b'_j = n_j + p_continue b_j
-// P is accumulated as P <- P + x (1 - P), which keeps small probabilities accurate in FP32.
+// P is accumulated as P <- P + x (1 - P), which keeps small probabilities accurate in
+// FP32, and the survival product S = prod_d (1 - x_d) alongside it, so that
+// 1 - a' = (1 - a) S is formed without cancellation.
 #include "common.cuh"
 
 namespace pf {
@@ -22,17 +25,19 @@ __global__ void __launch_bounds__(256) k_diff_step(int H, int W, int pitch, floa
         return;
     }
     const float* b = ab + plane;
-    float P = 0.0f;
+    float P = 0.0f, S = 1.0f;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const int ri = r + dir_dr(d), ci = c + dir_dc(d);
         if (ri < 0 || ri >= H || ci < 0 || ci >= W) continue;
         const float x = __ldg(b + (size_t)ri * pitch + ci) * __ldg(q + d * plane + j);
         P = fmaf(x, 1.0f - P, P);
+        S *= 1.0f - x;
     }
-    const float a = ab[j];
-    const float n = (1.0f - a) * P;
-    abn[j] = a + n;
+    float a, ua;
+    a_decode(ab[j], a, ua);
+    const float n = ua * P;
+    abn[j] = a_encode(a + n, ua * S);
     abn[plane + j] = fmaf(pc, b[j], n);
 }
 
@@ -112,7 +117,9 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
         for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
         const float la = __ldg(la1 + j), lb = __ldg(lb1 + j);
         const float ln = la + lb;
-        const float lP = ln * (1.0f - __ldg(a + j));
+        float av, ua;
+        a_decode(__ldg(a + j), av, ua);
+        const float lP = ln * ua;
         const bool interior = (y >= 1 && y <= kAY && x >= 1 && x <= kAX);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {

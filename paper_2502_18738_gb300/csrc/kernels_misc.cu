@@ -30,9 +30,32 @@ __global__ void k_diff_init(const uint8_t* __restrict__ S, int H, int W, int pit
     const int r = (int)(idx / W), c = (int)(idx % W);
     const uint8_t s = S[idx];
     const size_t j = (size_t)r * pitch + c;
-    ab[j] = (s == 2 || s == 3) ? 1.0f : 0.0f;
+    ab[j] = (s == 2 || s == 3) ? -0.0f : 0.0f;  // encoded a: -0.0 is a = 1
     ab[(size_t)H * pitch + j] = (s == 2) ? 1.0f : 0.0f;
     burn[idx] = s != 0;
+}
+
+__global__ void k_diff_pack(const float* __restrict__ dense, int H, int W, int pitch, float* __restrict__ ab) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t HW = (size_t)H * W;
+    if (idx >= HW) return;
+    const int r = (int)(idx / W), c = (int)(idx % W);
+    const size_t j = (size_t)r * pitch + c;
+    const float a = dense[idx];
+    ab[j] = a_encode(a, 1.0f - a);
+    ab[(size_t)H * pitch + j] = dense[HW + idx];
+}
+
+__global__ void k_diff_unpack(const float* __restrict__ ab, int H, int W, int pitch, float* __restrict__ dense) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t HW = (size_t)H * W;
+    if (idx >= HW) return;
+    const int r = (int)(idx / W), c = (int)(idx % W);
+    const size_t j = (size_t)r * pitch + c;
+    float a, ua;
+    a_decode(ab[j], a, ua);
+    dense[idx] = a;
+    dense[HW + idx] = ab[(size_t)H * pitch + j];
 }
 
 constexpr int kBceThreads = 256;
@@ -94,6 +117,16 @@ void launch_validate_states(const uint8_t* S, size_t n, int* flags, cudaStream_t
 void launch_diff_init(const uint8_t* S, int H, int W, int pitch, float* ab, uint8_t* burn, cudaStream_t s) {
     const size_t n = (size_t)H * W;
     k_diff_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S, H, W, pitch, ab, burn);
+}
+
+void launch_diff_pack(const float* dense, int H, int W, int pitch, float* ab, cudaStream_t s) {
+    const size_t n = (size_t)H * W;
+    k_diff_pack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dense, H, W, pitch, ab);
+}
+
+void launch_diff_unpack(const float* ab, int H, int W, int pitch, float* dense, cudaStream_t s) {
+    const size_t n = (size_t)H * W;
+    k_diff_unpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ab, H, W, pitch, dense);
 }
 
 int bce_blocks(int64_t n) {

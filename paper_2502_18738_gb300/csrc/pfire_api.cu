@@ -429,9 +429,11 @@ int tape_begin(pf_ctx* ctx, int T) {
 
 int write_diff_out(pf_ctx* ctx, void* out) {
     if (!out) return PF_OK;
-    CK(cudaMemcpy2DAsync(out, sizeof(float) * ctx->W, ctx->cur_ab, sizeof(float) * ctx->P, sizeof(float) * ctx->W,
-                         2 * (size_t)ctx->H, cudaMemcpyDeviceToDevice, ctx->st));
-    return PF_OK;
+    {
+        LaunchScope ls(ctx, K_MISC);
+        launch_diff_unpack(ctx->cur_ab, ctx->H, ctx->W, ctx->P, (float*)out, ctx->st);
+    }
+    return check_launch(ctx, "diff unpack");
 }
 
 int write_discrete_out(pf_ctx* ctx, void* out) {
@@ -716,8 +718,12 @@ int pf_set_state(pf_ctx* ctx, int step, const void* S) {
                              cudaMemcpyDeviceToDevice, ctx->st));
     } else {
         float* dst = (ctx->cur_ab == ctx->work[0]) ? ctx->work[1] : ctx->work[0];
-        CK(cudaMemcpy2DAsync(dst, sizeof(float) * ctx->P, S, sizeof(float) * ctx->W, sizeof(float) * ctx->W,
-                             2 * (size_t)ctx->H, cudaMemcpyDeviceToDevice, ctx->st));
+        {
+            LaunchScope ls(ctx, K_MISC);
+            launch_diff_pack((const float*)S, ctx->H, ctx->W, ctx->P, dst, ctx->st);
+        }
+        int rc = check_launch(ctx, "diff pack");
+        if (rc) return rc;
         ctx->cur_ab = dst;
     }
     ctx->step = step;

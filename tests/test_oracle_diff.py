@@ -104,3 +104,17 @@ def test_c_oracle_matches_autograd_restatement_forward(orc):
     at, bt, _ = torch_ref.run(land, winds, [0, 4], d, S0, T, requires_grad=False)
     assert np.allclose(a, at.numpy(), rtol=0, atol=1e-13)
     assert np.allclose(b, bt.numpy(), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("x", [1e-20, 1e-9, 0.3])
+def test_single_source_gives_p_equal_bq_at_any_magnitude(orc, x):
+    # Eq. 9 with one source: P = b q exactly, also far below FP64's 1 - x resolution
+    H, W = 3, 4
+    q = np.zeros((8, H, W))
+    q[4, 1, 1] = 0.5          # cell (1,1) receives from its East neighbour (1,2)
+    a = np.zeros((H, W))
+    b = np.zeros((H, W))
+    b[1, 2] = 2 * x
+    a1, b1, P = orc.step_diff(a, b, q, 0.3, return_P=True)
+    assert P[1, 1] == pytest.approx(x, rel=1e-14)
+    assert a1[1, 1] == pytest.approx(x, rel=1e-14)
