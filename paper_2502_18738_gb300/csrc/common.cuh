@@ -100,6 +100,17 @@ void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin,
 
 void launch_diff_step(int H, int W, int pitch, float p_continue, const float* ab, float* ab_next,
                       const float* q, cudaStream_t s);
+// temporal-blocked differentiable forward: n <= diff_blocked_halo() steps per launch.
+// tab: 3-D map over the input (A, b) buffer (pitch, H, 2), box {64, 64, 2};
+// tq: 3-D map over q (pitch, H, 8), box {64, 64, 8}. out (nullable) receives the state
+// after n steps; all_out (nullable) receives the state after each step s at
+// all_out + s * all_stride.
+int diff_blocked_halo();
+int diff_blocked_box_rows();
+int diff_blocked_box_cols();
+int diff_blocked_configure();
+void launch_diff_blocked(const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc, int n,
+                         float* out, float* all_out, size_t all_stride, int nsm, int* err, cudaStream_t s);
 void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float* ab, const float* q,
                          const float* lam1, float* lam0, float* Gq, cudaStream_t s);
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,

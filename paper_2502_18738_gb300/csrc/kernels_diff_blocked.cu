@@ -1,0 +1,204 @@
+// Temporal-blocked differentiable forward step (the same update as k_diff_step, k
+// steps per launch).
+//
+// Persistent kernel, one CTA per SM. Each CTA walks a static list of 48 x 48-cell
+// interior tiles; for each it stages the 64 x 64 region (8-cell halo) of the state
+// (A, b) and of the eight q planes in shared memory with two TMA tile loads, prefetching
+// the next tile while it computes the current one. Each of the 512 threads owns an
+// 8-cell column strip of the region and keeps its cells' q (64 floats) and encoded a
+// in registers for the whole launch; b is exchanged through a shared-memory
+// ping-pong buffer, read through a rolling 3 x 3 register window (3 shared loads per
+// cell and step). After n <= 8 steps the interior, which is exact by then, is stored.
+// Cells outside the grid arrive as TMA zero fill (q = 0, a = b = 0) and stay 0.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace pf {
+
+namespace {
+
+constexpr int kRT = 64, kCT = 64;      // staged region
+constexpr int kHalo = 8;               // halo rows / columns = max steps per launch
+constexpr int kIR = kRT - 2 * kHalo;   // interior 48 x 48
+constexpr int kIC = kCT - 2 * kHalo;
+constexpr int kM = 8;                  // cells per thread (column strip)
+constexpr int kThreads = kCT * (kRT / kM);  // 512
+constexpr int kPlane = kRT * kCT;      // floats per staged plane
+
+struct Smem {
+    float q[8 * kPlane];     // staged q planes of the next tile (TMA destination)
+    float st[2 * kPlane];    // staged (A, b) of the next tile (TMA destination)
+    float b[2][kPlane];      // b ping-pong of the current tile
+};
+
+__device__ __forceinline__ void tile_origin(int tile, int tiles_x, int& r0, int& c0) {
+    const int ty = tile / tiles_x, tx = tile % tiles_x;
+    r0 = ty * kIR - kHalo;
+    c0 = tx * kIC - kHalo;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_diff_blocked(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap tq, int H, int pitch,
+                   float pc, int n, int tiles_x, int ntiles, float* __restrict__ out, float* __restrict__ all_out,
+                   size_t all_stride, int* __restrict__ err) {
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x;
+    const int x = tid % kCT;             // region column
+    const int ys = (tid / kCT) * kM;     // first region row of the strip
+    const uint32_t bytes = (uint32_t)((8 + 2) * kPlane * sizeof(float));
+    const size_t gplane = (size_t)H * pitch;
+
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int r0, c0;
+        tile_origin(tile, tiles_x, r0, c0);
+        mbar_arrive_expect_tx(&bar, bytes);
+        tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
+        tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
+    }
+    uint32_t parity = 0;
+    float q[kM][8];
+    float A[kM];
+    for (; tile < ntiles; tile += gridDim.x) {
+        const bool ok = mbar_wait_bounded(&bar, parity);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicExch(err, kErrTmaTimeout);
+                mbar_wait_bounded(&bar, parity);
+            }
+            return;
+        }
+        parity ^= 1u;
+        // stage -> registers (q, A) and -> ping-pong buffer 0 (b)
+#pragma unroll
+        for (int m = 0; m < kM; ++m) {
+            const int y = ys + m;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) q[m][d] = sm.q[d * kPlane + y * kCT + x];
+            A[m] = sm.st[y * kCT + x];
+            sm.b[0][y * kCT + x] = sm.st[kPlane + y * kCT + x];
+        }
+        fence_proxy_async();  // these generic reads of the stage precede the next TMA writes
+        __syncthreads();      // stage fully consumed
+        const int next = tile + gridDim.x;
+        if (tid == 0 && next < ntiles) {
+            int r0, c0;
+            tile_origin(next, tiles_x, r0, c0);
+            mbar_arrive_expect_tx(&bar, bytes);
+            tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
+            tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
+        }
+        int r0, c0;
+        tile_origin(tile, tiles_x, r0, c0);
+        const bool xin = (x >= 1 && x < kCT - 1);
+        int cur = 0;
+        for (int s = 0; s < n; ++s) {
+            const float* src = sm.b[cur];
+            float* dst = sm.b[cur ^ 1];
+            // rolling window over rows ys-1 .. ys+kM of columns x-1, x, x+1
+            float wl[3], wc[3], wr[3];
+            const int xl = xin ? x - 1 : x, xr = xin ? x + 1 : x;
+            const int y_first = ys > 0 ? ys - 1 : 0;
+            wl[0] = src[y_first * kCT + xl]; wc[0] = src[y_first * kCT + x]; wr[0] = src[y_first * kCT + xr];
+            wl[1] = src[ys * kCT + xl];      wc[1] = src[ys * kCT + x];      wr[1] = src[ys * kCT + xr];
+#pragma unroll
+            for (int m = 0; m < kM; ++m) {
+                const int y = ys + m;
+                const int yn = y + 1 < kRT ? y + 1 : y;
+                wl[2] = src[yn * kCT + xl]; wc[2] = src[yn * kCT + x]; wr[2] = src[yn * kCT + xr];
+                float bnew = wc[1];
+                if (xin && y >= 1 && y < kRT - 1) {
+                    // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
+                    const float nb[8] = {wl[0], wc[0], wr[0], wl[1], wr[1], wl[2], wc[2], wr[2]};
+                    float P = 0.0f, S = 1.0f;
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) {
+                        const float xx = nb[d] * q[m][d];
+                        P = fmaf(xx, 1.0f - P, P);
+                        S *= 1.0f - xx;
+                    }
+                    float a, ua;
+                    a_decode(A[m], a, ua);
+                    const float nn = ua * P;
+                    A[m] = a_encode(a + nn, ua * S);
+                    bnew = fmaf(pc, wc[1], nn);
+                }
+                dst[y * kCT + x] = bnew;
+                wl[0] = wl[1]; wc[0] = wc[1]; wr[0] = wr[1];
+                wl[1] = wl[2]; wc[1] = wc[2]; wr[1] = wr[2];
+            }
+            __syncthreads();
+            cur ^= 1;
+            if (all_out) {  // every intermediate state (segment recompute for the adjoint)
+                float* o = all_out + (size_t)s * all_stride;
+                const int gc = c0 + x;
+                if (x >= kHalo && x < kCT - kHalo && gc < pitch) {
+#pragma unroll
+                    for (int m = 0; m < kM; ++m) {
+                        const int y = ys + m, gr = r0 + y;
+                        if (y >= kHalo && y < kRT - kHalo && gr < H) {
+                            o[(size_t)gr * pitch + gc] = A[m];
+                            o[gplane + (size_t)gr * pitch + gc] = sm.b[cur][y * kCT + x];
+                        }
+                    }
+                }
+            }
+        }
+        if (out) {
+            const int gc = c0 + x;
+            if (x >= kHalo && x < kCT - kHalo && gc < pitch) {
+#pragma unroll
+                for (int m = 0; m < kM; ++m) {
+                    const int y = ys + m, gr = r0 + y;
+                    if (y >= kHalo && y < kRT - kHalo && gr < H) {
+                        out[(size_t)gr * pitch + gc] = A[m];
+                        out[gplane + (size_t)gr * pitch + gc] = sm.b[cur][y * kCT + x];
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the ping-pong buffers are reused by the next tile
+    }
+}
+
+}  // namespace
+
+int diff_blocked_halo() { return kHalo; }
+int diff_blocked_box_rows() { return kRT; }
+int diff_blocked_box_cols() { return kCT; }
+
+size_t diff_blocked_smem() { return sizeof(Smem) + 128; }
+
+int diff_blocked_configure() {
+    static int done = 0;
+    if (!done) {
+        if (cudaFuncSetAttribute(k_diff_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)diff_blocked_smem()) != cudaSuccess)
+            return -1;
+        done = 1;
+    }
+    return 0;
+}
+
+void launch_diff_blocked(const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc, int n,
+                         float* out, float* all_out, size_t all_stride, int nsm, int* err, cudaStream_t s) {
+    (void)W;
+    const int tiles_x = (pitch + kIC - 1) / kIC;
+    const int tiles_y = (H + kIR - 1) / kIR;
+    const int ntiles = tiles_x * tiles_y;
+    const int grid = ntiles < nsm ? ntiles : nsm;
+    k_diff_blocked<<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, pc, n, tiles_x, ntiles, out,
+                                                               all_out, all_stride, err);
+}
+
+}  // namespace pf

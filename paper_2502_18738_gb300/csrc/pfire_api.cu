@@ -91,7 +91,6 @@ struct pf_ctx {
     // adjoint
     float* lam[2] = {nullptr, nullptr};
     float* Gq = nullptr;
-    std::vector<float*> seg;
     double* partials = nullptr;
     double* gacc = nullptr;
     // misc
@@ -99,6 +98,11 @@ struct pf_ctx {
     int* hflags = nullptr;  // pinned mirror
     CUtensorMap tmapS[2];
     bool tmap_ok = false;
+    CUtensorMap tmapQ;       // q planes (pitch, H, 8), box of the blocked diff kernel
+    bool tmapQ_ok = false;
+    int nsm = 152;
+    float* seg_buf = nullptr;  // K-1 contiguous states (segment recompute)
+    int seg_cap = 0;
     int TH = 64, KH = 16;
     pf_tuning tun{0, 0, 0, 0};
     std::vector<ProfRec> prof;
@@ -230,6 +234,19 @@ bool encode_state_map(pf_ctx* c, CUtensorMap* m, uint8_t* base) {
     return r == CUDA_SUCCESS;
 }
 
+bool encode_f32_3d(CUtensorMap* m, const float* base, int P, int H, int planes, int box_c, int box_r, int box_p) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)H, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)P * H * 4};
+    cuuint32_t box[3] = {(cuuint32_t)box_c, (cuuint32_t)box_r, (cuuint32_t)box_p};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // ------------------------------------------------------------- q cache
 int epoch_of(const pf_ctx* c, int t) {
     int e = 0;
@@ -292,14 +309,27 @@ int device_error(pf_ctx* ctx) {
 // ------------------------------------------------------------- kernel choice
 int choose_kernel(const pf_ctx* c) {
     if (c->tun.kernel == 1) return 1;
-    if (c->tun.kernel == 2) return (c->form == PF_DISCRETE && c->tmap_ok) ? 2 : 1;
-    // automatic: the blocked kernel when its tensor maps exist
-    return (c->form == PF_DISCRETE && c->tmap_ok) ? 2 : 1;
+    // kernel 2 or automatic: the temporal-blocked kernel when its tensor maps exist
+    const bool ok = (c->form == PF_DISCRETE) ? c->tmap_ok : c->tmapQ_ok;
+    return ok ? 2 : 1;
 }
 
 int blocked_k(const pf_ctx* c) {
     int k = c->tun.k > 0 ? c->tun.k : 8;
-    return std::min(k, c->KH);
+    return std::min(k, c->form == PF_DISCRETE ? c->KH : diff_blocked_halo());
+}
+
+// one launch of the blocked diff kernel from `in`; out / all_out as in launch_diff_blocked
+int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* out, float* all_out) {
+    CUtensorMap tab;
+    if (!encode_f32_3d(&tab, in, ctx->P, ctx->H, 2, diff_blocked_box_cols(), diff_blocked_box_rows(), 2))
+        return fail(ctx, PF_ECUDA, "tensor map encoding of the state buffer failed");
+    {
+        LaunchScope ls(ctx, K_FBLK);
+        launch_diff_blocked(&tab, &ctx->tmapQ, ctx->H, ctx->W, ctx->P, pc, n, out, all_out, 2 * plane_elems(ctx),
+                            ctx->nsm, ctx->dflags, ctx->st);
+    }
+    return check_launch(ctx, "diff blocked");
 }
 
 // ------------------------------------------------------------- discrete runs
@@ -376,28 +406,44 @@ int choose_K(pf_ctx* ctx, int T) {
     return K;
 }
 
+// steps from t until the next checkpoint step (exclusive bound t + result)
+int steps_to_ckpt(const pf_ctx* c, int t) {
+    if (!c->tape_valid) return 0x7fffffff;
+    int n = 1;
+    while (!is_ckpt_step(c, t + n)) ++n;
+    return n;
+}
+
 int diff_steps(pf_ctx* ctx, int T) {
     const int end = ctx->step + T;
+    const int kern = choose_kernel(ctx);
     while (ctx->step < end) {
         const int t = ctx->step;
         int rc = ensure_q(ctx, epoch_of(ctx, t));
         if (rc) return rc;
+        int n = 1;
+        if (kern == 2) {
+            n = std::min({blocked_k(ctx), end - t, next_epoch_start(ctx, t) - t, steps_to_ckpt(ctx, t)});
+        }
         float* out;
-        if (ctx->tape_valid && is_ckpt_step(ctx, t + 1)) {
+        if (ctx->tape_valid && is_ckpt_step(ctx, t + n)) {
             out = take_slot(ctx, &rc);
             if (rc) return rc;
-            ctx->ckpts.push_back({t + 1, out});
+            ctx->ckpts.push_back({t + n, out});
         } else {
             out = (ctx->cur_ab == ctx->work[0]) ? ctx->work[1] : ctx->work[0];
         }
-        {
-            LaunchScope ls(ctx, K_FSTEP);
-            launch_diff_step(ctx->H, ctx->W, ctx->P, ctx->pc, ctx->cur_ab, out, ctx->q, ctx->st);
+        if (kern == 2) {
+            if ((rc = diff_blocked_launch(ctx, ctx->cur_ab, ctx->pc, n, out, nullptr))) return rc;
+        } else {
+            {
+                LaunchScope ls(ctx, K_FSTEP);
+                launch_diff_step(ctx->H, ctx->W, ctx->P, ctx->pc, ctx->cur_ab, out, ctx->q, ctx->st);
+            }
+            if ((rc = check_launch(ctx, "diff step"))) return rc;
         }
-        rc = check_launch(ctx, "diff step");
-        if (rc) return rc;
         ctx->cur_ab = out;
-        ctx->step = t + 1;
+        ctx->step = t + n;
     }
     return PF_OK;
 }
@@ -482,6 +528,13 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
     ctx->seed = seed;
     ctx->st = (cudaStream_t)cuda_stream;
     ctx->winds.push_back({0, nullptr, nullptr});
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            ctx->nsm = nsm;
+        cudaGetLastError();
+    }
     int rc = PF_OK;
     const size_t pe = plane_elems(ctx);
 #define ALLOC(ptr, bytes)                                         \
@@ -508,6 +561,10 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
         ctx->tmap_ok = encode_state_map(ctx, &ctx->tmapS[0], ctx->S[0]) &&
                        encode_state_map(ctx, &ctx->tmapS[1], ctx->S[1]);
     } else {
+        ctx->tmapQ_ok = diff_blocked_configure() == 0 &&
+                        encode_f32_3d(&ctx->tmapQ, ctx->q, ctx->P, H, 8, diff_blocked_box_cols(),
+                                      diff_blocked_box_rows(), 8);
+        cudaGetLastError();
         ALLOC(ctx->work[0], diff_state_bytes(ctx));
         ALLOC(ctx->work[1], diff_state_bytes(ctx));
         ALLOC(ctx->burn, (size_t)H * W);
@@ -774,11 +831,17 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
         ctx->gacc = ctx->partials + (size_t)nblk * 4;
     }
     const int segmax = ctx->K - 1;
-    while ((int)ctx->seg.size() < segmax) {
+    if (ctx->seg_cap < segmax) {
+        if (ctx->seg_buf) dfree(ctx, ctx->seg_buf);
+        ctx->seg_buf = nullptr;
+        ctx->seg_cap = 0;
         void* p;
-        if ((rc = dalloc(ctx, &p, sbytes))) return rc;
-        ctx->seg.push_back((float*)p);
+        if ((rc = dalloc(ctx, &p, sbytes * (size_t)segmax))) return rc;
+        ctx->seg_buf = (float*)p;
+        ctx->seg_cap = segmax;
     }
+    const size_t selems = 2 * pe;
+    const int kern = choose_kernel(ctx);
     // terminal adjoint
     CK(cudaMemsetAsync(ctx->lam[0], 0, sbytes, ctx->st));
     if (dL_da_T)
@@ -829,17 +892,25 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             if ((rc = check_launch(ctx, "prep"))) return rc;
             ctx->q_key_epoch = -1;
         }
-        // recompute states s0+1 .. s1-1 of the segment
+        // recompute states s0+1 .. s1-1 of the segment into the contiguous segment buffer
         std::vector<const float*> states;
         states.push_back(ctx->ckpts[si].second);
-        for (int t = s0 + 1; t < s1; ++t) {
-            float* out = ctx->seg[t - s0 - 1];
-            {
-                LaunchScope ls(ctx, K_FSTEP);
-                launch_diff_step(ctx->H, ctx->W, ctx->P, pc, states.back(), out, ctx->q, ctx->st);
+        for (int t = s0 + 1; t < s1; ++t) states.push_back(ctx->seg_buf + (size_t)(t - s0 - 1) * selems);
+        for (int t = s0; t < s1 - 1;) {
+            if (kern == 2) {
+                const int n = std::min(blocked_k(ctx), s1 - 1 - t);
+                if ((rc = diff_blocked_launch(ctx, states[t - s0], pc, n, nullptr, (float*)states[t - s0 + 1])))
+                    return rc;
+                t += n;
+            } else {
+                {
+                    LaunchScope ls(ctx, K_FSTEP);
+                    launch_diff_step(ctx->H, ctx->W, ctx->P, pc, states[t - s0], (float*)states[t - s0 + 1], ctx->q,
+                                     ctx->st);
+                }
+                if ((rc = check_launch(ctx, "diff step (recompute)"))) return rc;
+                t += 1;
             }
-            if ((rc = check_launch(ctx, "diff step (recompute)"))) return rc;
-            states.push_back(out);
         }
         for (int t = s1 - 1; t >= s0; --t) {
             {

@@ -40,11 +40,13 @@ def _model(pf, orc, land, V, th, H, W, **kw):
     return m, orc.Params(**p)
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("H,W", [(33, 47), (64, 64), (1, 50), (50, 1), (150, 260)])
-def test_single_step_random_states(pf, orc, H, W):
+def test_single_step_random_states(pf, orc, H, W, kernel):
     land = syn.make_landscape(H, W, 2)
     V, th = syn.smooth_wind(H, W, 2, 0, sigma=6.0)
     m, prm = _model(pf, orc, land, V, th, H, W)
+    m.set_tuning(kernel=kernel)
     S0 = np.where(land.burnable != 0, 1, 0).astype(np.uint8)
     m.forward(cuda(S0), 0)  # sets the burnable mask
     q = orc.prep(H, W, land.E, land.p_veg, land.p_den, V, th, prm, burnable=land.burnable)
@@ -71,11 +73,13 @@ def _set_winds(m, winds, starts):
         m.set_wind(cuda(V), cuda(th), s)
 
 
-@pytest.mark.parametrize("H,W,T", [(96, 80, 60), (200, 170, 120)])
-def test_trajectory(pf, orc, H, W, T):
+@pytest.mark.parametrize("H,W,T,kernel,k", [(96, 80, 60, 1, 0), (200, 170, 120, 1, 0), (96, 80, 60, 2, 3),
+                                           (200, 170, 120, 2, 8), (130, 300, 77, 2, 5)])
+def test_trajectory(pf, orc, H, W, T, kernel, k):
     land, winds, starts, S0 = _problem(H, W, T, 6)
     m, prm = _model(pf, orc, land, *winds[0], H, W)
     _set_winds(m, winds, starts)
+    m.set_tuning(kernel=kernel, k=k)
     out = m.forward(cuda(S0), T).cpu().numpy()
     a, b, tape = orc.diff_forward(land, winds, starts, prm, S0, T)
     # every single step, fed the oracle's state, within the per-step tolerance
@@ -95,14 +99,14 @@ def test_trajectory(pf, orc, H, W, T):
     assert a.max() > 0.9 and (a > 0.01).sum() > 100
 
 
-@pytest.mark.parametrize("K", [1, 7, 0])
-def test_gradients_match_oracle(pf, orc, K):
+@pytest.mark.parametrize("K,kernel", [(1, 1), (7, 1), (0, 1), (1, 2), (7, 2), (13, 2)])
+def test_gradients_match_oracle(pf, orc, K, kernel):
     import torch
     H, W, T = 72, 64, 48
     land, winds, starts, S0 = _problem(H, W, T, 13)
     m, prm = _model(pf, orc, land, *winds[0], H, W)
     _set_winds(m, winds, starts)
-    m.set_tuning(K=K)
+    m.set_tuning(K=K, kernel=kernel)
     y = (orc.forward_discrete(S0, orc.prep(H, W, land.E, land.p_veg, land.p_den, *winds[0],
                                             orc.Params(0.5, 0.05, 0.12, 0.08, 0.3)),
                               0.3, seed=2, T=T) >= 2).astype(np.float32)
