@@ -250,7 +250,7 @@ def main():
     tun = pf.pf_get_tuning(m.h)
     cells = Hs * Ws * Ts
     value = cells * world / (ms / 1000.0)
-    gpu_launches = sum(n for n, _ in prof.values())
+    gpu_launches = sum(n for n, _, _ in prof.values())
     # forward only
     ms_fwd = timed(lambda: pf.pf_forward(m.h, dev["S0"], Ts, out), max(1, args.steps))
     # plain one-launch-per-step comparator (forward)
@@ -260,17 +260,17 @@ def main():
         ms_fwd_plain = timed(lambda: pf.pf_forward(m.h, dev["S0"], Ts, out), 1)
         pf.pf_set_tuning(m.h, kernel=0)
 
-    # roofline of the dominant kernel (largest share of device time in the timed region)
+    # roofline of the dominant kernel (largest share of device time in the timed region):
+    # algorithmic bytes = per-cell-step bytes x the cell-steps its launches processed
     hbm, how = peaks()
-    kind, (n_l, t_l) = max(prof.items(), key=lambda kv: kv[1][1])
-    per_launch_cells = Hs * Ws
-    alg = {"adjoint_step": B_ADJ, "diff_step": B_FWD, "diff_blocked": B_FWD}.get(kind, B_FWD)
-    steps_per_launch = 1
-    achieved = alg * per_launch_cells * steps_per_launch / (t_l / n_l / 1000.0) / 1e9
+    kind, (n_l, cs_l, t_l) = max(prof.items(), key=lambda kv: kv[1][2])
+    alg = {"adjoint_step": B_ADJ, "adjoint_blocked": B_ADJ, "diff_step": B_FWD, "diff_blocked": B_FWD}.get(kind, B_FWD)
+    achieved = alg * cs_l / (t_l / 1000.0) / 1e9
     roof = {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None, "peak_source": how,
-            "launches": n_l, "ms_per_launch": t_l / n_l,
-            "share": t_l / max(1e-9, sum(t for _, t in prof.values()))}
+            "launches": n_l, "ms_per_launch": t_l / n_l, "cell_steps_per_launch": cs_l / n_l,
+            "alg_bytes_per_cell_step": alg,
+            "share": t_l / max(1e-9, sum(t for _, _, t in prof.values()))}
 
     # end to end through the C ABI with host buffers: inputs H2D, gradients D2H each step
     e2e = None
@@ -329,7 +329,7 @@ def main():
                 {"value": cells / (ms_fwd_plain / 1000.0), "unit": "cell-updates/s", "ms": ms_fwd_plain},
                 "fwd_adj_frac_hbm_alg": (B_FWD + B_ADJ) * cells / (ms / 1000.0) / 1e9 / hbm,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-                "kernels": {k: {"launches": n, "ms": t} for k, (n, t) in prof.items() if n},
+                "kernels": {k: {"launches": n, "cell_steps": cs, "ms": t} for k, (n, cs, t) in prof.items() if n},
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if dist is not None:

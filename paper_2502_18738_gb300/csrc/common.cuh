@@ -113,6 +113,14 @@ void launch_diff_blocked(const CUtensorMap* tab, const CUtensorMap* tq, int H, i
                          float* out, float* all_out, size_t all_stride, int nsm, int* err, cudaStream_t s);
 void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float* ab, const float* q,
                          const float* lam1, float* lam0, float* Gq, cudaStream_t s);
+// temporal-blocked adjoint with TMEM working set: n <= adjoint_blocked_max_steps() steps
+// t = t1-1 .. t1-n per launch. tst: 3-D map over a buffer of consecutive states
+// (pitch, H, 2 * nstates), box {64, 64, 2}; the state at t1-1-m is state index zlast-m.
+// tq as for launch_diff_blocked. Gq is accumulated.
+int adjoint_blocked_max_steps();
+int adjoint_blocked_configure();
+void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
+                            int n, const float* lam_in, float* lam_out, float* Gq, int nsm, int* err, cudaStream_t s);
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,
                                   cudaStream_t s);
 void launch_ignition_map_diff(int H, int W, int pitch, const float* ab, const float* q, float* P,

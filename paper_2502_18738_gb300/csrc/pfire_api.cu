@@ -29,10 +29,11 @@ namespace {
 
 thread_local std::string g_last_error = "no error";
 
-enum Kind { K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_PADJ, K_RED, K_MISC, K_NKINDS };
-const char* kKindNames[K_NKINDS] = {"prep",         "discrete_step", "discrete_blocked",
-                                    "diff_step",    "diff_blocked",  "adjoint_step",
-                                    "prep_adjoint", "reduce_fp64",   "misc"};
+enum Kind { K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_NKINDS };
+const char* kKindNames[K_NKINDS] = {"prep",         "discrete_step",    "discrete_blocked",
+                                    "diff_step",    "diff_blocked",     "adjoint_step",
+                                    "adjoint_blocked", "prep_adjoint",  "reduce_fp64",
+                                    "misc"};
 
 struct Epoch {
     int from;
@@ -108,6 +109,7 @@ struct pf_ctx {
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
     long long launches[K_NKINDS] = {0};
+    long long cell_steps[K_NKINDS] = {0};
     double prof_ms[K_NKINDS] = {0};
     std::vector<void*> allocs;
     std::string err = "no error";
@@ -164,8 +166,11 @@ struct LaunchScope {
     pf_ctx* c;
     int kind;
     cudaEvent_t e1 = nullptr;
-    LaunchScope(pf_ctx* c_, int k) : c(c_), kind(k) {
+    // steps: automaton steps the launch advances (or reverses) every cell by
+    LaunchScope(pf_ctx* c_, int k, int steps = 1) : c(c_), kind(k) {
         c->launches[k] += 1;
+        if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED)
+            c->cell_steps[k] += (long long)steps * c->H * c->W * (k == K_DSTEP || k == K_DBLK ? c->R : 1);
         if (!c->tun.profile) return;
         cudaEvent_t e0 = take();
         e1 = take();
@@ -325,7 +330,7 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
     if (!encode_f32_3d(&tab, in, ctx->P, ctx->H, 2, diff_blocked_box_cols(), diff_blocked_box_rows(), 2))
         return fail(ctx, PF_ECUDA, "tensor map encoding of the state buffer failed");
     {
-        LaunchScope ls(ctx, K_FBLK);
+        LaunchScope ls(ctx, K_FBLK, n);
         launch_diff_blocked(&tab, &ctx->tmapQ, ctx->H, ctx->W, ctx->P, pc, n, out, all_out, 2 * plane_elems(ctx),
                             ctx->nsm, ctx->dflags, ctx->st);
     }
@@ -355,7 +360,7 @@ int run_discrete(pf_ctx* ctx, int T) {
         const int src = ctx->scur, dst = 1 - ctx->scur;
         if (kern == 2) {
             n = std::min(n, blocked_k(ctx));
-            LaunchScope ls(ctx, K_DBLK);
+            LaunchScope ls(ctx, K_DBLK, n);
             launch_discrete_blocked_impl(g, &ctx->tmapS[src], ctx->TH, ctx->KH, ctx->S[dst], ctx->q, (uint32_t)t, n,
                                          ctx->dflags, ctx->st);
         } else {
@@ -830,7 +835,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
         ctx->partials = (double*)p;
         ctx->gacc = ctx->partials + (size_t)nblk * 4;
     }
-    const int segmax = ctx->K - 1;
+    const int segmax = ctx->K;  // states s0 .. s0+K-1 of one segment, consecutive
     if (ctx->seg_cap < segmax) {
         if (ctx->seg_buf) dfree(ctx, ctx->seg_buf);
         ctx->seg_buf = nullptr;
@@ -842,6 +847,11 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
     }
     const size_t selems = 2 * pe;
     const int kern = choose_kernel(ctx);
+    CUtensorMap tseg;
+    const bool adj_blocked = kern == 2 && adjoint_blocked_configure() == 0 &&
+                             encode_f32_3d(&tseg, ctx->seg_buf, ctx->P, ctx->H, 2 * ctx->seg_cap,
+                                           diff_blocked_box_cols(), diff_blocked_box_rows(), 2);
+    cudaGetLastError();
     // terminal adjoint
     CK(cudaMemsetAsync(ctx->lam[0], 0, sbytes, ctx->st));
     if (dL_da_T)
@@ -892,10 +902,11 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             if ((rc = check_launch(ctx, "prep"))) return rc;
             ctx->q_key_epoch = -1;
         }
-        // recompute states s0+1 .. s1-1 of the segment into the contiguous segment buffer
+        // the segment's states s0 .. s1-1, consecutive in the segment buffer: the
+        // checkpoint copied to slot 0, the rest recomputed
         std::vector<const float*> states;
-        states.push_back(ctx->ckpts[si].second);
-        for (int t = s0 + 1; t < s1; ++t) states.push_back(ctx->seg_buf + (size_t)(t - s0 - 1) * selems);
+        for (int t = s0; t < s1; ++t) states.push_back(ctx->seg_buf + (size_t)(t - s0) * selems);
+        CK(cudaMemcpyAsync((void*)states[0], ctx->ckpts[si].second, sbytes, cudaMemcpyDeviceToDevice, ctx->st));
         for (int t = s0; t < s1 - 1;) {
             if (kern == 2) {
                 const int n = std::min(blocked_k(ctx), s1 - 1 - t);
@@ -912,14 +923,28 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                 t += 1;
             }
         }
-        for (int t = s1 - 1; t >= s0; --t) {
-            {
-                LaunchScope ls(ctx, K_ADJ);
-                launch_adjoint_step(ctx->H, ctx->W, ctx->P, pc, states[t - s0], ctx->q, ctx->lam[lcur],
-                                    ctx->lam[1 - lcur], ctx->Gq, ctx->st);
+        if (adj_blocked) {
+            for (int t1 = s1; t1 > s0;) {
+                const int n = std::min(adjoint_blocked_max_steps(), t1 - s0);
+                {
+                    LaunchScope ls(ctx, K_ABLK, n);
+                    launch_adjoint_blocked(&tseg, &ctx->tmapQ, ctx->H, ctx->P, pc, t1 - 1 - s0, n, ctx->lam[lcur],
+                                           ctx->lam[1 - lcur], ctx->Gq, ctx->nsm, ctx->dflags, ctx->st);
+                }
+                if ((rc = check_launch(ctx, "adjoint blocked"))) return rc;
+                lcur = 1 - lcur;
+                t1 -= n;
             }
-            if ((rc = check_launch(ctx, "adjoint step"))) return rc;
-            lcur = 1 - lcur;
+        } else {
+            for (int t = s1 - 1; t >= s0; --t) {
+                {
+                    LaunchScope ls(ctx, K_ADJ);
+                    launch_adjoint_step(ctx->H, ctx->W, ctx->P, pc, states[t - s0], ctx->q, ctx->lam[lcur],
+                                        ctx->lam[1 - lcur], ctx->Gq, ctx->st);
+                }
+                if ((rc = check_launch(ctx, "adjoint step"))) return rc;
+                lcur = 1 - lcur;
+            }
         }
     }
     if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
@@ -929,7 +954,8 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
     return PF_OK;
 }
 
-int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* launches, double* ms, int reset) {
+int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* launches, long long* cell_steps,
+                    double* ms, int reset) {
     if (!ctx) return fail(nullptr, PF_EINVAL, "pf_profile_read: ctx is NULL");
     CK(cudaStreamSynchronize(ctx->st));
     prof_collect(ctx);
@@ -937,11 +963,13 @@ int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* l
     for (int i = 0; i < n; ++i) {
         if (kinds) kinds[i] = kKindNames[i];
         if (launches) launches[i] = ctx->launches[i];
+        if (cell_steps) cell_steps[i] = ctx->cell_steps[i];
         if (ms) ms[i] = ctx->prof_ms[i];
     }
     if (reset)
         for (int i = 0; i < K_NKINDS; ++i) {
             ctx->launches[i] = 0;
+            ctx->cell_steps[i] = 0;
             ctx->prof_ms[i] = 0.0;
         }
     return n;
