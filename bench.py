@@ -174,6 +174,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--K", type=int, default=0, help="checkpoint interval (0 = chosen by the library)")
+    ap.add_argument("--k", type=int, default=0, help="steps per blocked forward launch (0 = library default)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -207,6 +209,7 @@ def main():
 
     m = pf.FireModel(Hs, Ws, pf.PF_DIFF, seed=PHILOX_SEED + rank)
     setup(m)
+    pf.pf_set_tuning(m.h, K=args.K, k=args.k)
     g_a = torch.empty((Hs, Ws), dtype=torch.float32, device="cuda")
     gpv = torch.empty_like(g_a)
     gpd = torch.empty_like(g_a)
@@ -240,13 +243,13 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    pf.pf_set_tuning(m.h, profile=1)
+    pf.pf_set_tuning(m.h, K=args.K, k=args.k, profile=1)
     pf.pf_profile_read(m.h, reset=True)
     with Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/pfire_clocks_{rank}.csv") as clk:
         ms = timed(step, args.steps)
     prof = pf.pf_profile_read(m.h, reset=True)
-    pf.pf_set_tuning(m.h, profile=0)
+    pf.pf_set_tuning(m.h, K=args.K, k=args.k, profile=0)
     tun = pf.pf_get_tuning(m.h)
     cells = Hs * Ws * Ts
     value = cells * world / (ms / 1000.0)
@@ -256,9 +259,9 @@ def main():
     # plain one-launch-per-step comparator (forward)
     ms_fwd_plain = None
     if not args.no_plain:
-        pf.pf_set_tuning(m.h, kernel=1, K=tun["K"])
+        pf.pf_set_tuning(m.h, kernel=1, K=tun["K"], k=args.k)
         ms_fwd_plain = timed(lambda: pf.pf_forward(m.h, dev["S0"], Ts, out), 1)
-        pf.pf_set_tuning(m.h, kernel=0)
+        pf.pf_set_tuning(m.h, kernel=0, K=args.K, k=args.k)
 
     # roofline of the dominant kernel (largest share of device time in the timed region):
     # algorithmic bytes = per-cell-step bytes x the cell-steps its launches processed

@@ -83,10 +83,9 @@ struct pf_ctx {
     bool tape_valid = false;
     int tape_start = 0;
     int K = 1;
-    std::vector<std::pair<int, float*>> ckpts;  // (step, slot)
-    std::vector<float*> slot_pool;              // allocated slots, reused
-    size_t slots_used = 0;
-    float* tape_params[1] = {nullptr};
+    std::vector<std::pair<int, int>> ckpts;  // (step, arena slot)
+    float* arena = nullptr;                  // consecutive saved states, slot i at arena + i * state
+    int arena_cap = 0, arena_used = 0;
     float t_p_h = 0, t_c1 = 0, t_c2 = 0, t_a = 0, t_pc = 0, t_l = 0;
     long t_version = -1;
     // adjoint
@@ -378,15 +377,37 @@ int run_discrete(pf_ctx* ctx, int T) {
 }
 
 // ------------------------------------------------------------- diff runs
-float* take_slot(pf_ctx* ctx, int* rc) {
-    *rc = PF_OK;
-    if (ctx->slots_used < ctx->slot_pool.size()) return ctx->slot_pool[ctx->slots_used++];
+float* slot_ptr(const pf_ctx* c, int slot) { return c->arena + (size_t)slot * 2 * plane_elems(c); }
+
+// Make room for `need` slots in the tape arena; a larger arena takes over the used
+// slots (and the current-state pointer if it points into them).
+int arena_reserve(pf_ctx* ctx, int need) {
+    if (need <= ctx->arena_cap) return PF_OK;
+    const size_t sb = diff_state_bytes(ctx);
     void* p = nullptr;
-    *rc = dalloc(ctx, &p, diff_state_bytes(ctx));
-    if (*rc) return nullptr;
-    ctx->slot_pool.push_back((float*)p);
-    ctx->slots_used++;
-    return (float*)p;
+    int rc = dalloc(ctx, &p, sb * (size_t)need);
+    if (rc) return rc;
+    float* old = ctx->arena;
+    if (old && ctx->arena_used)
+        CK(cudaMemcpyAsync(p, old, sb * (size_t)ctx->arena_used, cudaMemcpyDeviceToDevice, ctx->st));
+    if (old && ctx->cur_ab >= old && ctx->cur_ab < old + (size_t)ctx->arena_cap * 2 * plane_elems(ctx))
+        ctx->cur_ab = (float*)p + (ctx->cur_ab - old);
+    if (old) dfree(ctx, old);
+    ctx->arena = (float*)p;
+    ctx->arena_cap = need;
+    return PF_OK;
+}
+
+// Take n consecutive slots; returns the first slot index (or -1 with *rc set).
+int take_slots(pf_ctx* ctx, int n, int* rc) {
+    *rc = PF_OK;
+    if (ctx->arena_used + n > ctx->arena_cap) {
+        *rc = arena_reserve(ctx, std::max(ctx->arena_used + n, ctx->arena_cap + ctx->arena_cap / 2 + 8));
+        if (*rc) return -1;
+    }
+    const int s0 = ctx->arena_used;
+    ctx->arena_used += n;
+    return s0;
 }
 
 bool is_ckpt_step(const pf_ctx* c, int t) {
@@ -403,8 +424,8 @@ int choose_K(pf_ctx* ctx, int T) {
         cudaGetLastError();
         free_b = 0;
     }
-    const double budget = 0.6 * (double)(free_b + ctx->slot_pool.size() * diff_state_bytes(ctx));
     const double sb = (double)diff_state_bytes(ctx);
+    const double budget = 0.6 * ((double)free_b + (double)ctx->arena_cap * sb);
     const int ne = (int)ctx->winds.size();
     if ((double)(T + 1 + ne) * sb <= budget) return 1;  // keep every state: no recomputation
     int K = std::max(2, (int)std::ceil(std::sqrt((double)T)));
@@ -422,32 +443,44 @@ int steps_to_ckpt(const pf_ctx* c, int t) {
 int diff_steps(pf_ctx* ctx, int T) {
     const int end = ctx->step + T;
     const int kern = choose_kernel(ctx);
+    // with K == 1 every state is saved: blocked launches write all of them into
+    // consecutive tape slots
+    const bool all_states = ctx->tape_valid && ctx->K == 1;
     while (ctx->step < end) {
         const int t = ctx->step;
         int rc = ensure_q(ctx, epoch_of(ctx, t));
         if (rc) return rc;
         int n = 1;
         if (kern == 2) {
-            n = std::min({blocked_k(ctx), end - t, next_epoch_start(ctx, t) - t, steps_to_ckpt(ctx, t)});
+            n = std::min({blocked_k(ctx), end - t, next_epoch_start(ctx, t) - t});
+            if (!all_states) n = std::min(n, steps_to_ckpt(ctx, t));
         }
-        float* out;
-        if (ctx->tape_valid && is_ckpt_step(ctx, t + n)) {
-            out = take_slot(ctx, &rc);
+        float* out = nullptr;
+        float* all_out = nullptr;
+        if (all_states) {
+            const int s = take_slots(ctx, n, &rc);
             if (rc) return rc;
-            ctx->ckpts.push_back({t + n, out});
+            for (int i = 0; i < n; ++i) ctx->ckpts.push_back({t + 1 + i, s + i});
+            all_out = slot_ptr(ctx, s);
+        } else if (ctx->tape_valid && is_ckpt_step(ctx, t + n)) {
+            const int s = take_slots(ctx, 1, &rc);
+            if (rc) return rc;
+            ctx->ckpts.push_back({t + n, s});
+            out = slot_ptr(ctx, s);
         } else {
             out = (ctx->cur_ab == ctx->work[0]) ? ctx->work[1] : ctx->work[0];
         }
         if (kern == 2) {
-            if ((rc = diff_blocked_launch(ctx, ctx->cur_ab, ctx->pc, n, out, nullptr))) return rc;
+            if ((rc = diff_blocked_launch(ctx, ctx->cur_ab, ctx->pc, n, out, all_out))) return rc;
         } else {
+            float* dst = out ? out : all_out;
             {
                 LaunchScope ls(ctx, K_FSTEP);
-                launch_diff_step(ctx->H, ctx->W, ctx->P, ctx->pc, ctx->cur_ab, out, ctx->q, ctx->st);
+                launch_diff_step(ctx->H, ctx->W, ctx->P, ctx->pc, ctx->cur_ab, dst, ctx->q, ctx->st);
             }
             if ((rc = check_launch(ctx, "diff step"))) return rc;
         }
-        ctx->cur_ab = out;
+        ctx->cur_ab = out ? out : all_out + (size_t)(n - 1) * 2 * plane_elems(ctx);
         ctx->step = t + n;
     }
     return PF_OK;
@@ -456,7 +489,14 @@ int diff_steps(pf_ctx* ctx, int T) {
 void tape_reset(pf_ctx* ctx) {
     ctx->tape_valid = false;
     ctx->ckpts.clear();
-    ctx->slots_used = 0;
+    // the current state may live in the arena: move it to a work buffer first
+    if (ctx->arena && ctx->cur_ab && ctx->cur_ab >= ctx->arena &&
+        ctx->cur_ab < ctx->arena + (size_t)ctx->arena_cap * 2 * plane_elems(ctx)) {
+        float* w = ctx->work[0];
+        cudaMemcpyAsync(w, ctx->cur_ab, diff_state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->st);
+        ctx->cur_ab = w;
+    }
+    ctx->arena_used = 0;
 }
 
 // Start a fresh tape at the current step with the current state as checkpoint 0.
@@ -467,13 +507,15 @@ int tape_begin(pf_ctx* ctx, int T) {
     ctx->t_p_h = ctx->p_h; ctx->t_c1 = ctx->c1; ctx->t_c2 = ctx->c2; ctx->t_a = ctx->a;
     ctx->t_pc = ctx->pc; ctx->t_l = ctx->l;
     ctx->t_version = ctx->version;
-    int rc;
-    float* s0 = take_slot(ctx, &rc);
+    const int want = ctx->K == 1 ? T + 1 : T / ctx->K + (int)ctx->winds.size() + 2;
+    int rc = arena_reserve(ctx, want);
     if (rc) return rc;
-    if (ctx->cur_ab != s0)
-        CK(cudaMemcpyAsync(s0, ctx->cur_ab, diff_state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->st));
+    const int s = take_slots(ctx, 1, &rc);
+    if (rc) return rc;
+    float* s0 = slot_ptr(ctx, s);
+    CK(cudaMemcpyAsync(s0, ctx->cur_ab, diff_state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->st));
     ctx->cur_ab = s0;
-    ctx->ckpts.push_back({ctx->step, s0});
+    ctx->ckpts.push_back({ctx->step, s});
     ctx->tape_valid = true;
     return PF_OK;
 }
@@ -835,7 +877,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
         ctx->partials = (double*)p;
         ctx->gacc = ctx->partials + (size_t)nblk * 4;
     }
-    const int segmax = ctx->K;  // states s0 .. s0+K-1 of one segment, consecutive
+    const int segmax = ctx->K > 1 ? ctx->K : 0;  // states s0 .. s0+K-1 of one segment, consecutive
     if (ctx->seg_cap < segmax) {
         if (ctx->seg_buf) dfree(ctx, ctx->seg_buf);
         ctx->seg_buf = nullptr;
@@ -848,7 +890,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
     const size_t selems = 2 * pe;
     const int kern = choose_kernel(ctx);
     CUtensorMap tseg;
-    const bool adj_blocked = kern == 2 && adjoint_blocked_configure() == 0 &&
+    const bool adj_blocked = kern == 2 && ctx->seg_buf && adjoint_blocked_configure() == 0 &&
                              encode_f32_3d(&tseg, ctx->seg_buf, ctx->P, ctx->H, 2 * ctx->seg_cap,
                                            diff_blocked_box_cols(), diff_blocked_box_rows(), 2);
     cudaGetLastError();
@@ -885,66 +927,90 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             return fail(ctx, PF_ECUDA, "memset Gq failed");
         return PF_OK;
     };
+    // switch q (and the dL/dq accumulator) to the epoch of step t
+    auto enter_epoch = [&](int t) -> int {
+        const int e = epoch_of(ctx, t);
+        if (e == cur_e) return PF_OK;
+        int r;
+        if (cur_e >= 0 && (r = flush(cur_e))) return r;
+        cur_e = e;
+        {
+            LaunchScope ls(ctx, K_PREP);
+            launch_prep(prep_args(ctx, e, true), ctx->q, ctx->st);
+        }
+        if ((r = check_launch(ctx, "prep"))) return r;
+        ctx->q_key_epoch = -1;  // the cache holds the recorded parameters' q now
+        return PF_OK;
+    };
     const float pc = ctx->t_pc;
-    for (int si = (int)ctx->ckpts.size() - 1; si >= 0; --si) {
-        const int s0 = ctx->ckpts[si].first;
-        const int s1 = (si + 1 < (int)ctx->ckpts.size()) ? ctx->ckpts[si + 1].first : T_end;
-        if (s1 <= s0) continue;
-        const int e = epoch_of(ctx, s0);
-        if (e != cur_e) {
-            if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
-            cur_e = e;
-            // q of epoch e with the recorded parameters (the cache may hold another epoch)
-            {
-                LaunchScope ls(ctx, K_PREP);
-                launch_prep(prep_args(ctx, e, true), ctx->q, ctx->st);
-            }
-            if ((rc = check_launch(ctx, "prep"))) return rc;
-            ctx->q_key_epoch = -1;
-        }
-        // the segment's states s0 .. s1-1, consecutive in the segment buffer: the
-        // checkpoint copied to slot 0, the rest recomputed
-        std::vector<const float*> states;
-        for (int t = s0; t < s1; ++t) states.push_back(ctx->seg_buf + (size_t)(t - s0) * selems);
-        CK(cudaMemcpyAsync((void*)states[0], ctx->ckpts[si].second, sbytes, cudaMemcpyDeviceToDevice, ctx->st));
-        for (int t = s0; t < s1 - 1;) {
-            if (kern == 2) {
-                const int n = std::min(blocked_k(ctx), s1 - 1 - t);
-                if ((rc = diff_blocked_launch(ctx, states[t - s0], pc, n, nullptr, (float*)states[t - s0 + 1])))
-                    return rc;
-                t += n;
-            } else {
-                {
-                    LaunchScope ls(ctx, K_FSTEP);
-                    launch_diff_step(ctx->H, ctx->W, ctx->P, pc, states[t - s0], (float*)states[t - s0 + 1], ctx->q,
-                                     ctx->st);
-                }
-                if ((rc = check_launch(ctx, "diff step (recompute)"))) return rc;
-                t += 1;
-            }
-        }
-        if (adj_blocked) {
-            for (int t1 = s1; t1 > s0;) {
-                const int n = std::min(adjoint_blocked_max_steps(), t1 - s0);
+    // adjoint steps t = t1-1 .. t0 over states held consecutively in `buf` (state
+    // index z(t) = t - tbase), with its tensor map
+    auto adjoint_run = [&](const float* buf, const CUtensorMap* tmap, int tbase, int t0, int t1) -> int {
+        int r;
+        while (t1 > t0) {
+            if (tmap) {
+                const int n = std::min(adjoint_blocked_max_steps(), t1 - t0);
                 {
                     LaunchScope ls(ctx, K_ABLK, n);
-                    launch_adjoint_blocked(&tseg, &ctx->tmapQ, ctx->H, ctx->P, pc, t1 - 1 - s0, n, ctx->lam[lcur],
+                    launch_adjoint_blocked(tmap, &ctx->tmapQ, ctx->H, ctx->P, pc, t1 - 1 - tbase, n, ctx->lam[lcur],
                                            ctx->lam[1 - lcur], ctx->Gq, ctx->nsm, ctx->dflags, ctx->st);
                 }
-                if ((rc = check_launch(ctx, "adjoint blocked"))) return rc;
-                lcur = 1 - lcur;
+                if ((r = check_launch(ctx, "adjoint blocked"))) return r;
                 t1 -= n;
-            }
-        } else {
-            for (int t = s1 - 1; t >= s0; --t) {
+            } else {
                 {
                     LaunchScope ls(ctx, K_ADJ);
-                    launch_adjoint_step(ctx->H, ctx->W, ctx->P, pc, states[t - s0], ctx->q, ctx->lam[lcur],
-                                        ctx->lam[1 - lcur], ctx->Gq, ctx->st);
+                    launch_adjoint_step(ctx->H, ctx->W, ctx->P, pc, buf + (size_t)(t1 - 1 - tbase) * selems, ctx->q,
+                                        ctx->lam[lcur], ctx->lam[1 - lcur], ctx->Gq, ctx->st);
                 }
-                if ((rc = check_launch(ctx, "adjoint step"))) return rc;
-                lcur = 1 - lcur;
+                if ((r = check_launch(ctx, "adjoint step"))) return r;
+                t1 -= 1;
             }
+            lcur = 1 - lcur;
+        }
+        return PF_OK;
+    };
+    if (ctx->K == 1) {
+        // every state is on the tape: no recomputation; runs end at wind-epoch starts
+        CUtensorMap tarena;
+        const bool ok = kern == 2 && adjoint_blocked_configure() == 0 &&
+                        encode_f32_3d(&tarena, ctx->arena, ctx->P, ctx->H, 2 * ctx->arena_cap,
+                                      diff_blocked_box_cols(), diff_blocked_box_rows(), 2);
+        cudaGetLastError();
+        const int t_start = ctx->tape_start;
+        for (int t1 = T_end; t1 > t_start;) {
+            if ((rc = enter_epoch(t1 - 1))) return rc;
+            const int t0 = std::max(t_start, ctx->winds[cur_e].from);
+            if ((rc = adjoint_run(ctx->arena, ok ? &tarena : nullptr, t_start, t0, t1))) return rc;
+            t1 = t0;
+        }
+    } else {
+        for (int si = (int)ctx->ckpts.size() - 1; si >= 0; --si) {
+            const int s0 = ctx->ckpts[si].first;
+            const int s1 = (si + 1 < (int)ctx->ckpts.size()) ? ctx->ckpts[si + 1].first : T_end;
+            if (s1 <= s0) continue;
+            if ((rc = enter_epoch(s0))) return rc;
+            // the segment's states s0 .. s1-1, consecutive in the segment buffer: the
+            // checkpoint copied to slot 0, the rest recomputed
+            float* seg = ctx->seg_buf;
+            CK(cudaMemcpyAsync(seg, slot_ptr(ctx, ctx->ckpts[si].second), sbytes, cudaMemcpyDeviceToDevice, ctx->st));
+            for (int t = s0; t < s1 - 1;) {
+                const float* in = seg + (size_t)(t - s0) * selems;
+                float* nxt = seg + (size_t)(t - s0 + 1) * selems;
+                if (kern == 2) {
+                    const int n = std::min(blocked_k(ctx), s1 - 1 - t);
+                    if ((rc = diff_blocked_launch(ctx, in, pc, n, nullptr, nxt))) return rc;
+                    t += n;
+                } else {
+                    {
+                        LaunchScope ls(ctx, K_FSTEP);
+                        launch_diff_step(ctx->H, ctx->W, ctx->P, pc, in, nxt, ctx->q, ctx->st);
+                    }
+                    if ((rc = check_launch(ctx, "diff step (recompute)"))) return rc;
+                    t += 1;
+                }
+            }
+            if ((rc = adjoint_run(seg, adj_blocked ? &tseg : nullptr, s0, s0, s1))) return rc;
         }
     }
     if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
