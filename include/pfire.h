@@ -141,6 +141,25 @@ int pf_ignition_map(pf_ctx* ctx, float* P_out);
  * (nullable; if given the call is synchronous). Context-free; runs on cuda_stream. */
 int pf_loss_bce(const float* a, const float* y, int64_t n, float* dL_da, double* loss, void* cuda_stream);
 
+/* pf_loss_bce without any device allocation, for callers that may not allocate
+ * device memory themselves or through the library: code whose device memory is owned
+ * by an allocator with a fixed budget (a caching allocator or a reserved pool, where a
+ * stray cudaMalloc fragments the pool or exceeds the budget), and latency-critical loops
+ * in which the device-wide synchronisation of cudaMalloc / cudaFree is not acceptable.
+ * The arithmetic and arguments are those of pf_loss_bce; the reduction scratch is a
+ * statically allocated device array of 16385 doubles (128 KB, held by every GPU that
+ * loads the library until the process exits), which bounds n to
+ * PF_NOALLOC_BCE_MAX_N elements (larger n: PF_EINVAL, message via pf_last_error(NULL)).
+ * The first call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture. All calls share
+ * the array: calls whose work overlaps on the GPU (different streams, or concurrent host
+ * threads) race on it and must be serialised by the caller. Each call overwrites every
+ * entry it reads, so no clearing is needed. The paper has no counterpart: this is a
+ * deployment variant of pf_loss_bce. The loss may differ from pf_loss_bce's in the last
+ * bits (a different block partition of the same FP64 reduction); dL_da is identical. */
+#define PF_NOALLOC_BCE_MAX_N 67108864LL
+int pf_loss_bce_noalloc(const float* a, const float* y, int64_t n, float* dL_da, double* loss, void* cuda_stream);
+
 /* Kernel selection and checkpoint interval. Zero fields mean "choose automatically".
  *   kernel  1 = plain one-launch-per-step kernels, 2 = temporal-blocked TMA kernels.
  *   k       steps per launch of the temporal-blocked kernels (1..16).

@@ -24,7 +24,8 @@ __all__ = [
     "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward",
     "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
     "pf_set_tuning", "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error",
-    "pf_version", "FireModel", "DiffFire", "PfJob", "EXPORTED_SYMBOLS",
+    "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob",
+    "EXPORTED_SYMBOLS",
 ]
 
 PF_DISCRETE, PF_DIFF = 0, 1
@@ -39,7 +40,9 @@ EXPORTED_SYMBOLS = [
     "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
+    "pf_loss_bce_noalloc",
 ]
+PF_NOALLOC_BCE_MAX_N = 67108864
 
 
 class PFireError(RuntimeError):
@@ -94,6 +97,7 @@ def load():
             "pf_set_state": ([vp, i, vp], i),
             "pf_ignition_map": ([vp, vp], i),
             "pf_loss_bce": ([vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double), vp], i),
+            "pf_loss_bce_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double), vp], i),
             "pf_set_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_get_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_profile_read": ([vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
@@ -214,6 +218,18 @@ def pf_loss_bce(a, y, dL_da=None, want_loss=True, stream=None):
     _check(load().pf_loss_bce(_ptr(a, torch.float32, n, "a"), _ptr(y, torch.float32, n, "y"), n,
                               _ptr(dL_da, torch.float32, n, "dL_da"),
                               ctypes.byref(loss) if want_loss else None, _stream(stream)))
+    return loss.value if want_loss else None
+
+
+def pf_loss_bce_noalloc(a, y, dL_da=None, want_loss=True, stream=None, n=None):
+    """pf_loss_bce with its scratch in a static device array (no device allocation);
+    n defaults to a.numel() (an explicit n is passed through unchecked, for tests of the
+    size limit)."""
+    n = a.numel() if n is None else int(n)
+    loss = ctypes.c_double()
+    _check(load().pf_loss_bce_noalloc(_ptr(a, torch.float32, None, "a"), _ptr(y, torch.float32, None, "y"), n,
+                                      _ptr(dL_da, torch.float32, None, "dL_da"),
+                                      ctypes.byref(loss) if want_loss else None, _stream(stream)))
     return loss.value if want_loss else None
 
 

@@ -60,6 +60,10 @@ long fault_alloc_at() {
 
 }  // namespace
 
+namespace pf {
+void set_context_free_error(const char* msg) { g_last_error = msg; }
+}  // namespace pf
+
 struct pf_ctx {
     int H = 0, W = 0, P = 0, form = 0, R = 1;
     uint64_t seed = 0;
