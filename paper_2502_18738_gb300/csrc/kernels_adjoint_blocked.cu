@@ -115,7 +115,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             failed = true;
             break;
         }
-        // prologue: q -> TMEM, dL/dq accumulator := 0, lambda' of the region -> registers
+        // prologue: lambda' of the region -> registers (all loads issued before any
+        // TMEM access, so they overlap), q -> TMEM, dL/dq accumulator := 0
+#pragma unroll
+        for (int k = 0; k < kM; ++k) {
+            const int gr = r0 + ys + k, gc = c0 + x;
+            const bool in = gr >= 0 && gr < H && gc >= 0 && gc < pitch;
+            la[k] = in ? __ldg(lam_in + (size_t)gr * pitch + gc) : 0.0f;
+            lb[k] = in ? __ldg(lam_in + gplane + (size_t)gr * pitch + gc) : 0.0f;
+        }
 #pragma unroll
         for (int k = 0; k < kM; ++k) {
             const int y = ys + k;
@@ -125,12 +133,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 qv[d] = sm.q[d * kPlane + y * kCT + x];
                 z[d] = 0.0f;
             }
-            tmem_st8(tbase + 16 * k, qv);
-            tmem_st8(tbase + 16 * k + 8, z);
-            const int gr = r0 + y, gc = c0 + x;
-            const bool in = gr >= 0 && gr < H && gc >= 0 && gc < pitch;
-            la[k] = in ? lam_in[(size_t)gr * pitch + gc] : 0.0f;
-            lb[k] = in ? lam_in[gplane + (size_t)gr * pitch + gc] : 0.0f;
+            tmem_st8_nc(tbase + 16 * k, qv);
+            tmem_st8_nc(tbase + 16 * k + 8, z);
         }
         tmem_wait_st();
         fence_proxy_async();
@@ -146,79 +150,125 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const float* stA = sm.st[s];
             const float* stB = sm.st[s] + kPlane;
-            float acc[3][kM + 2];
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int k = 0; k < kM + 2; ++k) acc[j][k] = 0.0f;
+            // rows whose targets still matter at this step: the halo shrinks by one per step
+            const int grow = n - m;
+            const int ylo = kHalo - grow > 1 ? kHalo - grow : 1;
+            const int yhi = kRT - kHalo + grow < kRT - 1 ? kRT - kHalo + grow : kRT - 1;
             const bool xin = x >= 1 && x < kCT - 1;
             const int xl = xin ? x - 1 : x, xr = xin ? x + 1 : x;
+            // contributions to source rows ys-1+R, as a rolling window of three rows
+            // (R = k, k+1, k+2 while cell k is processed) x three columns (x-1, x, x+1)
+            float w0[3] = {0.f, 0.f, 0.f}, w1[3] = {0.f, 0.f, 0.f}, w2[3] = {0.f, 0.f, 0.f};
+            float own[kM];  // this thread's column, rows ys .. ys+7, before cross-warp / strip terms
+            // b of rows y-1, y, y+1 in columns x-1, x, x+1 (rolling register window)
+            float bl[3], bc[3], br[3];
+            {
+                const int y0 = ys > 0 ? ys - 1 : 0;
+                bl[0] = stB[y0 * kCT + xl]; bc[0] = stB[y0 * kCT + x]; br[0] = stB[y0 * kCT + xr];
+                bl[1] = stB[ys * kCT + xl]; bc[1] = stB[ys * kCT + x]; br[1] = stB[ys * kCT + xr];
+            }
+            uint32_t cur[16], nxt[16];
+            if (ys >= ylo && ys < yhi) {
+                tmem_ld16_async(tbase, cur);
+                tmem_wait_ld16(cur);
+            }
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 const int y = ys + k;
-                float qv[8], gv[8];
-                tmem_ld8(tbase + 16 * k, qv);
-                tmem_ld8(tbase + 16 * k + 8, gv);
-                const int yu = y > 0 ? y - 1 : y, yd = y < kRT - 1 ? y + 1 : y;
-                if (xin && y >= 1 && y < kRT - 1) {
-                    // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
-                    const float nb[8] = {stB[yu * kCT + xl], stB[yu * kCT + x], stB[yu * kCT + xr],
-                                         stB[y * kCT + xl],  stB[y * kCT + xr], stB[yd * kCT + xl],
-                                         stB[yd * kCT + x],  stB[yd * kCT + xr]};
-                    float f[8], P = 0.0f;
-#pragma unroll
-                    for (int d = 0; d < 8; ++d) {
-                        const float xx = nb[d] * qv[d];
-                        f[d] = 1.0f - xx;
-                        P = fmaf(xx, 1.0f - P, P);
-                    }
-                    float pre[8], suf[8];
-                    pre[0] = 1.0f;
-#pragma unroll
-                    for (int d = 1; d < 8; ++d) pre[d] = pre[d - 1] * f[d - 1];
-                    suf[7] = 1.0f;
-#pragma unroll
-                    for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
-                    float av, ua;
-                    a_decode(stA[y * kCT + x], av, ua);
-                    const float ln = la[k] + lb[k];
-                    const float lP = ln * ua;
-                    la[k] = la[k] - ln * P;
-#pragma unroll
-                    for (int d = 0; d < 8; ++d) {
-                        const float loo = pre[d] * suf[d];
-                        gv[d] = fmaf(lP * nb[d], loo, gv[d]);
-                        acc[dir_dc(d) + 1][k + 1 + dir_dr(d)] += lP * qv[d] * loo;
-                    }
+                const bool act = y >= ylo && y < yhi;  // uniform across the warp
+                const bool act_next = k + 1 < kM && (y + 1) >= ylo && (y + 1) < yhi;
+                if (act_next) tmem_ld16_async(tbase + 16 * (k + 1), nxt);  // overlaps this cell's math
+                {
+                    const int yd = y + 1 < kRT ? y + 1 : y;
+                    bl[2] = stB[yd * kCT + xl]; bc[2] = stB[yd * kCT + x]; br[2] = stB[yd * kCT + xr];
                 }
-                tmem_st8(tbase + 16 * k + 8, gv);
+                if (act) {
+                    float qv[8], gv[8];
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) {
+                        qv[d] = __uint_as_float(cur[d]);
+                        gv[d] = __uint_as_float(cur[8 + d]);
+                    }
+                    if (xin) {
+                        // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
+                        const float nb[8] = {bl[0], bc[0], br[0], bl[1], br[1], bl[2], bc[2], br[2]};
+                        float f[8], P = 0.0f;
+#pragma unroll
+                        for (int d = 0; d < 8; ++d) {
+                            const float xx = nb[d] * qv[d];
+                            f[d] = fmaf(-nb[d], qv[d], 1.0f);
+                            P = fmaf(xx, 1.0f - P, P);
+                        }
+                        float pre[8], suf[8];
+                        pre[0] = 1.0f;
+#pragma unroll
+                        for (int d = 1; d < 8; ++d) pre[d] = pre[d - 1] * f[d - 1];
+                        suf[7] = 1.0f;
+#pragma unroll
+                        for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
+                        float av, ua;
+                        a_decode(stA[y * kCT + x], av, ua);
+                        const float ln = la[k] + lb[k];
+                        const float lP = ln * ua;
+                        la[k] = fmaf(-ln, P, la[k]);
+#pragma unroll
+                        for (int d = 0; d < 8; ++d) {
+                            const float t = lP * (pre[d] * suf[d]);   // l_P_j x leave-one-out product
+                            gv[d] = fmaf(t, nb[d], gv[d]);
+                            const float c = t * qv[d];
+                            const int j = dir_dc(d) + 1;
+                            if (dir_dr(d) < 0) w0[j] += c; else if (dir_dr(d) == 0) w1[j] += c; else w2[j] += c;
+                        }
+                    }
+                    tmem_st8_nc(tbase + 16 * k + 8, gv);
+                }
+                if (act_next) {
+                    tmem_wait_ld16(nxt);
+#pragma unroll
+                    for (int i2 = 0; i2 < 16; ++i2) cur[i2] = nxt[i2];
+                }
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    bl[j] = bl[j + 1]; bc[j] = bc[j + 1]; br[j] = br[j + 1];
+                }
+                // row R = k (source row ys + k - 1) is complete
+                if (k == 0) {
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) sm.vtop[ex][strip][j][x] = w0[j];
+                } else {
+                    const float fr = __shfl_down_sync(0xffffffffu, w0[0], 1);  // from column x + 1
+                    const float fl = __shfl_up_sync(0xffffffffu, w0[2], 1);    // from column x - 1
+                    own[k - 1] = w0[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
+                    if (x == 31) sm.el2r[ex][strip][k - 1] = w0[2];
+                    if (x == 32) sm.er2l[ex][strip][k - 1] = w0[0];
+                }
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    w0[j] = w1[j];
+                    w1[j] = w2[j];
+                    w2[j] = 0.0f;
+                }
+            }
+            // rows R = 8 (source row ys + 7) and R = 9 (the next strip's first row)
+            {
+                const float fr = __shfl_down_sync(0xffffffffu, w0[0], 1);
+                const float fl = __shfl_up_sync(0xffffffffu, w0[2], 1);
+                own[kM - 1] = w0[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
+                if (x == 31) sm.el2r[ex][strip][kM - 1] = w0[2];
+                if (x == 32) sm.er2l[ex][strip][kM - 1] = w0[0];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) sm.vbot[ex][strip][j][x] = w1[j];
             }
             tmem_wait_st();
-            // publish the contributions that leave this thread's strip or warp
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                sm.vtop[ex][strip][j][x] = acc[j][0];
-                sm.vbot[ex][strip][j][x] = acc[j][kM + 1];
-            }
-            if (x == 31) {
-#pragma unroll
-                for (int k = 0; k < kM; ++k) sm.el2r[ex][strip][k] = acc[2][k + 1];
-            }
-            if (x == 32) {
-#pragma unroll
-                for (int k = 0; k < kM; ++k) sm.er2l[ex][strip][k] = acc[0][k + 1];
-            }
             fence_proxy_async();  // stage s fully read before it is refilled by TMA
             __syncthreads();
             if (tid == 0 && i + 2 < total) issue_state(i + 2);
             // gather: lambda_b at the sources of this strip
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
-                float fr = __shfl_down_sync(0xffffffffu, acc[0][k + 1], 1);  // from column x + 1
-                float fl = __shfl_up_sync(0xffffffffu, acc[2][k + 1], 1);    // from column x - 1
-                if (lane == 31) fr = (x == 31) ? sm.er2l[ex][strip][k] : 0.0f;
-                if (lane == 0) fl = (x == 32) ? sm.el2r[ex][strip][k] : 0.0f;
-                float v = fmaf(pc, lb[k], acc[1][k + 1] + fr + fl);
+                float v = fmaf(pc, lb[k], own[k]);
+                if (lane == 31 && x == 31) v += sm.er2l[ex][strip][k];
+                if (lane == 0 && x == 32) v += sm.el2r[ex][strip][k];
                 if (k == 0 && strip > 0) {
                     v += sm.vbot[ex][strip - 1][1][x];
                     if (x + 1 < kCT) v += sm.vbot[ex][strip - 1][0][x + 1];
@@ -245,8 +295,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const size_t j = (size_t)gr * pitch + gc;
                 lam_out[j] = la[k];
                 lam_out[gplane + j] = lb[k];
+                // fire-and-forget reductions (no load round trip); each cell receives
+                // exactly one add per launch, so the result does not depend on timing
 #pragma unroll
-                for (int d = 0; d < 8; ++d) Gq[d * gplane + j] += gv[d];
+                for (int d = 0; d < 8; ++d) atomicAdd(Gq + d * gplane + j, gv[d]);
             }
         }
     }
