@@ -150,38 +150,46 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const float* stA = sm.st[s];
             const float* stB = sm.st[s] + kPlane;
-            // rows whose targets still matter at this step: the halo shrinks by one per step
-            const int grow = n - m;
-            const int ylo = kHalo - grow > 1 ? kHalo - grow : 1;
-            const int yhi = kRT - kHalo + grow < kRT - 1 ? kRT - kHalo + grow : kRT - 1;
+            // every row but the region's edges is processed: skipping the rows the shrinking
+            // halo no longer needs costs more in branching than it saves
+            const int ylo = 1, yhi = kRT - 1;
             const bool xin = x >= 1 && x < kCT - 1;
             const int xl = xin ? x - 1 : x, xr = xin ? x + 1 : x;
-            // contributions to source rows ys-1+R, as a rolling window of three rows
-            // (R = k, k+1, k+2 while cell k is processed) x three columns (x-1, x, x+1)
-            float w0[3] = {0.f, 0.f, 0.f}, w1[3] = {0.f, 0.f, 0.f}, w2[3] = {0.f, 0.f, 0.f};
+            // contributions to source rows ys-1+R, as a ring of three rows (R = k, k+1,
+            // k+2 while cell k is processed; slot R % 3) x three columns (x-1, x, x+1).
+            // All ring indices are compile-time constants after unrolling.
+            float w[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
             float own[kM];  // this thread's column, rows ys .. ys+7, before cross-warp / strip terms
-            // b of rows y-1, y, y+1 in columns x-1, x, x+1 (rolling register window)
-            float bl[3], bc[3], br[3];
+            // b of rows y-1, y, y+1 in columns x-1, x, x+1: ring slot (row - ys + 1) % 3
+            float bw[3][3];
             {
                 const int y0 = ys > 0 ? ys - 1 : 0;
-                bl[0] = stB[y0 * kCT + xl]; bc[0] = stB[y0 * kCT + x]; br[0] = stB[y0 * kCT + xr];
-                bl[1] = stB[ys * kCT + xl]; bc[1] = stB[ys * kCT + x]; br[1] = stB[ys * kCT + xr];
+                bw[0][0] = stB[y0 * kCT + xl]; bw[0][1] = stB[y0 * kCT + x]; bw[0][2] = stB[y0 * kCT + xr];
+                bw[1][0] = stB[ys * kCT + xl]; bw[1][1] = stB[ys * kCT + x]; bw[1][2] = stB[ys * kCT + xr];
             }
-            uint32_t cur[16], nxt[16];
+            uint32_t tm[2][16];  // TMEM q | dL/dq of cells k (slot k & 1) and k + 1
             if (ys >= ylo && ys < yhi) {
-                tmem_ld16_async(tbase, cur);
-                tmem_wait_ld16(cur);
+                tmem_ld16_async(tbase, tm[0]);
+                tmem_wait_ld16(tm[0]);
             }
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 const int y = ys + k;
                 const bool act = y >= ylo && y < yhi;  // uniform across the warp
                 const bool act_next = k + 1 < kM && (y + 1) >= ylo && (y + 1) < yhi;
+                uint32_t(&cur)[16] = tm[k & 1];
+                uint32_t(&nxt)[16] = tm[(k + 1) & 1];
                 if (act_next) tmem_ld16_async(tbase + 16 * (k + 1), nxt);  // overlaps this cell's math
+                float(&bu)[3] = bw[k % 3];
+                float(&bm)[3] = bw[(k + 1) % 3];
+                float(&bd)[3] = bw[(k + 2) % 3];
                 {
                     const int yd = y + 1 < kRT ? y + 1 : y;
-                    bl[2] = stB[yd * kCT + xl]; bc[2] = stB[yd * kCT + x]; br[2] = stB[yd * kCT + xr];
+                    bd[0] = stB[yd * kCT + xl]; bd[1] = stB[yd * kCT + x]; bd[2] = stB[yd * kCT + xr];
                 }
+                float(&wu)[3] = w[k % 3];        // source row y - 1 (R = k)
+                float(&wm)[3] = w[(k + 1) % 3];  // source row y
+                float(&wd)[3] = w[(k + 2) % 3];  // source row y + 1
                 if (act) {
                     float qv[8], gv[8];
 #pragma unroll
@@ -191,14 +199,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     if (xin) {
                         // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
-                        const float nb[8] = {bl[0], bc[0], br[0], bl[1], br[1], bl[2], bc[2], br[2]};
-                        float f[8], P = 0.0f;
+                        const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
+                        float f[8];
 #pragma unroll
-                        for (int d = 0; d < 8; ++d) {
-                            const float xx = nb[d] * qv[d];
-                            f[d] = fmaf(-nb[d], qv[d], 1.0f);
-                            P = fmaf(xx, 1.0f - P, P);
-                        }
+                        for (int d = 0; d < 8; ++d) f[d] = fmaf(-nb[d], qv[d], 1.0f);
                         float pre[8], suf[8];
                         pre[0] = 1.0f;
 #pragma unroll
@@ -206,6 +210,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         suf[7] = 1.0f;
 #pragma unroll
                         for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
+                        // P enters only l_a = l_a' - l_n P here, where 1 - S's absolute
+                        // error (a few 1e-8) is harmless; the forward keeps the recurrence
+                        const float P = 1.0f - pre[7] * f[7];
                         float av, ua;
                         a_decode(stA[y * kCT + x], av, ua);
                         const float ln = la[k] + lb[k];
@@ -217,47 +224,37 @@ __global__ void __launch_bounds__(kThreads, 1)
                             gv[d] = fmaf(t, nb[d], gv[d]);
                             const float c = t * qv[d];
                             const int j = dir_dc(d) + 1;
-                            if (dir_dr(d) < 0) w0[j] += c; else if (dir_dr(d) == 0) w1[j] += c; else w2[j] += c;
+                            if (dir_dr(d) < 0) wu[j] += c; else if (dir_dr(d) == 0) wm[j] += c; else wd[j] += c;
                         }
                     }
                     tmem_st8_nc(tbase + 16 * k + 8, gv);
                 }
-                if (act_next) {
-                    tmem_wait_ld16(nxt);
-#pragma unroll
-                    for (int i2 = 0; i2 < 16; ++i2) cur[i2] = nxt[i2];
-                }
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    bl[j] = bl[j + 1]; bc[j] = bc[j + 1]; br[j] = br[j + 1];
-                }
+                if (act_next) tmem_wait_ld16(nxt);
                 // row R = k (source row ys + k - 1) is complete
                 if (k == 0) {
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) sm.vtop[ex][strip][j][x] = w0[j];
+                    for (int j = 0; j < 3; ++j) sm.vtop[ex][strip][j][x] = wu[j];
                 } else {
-                    const float fr = __shfl_down_sync(0xffffffffu, w0[0], 1);  // from column x + 1
-                    const float fl = __shfl_up_sync(0xffffffffu, w0[2], 1);    // from column x - 1
-                    own[k - 1] = w0[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
-                    if (x == 31) sm.el2r[ex][strip][k - 1] = w0[2];
-                    if (x == 32) sm.er2l[ex][strip][k - 1] = w0[0];
+                    const float fr = __shfl_down_sync(0xffffffffu, wu[0], 1);  // from column x + 1
+                    const float fl = __shfl_up_sync(0xffffffffu, wu[2], 1);    // from column x - 1
+                    own[k - 1] = wu[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
+                    if (x == 31) sm.el2r[ex][strip][k - 1] = wu[2];
+                    if (x == 32) sm.er2l[ex][strip][k - 1] = wu[0];
                 }
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    w0[j] = w1[j];
-                    w1[j] = w2[j];
-                    w2[j] = 0.0f;
-                }
+                for (int j = 0; j < 3; ++j) wu[j] = 0.0f;  // the slot becomes row R = k + 3
             }
-            // rows R = 8 (source row ys + 7) and R = 9 (the next strip's first row)
+            // rows R = 8 (source row ys + 7, slot 8 % 3) and R = 9 (the next strip's first row)
             {
-                const float fr = __shfl_down_sync(0xffffffffu, w0[0], 1);
-                const float fl = __shfl_up_sync(0xffffffffu, w0[2], 1);
-                own[kM - 1] = w0[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
-                if (x == 31) sm.el2r[ex][strip][kM - 1] = w0[2];
-                if (x == 32) sm.er2l[ex][strip][kM - 1] = w0[0];
+                float(&w8)[3] = w[kM % 3];
+                float(&w9)[3] = w[(kM + 1) % 3];
+                const float fr = __shfl_down_sync(0xffffffffu, w8[0], 1);
+                const float fl = __shfl_up_sync(0xffffffffu, w8[2], 1);
+                own[kM - 1] = w8[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
+                if (x == 31) sm.el2r[ex][strip][kM - 1] = w8[2];
+                if (x == 32) sm.er2l[ex][strip][kM - 1] = w8[0];
 #pragma unroll
-                for (int j = 0; j < 3; ++j) sm.vbot[ex][strip][j][x] = w1[j];
+                for (int j = 0; j < 3; ++j) sm.vbot[ex][strip][j][x] = w9[j];
             }
             tmem_wait_st();
             fence_proxy_async();  // stage s fully read before it is refilled by TMA

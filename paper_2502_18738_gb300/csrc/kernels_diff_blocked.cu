@@ -105,37 +105,40 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < n; ++s) {
             const float* src = sm.b[cur];
             float* dst = sm.b[cur ^ 1];
-            // rolling window over rows ys-1 .. ys+kM of columns x-1, x, x+1
-            float wl[3], wc[3], wr[3];
+            // ring of b rows ys-1 .. ys+kM (slot (row - ys + 1) % 3) in columns x-1, x, x+1
+            float bw[3][3];
             const int xl = xin ? x - 1 : x, xr = xin ? x + 1 : x;
             const int y_first = ys > 0 ? ys - 1 : 0;
-            wl[0] = src[y_first * kCT + xl]; wc[0] = src[y_first * kCT + x]; wr[0] = src[y_first * kCT + xr];
-            wl[1] = src[ys * kCT + xl];      wc[1] = src[ys * kCT + x];      wr[1] = src[ys * kCT + xr];
+            bw[0][0] = src[y_first * kCT + xl]; bw[0][1] = src[y_first * kCT + x]; bw[0][2] = src[y_first * kCT + xr];
+            bw[1][0] = src[ys * kCT + xl];      bw[1][1] = src[ys * kCT + x];      bw[1][2] = src[ys * kCT + xr];
 #pragma unroll
             for (int m = 0; m < kM; ++m) {
                 const int y = ys + m;
+                float(&bu)[3] = bw[m % 3];
+                float(&bm)[3] = bw[(m + 1) % 3];
+                float(&bd)[3] = bw[(m + 2) % 3];
                 const int yn = y + 1 < kRT ? y + 1 : y;
-                wl[2] = src[yn * kCT + xl]; wc[2] = src[yn * kCT + x]; wr[2] = src[yn * kCT + xr];
-                float bnew = wc[1];
-                if (xin && y >= 1 && y < kRT - 1) {
-                    // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
-                    const float nb[8] = {wl[0], wc[0], wr[0], wl[1], wr[1], wl[2], wc[2], wr[2]};
-                    float P = 0.0f, S = 1.0f;
+                bd[0] = src[yn * kCT + xl]; bd[1] = src[yn * kCT + x]; bd[2] = src[yn * kCT + xr];
+                if (y >= 1 && y < kRT - 1) {  // the region's edge rows are never updated
+                    float bnew = bm[1];
+                    if (xin) {
+                        // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
+                        const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
+                        float P = 0.0f, S = 1.0f;
 #pragma unroll
-                    for (int d = 0; d < 8; ++d) {
-                        const float xx = nb[d] * q[m][d];
-                        P = fmaf(xx, 1.0f - P, P);
-                        S *= 1.0f - xx;
+                        for (int d = 0; d < 8; ++d) {
+                            const float xx = nb[d] * q[m][d];
+                            P = fmaf(xx, 1.0f - P, P);
+                            S *= 1.0f - xx;
+                        }
+                        float a, ua;
+                        a_decode(A[m], a, ua);
+                        const float nn = ua * P;
+                        A[m] = a_encode(a + nn, ua * S);
+                        bnew = fmaf(pc, bm[1], nn);
                     }
-                    float a, ua;
-                    a_decode(A[m], a, ua);
-                    const float nn = ua * P;
-                    A[m] = a_encode(a + nn, ua * S);
-                    bnew = fmaf(pc, wc[1], nn);
+                    dst[y * kCT + x] = bnew;
                 }
-                dst[y * kCT + x] = bnew;
-                wl[0] = wl[1]; wc[0] = wc[1]; wr[0] = wr[1];
-                wl[1] = wl[2]; wc[1] = wc[2]; wr[1] = wr[2];
             }
             __syncthreads();
             cur ^= 1;
