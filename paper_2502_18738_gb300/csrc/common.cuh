@@ -62,7 +62,31 @@ __device__ __forceinline__ void a_decode(float A, float& a, float& ua) {
 }
 __device__ __forceinline__ float a_encode(float a, float ua) { return a < 0.5f ? a : -ua; }
 
-// ---------------------------------------------------------------- launchers
+// Scaled adjoint. Ahead of the fire the exact lambda grows about 4x per step backwards
+// in time while the states it multiplies shrink as fast; their products, which carry
+// the (pulled) front's sensitivity, stay O(1), but lambda itself overflows FP32 within
+// ~60 steps. The adjoint therefore stores mu_j = lambda_j * 2^-sigma_j with the per-cell
+// exponent sigma_j = -floor(log2 a_j) of the cell's own state, clamped to [0, 100]
+// (0 for a >= 1/2), and rescales every transfer between cells by exact powers of two.
+// sigma = kSigmaZero marks a == 0 exactly (outside the light cone, or non-burnable):
+// there lambda multiplies only exact zeros and is held at 0.
+constexpr int kSigmaMax = 100;
+constexpr int kSigmaZero = 255;
+
+// 2^-sigma of a cell from its encoded state A (1 for a >= 1/2, >= 2^-100 otherwise)
+__device__ __forceinline__ float adj_unit_inv(float A) {
+    if (signbit(A)) return 1.0f;
+    return fmaxf(__int_as_float(__float_as_int(A) & 0x7f800000), 7.8886090522101181e-31f);  // 2^-100
+}
+__device__ __forceinline__ int adj_sigma(float A) {
+    if (__float_as_int(A) == 0) return kSigmaZero;
+    return 127 - (__float_as_int(adj_unit_inv(A)) >> 23);
+}
+// 2^sigma and 2^-sigma for sigma in [0, 100] (exact powers of two)
+__device__ __forceinline__ float adj_unit(int sigma) { return __int_as_float((sigma + 127) << 23); }
+__device__ __forceinline__ float adj_unit_inv_of(int sigma) { return __int_as_float((127 - sigma) << 23); }
+
+// ---------------------------------------------------------------- launchers// ---------------------------------------------------------------- launchers
 struct PrepArgs {
     int H, W, pitch;
     const float *E, *pveg, *pden, *V, *th;  // dense H*W, nullable
@@ -111,8 +135,13 @@ int diff_blocked_box_cols();
 int diff_blocked_configure();
 void launch_diff_blocked(const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc, int n,
                          float* out, float* all_out, size_t all_stride, int nsm, int* err, cudaStream_t s);
+// lam: scaled adjoint (mu_a, mu_b) [2][H][pitch]; sig: its exponents uint8 [H][pitch]
 void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float* ab, const float* q,
-                         const float* lam1, float* lam0, float* Gq, cudaStream_t s);
+                         const float* lam1, const uint8_t* sig1, float* lam0, uint8_t* sig0, float* Gq,
+                         cudaStream_t s);
+// terminal scaled adjoint from dL/da_T, dL/db_T (dense, nullable) and the state at T
+void launch_adjoint_init(const float* dLda, const float* dLdb, const float* ab, int H, int W, int pitch,
+                         float* lam, uint8_t* sig, cudaStream_t s);
 // temporal-blocked adjoint with TMEM working set: n <= adjoint_blocked_max_steps() steps
 // t = t1-1 .. t1-n per launch. tst: 3-D map over a buffer of consecutive states
 // (pitch, H, 2 * nstates), box {64, 64, 2}; the state at t1-1-m is state index zlast-m.
@@ -120,7 +149,8 @@ void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float*
 int adjoint_blocked_max_steps();
 int adjoint_blocked_configure();
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
-                            int n, const float* lam_in, float* lam_out, float* Gq, int nsm, int* err, cudaStream_t s);
+                            int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
+                            float* Gq, int nsm, int* err, cudaStream_t s);
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,
                                   cudaStream_t s);
 void launch_ignition_map_diff(int H, int W, int pitch, const float* ab, const float* q, float* P,

@@ -16,6 +16,8 @@
 //       - gathers l_b_i = p_c l_b'_i + sum of the C arriving at i: within a thread's
 //         strip directly, across lanes by warp shuffles, across warps and strips through
 //         small double-buffered shared-memory exchange rows (no atomics, fixed order);
+//   * carries lambda in the scaled form of common.cuh (per-cell power-of-two exponents
+//     from the cell's own state, so it stays finite ahead of the fire);
 //   * writes lambda at t0 for the interior and adds the tile's dL/dq into global memory.
 // The halo shrinks by one cell per step, so the 48 x 48 interior is exact for n <= 7.
 #include <cuda.h>
@@ -55,7 +57,8 @@ __device__ __forceinline__ void origin(int tile, int tiles_x, int& r0, int& c0) 
 __global__ void __launch_bounds__(kThreads, 1)
     k_adjoint_blocked(const __grid_constant__ CUtensorMap tst, const __grid_constant__ CUtensorMap tq, int H,
                       int pitch, float pc, int zlast, int n, int tiles_x, int ntiles,
-                      const float* __restrict__ lam_in, float* __restrict__ lam_out, float* __restrict__ Gq,
+                      const float* __restrict__ lam_in, const uint8_t* __restrict__ sig_in,
+                      float* __restrict__ lam_out, uint8_t* __restrict__ sig_out, float* __restrict__ Gq,
                       int* __restrict__ err) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
@@ -106,7 +109,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     bool failed = false;
-    float la[kM], lb[kM];
+    float la[kM], lb[kM];     // scaled adjoint mu of this thread's cells (lambda = mu 2^sigma)
+    uint32_t sgp[2];          // sigma at t + 1 of the 8 cells, 4 per word
     for (int l = 0; l < nloc && !failed; ++l) {
         const int tile = (int)blockIdx.x + l * (int)gridDim.x;
         int r0, c0;
@@ -117,12 +121,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         // prologue: lambda' of the region -> registers (all loads issued before any
         // TMEM access, so they overlap), q -> TMEM, dL/dq accumulator := 0
+        sgp[0] = sgp[1] = 0u;
 #pragma unroll
         for (int k = 0; k < kM; ++k) {
             const int gr = r0 + ys + k, gc = c0 + x;
             const bool in = gr >= 0 && gr < H && gc >= 0 && gc < pitch;
             la[k] = in ? __ldg(lam_in + (size_t)gr * pitch + gc) : 0.0f;
             lb[k] = in ? __ldg(lam_in + gplane + (size_t)gr * pitch + gc) : 0.0f;
+            const uint32_t sv = in ? (uint32_t)__ldg(sig_in + (size_t)gr * pitch + gc) : (uint32_t)kSigmaZero;
+            sgp[k >> 2] |= sv << (8 * (k & 3));
         }
 #pragma unroll
         for (int k = 0; k < kM; ++k) {
@@ -155,51 +162,68 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ylo = 1, yhi = kRT - 1;
             const bool xin = x >= 1 && x < kCT - 1;
             const int xl = xin ? x - 1 : x, xr = xin ? x + 1 : x;
+            uint32_t sgc[2] = {0u, 0u};  // sigma at t of the 8 cells (from the staged state)
+            float scl[kM];               // 2^(sigma(t+1) - sigma(t)) of each own cell (0 if masked)
             // contributions to source rows ys-1+R, as a ring of three rows (R = k, k+1,
-            // k+2 while cell k is processed; slot R % 3) x three columns (x-1, x, x+1).
-            // All ring indices are compile-time constants after unrolling.
+            // k+2 while cell k is processed; slot R % 3) x three columns (x-1, x, x+1),
+            // in the units of the source. Ring indices are compile-time constants.
             float w[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
             float own[kM];  // this thread's column, rows ys .. ys+7, before cross-warp / strip terms
-            // b of rows y-1, y, y+1 in columns x-1, x, x+1: ring slot (row - ys + 1) % 3
-            float bw[3][3];
+            // b and 2^-sigma(t) of rows y-1, y, y+1 in columns x-1, x, x+1: ring slot (row - ys + 1) % 3
+            float bw[3][3], uw[3][3];
             {
                 const int y0 = ys > 0 ? ys - 1 : 0;
-                bw[0][0] = stB[y0 * kCT + xl]; bw[0][1] = stB[y0 * kCT + x]; bw[0][2] = stB[y0 * kCT + xr];
-                bw[1][0] = stB[ys * kCT + xl]; bw[1][1] = stB[ys * kCT + x]; bw[1][2] = stB[ys * kCT + xr];
-            }
-            uint32_t tm[2][16];  // TMEM q | dL/dq of cells k (slot k & 1) and k + 1
-            if (ys >= ylo && ys < yhi) {
-                tmem_ld16_async(tbase, tm[0]);
-                tmem_wait_ld16(tm[0]);
+                const int cols[3] = {xl, x, xr};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    bw[0][c] = stB[y0 * kCT + cols[c]];
+                    uw[0][c] = adj_unit_inv(stA[y0 * kCT + cols[c]]);
+                    bw[1][c] = stB[ys * kCT + cols[c]];
+                    uw[1][c] = adj_unit_inv(stA[ys * kCT + cols[c]]);
+                }
             }
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 const int y = ys + k;
-                const bool act = y >= ylo && y < yhi;  // uniform across the warp
-                const bool act_next = k + 1 < kM && (y + 1) >= ylo && (y + 1) < yhi;
-                uint32_t(&cur)[16] = tm[k & 1];
-                uint32_t(&nxt)[16] = tm[(k + 1) & 1];
-                if (act_next) tmem_ld16_async(tbase + 16 * (k + 1), nxt);  // overlaps this cell's math
                 float(&bu)[3] = bw[k % 3];
                 float(&bm)[3] = bw[(k + 1) % 3];
                 float(&bd)[3] = bw[(k + 2) % 3];
+                float(&uu)[3] = uw[k % 3];
+                float(&um)[3] = uw[(k + 1) % 3];
+                float(&ud)[3] = uw[(k + 2) % 3];
                 {
                     const int yd = y + 1 < kRT ? y + 1 : y;
-                    bd[0] = stB[yd * kCT + xl]; bd[1] = stB[yd * kCT + x]; bd[2] = stB[yd * kCT + xr];
+                    const int cols[3] = {xl, x, xr};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        bd[c] = stB[yd * kCT + cols[c]];
+                        ud[c] = adj_unit_inv(stA[yd * kCT + cols[c]]);
+                    }
                 }
                 float(&wu)[3] = w[k % 3];        // source row y - 1 (R = k)
                 float(&wm)[3] = w[(k + 1) % 3];  // source row y
                 float(&wd)[3] = w[(k + 2) % 3];  // source row y + 1
-                if (act) {
+                const float Aown = stA[y * kCT + x];
+                const int sg = adj_sigma(Aown);
+                sgc[k >> 2] |= (uint32_t)sg << (8 * (k & 3));
+                const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
+                const bool live = sp != kSigmaZero;  // a > 0 at t + 1
+                const float Up = live ? adj_unit(sp) : 0.0f;
+                scl[k] = (sg == kSigmaZero) ? 0.0f : Up * um[1];
+                uint32_t tmv[16];
+                tmem_ld16_async(tbase + 16 * k, tmv);
+                tmem_wait_ld16(tmv);
+                if (y >= ylo && y < yhi) {  // uniform across the warp
                     float qv[8], gv[8];
 #pragma unroll
                     for (int d = 0; d < 8; ++d) {
-                        qv[d] = __uint_as_float(cur[d]);
-                        gv[d] = __uint_as_float(cur[8 + d]);
+                        qv[d] = __uint_as_float(tmv[d]);
+                        gv[d] = __uint_as_float(tmv[8 + d]);
                     }
-                    if (xin) {
+                    if (xin && live) {
                         // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
                         const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
+                        const float nu[8] = {uu[0], uu[1], uu[2], um[0], um[2], ud[0], ud[1], ud[2]};
                         float f[8];
 #pragma unroll
                         for (int d = 0; d < 8; ++d) f[d] = fmaf(-nb[d], qv[d], 1.0f);
@@ -214,22 +238,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // error (a few 1e-8) is harmless; the forward keeps the recurrence
                         const float P = 1.0f - pre[7] * f[7];
                         float av, ua;
-                        a_decode(stA[y * kCT + x], av, ua);
+                        a_decode(Aown, av, ua);
                         const float ln = la[k] + lb[k];
-                        const float lP = ln * ua;
-                        la[k] = fmaf(-ln, P, la[k]);
+                        const float tg = ln * ua;  // l_P_j in units 2^sigma'(j)
+                        la[k] = fmaf(-ln, P, la[k]) * scl[k];
 #pragma unroll
                         for (int d = 0; d < 8; ++d) {
-                            const float t = lP * (pre[d] * suf[d]);   // l_P_j x leave-one-out product
-                            gv[d] = fmaf(t, nb[d], gv[d]);
-                            const float c = t * qv[d];
+                            const float t = tg * (pre[d] * suf[d]);
+                            gv[d] = fmaf(t, nb[d] * Up, gv[d]);
+                            const float c = t * qv[d] * (Up * nu[d]);  // in units of source i
                             const int j = dir_dc(d) + 1;
                             if (dir_dr(d) < 0) wu[j] += c; else if (dir_dr(d) == 0) wm[j] += c; else wd[j] += c;
                         }
+                    } else {
+                        la[k] *= scl[k];
                     }
                     tmem_st8_nc(tbase + 16 * k + 8, gv);
+                } else {
+                    la[k] *= scl[k];
                 }
-                if (act_next) tmem_wait_ld16(nxt);
                 // row R = k (source row ys + k - 1) is complete
                 if (k == 0) {
 #pragma unroll
@@ -263,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // gather: lambda_b at the sources of this strip
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
-                float v = fmaf(pc, lb[k], own[k]);
+                float v = fmaf(pc * scl[k], lb[k], own[k]);
                 if (lane == 31 && x == 31) v += sm.er2l[ex][strip][k];
                 if (lane == 0 && x == 32) v += sm.el2r[ex][strip][k];
                 if (k == 0 && strip > 0) {
@@ -277,7 +304,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (x >= 1) v += sm.vtop[ex][strip + 1][2][x - 1];
                 }
                 lb[k] = v;
+                if (((sgc[k >> 2] >> (8 * (k & 3))) & 0xffu) == (uint32_t)kSigmaZero) {
+                    la[k] = 0.0f;  // a == 0 at t: lambda multiplies only zeros
+                    lb[k] = 0.0f;
+                }
             }
+            sgp[0] = sgc[0];
+            sgp[1] = sgc[1];
         }
         if (failed) break;
         // lambda at t0 and the tile's dL/dq for the interior
@@ -292,6 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const size_t j = (size_t)gr * pitch + gc;
                 lam_out[j] = la[k];
                 lam_out[gplane + j] = lb[k];
+                sig_out[j] = (uint8_t)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
                 // fire-and-forget reductions (no load round trip); each cell receives
                 // exactly one add per launch, so the result does not depend on timing
 #pragma unroll
@@ -328,13 +362,14 @@ int adjoint_blocked_configure() {
 }
 
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
-                            int n, const float* lam_in, float* lam_out, float* Gq, int nsm, int* err, cudaStream_t s) {
+                            int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
+                            float* Gq, int nsm, int* err, cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
     const int tiles_y = (H + kIR - 1) / kIR;
     const int ntiles = tiles_x * tiles_y;
     const int grid = ntiles < nsm ? ntiles : nsm;
     k_adjoint_blocked<<<grid, kThreads, adjoint_blocked_smem(), s>>>(*tst, *tq, H, pitch, pc, zlast, n, tiles_x,
-                                                                     ntiles, lam_in, lam_out, Gq, err);
+                                                                     ntiles, lam_in, sig_in, lam_out, sig_out, Gq, err);
 }
 
 }  // namespace pf

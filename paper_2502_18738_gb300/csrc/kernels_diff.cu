@@ -64,18 +64,22 @@ __global__ void k_ignition_map_diff(int H, int W, int pitch, const float* __rest
 //   l_n = l_a'_j + l_b'_j,  l_a_j = l_a'_j - l_n P_j,  l_P_j = l_n (1 - a_j)
 //   l_b_i = p_c l_b'_i + sum_{targets j of i} l_P_j q_dj prod_{e != d} (1 - b_e q_ej)
 //   Gq_dj += l_P_j b_{j+d} prod_{e != d} (1 - b_e q_ej)
-// The leave-one-out products come from prefix / suffix products (no division, since a
-// factor 1 - b q can be exactly 0). Each block computes the per-target contributions of
-// its tile plus a one-cell ring into shared memory, then gathers them per source cell.
+// in the scaled form of common.cuh (lambda = mu 2^sigma). The leave-one-out products
+// come from prefix / suffix products (no division, since a factor 1 - b q can be exactly
+// 0). Each block computes the per-target contributions of its tile plus a one-cell ring
+// into shared memory, then gathers them per source cell.
 constexpr int kAX = 32, kAY = 8;
 
 __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pitch, float pc,
                                                             const float* __restrict__ ab,
                                                             const float* __restrict__ q,
                                                             const float* __restrict__ lam1,
-                                                            float* __restrict__ lam0, float* __restrict__ Gq) {
-    __shared__ float sb[kAY + 4][kAX + 4];          // b, rows r0-2 .. r0+kAY+1
-    __shared__ float sc[8][kAY + 2][kAX + 2];       // contributions of targets j
+                                                            const uint8_t* __restrict__ sig1,
+                                                            float* __restrict__ lam0, uint8_t* __restrict__ sig0,
+                                                            float* __restrict__ Gq) {
+    __shared__ float sb[kAY + 4][kAX + 4];          // b at t, rows r0-2 .. r0+kAY+1
+    __shared__ float su[kAY + 4][kAX + 4];          // 2^-sigma(t) of the same cells
+    __shared__ float sc[8][kAY + 2][kAX + 2];       // contributions of targets j, in source units
     const int c0 = blockIdx.x * kAX, r0 = blockIdx.y * kAY;
     const int tid = threadIdx.y * kAX + threadIdx.x;
     const size_t plane = (size_t)H * pitch;
@@ -86,18 +90,22 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
     for (int i = tid; i < (kAY + 4) * (kAX + 4); i += kAX * kAY) {
         const int y = i / (kAX + 4), x = i % (kAX + 4);
         const int r = r0 - 2 + y, c = c0 - 2 + x;
-        sb[y][x] = (r >= 0 && r < H && c >= 0 && c < W) ? b[(size_t)r * pitch + c] : 0.0f;
+        const bool in = r >= 0 && r < H && c >= 0 && c < W;
+        sb[y][x] = in ? b[(size_t)r * pitch + c] : 0.0f;
+        su[y][x] = in ? adj_unit_inv(a[(size_t)r * pitch + c]) : 1.0f;
     }
     __syncthreads();
     for (int i = tid; i < (kAY + 2) * (kAX + 2); i += kAX * kAY) {
         const int y = i / (kAX + 2), x = i % (kAX + 2);
         const int r = r0 - 1 + y, c = c0 - 1 + x;
-        if (r < 0 || r >= H || c < 0 || c >= W) {
+        const size_t j = (size_t)r * pitch + c;
+        const int sgp = (r >= 0 && r < H && c >= 0 && c < W) ? __ldg(sig1 + j) : kSigmaZero;
+        if (sgp == kSigmaZero) {  // outside the grid, or a = 0 at t + 1 (so also at t)
 #pragma unroll
             for (int d = 0; d < 8; ++d) sc[d][y][x] = 0.0f;
             continue;
         }
-        const size_t j = (size_t)r * pitch + c;
+        const float Up = adj_unit(sgp);  // 2^sigma'(j)
         float qd[8], bi[8], f[8];
         float P = 0.0f;
 #pragma unroll
@@ -119,25 +127,57 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
         const float ln = la + lb;
         float av, ua;
         a_decode(__ldg(a + j), av, ua);
-        const float lP = ln * ua;
+        const float tg = ln * ua;  // l_P_j in units 2^sigma'(j)
         const bool interior = (y >= 1 && y <= kAY && x >= 1 && x <= kAX);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
-            const float loo = pre[d] * suf[d];
-            sc[d][y][x] = lP * qd[d] * loo;
-            if (interior) Gq[d * plane + j] += lP * bi[d] * loo;
+            const float t = tg * (pre[d] * suf[d]);
+            const float r_d = Up * su[y + 1 + dir_dr(d)][x + 1 + dir_dc(d)];  // 2^(sigma'(j) - sigma(i))
+            sc[d][y][x] = t * qd[d] * r_d;
+            if (interior) Gq[d * plane + j] = fmaf(t, bi[d] * Up, Gq[d * plane + j]);
         }
-        if (interior) lam0[j] = la - ln * P;
+        if (interior) lam0[j] = (la - ln * P) * (Up * su[y + 1][x + 1]);
     }
     __syncthreads();
     const int x = threadIdx.x, y = threadIdx.y;
     const int r = r0 + y, c = c0 + x;
     if (r >= H || c >= W) return;
     const size_t j = (size_t)r * pitch + c;
-    float acc = pc * __ldg(lb1 + j);
+    const int sgp = __ldg(sig1 + j);
+    const int sg = adj_sigma(__ldg(a + j));
+    float acc = 0.0f;
+    if (sgp != kSigmaZero) acc = pc * __ldg(lb1 + j) * (adj_unit(sgp) * su[y + 2][x + 2]);
 #pragma unroll
     for (int d = 0; d < 8; ++d) acc += sc[d][y + 1 - dir_dr(d)][x + 1 - dir_dc(d)];  // target j = i - offset
+    if (sg == kSigmaZero || sgp == kSigmaZero) {  // a == 0 at t: lambda multiplies only zeros
+        acc = 0.0f;
+        lam0[j] = 0.0f;
+    }
     lam0[plane + j] = acc;
+    sig0[j] = (uint8_t)sg;
+}
+
+__global__ void k_adjoint_init(const float* __restrict__ dLda, const float* __restrict__ dLdb,
+                               const float* __restrict__ ab, int H, int W, int pitch, float* __restrict__ lam,
+                               uint8_t* __restrict__ sig) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= H || c >= pitch) return;
+    const size_t plane = (size_t)H * pitch;
+    const size_t j = (size_t)r * pitch + c;
+    float la = 0.0f, lb = 0.0f;
+    int sg = kSigmaZero;
+    if (c < W) {
+        sg = adj_sigma(ab[j]);
+        if (sg != kSigmaZero) {
+            const float ui = adj_unit_inv_of(sg);
+            if (dLda) la = dLda[(size_t)r * W + c] * ui;
+            if (dLdb) lb = dLdb[(size_t)r * W + c] * ui;
+        }
+    }
+    lam[j] = la;
+    lam[plane + j] = lb;
+    sig[j] = (uint8_t)sg;
 }
 
 }  // namespace
@@ -155,10 +195,17 @@ void launch_ignition_map_diff(int H, int W, int pitch, const float* ab, const fl
 }
 
 void launch_adjoint_step(int H, int W, int pitch, float pc, const float* ab, const float* q, const float* lam1,
-                         float* lam0, float* Gq, cudaStream_t s) {
+                         const uint8_t* sig1, float* lam0, uint8_t* sig0, float* Gq, cudaStream_t s) {
     dim3 blk(kAX, kAY);
     dim3 grd((W + kAX - 1) / kAX, (H + kAY - 1) / kAY);
-    k_adjoint_step<<<grd, blk, 0, s>>>(H, W, pitch, pc, ab, q, lam1, lam0, Gq);
+    k_adjoint_step<<<grd, blk, 0, s>>>(H, W, pitch, pc, ab, q, lam1, sig1, lam0, sig0, Gq);
+}
+
+void launch_adjoint_init(const float* dLda, const float* dLdb, const float* ab, int H, int W, int pitch, float* lam,
+                         uint8_t* sig, cudaStream_t s) {
+    dim3 blk(64, 4);
+    dim3 grd((pitch + 63) / 64, (H + 3) / 4);
+    k_adjoint_init<<<grd, blk, 0, s>>>(dLda, dLdb, ab, H, W, pitch, lam, sig);
 }
 
 }  // namespace pf

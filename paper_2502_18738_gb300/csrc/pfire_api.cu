@@ -93,7 +93,8 @@ struct pf_ctx {
     float t_p_h = 0, t_c1 = 0, t_c2 = 0, t_a = 0, t_pc = 0, t_l = 0;
     long t_version = -1;
     // adjoint
-    float* lam[2] = {nullptr, nullptr};
+    float* lam[2] = {nullptr, nullptr};   // scaled adjoint mu (lambda = mu 2^sigma)
+    uint8_t* sig[2] = {nullptr, nullptr};  // its per-cell exponents sigma
     float* Gq = nullptr;
     double* partials = nullptr;
     double* gacc = nullptr;
@@ -863,12 +864,18 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
     const size_t sbytes = diff_state_bytes(ctx);
     int rc;
     // lazily allocated adjoint buffers
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (!ctx->lam[i]) {
             void* p;
             if ((rc = dalloc(ctx, &p, sbytes))) return rc;
             ctx->lam[i] = (float*)p;
         }
+        if (!ctx->sig[i]) {
+            void* p;
+            if ((rc = dalloc(ctx, &p, pe))) return rc;
+            ctx->sig[i] = (uint8_t*)p;
+        }
+    }
     if (!ctx->Gq) {
         void* p;
         if ((rc = dalloc(ctx, &p, 8 * pe * sizeof(float)))) return rc;
@@ -898,14 +905,12 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                              encode_f32_3d(&tseg, ctx->seg_buf, ctx->P, ctx->H, 2 * ctx->seg_cap,
                                            diff_blocked_box_cols(), diff_blocked_box_rows(), 2);
     cudaGetLastError();
-    // terminal adjoint
-    CK(cudaMemsetAsync(ctx->lam[0], 0, sbytes, ctx->st));
-    if (dL_da_T)
-        CK(cudaMemcpy2DAsync(ctx->lam[0], sizeof(float) * ctx->P, dL_da_T, sizeof(float) * ctx->W,
-                             sizeof(float) * ctx->W, ctx->H, cudaMemcpyDeviceToDevice, ctx->st));
-    if (dL_db_T)
-        CK(cudaMemcpy2DAsync(ctx->lam[0] + pe, sizeof(float) * ctx->P, dL_db_T, sizeof(float) * ctx->W,
-                             sizeof(float) * ctx->W, ctx->H, cudaMemcpyDeviceToDevice, ctx->st));
+    // terminal adjoint, in the scaled form (exponents from the state at T)
+    {
+        LaunchScope ls(ctx, K_MISC);
+        launch_adjoint_init(dL_da_T, dL_db_T, ctx->cur_ab, ctx->H, ctx->W, ctx->P, ctx->lam[0], ctx->sig[0], ctx->st);
+    }
+    if ((rc = check_launch(ctx, "adjoint init"))) return rc;
     CK(cudaMemsetAsync(ctx->gacc, 0, 4 * sizeof(double), ctx->st));
     const size_t cell_bytes = (size_t)ctx->H * ctx->W * sizeof(float);
     if (grad_pveg) CK(cudaMemsetAsync(grad_pveg, 0, cell_bytes, ctx->st));
@@ -957,7 +962,8 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                 {
                     LaunchScope ls(ctx, K_ABLK, n);
                     launch_adjoint_blocked(tmap, &ctx->tmapQ, ctx->H, ctx->P, pc, t1 - 1 - tbase, n, ctx->lam[lcur],
-                                           ctx->lam[1 - lcur], ctx->Gq, ctx->nsm, ctx->dflags, ctx->st);
+                                           ctx->sig[lcur], ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->Gq, ctx->nsm,
+                                           ctx->dflags, ctx->st);
                 }
                 if ((r = check_launch(ctx, "adjoint blocked"))) return r;
                 t1 -= n;
@@ -965,7 +971,8 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                 {
                     LaunchScope ls(ctx, K_ADJ);
                     launch_adjoint_step(ctx->H, ctx->W, ctx->P, pc, buf + (size_t)(t1 - 1 - tbase) * selems, ctx->q,
-                                        ctx->lam[lcur], ctx->lam[1 - lcur], ctx->Gq, ctx->st);
+                                        ctx->lam[lcur], ctx->sig[lcur], ctx->lam[1 - lcur], ctx->sig[1 - lcur],
+                                        ctx->Gq, ctx->st);
                 }
                 if ((r = check_launch(ctx, "adjoint step"))) return r;
                 t1 -= 1;
