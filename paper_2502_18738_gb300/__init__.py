@@ -24,7 +24,7 @@ __all__ = [
     "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward",
     "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
     "pf_set_tuning", "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error",
-    "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob",
+    "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
     "EXPORTED_SYMBOLS",
 ]
 
@@ -255,6 +255,30 @@ def pf_profile_read(h, reset=False) -> dict:
     if m < 0:
         _check(m, h)
     return {kinds[i].decode(): (int(launches[i]), int(steps[i]), float(ms[i])) for i in range(m)}
+
+
+def make_job(S_init, T, S_out=None, form=PF_DISCRETE, seed=0, run=0, fire_id=0, E=None, p_veg=None, p_den=None,
+             V_w=None, theta_w=None, p_h=0.58, c1=0.045, c2=0.131, a=0.078, p_continue=0.3, l=30.0):
+    """A PfJob over CUDA tensors (S_init uint8 [H][W]); allocates S_out if not given
+    (uint8 [H][W] discrete, FP32 [2][H][W] differentiable). Returns (job, S_out); the job
+    keeps references to every tensor it points into."""
+    H, W = S_init.shape
+    if S_out is None:
+        S_out = (torch.empty((H, W), dtype=torch.uint8, device="cuda") if form == PF_DISCRETE
+                 else torch.empty((2, H, W), dtype=torch.float32, device="cuda"))
+    n = H * W
+    j = PfJob()
+    j.H, j.W, j.T, j.form = H, W, int(T), int(form)
+    j.seed, j.run, j.fire_id = int(seed) & (2**64 - 1), int(run), int(fire_id)
+    for name, t in (("E", E), ("p_veg", p_veg), ("p_den", p_den), ("V_w", V_w), ("theta_w", theta_w)):
+        p = _ptr(t, torch.float32, n, name)
+        setattr(j, name, p.value if p is not None else None)
+    j.p_h, j.c1, j.c2, j.a, j.p_continue, j.l = p_h, c1, c2, a, p_continue, l
+    j.S_init = _ptr(S_init, torch.uint8, n, "S_init").value
+    j.S_out = _ptr(S_out, torch.uint8 if form == PF_DISCRETE else torch.float32,
+                   n * (1 if form == PF_DISCRETE else 2), "S_out").value
+    j._keep = (S_init, S_out, E, p_veg, p_den, V_w, theta_w)  # the struct holds raw pointers into these
+    return j, S_out
 
 
 def pf_batch_submit(jobs, stream=None):

@@ -86,7 +86,7 @@ __device__ __forceinline__ int adj_sigma(float A) {
 __device__ __forceinline__ float adj_unit(int sigma) { return __int_as_float((sigma + 127) << 23); }
 __device__ __forceinline__ float adj_unit_inv_of(int sigma) { return __int_as_float((127 - sigma) << 23); }
 
-// ---------------------------------------------------------------- launchers// ---------------------------------------------------------------- launchers
+// ---------------------------------------------------------------- launchers
 struct PrepArgs {
     int H, W, pitch;
     const float *E, *pveg, *pden, *V, *th;  // dense H*W, nullable
@@ -158,5 +158,33 @@ void launch_ignition_map_diff(int H, int W, int pitch, const float* ab, const fl
 // dense FP32 (a, b) [2][H][W]  <->  pitched encoded (A, b) [2][H][pitch]
 void launch_diff_pack(const float* dense, int H, int W, int pitch, float* ab, cudaStream_t s);
 void launch_diff_unpack(const float* ab, int H, int W, int pitch, float* dense, cudaStream_t s);
+
+// batched fires (kernels_batch.cu)
+struct BatchJobDev {
+    int H, W, P, T, form, nblk, tiles_x, tiles_y;
+    uint32_t key0, key1, run, fire;
+    float pc;
+    void* st[2];
+    const float* q;
+    int* gen;
+    void* out;
+};
+struct BatchPlan {
+    const BatchJobDev* jobs;
+    const long long* blk_start;
+    const long long* tile_pref;
+    const int* jobs_in_blk;
+    int max_blk;
+    long long total;
+    unsigned long long* counter;
+    int* err;
+    long long wait_limit_ns;  // bound on one wait for a neighbouring tile
+    int withhold;
+};
+int batch_tile_rows();
+int batch_tile_cols();
+int batch_steps_per_item();
+int batch_blocks_per_sm();
+void launch_batch(const BatchPlan& plan, int grid, cudaStream_t s);
 
 }  // namespace pf

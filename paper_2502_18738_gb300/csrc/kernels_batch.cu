@@ -1,0 +1,231 @@
+// Batched fires: one persistent kernel steps many independent fires of uneven size and
+// step count from a device work queue.
+//
+// A work item is (fire, tile, block b): advance one 32 x 64-cell interior tile of one fire
+// by up to kB steps (global steps b*kB ..), reading the tile plus a kB-cell halo from the
+// fire's state buffer b % 2 and writing the interior to buffer (b+1) % 2 (or, for the
+// fire's last block, to its output). Items are handed out by one atomic counter in
+// block-major order (every fire's block b before any block b+1), and an item starts
+// only once the 3 x 3 neighbouring tiles have published generation >= b, which also
+// guarantees they have finished reading the buffer it overwrites. Because an item waits
+// only on items handed out before it, the earliest unfinished item never waits, so the
+// queue always drains, whatever number of CTAs is resident. Every wait is bounded in time (globaltimer): on
+// timeout the CTA records an error and every CTA stops taking work.
+#include "common.cuh"
+
+namespace pf {
+
+// BatchJobDev / BatchPlan (common.cuh): per-fire buffers and the item decoding tables:
+// jobs sorted by block count, descending; blk_start[b] = first item of block b;
+// tile_pref[j] = tiles of jobs 0 .. j-1; jobs_in_blk[b] = jobs with more than b blocks.
+
+namespace {
+
+constexpr int kB = 4;               // steps per item (= halo)
+constexpr int kTR = 32, kTC = 64;   // interior rows / columns
+constexpr int kRR = kTR + 2 * kB;   // 40 region rows
+constexpr int kRC = kTC + 2 * kB;   // 72 region columns
+constexpr int kBThreads = 256;
+constexpr int kErrBatchTimeout = 2;  // a wait for a neighbouring tile ran out
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int upper_bound_ll(const long long* a, int n, long long v) {
+    int lo = 0, hi = n;  // first index with a[idx] > v
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] > v) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint8_t disc_update(uint8_t s, const uint8_t* nb, const BatchJobDev& J, const float* q,
+                                               size_t qplane, size_t qoff, uint32_t cell, uint32_t step) {
+    if (s == 1) {
+        float P = 0.0f;
+        bool any = false;
+#pragma unroll
+        for (int d = 0; d < 8; ++d)
+            if (nb[d] == 2) {
+                any = true;
+                const float x = __ldg(q + d * qplane + qoff);
+                P = fmaf(x, 1.0f - P, P);
+            }
+        if (!any) return 1;
+        const U4 r = philox10(cell, J.run, step, J.fire, J.key0, J.key1);
+        return u24(r.x) < P ? 2 : 1;
+    }
+    if (s == 2) {
+        const U4 r = philox10(cell, J.run, step, J.fire, J.key0, J.key1);
+        return u24(r.y) < J.pc ? 2 : 3;
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
+    __shared__ float sA[2][kRR][kRC];
+    __shared__ float sB[2][kRR][kRC];
+    __shared__ long long s_item;
+    __shared__ int s_ok;
+    uint8_t(&s8)[2][kRR][kRC * 4] = *reinterpret_cast<uint8_t(*)[2][kRR][kRC * 4]>(&sA);  // discrete reuse
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            s_item = (*(volatile int*)plan.err) ? plan.total : (long long)atomicAdd(plan.counter, 1ull);
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= plan.total) return;
+        // decode (block, job, tile)
+        const int b = upper_bound_ll(plan.blk_start, plan.max_blk + 1, item) - 1;
+        const long long r = item - plan.blk_start[b];
+        const int j = upper_bound_ll(plan.tile_pref, plan.jobs_in_blk[b] + 1, r) - 1;
+        const int tile = (int)(r - plan.tile_pref[j]);
+        const BatchJobDev& J = plan.jobs[j];
+        const int ty = tile / J.tiles_x, tx = tile % J.tiles_x;
+        const int r0 = ty * kTR - kB, c0 = tx * kTC - kB;
+        // wait until the 3 x 3 neighbourhood has completed block b - 1
+        if (tid == 0) {
+            int ok = 1;
+            for (int dy = -1; dy <= 1 && ok; ++dy)
+                for (int dx = -1; dx <= 1 && ok; ++dx) {
+                    const int yy = ty + dy, xx = tx + dx;
+                    if (yy < 0 || yy >= J.tiles_y || xx < 0 || xx >= J.tiles_x) continue;
+                    const volatile int* g = J.gen + yy * J.tiles_x + xx;
+                    if (*g >= b) continue;
+                    const unsigned long long t0 = global_ns();
+                    while (*g < b) {
+                        if (global_ns() - t0 > (unsigned long long)plan.wait_limit_ns || *(volatile int*)plan.err) {
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                }
+            __threadfence();
+            s_ok = ok;
+            if (!ok) atomicCAS(plan.err, 0, kErrBatchTimeout);
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const int steps = min(kB, J.T - b * kB);
+        const uint32_t step0 = (uint32_t)(b * kB);
+        const bool last = b == J.nblk - 1;
+        const size_t plane = (size_t)J.H * J.P;
+        if (J.form == 0) {  // discrete
+            const uint8_t* in = (const uint8_t*)J.st[b & 1];
+            for (int i = tid; i < kRR * kRC; i += kBThreads) {
+                const int y = i / kRC, x = i % kRC, gr = r0 + y, gc = c0 + x;
+                const uint8_t v = (gr >= 0 && gr < J.H && gc >= 0 && gc < J.W) ? __ldcg(in + (size_t)gr * J.P + gc) : 0;
+                s8[0][y][x] = v;
+                s8[1][y][x] = v;
+            }
+            __syncthreads();
+            int cur = 0;
+            for (int s = 0; s < steps; ++s) {
+                for (int i = tid; i < (kRR - 2) * (kRC - 2); i += kBThreads) {
+                    const int y = 1 + i / (kRC - 2), x = 1 + i % (kRC - 2), gr = r0 + y, gc = c0 + x;
+                    const uint8_t sv = s8[cur][y][x];
+                    uint8_t nv = sv;
+                    if (sv == 1 || sv == 2) {  // states 1/2 exist only inside the grid
+                        uint8_t nb[8];
+#pragma unroll
+                        for (int d = 0; d < 8; ++d) nb[d] = s8[cur][y + dir_dr(d)][x + dir_dc(d)];
+                        nv = disc_update(sv, nb, J, J.q, plane, (size_t)gr * J.P + gc, (uint32_t)gr * (uint32_t)J.W + (uint32_t)gc,
+                                         step0 + (uint32_t)s);
+                    }
+                    s8[cur ^ 1][y][x] = nv;
+                }
+                __syncthreads();
+                cur ^= 1;
+            }
+            for (int i = tid; i < kTR * kTC; i += kBThreads) {
+                const int y = kB + i / kTC, x = kB + i % kTC, gr = r0 + y, gc = c0 + x;
+                if (gr >= J.H || gc >= J.W) continue;
+                const uint8_t v = s8[cur][y][x];
+                if (last) ((uint8_t*)J.out)[(size_t)gr * J.W + gc] = v;
+                else ((uint8_t*)J.st[(b + 1) & 1])[(size_t)gr * J.P + gc] = v;
+            }
+        } else {
+            const float* in = (const float*)J.st[b & 1];
+            for (int i = tid; i < kRR * kRC; i += kBThreads) {
+                const int y = i / kRC, x = i % kRC, gr = r0 + y, gc = c0 + x;
+                const bool inside = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
+                const size_t g = (size_t)gr * J.P + gc;
+                sA[0][y][x] = inside ? __ldcg(in + g) : 0.0f;
+                const float bv = inside ? __ldcg(in + plane + g) : 0.0f;
+                sB[0][y][x] = bv;
+                sB[1][y][x] = bv;
+            }
+            __syncthreads();
+            int cur = 0;
+            for (int s = 0; s < steps; ++s) {
+                for (int i = tid; i < (kRR - 2) * (kRC - 2); i += kBThreads) {
+                    const int y = 1 + i / (kRC - 2), x = 1 + i % (kRC - 2), gr = r0 + y, gc = c0 + x;
+                    float bnew = sB[cur][y][x];
+                    if (gr >= 0 && gr < J.H && gc >= 0 && gc < J.W) {
+                        const size_t qoff = (size_t)gr * J.P + gc;
+                        float P = 0.0f, S = 1.0f;
+#pragma unroll
+                        for (int d = 0; d < 8; ++d) {
+                            const float xx = sB[cur][y + dir_dr(d)][x + dir_dc(d)] * __ldg(J.q + d * plane + qoff);
+                            P = fmaf(xx, 1.0f - P, P);
+                            S *= 1.0f - xx;
+                        }
+                        float a, ua;
+                        a_decode(sA[0][y][x], a, ua);
+                        const float n = ua * P;
+                        sA[0][y][x] = a_encode(a + n, ua * S);  // own cell only: in place
+                        bnew = fmaf(J.pc, sB[cur][y][x], n);
+                    }
+                    sB[cur ^ 1][y][x] = bnew;
+                }
+                __syncthreads();
+                cur ^= 1;
+            }
+            for (int i = tid; i < kTR * kTC; i += kBThreads) {
+                const int y = kB + i / kTC, x = kB + i % kTC, gr = r0 + y, gc = c0 + x;
+                if (gr >= J.H || gc >= J.W) continue;
+                const float Av = sA[0][y][x], bv = sB[cur][y][x];
+                if (last) {
+                    float a, ua;
+                    a_decode(Av, a, ua);
+                    float* o = (float*)J.out;
+                    o[(size_t)gr * J.W + gc] = a;
+                    o[(size_t)J.H * J.W + (size_t)gr * J.W + gc] = bv;
+                } else {
+                    float* o = (float*)J.st[(b + 1) & 1];
+                    o[(size_t)gr * J.P + gc] = Av;
+                    o[plane + (size_t)gr * J.P + gc] = bv;
+                }
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0 && !(plan.withhold && j == 0 && tile == 0 && J.nblk > 1 && b == 0)) {
+            atomicExch(J.gen + tile, b + 1);
+        }
+    }
+}
+
+}  // namespace
+
+int batch_tile_rows() { return kTR; }
+int batch_tile_cols() { return kTC; }
+int batch_steps_per_item() { return kB; }
+
+void launch_batch(const BatchPlan& plan, int grid, cudaStream_t s) {
+    k_batch<<<grid, kBThreads, 0, s>>>(plan);
+}
+
+int batch_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch, kBThreads, 0) != cudaSuccess) nb = 1;
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace pf

@@ -1084,10 +1084,198 @@ int pf_loss_bce(const float* a, const float* y, int64_t n, float* dL_da, double*
 }
 
 int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
-    (void)jobs;
-    (void)n;
-    (void)cuda_stream;
-    return fail(nullptr, PF_ESTATE, "pf_batch_submit: not built yet");
+    pf_ctx* ctx = nullptr;  // context-free: errors go to pf_last_error(NULL)
+    if (n < 0 || (n > 0 && !jobs)) return fail(nullptr, PF_EINVAL, "pf_batch_submit: bad job array");
+    if (n == 0) return PF_OK;
+    const int kB = batch_steps_per_item(), kTR = batch_tile_rows(), kTC = batch_tile_cols();
+    for (int i = 0; i < n; ++i) {
+        const pf_job& J = jobs[i];
+        if (J.H < 1 || J.W < 1 || J.H > 65536 || J.W > 65536 || (uint64_t)J.H * J.W >= (1ull << 32))
+            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: bad grid %dx%d", i, J.H, J.W);
+        if (J.T < 0 || (J.form != PF_DISCRETE && J.form != PF_DIFF) || !J.S_init || !J.S_out)
+            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: bad T, form or NULL state", i);
+        const float v[6] = {J.p_h, J.c1, J.c2, J.a, J.p_continue, J.l};
+        for (float x : v)
+            if (!std::isfinite(x)) return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: non-finite parameter", i);
+        if (J.p_h < 0 || J.p_continue < 0 || J.p_continue > 1 || !(J.l > 0))
+            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: parameter out of range", i);
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // order jobs by block count, descending (block-major item order)
+    std::vector<int> order(n);
+    std::vector<int> nblk(n);
+    for (int i = 0; i < n; ++i) {
+        order[i] = i;
+        nblk[i] = std::max(1, (jobs[i].T + kB - 1) / kB);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nblk[x] > nblk[y]; });
+    // one arena: per job two state buffers, q, a burnable mask and tile counters
+    struct Lay { size_t st, q, mask, gen, stbytes; int P, tx, ty; };
+    std::vector<Lay> lay(n);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    for (int k = 0; k < n; ++k) {
+        const pf_job& J = jobs[order[k]];
+        Lay& L = lay[k];
+        L.P = pitch_of(J.W);
+        L.tx = (J.W + kTC - 1) / kTC;
+        L.ty = (J.H + kTR - 1) / kTR;
+        const size_t plane = (size_t)J.H * L.P;
+        L.stbytes = J.form == PF_DISCRETE ? plane : 2 * plane * sizeof(float);
+        L.st = take(2 * L.stbytes);
+        L.q = take(8 * plane * sizeof(float));
+        L.mask = take((size_t)J.H * J.W);
+        L.gen = take((size_t)L.tx * L.ty * sizeof(int));
+    }
+    const int max_blk = nblk[order[0]];
+    std::vector<long long> tile_pref(n + 1, 0), blk_start(max_blk + 1, 0);
+    std::vector<int> jobs_in_blk(max_blk, 0);
+    for (int k = 0; k < n; ++k) tile_pref[k + 1] = tile_pref[k] + (long long)lay[k].tx * lay[k].ty;
+    for (int b = 0; b < max_blk; ++b) {
+        int m = 0;
+        while (m < n && nblk[order[m]] > b) ++m;
+        jobs_in_blk[b] = m;
+        blk_start[b + 1] = blk_start[b] + tile_pref[m];
+    }
+    const size_t o_jobs = take(sizeof(BatchJobDev) * n);
+    const size_t o_bs = take(sizeof(long long) * (max_blk + 1));
+    const size_t o_tp = take(sizeof(long long) * (n + 1));
+    const size_t o_jb = take(sizeof(int) * max_blk);
+    const size_t o_ctl = take(sizeof(unsigned long long) + sizeof(int) * 4);
+    const size_t o_vf = take(sizeof(int) * n);  // per-job input validation flags
+    char* arena = nullptr;
+    if (cudaMalloc((void**)&arena, off) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, PF_ENOMEM, "pf_batch_submit: %zu-byte arena allocation failed", off);
+    }
+    std::vector<BatchJobDev> hj(n);
+    for (int k = 0; k < n; ++k) {
+        const pf_job& J = jobs[order[k]];
+        const Lay& L = lay[k];
+        BatchJobDev& D = hj[k];
+        D.H = J.H; D.W = J.W; D.P = L.P; D.T = J.T; D.form = J.form; D.nblk = nblk[order[k]];
+        D.tiles_x = L.tx; D.tiles_y = L.ty;
+        D.key0 = (uint32_t)J.seed; D.key1 = (uint32_t)(J.seed >> 32); D.run = J.run; D.fire = J.fire_id;
+        D.pc = J.p_continue;
+        D.st[0] = arena + L.st;
+        D.st[1] = arena + L.st + L.stbytes;
+        D.q = (const float*)(arena + L.q);
+        D.gen = (int*)(arena + L.gen);
+        D.out = J.S_out;
+    }
+    unsigned long long* counter = (unsigned long long*)(arena + o_ctl);
+    int* derr = (int*)(arena + o_ctl + sizeof(unsigned long long));
+    int rc = PF_OK;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaSuccess;
+    const char* sl = getenv("PF_BATCH_WAIT_NS");
+    const char* wh = getenv("PF_BATCH_TEST_WITHHOLD");
+    BatchPlan plan;
+    plan.jobs = (const BatchJobDev*)(arena + o_jobs);
+    plan.blk_start = (const long long*)(arena + o_bs);
+    plan.tile_pref = (const long long*)(arena + o_tp);
+    plan.jobs_in_blk = (const int*)(arena + o_jb);
+    plan.max_blk = max_blk;
+    plan.total = blk_start[max_blk];
+    plan.counter = counter;
+    plan.err = derr;
+    plan.wait_limit_ns = sl ? std::max(1000ll, atoll(sl)) : 4000000000ll;  // 4 s
+    plan.withhold = wh ? atoi(wh) : 0;
+    int nsm = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nsm * batch_blocks_per_sm();
+    int herr = 0;
+    std::vector<int> hvf(n, 0);
+    // inputs: state codes 0..3, finite fields, p_veg / p_den >= -1 (as pf_forward / pf_set_env)
+    e = cudaMemsetAsync(arena + o_vf, 0, sizeof(int) * n, st);
+    if (e != cudaSuccess) goto cuda_fail;
+    for (int k = 0; k < n; ++k) {
+        const pf_job& J = jobs[order[k]];
+        int* fl = (int*)(arena + o_vf) + k;
+        const size_t hw = (size_t)J.H * J.W;
+        launch_validate_states(J.S_init, hw, fl, st);
+        const float* f[5] = {J.E, J.p_veg, J.p_den, J.V_w, J.theta_w};
+        const float lo[5] = {-INFINITY, -1.0f, -1.0f, -INFINITY, -INFINITY};
+        for (int i = 0; i < 5; ++i)
+            if (f[i]) launch_validate_fields(f[i], hw, lo[i], 1 + i, fl, st);
+    }
+    e = cudaMemcpyAsync(hvf.data(), arena + o_vf, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) goto cuda_fail;
+    for (int k = 0; k < n; ++k)
+        if (hvf[k]) {
+            rc = fail(nullptr, PF_EINVAL,
+                      "pf_batch_submit: job %d: state codes other than 0..3, NaN/inf fields, or p_veg/p_den < -1",
+                      order[k]);
+            goto done;
+        }
+    // tables (pageable host memory: copied before the capture, synchronously)
+    e = cudaMemcpy(arena + o_jobs, hj.data(), sizeof(BatchJobDev) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(arena + o_bs, blk_start.data(), sizeof(long long) * (max_blk + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(arena + o_tp, tile_pref.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(arena + o_jb, jobs_in_blk.data(), sizeof(int) * max_blk, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) goto cuda_fail;
+    // the whole submission (initial states, prep of every fire, the persistent kernel)
+    // is captured into one CUDA graph and launched once
+    // (captured on a private stream: the caller's may be the legacy default stream,
+    // which cannot capture; the graph is then launched on the caller's stream)
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) goto cuda_fail;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) goto cuda_fail;
+    cudaMemsetAsync(arena + o_ctl, 0, sizeof(unsigned long long) + sizeof(int) * 4, cs);
+    for (int k = 0; k < n; ++k) {
+        const pf_job& J = jobs[order[k]];
+        const Lay& L = lay[k];
+        cudaMemsetAsync(arena + L.st, 0, 2 * L.stbytes, cs);
+        cudaMemsetAsync(arena + L.gen, 0, (size_t)L.tx * L.ty * sizeof(int), cs);
+        uint8_t* mask = (uint8_t*)(arena + L.mask);
+        if (J.form == PF_DISCRETE) {
+            cudaMemcpy2DAsync(arena + L.st, L.P, J.S_init, J.W, J.W, J.H, cudaMemcpyDeviceToDevice, cs);
+        } else {
+            launch_diff_init(J.S_init, J.H, J.W, L.P, (float*)(arena + L.st), mask, cs);
+        }
+        PrepArgs g;
+        g.H = J.H; g.W = J.W; g.pitch = L.P;
+        g.E = J.E; g.pveg = J.p_veg; g.pden = J.p_den; g.V = J.V_w; g.th = J.theta_w;
+        g.burnable = J.form == PF_DIFF ? mask : nullptr;
+        g.p_h = J.p_h; g.c1 = J.c1; g.c2 = J.c2; g.a = J.a; g.l = J.l;
+        prep_derive(g);
+        launch_prep(g, (float*)(arena + L.q), cs);
+    }
+    launch_batch(plan, grid, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (e != cudaSuccess) goto cuda_fail;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) goto cuda_fail;
+    e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) goto cuda_fail;
+    e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) goto cuda_fail;
+    if (herr) rc = fail(nullptr, PF_ETIMEOUT, "pf_batch_submit: a bounded wait for a neighbouring tile ran out");
+    goto done;
+cuda_fail:
+    rc = fail(nullptr, PF_ECUDA, "pf_batch_submit: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+done:
+    if (cs) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+            cudaGraph_t g2 = nullptr;
+            if (cudaStreamEndCapture(cs, &g2) == cudaSuccess && g2) cudaGraphDestroy(g2);
+        }
+        cudaStreamDestroy(cs);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamSynchronize(st);
+    cudaFree(arena);
+    cudaGetLastError();
+    (void)ctx;
+    return rc;
 }
 
 }  // extern "C"
