@@ -177,11 +177,14 @@ int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t);
 int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t);
 
 /* Per-kernel-kind launch counts, cell-steps processed (cells x automaton steps the
- * launches advanced or reversed) and, if profiling, summed device milliseconds since the
+ * launches advanced or reversed), the part of those cell-steps the temporal-blocked
+ * kernels skipped because their tile was quiescent (forward: b = 0 in the whole tile
+ * region, so nothing changes; adjoint: a = 0 in the whole region, so lambda is 0; the
+ * results are exact either way) and, if profiling, summed device milliseconds since the
  * last reset. kinds[i] is a static name string; any output array may be NULL.
  * Synchronous. Returns the number of kinds written (<= max_kinds) or a negative pf_status. */
 int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* launches, long long* cell_steps,
-                    double* ms, int reset);
+                    long long* skipped_cell_steps, double* ms, int reset);
 
 /* ----------------------------------------------------------- batched fires */
 

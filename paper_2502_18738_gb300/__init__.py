@@ -101,7 +101,8 @@ def load():
             "pf_set_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_get_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_profile_read": ([vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
-                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double), i], i),
+                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_double), i], i),
             "pf_batch_submit": ([ctypes.POINTER(PfJob), i, vp], i),
             "pf_last_error": ([vp], ctypes.c_char_p),
             "pf_version": ([], ctypes.c_char_p),
@@ -245,16 +246,18 @@ def pf_get_tuning(h) -> dict:
 
 
 def pf_profile_read(h, reset=False) -> dict:
-    """{kernel kind: (launches, cell_steps, device ms)} since the last reset."""
+    """{kernel kind: (launches, cell_steps, device ms, skipped cell_steps)} since the last
+    reset; skipped = cell-steps of quiescent tiles the blocked kernels did not compute."""
     n = 16
     kinds = (ctypes.c_char_p * n)()
     launches = (ctypes.c_longlong * n)()
     steps = (ctypes.c_longlong * n)()
+    skipped = (ctypes.c_longlong * n)()
     ms = (ctypes.c_double * n)()
-    m = load().pf_profile_read(h, n, kinds, launches, steps, ms, int(bool(reset)))
+    m = load().pf_profile_read(h, n, kinds, launches, steps, skipped, ms, int(bool(reset)))
     if m < 0:
         _check(m, h)
-    return {kinds[i].decode(): (int(launches[i]), int(steps[i]), float(ms[i])) for i in range(m)}
+    return {kinds[i].decode(): (int(launches[i]), int(steps[i]), float(ms[i]), int(skipped[i])) for i in range(m)}
 
 
 def make_job(S_init, T, S_out=None, form=PF_DISCRETE, seed=0, run=0, fire_id=0, E=None, p_veg=None, p_den=None,

@@ -62,6 +62,15 @@ __device__ __forceinline__ void a_decode(float A, float& a, float& ua) {
 }
 __device__ __forceinline__ float a_encode(float a, float ua) { return a < 0.5f ? a : -ua; }
 
+// Eq. 9 over the factors x_d = b_i q_dj of a differentiable step: S = prod_d (1 - x_d)
+// and P = 1 - S, accumulated as P += x_d S (the term x_d prod_{e<d} (1 - x_e)). Both are
+// sums / products of non-negative terms, so P keeps its relative accuracy when it is
+// small and S when P is close to 1.
+__device__ __forceinline__ void ign_acc(float x, float& P, float& S) {
+    P = fmaf(x, S, P);
+    S = fmaf(-x, S, S);
+}
+
 // Scaled adjoint. Ahead of the fire the exact lambda grows about 4x per step backwards
 // in time while the states it multiplies shrink as fast; their products, which carry
 // the (pulled) front's sensitivity, stay O(1), but lambda itself overflows FP32 within
@@ -133,8 +142,11 @@ int diff_blocked_halo();
 int diff_blocked_box_rows();
 int diff_blocked_box_cols();
 int diff_blocked_configure();
+// skipped (nullable) accumulates the interior cell-steps of quiescent tiles (b = 0 in the
+// whole region: the steps change nothing and are not computed).
 void launch_diff_blocked(const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc, int n,
-                         float* out, float* all_out, size_t all_stride, int nsm, int* err, cudaStream_t s);
+                         float* out, float* all_out, size_t all_stride, unsigned long long* skipped, int nsm,
+                         int* err, cudaStream_t s);
 // lam: scaled adjoint (mu_a, mu_b) [2][H][pitch]; sig: its exponents uint8 [H][pitch]
 void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float* ab, const float* q,
                          const float* lam1, const uint8_t* sig1, float* lam0, uint8_t* sig0, float* Gq,
@@ -145,12 +157,20 @@ void launch_adjoint_init(const float* dLda, const float* dLdb, const float* ab, 
 // temporal-blocked adjoint with TMEM working set: n <= adjoint_blocked_max_steps() steps
 // t = t1-1 .. t1-n per launch. tst: 3-D map over a buffer of consecutive states
 // (pitch, H, 2 * nstates), box {64, 64, 2}; the state at t1-1-m is state index zlast-m.
-// tq as for launch_diff_blocked. Gq is accumulated.
+// tq as for launch_diff_blocked. Gq is accumulated. Only the tiles listed by the
+// pre-pass launch_adjoint_tiles run: from A_latest, the encoded a plane of the state at
+// t1-1, it lists the tiles with a > 0 somewhere in their region (tile_list, capacity
+// adjoint_blocked_tiles(); tile_count: one device int) and writes lambda = 0,
+// sigma = kSigmaZero for the others, whose interior cell-steps it adds to skipped.
 int adjoint_blocked_max_steps();
 int adjoint_blocked_configure();
+int adjoint_blocked_tiles(int H, int pitch);
+void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
+                          int* tile_list, int* tile_count, unsigned long long* skipped, cudaStream_t s);
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
-                            float* Gq, int nsm, int* err, cudaStream_t s);
+                            float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,
+                            cudaStream_t s);
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,
                                   cudaStream_t s);
 void launch_ignition_map_diff(int H, int W, int pitch, const float* ab, const float* q, float* P,

@@ -56,7 +56,8 @@ __device__ __forceinline__ void origin(int tile, int tiles_x, int& r0, int& c0) 
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_adjoint_blocked(const __grid_constant__ CUtensorMap tst, const __grid_constant__ CUtensorMap tq, int H,
-                      int pitch, float pc, int zlast, int n, int tiles_x, int ntiles,
+                      int pitch, float pc, int zlast, int n, int tiles_x, const int* __restrict__ tiles,
+                      const int* __restrict__ ntiles_live,
                       const float* __restrict__ lam_in, const uint8_t* __restrict__ sig_in,
                       float* __restrict__ lam_out, uint8_t* __restrict__ sig_out, float* __restrict__ Gq,
                       int* __restrict__ err) {
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const size_t gplane = (size_t)H * pitch;
+    const int ntiles = *ntiles_live;  // tiles not ahead of the fire (k_adjoint_tiles)
     const int nloc = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
     if (nloc <= 0) return;
     const int total = nloc * n;
@@ -91,14 +93,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto issue_state = [&](int i) {
         const int l = i / n, m = i % n;
         int r0, c0;
-        origin((int)blockIdx.x + l * (int)gridDim.x, tiles_x, r0, c0);
+        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x], tiles_x, r0, c0);
         const int s = i & 1;
         mbar_arrive_expect_tx(&sbar[s], (uint32_t)(2 * kPlane * sizeof(float)));
         tma_load_3d(sm.st[s], &tst, &sbar[s], c0, r0, 2 * (zlast - m));
     };
     auto issue_q = [&](int l) {
         int r0, c0;
-        origin((int)blockIdx.x + l * (int)gridDim.x, tiles_x, r0, c0);
+        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x], tiles_x, r0, c0);
         mbar_arrive_expect_tx(&qbar, (uint32_t)(8 * kPlane * sizeof(float)));
         tma_load_3d(sm.q, &tq, &qbar, c0, r0, 0);
     };
@@ -112,9 +114,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     float la[kM], lb[kM];     // scaled adjoint mu of this thread's cells (lambda = mu 2^sigma)
     uint32_t sgp[2];          // sigma at t + 1 of the 8 cells, 4 per word
     for (int l = 0; l < nloc && !failed; ++l) {
-        const int tile = (int)blockIdx.x + l * (int)gridDim.x;
         int r0, c0;
-        origin(tile, tiles_x, r0, c0);
+        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x], tiles_x, r0, c0);
         if (!__syncthreads_and(mbar_wait_bounded(&qbar, (uint32_t)(l & 1)))) {
             failed = true;
             break;
@@ -227,28 +228,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                         float f[8];
 #pragma unroll
                         for (int d = 0; d < 8; ++d) f[d] = fmaf(-nb[d], qv[d], 1.0f);
-                        float pre[8], suf[8];
-                        pre[0] = 1.0f;
-#pragma unroll
-                        for (int d = 1; d < 8; ++d) pre[d] = pre[d - 1] * f[d - 1];
-                        suf[7] = 1.0f;
-#pragma unroll
-                        for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
-                        // P enters only l_a = l_a' - l_n P here, where 1 - S's absolute
-                        // error (a few 1e-8) is harmless; the forward keeps the recurrence
-                        const float P = 1.0f - pre[7] * f[7];
                         float av, ua;
                         a_decode(Aown, av, ua);
                         const float ln = la[k] + lb[k];
                         const float tg = ln * ua;  // l_P_j in units 2^sigma'(j)
+                        // t_d = tg prod_{e != d} f_e by a product tree over pairs and
+                        // halves (no division: a factor can be exactly 0)
+                        const float p01 = f[0] * f[1], p23 = f[2] * f[3], p45 = f[4] * f[5], p67 = f[6] * f[7];
+                        const float p03 = p01 * p23, p47 = p45 * p67;
+                        // P enters only l_a = l_a' - l_n P here, where 1 - S's absolute
+                        // error (a few 1e-8) is harmless; the forward keeps the recurrence
+                        const float P = 1.0f - p03 * p47;
+                        const float g03 = tg * p47, g47 = tg * p03;
+                        const float r01 = g03 * p23, r23 = g03 * p01, r45 = g47 * p67, r67 = g47 * p45;
+                        const float t[8] = {f[1] * r01, f[0] * r01, f[3] * r23, f[2] * r23,
+                                            f[5] * r45, f[4] * r45, f[7] * r67, f[6] * r67};
                         la[k] = fmaf(-ln, P, la[k]) * scl[k];
 #pragma unroll
                         for (int d = 0; d < 8; ++d) {
-                            const float t = tg * (pre[d] * suf[d]);
-                            gv[d] = fmaf(t, nb[d] * Up, gv[d]);
-                            const float c = t * qv[d] * (Up * nu[d]);  // in units of source i
+                            gv[d] = fmaf(t[d], nb[d] * Up, gv[d]);
+                            const float tq = t[d] * qv[d];
+                            const float r = Up * nu[d];  // 2^(sigma'(j) - sigma(i)): to the units of source i
                             const int j = dir_dc(d) + 1;
-                            if (dir_dr(d) < 0) wu[j] += c; else if (dir_dr(d) == 0) wm[j] += c; else wd[j] += c;
+                            if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
+                            else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
+                            else wd[j] = fmaf(tq, r, wd[j]);
                         }
                     } else {
                         la[k] *= scl[k];
@@ -344,6 +348,49 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) tmem_dealloc(tslot, kTmemCols);
 }
 
+// Pre-pass of one adjoint launch: for each tile, whether any cell of its 64 x 64 region
+// has a > 0 in the latest state of the launch's steps (A at t1 - 1, the encoded a plane).
+// a never decreases in time, so a tile with a = 0 in its whole region has a = b = 0 there
+// at every step of the launch: all its lambdas end masked to 0 and every dL/dq term
+// carries a factor b_i = 0. Such a tile's interior gets lambda = 0, sigma = kSigmaZero
+// here; the others are listed (in any order: each tile writes only its own interior and
+// adds to its own cells' dL/dq once) for k_adjoint_blocked.
+__global__ void __launch_bounds__(256) k_adjoint_tiles(const float* __restrict__ A, int H, int W, int pitch,
+                                                       int tiles_x, int n, int* __restrict__ list,
+                                                       int* __restrict__ count, float* __restrict__ lam_out,
+                                                       uint8_t* __restrict__ sig_out,
+                                                       unsigned long long* __restrict__ skipped) {
+    const int tile = blockIdx.x;
+    int r0, c0;
+    origin(tile, tiles_x, r0, c0);
+    const int tid = threadIdx.x;
+    bool any = false;
+    // 64 rows x 16 float4 (c0 and pitch are multiples of 4 floats: a float4 is wholly
+    // inside or wholly outside [0, pitch))
+    for (int i = tid; i < kRT * (kCT / 4); i += 256) {
+        const int gr = r0 + i / (kCT / 4), gc = c0 + 4 * (i % (kCT / 4));
+        if (gr < 0 || gr >= H || gc < 0 || gc >= pitch) continue;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(A + (size_t)gr * pitch + gc));
+        any |= (v.x | v.y | v.z | v.w) != 0u;
+    }
+    if (__syncthreads_or(any)) {
+        if (tid == 0) list[atomicAdd(count, 1)] = tile;
+        return;
+    }
+    const size_t gplane = (size_t)H * pitch;
+    const int ir0 = r0 + kHalo, ic0 = c0 + kHalo;
+    for (int i = tid; i < kIR * kIC; i += 256) {
+        const int gr = ir0 + i / kIC, gc = ic0 + i % kIC;
+        if (gr >= H || gc >= pitch) continue;
+        const size_t j = (size_t)gr * pitch + gc;
+        lam_out[j] = 0.0f;
+        lam_out[gplane + j] = 0.0f;
+        sig_out[j] = (uint8_t)kSigmaZero;
+    }
+    if (tid == 0 && skipped)
+        atomicAdd(skipped, (unsigned long long)(min(kIR, H - ir0) * min(kIC, W - ic0)) * (unsigned long long)n);
+}
+
 }  // namespace
 
 int adjoint_blocked_max_steps() { return kMaxSteps; }
@@ -361,15 +408,26 @@ int adjoint_blocked_configure() {
     return 0;
 }
 
+int adjoint_blocked_tiles(int H, int pitch) { return ((pitch + kIC - 1) / kIC) * ((H + kIR - 1) / kIR); }
+
+void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
+                          int* tile_list, int* tile_count, unsigned long long* skipped, cudaStream_t s) {
+    const int tiles_x = (pitch + kIC - 1) / kIC;
+    cudaMemsetAsync(tile_count, 0, sizeof(int), s);
+    k_adjoint_tiles<<<adjoint_blocked_tiles(H, pitch), 256, 0, s>>>(A_latest, H, W, pitch, tiles_x, n, tile_list,
+                                                                    tile_count, lam_out, sig_out, skipped);
+}
+
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
-                            float* Gq, int nsm, int* err, cudaStream_t s) {
+                            float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,
+                            cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
-    const int tiles_y = (H + kIR - 1) / kIR;
-    const int ntiles = tiles_x * tiles_y;
+    const int ntiles = adjoint_blocked_tiles(H, pitch);
     const int grid = ntiles < nsm ? ntiles : nsm;
     k_adjoint_blocked<<<grid, kThreads, adjoint_blocked_smem(), s>>>(*tst, *tq, H, pitch, pc, zlast, n, tiles_x,
-                                                                     ntiles, lam_in, sig_in, lam_out, sig_out, Gq, err);
+                                                                     tile_list, tile_count, lam_in, sig_in, lam_out,
+                                                                     sig_out, Gq, err);
 }
 
 }  // namespace pf

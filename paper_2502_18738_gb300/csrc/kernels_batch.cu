@@ -173,8 +173,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
 #pragma unroll
                         for (int d = 0; d < 8; ++d) {
                             const float xx = sB[cur][y + dir_dr(d)][x + dir_dc(d)] * __ldg(J.q + d * plane + qoff);
-                            P = fmaf(xx, 1.0f - P, P);
-                            S *= 1.0f - xx;
+                            ign_acc(xx, P, S);
                         }
                         float a, ua;
                         a_decode(sA[0][y][x], a, ua);

@@ -31,8 +31,7 @@ __global__ void __launch_bounds__(256) k_diff_step(int H, int W, int pitch, floa
         const int ri = r + dir_dr(d), ci = c + dir_dc(d);
         if (ri < 0 || ri >= H || ci < 0 || ci >= W) continue;
         const float x = __ldg(b + (size_t)ri * pitch + ci) * __ldg(q + d * plane + j);
-        P = fmaf(x, 1.0f - P, P);
-        S *= 1.0f - x;
+        ign_acc(x, P, S);
     }
     float a, ua;
     a_decode(ab[j], a, ua);
@@ -49,12 +48,12 @@ __global__ void k_ignition_map_diff(int H, int W, int pitch, const float* __rest
     const size_t plane = (size_t)H * pitch;
     const size_t j = (size_t)r * pitch + c;
     const float* b = ab + plane;
-    float P = 0.0f;
+    float P = 0.0f, S = 1.0f;
     for (int d = 0; d < 8; ++d) {
         const int ri = r + dir_dr(d), ci = c + dir_dc(d);
         if (ri < 0 || ri >= H || ci < 0 || ci >= W) continue;
         const float x = b[(size_t)ri * pitch + ci] * q[d * plane + j];
-        P = fmaf(x, 1.0f - P, P);
+        ign_acc(x, P, S);
     }
     Pout[idx] = P;
 }
@@ -107,14 +106,14 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
         }
         const float Up = adj_unit(sgp);  // 2^sigma'(j)
         float qd[8], bi[8], f[8];
-        float P = 0.0f;
+        float P = 0.0f, S = 1.0f;
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             qd[d] = __ldg(q + d * plane + j);
             bi[d] = sb[y + 1 + dir_dr(d)][x + 1 + dir_dc(d)];
             const float xx = bi[d] * qd[d];
             f[d] = 1.0f - xx;
-            P = fmaf(xx, 1.0f - P, P);
+            ign_acc(xx, P, S);
         }
         float pre[8], suf[8];
         pre[0] = 1.0f;

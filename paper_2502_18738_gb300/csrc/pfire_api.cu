@@ -29,11 +29,11 @@ namespace {
 
 thread_local std::string g_last_error = "no error";
 
-enum Kind { K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_NKINDS };
+enum Kind { K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_ATILES, K_NKINDS };
 const char* kKindNames[K_NKINDS] = {"prep",         "discrete_step",    "discrete_blocked",
                                     "diff_step",    "diff_blocked",     "adjoint_step",
                                     "adjoint_blocked", "prep_adjoint",  "reduce_fp64",
-                                    "misc"};
+                                    "misc",         "adjoint_tiles"};
 
 struct Epoch {
     int from;
@@ -101,6 +101,8 @@ struct pf_ctx {
     // misc
     int* dflags = nullptr;  // [0] device error word, [1..] validation flags
     int* hflags = nullptr;  // pinned mirror
+    unsigned long long* dskip = nullptr;  // per kernel kind: cell-steps of skipped quiescent tiles
+    int* tile_list = nullptr;             // live tiles of one blocked-adjoint launch (count: dflags[8])
     CUtensorMap tmapS[2];
     bool tmap_ok = false;
     CUtensorMap tmapQ;       // q planes (pitch, H, 8), box of the blocked diff kernel
@@ -173,7 +175,7 @@ struct LaunchScope {
     // steps: automaton steps the launch advances (or reverses) every cell by
     LaunchScope(pf_ctx* c_, int k, int steps = 1) : c(c_), kind(k) {
         c->launches[k] += 1;
-        if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED)
+        if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED && k != K_ATILES)
             c->cell_steps[k] += (long long)steps * c->H * c->W * (k == K_DSTEP || k == K_DBLK ? c->R : 1);
         if (!c->tun.profile) return;
         cudaEvent_t e0 = take();
@@ -336,7 +338,7 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
     {
         LaunchScope ls(ctx, K_FBLK, n);
         launch_diff_blocked(&tab, &ctx->tmapQ, ctx->H, ctx->W, ctx->P, pc, n, out, all_out, 2 * plane_elems(ctx),
-                            ctx->nsm, ctx->dflags, ctx->st);
+                            ctx->dskip + K_FBLK, ctx->nsm, ctx->dflags, ctx->st);
     }
     return check_launch(ctx, "diff blocked");
 }
@@ -598,12 +600,15 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
     } while (0)
     ALLOC(ctx->q, 8 * pe * sizeof(float));
     ALLOC(ctx->dflags, 16 * sizeof(int));
+    ALLOC(ctx->dskip, K_NKINDS * sizeof(unsigned long long));
     if (cudaMallocHost((void**)&ctx->hflags, 16 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         rc = fail(ctx, PF_ENOMEM, "pinned flag allocation failed");
         goto failed;
     }
     if (cudaMemsetAsync(ctx->dflags, 0, 16 * sizeof(int), ctx->st) != cudaSuccess) goto cuda_failed;
+    if (cudaMemsetAsync(ctx->dskip, 0, K_NKINDS * sizeof(unsigned long long), ctx->st) != cudaSuccess)
+        goto cuda_failed;
     if (form == PF_DISCRETE) {
         const size_t sb = (size_t)realisations * pe;
         ALLOC(ctx->S[0], sb);
@@ -620,6 +625,7 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
         ALLOC(ctx->work[0], diff_state_bytes(ctx));
         ALLOC(ctx->work[1], diff_state_bytes(ctx));
         ALLOC(ctx->burn, (size_t)H * W);
+        ALLOC(ctx->tile_list, (size_t)adjoint_blocked_tiles(H, ctx->P) * sizeof(int));
         if (cudaMemsetAsync(ctx->work[0], 0, diff_state_bytes(ctx), ctx->st) != cudaSuccess) goto cuda_failed;
         if (cudaMemsetAsync(ctx->work[1], 0, diff_state_bytes(ctx), ctx->st) != cudaSuccess) goto cuda_failed;
         if (cudaMemsetAsync(ctx->burn, 1, (size_t)H * W, ctx->st) != cudaSuccess) goto cuda_failed;
@@ -960,10 +966,16 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             if (tmap) {
                 const int n = std::min(adjoint_blocked_max_steps(), t1 - t0);
                 {
+                    LaunchScope ls(ctx, K_ATILES);
+                    launch_adjoint_tiles(buf + (size_t)(t1 - 1 - tbase) * selems, ctx->H, ctx->W, ctx->P, n,
+                                         ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->tile_list, ctx->dflags + 8,
+                                         ctx->dskip + K_ABLK, ctx->st);
+                }
+                {
                     LaunchScope ls(ctx, K_ABLK, n);
                     launch_adjoint_blocked(tmap, &ctx->tmapQ, ctx->H, ctx->P, pc, t1 - 1 - tbase, n, ctx->lam[lcur],
-                                           ctx->sig[lcur], ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->Gq, ctx->nsm,
-                                           ctx->dflags, ctx->st);
+                                           ctx->sig[lcur], ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->Gq,
+                                           ctx->tile_list, ctx->dflags + 8, ctx->nsm, ctx->dflags, ctx->st);
                 }
                 if ((r = check_launch(ctx, "adjoint blocked"))) return r;
                 t1 -= n;
@@ -1032,8 +1044,10 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
 }
 
 int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* launches, long long* cell_steps,
-                    double* ms, int reset) {
+                    long long* skipped_cell_steps, double* ms, int reset) {
     if (!ctx) return fail(nullptr, PF_EINVAL, "pf_profile_read: ctx is NULL");
+    unsigned long long skip[K_NKINDS];
+    CK(cudaMemcpyAsync(skip, ctx->dskip, sizeof(skip), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     prof_collect(ctx);
     int n = std::min(max_kinds, (int)K_NKINDS);
@@ -1041,14 +1055,17 @@ int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* l
         if (kinds) kinds[i] = kKindNames[i];
         if (launches) launches[i] = ctx->launches[i];
         if (cell_steps) cell_steps[i] = ctx->cell_steps[i];
+        if (skipped_cell_steps) skipped_cell_steps[i] = (long long)skip[i];
         if (ms) ms[i] = ctx->prof_ms[i];
     }
-    if (reset)
+    if (reset) {
         for (int i = 0; i < K_NKINDS; ++i) {
             ctx->launches[i] = 0;
             ctx->cell_steps[i] = 0;
             ctx->prof_ms[i] = 0.0;
         }
+        CK(cudaMemsetAsync(ctx->dskip, 0, sizeof(skip), ctx->st));
+    }
     return n;
 }
 

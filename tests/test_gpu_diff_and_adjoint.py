@@ -74,7 +74,7 @@ def _set_winds(m, winds, starts):
 
 
 @pytest.mark.parametrize("H,W,T,kernel,k", [(96, 80, 60, 1, 0), (200, 170, 120, 1, 0), (96, 80, 60, 2, 3),
-                                           (200, 170, 120, 2, 8), (130, 300, 77, 2, 5)])
+                                           (200, 170, 120, 2, 8), (130, 300, 77, 2, 5), (130, 300, 77, 2, 4)])
 def test_trajectory(pf, orc, H, W, T, kernel, k):
     land, winds, starts, S0 = _problem(H, W, T, 6)
     m, prm = _model(pf, orc, land, *winds[0], H, W)
@@ -160,3 +160,35 @@ def test_autograd_function(pf, orc):
     g4, gpv, gpd = orc.diff_backward(land, winds, starts, prm, S0, tape, np.ones((H, W)), 0.5 * np.ones((H, W)))
     assert np.allclose(params.grad.numpy(), g4, rtol=GRAD_RTOL)
     assert np.allclose(pv.grad.cpu().numpy(), gpv, rtol=GRAD_RTOL, atol=1e-5 * np.abs(gpv).max())
+
+
+@pytest.mark.parametrize("k", [4, 8])
+def test_quiescent_tiles_are_skipped_exactly(pf, orc, k):
+    """A fire in one corner of a 600 x 500 grid: most blocked-kernel tiles are quiescent
+    (forward: b = 0 in the whole region; adjoint: a = 0 in the whole region) for most
+    steps and are skipped. The forward must equal the plain kernel's bit for bit, the
+    gradients must equal the plain adjoint's within rounding, and the skipped counts
+    must be positive and below the totals."""
+    import torch
+    H, W, T = 600, 500, 40
+    land = syn.make_landscape(H, W, 21)
+    V, th = syn.smooth_wind(H, W, 21, 0, sigma=8.0)
+    S0 = syn.initial_state(land, [(20, 30), (35, 12)])
+    runs = {}
+    for kernel in (1, 2):
+        m, prm = _model(pf, orc, land, V, th, H, W)
+        m.set_tuning(kernel=kernel, k=k, K=9, profile=1)
+        pf.pf_profile_read(m.h, reset=True)
+        out = m.forward(cuda(S0), T)
+        g_a = cuda(np.random.default_rng(1).standard_normal((H, W)).astype(np.float32) * 1e-3)
+        g4, gpv, gpd = m.backward(g_a, None)
+        runs[kernel] = (out.cpu().numpy(), g4, gpv.cpu().numpy(), pf.pf_profile_read(m.h))
+        m.close()
+    (o1, g1, pv1, _), (o2, g2, pv2, prof) = runs[1], runs[2]
+    assert np.array_equal(o1, o2)
+    for a, b in zip(g1, g2):
+        assert a == pytest.approx(b, rel=1e-5)
+    _close(pv2, pv1, 1e-4, 1e-6 * np.abs(pv1).max())
+    for kind in ("diff_blocked", "adjoint_blocked"):
+        launches, cell_steps, _, skipped = prof[kind]
+        assert launches > 0 and 0 < skipped < cell_steps, (kind, prof[kind])
