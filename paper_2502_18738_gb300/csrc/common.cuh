@@ -142,11 +142,23 @@ int diff_blocked_halo();
 int diff_blocked_box_rows();
 int diff_blocked_box_cols();
 int diff_blocked_configure();
-// skipped (nullable) accumulates the interior cell-steps of quiescent tiles (b = 0 in the
-// whole region: the steps change nothing and are not computed).
-void launch_diff_blocked(const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc, int n,
-                         float* out, float* all_out, size_t all_stride, unsigned long long* skipped, int nsm,
-                         int* err, cudaStream_t s);
+// halo: 8, or 4 when every launch of the chain has n <= 4 (fixes the tile geometry).
+// Only the tiles listed by the pre-pass launch_fwd_tiles run; it decides from the tile
+// activity act_in (b > 0 in a tile's interior, from the previous launch's act_out or from
+// launch_fwd_act_init at the start of a chain) and handles the quiescent tiles itself.
+// k_diff_blocked writes act_out for the tiles it runs. skipped (nullable) accumulates the
+// interior cell-steps of quiescent tiles.
+int diff_blocked_tiles(int halo, int H, int pitch);
+void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* act, uint8_t* wasdead,
+                         cudaStream_t s);
+void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
+                      uint8_t* act_out, uint8_t* wasdead, int* tile_list, int* tile_count, float* out,
+                      bool out_is_prev_in, float* all_out, size_t all_stride, unsigned long long* skipped,
+                      cudaStream_t s);
+void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
+                         int n, const int* tile_list, const int* tile_count, float* out, float* all_out,
+                         size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
+                         cudaStream_t s);
 // lam: scaled adjoint (mu_a, mu_b) [2][H][pitch]; sig: its exponents uint8 [H][pitch]
 void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float* ab, const float* q,
                          const float* lam1, const uint8_t* sig1, float* lam0, uint8_t* sig0, float* Gq,

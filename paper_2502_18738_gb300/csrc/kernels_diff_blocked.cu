@@ -45,8 +45,9 @@ __device__ __forceinline__ void tile_origin(int tile, int tiles_x, int& r0, int&
 template <int kHalo>
 __global__ void __launch_bounds__(kThreads, 1)
     k_diff_blocked(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap tq, int H, int pitch,
-                   int W, float pc, int n, int tiles_x, int ntiles, float* __restrict__ out,
-                   float* __restrict__ all_out, size_t all_stride, unsigned long long* __restrict__ skipped,
+                   int W, float pc, int n, int tiles_x, const int* __restrict__ tiles,
+                   const int* __restrict__ ntiles_live, float* __restrict__ out, float* __restrict__ all_out,
+                   size_t all_stride, uint8_t* __restrict__ act_out, unsigned long long* __restrict__ skipped,
                    int* __restrict__ err) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
@@ -57,8 +58,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t bytes = (uint32_t)((8 + 2) * kPlane * sizeof(float));
     const size_t gplane = (size_t)H * pitch;
 
-    int tile = blockIdx.x;
-    if (tile >= ntiles) return;
+    const int ntiles = *ntiles_live;  // tiles listed by k_fwd_tiles
+    int li = blockIdx.x;
+    if (li >= ntiles) return;
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (tid == 0) {
         int r0, c0;
-        tile_origin<kHalo>(tile, tiles_x, r0, c0);
+        tile_origin<kHalo>(tiles[li], tiles_x, r0, c0);
         mbar_arrive_expect_tx(&bar, bytes);
         tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
         tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
@@ -74,7 +76,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t parity = 0;
     float q[kM][8];
     float A[kM];
-    for (; tile < ntiles; tile += gridDim.x) {
+    for (; li < ntiles; li += gridDim.x) {
+        const int tile = tiles[li];
         const bool ok = mbar_wait_bounded(&bar, parity);
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
@@ -100,10 +103,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // b = 0 in the whole region: every P is 0 at every step of the launch, so the
         // region's state does not change and the steps are skipped (the stores remain)
         const bool live = __syncthreads_or(burning);  // also: stage fully consumed
-        const int next = tile + gridDim.x;
+        const int next = li + gridDim.x;
         if (tid == 0 && next < ntiles) {
             int r0, c0;
-            tile_origin<kHalo>(next, tiles_x, r0, c0);
+            tile_origin<kHalo>(tiles[next], tiles_x, r0, c0);
             mbar_arrive_expect_tx(&bar, bytes);
             tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
             tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
@@ -185,7 +188,104 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-        __syncthreads();  // the ping-pong buffers are reused by the next tile
+        // whether b > 0 anywhere in the interior after the launch (for the next launch's
+        // tile list); the barrier also protects the ping-pong buffers reused by the next tile
+        bool act = false;
+        if (x >= kHalo && x < kCT - kHalo) {
+#pragma unroll
+            for (int m = 0; m < kM; ++m) {
+                const int y = ys + m;
+                if (y >= kHalo && y < kRT - kHalo) act |= sm.b[cur][y * kCT + x] != 0.0f;
+            }
+        }
+        act = __syncthreads_or(act);
+        if (tid == 0) act_out[tile] = act ? 1 : 0;
+    }
+}
+
+// Tile activity of a state (start of a chain of launches): act[tile] = b > 0 somewhere in
+// the tile's interior; wasdead[tile] = 0 (nothing is known about the other buffers).
+template <int kHalo>
+__global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ ab, int H, int pitch, int tiles_x,
+                                                      uint8_t* __restrict__ act, uint8_t* __restrict__ wasdead) {
+    constexpr int kI = kRT - 2 * kHalo;
+    const int tile = blockIdx.x;
+    int r0, c0;
+    tile_origin<kHalo>(tile, tiles_x, r0, c0);
+    r0 += kHalo;
+    c0 += kHalo;
+    const float* b = ab + (size_t)H * pitch;
+    bool any = false;
+    for (int i = threadIdx.x; i < kI * kI; i += 256) {
+        const int gr = r0 + i / kI, gc = c0 + i % kI;
+        if (gr < H && gc < pitch) any |= __ldg(b + (size_t)gr * pitch + gc) != 0.0f;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        act[tile] = any ? 1 : 0;
+        wasdead[tile] = 0;
+    }
+}
+
+// Pre-pass of one forward launch. A tile is live if b > 0 anywhere in the interiors of
+// the 3 x 3 tiles around it (act_in, from the previous launch or k_fwd_act_init): its
+// region (interior + halo <= one interior) lies inside them, so a tile that is not live
+// has b = 0 in its whole region and its state does not change during the launch. Live
+// tiles are listed for k_diff_blocked. A quiescent tile's interior is copied to the
+// outputs, except into `out` when out holds the previous launch's input and the tile was
+// quiescent then too (out already holds this state). act_out = 0 for quiescent tiles.
+template <int kHalo>
+__global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in, int H, int W, int pitch,
+                                                   int tiles_x, int tiles_y, int n, const uint8_t* __restrict__ act_in,
+                                                   uint8_t* __restrict__ act_out, uint8_t* __restrict__ wasdead,
+                                                   int* __restrict__ list, int* __restrict__ count,
+                                                   float* __restrict__ out, int out_is_prev_in,
+                                                   float* __restrict__ all_out, size_t all_stride,
+                                                   unsigned long long* __restrict__ skipped) {
+    constexpr int kI = kRT - 2 * kHalo;
+    const int tile = blockIdx.x;
+    const int ty = tile / tiles_x, tx = tile % tiles_x;
+    bool live = false;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int yy = ty + dy, xx = tx + dx;
+            if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) live |= act_in[yy * tiles_x + xx] != 0;
+        }
+    if (live) {
+        if (threadIdx.x == 0) {
+            list[atomicAdd(count, 1)] = tile;
+            wasdead[tile] = 0;
+        }
+        return;
+    }
+    const int r0 = ty * kI, c0 = tx * kI;
+    const size_t gplane = (size_t)H * pitch;
+    const bool copy_out = out && !(out_is_prev_in && wasdead[tile]);
+    if (copy_out || all_out) {
+        // float4 columns: c0 and pitch are multiples of 4
+        for (int i = threadIdx.x; i < kI * (kI / 4); i += 256) {
+            const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
+            if (gr >= H || gc >= pitch) continue;
+            const size_t j = (size_t)gr * pitch + gc;
+            const float4 a = __ldg(reinterpret_cast<const float4*>(in + j));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(in + gplane + j));
+            if (copy_out) {
+                *reinterpret_cast<float4*>(out + j) = a;
+                *reinterpret_cast<float4*>(out + gplane + j) = b;
+            }
+            if (all_out)
+                for (int s = 0; s < n; ++s) {
+                    float* o = all_out + (size_t)s * all_stride;
+                    *reinterpret_cast<float4*>(o + j) = a;
+                    *reinterpret_cast<float4*>(o + gplane + j) = b;
+                }
+        }
+    }
+    if (threadIdx.x == 0) {
+        act_out[tile] = 0;
+        wasdead[tile] = 1;
+        if (skipped)
+            atomicAdd(skipped, (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)n);
     }
 }
 
@@ -210,21 +310,56 @@ int diff_blocked_configure() {
     return 0;
 }
 
-void launch_diff_blocked(const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc, int n,
-                         float* out, float* all_out, size_t all_stride, unsigned long long* skipped, int nsm, int* err,
+int diff_blocked_tiles(int halo, int H, int pitch) {
+    const int inner = kRT - 2 * halo;
+    return ((pitch + inner - 1) / inner) * ((H + inner - 1) / inner);
+}
+
+void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* act, uint8_t* wasdead,
                          cudaStream_t s) {
-    const int halo = n <= 4 ? 4 : 8;
+    const int inner = kRT - 2 * halo;
+    const int tiles_x = (pitch + inner - 1) / inner;
+    const int ntiles = diff_blocked_tiles(halo, H, pitch);
+    if (halo == 4)
+        k_fwd_act_init<4><<<ntiles, 256, 0, s>>>(ab, H, pitch, tiles_x, act, wasdead);
+    else
+        k_fwd_act_init<8><<<ntiles, 256, 0, s>>>(ab, H, pitch, tiles_x, act, wasdead);
+}
+
+void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
+                      uint8_t* act_out, uint8_t* wasdead, int* tile_list, int* tile_count, float* out,
+                      bool out_is_prev_in, float* all_out, size_t all_stride, unsigned long long* skipped,
+                      cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int tiles_y = (H + inner - 1) / inner;
-    const int ntiles = tiles_x * tiles_y;
+    cudaMemsetAsync(tile_count, 0, sizeof(int), s);
+    if (halo == 4)
+        k_fwd_tiles<4><<<tiles_x * tiles_y, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
+                                                         wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
+                                                         all_out, all_stride, skipped);
+    else
+        k_fwd_tiles<8><<<tiles_x * tiles_y, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
+                                                         wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
+                                                         all_out, all_stride, skipped);
+}
+
+void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
+                         int n, const int* tile_list, const int* tile_count, float* out, float* all_out,
+                         size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
+                         cudaStream_t s) {
+    const int inner = kRT - 2 * halo;
+    const int tiles_x = (pitch + inner - 1) / inner;
+    const int ntiles = diff_blocked_tiles(halo, H, pitch);
     const int grid = ntiles < nsm ? ntiles : nsm;
     if (halo == 4)
-        k_diff_blocked<4><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, ntiles,
-                                                                      out, all_out, all_stride, skipped, err);
+        k_diff_blocked<4><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, tile_list,
+                                                                      tile_count, out, all_out, all_stride, act_out,
+                                                                      skipped, err);
     else
-        k_diff_blocked<8><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, ntiles,
-                                                                      out, all_out, all_stride, skipped, err);
+        k_diff_blocked<8><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, tile_list,
+                                                                      tile_count, out, all_out, all_stride, act_out,
+                                                                      skipped, err);
 }
 
 }  // namespace pf

@@ -29,11 +29,13 @@ namespace {
 
 thread_local std::string g_last_error = "no error";
 
-enum Kind { K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_ATILES, K_NKINDS };
+enum Kind {
+    K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_ATILES, K_FTILES, K_NKINDS
+};
 const char* kKindNames[K_NKINDS] = {"prep",         "discrete_step",    "discrete_blocked",
                                     "diff_step",    "diff_blocked",     "adjoint_step",
                                     "adjoint_blocked", "prep_adjoint",  "reduce_fp64",
-                                    "misc",         "adjoint_tiles"};
+                                    "misc",         "adjoint_tiles",    "diff_tiles"};
 
 struct Epoch {
     int from;
@@ -103,6 +105,15 @@ struct pf_ctx {
     int* hflags = nullptr;  // pinned mirror
     unsigned long long* dskip = nullptr;  // per kernel kind: cell-steps of skipped quiescent tiles
     int* tile_list = nullptr;             // live tiles of one blocked-adjoint launch (count: dflags[8])
+    // tile activity of the blocked forward (b > 0 in a tile's interior), carried along a
+    // chain of launches: act ping-pong, quiescent-last-launch flags, live list (count: dflags[9])
+    uint8_t* fact[2] = {nullptr, nullptr};
+    uint8_t* fwasdead = nullptr;
+    int* flist = nullptr;
+    const float* fl_state = nullptr;    // the state fact[fl_par] describes (nullptr: none)
+    const float* fl_prev_in = nullptr;  // input of the chain's previous launch
+    int fl_par = 0;
+    int fl_halo = 0;
     CUtensorMap tmapS[2];
     bool tmap_ok = false;
     CUtensorMap tmapQ;       // q planes (pitch, H, 8), box of the blocked diff kernel
@@ -175,7 +186,7 @@ struct LaunchScope {
     // steps: automaton steps the launch advances (or reverses) every cell by
     LaunchScope(pf_ctx* c_, int k, int steps = 1) : c(c_), kind(k) {
         c->launches[k] += 1;
-        if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED && k != K_ATILES)
+        if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED && k != K_ATILES && k != K_FTILES)
             c->cell_steps[k] += (long long)steps * c->H * c->W * (k == K_DSTEP || k == K_DBLK ? c->R : 1);
         if (!c->tun.profile) return;
         cudaEvent_t e0 = take();
@@ -330,16 +341,39 @@ int blocked_k(const pf_ctx* c) {
     return std::min(k, c->form == PF_DISCRETE ? c->KH : diff_blocked_halo());
 }
 
-// one launch of the blocked diff kernel from `in`; out / all_out as in launch_diff_blocked
+// One launch of the blocked diff kernel from `in`; out / all_out as in launch_diff_blocked.
+// Launches form chains (the output of one is the input of the next) along which the
+// tile activity is carried; a chain starts wherever `in` is not the state the activity
+// describes (ctx->fl_state, reset by every caller that starts a new sequence).
 int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* out, float* all_out) {
     CUtensorMap tab;
     if (!encode_f32_3d(&tab, in, ctx->P, ctx->H, 2, diff_blocked_box_cols(), diff_blocked_box_rows(), 2))
         return fail(ctx, PF_ECUDA, "tensor map encoding of the state buffer failed");
+    const int halo = blocked_k(ctx) <= 4 ? 4 : 8;
+    if (ctx->fl_state != in || ctx->fl_halo != halo) {
+        {
+            LaunchScope ls(ctx, K_FTILES);
+            launch_fwd_act_init(halo, in, ctx->H, ctx->P, ctx->fact[ctx->fl_par], ctx->fwasdead, ctx->st);
+        }
+        ctx->fl_halo = halo;
+        ctx->fl_prev_in = nullptr;
+    }
+    const size_t stride = 2 * plane_elems(ctx);
+    {
+        LaunchScope ls(ctx, K_FTILES);
+        launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
+                         ctx->fwasdead, ctx->flist, ctx->dflags + 9, out, out && out == ctx->fl_prev_in, all_out,
+                         stride, ctx->dskip + K_FBLK, ctx->st);
+    }
     {
         LaunchScope ls(ctx, K_FBLK, n);
-        launch_diff_blocked(&tab, &ctx->tmapQ, ctx->H, ctx->W, ctx->P, pc, n, out, all_out, 2 * plane_elems(ctx),
-                            ctx->dskip + K_FBLK, ctx->nsm, ctx->dflags, ctx->st);
+        launch_diff_blocked(halo, &tab, &ctx->tmapQ, ctx->H, ctx->W, ctx->P, pc, n, ctx->flist, ctx->dflags + 9, out,
+                            all_out, stride, ctx->fact[1 - ctx->fl_par], ctx->dskip + K_FBLK, ctx->nsm, ctx->dflags,
+                            ctx->st);
     }
+    ctx->fl_par ^= 1;
+    ctx->fl_state = out ? out : all_out + (size_t)(n - 1) * stride;
+    ctx->fl_prev_in = in;
     return check_launch(ctx, "diff blocked");
 }
 
@@ -450,6 +484,7 @@ int steps_to_ckpt(const pf_ctx* c, int t) {
 int diff_steps(pf_ctx* ctx, int T) {
     const int end = ctx->step + T;
     const int kern = choose_kernel(ctx);
+    ctx->fl_state = nullptr;  // the current state may have been set by other means
     // with K == 1 every state is saved: blocked launches write all of them into
     // consecutive tape slots
     const bool all_states = ctx->tape_valid && ctx->K == 1;
@@ -626,6 +661,13 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
         ALLOC(ctx->work[1], diff_state_bytes(ctx));
         ALLOC(ctx->burn, (size_t)H * W);
         ALLOC(ctx->tile_list, (size_t)adjoint_blocked_tiles(H, ctx->P) * sizeof(int));
+        {
+            const size_t nt = (size_t)std::max(diff_blocked_tiles(8, H, ctx->P), diff_blocked_tiles(4, H, ctx->P));
+            ALLOC(ctx->fact[0], nt);
+            ALLOC(ctx->fact[1], nt);
+            ALLOC(ctx->fwasdead, nt);
+            ALLOC(ctx->flist, nt * sizeof(int));
+        }
         if (cudaMemsetAsync(ctx->work[0], 0, diff_state_bytes(ctx), ctx->st) != cudaSuccess) goto cuda_failed;
         if (cudaMemsetAsync(ctx->work[1], 0, diff_state_bytes(ctx), ctx->st) != cudaSuccess) goto cuda_failed;
         if (cudaMemsetAsync(ctx->burn, 1, (size_t)H * W, ctx->st) != cudaSuccess) goto cuda_failed;
@@ -1017,6 +1059,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             // checkpoint copied to slot 0, the rest recomputed
             float* seg = ctx->seg_buf;
             CK(cudaMemcpyAsync(seg, slot_ptr(ctx, ctx->ckpts[si].second), sbytes, cudaMemcpyDeviceToDevice, ctx->st));
+            ctx->fl_state = nullptr;  // a new chain starts from the checkpoint
             for (int t = s0; t < s1 - 1;) {
                 const float* in = seg + (size_t)(t - s0) * selems;
                 float* nxt = seg + (size_t)(t - s0 + 1) * selems;
