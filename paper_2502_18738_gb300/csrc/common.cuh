@@ -151,10 +151,13 @@ int diff_blocked_configure();
 int diff_blocked_tiles(int halo, int H, int pitch);
 void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* act, uint8_t* wasdead,
                          cudaStream_t s);
+// seg_dirty (nullable): all_out lies in a segment buffer reused across segments, whose
+// slots zero_base + s * all_stride (s < zero_slots) hold zeros for tiles not dirty; void
+// tiles (a = b = 0 in the whole region) then write nothing there (see k_fwd_tiles).
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* wasdead, int* tile_list, int* tile_count, float* out,
-                      bool out_is_prev_in, float* all_out, size_t all_stride, unsigned long long* skipped,
-                      cudaStream_t s);
+                      bool out_is_prev_in, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
+                      int zero_slots, unsigned long long* skipped, cudaStream_t s);
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
                          int n, const int* tile_list, const int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,

@@ -225,34 +225,52 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
                         const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
                         const float nu[8] = {uu[0], uu[1], uu[2], um[0], um[2], ud[0], ud[1], ud[2]};
-                        float f[8];
-#pragma unroll
-                        for (int d = 0; d < 8; ++d) f[d] = fmaf(-nb[d], qv[d], 1.0f);
                         float av, ua;
                         a_decode(Aown, av, ua);
                         const float ln = la[k] + lb[k];
                         const float tg = ln * ua;  // l_P_j in units 2^sigma'(j)
-                        // t_d = tg prod_{e != d} f_e by a product tree over pairs and
-                        // halves (no division: a factor can be exactly 0)
-                        const float p01 = f[0] * f[1], p23 = f[2] * f[3], p45 = f[4] * f[5], p67 = f[6] * f[7];
-                        const float p03 = p01 * p23, p47 = p45 * p67;
-                        // P enters only l_a = l_a' - l_n P here, where 1 - S's absolute
-                        // error (a few 1e-8) is harmless; the forward keeps the recurrence
-                        const float P = 1.0f - p03 * p47;
-                        const float g03 = tg * p47, g47 = tg * p03;
-                        const float r01 = g03 * p23, r23 = g03 * p01, r45 = g47 * p67, r67 = g47 * p45;
-                        const float t[8] = {f[1] * r01, f[0] * r01, f[3] * r23, f[2] * r23,
-                                            f[5] * r45, f[4] * r45, f[7] * r67, f[6] * r67};
-                        la[k] = fmaf(-ln, P, la[k]) * scl[k];
+                        bool quiet = true;  // no neighbour burning (behind or ahead of the front)
 #pragma unroll
-                        for (int d = 0; d < 8; ++d) {
-                            gv[d] = fmaf(t[d], nb[d] * Up, gv[d]);
-                            const float tq = t[d] * qv[d];
-                            const float r = Up * nu[d];  // 2^(sigma'(j) - sigma(i)): to the units of source i
-                            const int j = dir_dc(d) + 1;
-                            if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
-                            else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
-                            else wd[j] = fmaf(tq, r, wd[j]);
+                        for (int d = 0; d < 8; ++d) quiet &= nb[d] == 0.0f;
+                        if (quiet) {
+                            // P = 0, every leave-one-out product is 1 and every dL/dq term
+                            // carries b_i = 0: only the contributions t_d q_dj = tg q_dj remain
+                            la[k] *= scl[k];
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) {
+                                const float tq = tg * qv[d];
+                                const float r = Up * nu[d];
+                                const int j = dir_dc(d) + 1;
+                                if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
+                                else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
+                                else wd[j] = fmaf(tq, r, wd[j]);
+                            }
+                        } else {
+                            float f[8];
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) f[d] = fmaf(-nb[d], qv[d], 1.0f);
+                            // t_d = tg prod_{e != d} f_e by a product tree over pairs and
+                            // halves (no division: a factor can be exactly 0)
+                            const float p01 = f[0] * f[1], p23 = f[2] * f[3], p45 = f[4] * f[5], p67 = f[6] * f[7];
+                            const float p03 = p01 * p23, p47 = p45 * p67;
+                            // P enters only l_a = l_a' - l_n P here, where 1 - S's absolute
+                            // error (a few 1e-8) is harmless; the forward keeps the recurrence
+                            const float P = 1.0f - p03 * p47;
+                            const float g03 = tg * p47, g47 = tg * p03;
+                            const float r01 = g03 * p23, r23 = g03 * p01, r45 = g47 * p67, r67 = g47 * p45;
+                            const float t[8] = {f[1] * r01, f[0] * r01, f[3] * r23, f[2] * r23,
+                                                f[5] * r45, f[4] * r45, f[7] * r67, f[6] * r67};
+                            la[k] = fmaf(-ln, P, la[k]) * scl[k];
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) {
+                                gv[d] = fmaf(t[d], nb[d] * Up, gv[d]);
+                                const float tq = t[d] * qv[d];
+                                const float r = Up * nu[d];  // 2^(sigma'(j) - sigma(i)): to the units of source i
+                                const int j = dir_dc(d) + 1;
+                                if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
+                                else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
+                                else wd[j] = fmaf(tq, r, wd[j]);
+                            }
                         }
                     } else {
                         la[k] *= scl[k];

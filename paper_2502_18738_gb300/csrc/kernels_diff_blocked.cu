@@ -234,6 +234,13 @@ __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ 
 // tiles are listed for k_diff_blocked. A quiescent tile's interior is copied to the
 // outputs, except into `out` when out holds the previous launch's input and the tile was
 // quiescent then too (out already holds this state). act_out = 0 for quiescent tiles.
+//
+// Segment buffers (seg_dirty != nullptr): all_out is a run of slots of a buffer that is
+// reused from segment to segment, and seg_dirty[tile] records whether the tile's interior
+// may be nonzero in any of its zero_slots slots from zero_base on. A quiescent tile with
+// a = 0 in its whole region is void (exactly zero there for the whole launch); its
+// slots only have to hold zeros, which they already do unless the tile is dirty, in
+// which case all of them are zeroed once.
 template <int kHalo>
 __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in, int H, int W, int pitch,
                                                    int tiles_x, int tiles_y, int n, const uint8_t* __restrict__ act_in,
@@ -241,7 +248,8 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                                                    int* __restrict__ list, int* __restrict__ count,
                                                    float* __restrict__ out, int out_is_prev_in,
                                                    float* __restrict__ all_out, size_t all_stride,
-                                                   unsigned long long* __restrict__ skipped) {
+                                                   uint8_t* __restrict__ seg_dirty, float* __restrict__ zero_base,
+                                                   int zero_slots, unsigned long long* __restrict__ skipped) {
     constexpr int kI = kRT - 2 * kHalo;
     const int tile = blockIdx.x;
     const int ty = tile / tiles_x, tx = tile % tiles_x;
@@ -255,13 +263,45 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
         if (threadIdx.x == 0) {
             list[atomicAdd(count, 1)] = tile;
             wasdead[tile] = 0;
+            if (seg_dirty) seg_dirty[tile] = 1;
         }
         return;
     }
     const int r0 = ty * kI, c0 = tx * kI;
     const size_t gplane = (size_t)H * pitch;
+    bool write_all = all_out != nullptr;
+    if (seg_dirty) {
+        // void test over the whole region (float4 columns: c0 - kHalo and pitch are
+        // multiples of 4, so a float4 is wholly inside or wholly outside [0, pitch))
+        bool any = false;
+        for (int i = threadIdx.x; i < kRT * (kCT / 4); i += 256) {
+            const int gr = r0 - kHalo + i / (kCT / 4), gc = c0 - kHalo + 4 * (i % (kCT / 4));
+            if (gr < 0 || gr >= H || gc < 0 || gc >= pitch) continue;
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + (size_t)gr * pitch + gc));
+            any |= (v.x | v.y | v.z | v.w) != 0u;
+        }
+        const bool is_void = !__syncthreads_or(any);
+        if (is_void) {
+            write_all = false;
+            if (seg_dirty[tile]) {
+                for (int i = threadIdx.x; i < kI * (kI / 4); i += 256) {
+                    const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
+                    if (gr >= H || gc >= pitch) continue;
+                    const size_t j = (size_t)gr * pitch + gc;
+                    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int s = 0; s < zero_slots; ++s) {
+                        float* o = zero_base + (size_t)s * all_stride;
+                        *reinterpret_cast<float4*>(o + j) = z;
+                        *reinterpret_cast<float4*>(o + gplane + j) = z;
+                    }
+                }
+            }
+        }
+        __syncthreads();  // every thread has read seg_dirty[tile] before it changes
+        if (threadIdx.x == 0) seg_dirty[tile] = is_void ? 0 : 1;
+    }
     const bool copy_out = out && !(out_is_prev_in && wasdead[tile]);
-    if (copy_out || all_out) {
+    if (copy_out || write_all) {
         // float4 columns: c0 and pitch are multiples of 4
         for (int i = threadIdx.x; i < kI * (kI / 4); i += 256) {
             const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
@@ -273,7 +313,7 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                 *reinterpret_cast<float4*>(out + j) = a;
                 *reinterpret_cast<float4*>(out + gplane + j) = b;
             }
-            if (all_out)
+            if (write_all)
                 for (int s = 0; s < n; ++s) {
                     float* o = all_out + (size_t)s * all_stride;
                     *reinterpret_cast<float4*>(o + j) = a;
@@ -328,8 +368,8 @@ void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* a
 
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* wasdead, int* tile_list, int* tile_count, float* out,
-                      bool out_is_prev_in, float* all_out, size_t all_stride, unsigned long long* skipped,
-                      cudaStream_t s) {
+                      bool out_is_prev_in, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
+                      int zero_slots, unsigned long long* skipped, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int tiles_y = (H + inner - 1) / inner;
@@ -337,11 +377,13 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
     if (halo == 4)
         k_fwd_tiles<4><<<tiles_x * tiles_y, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
-                                                         all_out, all_stride, skipped);
+                                                         all_out, all_stride, seg_dirty, zero_base, zero_slots,
+                                                         skipped);
     else
         k_fwd_tiles<8><<<tiles_x * tiles_y, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
-                                                         all_out, all_stride, skipped);
+                                                         all_out, all_stride, seg_dirty, zero_base, zero_slots,
+                                                         skipped);
 }
 
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,

@@ -157,8 +157,18 @@ __global__ void __launch_bounds__(kAdjThreads) k_prep_adjoint(PrepArgs g, const 
     for (size_t j = (size_t)blockIdx.x * kAdjThreads + threadIdx.x; j < HW; j += (size_t)gridDim.x * kAdjThreads) {
         const int r = (int)(j / g.W), c = (int)(j % g.W);
         if (g.burnable && g.burnable[j] == 0) continue;
-        const CellFactors f = load_cell(g, r, c);
         const float* gq = Gq + (size_t)r * g.pitch + c;
+        // cells no fire reached during the epoch have dL/dq = 0 in every direction and
+        // contribute nothing: skip their (transcendental-heavy) derivative evaluation
+        float gqv[8];
+        bool any = false;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            gqv[d] = gq[d * plane];
+            any |= gqv[d] != 0.0f;
+        }
+        if (!any) continue;
+        const CellFactors f = load_cell(g, r, c);
         float sh = 0.f, s1 = 0.f, s2 = 0.f, sa = 0.f, se = 0.f;
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
@@ -167,7 +177,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_prep_adjoint(PrepArgs g, const 
             const float e = expf(expo);
             float pp;
             const float qq = q_of(f, e, &pp);
-            const float gpp = gq[d * plane] * kC * ((1.0f - qq) * (1.0f + qq));  // tanh'
+            const float gpp = gqv[d] * kC * ((1.0f - qq) * (1.0f + qq));  // tanh'
             se += gpp * e;              // d pp / d(p_h (1+pv)(1+pd)) summed over d
             sh += gpp * f.G * e;        // d pp / d p_h
             s1 += gpp * pp * f.V;       // d pp / d c1

@@ -121,6 +121,8 @@ struct pf_ctx {
     int nsm = 152;
     float* seg_buf = nullptr;  // K-1 contiguous states (segment recompute)
     int seg_cap = 0;
+    uint8_t* seg_dirty = nullptr;  // per forward tile: its interior may be nonzero in slots 1.. of seg_buf
+    int seg_halo = 0;              // tile geometry seg_dirty refers to
     int TH = 64, KH = 16;
     pf_tuning tun{0, 0, 0, 0};
     std::vector<ProfRec> prof;
@@ -345,7 +347,8 @@ int blocked_k(const pf_ctx* c) {
 // Launches form chains (the output of one is the input of the next) along which the
 // tile activity is carried; a chain starts wherever `in` is not the state the activity
 // describes (ctx->fl_state, reset by every caller that starts a new sequence).
-int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* out, float* all_out) {
+int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* out, float* all_out,
+                        bool seg = false) {
     CUtensorMap tab;
     if (!encode_f32_3d(&tab, in, ctx->P, ctx->H, 2, diff_blocked_box_cols(), diff_blocked_box_rows(), 2))
         return fail(ctx, PF_ECUDA, "tensor map encoding of the state buffer failed");
@@ -363,7 +366,8 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
         LaunchScope ls(ctx, K_FTILES);
         launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
                          ctx->fwasdead, ctx->flist, ctx->dflags + 9, out, out && out == ctx->fl_prev_in, all_out,
-                         stride, ctx->dskip + K_FBLK, ctx->st);
+                         stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_buf + stride : nullptr,
+                         ctx->seg_cap - 1, ctx->dskip + K_FBLK, ctx->st);
     }
     {
         LaunchScope ls(ctx, K_FBLK, n);
@@ -945,6 +949,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
         if ((rc = dalloc(ctx, &p, sbytes * (size_t)segmax))) return rc;
         ctx->seg_buf = (float*)p;
         ctx->seg_cap = segmax;
+        ctx->seg_halo = 0;  // contents unknown: cleared before the first blocked recompute
     }
     const size_t selems = 2 * pe;
     const int kern = choose_kernel(ctx);
@@ -1058,6 +1063,26 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             // the segment's states s0 .. s1-1, consecutive in the segment buffer: the
             // checkpoint copied to slot 0, the rest recomputed
             float* seg = ctx->seg_buf;
+            if (kern == 2) {
+                // blocked recompute: the slots hold zeros wherever seg_dirty is clear
+                const int halo = blocked_k(ctx) <= 4 ? 4 : 8;
+                if (ctx->seg_halo != halo) {
+                    if (!ctx->seg_dirty) {
+                        void* p;
+                        const int nt = std::max(diff_blocked_tiles(8, ctx->H, ctx->P), diff_blocked_tiles(4, ctx->H, ctx->P));
+                        if ((rc = dalloc(ctx, &p, (size_t)nt))) return rc;
+                        ctx->seg_dirty = (uint8_t*)p;
+                    }
+                    CK(cudaMemsetAsync(seg, 0, sbytes * (size_t)ctx->seg_cap, ctx->st));
+                    CK(cudaMemsetAsync(ctx->seg_dirty, 0,
+                                       (size_t)std::max(diff_blocked_tiles(8, ctx->H, ctx->P),
+                                                        diff_blocked_tiles(4, ctx->H, ctx->P)),
+                                       ctx->st));
+                    ctx->seg_halo = halo;
+                }
+            } else {
+                ctx->seg_halo = 0;  // the plain kernel writes every cell of the slots
+            }
             CK(cudaMemcpyAsync(seg, slot_ptr(ctx, ctx->ckpts[si].second), sbytes, cudaMemcpyDeviceToDevice, ctx->st));
             ctx->fl_state = nullptr;  // a new chain starts from the checkpoint
             for (int t = s0; t < s1 - 1;) {
@@ -1065,7 +1090,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                 float* nxt = seg + (size_t)(t - s0 + 1) * selems;
                 if (kern == 2) {
                     const int n = std::min(blocked_k(ctx), s1 - 1 - t);
-                    if ((rc = diff_blocked_launch(ctx, in, pc, n, nullptr, nxt))) return rc;
+                    if ((rc = diff_blocked_launch(ctx, in, pc, n, nullptr, nxt, true))) return rc;
                     t += n;
                 } else {
                     {
