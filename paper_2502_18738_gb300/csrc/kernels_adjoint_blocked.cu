@@ -374,38 +374,39 @@ __global__ void __launch_bounds__(kThreads, 1)
 // here; the others are listed (in any order: each tile writes only its own interior and
 // adds to its own cells' dL/dq once) for k_adjoint_blocked.
 __global__ void __launch_bounds__(256) k_adjoint_tiles(const float* __restrict__ A, int H, int W, int pitch,
-                                                       int tiles_x, int n, int* __restrict__ list,
+                                                       int tiles_x, int ntiles, int n, int* __restrict__ list,
                                                        int* __restrict__ count, float* __restrict__ lam_out,
                                                        uint8_t* __restrict__ sig_out,
                                                        unsigned long long* __restrict__ skipped) {
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;  // one warp per tile
+    if (tile >= ntiles) return;
     int r0, c0;
     origin(tile, tiles_x, r0, c0);
-    const int tid = threadIdx.x;
-    bool any = false;
+    uint32_t any = 0u;
     // 64 rows x 16 float4 (c0 and pitch are multiples of 4 floats: a float4 is wholly
     // inside or wholly outside [0, pitch))
-    for (int i = tid; i < kRT * (kCT / 4); i += 256) {
+    for (int i = lane; i < kRT * (kCT / 4); i += 32) {
         const int gr = r0 + i / (kCT / 4), gc = c0 + 4 * (i % (kCT / 4));
         if (gr < 0 || gr >= H || gc < 0 || gc >= pitch) continue;
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(A + (size_t)gr * pitch + gc));
-        any |= (v.x | v.y | v.z | v.w) != 0u;
+        any |= v.x | v.y | v.z | v.w;
     }
-    if (__syncthreads_or(any)) {
-        if (tid == 0) list[atomicAdd(count, 1)] = tile;
+    if (__any_sync(0xffffffffu, any != 0u)) {
+        if (lane == 0) list[atomicAdd(count, 1)] = tile;
         return;
     }
     const size_t gplane = (size_t)H * pitch;
     const int ir0 = r0 + kHalo, ic0 = c0 + kHalo;
-    for (int i = tid; i < kIR * kIC; i += 256) {
-        const int gr = ir0 + i / kIC, gc = ic0 + i % kIC;
+    for (int i = lane; i < kIR * (kIC / 4); i += 32) {
+        const int gr = ir0 + i / (kIC / 4), gc = ic0 + 4 * (i % (kIC / 4));
         if (gr >= H || gc >= pitch) continue;
         const size_t j = (size_t)gr * pitch + gc;
-        lam_out[j] = 0.0f;
-        lam_out[gplane + j] = 0.0f;
-        sig_out[j] = (uint8_t)kSigmaZero;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(lam_out + j) = z;
+        *reinterpret_cast<float4*>(lam_out + gplane + j) = z;
+        *reinterpret_cast<uint32_t*>(sig_out + j) = 0x01010101u * (uint32_t)kSigmaZero;
     }
-    if (tid == 0 && skipped)
+    if (lane == 0 && skipped)
         atomicAdd(skipped, (unsigned long long)(min(kIR, H - ir0) * min(kIC, W - ic0)) * (unsigned long long)n);
 }
 
@@ -432,8 +433,9 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
                           int* tile_list, int* tile_count, unsigned long long* skipped, cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
     cudaMemsetAsync(tile_count, 0, sizeof(int), s);
-    k_adjoint_tiles<<<adjoint_blocked_tiles(H, pitch), 256, 0, s>>>(A_latest, H, W, pitch, tiles_x, n, tile_list,
-                                                                    tile_count, lam_out, sig_out, skipped);
+    const int ntiles = adjoint_blocked_tiles(H, pitch);
+    k_adjoint_tiles<<<(ntiles + 7) / 8, 256, 0, s>>>(A_latest, H, W, pitch, tiles_x, ntiles, n, tile_list, tile_count,
+                                                     lam_out, sig_out, skipped);
 }
 
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,

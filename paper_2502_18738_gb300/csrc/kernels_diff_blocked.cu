@@ -34,6 +34,10 @@ struct Smem {
     float b[2][kPlane];      // b ping-pong of the current tile
 };
 
+// Tile activity flags, one byte per tile: kActB = b > 0 somewhere in the tile's
+// interior, kActA = a > 0 somewhere in it (encoded A != +0).
+constexpr uint8_t kActB = 1, kActA = 2;
+
 template <int kHalo>
 __device__ __forceinline__ void tile_origin(int tile, int tiles_x, int& r0, int& c0) {
     constexpr int kIR = kRT - 2 * kHalo, kIC = kCT - 2 * kHalo;
@@ -190,57 +194,69 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         // whether b > 0 anywhere in the interior after the launch (for the next launch's
         // tile list); the barrier also protects the ping-pong buffers reused by the next tile
-        bool act = false;
+        bool actB = false, actA = false;
         if (x >= kHalo && x < kCT - kHalo) {
 #pragma unroll
             for (int m = 0; m < kM; ++m) {
                 const int y = ys + m;
-                if (y >= kHalo && y < kRT - kHalo) act |= sm.b[cur][y * kCT + x] != 0.0f;
+                if (y >= kHalo && y < kRT - kHalo) {
+                    actB |= sm.b[cur][y * kCT + x] != 0.0f;
+                    actA |= __float_as_uint(A[m]) != 0u;
+                }
             }
         }
-        act = __syncthreads_or(act);
-        if (tid == 0) act_out[tile] = act ? 1 : 0;
+        actB = __syncthreads_or(actB);
+        actA = __syncthreads_or(actA);
+        if (tid == 0) act_out[tile] = (actA ? kActA : 0) | (actB ? kActB : 0);
     }
 }
 
-// Tile activity of a state (start of a chain of launches): act[tile] = b > 0 somewhere in
-// the tile's interior; wasdead[tile] = 0 (nothing is known about the other buffers).
+// Activity of a state at the start of a chain of launches; wasdead[tile] = 0 (nothing is
+// known about the other buffers). One warp per tile.
 template <int kHalo>
 __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ ab, int H, int pitch, int tiles_x,
-                                                      uint8_t* __restrict__ act, uint8_t* __restrict__ wasdead) {
+                                                      int ntiles, uint8_t* __restrict__ act,
+                                                      uint8_t* __restrict__ wasdead) {
     constexpr int kI = kRT - 2 * kHalo;
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (tile >= ntiles) return;
     int r0, c0;
     tile_origin<kHalo>(tile, tiles_x, r0, c0);
     r0 += kHalo;
     c0 += kHalo;
-    const float* b = ab + (size_t)H * pitch;
-    bool any = false;
-    for (int i = threadIdx.x; i < kI * kI; i += 256) {
-        const int gr = r0 + i / kI, gc = c0 + i % kI;
-        if (gr < H && gc < pitch) any |= __ldg(b + (size_t)gr * pitch + gc) != 0.0f;
+    const size_t gplane = (size_t)H * pitch;
+    uint32_t anyA = 0u, anyB = 0u;
+    // float4 columns: c0 and pitch are multiples of 4
+    for (int i = lane; i < kI * (kI / 4); i += 32) {
+        const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
+        if (gr >= H || gc >= pitch) continue;
+        const uint4 a = __ldg(reinterpret_cast<const uint4*>(ab + (size_t)gr * pitch + gc));
+        const uint4 b = __ldg(reinterpret_cast<const uint4*>(ab + gplane + (size_t)gr * pitch + gc));
+        anyA |= a.x | a.y | a.z | a.w;
+        anyB |= (b.x | b.y | b.z | b.w) & 0x7fffffffu;
     }
-    any = __syncthreads_or(any);
-    if (threadIdx.x == 0) {
-        act[tile] = any ? 1 : 0;
+    const bool hasA = __any_sync(0xffffffffu, anyA != 0u), hasB = __any_sync(0xffffffffu, anyB != 0u);
+    if (lane == 0) {
+        act[tile] = (hasA ? kActA : 0) | (hasB ? kActB : 0);
         wasdead[tile] = 0;
     }
 }
 
-// Pre-pass of one forward launch. A tile is live if b > 0 anywhere in the interiors of
-// the 3 x 3 tiles around it (act_in, from the previous launch or k_fwd_act_init): its
-// region (interior + halo <= one interior) lies inside them, so a tile that is not live
-// has b = 0 in its whole region and its state does not change during the launch. Live
-// tiles are listed for k_diff_blocked. A quiescent tile's interior is copied to the
-// outputs, except into `out` when out holds the previous launch's input and the tile was
-// quiescent then too (out already holds this state). act_out = 0 for quiescent tiles.
+// Pre-pass of one forward launch, one warp per tile. A tile is live if b > 0 anywhere in
+// the interiors of the 3 x 3 tiles around it (act_in, from the previous launch or
+// k_fwd_act_init): its region (interior + halo <= one interior) lies inside them, so a
+// tile that is not live has b = 0 in its whole region and its state does not change
+// during the launch. Live tiles are listed for k_diff_blocked, which writes their
+// act_out. A quiescent tile keeps its kActA flag; its interior is copied to the outputs,
+// except into `out` when out holds the previous launch's input and the tile was
+// quiescent then too (out already holds this state).
 //
 // Segment buffers (seg_dirty != nullptr): all_out is a run of slots of a buffer that is
 // reused from segment to segment, and seg_dirty[tile] records whether the tile's interior
 // may be nonzero in any of its zero_slots slots from zero_base on. A quiescent tile with
-// a = 0 in its whole region is void (exactly zero there for the whole launch); its
-// slots only have to hold zeros, which they already do unless the tile is dirty, in
-// which case all of them are zeroed once.
+// a = 0 in the 3 x 3 interiors around it is void (exactly zero in its whole region for
+// the whole launch); its slots only have to hold zeros, which they already do unless the
+// tile is dirty, in which case all of them are zeroed once.
 template <int kHalo>
 __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in, int H, int W, int pitch,
                                                    int tiles_x, int tiles_y, int n, const uint8_t* __restrict__ act_in,
@@ -251,16 +267,17 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                                                    uint8_t* __restrict__ seg_dirty, float* __restrict__ zero_base,
                                                    int zero_slots, unsigned long long* __restrict__ skipped) {
     constexpr int kI = kRT - 2 * kHalo;
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (tile >= tiles_x * tiles_y) return;
     const int ty = tile / tiles_x, tx = tile % tiles_x;
-    bool live = false;
+    uint32_t around = 0u;
     for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
             const int yy = ty + dy, xx = tx + dx;
-            if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) live |= act_in[yy * tiles_x + xx] != 0;
+            if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) around |= act_in[yy * tiles_x + xx];
         }
-    if (live) {
-        if (threadIdx.x == 0) {
+    if (around & kActB) {
+        if (lane == 0) {
             list[atomicAdd(count, 1)] = tile;
             wasdead[tile] = 0;
             if (seg_dirty) seg_dirty[tile] = 1;
@@ -270,40 +287,30 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
     const int r0 = ty * kI, c0 = tx * kI;
     const size_t gplane = (size_t)H * pitch;
     bool write_all = all_out != nullptr;
-    if (seg_dirty) {
-        // void test over the whole region (float4 columns: c0 - kHalo and pitch are
-        // multiples of 4, so a float4 is wholly inside or wholly outside [0, pitch))
-        bool any = false;
-        for (int i = threadIdx.x; i < kRT * (kCT / 4); i += 256) {
-            const int gr = r0 - kHalo + i / (kCT / 4), gc = c0 - kHalo + 4 * (i % (kCT / 4));
-            if (gr < 0 || gr >= H || gc < 0 || gc >= pitch) continue;
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(in + (size_t)gr * pitch + gc));
-            any |= (v.x | v.y | v.z | v.w) != 0u;
-        }
-        const bool is_void = !__syncthreads_or(any);
-        if (is_void) {
-            write_all = false;
-            if (seg_dirty[tile]) {
-                for (int i = threadIdx.x; i < kI * (kI / 4); i += 256) {
-                    const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
-                    if (gr >= H || gc >= pitch) continue;
-                    const size_t j = (size_t)gr * pitch + gc;
-                    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                    for (int s = 0; s < zero_slots; ++s) {
-                        float* o = zero_base + (size_t)s * all_stride;
-                        *reinterpret_cast<float4*>(o + j) = z;
-                        *reinterpret_cast<float4*>(o + gplane + j) = z;
-                    }
+    if (seg_dirty && !(around & kActA)) {
+        write_all = false;
+        if (seg_dirty[tile]) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = lane; i < kI * (kI / 4); i += 32) {
+                const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
+                if (gr >= H || gc >= pitch) continue;
+                const size_t j = (size_t)gr * pitch + gc;
+                for (int s = 0; s < zero_slots; ++s) {
+                    float* o = zero_base + (size_t)s * all_stride;
+                    *reinterpret_cast<float4*>(o + j) = z;
+                    *reinterpret_cast<float4*>(o + gplane + j) = z;
                 }
             }
+            __syncwarp();
+            if (lane == 0) seg_dirty[tile] = 0;
         }
-        __syncthreads();  // every thread has read seg_dirty[tile] before it changes
-        if (threadIdx.x == 0) seg_dirty[tile] = is_void ? 0 : 1;
+    } else if (seg_dirty && lane == 0) {
+        seg_dirty[tile] = 1;
     }
     const bool copy_out = out && !(out_is_prev_in && wasdead[tile]);
     if (copy_out || write_all) {
         // float4 columns: c0 and pitch are multiples of 4
-        for (int i = threadIdx.x; i < kI * (kI / 4); i += 256) {
+        for (int i = lane; i < kI * (kI / 4); i += 32) {
             const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
             if (gr >= H || gc >= pitch) continue;
             const size_t j = (size_t)gr * pitch + gc;
@@ -321,8 +328,9 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                 }
         }
     }
-    if (threadIdx.x == 0) {
-        act_out[tile] = 0;
+    __syncwarp();  // wasdead[tile] read by every lane before it changes
+    if (lane == 0) {
+        act_out[tile] = act_in[tile] & kActA;
         wasdead[tile] = 1;
         if (skipped)
             atomicAdd(skipped, (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)n);
@@ -360,10 +368,11 @@ void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* a
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int ntiles = diff_blocked_tiles(halo, H, pitch);
+    const int blocks = (ntiles + 7) / 8;  // one warp per tile
     if (halo == 4)
-        k_fwd_act_init<4><<<ntiles, 256, 0, s>>>(ab, H, pitch, tiles_x, act, wasdead);
+        k_fwd_act_init<4><<<blocks, 256, 0, s>>>(ab, H, pitch, tiles_x, ntiles, act, wasdead);
     else
-        k_fwd_act_init<8><<<ntiles, 256, 0, s>>>(ab, H, pitch, tiles_x, act, wasdead);
+        k_fwd_act_init<8><<<blocks, 256, 0, s>>>(ab, H, pitch, tiles_x, ntiles, act, wasdead);
 }
 
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
@@ -375,12 +384,12 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
     const int tiles_y = (H + inner - 1) / inner;
     cudaMemsetAsync(tile_count, 0, sizeof(int), s);
     if (halo == 4)
-        k_fwd_tiles<4><<<tiles_x * tiles_y, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
+        k_fwd_tiles<4><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
                                                          all_out, all_stride, seg_dirty, zero_base, zero_slots,
                                                          skipped);
     else
-        k_fwd_tiles<8><<<tiles_x * tiles_y, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
+        k_fwd_tiles<8><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
                                                          all_out, all_stride, seg_dirty, zero_base, zero_slots,
                                                          skipped);
