@@ -45,6 +45,35 @@ WORKLOAD = "8192x8192 differentiable fwd+adjoint, T=2000, wind resampled every 1
 B_FWD, B_ADJ = 16, 24  # algorithmic bytes per cell-step: (a, b) in + out; state, lambda in, lambda out
 
 
+# DRAM traffic of the blocked kernels measured by ncu over every launch of one timed step
+# of the default workload (dram__bytes_read.sum + dram__bytes_write.sum, summed; see
+# profiles/dram_traffic_fwd_adjoint_8192sq_T2000.md), per cell-step the kernel computed.
+# A figure is used only while the kernel's sources hash to the value it was taken on.
+NCU_TRAFFIC = {
+    "adjoint_blocked": {"files": ["kernels_adjoint_blocked.cu", "common.cuh", "tma.cuh", "tmem.cuh"],
+                        "sha256_16": "062746f0c9917bf3", "bytes_per_computed_cell_step": 37.10},
+    "diff_blocked": {"files": ["kernels_diff_blocked.cu", "common.cuh", "tma.cuh"],
+                     "sha256_16": "a5bcf496e2c941f5", "bytes_per_computed_cell_step": 15.33},
+}
+
+
+def ncu_traffic(kind):
+    """Measured DRAM bytes per computed cell-step of a kernel kind, or None when the
+    kernel has changed since the counters were taken."""
+    import hashlib
+    e = NCU_TRAFFIC.get(kind)
+    if e is None:
+        return None
+    h = hashlib.sha256()
+    try:
+        for f in e["files"]:
+            with open(os.path.join(ROOT, "paper_2502_18738_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return e["bytes_per_computed_cell_step"] if h.hexdigest()[:16] == e["sha256_16"] else None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -139,6 +168,77 @@ def oracle_sample(land, winds, S0, y, T_s, crop):
     return crop * crop * T_s / dt, dt, orc.num_threads()
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the step time a multi-replica run reports)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def discrete_ensemble(pf, torch, timed, seed=1, N=1024, R=64, T=1000):
+    """The discrete forward ensemble (N^2 grid, R realisations in one context, smooth
+    per-cell wind, T steps): temporal-blocked kernel against the plain per-step kernel
+    on the same GPU, cell-updates/s (N^2 R T per run)."""
+    land = syn.make_landscape(N, N, seed)
+    V, th = syn.smooth_wind(N, N, seed, 0)
+    S0 = np.broadcast_to(syn.initial_state(land, syn.random_ignitions(land, seed)), (R, N, N)).copy()
+    c = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    m = pf.FireModel(N, N, pf.PF_DISCRETE, R, seed=seed)
+    m.set_env(c(land.E), c(land.p_veg), c(land.p_den), c(V), c(th))
+    m.set_params(**PARAMS)
+    S0d = c(S0)
+    out = {}
+    for name, kern in (("blocked", 2), ("plain", 1)):
+        m.set_tuning(kernel=kern)
+        m.forward(S0d, 20)  # warm-up
+        ms = timed(lambda: m.forward(S0d, T), 1)
+        out[name] = N * N * R * T / (ms / 1000.0)
+    m.close()
+    return {"config": f"{N}x{N}, R={R} realisations, T={T}, discrete uint8", "unit": "cell-updates/s",
+            "blocked": out["blocked"], "plain": out["plain"], "speedup": out["blocked"] / out["plain"]}
+
+
+def batched_fires(pf, torch, timed, n_fires=64, seed=4):
+    """Uneven fires (side log-uniform in [64, 2048], T uniform in [100, 1000], 1-5
+    ignitions, half discrete / half differentiable) through one pf_batch_submit, against
+    the same fires run one after another through per-fire contexts with the plain
+    per-step kernels; cell-updates/s over sum(side^2 T)."""
+    rng = np.random.default_rng(seed)
+    fires = []
+    for i in range(n_fires):
+        side = int(round(np.exp(rng.uniform(np.log(64), np.log(2048)))))
+        T = int(rng.integers(100, 1001))
+        land = syn.make_landscape(side, side, 100 + i)
+        V, th = syn.smooth_wind(side, side, 100 + i, 0)
+        S0 = syn.initial_state(land, syn.random_ignitions(land, 100 + i))
+        fires.append((side, T, i % 2, land, V, th, S0))
+    c = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    dev = [(side, T, form, c(land.E), c(land.p_veg), c(land.p_den), c(V), c(th), c(S0))
+           for side, T, form, land, V, th, S0 in fires]
+    cells = sum(side * side * T for side, T, *_ in fires)
+    jobs = [pf.make_job(S0, T, form=form, seed=seed, fire_id=i, E=E, p_veg=pv, p_den=pd, V_w=V, theta_w=th,
+                        **PARAMS)[0] for i, (side, T, form, E, pv, pd, V, th, S0) in enumerate(dev)]
+    pf.pf_batch_submit(jobs)  # warm-up
+    ms_batch = timed(lambda: pf.pf_batch_submit(jobs), 1)
+
+    def plain_all():
+        for i, (side, T, form, E, pv, pd, V, th, S0) in enumerate(dev):
+            m = pf.FireModel(side, side, form, 1, seed=seed)
+            m.set_env(E, pv, pd, V, th)
+            m.set_params(**PARAMS)
+            m.set_tuning(kernel=1)
+            m.forward(S0, T)
+            m.close()
+    ms_plain = timed(plain_all, 1)
+    return {"config": f"{n_fires} fires, side log-uniform [64, 2048], T uniform [100, 1000], "
+                      "half discrete / half differentiable, forward", "unit": "cell-updates/s",
+            "cell_steps": cells, "batched": cells / (ms_batch / 1000.0), "plain_per_fire": cells / (ms_plain / 1000.0),
+            "speedup": ms_plain / ms_batch}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle on a bounded sample, rank 0 only."""
     if rank != 0:
@@ -174,6 +274,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the discrete-ensemble and batched-fires comparisons against the plain kernels")
     ap.add_argument("--K", type=int, default=0, help="checkpoint interval (0 = chosen by the library)")
     ap.add_argument("--k", type=int, default=0, help="steps per blocked forward launch (0 = library default)")
     args = ap.parse_args()
@@ -233,12 +335,7 @@ def main():
             fn()
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1) / n
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / n, dist, "cuda")
 
     for _ in range(args.warmup):
         step()
@@ -271,8 +368,13 @@ def main():
     kind, (n_l, cs_l, t_l, sk_l) = max(prof.items(), key=lambda kv: kv[1][2])
     alg = {"adjoint_step": B_ADJ, "adjoint_blocked": B_ADJ, "diff_step": B_FWD, "diff_blocked": B_FWD}.get(kind, B_FWD)
     achieved = alg * (cs_l - sk_l) / (t_l / 1000.0) / 1e9
+    tb = ncu_traffic(kind)
     roof = {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": how,
+            "frac": achieved / hbm, "peak_source": how,
+            # measured DRAM bytes per launch (ncu, per computed cell-step x this run's
+            # computed cell-steps per launch); null if the kernel changed since
+            "traffic": None if tb is None else tb * (cs_l - sk_l) / n_l,
+            "traffic_bytes_per_computed_cell_step": tb,
             "launches": n_l, "ms_per_launch": t_l / n_l, "cell_steps_per_launch": (cs_l - sk_l) / n_l,
             "skipped_frac": sk_l / max(1, cs_l),
             "alg_bytes_per_cell_step": alg,
@@ -315,6 +417,11 @@ def main():
         e2e = {"value": cells * world / (ms_e2e / 1000.0), "unit": "cell-updates/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
 
+    extras = {}
+    if not args.no_extras:
+        extras["discrete_ensemble"] = discrete_ensemble(pf, torch, timed)
+        extras["batched_fires"] = batched_fires(pf, torch, timed)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt, thr = oracle_sample(land, winds, S0, y, 60, 1024)
@@ -338,7 +445,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": n, "cell_steps": cs, "skipped_cell_steps": sk, "ms": t}
                             for k, (n, cs, t, sk) in prof.items() if n},
-                "clocks": clk.summary()}
+                "clocks": clk.summary(), **extras}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
