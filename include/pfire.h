@@ -176,6 +176,18 @@ typedef struct pf_tuning {
 int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t);
 int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t);
 
+/* Autotuner (no counterpart in the paper, which has one PyTorch code path). Times, on
+ * this context's grid, fields and parameters, a forward of T_probe steps from S_init
+ * (device, uint8 [R][H][W] as for pf_forward) with each candidate launch configuration:
+ * the plain per-step kernels and the temporal-blocked kernels at several depths k (for
+ * the differentiable form k <= 4 also selects the 4-cell-halo tile geometry). Keeps
+ * the fastest as the context's kernel and k (the checkpoint interval K stays chosen by
+ * memory), and writes the resulting tuning to *chosen (nullable, host). Results do not
+ * depend on the choice: the kernels compute the same arithmetic. The probe runs leave
+ * no tape: call pf_forward before pf_backward. Synchronous. PF_EINVAL for NULL
+ * arguments, T_probe < 1 or invalid state codes. */
+int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chosen);
+
 /* Per-kernel-kind launch counts, cell-steps processed (cells x automaton steps the
  * launches advanced or reversed), the part of those cell-steps the temporal-blocked
  * kernels skipped because their tile was quiescent (forward: b = 0 in the whole tile

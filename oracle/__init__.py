@@ -138,11 +138,13 @@ class Params:
 
     def __init__(self, p_h, c1, c2, a, p_continue, l=30.0, exact=False):
         r = (lambda v: float(v)) if exact else f32
+        self.exact = exact
         self.p_h, self.c1, self.c2, self.a = r(p_h), r(c1), r(c2), r(a)
         self.p_continue, self.l = f32(p_continue), r(l)
 
     def with_(self, **kw):
-        d = dict(p_h=self.p_h, c1=self.c1, c2=self.c2, a=self.a, p_continue=self.p_continue, l=self.l)
+        d = dict(p_h=self.p_h, c1=self.c1, c2=self.c2, a=self.a, p_continue=self.p_continue, l=self.l,
+                 exact=self.exact)
         d.update(kw)
         return Params(**d)
 

@@ -23,7 +23,7 @@ __all__ = [
     "PFireError", "build", "load", "PF_DISCRETE", "PF_DIFF",
     "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward",
     "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
-    "pf_set_tuning", "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error",
+    "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_profile_read", "pf_batch_submit", "pf_last_error",
     "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
     "EXPORTED_SYMBOLS",
 ]
@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = [
     "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
-    "pf_loss_bce_noalloc",
+    "pf_loss_bce_noalloc", "pf_autotune",
 ]
 PF_NOALLOC_BCE_MAX_N = 67108864
 
@@ -100,6 +100,7 @@ def load():
             "pf_loss_bce_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double), vp], i),
             "pf_set_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_get_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
+            "pf_autotune": ([vp, vp, i, ctypes.POINTER(PfTuning)], i),
             "pf_profile_read": ([vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_double), i], i),
@@ -245,6 +246,14 @@ def pf_get_tuning(h) -> dict:
     return dict(kernel=t.kernel, k=t.k, K=t.K, profile=t.profile)
 
 
+def pf_autotune(h, S_init, T_probe) -> dict:
+    """Time the candidate launch configurations on a T_probe-step forward from S_init
+    and keep the fastest; returns the resulting tuning."""
+    t = PfTuning()
+    _check(load().pf_autotune(h, _ptr(S_init, torch.uint8, None, "S_init"), int(T_probe), ctypes.byref(t)), h)
+    return dict(kernel=t.kernel, k=t.k, K=t.K, profile=t.profile)
+
+
 def pf_profile_read(h, reset=False) -> dict:
     """{kernel kind: (launches, cell_steps, device ms, skipped cell_steps)} since the last
     reset; skipped = cell-steps of quiescent tiles the blocked kernels did not compute."""
@@ -316,6 +325,9 @@ class FireModel:
 
     def set_tuning(self, **kw):
         pf_set_tuning(self.h, **kw)
+
+    def autotune(self, S_init, T_probe=64):
+        return pf_autotune(self.h, S_init, T_probe)
 
     def _out(self):
         if self.form == PF_DISCRETE:

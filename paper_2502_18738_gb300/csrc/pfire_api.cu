@@ -818,6 +818,74 @@ int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t) {
     return PF_OK;
 }
 
+int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chosen) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_autotune: ctx is NULL");
+    if (!S_init) return fail(ctx, PF_EINVAL, "pf_autotune: S_init is NULL");
+    if (T_probe < 1) return fail(ctx, PF_EINVAL, "pf_autotune: T_probe must be >= 1");
+    int rc = validate_states(ctx, S_init, (size_t)ctx->R * ctx->H * ctx->W);
+    if (rc) return rc;
+    // candidates (kernel, k): the plain per-step kernels and the temporal-blocked ones at
+    // several depths (the differentiable blocked kernel switches to its 4-cell halo for k <= 4)
+    std::vector<std::pair<int, int>> cand = {{1, 1}};
+    if (ctx->form == PF_DISCRETE) {
+        if (ctx->tmap_ok)
+            for (int k : {4, 8, 16})
+                if (k <= ctx->KH) cand.push_back({2, k});
+    } else if (ctx->tmapQ_ok) {
+        for (int k : {2, 4, 6, 8}) cand.push_back({2, k});
+    }
+    const pf_tuning saved = ctx->tun;
+    tape_reset(ctx);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PF_ECUDA, "pf_autotune: event creation failed");
+    }
+    float best_ms = 0.f;
+    int best = -1;
+    for (int rep = 0; rep < 2 && rc == PF_OK; ++rep)  // first pass warms every variant up
+        for (size_t c = 0; c < cand.size() && rc == PF_OK; ++c) {
+            ctx->tun.kernel = cand[c].first;
+            ctx->tun.k = cand[c].second;
+            ctx->step = 0;
+            if (ctx->form == PF_DISCRETE) {
+                ctx->scur = 0;
+                if (cudaMemcpy2DAsync(ctx->S[0], ctx->P, S_init, ctx->W, ctx->W, (size_t)ctx->R * ctx->H,
+                                      cudaMemcpyDeviceToDevice, ctx->st) != cudaSuccess) {
+                    rc = fail(ctx, PF_ECUDA, "pf_autotune: state copy failed");
+                    break;
+                }
+            } else {
+                launch_diff_init(S_init, ctx->H, ctx->W, ctx->P, ctx->work[0], ctx->burn, ctx->st);
+                ctx->cur_ab = ctx->work[0];
+                ctx->version++;
+            }
+            cudaEventRecord(e0, ctx->st);
+            rc = ctx->form == PF_DISCRETE ? run_discrete(ctx, T_probe) : diff_steps(ctx, T_probe);
+            cudaEventRecord(e1, ctx->st);
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = fail(ctx, PF_ECUDA, "pf_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 && (best < 0 || ms < best_ms)) {
+                best_ms = ms;
+                best = (int)c;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tun = saved;
+    ctx->step = 0;
+    if (rc) return rc;
+    ctx->tun.kernel = cand[best].first;
+    ctx->tun.k = cand[best].second;
+    if (chosen) pf_get_tuning(ctx, chosen);
+    return PF_OK;
+}
+
 int pf_forward(pf_ctx* ctx, const uint8_t* S_init, int T, void* S_out) {
     if (!ctx) return fail(nullptr, PF_EINVAL, "pf_forward: ctx is NULL");
     if (!S_init) return fail(ctx, PF_EINVAL, "pf_forward: S_init is NULL");
