@@ -198,6 +198,46 @@ int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chos
 int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* launches, long long* cell_steps,
                     long long* skipped_cell_steps, double* ms, int reset);
 
+/* ------------------------------------------- the paper's accumulator calibration path */
+
+/* Accumulator of the discrete form (Sec. 2.2, data flow of Fig. 4: "the p_ignite values
+ * of newly ignited cells are accumulated"). acc: device FP32 [R][H][W], caller-owned,
+ * NULL disables. While set, pf_forward zero-fills it and records the trajectory (its
+ * initial state, parameters and fields), and every step of pf_forward / pf_advance
+ * writes into acc[r][j] the FP32 p_ignite (Eq. 9) with which cell j ignited; a cell
+ * ignites at most once, and cells that never ignite (or burned from the start) keep 0.
+ * PF_EINVAL for the differentiable form. */
+int pf_set_accumulator(pf_ctx* ctx, float* acc);
+
+/* Replace the Philox key of the context (the paper's model.reset() draws a new seed
+ * per calibration epoch, Alg. 1). Invalidates recorded trajectories and tapes. */
+int pf_reseed(pf_ctx* ctx, uint64_t seed);
+
+/* Gradient of a loss of the accumulator (Sec. 2.3, back-propagation): with the sampled
+ * trajectory held fixed, only the p_ignite of newly ignited cells depends on the
+ * parameters, dp_ignite_j / dq_dj = beta_i prod_{e != d} (1 - beta_e q_ej) (beta: the
+ * burning indicators of the step, Eq. 9), chained through Eq. 1-5 to (p_h, c1, c2, a)
+ * and per-cell p_veg, p_den. The trajectory of the last pf_forward (+ pf_advance) with an
+ * accumulator set is replayed from its initial state with the same Philox draws.
+ *   dL_dacc     device FP32 [R][H][W]; realisations are summed.
+ *   step_mask   host uint8 [steps run] or NULL (all): steps whose ignitions carry
+ *               gradient (the paper's "step rings"); the others count as constants.
+ *   grad_params host double[4]: dL/d(p_h, c1, c2, a), FP64 fixed-order reduction.
+ *   grad_pveg, grad_pden  device FP32 [H][W] or NULL.
+ * Synchronous. PF_ESTATE if no trajectory was recorded, or parameters, fields or wind
+ * changed since it was. */
+int pf_backward_dca(pf_ctx* ctx, const float* dL_dacc, const uint8_t* step_mask, double grad_params[4],
+                    float* grad_pveg, float* grad_pden);
+
+/* Loss of Eq. 10 on one H x W map: binary cross-entropy with logits of yhat against the
+ * 0/1 observation y, averaged over the crop to the bounding box of the union of the
+ * non-zero entries of yhat and y (the paper's acceleration; 0 if both are all zero),
+ * plus the mean of (AvgPool(y) - AvgPool(yhat))^2 over the 4 x 4, stride-4 windows that
+ * fit in the map. yhat, y: device FP32 [H][W]; dL_dyhat: device FP32 [H][W] or NULL;
+ * loss: host double or NULL (then the call is asynchronous on cuda_stream). Block
+ * partials are reduced in FP64 in a fixed order. */
+int pf_loss_eq10(const float* yhat, const float* y, int H, int W, float* dL_dyhat, double* loss, void* cuda_stream);
+
 /* ----------------------------------------------------------- batched fires */
 
 /* One independent fire for pf_batch_submit. All pointers are device pointers; the

@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = [
     "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
-    "pf_loss_bce_noalloc", "pf_autotune",
+    "pf_loss_bce_noalloc", "pf_autotune", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
 ]
 PF_NOALLOC_BCE_MAX_N = 67108864
 
@@ -101,6 +101,10 @@ def load():
             "pf_set_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_get_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_autotune": ([vp, vp, i, ctypes.POINTER(PfTuning)], i),
+            "pf_set_accumulator": ([vp, vp], i),
+            "pf_reseed": ([vp, ctypes.c_uint64], i),
+            "pf_backward_dca": ([vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp], i),
+            "pf_loss_eq10": ([vp, vp, i, i, vp, ctypes.POINTER(ctypes.c_double), vp], i),
             "pf_profile_read": ([vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_double), i], i),
@@ -254,6 +258,40 @@ def pf_autotune(h, S_init, T_probe) -> dict:
     return dict(kernel=t.kernel, k=t.k, K=t.K, profile=t.profile)
 
 
+def pf_set_accumulator(h, acc):
+    """acc: CUDA FP32 tensor [R][H][W] (kept alive by the caller), or None."""
+    _check(load().pf_set_accumulator(h, _ptr(acc, torch.float32, None, "acc")), h)
+
+
+def pf_reseed(h, seed):
+    _check(load().pf_reseed(h, int(seed) & (2**64 - 1)), h)
+
+
+def pf_backward_dca(h, dL_dacc, step_mask=None, grad_pveg=None, grad_pden=None):
+    """Gradient of a loss of the accumulator; step_mask: host bool/uint8 array over the
+    steps run (None: all). Returns the 4 parameter gradients (p_h, c1, c2, a)."""
+    g4 = (ctypes.c_double * 4)()
+    m = None
+    if step_mask is not None:
+        import numpy as np
+        mk = np.ascontiguousarray(np.asarray(step_mask).astype(np.uint8))
+        m = mk.ctypes.data_as(ctypes.c_void_p)
+    _check(load().pf_backward_dca(h, _ptr(dL_dacc, torch.float32, None, "dL_dacc"), m, g4,
+                                  _ptr(grad_pveg, torch.float32, None, "grad_pveg"),
+                                  _ptr(grad_pden, torch.float32, None, "grad_pden")), h)
+    return list(g4)
+
+
+def pf_loss_eq10(yhat, y, dL_dyhat=None, want_loss=True, stream=None):
+    """Eq. 10 on one map (CUDA FP32 [H][W] tensors); returns the loss (or None)."""
+    H, W = yhat.shape
+    loss = ctypes.c_double(0.0)
+    _check(load().pf_loss_eq10(_ptr(yhat, torch.float32, H * W, "yhat"), _ptr(y, torch.float32, H * W, "y"), H, W,
+                               _ptr(dL_dyhat, torch.float32, H * W, "dL_dyhat"),
+                               ctypes.byref(loss) if want_loss else None, _stream(stream)))
+    return loss.value if want_loss else None
+
+
 def pf_profile_read(h, reset=False) -> dict:
     """{kernel kind: (launches, cell_steps, device ms, skipped cell_steps)} since the last
     reset; skipped = cell-steps of quiescent tiles the blocked kernels did not compute."""
@@ -328,6 +366,23 @@ class FireModel:
 
     def autotune(self, S_init, T_probe=64):
         return pf_autotune(self.h, S_init, T_probe)
+
+    def set_accumulator(self, acc=None):
+        """Attach (or, with None, detach) an FP32 [R][H][W] accumulator tensor; returns it."""
+        self._acc = acc
+        pf_set_accumulator(self.h, acc)
+        return acc
+
+    def reseed(self, seed):
+        pf_reseed(self.h, seed)
+
+    def backward_dca(self, dL_dacc, step_mask=None, per_cell=True):
+        gpv = gpd = None
+        if per_cell:
+            gpv = torch.empty((self.H, self.W), dtype=torch.float32, device="cuda")
+            gpd = torch.empty_like(gpv)
+        g = pf_backward_dca(self.h, dL_dacc, step_mask, gpv, gpd)
+        return g, gpv, gpd
 
     def _out(self):
         if self.form == PF_DISCRETE:

@@ -121,9 +121,20 @@ struct DiscreteArgs {
     int H, W, pitch, R;
     float p_continue;
     uint32_t key0, key1, fire, run0;
+    // accumulator (nullable): dense [R][H][W] FP32; a cell that ignites gets the p_ignite
+    // it ignited with. Kernels write it for cells in rows [acc_r0, acc_r1) and columns
+    // [acc_c0, acc_c1) of the grid they compute exactly once (the launcher sets these).
+    float* acc;
+    int acc_r0, acc_r1, acc_c0, acc_c1;
 };
 void launch_discrete_step(const DiscreteArgs& g, const uint8_t* S, uint8_t* Sn, const float* q,
                           uint32_t step, cudaStream_t s);
+// DCA gradient of one step (the paper's accumulator path): for each cell j that ignites
+// between S (step t) and Sn (t + 1) in any realisation, Gq[d][j] += w_j beta_i
+// prod_{e != d} (1 - beta_e q_ej), beta the burning indicators of S; w dense [R][H][W]
+// (dL/dacc); realisations are summed in a fixed order.
+void launch_dca_step(const DiscreteArgs& g, const uint8_t* S, const uint8_t* Sn, const float* q, const float* w,
+                     float* Gq, cudaStream_t s);
 // temporal-blocked: k <= KH steps per launch from global step `step`; `tin` is a 3-D
 // tensor map over the [R][H][pitch] uint8 input buffer with box {160, TH + 2 KH, 1}.
 int discrete_blocked_tile_rows();

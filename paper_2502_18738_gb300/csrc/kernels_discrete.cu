@@ -23,7 +23,7 @@ __device__ __forceinline__ uint64_t row_burning(uint32_t left, uint32_t mid, uin
 // U/C/D are the burning flags of the rows above / at / below (row_burning layout).
 __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64_t C, uint64_t D, int r,
                                                 int col0, size_t qoff, size_t qplane, const float* __restrict__ q,
-                                                const DiscreteArgs& g, uint32_t run, uint32_t step) {
+                                                const DiscreteArgs& g, uint32_t run, uint32_t step, int rr) {
     const uint64_t all3 = U | C | D;
     const uint64_t nb64 = (all3 << 8) | (all3 >> 8) | U | D;  // neighbours of byte positions 1..4
     const uint32_t nb = (uint32_t)(nb64 >> 8) & 0x01010101u;
@@ -51,6 +51,8 @@ __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64
             }
             const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
             ns = (u24(x.x) < P) ? 2u : 1u;
+            if (ns == 2u && g.acc && r >= g.acc_r0 && r < g.acc_r1 && col >= g.acc_c0 && col < g.acc_c1)
+                g.acc[((size_t)rr * g.H + r) * g.W + col] = P;  // the accumulator (Sec. 2.2 data flow)
         } else {
             const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
             ns = (u24(x.y) < g.p_continue) ? 2u : 3u;
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(256) k_discrete_step(DiscreteArgs g, const uin
     const uint64_t C = row_burning(ld(r, w - 1), mid, ld(r, w + 1));
     const uint64_t D = row_burning(ld(r + 1, w - 1), ld(r + 1, w), ld(r + 1, w + 1));
     const uint32_t out = update_word(mid, U, C, D, r, 4 * w, (size_t)r * g.pitch + 4 * w, (size_t)g.H * g.pitch,
-                                     q, g, g.run0 + (uint32_t)rr, step);
+                                     q, g, g.run0 + (uint32_t)rr, step, rr);
     reinterpret_cast<uint32_t*>(Sn + (size_t)rr * g.H * g.pitch)[(size_t)r * wpr + w] = out;
 }
 
@@ -143,6 +145,12 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
     const size_t qplane = (size_t)g.H * g.pitch;
     uint32_t* src = A;
     uint32_t* dst = B;
+    // the accumulator is written by the tile that owns a cell's interior position
+    DiscreteArgs ga = g;
+    ga.acc_r0 = r0;
+    ga.acc_r1 = r0 + TH;
+    ga.acc_c0 = c0;
+    ga.acc_c1 = c0 + kTW < g.W ? c0 + kTW : g.W;
     if (any_burning) {
         const int y_off = r0 - KH, x_off = c0 - kXH;
         for (int s = 0; s < k; ++s) {
@@ -167,7 +175,8 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
                 // states 1/2 exist only inside the grid, so gr/gc are valid whenever a
                 // cell is active; the q offset is formed but only read for such cells
                 const size_t qoff = (size_t)gr * g.pitch + gc;
-                dst[y * kCW + m] = update_word(mid, U, C, D, gr, gc, qoff, qplane, q, g, g.run0 + (uint32_t)rr, step);
+                dst[y * kCW + m] = update_word(mid, U, C, D, gr, gc, qoff, qplane, q, ga, g.run0 + (uint32_t)rr, step,
+                                               rr);
             }
             __syncthreads();
             uint32_t* t = src; src = dst; dst = t;
@@ -183,6 +192,47 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
         const uint4 val = *reinterpret_cast<const uint4*>(reinterpret_cast<const uint8_t*>(src) + (KH + y) * kCT + kXH + 16 * v);
         *reinterpret_cast<uint4*>(out + (size_t)gr * g.pitch + gc) = val;
     }
+}
+
+// DCA gradient of one step: thread per cell, realisations summed in order (no atomics).
+__global__ void __launch_bounds__(256) k_dca_step(DiscreteArgs g, const uint8_t* __restrict__ S,
+                                                  const uint8_t* __restrict__ Sn, const float* __restrict__ q,
+                                                  const float* __restrict__ w, float* __restrict__ Gq) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t HW = (size_t)g.H * g.W;
+    if (idx >= HW) return;
+    const int r = (int)(idx / g.W), c = (int)(idx % g.W);
+    const size_t plane = (size_t)g.H * g.pitch;
+    const size_t j = (size_t)r * g.pitch + c;
+    float G[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool any = false;
+    for (int rr = 0; rr < g.R; ++rr) {
+        const size_t o = (size_t)rr * plane;
+        if (S[o + j] != 1 || Sn[o + j] != 2) continue;
+        const float wj = __ldg(w + (size_t)rr * HW + idx);
+        if (wj == 0.0f) continue;
+        any = true;
+        float beta[8], f[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int ri = r + dir_dr(d), ci = c + dir_dc(d);
+            beta[d] = (ri >= 0 && ri < g.H && ci >= 0 && ci < g.W && S[o + (size_t)ri * g.pitch + ci] == 2) ? 1.0f : 0.0f;
+            f[d] = fmaf(-beta[d], __ldg(q + d * plane + j), 1.0f);
+        }
+        // leave-one-out products by prefix / suffix (no division: a factor can be 0)
+        float pre[8], suf[8];
+        pre[0] = 1.0f;
+#pragma unroll
+        for (int d = 1; d < 8; ++d) pre[d] = pre[d - 1] * f[d - 1];
+        suf[7] = 1.0f;
+#pragma unroll
+        for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) G[d] = fmaf(wj * beta[d], pre[d] * suf[d], G[d]);
+    }
+    if (!any) return;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) Gq[d * plane + j] += G[d];
 }
 
 __global__ void k_ignition_map_discrete(DiscreteArgs g, const uint8_t* __restrict__ S, const float* __restrict__ q,
@@ -215,6 +265,12 @@ void launch_discrete_step(const DiscreteArgs& g, const uint8_t* S, uint8_t* Sn, 
     const size_t total = (size_t)g.R * g.H * (g.pitch >> 2);
     const unsigned blocks = (unsigned)((total + 255) / 256);
     k_discrete_step<<<blocks, 256, 0, s>>>(g, S, Sn, q, step);
+}
+
+void launch_dca_step(const DiscreteArgs& g, const uint8_t* S, const uint8_t* Sn, const float* q, const float* w,
+                     float* Gq, cudaStream_t s) {
+    const size_t HW = (size_t)g.H * g.W;
+    k_dca_step<<<(unsigned)((HW + 255) / 256), 256, 0, s>>>(g, S, Sn, q, w, Gq);
 }
 
 int discrete_blocked_tile_rows() { return 64; }

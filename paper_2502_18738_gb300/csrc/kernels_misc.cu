@@ -102,7 +102,168 @@ __global__ void k_bce_final(double* partials, int nblk, int64_t n) {
     }
 }
 
+// ------------------------------------------------------------------ Eq. 10
+// Scratch (doubles): [0, nblk) BCE block partials, [nblk, 2 nblk) pooled-MSE block
+// partials, [2 nblk] the loss, then 4 ints: the crop's row / column bounds.
+constexpr int kEqThreads = 256;
+
+__device__ __forceinline__ int* eq10_box(double* scratch, int nblk) {
+    return reinterpret_cast<int*>(scratch + 2 * nblk + 1);
+}
+
+__global__ void k_eq10_init(double* scratch, int nblk, int H, int W) {
+    int* box = eq10_box(scratch, nblk);
+    box[0] = H;   // first row with a non-zero prediction or target
+    box[1] = -1;  // last such row
+    box[2] = W;
+    box[3] = -1;
+}
+
+// crop of the BCE term: bounding box of the union of the non-zero entries
+__global__ void __launch_bounds__(kEqThreads) k_eq10_box(const float* __restrict__ yhat, const float* __restrict__ y,
+                                                         int H, int W, double* scratch, int nblk) {
+    int r0 = H, r1 = -1, c0 = W, c1 = -1;
+    const int64_t n = (int64_t)H * W;
+    for (int64_t i = (int64_t)blockIdx.x * kEqThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kEqThreads) {
+        if (yhat[i] != 0.0f || y[i] != 0.0f) {
+            const int r = (int)(i / W), c = (int)(i % W);
+            r0 = min(r0, r); r1 = max(r1, r); c0 = min(c0, c); c1 = max(c1, c);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        r0 = min(r0, __shfl_down_sync(0xffffffffu, r0, o));
+        r1 = max(r1, __shfl_down_sync(0xffffffffu, r1, o));
+        c0 = min(c0, __shfl_down_sync(0xffffffffu, c0, o));
+        c1 = max(c1, __shfl_down_sync(0xffffffffu, c1, o));
+    }
+    if ((threadIdx.x & 31) == 0 && r1 >= 0) {
+        int* box = eq10_box(scratch, nblk);
+        atomicMin(box + 0, r0); atomicMax(box + 1, r1); atomicMin(box + 2, c0); atomicMax(box + 3, c1);
+    }
+}
+
+// BCE with logits over the crop; dL/dyhat = (sigmoid(x) - y) / N there, 0 elsewhere
+__global__ void __launch_bounds__(kEqThreads) k_eq10_bce(const float* __restrict__ yhat, const float* __restrict__ y,
+                                                         int H, int W, float* __restrict__ g, double* scratch,
+                                                         int nblk) {
+    const int* box = eq10_box(scratch, nblk);
+    const int r0 = box[0], r1 = box[1], c0 = box[2], c1 = box[3];
+    const bool any = r1 >= 0;
+    const int64_t N = any ? (int64_t)(r1 - r0 + 1) * (c1 - c0 + 1) : 1;
+    const float inv_n = (float)(1.0 / (double)N);
+    double acc = 0.0;
+    const int64_t n = (int64_t)H * W;
+    for (int64_t i = (int64_t)blockIdx.x * kEqThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kEqThreads) {
+        const int r = (int)(i / W), c = (int)(i % W);
+        float gi = 0.0f;
+        if (any && r >= r0 && r <= r1 && c >= c0 && c <= c1) {
+            const float x = yhat[i], t = y[i];
+            // -[t log s(x) + (1 - t) log(1 - s(x))] = max(x, 0) - t x + log(1 + exp(-|x|))
+            acc += (double)(fmaxf(x, 0.0f) - t * x + log1pf(expf(-fabsf(x))));
+            const float sg = 1.0f / (1.0f + expf(-x));
+            gi = (sg - t) * inv_n;
+        }
+        if (g) g[i] = gi;
+    }
+    __shared__ double red[kEqThreads / 32];
+    const double v = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kEqThreads / 32; ++w) t += red[w];
+        scratch[blockIdx.x] = t;
+    }
+}
+
+// mean squared difference of the 4 x 4, stride-4 average pools (windows inside the map)
+__global__ void __launch_bounds__(kEqThreads) k_eq10_pool(const float* __restrict__ yhat, const float* __restrict__ y,
+                                                          int H, int W, float* __restrict__ g, double* scratch,
+                                                          int nblk) {
+    const int Hp = H / 4, Wp = W / 4;
+    const int64_t np = (int64_t)Hp * Wp;
+    const float scale = np ? (float)(2.0 / ((double)np * 16.0)) : 0.0f;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kEqThreads + threadIdx.x; i < np; i += (int64_t)gridDim.x * kEqThreads) {
+        const int pr = (int)(i / Wp), pc = (int)(i % Wp);
+        float sx = 0.0f, sy = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int64_t j = (int64_t)(4 * pr + a) * W + 4 * pc + b;
+                sx += yhat[j];
+                sy += y[j];
+            }
+        const float diff = (sx - sy) * (1.0f / 16.0f);
+        acc += (double)diff * (double)diff;
+        if (g) {
+            const float gd = scale * diff;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) g[(int64_t)(4 * pr + a) * W + 4 * pc + b] += gd;
+        }
+    }
+    __shared__ double red[kEqThreads / 32];
+    const double v = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kEqThreads / 32; ++w) t += red[w];
+        scratch[nblk + blockIdx.x] = t;
+    }
+}
+
+// loss = (sum of BCE partials) / N + (sum of pooled partials) / N_pool, fixed order
+__global__ void k_eq10_final(double* scratch, int nblk, int H, int W) {
+    __shared__ double red[2][32];
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        s0 += scratch[b];
+        s1 += scratch[nblk + b];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s0;
+        red[1][threadIdx.x >> 5] = s1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t0 += red[0][w];
+            t1 += red[1][w];
+        }
+        const int* box = eq10_box(scratch, nblk);
+        const double N = box[1] >= 0 ? (double)(box[1] - box[0] + 1) * (double)(box[3] - box[2] + 1) : 1.0;
+        const double np = (double)(H / 4) * (double)(W / 4);
+        scratch[2 * nblk] = (box[1] >= 0 ? t0 / N : 0.0) + (np > 0 ? t1 / np : 0.0);
+    }
+}
+
 }  // namespace
+
+int eq10_blocks(int H, int W) {
+    const int64_t n = (int64_t)H * W;
+    return (int)std::min<int64_t>(std::max<int64_t>((n + kEqThreads - 1) / kEqThreads, 1), 152 * 8);
+}
+
+size_t eq10_scratch_bytes(int H, int W) { return (2 * (size_t)eq10_blocks(H, W) + 1 + 2) * sizeof(double); }
+
+const double* eq10_result(const double* scratch, int nblk) { return scratch + 2 * nblk; }
+
+void launch_eq10(const float* yhat, const float* y, int H, int W, float* g, double* scratch, int nblk,
+                 cudaStream_t s) {
+    k_eq10_init<<<1, 1, 0, s>>>(scratch, nblk, H, W);
+    k_eq10_box<<<nblk, kEqThreads, 0, s>>>(yhat, y, H, W, scratch, nblk);
+    k_eq10_bce<<<nblk, kEqThreads, 0, s>>>(yhat, y, H, W, g, scratch, nblk);
+    k_eq10_pool<<<nblk, kEqThreads, 0, s>>>(yhat, y, H, W, g, scratch, nblk);
+    k_eq10_final<<<1, 1024, 0, s>>>(scratch, nblk, H, W);
+}
 
 void launch_validate_fields(const float* x, size_t n, float lo, int bit, int* flags, cudaStream_t s) {
     unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 8);

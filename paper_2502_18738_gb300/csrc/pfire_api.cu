@@ -20,6 +20,10 @@ void launch_validate_fields(const float* x, size_t n, float lo, int bit, int* fl
 void launch_validate_states(const uint8_t* S, size_t n, int* flags, cudaStream_t s);
 void launch_diff_init(const uint8_t* S, int H, int W, int pitch, float* ab, uint8_t* burn, cudaStream_t s);
 void launch_bce(const float* a, const float* y, int64_t n, float* g, double* partials, int nblk, cudaStream_t s);
+int eq10_blocks(int H, int W);
+size_t eq10_scratch_bytes(int H, int W);
+const double* eq10_result(const double* scratch, int nblk);
+void launch_eq10(const float* yhat, const float* y, int H, int W, float* g, double* scratch, int nblk, cudaStream_t s);
 int bce_blocks(int64_t n);
 }  // namespace pf
 
@@ -30,12 +34,14 @@ namespace {
 thread_local std::string g_last_error = "no error";
 
 enum Kind {
-    K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_ATILES, K_FTILES, K_NKINDS
+    K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_ATILES, K_FTILES, K_DCA,
+    K_NKINDS
 };
 const char* kKindNames[K_NKINDS] = {"prep",         "discrete_step",    "discrete_blocked",
                                     "diff_step",    "diff_blocked",     "adjoint_step",
                                     "adjoint_blocked", "prep_adjoint",  "reduce_fp64",
-                                    "misc",         "adjoint_tiles",    "diff_tiles"};
+                                    "misc",         "adjoint_tiles",    "diff_tiles",
+                                    "dca_step"};
 
 struct Epoch {
     int from;
@@ -82,6 +88,13 @@ struct pf_ctx {
     int step = 0;
     uint8_t* S[2] = {nullptr, nullptr};  // discrete [R][H][P]
     int scur = 0;
+    // the paper's accumulator path (discrete form): caller's accumulator [R][H][W], the
+    // initial state of the recorded trajectory and the context version it was run with
+    float* acc = nullptr;
+    uint8_t* dca_S0 = nullptr;
+    uint8_t* dca_S[2] = {nullptr, nullptr};
+    bool dca_valid = false;
+    long long dca_version = -1;
     float* work[2] = {nullptr, nullptr};  // diff [2][H][P]
     float* cur_ab = nullptr;              // where the current diff state lives
     uint8_t* burn = nullptr;              // diff burnable mask, dense H*W
@@ -188,7 +201,8 @@ struct LaunchScope {
     // steps: automaton steps the launch advances (or reverses) every cell by
     LaunchScope(pf_ctx* c_, int k, int steps = 1) : c(c_), kind(k) {
         c->launches[k] += 1;
-        if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED && k != K_ATILES && k != K_FTILES)
+        if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED && k != K_ATILES && k != K_FTILES &&
+            k != K_DCA)
             c->cell_steps[k] += (long long)steps * c->H * c->W * (k == K_DSTEP || k == K_DBLK ? c->R : 1);
         if (!c->tun.profile) return;
         cudaEvent_t e0 = take();
@@ -388,6 +402,8 @@ DiscreteArgs dargs(const pf_ctx* c) {
     g.p_continue = c->pc;
     g.key0 = (uint32_t)c->seed; g.key1 = (uint32_t)(c->seed >> 32);
     g.fire = 0; g.run0 = 0;
+    g.acc = c->acc;
+    g.acc_r0 = 0; g.acc_r1 = c->H; g.acc_c0 = 0; g.acc_c1 = c->W;
     return g;
 }
 
@@ -597,6 +613,26 @@ int validate_states(pf_ctx* ctx, const uint8_t* S, size_t n) {
 }
 
 }  // namespace
+
+// Start recording a discrete trajectory for the accumulator path: zero the accumulator,
+// keep the initial state (now in S[0]) and the parameters it runs with.
+int dca_record(pf_ctx* ctx) {
+    const size_t sb = (size_t)ctx->R * ctx->H * ctx->P;
+    int rc;
+    for (uint8_t** b : {&ctx->dca_S0, &ctx->dca_S[0], &ctx->dca_S[1]}) {
+        if (*b) continue;
+        void* p;
+        if ((rc = dalloc(ctx, &p, sb))) return rc;
+        *b = (uint8_t*)p;
+    }
+    CK(cudaMemcpyAsync(ctx->dca_S0, ctx->S[0], sb, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemsetAsync(ctx->acc, 0, sb / ctx->P * ctx->W * sizeof(float), ctx->st));
+    ctx->t_p_h = ctx->p_h; ctx->t_c1 = ctx->c1; ctx->t_c2 = ctx->c2; ctx->t_a = ctx->a;
+    ctx->t_pc = ctx->pc; ctx->t_l = ctx->l;
+    ctx->dca_version = ctx->version;
+    ctx->dca_valid = true;
+    return PF_OK;
+}
 
 // =================================================================== C ABI
 extern "C" {
@@ -898,6 +934,7 @@ int pf_forward(pf_ctx* ctx, const uint8_t* S_init, int T, void* S_out) {
         ctx->scur = 0;
         CK(cudaMemcpy2DAsync(ctx->S[0], ctx->P, S_init, ctx->W, ctx->W, (size_t)ctx->R * ctx->H,
                              cudaMemcpyDeviceToDevice, ctx->st));
+        if (ctx->acc && (rc = dca_record(ctx))) return rc;
         rc = run_discrete(ctx, T);
         if (rc) return rc;
         return write_discrete_out(ctx, S_out);
@@ -940,6 +977,7 @@ int pf_set_state(pf_ctx* ctx, int step, const void* S) {
     if (!ctx) return fail(nullptr, PF_EINVAL, "pf_set_state: ctx is NULL");
     if (!S || step < 0) return fail(ctx, PF_EINVAL, "pf_set_state: NULL state or negative step");
     tape_reset(ctx);
+    ctx->dca_valid = false;
     if (ctx->form == PF_DISCRETE) {
         int rc = validate_states(ctx, (const uint8_t*)S, (size_t)ctx->R * ctx->H * ctx->W);
         if (rc) return rc;
@@ -1203,6 +1241,135 @@ int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* l
         CK(cudaMemsetAsync(ctx->dskip, 0, sizeof(skip), ctx->st));
     }
     return n;
+}
+
+int pf_set_accumulator(pf_ctx* ctx, float* acc) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_set_accumulator: ctx is NULL");
+    if (ctx->form != PF_DISCRETE) return fail(ctx, PF_EINVAL, "pf_set_accumulator: the accumulator is of the discrete form");
+    ctx->acc = acc;
+    ctx->dca_valid = false;
+    return PF_OK;
+}
+
+int pf_reseed(pf_ctx* ctx, uint64_t seed) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_reseed: ctx is NULL");
+    ctx->seed = seed;
+    ctx->dca_valid = false;
+    tape_reset(ctx);
+    return PF_OK;
+}
+
+int pf_backward_dca(pf_ctx* ctx, const float* dL_dacc, const uint8_t* step_mask, double grad_params[4],
+                    float* grad_pveg, float* grad_pden) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_backward_dca: ctx is NULL");
+    if (!dL_dacc || !grad_params) return fail(ctx, PF_EINVAL, "pf_backward_dca: NULL dL_dacc or grad_params");
+    if (ctx->form != PF_DISCRETE || !ctx->dca_valid)
+        return fail(ctx, PF_ESTATE, "pf_backward_dca: no trajectory recorded (set an accumulator, then pf_forward)");
+    if (ctx->dca_version != ctx->version)
+        return fail(ctx, PF_ESTATE, "pf_backward_dca: parameters, fields or wind changed since pf_forward");
+    const size_t pe = plane_elems(ctx);
+    const size_t sb = (size_t)ctx->R * pe;
+    int rc;
+    if (!ctx->Gq) {
+        void* p;
+        if ((rc = dalloc(ctx, &p, 8 * pe * sizeof(float)))) return rc;
+        ctx->Gq = (float*)p;
+    }
+    const int nblk = prep_adjoint_blocks(ctx->H, ctx->W);
+    if (!ctx->partials) {
+        void* p;
+        if ((rc = dalloc(ctx, &p, (size_t)nblk * 4 * sizeof(double) + 4 * sizeof(double)))) return rc;
+        ctx->partials = (double*)p;
+        ctx->gacc = ctx->partials + (size_t)nblk * 4;
+    }
+    const size_t cell_bytes = (size_t)ctx->H * ctx->W * sizeof(float);
+    CK(cudaMemsetAsync(ctx->gacc, 0, 4 * sizeof(double), ctx->st));
+    if (grad_pveg) CK(cudaMemsetAsync(grad_pveg, 0, cell_bytes, ctx->st));
+    if (grad_pden) CK(cudaMemsetAsync(grad_pden, 0, cell_bytes, ctx->st));
+    CK(cudaMemsetAsync(ctx->Gq, 0, 8 * pe * sizeof(float), ctx->st));
+    CK(cudaMemcpyAsync(ctx->dca_S[0], ctx->dca_S0, sb, cudaMemcpyDeviceToDevice, ctx->st));
+    DiscreteArgs g = dargs(ctx);
+    g.p_continue = ctx->t_pc;
+    g.acc = nullptr;
+    auto flush = [&](int e) -> int {
+        {
+            LaunchScope ls(ctx, K_PADJ);
+            launch_prep_adjoint(prep_args(ctx, e, true), ctx->Gq, ctx->partials, grad_pveg, grad_pden, ctx->st);
+        }
+        int r = check_launch(ctx, "prep adjoint");
+        if (r) return r;
+        {
+            LaunchScope ls(ctx, K_RED);
+            launch_reduce_partials(ctx->partials, nblk, ctx->gacc, ctx->st);
+        }
+        if ((r = check_launch(ctx, "fp64 reduction"))) return r;
+        if (cudaMemsetAsync(ctx->Gq, 0, 8 * pe * sizeof(float), ctx->st) != cudaSuccess)
+            return fail(ctx, PF_ECUDA, "memset Gq failed");
+        return PF_OK;
+    };
+    // replay the trajectory (same Philox counters) with the plain step; at every attached
+    // step add the gradient of the cells that ignite in it
+    int cur = 0, cur_e = -1;
+    for (int t = 0; t < ctx->step; ++t) {
+        const int e = epoch_of(ctx, t);
+        if (e != cur_e) {
+            if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
+            cur_e = e;
+            {
+                LaunchScope ls(ctx, K_PREP);
+                launch_prep(prep_args(ctx, e, true), ctx->q, ctx->st);
+            }
+            if ((rc = check_launch(ctx, "prep"))) return rc;
+            ctx->q_key_epoch = -1;
+        }
+        {
+            LaunchScope ls(ctx, K_DSTEP);
+            launch_discrete_step(g, ctx->dca_S[cur], ctx->dca_S[1 - cur], ctx->q, (uint32_t)t, ctx->st);
+        }
+        if ((rc = check_launch(ctx, "discrete step (replay)"))) return rc;
+        if (!step_mask || step_mask[t]) {
+            {
+                LaunchScope ls(ctx, K_DCA);
+                launch_dca_step(g, ctx->dca_S[cur], ctx->dca_S[1 - cur], ctx->q, dL_dacc, ctx->Gq, ctx->st);
+            }
+            if ((rc = check_launch(ctx, "dca step"))) return rc;
+        }
+        cur = 1 - cur;
+    }
+    if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
+    CK(cudaMemcpyAsync(ctx->hflags + 4, ctx->gacc, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    std::memcpy(grad_params, ctx->hflags + 4, 4 * sizeof(double));
+    return PF_OK;
+}
+
+int pf_loss_eq10(const float* yhat, const float* y, int H, int W, float* dL_dyhat, double* loss, void* cuda_stream) {
+    if (!yhat || !y || H < 1 || W < 1) return fail(nullptr, PF_EINVAL, "pf_loss_eq10: NULL map or empty grid");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int nblk = eq10_blocks(H, W);
+    static thread_local double* cached = nullptr;
+    static thread_local size_t cached_bytes = 0;
+    const size_t need = eq10_scratch_bytes(H, W);
+    if (cached_bytes < need) {
+        if (cached) cudaFree(cached);
+        if (cudaMalloc((void**)&cached, need) != cudaSuccess) {
+            cudaGetLastError();
+            cached = nullptr;
+            cached_bytes = 0;
+            return fail(nullptr, PF_ENOMEM, "pf_loss_eq10: scratch allocation failed");
+        }
+        cached_bytes = need;
+    }
+    launch_eq10(yhat, y, H, W, dL_dyhat, cached, nblk, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && loss) {
+        double h = 0.0;
+        e = cudaMemcpyAsync(&h, eq10_result(cached, nblk), sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        *loss = h;
+    }
+    if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, "pf_loss_eq10: %s", cudaGetErrorString(e));
+    return PF_OK;
 }
 
 int pf_loss_bce(const float* a, const float* y, int64_t n, float* dL_da, double* loss, void* cuda_stream) {
