@@ -79,6 +79,14 @@ int pf_set_env(pf_ctx* ctx, const float* E, const float* p_veg, const float* p_d
  * until the next epoch. from_step must be > 0 and larger than every earlier epoch's;
  * NULL V_w means calm. The data is copied into the context (8 bytes per cell per
  * epoch). Used to resample the wind during a run and replayed by pf_backward. */
+/* Slope given directly (Sec. 2.1: an H x W x 3 x 3 tensor of the slope from each cell to
+ * its neighbours, degrees): slope_deg device FP32 [H][W][3][3], entry [r][c][dr+1][dc+1]
+ * is Eq. 1's theta_s with E the cell (r, c) and E-hat its neighbour (r+dr, c+dc), i.e.
+ * the slope of spread into (r, c) from that neighbour (the centre entry is unused). It
+ * replaces the slopes derived from E until cleared with NULL. Copied. PF_EINVAL for
+ * NaN / inf. */
+int pf_set_slope(pf_ctx* ctx, const float* slope_deg);
+
 int pf_set_wind(pf_ctx* ctx, const float* V_w, const float* theta_w_deg, int from_step);
 
 /* Model parameters (Sec. 2.1 list; Eq. 2-4): p_h base probability, c1 wind-speed
@@ -237,6 +245,24 @@ int pf_backward_dca(pf_ctx* ctx, const float* dL_dacc, const uint8_t* step_mask,
  * loss: host double or NULL (then the call is asynchronous on cuda_stream). Block
  * partials are reduced in FP64 in a fixed order. */
 int pf_loss_eq10(const float* yhat, const float* y, int H, int W, float* dL_dyhat, double* loss, void* cuda_stream);
+
+/* ----------------------------------------------------------- ensemble metrics */
+
+/* A cell is affected when its state is 2 (burning) or 3 (burned). All maps are device
+ * uint8 state arrays; results are exact integer counts. */
+
+/* Probability of arrival from an ensemble (the paper: "computed using an ensemble of
+ * numerous CA runs ... by averaging these runs"): P_out[j] (device FP32 [H][W]) = the
+ * fraction of the R realisations of S ([R][H][W]) in which cell j is affected. Async. */
+int pf_arrival_probability(const uint8_t* S, int R, int H, int W, float* P_out, void* cuda_stream);
+
+/* Affected cells of each of R maps of HW cells (S [R][HW]) into counts (host, R long
+ * longs): the |A_t| of Eq. 12 for the state at one step. Synchronous. */
+int pf_affected_count(const uint8_t* S, int R, int64_t HW, long long* counts, void* cuda_stream);
+
+/* Jaccard index of Eq. 11 between the affected sets of two maps of n cells:
+ * |A and B| / |A or B|, 1 when both are empty. *out: host double. Synchronous. */
+int pf_jaccard(const uint8_t* A, const uint8_t* B, int64_t n, double* out, void* cuda_stream);
 
 /* ----------------------------------------------------------- batched fires */
 

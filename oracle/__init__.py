@@ -67,7 +67,7 @@ def _load():
         lib.orc_philox4x32_10.argtypes = [P_U32, P_U32, P_U32]
         lib.orc_cell_draws.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                        ctypes.c_uint32, ctypes.c_uint32, P_D, P_D]
-        lib.orc_prep.argtypes = [ctypes.c_int, ctypes.c_int, P_F, P_F, P_F, P_F, P_F, P_U8,
+        lib.orc_prep.argtypes = [ctypes.c_int, ctypes.c_int, P_F, P_F, P_F, P_F, P_F, P_F, P_U8,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_double, P_D]
         lib.orc_step_discrete.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P_U8, P_U8, P_D,
@@ -80,7 +80,7 @@ def _load():
                                       P_D, P_D, P_D]
         lib.orc_adjoint_step.argtypes = [ctypes.c_int, ctypes.c_int, P_D, P_D, P_D, ctypes.c_double,
                                          P_D, P_D, P_D, P_D, P_D]
-        lib.orc_prep_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, P_F, P_F, P_F, P_F, P_F, P_U8,
+        lib.orc_prep_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, P_F, P_F, P_F, P_F, P_F, P_F, P_U8,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, P_D, P_D, P_D, P_D]
         lib.orc_num_threads.restype = ctypes.c_int
@@ -149,12 +149,13 @@ class Params:
         return Params(**d)
 
 
-def prep(H, W, E, p_veg, p_den, V, theta, prm: Params, burnable=None, exact_params=False):
-    """q[8, H, W] (FP64): f_p(p_propagate) into cell j from its neighbour in direction d."""
-    E, p_veg, p_den, V, theta = map(_f32, (E, p_veg, p_den, V, theta))
+def prep(H, W, E, p_veg, p_den, V, theta, prm: Params, burnable=None, exact_params=False, slope=None):
+    """q[8, H, W] (FP64): f_p(p_propagate) into cell j from its neighbour in direction d.
+    slope: the H x W x 3 x 3 slope input in degrees (Sec. 2.1), used instead of E."""
+    E, p_veg, p_den, V, theta, slope = map(_f32, (E, p_veg, p_den, V, theta, slope))
     burnable = _u8(burnable)
     q = np.zeros((8, H, W), dtype=np.float64)
-    _load().orc_prep(H, W, _ptr(E, P_F), _ptr(p_veg, P_F), _ptr(p_den, P_F), _ptr(V, P_F),
+    _load().orc_prep(H, W, _ptr(E, P_F), _ptr(slope, P_F), _ptr(p_veg, P_F), _ptr(p_den, P_F), _ptr(V, P_F),
                      _ptr(theta, P_F), _ptr(burnable, P_U8), prm.p_h, prm.c1, prm.c2, prm.a, prm.l,
                      _ptr(q, P_D))
     return q
@@ -237,14 +238,14 @@ def adjoint_step(a, b, q, p_continue, la1, lb1, Gq):
     return la0, lb0
 
 
-def prep_adjoint(H, W, E, p_veg, p_den, V, theta, prm: Params, Gq, burnable=None):
-    E, p_veg, p_den, V, theta = map(_f32, (E, p_veg, p_den, V, theta))
+def prep_adjoint(H, W, E, p_veg, p_den, V, theta, prm: Params, Gq, burnable=None, slope=None):
+    E, p_veg, p_den, V, theta, slope = map(_f32, (E, p_veg, p_den, V, theta, slope))
     burnable = _u8(burnable)
     g4 = np.zeros(4)
     gpv = np.zeros((H, W))
     gpd = np.zeros((H, W))
     Gq = _f64(Gq)
-    _load().orc_prep_adjoint(H, W, _ptr(E, P_F), _ptr(p_veg, P_F), _ptr(p_den, P_F), _ptr(V, P_F),
+    _load().orc_prep_adjoint(H, W, _ptr(E, P_F), _ptr(slope, P_F), _ptr(p_veg, P_F), _ptr(p_den, P_F), _ptr(V, P_F),
                              _ptr(theta, P_F), _ptr(burnable, P_U8), prm.p_h, prm.c1, prm.c2, prm.a,
                              prm.l, _ptr(Gq, P_D), _ptr(g4, P_D), _ptr(gpv, P_D), _ptr(gpd, P_D))
     return g4, gpv, gpd

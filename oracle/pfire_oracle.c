@@ -89,15 +89,22 @@ static double orc_rad(double deg) { return deg * (M_PI / 180.0); }
 
 /* Per-direction factors of one (j, d) pair, following Eq. 1-4. Returns 0 when the
  * neighbour i is outside the grid. */
-static int orc_factors(int H, int W, int r, int c, int d, const float* E, const float* V,
+/* slope: the H x W x 3 x 3 input of Sec. 2.1 (degrees, [r][c][dr+1][dc+1], Eq. 1 with E
+ * the cell and E-hat its neighbour) when given, else Eq. 1 from the altitude map E */
+static int orc_factors(int H, int W, int r, int c, int d, const float* E, const float* slope, const float* V,
                        const float* th, double c1, double c2, double a, double l,
                        double* pw, double* ps, double* theta_s, double* cos_m1, double* Vj) {
     int ri = r + ORC_DR[d], ci = c + ORC_DC[d];
     if (ri < 0 || ri >= H || ci < 0 || ci >= W) return 0;
     size_t j = (size_t)r * W + c, i = (size_t)ri * W + ci;
-    double k = (ORC_DR[d] != 0 && ORC_DC[d] != 0) ? sqrt(2.0) : 1.0;   /* Eq. 1 */
-    double dE = E ? ((double)E[j] - (double)E[i]) : 0.0;
-    double ts = orc_deg(atan(dE / (k * l)));                              /* Eq. 1, degrees */
+    double ts;
+    if (slope) {
+        ts = (double)slope[j * 9 + (size_t)(ORC_DR[d] + 1) * 3 + (size_t)(ORC_DC[d] + 1)];
+    } else {
+        double k = (ORC_DR[d] != 0 && ORC_DC[d] != 0) ? sqrt(2.0) : 1.0;   /* Eq. 1 */
+        double dE = E ? ((double)E[j] - (double)E[i]) : 0.0;
+        ts = orc_deg(atan(dE / (k * l)));                                   /* Eq. 1, degrees */
+    }
     double v = V ? (double)V[j] : 0.0;
     double phi = orc_deg(atan2((double)ORC_DR[d], (double)(-ORC_DC[d])));
     double theta = (th ? (double)th[j] : 0.0) - phi;
@@ -111,7 +118,7 @@ static int orc_factors(int H, int W, int r, int c, int d, const float* E, const 
 }
 
 /* q[d][j] = f_p(p_propagate) for the burning neighbour in direction d of cell j. */
-void orc_prep(int H, int W, const float* E, const float* p_veg, const float* p_den,
+void orc_prep(int H, int W, const float* E, const float* slope, const float* p_veg, const float* p_den,
               const float* V, const float* th, const uint8_t* burnable, double p_h, double c1,
               double c2, double a, double l, double* q) {
     size_t HW = (size_t)H * W;
@@ -124,7 +131,7 @@ void orc_prep(int H, int W, const float* E, const float* p_veg, const float* p_d
             for (int d = 0; d < 8; ++d) {
                 double pw, ps, ts, cm1, v;
                 double qq = 0.0;
-                if (orc_factors(H, W, r, c, d, E, V, th, c1, c2, a, l, &pw, &ps, &ts, &cm1, &v)) {
+                if (orc_factors(H, W, r, c, d, E, slope, V, th, c1, c2, a, l, &pw, &ps, &ts, &cm1, &v)) {
                     double pp = p_h * (1.0 + pv) * (1.0 + pd) * pw * ps;          /* Eq. 2 */
                     qq = tanh(ORC_C_FP * pp);                                      /* Eq. 5 */
                 }
@@ -275,7 +282,7 @@ void orc_adjoint_step(int H, int W, const double* a, const double* b, const doub
 
 /* Chain rule of orc_prep. Gq = dL/dq (8*H*W). grad4 (accumulated) = dL/d(p_h, c1, c2, a);
  * g_pveg, g_pden (nullable, H*W, accumulated) = per-cell gradients. */
-void orc_prep_adjoint(int H, int W, const float* E, const float* p_veg, const float* p_den,
+void orc_prep_adjoint(int H, int W, const float* E, const float* slope, const float* p_veg, const float* p_den,
                       const float* V, const float* th, const uint8_t* burnable, double p_h, double c1,
                       double c2, double a, double l, const double* Gq, double grad4[4], double* g_pveg,
                       double* g_pden) {
@@ -289,7 +296,7 @@ void orc_prep_adjoint(int H, int W, const float* E, const float* p_veg, const fl
             double pd = p_den ? (double)p_den[j] : 0.0;
             for (int d = 0; d < 8; ++d) {
                 double pw, ps, ts, cm1, v;
-                if (!orc_factors(H, W, r, c, d, E, V, th, c1, c2, a, l, &pw, &ps, &ts, &cm1, &v)) continue;
+                if (!orc_factors(H, W, r, c, d, E, slope, V, th, c1, c2, a, l, &pw, &ps, &ts, &cm1, &v)) continue;
                 double pp = p_h * (1.0 + pv) * (1.0 + pd) * pw * ps;
                 double qq = tanh(ORC_C_FP * pp);
                 double gpp = Gq[(size_t)d * HW + j] * ORC_C_FP * (1.0 - qq * qq);  /* tanh' */

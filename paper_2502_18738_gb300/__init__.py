@@ -25,6 +25,8 @@ __all__ = [
     "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
     "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_profile_read", "pf_batch_submit", "pf_last_error",
     "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
+    "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10", "pf_arrival_probability",
+    "pf_affected_count", "pf_jaccard", "manhattan", "pf_set_slope",
     "EXPORTED_SYMBOLS",
 ]
 
@@ -41,6 +43,7 @@ EXPORTED_SYMBOLS = [
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
     "pf_loss_bce_noalloc", "pf_autotune", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
+    "pf_arrival_probability", "pf_affected_count", "pf_jaccard", "pf_set_slope",
 ]
 PF_NOALLOC_BCE_MAX_N = 67108864
 
@@ -105,6 +108,10 @@ def load():
             "pf_reseed": ([vp, ctypes.c_uint64], i),
             "pf_backward_dca": ([vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp], i),
             "pf_loss_eq10": ([vp, vp, i, i, vp, ctypes.POINTER(ctypes.c_double), vp], i),
+            "pf_arrival_probability": ([vp, i, i, i, vp, vp], i),
+            "pf_set_slope": ([vp, vp], i),
+            "pf_affected_count": ([vp, i, ctypes.c_int64, ctypes.POINTER(ctypes.c_longlong), vp], i),
+            "pf_jaccard": ([vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp], i),
             "pf_profile_read": ([vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_double), i], i),
@@ -173,6 +180,11 @@ def pf_set_env(h, H, W, E=None, p_veg=None, p_den=None, V_w=None, theta_w=None):
     f = torch.float32
     _check(load().pf_set_env(h, _ptr(E, f, n, "E"), _ptr(p_veg, f, n, "p_veg"), _ptr(p_den, f, n, "p_den"),
                              _ptr(V_w, f, n, "V_w"), _ptr(theta_w, f, n, "theta_w")), h)
+
+
+def pf_set_slope(h, H, W, slope_deg):
+    """slope_deg: CUDA FP32 [H][W][3][3] (degrees) or None to use the altitude map again."""
+    _check(load().pf_set_slope(h, _ptr(slope_deg, torch.float32, H * W * 9, "slope")), h)
 
 
 def pf_set_wind(h, H, W, V_w, theta_w, from_step):
@@ -292,6 +304,37 @@ def pf_loss_eq10(yhat, y, dL_dyhat=None, want_loss=True, stream=None):
     return loss.value if want_loss else None
 
 
+def pf_arrival_probability(S, P_out=None, stream=None):
+    """S: CUDA uint8 [R][H][W]; returns FP32 [H][W] fraction of realisations affected."""
+    R, H, W = S.shape
+    P_out = torch.empty((H, W), dtype=torch.float32, device="cuda") if P_out is None else P_out
+    _check(load().pf_arrival_probability(_ptr(S, torch.uint8, R * H * W, "S"), R, H, W,
+                                         _ptr(P_out, torch.float32, H * W, "P_out"), _stream(stream)))
+    return P_out
+
+
+def pf_affected_count(S, stream=None):
+    """S: CUDA uint8 [R][...]; returns a list of R affected-cell counts."""
+    R = S.shape[0]
+    n = S.numel() // R
+    out = (ctypes.c_longlong * R)()
+    _check(load().pf_affected_count(_ptr(S, torch.uint8, None, "S"), R, n, out, _stream(stream)))
+    return [int(v) for v in out]
+
+
+def pf_jaccard(A, B, stream=None):
+    """Eq. 11 between the affected sets of two CUDA uint8 state maps of equal size."""
+    out = ctypes.c_double(0.0)
+    _check(load().pf_jaccard(_ptr(A, torch.uint8, None, "A"), _ptr(B, torch.uint8, A.numel(), "B"), A.numel(),
+                             ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def manhattan(counts_a, counts_b):
+    """Eq. 12 from two series of affected-cell counts (pf_affected_count per step)."""
+    return int(sum(abs(int(x) - int(y)) for x, y in zip(counts_a, counts_b)))
+
+
 def pf_profile_read(h, reset=False) -> dict:
     """{kernel kind: (launches, cell_steps, device ms, skipped cell_steps)} since the last
     reset; skipped = cell-steps of quiescent tiles the blocked kernels did not compute."""
@@ -357,6 +400,9 @@ class FireModel:
 
     def set_wind(self, V_w, theta_w, from_step):
         pf_set_wind(self.h, self.H, self.W, V_w, theta_w, from_step)
+
+    def set_slope(self, slope_deg=None):
+        pf_set_slope(self.h, self.H, self.W, slope_deg)
 
     def set_params(self, p_h, c1, c2, a, p_continue, l=30.0):
         pf_set_params(self.h, p_h, c1, c2, a, p_continue, l)

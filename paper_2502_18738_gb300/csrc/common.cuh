@@ -100,6 +100,7 @@ struct PrepArgs {
     int H, W, pitch;
     const float *E, *pveg, *pden, *V, *th;  // dense H*W, nullable
     const uint8_t* burnable;                 // dense H*W, nullable
+    const float* slope;                      // dense [H][W][3][3] degrees (replaces E), nullable
     float p_h, c1, c2, a, l;
     // derived on the host in FP64 and split into hi + lo floats:
     // a * 180/pi, 1/l and 1/(sqrt(2) l)

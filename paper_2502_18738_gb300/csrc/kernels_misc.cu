@@ -245,7 +245,60 @@ __global__ void k_eq10_final(double* scratch, int nblk, int H, int W) {
     }
 }
 
+// ------------------------------------------------------- ensemble metrics
+__device__ __forceinline__ bool affected(uint8_t s) { return s == 2 || s == 3; }
+
+// probability of arrival: the fraction of realisations in which the cell burned or burns
+__global__ void k_arrival(const uint8_t* __restrict__ S, int R, int64_t HW, float* __restrict__ P) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < HW; j += (int64_t)gridDim.x * blockDim.x) {
+        int n = 0;
+        for (int r = 0; r < R; ++r) n += affected(S[(int64_t)r * HW + j]);
+        P[j] = (float)n / (float)R;  // correctly rounded quotient of the count
+    }
+}
+
+// integer counts: out[0] += |affected(A) and affected(B)|, out[1] += |either|; or, with
+// B == nullptr, out[r] += affected cells of realisation r (blockIdx.y = r)
+__global__ void k_count(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B, int64_t n,
+                        unsigned long long* __restrict__ out) {
+    unsigned long long c0 = 0, c1 = 0;
+    const uint8_t* a = A + (B ? 0 : (int64_t)blockIdx.y * n);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const bool x = affected(a[j]);
+        if (B) {
+            const bool y = affected(B[j]);
+            c0 += (x && y);
+            c1 += (x || y);
+        } else {
+            c0 += x;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_down_sync(0xffffffffu, c0, o);
+        c1 += __shfl_down_sync(0xffffffffu, c1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (B) {
+            if (c0) atomicAdd(out + 0, c0);
+            if (c1) atomicAdd(out + 1, c1);
+        } else if (c0) {
+            atomicAdd(out + blockIdx.y, c0);
+        }
+    }
+}
+
 }  // namespace
+
+void launch_arrival(const uint8_t* S, int R, int64_t HW, float* P, cudaStream_t s) {
+    const int blocks = (int)std::min<int64_t>(std::max<int64_t>((HW + 255) / 256, 1), 152 * 8);
+    k_arrival<<<blocks, 256, 0, s>>>(S, R, HW, P);
+}
+
+void launch_count(const uint8_t* A, const uint8_t* B, int64_t n, int R, unsigned long long* out, cudaStream_t s) {
+    const int blocks = (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 4);
+    k_count<<<dim3(blocks, B ? 1 : R), 256, 0, s>>>(A, B, n, out);
+}
 
 int eq10_blocks(int H, int W) {
     const int64_t n = (int64_t)H * W;

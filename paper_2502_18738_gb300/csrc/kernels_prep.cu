@@ -94,15 +94,23 @@ __device__ __forceinline__ bool dir_exponent(const PrepArgs& g, const CellFactor
                                              float& expo, float& theta_s, float& cosm1) {
     const int ri = r + dir_dr(d), ci = c + dir_dc(d);
     if (ri < 0 || ri >= g.H || ci < 0 || ci >= g.W) return false;
-    float dE = 0.0f;
-    if (g.E) dE = f.Ej - g.E[(size_t)ri * g.W + ci];
-    const bool diag = (dir_dr(d) != 0) && (dir_dc(d) != 0);
-    const float x = diag ? df_times(dE, g.ikl_d_hi, g.ikl_d_lo) : df_times(dE, g.ikl_e_hi, g.ikl_e_lo);
-    const float t = atanf(x);                                           // Eq. 1, radians
-    theta_s = t * kRadToDeg;
     cosm1 = cos_rel(d, f.cw, f.sw) - 1.0f;
-    // Eq. 3 x Eq. 4 exponent: c1 V + c2 V (cos - 1) + a theta_s(deg), a*180/pi as hi + lo
-    expo = fmaf(g.c2 * f.V, cosm1, fmaf(g.c1, f.V, df_times(t, g.adeg_hi, g.adeg_lo)));
+    float slope_term;
+    if (g.slope) {
+        // the H x W x 3 x 3 slope input (Sec. 2.1), degrees, [r][c][dr+1][dc+1]
+        theta_s = g.slope[((size_t)r * g.W + c) * 9 + (dir_dr(d) + 1) * 3 + (dir_dc(d) + 1)];
+        slope_term = g.a * theta_s;
+    } else {
+        float dE = 0.0f;
+        if (g.E) dE = f.Ej - g.E[(size_t)ri * g.W + ci];
+        const bool diag = (dir_dr(d) != 0) && (dir_dc(d) != 0);
+        const float x = diag ? df_times(dE, g.ikl_d_hi, g.ikl_d_lo) : df_times(dE, g.ikl_e_hi, g.ikl_e_lo);
+        const float t = atanf(x);                                       // Eq. 1, radians
+        theta_s = t * kRadToDeg;
+        slope_term = df_times(t, g.adeg_hi, g.adeg_lo);                 // a theta_s(deg), a*180/pi as hi + lo
+    }
+    // Eq. 3 x Eq. 4 exponent: c1 V + c2 V (cos - 1) + a theta_s
+    expo = fmaf(g.c2 * f.V, cosm1, fmaf(g.c1, f.V, slope_term));
     return true;
 }
 

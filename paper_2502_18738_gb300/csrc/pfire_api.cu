@@ -20,6 +20,8 @@ void launch_validate_fields(const float* x, size_t n, float lo, int bit, int* fl
 void launch_validate_states(const uint8_t* S, size_t n, int* flags, cudaStream_t s);
 void launch_diff_init(const uint8_t* S, int H, int W, int pitch, float* ab, uint8_t* burn, cudaStream_t s);
 void launch_bce(const float* a, const float* y, int64_t n, float* g, double* partials, int nblk, cudaStream_t s);
+void launch_arrival(const uint8_t* S, int R, int64_t HW, float* P, cudaStream_t s);
+void launch_count(const uint8_t* A, const uint8_t* B, int64_t n, int R, unsigned long long* out, cudaStream_t s);
 int eq10_blocks(int H, int W);
 size_t eq10_scratch_bytes(int H, int W);
 const double* eq10_result(const double* scratch, int nblk);
@@ -91,6 +93,7 @@ struct pf_ctx {
     // the paper's accumulator path (discrete form): caller's accumulator [R][H][W], the
     // initial state of the recorded trajectory and the context version it was run with
     float* acc = nullptr;
+    float* slope = nullptr;  // H x W x 3 x 3 slope input (degrees), replaces E when set
     uint8_t* dca_S0 = nullptr;
     uint8_t* dca_S[2] = {nullptr, nullptr};
     bool dca_valid = false;
@@ -300,11 +303,12 @@ int next_epoch_start(const pf_ctx* c, int t) {
 }
 
 PrepArgs prep_args(const pf_ctx* c, int e, bool use_tape_params) {
-    PrepArgs g;
+    PrepArgs g{};
     g.H = c->H; g.W = c->W; g.pitch = c->P;
     g.E = c->E; g.pveg = c->pveg; g.pden = c->pden;
     g.V = c->winds[e].V; g.th = c->winds[e].th;
     g.burnable = (c->form == PF_DIFF) ? c->burn : nullptr;
+    g.slope = c->slope;
     if (use_tape_params) {
         g.p_h = c->t_p_h; g.c1 = c->t_c1; g.c2 = c->t_c2; g.a = c->t_a; g.l = c->t_l;
     } else {
@@ -812,6 +816,35 @@ int pf_set_env(pf_ctx* ctx, const float* E, const float* p_veg, const float* p_d
     ctx->winds.resize(1);
     if ((rc = copy_field(ctx, &ctx->winds[0].V, V_w))) return rc;
     if ((rc = copy_field(ctx, &ctx->winds[0].th, theta_w_deg))) return rc;
+    ctx->version++;
+    tape_reset(ctx);
+    return PF_OK;
+}
+
+int pf_set_slope(pf_ctx* ctx, const float* slope_deg) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_set_slope: ctx is NULL");
+    if (!slope_deg) {
+        if (ctx->slope) dfree(ctx, ctx->slope);
+        ctx->slope = nullptr;
+    } else {
+        const size_t n = (size_t)ctx->H * ctx->W * 9;
+        CK(cudaMemsetAsync(ctx->dflags + 1, 0, sizeof(int), ctx->st));
+        {
+            LaunchScope ls(ctx, K_MISC);
+            launch_validate_fields(slope_deg, n, -INFINITY, 0, ctx->dflags + 1, ctx->st);
+        }
+        int rc = check_launch(ctx, "validate slope");
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(ctx->hflags + 1, ctx->dflags + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if (ctx->hflags[1]) return fail(ctx, PF_EINVAL, "pf_set_slope: NaN or infinite slope values");
+        if (!ctx->slope) {
+            void* p;
+            if ((rc = dalloc(ctx, &p, n * sizeof(float)))) return rc;
+            ctx->slope = (float*)p;
+        }
+        CK(cudaMemcpyAsync(ctx->slope, slope_deg, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+    }
     ctx->version++;
     tape_reset(ctx);
     return PF_OK;
@@ -1343,6 +1376,69 @@ int pf_backward_dca(pf_ctx* ctx, const float* dL_dacc, const uint8_t* step_mask,
     return PF_OK;
 }
 
+int pf_arrival_probability(const uint8_t* S, int R, int H, int W, float* P_out, void* cuda_stream) {
+    if (!S || !P_out || R < 1 || H < 1 || W < 1) return fail(nullptr, PF_EINVAL, "pf_arrival_probability: bad arguments");
+    launch_arrival(S, R, (int64_t)H * W, P_out, (cudaStream_t)cuda_stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, "pf_arrival_probability: %s", cudaGetErrorString(e));
+    return PF_OK;
+}
+
+// device scratch of the counting entry points: one small buffer per thread
+static unsigned long long* count_scratch(int n, int* rc) {
+    static thread_local unsigned long long* buf = nullptr;
+    static thread_local int cap = 0;
+    *rc = PF_OK;
+    if (cap < n) {
+        if (buf) cudaFree(buf);
+        buf = nullptr;
+        cap = 0;
+        if (cudaMalloc((void**)&buf, sizeof(unsigned long long) * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            *rc = PF_ENOMEM;
+            return nullptr;
+        }
+        cap = n;
+    }
+    return buf;
+}
+
+int pf_affected_count(const uint8_t* S, int R, int64_t HW, long long* counts, void* cuda_stream) {
+    if (!S || !counts || R < 1 || HW < 1) return fail(nullptr, PF_EINVAL, "pf_affected_count: bad arguments");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc;
+    unsigned long long* d = count_scratch(R, &rc);
+    if (!d) return fail(nullptr, rc, "pf_affected_count: scratch allocation failed");
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * R, st);
+    if (e == cudaSuccess) {
+        launch_count(S, nullptr, HW, R, d, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d, sizeof(long long) * R, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, "pf_affected_count: %s", cudaGetErrorString(e));
+    return PF_OK;
+}
+
+int pf_jaccard(const uint8_t* A, const uint8_t* B, int64_t n, double* out, void* cuda_stream) {
+    if (!A || !B || !out || n < 1) return fail(nullptr, PF_EINVAL, "pf_jaccard: bad arguments");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc;
+    unsigned long long* d = count_scratch(2, &rc);
+    if (!d) return fail(nullptr, rc, "pf_jaccard: scratch allocation failed");
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(h), st);
+    if (e == cudaSuccess) {
+        launch_count(A, B, n, 1, d, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, "pf_jaccard: %s", cudaGetErrorString(e));
+    *out = h[1] ? (double)h[0] / (double)h[1] : 1.0;
+    return PF_OK;
+}
+
 int pf_loss_eq10(const float* yhat, const float* y, int H, int W, float* dL_dyhat, double* loss, void* cuda_stream) {
     if (!yhat || !y || H < 1 || W < 1) return fail(nullptr, PF_EINVAL, "pf_loss_eq10: NULL map or empty grid");
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -1557,7 +1653,7 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
         } else {
             launch_diff_init(J.S_init, J.H, J.W, L.P, (float*)(arena + L.st), mask, cs);
         }
-        PrepArgs g;
+        PrepArgs g{};
         g.H = J.H; g.W = J.W; g.pitch = L.P;
         g.E = J.E; g.pveg = J.p_veg; g.pden = J.p_den; g.V = J.V_w; g.th = J.theta_w;
         g.burnable = J.form == PF_DIFF ? mask : nullptr;

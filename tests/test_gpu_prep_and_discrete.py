@@ -165,3 +165,31 @@ def test_invalid_inputs_are_rejected(pf, orc):
     with pytest.raises(pf.PFireError) as e:
         m.backward()
     assert e.value.code == pf.PF_ESTATE
+
+
+def test_slope_tensor_input_matches_oracle(pf, orc):
+    """pf_set_slope (the H x W x 3 x 3 slope input, degrees) replaces the slopes derived
+    from E: q read through lattice ignition maps equals the oracle's prep with the same
+    slope tensor; clearing it returns to the altitude path."""
+    H, W = 41, 37
+    m, land, V, th, prm, q_E = _setup(pf, orc, H, W, seed=12)
+    rng = np.random.default_rng(5)
+    slope = rng.uniform(-25, 25, (H, W, 3, 3)).astype(np.float32)
+    m.set_slope(cuda(slope))
+    q = orc.prep(H, W, None, land.p_veg, land.p_den, V, th, prm, slope=slope)
+    for rho in range(3):
+        for gam in range(3):
+            S, on = lattice_state(H, W, rho, gam)
+            m.set_state(0, cuda(S))
+            P = m.ignition_map()[0].cpu().numpy().astype(np.float64)
+            d = lattice_direction(H, W, rho, gam)
+            rr, cc = np.nonzero(~on)
+            want = q[d[rr, cc], rr, cc]
+            assert np.all(np.abs(P[rr, cc] - want) <= 2e-6 * np.abs(want) + 1e-7), (rho, gam)
+    m.set_slope(None)
+    S, on = lattice_state(H, W, 0, 0)
+    m.set_state(0, cuda(S))
+    P = m.ignition_map()[0].cpu().numpy().astype(np.float64)
+    d = lattice_direction(H, W, 0, 0)
+    rr, cc = np.nonzero(~on)
+    assert np.all(np.abs(P[rr, cc] - q_E[d[rr, cc], rr, cc]) <= 2e-6 * q_E[d[rr, cc], rr, cc] + 1e-7)

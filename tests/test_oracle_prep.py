@@ -118,3 +118,41 @@ def test_constant_c_reproduces_its_design():
     r6 = minimize_scalar(lambda c: np.sum((1 - c ** (-x) - x) ** 2), bounds=(1.01, 50), method="bounded")
     r7 = minimize_scalar(lambda c: np.sum((1 - (x + 1) ** (-c) - x) ** 2), bounds=(0.01, 10), method="bounded")
     assert res.fun < r6.fun and res.fun < r7.fun
+
+
+def test_slope_tensor_input_reproduces_the_altitude_path(orc):
+    """The H x W x 3 x 3 slope input of Sec. 2.1 ([r][c][dr+1][dc+1], degrees, Eq. 1 with E
+    the cell and E-hat the neighbour) in place of E: fed the angles of an altitude map it
+    gives the same q; all-zero slopes give flat ground; one angle moves only its q."""
+    import numpy as np
+    import synthetic as syn
+    H, W = 13, 11
+    land = syn.make_landscape(H, W, 2)
+    V, th = syn.uniform_wind(H, W, 4.0, 30.0)
+    prm = orc.Params(0.58, 0.045, 0.131, 0.078, 0.3)
+    E = land.E.astype(np.float64)
+    slope = np.zeros((H, W, 3, 3), np.float32)
+    for dr in (-1, 0, 1):
+        for dc in (-1, 0, 1):
+            if dr == dc == 0:
+                continue
+            k = np.sqrt(2.0) if dr and dc else 1.0
+            nb = np.zeros_like(E)
+            rs, re_ = max(0, -dr), H - max(0, dr)
+            cs, ce = max(0, -dc), W - max(0, dc)
+            nb[rs:re_, cs:ce] = E[rs + dr:re_ + dr, cs + dc:ce + dc]
+            slope[:, :, dr + 1, dc + 1] = np.degrees(np.arctan((E - nb) / (k * 30.0)))
+    q_E = orc.prep(H, W, land.E, land.p_veg, land.p_den, V, th, prm)
+    q_s = orc.prep(H, W, None, land.p_veg, land.p_den, V, th, prm, slope=slope)
+    assert np.allclose(q_s, q_E, rtol=2e-6, atol=0)  # the angles went through FP32
+    flat = orc.prep(H, W, None, land.p_veg, land.p_den, V, th, prm)
+    assert np.array_equal(orc.prep(H, W, None, land.p_veg, land.p_den, V, th, prm,
+                                   slope=np.zeros((H, W, 3, 3), np.float32)), flat)
+    one = np.zeros((H, W, 3, 3), np.float32)
+    one[6, 5, 0, 2] = 20.0  # cell (6, 5), neighbour (5, 6): direction d = 2
+    q1 = orc.prep(H, W, None, land.p_veg, land.p_den, V, th, prm, slope=one)
+    diff = np.argwhere(q1 != flat)
+    assert [tuple(x) for x in diff] == [(2, 6, 5)]
+    # Eq. 4: the slope factor exp(a theta_s) multiplies p_propagate inside f_p = tanh(c x)
+    x_flat = np.arctanh(flat[2, 6, 5]) / orc.C_FP
+    assert np.arctanh(q1[2, 6, 5]) / orc.C_FP == pytest.approx(x_flat * np.exp(prm.a * 20.0), rel=1e-12)
