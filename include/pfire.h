@@ -280,11 +280,23 @@ typedef struct pf_job {
     float p_h, c1, c2, a, p_continue, l;
     const uint8_t* S_init;
     void* S_out;
+    /* differentiable jobs only (all NULL: forward only). dL_da: device FP32 [H][W], the
+     * gradient of a loss with respect to a_T; then grad_params (device double[4],
+     * required) receives dL/d(p_h, c1, c2, a) and grad_pveg / grad_pden (device FP32
+     * [H][W], nullable) the per-cell gradients, as pf_backward computes them. Every state
+     * of such a job is kept on the device during the submission ((T + 1) x 8 B per cell). */
+    const float* dL_da;
+    double* grad_params;
+    float *grad_pveg, *grad_pden;
 } pf_job;
 
 /* Run n independent fires of uneven sizes and step counts (each as pf_forward would,
  * bit-identically for the discrete form) from one device work queue in a persistent
- * kernel. Synchronous. Returns PF_ETIMEOUT if a bounded device-side wait ran out. */
+ * kernel, then, for the differentiable jobs that carry dL_da, their reverse-time adjoint
+ * from a second work queue (block by block from each job's last step), and the
+ * parameter and per-cell gradients; the whole submission is one captured CUDA graph.
+ * Synchronous. PF_ETIMEOUT if a bounded device-side wait ran out, PF_ENOMEM if the
+ * states of the differentiable jobs with an adjoint do not fit. */
 int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream);
 
 /* Message of the last failure on ctx (or of the last context-free call when ctx is

@@ -65,7 +65,9 @@ class PfJob(ctypes.Structure):
                 ("V_w", ctypes.c_void_p), ("theta_w", ctypes.c_void_p),
                 ("p_h", ctypes.c_float), ("c1", ctypes.c_float), ("c2", ctypes.c_float), ("a", ctypes.c_float),
                 ("p_continue", ctypes.c_float), ("l", ctypes.c_float),
-                ("S_init", ctypes.c_void_p), ("S_out", ctypes.c_void_p)]
+                ("S_init", ctypes.c_void_p), ("S_out", ctypes.c_void_p),
+                ("dL_da", ctypes.c_void_p), ("grad_params", ctypes.c_void_p),
+                ("grad_pveg", ctypes.c_void_p), ("grad_pden", ctypes.c_void_p)]
 
 
 _lib = None
@@ -351,7 +353,8 @@ def pf_profile_read(h, reset=False) -> dict:
 
 
 def make_job(S_init, T, S_out=None, form=PF_DISCRETE, seed=0, run=0, fire_id=0, E=None, p_veg=None, p_den=None,
-             V_w=None, theta_w=None, p_h=0.58, c1=0.045, c2=0.131, a=0.078, p_continue=0.3, l=30.0):
+             V_w=None, theta_w=None, p_h=0.58, c1=0.045, c2=0.131, a=0.078, p_continue=0.3, l=30.0,
+             dL_da=None, grad_params=None, grad_pveg=None, grad_pden=None):
     """A PfJob over CUDA tensors (S_init uint8 [H][W]); allocates S_out if not given
     (uint8 [H][W] discrete, FP32 [2][H][W] differentiable). Returns (job, S_out); the job
     keeps references to every tensor it points into."""
@@ -370,7 +373,14 @@ def make_job(S_init, T, S_out=None, form=PF_DISCRETE, seed=0, run=0, fire_id=0, 
     j.S_init = _ptr(S_init, torch.uint8, n, "S_init").value
     j.S_out = _ptr(S_out, torch.uint8 if form == PF_DISCRETE else torch.float32,
                    n * (1 if form == PF_DISCRETE else 2), "S_out").value
-    j._keep = (S_init, S_out, E, p_veg, p_den, V_w, theta_w)  # the struct holds raw pointers into these
+    if dL_da is not None and grad_params is None:
+        grad_params = torch.zeros(4, dtype=torch.float64, device="cuda")
+    for name, t, dt, nn in (("dL_da", dL_da, torch.float32, n), ("grad_params", grad_params, torch.float64, 4),
+                            ("grad_pveg", grad_pveg, torch.float32, n), ("grad_pden", grad_pden, torch.float32, n)):
+        p = _ptr(t, dt, nn, name)
+        setattr(j, name, p.value if p is not None else None)
+    j._keep = (S_init, S_out, E, p_veg, p_den, V_w, theta_w, dL_da, grad_params, grad_pveg, grad_pden)
+    j.grads = grad_params  # device double[4] (p_h, c1, c2, a) after pf_batch_submit, or None
     return j, S_out
 
 

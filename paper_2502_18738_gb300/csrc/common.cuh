@@ -215,6 +215,14 @@ struct BatchJobDev {
     const float* q;
     int* gen;
     void* out;
+    // differentiable jobs with an adjoint: every state [T+1][2][H][P] (the forward writes
+    // it), the scaled adjoint ping-pong at block boundaries and dL/dq [8][H][P]
+    float* tape;
+    float* lam[2];
+    uint8_t* sig[2];
+    float* Gq;
+    int* gen_b;  // backward tile generations
+    int btiles_x, btiles_y;
 };
 struct BatchPlan {
     const BatchJobDev* jobs;
@@ -233,5 +241,12 @@ int batch_tile_cols();
 int batch_steps_per_item();
 int batch_blocks_per_sm();
 void launch_batch(const BatchPlan& plan, int grid, cudaStream_t s);
+// reverse-time adjoint of the differentiable jobs with a tape: plan items are (job,
+// backward tile, block counted from the job's last block)
+int batch_adj_tile_rows();
+int batch_adj_tile_cols();
+int batch_adj_blocks_per_sm();
+int batch_adj_configure();
+void launch_batch_adj(const BatchPlan& plan, int grid, cudaStream_t s);
 
 }  // namespace pf

@@ -185,6 +185,15 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
                 }
                 __syncthreads();
                 cur ^= 1;
+                if (J.tape) {  // the state at step0 + s + 1 of the interior, for the adjoint
+                    float* o = J.tape + (size_t)(step0 + s + 1) * 2 * plane;
+                    for (int i = tid; i < kTR * kTC; i += kBThreads) {
+                        const int y = kB + i / kTC, x = kB + i % kTC, gr = r0 + y, gc = c0 + x;
+                        if (gr >= J.H || gc >= J.W) continue;
+                        o[(size_t)gr * J.P + gc] = sA[0][y][x];
+                        o[plane + (size_t)gr * J.P + gc] = sB[cur][y][x];
+                    }
+                }
             }
             for (int i = tid; i < kTR * kTC; i += kBThreads) {
                 const int y = kB + i / kTC, x = kB + i % kTC, gr = r0 + y, gc = c0 + x;
@@ -211,6 +220,180 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
     }
 }
 
+// ------------------------------------------------------------------ adjoint
+// Work item (job, backward tile, rb): the adjoint of the job's block b = nblk - 1 - rb,
+// steps t = t1 - 1 .. t0 (the same blocks as the forward), over a 16 x 32 interior with
+// a 5-cell halo: per step the valid region shrinks by one cell, and the targets' own
+// lambda at t + 1 must be valid one ring beyond the sources. lambda at t1 (scaled form,
+// common.cuh) is read from the job's ping-pong buffer (b + 1) % 2 and lambda at t0 is
+// written to b % 2; the item starts once the 3 x 3 neighbouring tiles have finished
+// rb - 1 (so their lambda at t1 is there and they no longer read buffer b % 2).
+// dL/dq of the interior is accumulated in the job's Gq (the tile's items run one after
+// another, so the read-modify-write has no concurrent writer). Each step is the
+// arithmetic of k_adjoint_step.
+constexpr int kAR = 16, kAC = 32, kAH = kB + 1;
+constexpr int kARR = kAR + 2 * kAH, kARC = kAC + 2 * kAH;  // 26 x 42
+constexpr int kAThreads = 256;
+
+struct AdjSmem {
+    float mua[kARR][kARC], mub[kARR][kARC];  // scaled lambda (mu) at t + 1, then at t
+    float sa[kARR][kARC], sb[kARR][kARC];    // state (A, b) at t
+    float su[kARR][kARC];                    // 2^-sigma(t)
+    float sc[8][kARR][kARC];                 // contributions of targets, in source units
+    uint8_t sg[kARR][kARC];                  // sigma at t + 1, then at t
+};
+
+__global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
+    extern __shared__ __align__(16) uint8_t adj_raw[];
+    AdjSmem& sm = *reinterpret_cast<AdjSmem*>(adj_raw);
+    __shared__ long long s_item;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = (*(volatile int*)plan.err) ? plan.total : (long long)atomicAdd(plan.counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= plan.total) return;
+        const int rb = upper_bound_ll(plan.blk_start, plan.max_blk + 1, item) - 1;
+        const long long r = item - plan.blk_start[rb];
+        const int j = upper_bound_ll(plan.tile_pref, plan.jobs_in_blk[rb] + 1, r) - 1;
+        const int tile = (int)(r - plan.tile_pref[j]);
+        const BatchJobDev& J = plan.jobs[j];
+        const int ty = tile / J.btiles_x, tx = tile % J.btiles_x;
+        const int r0 = ty * kAR - kAH, c0 = tx * kAC - kAH;
+        if (tid == 0) {
+            int ok = 1;
+            for (int dy = -1; dy <= 1 && ok; ++dy)
+                for (int dx = -1; dx <= 1 && ok; ++dx) {
+                    const int yy = ty + dy, xx = tx + dx;
+                    if (yy < 0 || yy >= J.btiles_y || xx < 0 || xx >= J.btiles_x) continue;
+                    const volatile int* g = J.gen_b + yy * J.btiles_x + xx;
+                    if (*g >= rb) continue;
+                    const unsigned long long tw = global_ns();
+                    while (*g < rb) {
+                        if (global_ns() - tw > (unsigned long long)plan.wait_limit_ns || *(volatile int*)plan.err) {
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                }
+            __threadfence();
+            s_ok = ok;
+            if (!ok) atomicCAS(plan.err, 0, kErrBatchTimeout);
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const int b = J.nblk - 1 - rb;
+        const int t0 = b * kB, t1 = min(J.T, t0 + kB);
+        const size_t plane = (size_t)J.H * J.P;
+        // lambda at t1 over the whole region
+        {
+            const float* lin = J.lam[(b + 1) & 1];
+            const uint8_t* sin_ = J.sig[(b + 1) & 1];
+            for (int i = tid; i < kARR * kARC; i += kAThreads) {
+                const int y = i / kARC, x = i % kARC, gr = r0 + y, gc = c0 + x;
+                const bool in = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
+                const size_t g = (size_t)gr * J.P + gc;
+                sm.mua[y][x] = in ? __ldcg(lin + g) : 0.0f;
+                sm.mub[y][x] = in ? __ldcg(lin + plane + g) : 0.0f;
+                sm.sg[y][x] = in ? __ldcg(sin_ + g) : (uint8_t)kSigmaZero;
+            }
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            const float* st = J.tape + (size_t)t * 2 * plane;
+            for (int i = tid; i < kARR * kARC; i += kAThreads) {
+                const int y = i / kARC, x = i % kARC, gr = r0 + y, gc = c0 + x;
+                const bool in = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
+                const size_t g = (size_t)gr * J.P + gc;
+                const float A = in ? __ldcg(st + g) : 0.0f;
+                sm.sa[y][x] = A;
+                sm.sb[y][x] = in ? __ldcg(st + plane + g) : 0.0f;
+                sm.su[y][x] = in ? adj_unit_inv(A) : 1.0f;
+            }
+            __syncthreads();
+            // targets j: contributions to their sources and, in the interior, dL/dq
+            for (int i = tid; i < (kARR - 2) * (kARC - 2); i += kAThreads) {
+                const int y = 1 + i / (kARC - 2), x = 1 + i % (kARC - 2), gr = r0 + y, gc = c0 + x;
+                const int sgp = sm.sg[y][x];
+                if (sgp == kSigmaZero || gr < 0 || gr >= J.H || gc < 0 || gc >= J.W) {
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) sm.sc[d][y][x] = 0.0f;
+                    continue;
+                }
+                const size_t g = (size_t)gr * J.P + gc;
+                const float Up = adj_unit(sgp);
+                float qd[8], bi[8], f[8];
+                float P = 0.0f, S = 1.0f;
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    qd[d] = __ldg(J.q + d * plane + g);
+                    bi[d] = sm.sb[y + dir_dr(d)][x + dir_dc(d)];
+                    const float xx = bi[d] * qd[d];
+                    f[d] = 1.0f - xx;
+                    ign_acc(xx, P, S);
+                }
+                float pre[8], suf[8];
+                pre[0] = 1.0f;
+#pragma unroll
+                for (int d = 1; d < 8; ++d) pre[d] = pre[d - 1] * f[d - 1];
+                suf[7] = 1.0f;
+#pragma unroll
+                for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
+                const float la = sm.mua[y][x], lb = sm.mub[y][x];
+                const float ln = la + lb;
+                float av, ua;
+                a_decode(sm.sa[y][x], av, ua);
+                const float tg = ln * ua;
+                const bool interior = y >= kAH && y < kAH + kAR && x >= kAH && x < kAH + kAC;
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    const float tt = tg * (pre[d] * suf[d]);
+                    const float r_d = Up * sm.su[y + dir_dr(d)][x + dir_dc(d)];
+                    sm.sc[d][y][x] = tt * qd[d] * r_d;
+                    if (interior) J.Gq[d * plane + g] = fmaf(tt, bi[d] * Up, J.Gq[d * plane + g]);
+                }
+                sm.mua[y][x] = (la - ln * P) * (Up * sm.su[y][x]);  // own cell: in place
+            }
+            __syncthreads();
+            // sources i: lambda_b at t, and the masks of cells with a = 0
+            for (int i = tid; i < (kARR - 4) * (kARC - 4); i += kAThreads) {
+                const int y = 2 + i / (kARC - 4), x = 2 + i % (kARC - 4), gr = r0 + y, gc = c0 + x;
+                const bool in = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
+                const int sgp = sm.sg[y][x];
+                const int sgt = in ? adj_sigma(sm.sa[y][x]) : kSigmaZero;
+                float acc = 0.0f;
+                if (sgp != kSigmaZero) acc = J.pc * sm.mub[y][x] * (adj_unit(sgp) * sm.su[y][x]);
+#pragma unroll
+                for (int d = 0; d < 8; ++d) acc += sm.sc[d][y - dir_dr(d)][x - dir_dc(d)];
+                if (sgt == kSigmaZero || sgp == kSigmaZero) {
+                    acc = 0.0f;
+                    sm.mua[y][x] = 0.0f;
+                }
+                sm.mub[y][x] = acc;
+                sm.sg[y][x] = (uint8_t)sgt;
+            }
+            __syncthreads();
+        }
+        // lambda at t0 of the interior
+        {
+            float* lo = J.lam[b & 1];
+            uint8_t* so = J.sig[b & 1];
+            for (int i = tid; i < kAR * kAC; i += kAThreads) {
+                const int y = kAH + i / kAC, x = kAH + i % kAC, gr = r0 + y, gc = c0 + x;
+                if (gr >= J.H || gc >= J.W) continue;
+                const size_t g = (size_t)gr * J.P + gc;
+                lo[g] = sm.mua[y][x];
+                lo[plane + g] = sm.mub[y][x];
+                so[g] = sm.sg[y][x];
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicExch(J.gen_b + tile, rb + 1);
+    }
+}
+
 }  // namespace
 
 int batch_tile_rows() { return kTR; }
@@ -219,6 +402,31 @@ int batch_steps_per_item() { return kB; }
 
 void launch_batch(const BatchPlan& plan, int grid, cudaStream_t s) {
     k_batch<<<grid, kBThreads, 0, s>>>(plan);
+}
+
+int batch_adj_tile_rows() { return kAR; }
+int batch_adj_tile_cols() { return kAC; }
+
+int batch_adj_configure() {
+    static int done = 0;
+    if (!done) {
+        if (cudaFuncSetAttribute(k_batch_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(AdjSmem)) !=
+            cudaSuccess)
+            return -1;
+        done = 1;
+    }
+    return 0;
+}
+
+int batch_adj_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_adj, kAThreads, sizeof(AdjSmem)) != cudaSuccess)
+        nb = 1;
+    return nb > 0 ? nb : 1;
+}
+
+void launch_batch_adj(const BatchPlan& plan, int grid, cudaStream_t s) {
+    k_batch_adj<<<grid, kAThreads, sizeof(AdjSmem), s>>>(plan);
 }
 
 int batch_blocks_per_sm() {

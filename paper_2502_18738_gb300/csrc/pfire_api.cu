@@ -1515,6 +1515,8 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
             if (!std::isfinite(x)) return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: non-finite parameter", i);
         if (J.p_h < 0 || J.p_continue < 0 || J.p_continue > 1 || !(J.l > 0))
             return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: parameter out of range", i);
+        if (J.dL_da && (J.form != PF_DIFF || !J.grad_params))
+            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: dL_da needs the differentiable form and grad_params", i);
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // order jobs by block count, descending (block-major item order)
@@ -1526,7 +1528,14 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
     }
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nblk[x] > nblk[y]; });
     // one arena: per job two state buffers, q, a burnable mask and tile counters
-    struct Lay { size_t st, q, mask, gen, stbytes; int P, tx, ty; };
+    struct Lay {
+        size_t st, q, mask, gen, stbytes;
+        int P, tx, ty;
+        bool adj;  // differentiable job with an adjoint
+        size_t tape, lam, sig, gq, genb;
+        int btx, bty;
+    };
+    const int kAR = batch_adj_tile_rows(), kAC = batch_adj_tile_cols();
     std::vector<Lay> lay(n);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
@@ -1542,7 +1551,34 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
         L.q = take(8 * plane * sizeof(float));
         L.mask = take((size_t)J.H * J.W);
         L.gen = take((size_t)L.tx * L.ty * sizeof(int));
+        L.adj = J.dL_da != nullptr;
+        if (L.adj) {
+            L.btx = (J.W + kAC - 1) / kAC;
+            L.bty = (J.H + kAR - 1) / kAR;
+            L.tape = take((size_t)(J.T + 1) * 2 * plane * sizeof(float));
+            L.lam = take(2 * 2 * plane * sizeof(float));
+            L.sig = take(2 * plane);
+            L.gq = take(8 * plane * sizeof(float));
+            L.genb = take((size_t)L.btx * L.bty * sizeof(int));
+        }
     }
+    // backward: the adjoint jobs in the same (block count, descending) order
+    std::vector<int> ab;  // positions in `order`
+    for (int k = 0; k < n; ++k)
+        if (lay[k].adj) ab.push_back(k);
+    const int nb = (int)ab.size();
+    const int max_blk_b = nb ? nblk[order[ab[0]]] : 0;
+    std::vector<long long> tile_pref_b(nb + 1, 0), blk_start_b(max_blk_b + 1, 0);
+    std::vector<int> jobs_in_blk_b(std::max(1, max_blk_b), 0);
+    for (int k = 0; k < nb; ++k) tile_pref_b[k + 1] = tile_pref_b[k] + (long long)lay[ab[k]].btx * lay[ab[k]].bty;
+    for (int b = 0; b < max_blk_b; ++b) {
+        int m = 0;
+        while (m < nb && nblk[order[ab[m]]] > b) ++m;
+        jobs_in_blk_b[b] = m;
+        blk_start_b[b + 1] = blk_start_b[b] + tile_pref_b[m];
+    }
+    int nblk_prep = 1;
+    for (int k : ab) nblk_prep = std::max(nblk_prep, prep_adjoint_blocks(jobs[order[k]].H, jobs[order[k]].W));
     const int max_blk = nblk[order[0]];
     std::vector<long long> tile_pref(n + 1, 0), blk_start(max_blk + 1, 0);
     std::vector<int> jobs_in_blk(max_blk, 0);
@@ -1559,6 +1595,12 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
     const size_t o_jb = take(sizeof(int) * max_blk);
     const size_t o_ctl = take(sizeof(unsigned long long) + sizeof(int) * 4);
     const size_t o_vf = take(sizeof(int) * n);  // per-job input validation flags
+    const size_t o_jobs_b = take(sizeof(BatchJobDev) * std::max(1, nb));
+    const size_t o_bs_b = take(sizeof(long long) * (max_blk_b + 1));
+    const size_t o_tp_b = take(sizeof(long long) * (nb + 1));
+    const size_t o_jb_b = take(sizeof(int) * std::max(1, max_blk_b));
+    const size_t o_ctl_b = take(sizeof(unsigned long long));
+    const size_t o_part = take(sizeof(double) * 4 * (size_t)nblk_prep);
     char* arena = nullptr;
     if (cudaMalloc((void**)&arena, off) != cudaSuccess) {
         cudaGetLastError();
@@ -1578,7 +1620,27 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
         D.q = (const float*)(arena + L.q);
         D.gen = (int*)(arena + L.gen);
         D.out = J.S_out;
+        D.tape = nullptr;
+        D.lam[0] = D.lam[1] = nullptr;
+        D.sig[0] = D.sig[1] = nullptr;
+        D.Gq = nullptr;
+        D.gen_b = nullptr;
+        D.btiles_x = D.btiles_y = 0;
+        if (L.adj) {
+            const size_t plane = (size_t)J.H * L.P;
+            D.tape = (float*)(arena + L.tape);
+            D.lam[0] = (float*)(arena + L.lam);
+            D.lam[1] = D.lam[0] + 2 * plane;
+            D.sig[0] = (uint8_t*)(arena + L.sig);
+            D.sig[1] = D.sig[0] + plane;
+            D.Gq = (float*)(arena + L.gq);
+            D.gen_b = (int*)(arena + L.genb);
+            D.btiles_x = L.btx;
+            D.btiles_y = L.bty;
+        }
     }
+    std::vector<BatchJobDev> hjb(std::max(1, nb));
+    for (int k = 0; k < nb; ++k) hjb[k] = hj[ab[k]];
     unsigned long long* counter = (unsigned long long*)(arena + o_ctl);
     int* derr = (int*)(arena + o_ctl + sizeof(unsigned long long));
     int rc = PF_OK;
@@ -1599,6 +1661,15 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
     plan.err = derr;
     plan.wait_limit_ns = sl ? std::max(1000ll, atoll(sl)) : 4000000000ll;  // 4 s
     plan.withhold = wh ? atoi(wh) : 0;
+    BatchPlan plan_b = plan;
+    plan_b.jobs = (const BatchJobDev*)(arena + o_jobs_b);
+    plan_b.blk_start = (const long long*)(arena + o_bs_b);
+    plan_b.tile_pref = (const long long*)(arena + o_tp_b);
+    plan_b.jobs_in_blk = (const int*)(arena + o_jb_b);
+    plan_b.max_blk = max_blk_b;
+    plan_b.total = blk_start_b[max_blk_b];
+    plan_b.counter = (unsigned long long*)(arena + o_ctl_b);
+    plan_b.withhold = 0;
     int nsm = 152, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = nsm * batch_blocks_per_sm();
@@ -1632,6 +1703,14 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaMemcpy(arena + o_bs, blk_start.data(), sizeof(long long) * (max_blk + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(arena + o_tp, tile_pref.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(arena + o_jb, jobs_in_blk.data(), sizeof(int) * max_blk, cudaMemcpyHostToDevice);
+    if (nb) {
+        if (e == cudaSuccess) e = cudaMemcpy(arena + o_jobs_b, hjb.data(), sizeof(BatchJobDev) * nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(arena + o_bs_b, blk_start_b.data(), sizeof(long long) * (max_blk_b + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(arena + o_tp_b, tile_pref_b.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(arena + o_jb_b, jobs_in_blk_b.data(), sizeof(int) * max_blk_b, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && batch_adj_configure() != 0) e = cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess) goto cuda_fail;
     // the whole submission (initial states, prep of every fire, the persistent kernel)
     // is captured into one CUDA graph and launched once
@@ -1660,8 +1739,44 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
         g.p_h = J.p_h; g.c1 = J.c1; g.c2 = J.c2; g.a = J.a; g.l = J.l;
         prep_derive(g);
         launch_prep(g, (float*)(arena + L.q), cs);
+        if (L.adj) {
+            const size_t plane = (size_t)J.H * L.P;
+            cudaMemcpyAsync(arena + L.tape, arena + L.st, 2 * plane * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+            cudaMemsetAsync(arena + L.gq, 0, 8 * plane * sizeof(float), cs);
+            cudaMemsetAsync(arena + L.genb, 0, (size_t)L.btx * L.bty * sizeof(int), cs);
+        }
     }
     launch_batch(plan, grid, cs);
+    if (nb) {
+        // terminal adjoint of each job from dL/da_T and its state at T, then the
+        // backward work queue, then each job's chain rule of prep and FP64 reduction
+        cudaMemsetAsync(arena + o_ctl_b, 0, sizeof(unsigned long long), cs);
+        for (int k : ab) {
+            const pf_job& J = jobs[order[k]];
+            const BatchJobDev& D = hj[k];
+            const size_t plane = (size_t)J.H * lay[k].P;
+            const int z = D.nblk & 1;
+            launch_adjoint_init(J.dL_da, nullptr, D.tape + (size_t)J.T * 2 * plane, J.H, J.W, lay[k].P, D.lam[z],
+                                D.sig[z], cs);
+        }
+        launch_batch_adj(plan_b, nsm * batch_adj_blocks_per_sm(), cs);
+        for (int k : ab) {
+            const pf_job& J = jobs[order[k]];
+            const Lay& L = lay[k];
+            PrepArgs g{};
+            g.H = J.H; g.W = J.W; g.pitch = L.P;
+            g.E = J.E; g.pveg = J.p_veg; g.pden = J.p_den; g.V = J.V_w; g.th = J.theta_w;
+            g.burnable = (uint8_t*)(arena + L.mask);
+            g.p_h = J.p_h; g.c1 = J.c1; g.c2 = J.c2; g.a = J.a; g.l = J.l;
+            prep_derive(g);
+            cudaMemsetAsync(J.grad_params, 0, 4 * sizeof(double), cs);
+            if (J.grad_pveg) cudaMemsetAsync(J.grad_pveg, 0, (size_t)J.H * J.W * sizeof(float), cs);
+            if (J.grad_pden) cudaMemsetAsync(J.grad_pden, 0, (size_t)J.H * J.W * sizeof(float), cs);
+            const int npb = prep_adjoint_blocks(J.H, J.W);
+            launch_prep_adjoint(g, hj[k].Gq, (double*)(arena + o_part), J.grad_pveg, J.grad_pden, cs);
+            launch_reduce_partials((double*)(arena + o_part), npb, J.grad_params, cs);
+        }
+    }
     e = cudaStreamEndCapture(cs, &graph);
     if (e != cudaSuccess) goto cuda_fail;
     e = cudaGraphInstantiate(&exec, graph, 0);

@@ -190,3 +190,44 @@ def test_bounded_wait_times_out_and_library_stays_usable(pf, monkeypatch):
     set_landscape(m, land, V, th)
     m.set_params(**PRM)
     assert np.array_equal(out.cpu().numpy(), m.forward(cuda(S0), T).cpu().numpy()[0])
+
+
+def test_batched_adjoint_matches_per_fire_backward_and_oracle(pf, orc):
+    """Differentiable jobs with dL/da_T in a submit that also holds discrete fires: the
+    batched adjoint (reverse-time work queue) gives the gradients a per-fire context
+    computes with the plain kernels, and the oracle's."""
+    import torch
+    prm = orc.Params(**PRM)
+    shapes = [(45, 77, 37), (100, 70, 23), (33, 40, 0), (64, 64, 4), (90, 130, 30)]
+    jobs, keep = [], []
+    for i, (H, W, T) in enumerate(shapes):
+        land, V, th, S0 = _fire(H, W, 400 + i)
+        w = torch.from_numpy(np.random.default_rng(i).standard_normal((H, W)).astype(np.float32) * 1e-2).cuda()
+        gpv = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        gpd = torch.empty_like(gpv)
+        j, out = _job(pf, land, V, th, S0, T, 1, dL_da=w, grad_pveg=gpv, grad_pden=gpd)
+        jobs.append(j)
+        keep.append((land, V, th, S0, T, w, j, gpv, gpd))
+        jd, _ = _job(pf, land, V, th, S0, T + 3, 0, seed=2, fire_id=i)
+        jobs.append(jd)
+    pf.pf_batch_submit(jobs)
+    for land, V, th, S0, T, w, j, gpv, gpd in keep:
+        H, W = S0.shape
+        g4 = j.grads.cpu().numpy()
+        m = pf.FireModel(H, W, 1, 1)
+        set_landscape(m, land, V, th)
+        m.set_params(**PRM)
+        m.set_tuning(kernel=1, K=1)
+        m.forward(cuda(S0), T)
+        r4, rpv, rpd = m.backward(w, None)
+        m.close()
+        assert np.allclose(g4, r4, rtol=1e-6, atol=1e-12), (T, g4, r4)
+        assert np.allclose(gpv.cpu().numpy(), rpv.cpu().numpy(), rtol=1e-5, atol=1e-9)
+        if T == 0:
+            assert not g4.any()
+            continue
+        a, b, tape = orc.diff_forward(land, [(V, th)], [0], prm, S0, T)
+        want4, wpv, _ = orc.diff_backward(land, [(V, th)], [0], prm, S0, tape, w.cpu().numpy().astype(np.float64),
+                                          np.zeros((H, W)))
+        for k in range(4):
+            assert g4[k] == pytest.approx(want4[k], rel=1e-3, abs=1e-9)
