@@ -203,9 +203,10 @@ def discrete_ensemble(pf, torch, timed, seed=1, N=1024, R=64, T=1000):
 
 def batched_fires(pf, torch, timed, n_fires=64, seed=4):
     """Uneven fires (side log-uniform in [64, 2048], T uniform in [100, 1000], 1-5
-    ignitions, half discrete / half differentiable) through one pf_batch_submit, against
-    the same fires run one after another through per-fire contexts with the plain
-    per-step kernels; cell-updates/s over sum(side^2 T)."""
+    ignitions, half discrete / half differentiable, the latter with an adjoint) through
+    one pf_batch_submit, against the same fires run one after another through per-fire
+    contexts with the plain per-step kernels; cell-updates/s over sum(side^2 T), the
+    differentiable fires counted twice (forward and adjoint)."""
     rng = np.random.default_rng(seed)
     fires = []
     for i in range(n_fires):
@@ -218,9 +219,12 @@ def batched_fires(pf, torch, timed, n_fires=64, seed=4):
     c = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
     dev = [(side, T, form, c(land.E), c(land.p_veg), c(land.p_den), c(V), c(th), c(S0))
            for side, T, form, land, V, th, S0 in fires]
-    cells = sum(side * side * T for side, T, *_ in fires)
+    # forward cell-steps of every fire plus the adjoint's of the differentiable ones
+    cells = sum(side * side * T * (2 if form == 1 else 1) for side, T, form, *_ in fires)
+    wts = [torch.full((side, side), 1e-6, dtype=torch.float32, device="cuda") if form == 1 else None
+           for side, T, form, *_ in fires]
     jobs = [pf.make_job(S0, T, form=form, seed=seed, fire_id=i, E=E, p_veg=pv, p_den=pd, V_w=V, theta_w=th,
-                        **PARAMS)[0] for i, (side, T, form, E, pv, pd, V, th, S0) in enumerate(dev)]
+                        dL_da=wts[i], **PARAMS)[0] for i, (side, T, form, E, pv, pd, V, th, S0) in enumerate(dev)]
     pf.pf_batch_submit(jobs)  # warm-up
     ms_batch = timed(lambda: pf.pf_batch_submit(jobs), 1)
 
@@ -231,10 +235,13 @@ def batched_fires(pf, torch, timed, n_fires=64, seed=4):
             m.set_params(**PARAMS)
             m.set_tuning(kernel=1)
             m.forward(S0, T)
+            if form == 1:
+                m.backward(wts[i], None, per_cell=False)
             m.close()
     ms_plain = timed(plain_all, 1)
     return {"config": f"{n_fires} fires, side log-uniform [64, 2048], T uniform [100, 1000], "
-                      "half discrete / half differentiable, forward", "unit": "cell-updates/s",
+                      "half discrete / half differentiable, forward + adjoint of the differentiable ones",
+            "unit": "cell-updates/s",
             "cell_steps": cells, "batched": cells / (ms_batch / 1000.0), "plain_per_fire": cells / (ms_plain / 1000.0),
             "speedup": ms_plain / ms_batch}
 

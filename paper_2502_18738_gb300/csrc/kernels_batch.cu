@@ -118,15 +118,18 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
         const size_t plane = (size_t)J.H * J.P;
         if (J.form == 0) {  // discrete
             const uint8_t* in = (const uint8_t*)J.st[b & 1];
+            bool burning = false;
             for (int i = tid; i < kRR * kRC; i += kBThreads) {
                 const int y = i / kRC, x = i % kRC, gr = r0 + y, gc = c0 + x;
                 const uint8_t v = (gr >= 0 && gr < J.H && gc >= 0 && gc < J.W) ? __ldcg(in + (size_t)gr * J.P + gc) : 0;
                 s8[0][y][x] = v;
                 s8[1][y][x] = v;
+                burning |= v == 2;
             }
-            __syncthreads();
+            // nothing burns in the region: no cell can change during the item's steps
+            const int nsteps = __syncthreads_or(burning) ? steps : 0;
             int cur = 0;
-            for (int s = 0; s < steps; ++s) {
+            for (int s = 0; s < nsteps; ++s) {
                 for (int i = tid; i < (kRR - 2) * (kRC - 2); i += kBThreads) {
                     const int y = 1 + i / (kRC - 2), x = 1 + i % (kRC - 2), gr = r0 + y, gc = c0 + x;
                     const uint8_t sv = s8[cur][y][x];
@@ -152,6 +155,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
             }
         } else {
             const float* in = (const float*)J.st[b & 1];
+            bool burning = false;
             for (int i = tid; i < kRR * kRC; i += kBThreads) {
                 const int y = i / kRC, x = i % kRC, gr = r0 + y, gc = c0 + x;
                 const bool inside = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
@@ -160,31 +164,35 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
                 const float bv = inside ? __ldcg(in + plane + g) : 0.0f;
                 sB[0][y][x] = bv;
                 sB[1][y][x] = bv;
+                burning |= bv != 0.0f;
             }
-            __syncthreads();
+            // b = 0 in the whole region: every P is 0, the state does not change
+            const bool live = __syncthreads_or(burning);
             int cur = 0;
             for (int s = 0; s < steps; ++s) {
-                for (int i = tid; i < (kRR - 2) * (kRC - 2); i += kBThreads) {
-                    const int y = 1 + i / (kRC - 2), x = 1 + i % (kRC - 2), gr = r0 + y, gc = c0 + x;
-                    float bnew = sB[cur][y][x];
-                    if (gr >= 0 && gr < J.H && gc >= 0 && gc < J.W) {
-                        const size_t qoff = (size_t)gr * J.P + gc;
-                        float P = 0.0f, S = 1.0f;
+                if (live) {
+                    for (int i = tid; i < (kRR - 2) * (kRC - 2); i += kBThreads) {
+                        const int y = 1 + i / (kRC - 2), x = 1 + i % (kRC - 2), gr = r0 + y, gc = c0 + x;
+                        float bnew = sB[cur][y][x];
+                        if (gr >= 0 && gr < J.H && gc >= 0 && gc < J.W) {
+                            const size_t qoff = (size_t)gr * J.P + gc;
+                            float P = 0.0f, S = 1.0f;
 #pragma unroll
-                        for (int d = 0; d < 8; ++d) {
-                            const float xx = sB[cur][y + dir_dr(d)][x + dir_dc(d)] * __ldg(J.q + d * plane + qoff);
-                            ign_acc(xx, P, S);
+                            for (int d = 0; d < 8; ++d) {
+                                const float xx = sB[cur][y + dir_dr(d)][x + dir_dc(d)] * __ldg(J.q + d * plane + qoff);
+                                ign_acc(xx, P, S);
+                            }
+                            float a, ua;
+                            a_decode(sA[0][y][x], a, ua);
+                            const float n = ua * P;
+                            sA[0][y][x] = a_encode(a + n, ua * S);  // own cell only: in place
+                            bnew = fmaf(J.pc, sB[cur][y][x], n);
                         }
-                        float a, ua;
-                        a_decode(sA[0][y][x], a, ua);
-                        const float n = ua * P;
-                        sA[0][y][x] = a_encode(a + n, ua * S);  // own cell only: in place
-                        bnew = fmaf(J.pc, sB[cur][y][x], n);
+                        sB[cur ^ 1][y][x] = bnew;
                     }
-                    sB[cur ^ 1][y][x] = bnew;
+                    __syncthreads();
+                    cur ^= 1;
                 }
-                __syncthreads();
-                cur ^= 1;
                 if (J.tape) {  // the state at step0 + s + 1 of the interior, for the adjoint
                     float* o = J.tape + (size_t)(step0 + s + 1) * 2 * plane;
                     for (int i = tid; i < kTR * kTC; i += kBThreads) {
@@ -240,7 +248,9 @@ struct AdjSmem {
     float sa[kARR][kARC], sb[kARR][kARC];    // state (A, b) at t
     float su[kARR][kARC];                    // 2^-sigma(t)
     float sc[8][kARR][kARC];                 // contributions of targets, in source units
+    float gq[8][kAR][kAC];                   // the item's dL/dq of the interior
     uint8_t sg[kARR][kARC];                  // sigma at t + 1, then at t
+    int live;
 };
 
 __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
@@ -287,6 +297,36 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
         const int b = J.nblk - 1 - rb;
         const int t0 = b * kB, t1 = min(J.T, t0 + kB);
         const size_t plane = (size_t)J.H * J.P;
+        // a = 0 in the whole region at t1 - 1 (so at every step of the item, a never
+        // decreases): every lambda ends masked to 0 and every dL/dq term has b_i = 0
+        {
+            bool any = t1 <= t0;  // no steps: lambda is carried over unchanged
+            if (!any) {
+                const float* st = J.tape + (size_t)(t1 - 1) * 2 * plane;
+                for (int i = tid; i < kARR * kARC; i += kAThreads) {
+                    const int y = i / kARC, x = i % kARC, gr = r0 + y, gc = c0 + x;
+                    if (gr >= 0 && gr < J.H && gc >= 0 && gc < J.W)
+                        any |= __float_as_uint(__ldcg(st + (size_t)gr * J.P + gc)) != 0u;
+                }
+            }
+            if (!__syncthreads_or(any)) {
+                float* lo = J.lam[b & 1];
+                uint8_t* so = J.sig[b & 1];
+                for (int i = tid; i < kAR * kAC; i += kAThreads) {
+                    const int gr = r0 + kAH + i / kAC, gc = c0 + kAH + i % kAC;
+                    if (gr >= J.H || gc >= J.W) continue;
+                    const size_t g = (size_t)gr * J.P + gc;
+                    lo[g] = 0.0f;
+                    lo[plane + g] = 0.0f;
+                    so[g] = (uint8_t)kSigmaZero;
+                }
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) atomicExch(J.gen_b + tile, rb + 1);
+                continue;
+            }
+        }
+        for (int i = tid; i < 8 * kAR * kAC; i += kAThreads) (&sm.gq[0][0][0])[i] = 0.0f;
         // lambda at t1 over the whole region
         {
             const float* lin = J.lam[(b + 1) & 1];
@@ -351,7 +391,7 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                     const float tt = tg * (pre[d] * suf[d]);
                     const float r_d = Up * sm.su[y + dir_dr(d)][x + dir_dc(d)];
                     sm.sc[d][y][x] = tt * qd[d] * r_d;
-                    if (interior) J.Gq[d * plane + g] = fmaf(tt, bi[d] * Up, J.Gq[d * plane + g]);
+                    if (interior) sm.gq[d][y - kAH][x - kAH] = fmaf(tt, bi[d] * Up, sm.gq[d][y - kAH][x - kAH]);
                 }
                 sm.mua[y][x] = (la - ln * P) * (Up * sm.su[y][x]);  // own cell: in place
             }
@@ -375,7 +415,7 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
             }
             __syncthreads();
         }
-        // lambda at t0 of the interior
+        // lambda at t0 and the item's dL/dq of the interior (one read-modify-write per item)
         {
             float* lo = J.lam[b & 1];
             uint8_t* so = J.sig[b & 1];
@@ -386,6 +426,8 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                 lo[g] = sm.mua[y][x];
                 lo[plane + g] = sm.mub[y][x];
                 so[g] = sm.sg[y][x];
+#pragma unroll
+                for (int d = 0; d < 8; ++d) J.Gq[d * plane + g] += sm.gq[d][i / kAC][i % kAC];
             }
         }
         __threadfence();
