@@ -152,10 +152,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int m = 0; m < n; ++m) {
             const int i = l * n + m;
             const int s = i & 1, ex = i & 1;
-            if (!__syncthreads_and(mbar_wait_bounded(&sbar[s], (uint32_t)((i >> 1) & 1)))) {
-                failed = true;
-                break;
-            }
+            // each thread waits for the stage itself; a wait that ran out is agreed on at
+            // the step's barrier below (one barrier per step)
+            const bool stage_ok = mbar_wait_bounded(&sbar[s], (uint32_t)((i >> 1) & 1));
             const float* stA = sm.st[s];
             const float* stB = sm.st[s] + kPlane;
             // every row but the region's edges is processed: skipping the rows the shrinking
@@ -236,14 +235,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                             // P = 0, every leave-one-out product is 1 and every dL/dq term
                             // carries b_i = 0: only the contributions t_d q_dj = tg q_dj remain
                             la[k] *= scl[k];
+                            if (tg != 0.0f) {  // 0 for cells burned out to a = 1 exactly
 #pragma unroll
-                            for (int d = 0; d < 8; ++d) {
-                                const float tq = tg * qv[d];
-                                const float r = Up * nu[d];
-                                const int j = dir_dc(d) + 1;
-                                if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
-                                else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
-                                else wd[j] = fmaf(tq, r, wd[j]);
+                                for (int d = 0; d < 8; ++d) {
+                                    const float tq = tg * qv[d];
+                                    const float r = Up * nu[d];
+                                    const int j = dir_dc(d) + 1;
+                                    if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
+                                    else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
+                                    else wd[j] = fmaf(tq, r, wd[j]);
+                                }
                             }
                         } else {
                             float f[8];
@@ -256,20 +257,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                             // P enters only l_a = l_a' - l_n P here, where 1 - S's absolute
                             // error (a few 1e-8) is harmless; the forward keeps the recurrence
                             const float P = 1.0f - p03 * p47;
-                            const float g03 = tg * p47, g47 = tg * p03;
-                            const float r01 = g03 * p23, r23 = g03 * p01, r45 = g47 * p67, r67 = g47 * p45;
-                            const float t[8] = {f[1] * r01, f[0] * r01, f[3] * r23, f[2] * r23,
-                                                f[5] * r45, f[4] * r45, f[7] * r67, f[6] * r67};
                             la[k] = fmaf(-ln, P, la[k]) * scl[k];
+                            if (tg != 0.0f) {
+                                const float g03 = tg * p47, g47 = tg * p03;
+                                const float r01 = g03 * p23, r23 = g03 * p01, r45 = g47 * p67, r67 = g47 * p45;
+                                const float t[8] = {f[1] * r01, f[0] * r01, f[3] * r23, f[2] * r23,
+                                                    f[5] * r45, f[4] * r45, f[7] * r67, f[6] * r67};
 #pragma unroll
-                            for (int d = 0; d < 8; ++d) {
-                                gv[d] = fmaf(t[d], nb[d] * Up, gv[d]);
-                                const float tq = t[d] * qv[d];
-                                const float r = Up * nu[d];  // 2^(sigma'(j) - sigma(i)): to the units of source i
-                                const int j = dir_dc(d) + 1;
-                                if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
-                                else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
-                                else wd[j] = fmaf(tq, r, wd[j]);
+                                for (int d = 0; d < 8; ++d) {
+                                    gv[d] = fmaf(t[d], nb[d] * Up, gv[d]);
+                                    const float tq = t[d] * qv[d];
+                                    const float r = Up * nu[d];  // 2^(sigma'(j) - sigma(i)): to the units of source i
+                                    const int j = dir_dc(d) + 1;
+                                    if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
+                                    else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
+                                    else wd[j] = fmaf(tq, r, wd[j]);
+                                }
                             }
                         }
                     } else {
@@ -307,7 +310,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tmem_wait_st();
             fence_proxy_async();  // stage s fully read before it is refilled by TMA
-            __syncthreads();
+            if (!__syncthreads_and(stage_ok)) {
+                failed = true;
+                break;
+            }
             if (tid == 0 && i + 2 < total) issue_state(i + 2);
             // gather: lambda_b at the sources of this strip
 #pragma unroll
