@@ -82,7 +82,13 @@ struct pf_ctx {
     float *E = nullptr, *pveg = nullptr, *pden = nullptr;
     std::vector<Epoch> winds;
     // q cache
-    float* q = nullptr;
+    float* q = nullptr;      // q of the current wind epoch (q_own or one of qcache)
+    float* q_own = nullptr;  // the context's own q buffer
+    // per-epoch q kept from a taped forward for its adjoint (differentiable form, when
+    // the epochs fit in 30% of the free memory), with the version each was made at
+    std::vector<float*> qcache;
+    std::vector<long> qcache_ver;
+    bool qcache_on = false;
     long q_key_epoch = -1;
     long q_key_version = -1;
     long version = 0;  // bumped whenever params / env / wind / mask change
@@ -318,14 +324,42 @@ PrepArgs prep_args(const pf_ctx* c, int e, bool use_tape_params) {
     return g;
 }
 
+// Point the kernels at another q buffer (the blocked diff kernels read q through a
+// tensor map, re-encoded here).
+int use_q_buffer(pf_ctx* ctx, float* buf) {
+    if (ctx->q == buf) return PF_OK;
+    ctx->q = buf;
+    if (ctx->form == PF_DIFF && ctx->tmapQ_ok &&
+        !encode_f32_3d(&ctx->tmapQ, buf, ctx->P, ctx->H, 8, diff_blocked_box_cols(), diff_blocked_box_rows(), 8))
+        return fail(ctx, PF_ECUDA, "tensor map encoding of q failed");
+    return PF_OK;
+}
+
 int ensure_q(pf_ctx* ctx, int e) {
-    if (ctx->q_key_epoch == e && ctx->q_key_version == ctx->version) return PF_OK;
+    int rc;
+    // a taped forward keeps every epoch's q for the adjoint when the cache is on
+    const bool cache = ctx->qcache_on && ctx->tape_valid && e < (int)ctx->qcache.size();
+    if (cache && ctx->qcache[e] && ctx->qcache_ver[e] == ctx->version) {
+        if ((rc = use_q_buffer(ctx, ctx->qcache[e]))) return rc;
+        ctx->q_key_epoch = e;
+        ctx->q_key_version = ctx->version;
+        return PF_OK;
+    }
+    if (cache && !ctx->qcache[e]) {
+        void* p;
+        if (dalloc(ctx, &p, 8 * plane_elems(ctx) * sizeof(float)) == PF_OK) ctx->qcache[e] = (float*)p;
+        else cudaGetLastError();
+    }
+    float* dst = (cache && ctx->qcache[e]) ? ctx->qcache[e] : ctx->q_own;
+    if (ctx->q == dst && ctx->q_key_epoch == e && ctx->q_key_version == ctx->version) return PF_OK;
+    if ((rc = use_q_buffer(ctx, dst))) return rc;
     {
         LaunchScope ls(ctx, K_PREP);
         launch_prep(prep_args(ctx, e, false), ctx->q, ctx->st);
     }
-    int rc = check_launch(ctx, "prep");
+    rc = check_launch(ctx, "prep");
     if (rc) return rc;
+    if (dst != ctx->q_own) ctx->qcache_ver[e] = ctx->version;
     ctx->q_key_epoch = e;
     ctx->q_key_version = ctx->version;
     return PF_OK;
@@ -490,8 +524,19 @@ int choose_K(pf_ctx* ctx, int T) {
         free_b = 0;
     }
     const double sb = (double)diff_state_bytes(ctx);
-    const double budget = 0.6 * ((double)free_b + (double)ctx->arena_cap * sb);
     const int ne = (int)ctx->winds.size();
+    // keep every epoch's q for the adjoint (saves one prep per epoch) when they take at
+    // most 30% of the free memory; the tape gets the rest of the budget
+    double cached = 0.0;
+    for (float* b : ctx->qcache) cached += b ? 8.0 * (double)plane_elems(ctx) * sizeof(float) : 0.0;
+    const double qbytes = 8.0 * (double)plane_elems(ctx) * sizeof(float) * ne;
+    const double avail = (double)free_b + cached;
+    ctx->qcache_on = qbytes <= 0.3 * avail;
+    if ((int)ctx->qcache.size() < ne) {
+        ctx->qcache.resize(ne, nullptr);
+        ctx->qcache_ver.resize(ne, -1);
+    }
+    const double budget = 0.6 * (avail + (double)ctx->arena_cap * sb) - (ctx->qcache_on ? qbytes - cached : 0.0);
     if ((double)(T + 1 + ne) * sb <= budget) return 1;  // keep every state: no recomputation
     int K = std::max(2, (int)std::ceil(std::sqrt((double)T)));
     return K;
@@ -566,8 +611,11 @@ void tape_reset(pf_ctx* ctx) {
 }
 
 // Start a fresh tape at the current step with the current state as checkpoint 0.
+// The per-epoch q kept for the adjoint belongs to one tape: a new forward recomputes it.
 int tape_begin(pf_ctx* ctx, int T) {
     tape_reset(ctx);
+    for (long& v : ctx->qcache_ver) v = -1;
+    ctx->q_key_epoch = -1;
     ctx->K = choose_K(ctx, T);
     ctx->tape_start = ctx->step;
     ctx->t_p_h = ctx->p_h; ctx->t_c1 = ctx->c1; ctx->t_c2 = ctx->c2; ctx->t_a = ctx->a;
@@ -678,6 +726,7 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
         ptr = (decltype(ptr))p_;                                  \
     } while (0)
     ALLOC(ctx->q, 8 * pe * sizeof(float));
+    ctx->q_own = ctx->q;
     ALLOC(ctx->dflags, 16 * sizeof(int));
     ALLOC(ctx->dskip, K_NKINDS * sizeof(unsigned long long));
     if (cudaMallocHost((void**)&ctx->hflags, 16 * sizeof(int)) != cudaSuccess) {
@@ -1135,12 +1184,18 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
         int r;
         if (cur_e >= 0 && (r = flush(cur_e))) return r;
         cur_e = e;
-        {
-            LaunchScope ls(ctx, K_PREP);
-            launch_prep(prep_args(ctx, e, true), ctx->q, ctx->st);
+        if (e < (int)ctx->qcache.size() && ctx->qcache[e] && ctx->qcache_ver[e] == ctx->t_version) {
+            // the taped forward's q of this epoch (same parameters, fields and wind)
+            if ((r = use_q_buffer(ctx, ctx->qcache[e]))) return r;
+        } else {
+            if ((r = use_q_buffer(ctx, ctx->q_own))) return r;
+            {
+                LaunchScope ls(ctx, K_PREP);
+                launch_prep(prep_args(ctx, e, true), ctx->q, ctx->st);
+            }
+            if ((r = check_launch(ctx, "prep"))) return r;
         }
-        if ((r = check_launch(ctx, "prep"))) return r;
-        ctx->q_key_epoch = -1;  // the cache holds the recorded parameters' q now
+        ctx->q_key_epoch = -1;  // q now holds the recorded parameters' q
         return PF_OK;
     };
     const float pc = ctx->t_pc;
