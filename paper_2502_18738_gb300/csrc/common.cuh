@@ -181,6 +181,10 @@ void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float*
 // terminal scaled adjoint from dL/da_T, dL/db_T (dense, nullable) and the state at T
 void launch_adjoint_init(const float* dLda, const float* dLdb, const float* ab, int H, int W, int pitch,
                          float* lam, uint8_t* sig, cudaStream_t s);
+// Tile activity flags of the blocked forward (one byte per 48 x 48 interior tile, the
+// tiles of the 8-cell-halo geometry): b > 0 / a > 0 somewhere in the tile's interior.
+constexpr uint8_t kActB = 1, kActA = 2;
+
 // temporal-blocked adjoint with TMEM working set: n <= adjoint_blocked_max_steps() steps
 // t = t1-1 .. t1-n per launch. tst: 3-D map over a buffer of consecutive states
 // (pitch, H, 2 * nstates), box {64, 64, 2}; the state at t1-1-m is state index zlast-m.
@@ -194,6 +198,13 @@ int adjoint_blocked_configure();
 int adjoint_blocked_tiles(int H, int pitch);
 void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
                           int* tile_list, int* tile_count, unsigned long long* skipped, cudaStream_t s);
+// The same pre-pass from the forward's tile activity at a state s >= t1 - 1 (a never
+// decreases, so a tile with kActA in none of the 3 x 3 interiors around it has a = 0 in
+// its region at t1 - 1) instead of the state itself; a quiescent tile's lambda and sigma
+// are written only until both ping-pong buffers hold them (deadcnt[tile] counts that).
+void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
+                                uint8_t* deadcnt, int* tile_list, int* tile_count, unsigned long long* skipped,
+                                cudaStream_t s);
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
                             float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,

@@ -416,6 +416,52 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles(const float* __restrict__
         atomicAdd(skipped, (unsigned long long)(min(kIR, H - ir0) * min(kIC, W - ic0)) * (unsigned long long)n);
 }
 
+__global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __restrict__ act, int H, int W, int pitch,
+                                                             int tiles_x, int tiles_y, int n, int* __restrict__ list,
+                                                             int* __restrict__ count, float* __restrict__ lam_out,
+                                                             uint8_t* __restrict__ sig_out,
+                                                             uint8_t* __restrict__ deadcnt,
+                                                             unsigned long long* __restrict__ skipped) {
+    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;  // one warp per tile
+    if (tile >= tiles_x * tiles_y) return;
+    const int ty = tile / tiles_x, tx = tile % tiles_x;
+    uint32_t around = 0u;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int yy = ty + dy, xx = tx + dx;
+            if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) around |= act[yy * tiles_x + xx];
+        }
+    if (around & kActA) {
+        if (lane == 0) {
+            list[atomicAdd(count, 1)] = tile;
+            deadcnt[tile] = 0;
+        }
+        return;
+    }
+    int r0, c0;
+    origin(tile, tiles_x, r0, c0);
+    const int ir0 = r0 + kHalo, ic0 = c0 + kHalo;
+    const int dc = deadcnt[tile];
+    if (dc < 2) {  // the first two quiescent launches fill both ping-pong buffers
+        const size_t gplane = (size_t)H * pitch;
+        for (int i = lane; i < kIR * (kIC / 4); i += 32) {
+            const int gr = ir0 + i / (kIC / 4), gc = ic0 + 4 * (i % (kIC / 4));
+            if (gr >= H || gc >= pitch) continue;
+            const size_t j = (size_t)gr * pitch + gc;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(lam_out + j) = z;
+            *reinterpret_cast<float4*>(lam_out + gplane + j) = z;
+            *reinterpret_cast<uint32_t*>(sig_out + j) = 0x01010101u * (uint32_t)kSigmaZero;
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        if (dc < 2) deadcnt[tile] = (uint8_t)(dc + 1);
+        if (skipped)
+            atomicAdd(skipped, (unsigned long long)(min(kIR, H - ir0) * min(kIC, W - ic0)) * (unsigned long long)n);
+    }
+}
+
 }  // namespace
 
 int adjoint_blocked_max_steps() { return kMaxSteps; }
@@ -442,6 +488,16 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
     const int ntiles = adjoint_blocked_tiles(H, pitch);
     k_adjoint_tiles<<<(ntiles + 7) / 8, 256, 0, s>>>(A_latest, H, W, pitch, tiles_x, ntiles, n, tile_list, tile_count,
                                                      lam_out, sig_out, skipped);
+}
+
+void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
+                                uint8_t* deadcnt, int* tile_list, int* tile_count, unsigned long long* skipped,
+                                cudaStream_t s) {
+    const int tiles_x = (pitch + kIC - 1) / kIC, tiles_y = (H + kIR - 1) / kIR;
+    const int ntiles = tiles_x * tiles_y;
+    cudaMemsetAsync(tile_count, 0, sizeof(int), s);
+    k_adjoint_tiles_flags<<<(ntiles + 7) / 8, 256, 0, s>>>(act, H, W, pitch, tiles_x, tiles_y, n, tile_list, tile_count,
+                                                           lam_out, sig_out, deadcnt, skipped);
 }
 
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,

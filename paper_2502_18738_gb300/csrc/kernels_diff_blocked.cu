@@ -34,9 +34,7 @@ struct Smem {
     float b[2][kPlane];      // b ping-pong of the current tile
 };
 
-// Tile activity flags, one byte per tile: kActB = b > 0 somewhere in the tile's
-// interior, kActA = a > 0 somewhere in it (encoded A != +0).
-constexpr uint8_t kActB = 1, kActA = 2;
+// Tile activity flags (kActB, kActA: common.cuh); kActA tests the encoded A != +0.
 
 template <int kHalo>
 __device__ __forceinline__ void tile_origin(int tile, int tiles_x, int& r0, int& c0) {

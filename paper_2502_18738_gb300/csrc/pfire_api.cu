@@ -136,6 +136,14 @@ struct pf_ctx {
     const float* fl_prev_in = nullptr;  // input of the chain's previous launch
     int fl_par = 0;
     int fl_halo = 0;
+    // the tile activity at the end of every launch of a taped (K = 1) forward or of a
+    // segment's recompute, for the adjoint's tile lists: actrec_end[i] is the step whose
+    // state slot i describes; adeadcnt counts the adjoint's quiescent launches per tile
+    uint8_t* actrec = nullptr;
+    int actrec_cap = 0;
+    std::vector<int> actrec_end;
+    bool actrec_on = false;
+    uint8_t* adeadcnt = nullptr;
     CUtensorMap tmapS[2];
     bool tmap_ok = false;
     CUtensorMap tmapQ;       // q planes (pitch, H, 8), box of the blocked diff kernel
@@ -399,8 +407,29 @@ int blocked_k(const pf_ctx* c) {
 // Launches form chains (the output of one is the input of the next) along which the
 // tile activity is carried; a chain starts wherever `in` is not the state the activity
 // describes (ctx->fl_state, reset by every caller that starts a new sequence).
+// keep the activity flags of the state at `end_step` (just produced in fact[fl_par])
+int actrec_push(pf_ctx* ctx, int end_step) {
+    const size_t nt = (size_t)diff_blocked_tiles(8, ctx->H, ctx->P);
+    const int i = (int)ctx->actrec_end.size();
+    if (i >= ctx->actrec_cap) {
+        const int cap = std::max(16, 2 * ctx->actrec_cap);
+        void* p;
+        int rc = dalloc(ctx, &p, nt * cap);
+        if (rc) return rc;
+        if (ctx->actrec) {
+            CK(cudaMemcpyAsync(p, ctx->actrec, nt * ctx->actrec_cap, cudaMemcpyDeviceToDevice, ctx->st));
+            dfree(ctx, ctx->actrec);
+        }
+        ctx->actrec = (uint8_t*)p;
+        ctx->actrec_cap = cap;
+    }
+    CK(cudaMemcpyAsync(ctx->actrec + nt * i, ctx->fact[ctx->fl_par], nt, cudaMemcpyDeviceToDevice, ctx->st));
+    ctx->actrec_end.push_back(end_step);
+    return PF_OK;
+}
+
 int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* out, float* all_out,
-                        bool seg = false) {
+                        bool seg = false, int end_step = -1) {
     CUtensorMap tab;
     if (!encode_f32_3d(&tab, in, ctx->P, ctx->H, 2, diff_blocked_box_cols(), diff_blocked_box_rows(), 2))
         return fail(ctx, PF_ECUDA, "tensor map encoding of the state buffer failed");
@@ -430,6 +459,10 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
     ctx->fl_par ^= 1;
     ctx->fl_state = out ? out : all_out + (size_t)(n - 1) * stride;
     ctx->fl_prev_in = in;
+    if (ctx->actrec_on && end_step >= 0 && halo == 8) {
+        int rc = actrec_push(ctx, end_step);
+        if (rc) return rc;
+    }
     return check_launch(ctx, "diff blocked");
 }
 
@@ -582,7 +615,9 @@ int diff_steps(pf_ctx* ctx, int T) {
             out = (ctx->cur_ab == ctx->work[0]) ? ctx->work[1] : ctx->work[0];
         }
         if (kern == 2) {
-            if ((rc = diff_blocked_launch(ctx, ctx->cur_ab, ctx->pc, n, out, all_out))) return rc;
+            if ((rc = diff_blocked_launch(ctx, ctx->cur_ab, ctx->pc, n, out, all_out, false,
+                                          all_states ? t + n : -1)))
+                return rc;
         } else {
             float* dst = out ? out : all_out;
             {
@@ -599,6 +634,8 @@ int diff_steps(pf_ctx* ctx, int T) {
 
 void tape_reset(pf_ctx* ctx) {
     ctx->tape_valid = false;
+    ctx->actrec_on = false;
+    ctx->actrec_end.clear();
     ctx->ckpts.clear();
     // the current state may live in the arena: move it to a work buffer first
     if (ctx->arena && ctx->cur_ab && ctx->cur_ab >= ctx->arena &&
@@ -616,6 +653,8 @@ int tape_begin(pf_ctx* ctx, int T) {
     tape_reset(ctx);
     for (long& v : ctx->qcache_ver) v = -1;
     ctx->q_key_epoch = -1;
+    ctx->actrec_end.clear();
+    ctx->actrec_on = true;
     ctx->K = choose_K(ctx, T);
     ctx->tape_start = ctx->step;
     ctx->t_p_h = ctx->p_h; ctx->t_c1 = ctx->c1; ctx->t_c2 = ctx->c2; ctx->t_a = ctx->a;
@@ -754,6 +793,7 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
         ALLOC(ctx->work[1], diff_state_bytes(ctx));
         ALLOC(ctx->burn, (size_t)H * W);
         ALLOC(ctx->tile_list, (size_t)adjoint_blocked_tiles(H, ctx->P) * sizeof(int));
+        ALLOC(ctx->adeadcnt, (size_t)adjoint_blocked_tiles(H, ctx->P));
         {
             const size_t nt = (size_t)std::max(diff_blocked_tiles(8, H, ctx->P), diff_blocked_tiles(4, H, ctx->P));
             ALLOC(ctx->fact[0], nt);
@@ -1157,6 +1197,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
     if (grad_pveg) CK(cudaMemsetAsync(grad_pveg, 0, cell_bytes, ctx->st));
     if (grad_pden) CK(cudaMemsetAsync(grad_pden, 0, cell_bytes, ctx->st));
     CK(cudaMemsetAsync(ctx->Gq, 0, 8 * pe * sizeof(float), ctx->st));
+    CK(cudaMemsetAsync(ctx->adeadcnt, 0, (size_t)adjoint_blocked_tiles(ctx->H, ctx->P), ctx->st));
 
     const int T_end = ctx->step;
     int lcur = 0;
@@ -1206,11 +1247,21 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
         while (t1 > t0) {
             if (tmap) {
                 const int n = std::min(adjoint_blocked_max_steps(), t1 - t0);
+                // the earliest recorded activity at or after t1 - 1, if any
+                int ri = -1;
+                for (int k = 0; k < (int)ctx->actrec_end.size(); ++k)
+                    if (ctx->actrec_end[k] >= t1 - 1 && (ri < 0 || ctx->actrec_end[k] < ctx->actrec_end[ri])) ri = k;
                 {
                     LaunchScope ls(ctx, K_ATILES);
-                    launch_adjoint_tiles(buf + (size_t)(t1 - 1 - tbase) * selems, ctx->H, ctx->W, ctx->P, n,
-                                         ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->tile_list, ctx->dflags + 8,
-                                         ctx->dskip + K_ABLK, ctx->st);
+                    if (ri >= 0)
+                        launch_adjoint_tiles_flags(ctx->actrec + (size_t)ri * diff_blocked_tiles(8, ctx->H, ctx->P),
+                                                   ctx->H, ctx->W, ctx->P, n, ctx->lam[1 - lcur], ctx->sig[1 - lcur],
+                                                   ctx->adeadcnt, ctx->tile_list, ctx->dflags + 8,
+                                                   ctx->dskip + K_ABLK, ctx->st);
+                    else
+                        launch_adjoint_tiles(buf + (size_t)(t1 - 1 - tbase) * selems, ctx->H, ctx->W, ctx->P, n,
+                                             ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->tile_list, ctx->dflags + 8,
+                                             ctx->dskip + K_ABLK, ctx->st);
                 }
                 {
                     LaunchScope ls(ctx, K_ABLK, n);
@@ -1279,12 +1330,14 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             }
             CK(cudaMemcpyAsync(seg, slot_ptr(ctx, ctx->ckpts[si].second), sbytes, cudaMemcpyDeviceToDevice, ctx->st));
             ctx->fl_state = nullptr;  // a new chain starts from the checkpoint
+            ctx->actrec_end.clear();
+            ctx->actrec_on = true;
             for (int t = s0; t < s1 - 1;) {
                 const float* in = seg + (size_t)(t - s0) * selems;
                 float* nxt = seg + (size_t)(t - s0 + 1) * selems;
                 if (kern == 2) {
                     const int n = std::min(blocked_k(ctx), s1 - 1 - t);
-                    if ((rc = diff_blocked_launch(ctx, in, pc, n, nullptr, nxt, true))) return rc;
+                    if ((rc = diff_blocked_launch(ctx, in, pc, n, nullptr, nxt, true, t + n))) return rc;
                     t += n;
                 } else {
                     {
