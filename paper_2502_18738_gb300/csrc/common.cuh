@@ -166,10 +166,14 @@ void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* a
 // seg_dirty (nullable): all_out lies in a segment buffer reused across segments, whose
 // slots zero_base + s * all_stride (s < zero_slots) hold zeros for tiles not dirty; void
 // tiles (a = b = 0 in the whole region) then write nothing there (see k_fwd_tiles).
+// frozen (segment buffers only, launches aligned with the adjoint's): quiescent tiles get
+// kFrozen in act_out, and those with b = 0 in the 5 x 5 interiors around them write only
+// the launch's last slot (the next launch's input): every tile whose region reaches into
+// them is frozen too and reads its first slot instead of the intermediate ones.
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* wasdead, int* tile_list, int* tile_count, float* out,
                       bool out_is_prev_in, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
-                      int zero_slots, unsigned long long* skipped, cudaStream_t s);
+                      int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s);
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
                          int n, const int* tile_list, const int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
@@ -184,6 +188,13 @@ void launch_adjoint_init(const float* dLda, const float* dLdb, const float* ab, 
 // Tile activity flags of the blocked forward (one byte per 48 x 48 interior tile, the
 // tiles of the 8-cell-halo geometry): b > 0 / a > 0 somewhere in the tile's interior.
 constexpr uint8_t kActB = 1, kActA = 2;
+// recorded per launch of an aligned recompute (see k_fwd_tiles): b = 0 in the 3 x 3
+// interiors around the tile at the launch's first state, so the tile's region is
+// constant over the launch's steps
+constexpr uint8_t kFrozen = 4;
+// an adjoint tile-list entry with this bit reads the state of its launch's first step
+// for every step (its region is constant over the launch)
+constexpr int kTileFrozenBit = 1 << 30;
 
 // temporal-blocked adjoint with TMEM working set: n <= adjoint_blocked_max_steps() steps
 // t = t1-1 .. t1-n per launch. tst: 3-D map over a buffer of consecutive states
@@ -202,9 +213,11 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
 // decreases, so a tile with kActA in none of the 3 x 3 interiors around it has a = 0 in
 // its region at t1 - 1) instead of the state itself; a quiescent tile's lambda and sigma
 // are written only until both ping-pong buffers hold them (deadcnt[tile] counts that).
+// use_frozen: the flags come from a recompute launch aligned with this adjoint launch;
+// tiles recorded kFrozen are listed with kTileFrozenBit.
 void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
-                                uint8_t* deadcnt, int* tile_list, int* tile_count, unsigned long long* skipped,
-                                cudaStream_t s);
+                                uint8_t* deadcnt, int* tile_list, int* tile_count, bool use_frozen,
+                                unsigned long long* skipped, cudaStream_t s);
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
                             float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,

@@ -93,14 +93,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto issue_state = [&](int i) {
         const int l = i / n, m = i % n;
         int r0, c0;
-        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x], tiles_x, r0, c0);
+        const int e = tiles[(int)blockIdx.x + l * (int)gridDim.x];
+        origin(e & ~kTileFrozenBit, tiles_x, r0, c0);
         const int s = i & 1;
         mbar_arrive_expect_tx(&sbar[s], (uint32_t)(2 * kPlane * sizeof(float)));
-        tma_load_3d(sm.st[s], &tst, &sbar[s], c0, r0, 2 * (zlast - m));
+        // a frozen tile's region is constant over the launch: its first state for every step
+        tma_load_3d(sm.st[s], &tst, &sbar[s], c0, r0, 2 * (zlast - ((e & kTileFrozenBit) ? n - 1 : m)));
     };
     auto issue_q = [&](int l) {
         int r0, c0;
-        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x], tiles_x, r0, c0);
+        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x] & ~kTileFrozenBit, tiles_x, r0, c0);
         mbar_arrive_expect_tx(&qbar, (uint32_t)(8 * kPlane * sizeof(float)));
         tma_load_3d(sm.q, &tq, &qbar, c0, r0, 0);
     };
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t sgp[2];          // sigma at t + 1 of the 8 cells, 4 per word
     for (int l = 0; l < nloc && !failed; ++l) {
         int r0, c0;
-        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x], tiles_x, r0, c0);
+        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x] & ~kTileFrozenBit, tiles_x, r0, c0);
         if (!__syncthreads_and(mbar_wait_bounded(&qbar, (uint32_t)(l & 1)))) {
             failed = true;
             break;
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __re
                                                              int tiles_x, int tiles_y, int n, int* __restrict__ list,
                                                              int* __restrict__ count, float* __restrict__ lam_out,
                                                              uint8_t* __restrict__ sig_out,
-                                                             uint8_t* __restrict__ deadcnt,
+                                                             uint8_t* __restrict__ deadcnt, int use_frozen,
                                                              unsigned long long* __restrict__ skipped) {
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;  // one warp per tile
     if (tile >= tiles_x * tiles_y) return;
@@ -433,7 +435,8 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __re
         }
     if (around & kActA) {
         if (lane == 0) {
-            list[atomicAdd(count, 1)] = tile;
+            const bool fz = use_frozen && (act[tile] & kFrozen);
+            list[atomicAdd(count, 1)] = tile | (fz ? kTileFrozenBit : 0);
             deadcnt[tile] = 0;
         }
         return;
@@ -491,13 +494,13 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
 }
 
 void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
-                                uint8_t* deadcnt, int* tile_list, int* tile_count, unsigned long long* skipped,
-                                cudaStream_t s) {
+                                uint8_t* deadcnt, int* tile_list, int* tile_count, bool use_frozen,
+                                unsigned long long* skipped, cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC, tiles_y = (H + kIR - 1) / kIR;
     const int ntiles = tiles_x * tiles_y;
     cudaMemsetAsync(tile_count, 0, sizeof(int), s);
     k_adjoint_tiles_flags<<<(ntiles + 7) / 8, 256, 0, s>>>(act, H, W, pitch, tiles_x, tiles_y, n, tile_list, tile_count,
-                                                           lam_out, sig_out, deadcnt, skipped);
+                                                           lam_out, sig_out, deadcnt, use_frozen ? 1 : 0, skipped);
 }
 
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,

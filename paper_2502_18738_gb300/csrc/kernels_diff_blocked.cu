@@ -263,16 +263,20 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                                                    float* __restrict__ out, int out_is_prev_in,
                                                    float* __restrict__ all_out, size_t all_stride,
                                                    uint8_t* __restrict__ seg_dirty, float* __restrict__ zero_base,
-                                                   int zero_slots, unsigned long long* __restrict__ skipped) {
+                                                   int zero_slots, int frozen,
+                                                   unsigned long long* __restrict__ skipped) {
     constexpr int kI = kRT - 2 * kHalo;
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (tile >= tiles_x * tiles_y) return;
     const int ty = tile / tiles_x, tx = tile % tiles_x;
-    uint32_t around = 0u;
-    for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
+    uint32_t around = 0u, around5 = 0u;
+    for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
             const int yy = ty + dy, xx = tx + dx;
-            if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) around |= act_in[yy * tiles_x + xx];
+            if (yy < 0 || yy >= tiles_y || xx < 0 || xx >= tiles_x) continue;
+            const uint32_t f = act_in[yy * tiles_x + xx];
+            around5 |= f;
+            if (dy >= -1 && dy <= 1 && dx >= -1 && dx <= 1) around |= f;
         }
     if (around & kActB) {
         if (lane == 0) {
@@ -305,6 +309,8 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
     } else if (seg_dirty && lane == 0) {
         seg_dirty[tile] = 1;
     }
+    // far from anything burning: only the last slot (the next launch's input) is read
+    const bool last_only = frozen && write_all && !(around5 & kActB);
     const bool copy_out = out && !(out_is_prev_in && wasdead[tile]);
     if (copy_out || write_all) {
         // float4 columns: c0 and pitch are multiples of 4
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                 *reinterpret_cast<float4*>(out + gplane + j) = b;
             }
             if (write_all)
-                for (int s = 0; s < n; ++s) {
+                for (int s = last_only ? n - 1 : 0; s < n; ++s) {
                     float* o = all_out + (size_t)s * all_stride;
                     *reinterpret_cast<float4*>(o + j) = a;
                     *reinterpret_cast<float4*>(o + gplane + j) = b;
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
     }
     __syncwarp();  // wasdead[tile] read by every lane before it changes
     if (lane == 0) {
-        act_out[tile] = act_in[tile] & kActA;
+        act_out[tile] = (uint8_t)((act_in[tile] & kActA) | (frozen ? kFrozen : 0));
         wasdead[tile] = 1;
         if (skipped)
             atomicAdd(skipped, (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)n);
@@ -376,7 +382,7 @@ void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* a
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* wasdead, int* tile_list, int* tile_count, float* out,
                       bool out_is_prev_in, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
-                      int zero_slots, unsigned long long* skipped, cudaStream_t s) {
+                      int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int tiles_y = (H + inner - 1) / inner;
@@ -385,12 +391,12 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
         k_fwd_tiles<4><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
                                                          all_out, all_stride, seg_dirty, zero_base, zero_slots,
-                                                         skipped);
+                                                         frozen ? 1 : 0, skipped);
     else
         k_fwd_tiles<8><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
                                                          all_out, all_stride, seg_dirty, zero_base, zero_slots,
-                                                         skipped);
+                                                         frozen ? 1 : 0, skipped);
 }
 
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,

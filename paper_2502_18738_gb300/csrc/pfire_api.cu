@@ -429,7 +429,7 @@ int actrec_push(pf_ctx* ctx, int end_step) {
 }
 
 int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* out, float* all_out,
-                        bool seg = false, int end_step = -1) {
+                        bool seg = false, int end_step = -1, bool frozen = false) {
     CUtensorMap tab;
     if (!encode_f32_3d(&tab, in, ctx->P, ctx->H, 2, diff_blocked_box_cols(), diff_blocked_box_rows(), 2))
         return fail(ctx, PF_ECUDA, "tensor map encoding of the state buffer failed");
@@ -448,7 +448,7 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
         launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
                          ctx->fwasdead, ctx->flist, ctx->dflags + 9, out, out && out == ctx->fl_prev_in, all_out,
                          stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_buf + stride : nullptr,
-                         ctx->seg_cap - 1, ctx->dskip + K_FBLK, ctx->st);
+                         ctx->seg_cap - 1, seg && frozen && halo == 8, ctx->dskip + K_FBLK, ctx->st);
     }
     {
         LaunchScope ls(ctx, K_FBLK, n);
@@ -1242,11 +1242,16 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
     const float pc = ctx->t_pc;
     // adjoint steps t = t1-1 .. t0 over states held consecutively in `buf` (state
     // index z(t) = t - tbase), with its tensor map
-    auto adjoint_run = [&](const float* buf, const CUtensorMap* tmap, int tbase, int t0, int t1) -> int {
+    // With `align` > 0 the launches are [t0 + align i, t0 + align (i + 1)) like the
+    // segment's recompute launches, whose recorded tile flags then describe exactly the
+    // states of each adjoint launch (kFrozen tiles read one state for all steps).
+    auto adjoint_run = [&](const float* buf, const CUtensorMap* tmap, int tbase, int t0, int t1,
+                           int align = 0) -> int {
         int r;
         while (t1 > t0) {
             if (tmap) {
-                const int n = std::min(adjoint_blocked_max_steps(), t1 - t0);
+                int n = std::min(adjoint_blocked_max_steps(), t1 - t0);
+                if (align > 0) n = (t1 - t0) % align ? (t1 - t0) % align : align;
                 // the earliest recorded activity at or after t1 - 1, if any
                 int ri = -1;
                 for (int k = 0; k < (int)ctx->actrec_end.size(); ++k)
@@ -1257,6 +1262,9 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                         launch_adjoint_tiles_flags(ctx->actrec + (size_t)ri * diff_blocked_tiles(8, ctx->H, ctx->P),
                                                    ctx->H, ctx->W, ctx->P, n, ctx->lam[1 - lcur], ctx->sig[1 - lcur],
                                                    ctx->adeadcnt, ctx->tile_list, ctx->dflags + 8,
+                                                   // aligned: the record is this launch's own recompute
+                                                   // (a one-step launch reads one state anyway)
+                                                   align > 0,
                                                    ctx->dskip + K_ABLK, ctx->st);
                     else
                         launch_adjoint_tiles(buf + (size_t)(t1 - 1 - tbase) * selems, ctx->H, ctx->W, ctx->P, n,
@@ -1300,6 +1308,10 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             t1 = t0;
         }
     } else {
+        // recompute and adjoint launches of `chunk` steps from each segment start, so that
+        // the recorded flags of a recompute launch describe an adjoint launch's states
+        const int chunk = std::min(blocked_k(ctx), adjoint_blocked_max_steps());
+        const bool aligned = kern == 2 && adj_blocked && blocked_k(ctx) > 4;
         for (int si = (int)ctx->ckpts.size() - 1; si >= 0; --si) {
             const int s0 = ctx->ckpts[si].first;
             const int s1 = (si + 1 < (int)ctx->ckpts.size()) ? ctx->ckpts[si + 1].first : T_end;
@@ -1336,8 +1348,9 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                 const float* in = seg + (size_t)(t - s0) * selems;
                 float* nxt = seg + (size_t)(t - s0 + 1) * selems;
                 if (kern == 2) {
-                    const int n = std::min(blocked_k(ctx), s1 - 1 - t);
-                    if ((rc = diff_blocked_launch(ctx, in, pc, n, nullptr, nxt, true, t + n))) return rc;
+                    // launches of `chunk` steps from s0, the adjoint's launches below
+                    const int n = std::min(chunk, s1 - 1 - t);
+                    if ((rc = diff_blocked_launch(ctx, in, pc, n, nullptr, nxt, true, t + n, aligned))) return rc;
                     t += n;
                 } else {
                     {
@@ -1348,7 +1361,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                     t += 1;
                 }
             }
-            if ((rc = adjoint_run(seg, adj_blocked ? &tseg : nullptr, s0, s0, s1))) return rc;
+            if ((rc = adjoint_run(seg, adj_blocked ? &tseg : nullptr, s0, s0, s1, aligned ? chunk : 0))) return rc;
         }
     }
     if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
