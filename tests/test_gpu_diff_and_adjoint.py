@@ -192,3 +192,30 @@ def test_quiescent_tiles_are_skipped_exactly(pf, orc, k):
     for kind in ("diff_blocked", "adjoint_blocked"):
         launches, cell_steps, _, skipped = prof[kind]
         assert launches > 0 and 0 < skipped < cell_steps, (kind, prof[kind])
+
+
+@pytest.mark.parametrize("K,k", [(8, 8), (11, 8), (15, 6), (22, 8)])
+def test_blocked_gradients_equal_plain_with_checkpoint_segments(pf, orc, K, k):
+    """Segments of K steps with wind epochs at odd steps: the blocked path (recompute in
+    chunks aligned with the adjoint's launches, frozen and void tiles, recorded tile
+    activity) gives the plain path's gradients; the forward states are identical."""
+    import torch
+    H, W, T = 420, 380, 123
+    land = syn.make_landscape(H, W, 31)
+    winds = [syn.smooth_wind(H, W, 31, e, sigma=8.0) for e in range(3)]
+    starts = [0, 37, 90]
+    S0 = syn.initial_state(land, [(60, 70), (300, 250)])
+    w = cuda(np.random.default_rng(5).standard_normal((H, W)).astype(np.float32) * 1e-3)
+    res = {}
+    for kernel in (1, 2):
+        m, prm = _model(pf, orc, land, *winds[0], H, W)
+        _set_winds(m, winds, starts)
+        m.set_tuning(kernel=kernel, k=k, K=K)
+        out = m.forward(cuda(S0), T).cpu().numpy()
+        g4, gpv, gpd = m.backward(w, None)
+        res[kernel] = (out, g4, gpv.cpu().numpy())
+        m.close()
+    assert np.array_equal(res[1][0], res[2][0])
+    for a, b in zip(res[1][1], res[2][1]):
+        assert a == pytest.approx(b, rel=2e-5)
+    _close(res[2][2], res[1][2], 1e-4, 1e-6 * np.abs(res[1][2]).max())
