@@ -200,8 +200,9 @@ int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chos
  * launches advanced or reversed), the part of those cell-steps the temporal-blocked
  * kernels skipped because their tile was quiescent (forward: b = 0 in the whole tile
  * region, so nothing changes; adjoint: a = 0 in the whole region, so lambda is 0; the
- * results are exact either way) and, if profiling, summed device milliseconds since the
- * last reset. kinds[i] is a static name string; any output array may be NULL.
+ * results are exact either way; for the kind "adjoint_tiles" it counts the cell-steps the
+ * blocked adjoint ran on frozen tiles, whose region is constant over the launch) and, if
+ * profiling, summed device milliseconds since the last reset. kinds[i] is a static name string; any output array may be NULL.
  * Synchronous. Returns the number of kinds written (<= max_kinds) or a negative pf_status. */
 int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* launches, long long* cell_steps,
                     long long* skipped_cell_steps, double* ms, int reset);

@@ -214,10 +214,11 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
 // its region at t1 - 1) instead of the state itself; a quiescent tile's lambda and sigma
 // are written only until both ping-pong buffers hold them (deadcnt[tile] counts that).
 // use_frozen: the flags come from a recompute launch aligned with this adjoint launch;
-// tiles recorded kFrozen are listed with kTileFrozenBit.
+// tiles recorded kFrozen are listed with kTileFrozenBit (their interior cell-steps are
+// added to frozen_steps, nullable).
 void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
                                 uint8_t* deadcnt, int* tile_list, int* tile_count, bool use_frozen,
-                                unsigned long long* skipped, cudaStream_t s);
+                                unsigned long long* skipped, unsigned long long* frozen_steps, cudaStream_t s);
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
                             float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,

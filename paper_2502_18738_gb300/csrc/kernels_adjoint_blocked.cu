@@ -117,7 +117,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t sgp[2];          // sigma at t + 1 of the 8 cells, 4 per word
     for (int l = 0; l < nloc && !failed; ++l) {
         int r0, c0;
-        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x] & ~kTileFrozenBit, tiles_x, r0, c0);
+        const int ent = tiles[(int)blockIdx.x + l * (int)gridDim.x];
+        const bool frz = (ent & kTileFrozenBit) != 0;  // uniform across the CTA
+        origin(ent & ~kTileFrozenBit, tiles_x, r0, c0);
         if (!__syncthreads_and(mbar_wait_bounded(&qbar, (uint32_t)(l & 1)))) {
             failed = true;
             break;
@@ -134,17 +136,50 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sv = in ? (uint32_t)__ldg(sig_in + (size_t)gr * pitch + gc) : (uint32_t)kSigmaZero;
             sgp[k >> 2] |= sv << (8 * (k & 3));
         }
-#pragma unroll
-        for (int k = 0; k < kM; ++k) {
-            const int y = ys + k;
-            float qv[8], z[8];
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                qv[d] = sm.q[d * kPlane + y * kCT + x];
-                z[d] = 0.0f;
+        if (frz) {
+            // Frozen tile: the region's state is constant over the launch and b = 0 in
+            // it, so sigma(t) = sigma(t + 1), P = 0, every leave-one-out product is 1 and no
+            // dL/dq term survives; each step reduces to l_b,i <- p_c l_b,i + sum over the
+            // targets j = i - d of (l_a + l_b)_j K_dj, with the constants
+            // K_dj = (1 - a_j) q_dj 2^(sigma_j - sigma_i) kept in the dL/dq columns.
+            const int i0 = l * n;
+            if (!__syncthreads_and(mbar_wait_bounded(&sbar[i0 & 1], (uint32_t)((i0 >> 1) & 1)))) {
+                failed = true;
+                break;
             }
-            tmem_st8_nc(tbase + 16 * k, qv);
-            tmem_st8_nc(tbase + 16 * k + 8, z);
+            const float* stA = sm.st[i0 & 1];
+            const bool xin = x >= 1 && x < kCT - 1;
+#pragma unroll
+            for (int k = 0; k < kM; ++k) {
+                const int y = ys + k;
+                float kv[8];
+                const float Aj = stA[y * kCT + x];
+                const int sj = adj_sigma(Aj);
+                // as in the general path: edge rows and columns of the region contribute nothing
+                const bool use = xin && y >= 1 && y < kRT - 1 && sj != kSigmaZero;
+                float aj, uaj;
+                a_decode(Aj, aj, uaj);
+                const float Uj = use ? adj_unit(sj) : 0.0f;
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    const int yy = use ? y + dir_dr(d) : y, xx = use ? x + dir_dc(d) : x;
+                    kv[d] = (uaj * sm.q[d * kPlane + y * kCT + x]) * (Uj * adj_unit_inv(stA[yy * kCT + xx]));
+                }
+                tmem_st8_nc(tbase + 16 * k + 8, kv);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kM; ++k) {
+                const int y = ys + k;
+                float qv[8], z[8];
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    qv[d] = sm.q[d * kPlane + y * kCT + x];
+                    z[d] = 0.0f;
+                }
+                tmem_st8_nc(tbase + 16 * k, qv);
+                tmem_st8_nc(tbase + 16 * k + 8, z);
+            }
         }
         tmem_wait_st();
         fence_proxy_async();
@@ -172,6 +207,41 @@ __global__ void __launch_bounds__(kThreads, 1)
             float w[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
             float own[kM];  // this thread's column, rows ys .. ys+7, before cross-warp / strip terms
             // b and 2^-sigma(t) of rows y-1, y, y+1 in columns x-1, x, x+1: ring slot (row - ys + 1) % 3
+            if (frz) {
+#pragma unroll
+                for (int k = 0; k < kM; ++k) {
+                    const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
+                    scl[k] = (sp == kSigmaZero) ? 0.0f : 1.0f;  // sigma(t) = sigma(t + 1)
+                    float kv[8];
+                    tmem_ld8(tbase + 16 * k + 8, kv);
+                    float(&wu)[3] = w[k % 3];
+                    float(&wm)[3] = w[(k + 1) % 3];
+                    float(&wd)[3] = w[(k + 2) % 3];
+                    const float ln = la[k] + lb[k];  // l_a is unchanged (P = 0, no rescaling)
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) {
+                        const int j = dir_dc(d) + 1;
+                        if (dir_dr(d) < 0) wu[j] = fmaf(ln, kv[d], wu[j]);
+                        else if (dir_dr(d) == 0) wm[j] = fmaf(ln, kv[d], wm[j]);
+                        else wd[j] = fmaf(ln, kv[d], wd[j]);
+                    }
+                    // row R = k (source row ys + k - 1) is complete
+                    if (k == 0) {
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) sm.vtop[ex][strip][j][x] = wu[j];
+                    } else {
+                        const float fr = __shfl_down_sync(0xffffffffu, wu[0], 1);
+                        const float fl = __shfl_up_sync(0xffffffffu, wu[2], 1);
+                        own[k - 1] = wu[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
+                        if (x == 31) sm.el2r[ex][strip][k - 1] = wu[2];
+                        if (x == 32) sm.er2l[ex][strip][k - 1] = wu[0];
+                    }
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) wu[j] = 0.0f;
+                }
+                sgc[0] = sgp[0];
+                sgc[1] = sgp[1];
+            } else {
             float bw[3][3], uw[3][3];
             {
                 const int y0 = ys > 0 ? ys - 1 : 0;
@@ -298,6 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) wu[j] = 0.0f;  // the slot becomes row R = k + 3
             }
+            }
             // rows R = 8 (source row ys + 7, slot 8 % 3) and R = 9 (the next strip's first row)
             {
                 float(&w8)[3] = w[kM % 3];
@@ -349,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < kM; ++k) {
             const int y = ys + k;
             float gv[8];
-            tmem_ld8(tbase + 16 * k + 8, gv);
+            if (!frz) tmem_ld8(tbase + 16 * k + 8, gv);  // a frozen tile adds nothing to dL/dq
             const int gr = r0 + y, gc = c0 + x;
             if (xint && y >= kHalo && y < kRT - kHalo && gr < H && gc < pitch) {
                 const size_t j = (size_t)gr * pitch + gc;
@@ -358,8 +429,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 sig_out[j] = (uint8_t)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
                 // fire-and-forget reductions (no load round trip); each cell receives
                 // exactly one add per launch, so the result does not depend on timing
+                if (!frz) {
 #pragma unroll
-                for (int d = 0; d < 8; ++d) atomicAdd(Gq + d * gplane + j, gv[d]);
+                    for (int d = 0; d < 8; ++d) atomicAdd(Gq + d * gplane + j, gv[d]);
+                }
             }
         }
     }
@@ -423,7 +496,8 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __re
                                                              int* __restrict__ count, float* __restrict__ lam_out,
                                                              uint8_t* __restrict__ sig_out,
                                                              uint8_t* __restrict__ deadcnt, int use_frozen,
-                                                             unsigned long long* __restrict__ skipped) {
+                                                             unsigned long long* __restrict__ skipped,
+                                                             unsigned long long* __restrict__ frozen_steps) {
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;  // one warp per tile
     if (tile >= tiles_x * tiles_y) return;
     const int ty = tile / tiles_x, tx = tile % tiles_x;
@@ -438,6 +512,12 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __re
             const bool fz = use_frozen && (act[tile] & kFrozen);
             list[atomicAdd(count, 1)] = tile | (fz ? kTileFrozenBit : 0);
             deadcnt[tile] = 0;
+            if (fz && frozen_steps) {
+                int r0, c0;
+                origin(tile, tiles_x, r0, c0);
+                atomicAdd(frozen_steps, (unsigned long long)(min(kIR, H - r0 - kHalo) * min(kIC, W - c0 - kHalo)) *
+                                            (unsigned long long)n);
+            }
         }
         return;
     }
@@ -495,12 +575,13 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
 
 void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
                                 uint8_t* deadcnt, int* tile_list, int* tile_count, bool use_frozen,
-                                unsigned long long* skipped, cudaStream_t s) {
+                                unsigned long long* skipped, unsigned long long* frozen_steps, cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC, tiles_y = (H + kIR - 1) / kIR;
     const int ntiles = tiles_x * tiles_y;
     cudaMemsetAsync(tile_count, 0, sizeof(int), s);
     k_adjoint_tiles_flags<<<(ntiles + 7) / 8, 256, 0, s>>>(act, H, W, pitch, tiles_x, tiles_y, n, tile_list, tile_count,
-                                                           lam_out, sig_out, deadcnt, use_frozen ? 1 : 0, skipped);
+                                                           lam_out, sig_out, deadcnt, use_frozen ? 1 : 0, skipped,
+                                                           frozen_steps);
 }
 
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,

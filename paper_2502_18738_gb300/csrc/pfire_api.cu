@@ -1265,7 +1265,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                                                    // aligned: the record is this launch's own recompute
                                                    // (a one-step launch reads one state anyway)
                                                    align > 0,
-                                                   ctx->dskip + K_ABLK, ctx->st);
+                                                   ctx->dskip + K_ABLK, ctx->dskip + K_ATILES, ctx->st);
                     else
                         launch_adjoint_tiles(buf + (size_t)(t1 - 1 - tbase) * selems, ctx->H, ctx->W, ctx->P, n,
                                              ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->tile_list, ctx->dflags + 8,
