@@ -96,8 +96,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int e = tiles[(int)blockIdx.x + l * (int)gridDim.x];
         origin(e & ~kTileFrozenBit, tiles_x, r0, c0);
         const int s = i & 1;
+        if ((e & kTileFrozenBit) && m > 0) {
+            // a frozen tile's region is constant over the launch: its steps read only the
+            // first state (staged for m = 0); the later stages complete without a copy
+            mbar_arrive_expect_tx(&sbar[s], 0u);
+            return;
+        }
         mbar_arrive_expect_tx(&sbar[s], (uint32_t)(2 * kPlane * sizeof(float)));
-        // a frozen tile's region is constant over the launch: its first state for every step
         tma_load_3d(sm.st[s], &tst, &sbar[s], c0, r0, 2 * (zlast - ((e & kTileFrozenBit) ? n - 1 : m)));
     };
     auto issue_q = [&](int l) {
