@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // it, so sigma(t) = sigma(t + 1), P = 0, every leave-one-out product is 1 and no
             // dL/dq term survives; each step reduces to l_b,i <- p_c l_b,i + sum over the
             // targets j = i - d of (l_a + l_b)_j K_dj, with the constants
-            // K_dj = (1 - a_j) q_dj 2^(sigma_j - sigma_i) kept in the dL/dq columns.
+            // K_dj = (1 - a_j) q_dj 2^(sigma_j - sigma_i) kept in TMEM (64 consecutive
+            // columns, read with two loads and one wait per step).
             const int i0 = l * n;
             if (!__syncthreads_and(mbar_wait_bounded(&sbar[i0 & 1], (uint32_t)((i0 >> 1) & 1)))) {
                 failed = true;
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int yy = use ? y + dir_dr(d) : y, xx = use ? x + dir_dc(d) : x;
                     kv[d] = (uaj * sm.q[d * kPlane + y * kCT + x]) * (Uj * adj_unit_inv(stA[yy * kCT + xx]));
                 }
-                tmem_st8_nc(tbase + 16 * k + 8, kv);
+                tmem_st8_nc(tbase + 8 * k, kv);  // frozen layout: cell k in columns 8k .. 8k + 7
             }
         } else {
 #pragma unroll
@@ -213,12 +214,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             float own[kM];  // this thread's column, rows ys .. ys+7, before cross-warp / strip terms
             // b and 2^-sigma(t) of rows y-1, y, y+1 in columns x-1, x, x+1: ring slot (row - ys + 1) % 3
             if (frz) {
+                uint32_t ka[32], kb[32];
+                tmem_ld32_async(tbase, ka);
+                tmem_ld32_async(tbase + 32, kb);
+                tmem_wait_ld64(ka, kb);
 #pragma unroll
                 for (int k = 0; k < kM; ++k) {
                     const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
                     scl[k] = (sp == kSigmaZero) ? 0.0f : 1.0f;  // sigma(t) = sigma(t + 1)
                     float kv[8];
-                    tmem_ld8(tbase + 16 * k + 8, kv);
+#pragma unroll
+                    for (int d = 0; d < 8; ++d) kv[d] = __uint_as_float(k < 4 ? ka[8 * k + d] : kb[8 * (k - 4) + d]);
                     float(&wu)[3] = w[k % 3];
                     float(&wm)[3] = w[(k + 1) % 3];
                     float(&wd)[3] = w[(k + 2) % 3];
