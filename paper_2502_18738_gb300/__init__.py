@@ -26,7 +26,7 @@ __all__ = [
     "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_profile_read", "pf_batch_submit", "pf_last_error",
     "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
     "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10", "pf_arrival_probability",
-    "pf_affected_count", "pf_jaccard", "manhattan", "pf_set_slope",
+    "pf_affected_count", "pf_jaccard", "manhattan", "pf_set_slope", "simulate", "WildfireModel",
     "EXPORTED_SYMBOLS",
 ]
 
@@ -501,3 +501,101 @@ class DiffFire(torch.autograd.Function):
         g, gpv, gpd = ctx.model.backward(ga, gb, per_cell=True)
         g4 = torch.tensor(g, dtype=ctx.params_dtype, device=ctx.params_device)
         return None, None, None, g4, gpv, gpd, None, None, None, None, None
+
+
+def simulate(S_init, T, E=None, p_veg=None, p_den=None, V_w=None, theta_w=None, slope=None, realisations=1, seed=0,
+             p_h=0.58, c1=0.045, c2=0.131, a=0.078, p_continue=0.3, l=30.0, kernel=0):
+    """Run the discrete form for T steps (Sec. 2.2): S_init CUDA uint8 [H][W] (or
+    [R][H][W]); fields CUDA FP32 [H][W] (None: neutral), slope the optional
+    [H][W][3][3] tensor in degrees. Returns the uint8 state [R][H][W] after T steps."""
+    if S_init.dim() == 2:
+        S_init = S_init.expand(realisations, *S_init.shape).contiguous()
+    R, H, W = S_init.shape
+    m = FireModel(H, W, PF_DISCRETE, R, seed=seed)
+    try:
+        m.set_env(E, p_veg, p_den, V_w, theta_w)
+        if slope is not None:
+            m.set_slope(slope)
+        m.set_params(p_h, c1, c2, a, p_continue, l)
+        if kernel:
+            m.set_tuning(kernel=kernel)
+        return m.forward(S_init, T)
+    finally:
+        m.close()
+
+
+class WildfireModel:
+    """The paper's model object (Sec. 2.1 inputs and outputs, the calls of Alg. 1) over
+    the discrete form: ``compute(attach)`` advances one step, ``reset(seed)`` returns to
+    the initial fire, ``state`` is the two-channel (burning, burned) map, ``accumulator``
+    holds p_ignite of the newly ignited cells, ``ignition_map()`` is p_ignite, and
+    ``backward(dL_dacc)`` returns the parameter gradients through the attached steps.
+
+    Inputs: CUDA tensors H x W (wind velocity m/s, wind direction degrees counter-
+    clockwise from East, canopy p_veg, density p_den), the slope as H x W x 3 x 3 degrees
+    or an altitude map E, the initial fire as an H x W boolean (burning) map, an optional
+    non-burnable mask, and the five parameters."""
+
+    def __init__(self, initial_fire, wind_velocity=None, wind_direction=None, slope=None, altitude=None,
+                 canopy=None, density=None, non_burnable=None, p_h=0.58, c1=0.045, c2=0.131, a=0.078,
+                 p_continue=0.3, cell_size=30.0, seed=0):
+        H, W = initial_fire.shape
+        S = torch.ones((H, W), dtype=torch.uint8, device="cuda")
+        if non_burnable is not None:
+            S[non_burnable.bool()] = 0
+        S[initial_fire.bool()] = 2
+        self.S_init = S[None].contiguous()
+        self.H, self.W = H, W
+        self.params = dict(p_h=p_h, c1=c1, c2=c2, a=a, p_continue=p_continue, l=cell_size)
+        self.m = FireModel(H, W, PF_DISCRETE, 1, seed=seed)
+        self.fields = (altitude, canopy, density)
+        self.m.set_env(altitude, canopy, density, wind_velocity, wind_direction)
+        if slope is not None:
+            self.m.set_slope(slope.contiguous())
+        self.m.set_params(**self.params)
+        self.accumulator = self.m.set_accumulator(torch.zeros((1, H, W), dtype=torch.float32, device="cuda"))
+        self.seed = seed
+        self.reset(seed)
+
+    def set_parameters(self, **kw):
+        self.params.update(kw)
+        self.m.set_params(**self.params)
+
+    def set_wind(self, wind_velocity, wind_direction):
+        """Wind for the following steps. Alg. 1 sets it per iteration, before the
+        re-simulation from the initial fire; a change after steps were computed starts a
+        new wind epoch there and ends the recorded trajectory (call reset before backward)."""
+        if self.steps == 0:
+            self.m.set_env(*self.fields, wind_velocity, wind_direction)
+            self._S = self.m.forward(self.S_init, 0)
+        else:
+            self.m.set_wind(wind_velocity, wind_direction, self.steps)
+
+    def reset(self, seed=None):
+        if seed is not None:
+            self.seed = seed
+            self.m.reseed(seed)
+        self._S = self.m.forward(self.S_init, 0)
+        self.steps = 0
+        self.attached = []
+
+    def compute(self, attach=False):
+        self._S = self.m.advance(1)
+        self.attached.append(bool(attach))
+        self.steps += 1
+
+    @property
+    def state(self):
+        """Two-channel boolean map (burning, burned), 2 x H x W."""
+        s = self._S[0]
+        return torch.stack([s == 2, s == 3])
+
+    def ignition_map(self):
+        return self.m.ignition_map()[0]
+
+    def backward(self, dL_dacc):
+        """Gradients (p_h, c1, c2, a) of a loss whose gradient with respect to the
+        accumulator is dL_dacc (H x W); only the attached steps carry gradient."""
+        g, _, _ = self.m.backward_dca(dL_dacc.reshape(1, self.H, self.W).contiguous().float(),
+                                      step_mask=self.attached, per_cell=False)
+        return g

@@ -147,3 +147,34 @@ def test_calibration_loop_runs(pf):
     assert len(hist) == 12 and all(np.isfinite(l) and l > 0 for _, _, l in hist)
     assert p != [0.58, 0.045, 0.131, 0.078]
     assert list(np.nonzero(step_rings(10, 2, 2, 1))[0]) == [0, 1, 5, 8, 9]
+
+
+def test_paper_style_model_object(pf):
+    """WildfireModel (the paper's compute / reset / accumulator / state calls) runs the
+    same trajectory as a FireModel, and its backward uses the attached steps."""
+    import torch
+    H, W, T = 80, 90, 24
+    land, winds, _, S0 = _problem(H, W, 13, n_epochs=1)
+    V, th = winds[0]
+    fire = torch.from_numpy(S0 == 2).cuda()
+    nb = torch.from_numpy(S0 == 0).cuda()
+    wm = pf.WildfireModel(fire, cuda(V), cuda(th), altitude=cuda(land.E), canopy=cuda(land.p_veg),
+                          density=cuda(land.p_den), non_burnable=nb, seed=3, **{k: PRM[k] for k in
+                                                                               ("p_h", "c1", "c2", "a", "p_continue")})
+    attach = [t < 3 or t >= T - 5 for t in range(T)]
+    for t in range(T):
+        wm.compute(attach=attach[t])
+    m, acc = _model(pf, land, [(V, th)], [0], H, W, 1, seed=3)
+    out = m.forward(cuda(S0[None].copy()), T)
+    st = wm.state
+    assert torch.equal(st[0], out[0] == 2) and torch.equal(st[1], out[0] == 3)
+    assert torch.equal(wm.accumulator, acc)
+    w = torch.from_numpy(np.random.default_rng(2).standard_normal((H, W)).astype(np.float32)).cuda()
+    g_model = wm.backward(w)
+    g_ref, _, _ = m.backward_dca(w[None].contiguous(), np.array(attach), per_cell=False)
+    assert np.allclose(g_model, g_ref, rtol=0, atol=0)
+    wm.reset(seed=3)
+    assert wm.steps == 0 and int(wm.state[0].sum()) == int(fire.sum())
+    out2 = pf.simulate(cuda(S0), T, E=cuda(land.E), p_veg=cuda(land.p_veg), p_den=cuda(land.p_den), V_w=cuda(V),
+                       theta_w=cuda(th), seed=3, **PRM)
+    assert torch.equal(out2, out)
