@@ -219,3 +219,27 @@ def test_blocked_gradients_equal_plain_with_checkpoint_segments(pf, orc, K, k):
     for a, b in zip(res[1][1], res[2][1]):
         assert a == pytest.approx(b, rel=2e-5)
     _close(res[2][2], res[1][2], 1e-4, 1e-6 * np.abs(res[1][2]).max())
+
+
+@pytest.mark.parametrize("H,W,T,kernel", [(1, 1, 3, 2), (1, 70, 9, 2), (70, 1, 9, 1), (5, 5, 0, 2), (130, 97, 1, 2)])
+def test_degenerate_shapes_and_steps(pf, orc, H, W, T, kernel):
+    """Single cells, single rows / columns, T = 0 and T = 1: forward and gradients equal
+    the oracle's (T = 0: the gradient is zero)."""
+    import torch
+    land = syn.make_landscape(H, W, 17)
+    V, th = syn.smooth_wind(H, W, 17, 0, sigma=4.0)
+    S0 = syn.initial_state(land, [(H // 2, W // 2)])
+    m, prm = _model(pf, orc, land, V, th, H, W)
+    m.set_tuning(kernel=kernel)
+    out = m.forward(cuda(S0), T).cpu().numpy()
+    a, b, tape = orc.diff_forward(land, [(V, th)], [0], prm, S0, T)
+    _close(out[0].astype(np.float64), a, RUN_RTOL, RUN_ATOL)
+    _close(out[1].astype(np.float64), b, RUN_RTOL, RUN_ATOL)
+    w = np.random.default_rng(1).standard_normal((H, W))
+    g4, gpv, gpd = m.backward(cuda(w.astype(np.float32)), None)
+    want4, wpv, wpd = orc.diff_backward(land, [(V, th)], [0], prm, S0, tape, w.astype(np.float32).astype(np.float64),
+                                        np.zeros((H, W)))
+    if T == 0:
+        assert not any(g4) and not gpv.any()
+    for k in range(4):
+        assert g4[k] == pytest.approx(want4[k], rel=GRAD_RTOL, abs=1e-12)
