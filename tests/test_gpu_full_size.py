@@ -254,3 +254,90 @@ def test_1024_t900_adjoint_against_finite_difference(pf, orc):
     fd = (ls[0] - ls[1]) / (2 * h)
     assert g4[0] == pytest.approx(fd, rel=GRAD_RTOL), (g4[0], fd)
     m.close()
+
+
+def _five_fires(H, W, T, seed, uniform_wind):
+    land = syn.make_landscape(H, W, seed)
+    n_ep = (T + 99) // 100
+    if uniform_wind:
+        winds = [syn.uniform_wind(H, W, 5.0, 45.0)] * n_ep
+    else:
+        winds = [syn.smooth_wind(H, W, seed, e) for e in range(n_ep)]
+    starts = [100 * e for e in range(n_ep)]
+    ign = [(H // 2, W // 2)] + syn.random_ignitions(land, seed, 4, 4)
+    return land, winds, starts, syn.initial_state(land, ign)
+
+
+def _run(pf, land, winds, starts, S0, T, kernel):
+    H, W = S0.shape
+    m = pf.FireModel(H, W, pf.PF_DIFF)
+    set_landscape(m, land, *winds[0])
+    for (V, th), s in list(zip(winds, starts))[1:]:
+        m.set_wind(cuda(V), cuda(th), s)
+    m.set_params(**PRM)
+    m.set_tuning(kernel=kernel)
+    out = m.forward(cuda(S0), T).cpu().numpy()
+    m.close()
+    return out
+
+
+def test_1024_t300_five_fires_blocked_equals_plain(pf):
+    """The bench workload's structure at 1024 x 1024 (five ignitions, per-cell wind up
+    to 12 m/s resampled every 100 steps), T = 300: the bench's launch configuration
+    (blocked kernels with quiescent-tile skipping and tile activity) gives the plain
+    per-step kernels' states bit for bit."""
+    land, winds, starts, S0 = _five_fires(1024, 1024, 300, 5, uniform_wind=False)
+    assert np.array_equal(_run(pf, land, winds, starts, S0, 300, 2), _run(pf, land, winds, starts, S0, 300, 1))
+
+
+def test_1024_t300_five_fires_uniform_wind_matches_oracle(pf, orc):
+    """Five fires at 1024 x 1024 under a uniform 5 m/s wind, T = 300, blocked kernels:
+    a_T and b_T against the FP64 oracle within the after-T tolerance. (Under the per-cell
+    winds of the bench, up to 12 m/s, the upwind fronts are slow, pulled fronts whose
+    leading edge falls below FP32's range within this horizon, and the FP32 state drifts
+    from the FP64 oracle by up to 5e-3 in a by T = 300; see the design notes' reading of
+    the FP32 leading edge.)"""
+    land, winds, starts, S0 = _five_fires(1024, 1024, 300, 5, uniform_wind=True)
+    out = _run(pf, land, winds, starts, S0, 300, 2).astype(np.float64)
+    a, b, _ = orc.diff_forward(land, winds, starts, orc.Params(**PRM), S0, 300, keep_states=False)
+    for got, want in ((out[0], a), (out[1], b)):
+        err = np.abs(got - want) - (1e-4 * want + 1e-6)
+        assert err.max() <= 0, (float(err.max()), np.unravel_index(err.argmax(), err.shape))
+    assert (a > 0.5).sum() > 50000  # the fires did spread
+
+
+def test_uneven_batch_of_config4_distribution_matches_per_fire_contexts(pf):
+    """Twenty fires drawn like the uneven-batch workload (side log-uniform in [64, 2048],
+    T uniform in [100, 1000], 1-5 ignitions, half discrete / half differentiable with an
+    adjoint) through one pf_batch_submit: discrete final states equal per-fire contexts
+    bit for bit; differentiable states and gradients equal the plain-kernel contexts'."""
+    import torch
+    rng = np.random.default_rng(4)
+    jobs, keep = [], []
+    for i in range(20):
+        side = int(round(np.exp(rng.uniform(np.log(64), np.log(2048)))))
+        T = int(rng.integers(100, 1001))
+        land = syn.make_landscape(side, side, 700 + i)
+        V, th = syn.smooth_wind(side, side, 700 + i, 0)
+        S0 = syn.initial_state(land, syn.random_ignitions(land, 700 + i))
+        form = i % 2
+        w = (torch.full((side, side), 1e-6, dtype=torch.float32, device="cuda") if form == 1 else None)
+        j, out = pf.make_job(cuda(S0), T, form=form, seed=4, fire_id=0, E=cuda(land.E), p_veg=cuda(land.p_veg),
+                             p_den=cuda(land.p_den), V_w=cuda(V), theta_w=cuda(th), dL_da=w, **PRM)
+        jobs.append(j)
+        keep.append((side, T, form, land, V, th, S0, w, j, out))
+    pf.pf_batch_submit(jobs)
+    for side, T, form, land, V, th, S0, w, j, out in keep:
+        m = pf.FireModel(side, side, form, 1, seed=4)
+        set_landscape(m, land, V, th)
+        m.set_params(**PRM)
+        m.set_tuning(kernel=1, K=1)
+        if form == 0:
+            ref = m.forward(cuda(S0[None].copy()), T)[0]
+            assert np.array_equal(out.cpu().numpy(), ref.cpu().numpy())
+        else:
+            ref = m.forward(cuda(S0), T)
+            r4, _, _ = m.backward(w, None, per_cell=False)
+            assert np.array_equal(out.cpu().numpy(), ref.cpu().numpy())
+            assert np.allclose(j.grads.cpu().numpy(), r4, rtol=1e-6, atol=1e-12)
+        m.close()
