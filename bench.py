@@ -397,20 +397,22 @@ def main():
         hgpd = torch.empty_like(hgpv)
         hout = torch.empty((2, Hs, Ws), dtype=torch.float32).pin_memory()
         d2 = {k: torch.empty_like(v, device="cuda") for k, v in host.items() if k != "winds"}
-        dw = [(torch.empty_like(V, device="cuda"), torch.empty_like(th, device="cuda")) for V, th in host["winds"]]
+        dw0 = tuple(torch.empty_like(x, device="cuda") for x in host["winds"][0])
         h2d = sum(v.numel() * v.element_size() for k, v in host.items() if k != "winds")
         h2d += sum(V.numel() * 4 + th.numel() * 4 for V, th in host["winds"])
         d2h = hgpv.numel() * 4 * 2 + hout.numel() * 4 + 4 * 8
 
         def e2e_step():
+            # the fields and the first wind epoch are needed before the first step; the
+            # later epochs are uploaded by the library from the pinned host buffers on its
+            # copy stream while the run computes (pf_set_wind_async)
             for k in d2:
                 d2[k].copy_(host[k], non_blocking=True)
-            for (dV, dth), (V, th) in zip(dw, host["winds"]):
-                dV.copy_(V, non_blocking=True)
-                dth.copy_(th, non_blocking=True)
-            m.set_env(d2["E"], d2["pv"], d2["pd"], *dw[0])
-            for e, (V, th) in enumerate(dw[1:], start=1):
-                m.set_wind(V, th, e * EPOCH_STEPS)
+            for dx, x in zip(dw0, host["winds"][0]):
+                dx.copy_(x, non_blocking=True)
+            m.set_env(d2["E"], d2["pv"], d2["pd"], *dw0)
+            for e, (V, th) in enumerate(host["winds"][1:], start=1):
+                pf.pf_set_wind_async(m.h, Hs, Ws, V, th, e * EPOCH_STEPS)  # host buffers outlive the run
             m.set_params(**PARAMS)
             pf.pf_forward(m.h, d2["S0"], Ts, out)
             pf.pf_loss_bce(out[0], d2["y"], g_a, want_loss=False)

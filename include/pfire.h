@@ -75,10 +75,6 @@ void pf_destroy(pf_ctx* ctx);
 int pf_set_env(pf_ctx* ctx, const float* E, const float* p_veg, const float* p_den,
                const float* V_w, const float* theta_w_deg);
 
-/* Add a wind epoch (Eq. 3 inputs) that applies from global step from_step onwards,
- * until the next epoch. from_step must be > 0 and larger than every earlier epoch's;
- * NULL V_w means calm. The data is copied into the context (8 bytes per cell per
- * epoch). Used to resample the wind during a run and replayed by pf_backward. */
 /* Slope given directly (Sec. 2.1: an H x W x 3 x 3 tensor of the slope from each cell to
  * its neighbours, degrees): slope_deg device FP32 [H][W][3][3], entry [r][c][dr+1][dc+1]
  * is Eq. 1's theta_s with E the cell (r, c) and E-hat its neighbour (r+dr, c+dc), i.e.
@@ -87,7 +83,31 @@ int pf_set_env(pf_ctx* ctx, const float* E, const float* p_veg, const float* p_d
  * NaN / inf. */
 int pf_set_slope(pf_ctx* ctx, const float* slope_deg);
 
+/* Add a wind epoch (Eq. 3 inputs) that applies from global step from_step onwards,
+ * until the next epoch. from_step must be > 0 and larger than every earlier epoch's;
+ * NULL V_w means calm. V_w / theta_w_deg are H*W FP32 device arrays, copied into the
+ * context (8 bytes per cell per epoch) after a synchronous validation (PF_EINVAL for
+ * NaN / inf). Used to resample the wind during a run and replayed by pf_backward. */
 int pf_set_wind(pf_ctx* ctx, const float* V_w, const float* theta_w_deg, int from_step);
+
+/* pf_set_wind without blocking the host, for streaming the wind of later epochs while
+ * a run computes. V_w / theta_w_deg are H*W FP32 arrays in host memory (page-locked,
+ * for the copy to overlap; pageable memory works but is staged synchronously) or in
+ * device memory. The copy runs on a stream of the context's own, after the work already
+ * queued on the context's stream (the epoch's buffer may be one it released), and the
+ * context's stream waits for it only when a kernel first reads the epoch. The caller
+ * keeps the arrays valid and unchanged until the next pf_wait, pf_backward or
+ * pf_destroy returns. The values are checked on the device: NaN or infinite values are
+ * reported as PF_EINVAL by that next synchronising call, and the results of the runs
+ * that read the epoch are then undefined. Returns PF_EINVAL at once for an out-of-order
+ * from_step, PF_ENOMEM / PF_ECUDA. */
+int pf_set_wind_async(pf_ctx* ctx, const float* V_w, const float* theta_w_deg, int from_step);
+
+/* Wait for everything queued on the context (its stream and its upload stream) and
+ * report what the device recorded since the last report: PF_ETIMEOUT if a bounded
+ * device-side wait ran out, else PF_EINVAL for invalid values in an epoch uploaded by
+ * pf_set_wind_async. Each condition is cleared once reported. */
+int pf_wait(pf_ctx* ctx);
 
 /* Model parameters (Sec. 2.1 list; Eq. 2-4): p_h base probability, c1 wind-speed
  * factor, c2 wind-direction factor, a slope factor (per degree), p_continue
@@ -123,7 +143,8 @@ int pf_advance(pf_ctx* ctx, int T, void* S_out);
  *   grad_pveg, grad_pden  FP32 [H][W] device outputs (nullable): dL/dp_veg, dL/dp_den
  *                     per cell (0 at non-burnable cells).
  * Recomputes each checkpoint segment, newest first, then sweeps it backwards.
- * Synchronous (grad_params is on the host when it returns). */
+ * Synchronous (grad_params is on the host when it returns); reports what pf_wait
+ * reports. */
 int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double grad_params[4],
                 float* grad_pveg, float* grad_pden);
 

@@ -21,8 +21,8 @@ from . import build as _build
 
 __all__ = [
     "PFireError", "build", "load", "PF_DISCRETE", "PF_DIFF",
-    "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward",
-    "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
+    "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_wind_async", "pf_wait", "pf_set_params",
+    "pf_forward", "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
     "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_profile_read", "pf_batch_submit", "pf_last_error",
     "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
     "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10", "pf_arrival_probability",
@@ -43,7 +43,7 @@ EXPORTED_SYMBOLS = [
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
     "pf_loss_bce_noalloc", "pf_autotune", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
-    "pf_arrival_probability", "pf_affected_count", "pf_jaccard", "pf_set_slope",
+    "pf_arrival_probability", "pf_affected_count", "pf_jaccard", "pf_set_slope", "pf_set_wind_async", "pf_wait",
 ]
 PF_NOALLOC_BCE_MAX_N = 67108864
 
@@ -94,6 +94,8 @@ def load():
             "pf_destroy": ([vp], None),
             "pf_set_env": ([vp, vp, vp, vp, vp, vp], i),
             "pf_set_wind": ([vp, vp, vp, i], i),
+            "pf_set_wind_async": ([vp, vp, vp, i], i),
+            "pf_wait": ([vp], i),
             "pf_set_params": ([vp, f, f, f, f, f, f], i),
             "pf_forward": ([vp, vp, i, vp], i),
             "pf_advance": ([vp, i, vp], i),
@@ -150,6 +152,21 @@ def _ptr(t, dtype=None, numel=None, what="tensor"):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _hptr(t, dtype, numel, what):
+    """Pointer of a host or CUDA tensor (None -> NULL), after shape/dtype checks."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what} must be a tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{what} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -193,6 +210,19 @@ def pf_set_wind(h, H, W, V_w, theta_w, from_step):
     n = H * W
     _check(load().pf_set_wind(h, _ptr(V_w, torch.float32, n, "V_w"), _ptr(theta_w, torch.float32, n, "theta_w"),
                               int(from_step)), h)
+
+
+def pf_set_wind_async(h, H, W, V_w, theta_w, from_step):
+    """V_w / theta_w: FP32 H*W tensors in host memory (pinned, for the copy to overlap the
+    run) or on the device. They must stay alive and unchanged until the next pf_wait,
+    pf_backward or pf_destroy returns."""
+    n = H * W
+    _check(load().pf_set_wind_async(h, _hptr(V_w, torch.float32, n, "V_w"),
+                                    _hptr(theta_w, torch.float32, n, "theta_w"), int(from_step)), h)
+
+
+def pf_wait(h):
+    _check(load().pf_wait(h), h)
 
 
 def pf_set_params(h, p_h, c1, c2, a, p_continue, l=30.0):
@@ -411,6 +441,15 @@ class FireModel:
     def set_wind(self, V_w, theta_w, from_step):
         pf_set_wind(self.h, self.H, self.W, V_w, theta_w, from_step)
 
+    def set_wind_async(self, V_w, theta_w, from_step):
+        """pf_set_wind_async; the model keeps V_w / theta_w alive until the next wait()."""
+        pf_set_wind_async(self.h, self.H, self.W, V_w, theta_w, from_step)
+        self.__dict__.setdefault("_uploads", []).append((V_w, theta_w))
+
+    def wait(self):
+        pf_wait(self.h)
+        self.__dict__.pop("_uploads", None)
+
     def set_slope(self, slope_deg=None):
         pf_set_slope(self.h, self.H, self.W, slope_deg)
 
@@ -459,6 +498,7 @@ class FireModel:
             gpv = torch.empty((self.H, self.W), dtype=torch.float32, device="cuda")
             gpd = torch.empty_like(gpv)
         g = pf_backward(self.h, dL_da, dL_db, gpv, gpd)
+        self.__dict__.pop("_uploads", None)  # pf_backward waited for the uploads
         return g, gpv, gpd
 
     def state(self):

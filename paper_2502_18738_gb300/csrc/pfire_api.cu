@@ -49,6 +49,7 @@ struct Epoch {
     int from;
     float* V;   // dense H*W or nullptr (calm)
     float* th;  // dense H*W or nullptr
+    cudaEvent_t ready = nullptr;  // upload of pf_set_wind_async done (on the copy stream)
 };
 
 struct ProfRec {
@@ -81,6 +82,8 @@ struct pf_ctx {
     float p_h = 0.58f, c1 = 0.045f, c2 = 0.131f, a = 0.078f, pc = 0.3f, l = 30.0f;
     float *E = nullptr, *pveg = nullptr, *pden = nullptr;
     std::vector<Epoch> winds;
+    std::vector<float*> wind_pool;  // H*W buffers of dropped wind epochs, reused
+    cudaStream_t cst = nullptr;     // copy stream of pf_set_wind_async (created on first use)
     // q cache
     float* q = nullptr;      // q of the current wind epoch (q_own or one of qcache)
     float* q_own = nullptr;  // the context's own q buffer
@@ -123,7 +126,7 @@ struct pf_ctx {
     double* partials = nullptr;
     double* gacc = nullptr;
     // misc
-    int* dflags = nullptr;  // [0] device error word, [1..] validation flags
+    int* dflags = nullptr;  // [0] device error word, [1] validation, [3] async wind validation
     int* hflags = nullptr;  // pinned mirror
     unsigned long long* dskip = nullptr;  // per kernel kind: cell-steps of skipped quiescent tiles
     int* tile_list = nullptr;             // live tiles of one blocked-adjoint launch (count: dflags[8])
@@ -316,7 +319,11 @@ int next_epoch_start(const pf_ctx* c, int t) {
     return 0x7fffffff;
 }
 
-PrepArgs prep_args(const pf_ctx* c, int e, bool use_tape_params) {
+// Arguments of the prep kernels for wind epoch e. The caller launches on c->st next, so
+// an epoch still being uploaded by pf_set_wind_async is waited for here (a wait of the
+// stream on the upload's event; the host does not block).
+PrepArgs prep_args(pf_ctx* c, int e, bool use_tape_params) {
+    if (c->winds[e].ready) cudaStreamWaitEvent(c->st, c->winds[e].ready, 0);  // an error is caught by check_launch
     PrepArgs g{};
     g.H = c->H; g.W = c->W; g.pitch = c->P;
     g.E = c->E; g.pveg = c->pveg; g.pden = c->pden;
@@ -379,13 +386,23 @@ int sync_flags(pf_ctx* ctx, int n) {
     return PF_OK;
 }
 
+// Synchronises the context's streams and reports what the device recorded since the last
+// call: a bounded wait that ran out (PF_ETIMEOUT), else invalid values in a wind epoch
+// uploaded by pf_set_wind_async (PF_EINVAL). Both words are cleared once reported.
 int device_error(pf_ctx* ctx) {
-    int rc = sync_flags(ctx, 1);
+    if (ctx->cst) CK(cudaStreamSynchronize(ctx->cst));
+    int rc = sync_flags(ctx, 4);
     if (rc) return rc;
     if (ctx->hflags[0] != 0) {
         const int code = ctx->hflags[0];
         CK(cudaMemsetAsync(ctx->dflags, 0, sizeof(int), ctx->st));
         return fail(ctx, PF_ETIMEOUT, "a bounded device wait ran out (device code %d)", code);
+    }
+    if (ctx->hflags[3] != 0) {
+        const int bits = ctx->hflags[3];
+        CK(cudaMemsetAsync(ctx->dflags + 3, 0, sizeof(int), ctx->st));
+        return fail(ctx, PF_EINVAL, "pf_set_wind_async: NaN or infinite values in an uploaded %s",
+                    bits == 1 ? "V_w" : bits == 2 ? "theta_w" : "V_w and theta_w");
     }
     return PF_OK;
 }
@@ -823,6 +840,12 @@ failed : {
 void pf_destroy(pf_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->st);
+    if (ctx->cst) {
+        cudaStreamSynchronize(ctx->cst);
+        cudaStreamDestroy(ctx->cst);
+    }
+    for (auto& w : ctx->winds)
+        if (w.ready) cudaEventDestroy(w.ready);
     for (auto& r : ctx->prof) {
         cudaEventDestroy(r.e0);
         cudaEventDestroy(r.e1);
@@ -865,6 +888,37 @@ static int copy_field(pf_ctx* ctx, float** dst, const float* src) {
     return PF_OK;
 }
 
+// An H*W buffer for a wind epoch: one of a dropped epoch's (the stream orders its reuse
+// after the work that read it), else a new allocation.
+static int wind_buffer(pf_ctx* ctx, float** out) {
+    if (!ctx->wind_pool.empty()) {
+        *out = ctx->wind_pool.back();
+        ctx->wind_pool.pop_back();
+        return PF_OK;
+    }
+    void* p;
+    int rc = dalloc(ctx, &p, (size_t)ctx->H * ctx->W * sizeof(float));
+    if (rc) return rc;
+    *out = (float*)p;
+    return PF_OK;
+}
+
+// Drop the wind epochs after the first. Their buffers go to the pool; an upload still in
+// flight is ordered before any later work of the context's stream (which reuses them).
+static int drop_epochs(pf_ctx* ctx) {
+    for (size_t i = 1; i < ctx->winds.size(); ++i) {
+        Epoch& w = ctx->winds[i];
+        if (w.ready) {
+            CK(cudaStreamWaitEvent(ctx->st, w.ready, 0));
+            cudaEventDestroy(w.ready);
+        }
+        if (w.V) ctx->wind_pool.push_back(w.V);
+        if (w.th) ctx->wind_pool.push_back(w.th);
+    }
+    ctx->winds.resize(1);
+    return PF_OK;
+}
+
 static int validate_fields(pf_ctx* ctx, const float* const* f, const float* lo, int n) {
     const size_t cells = (size_t)ctx->H * ctx->W;
     CK(cudaMemsetAsync(ctx->dflags + 1, 0, sizeof(int), ctx->st));
@@ -898,11 +952,7 @@ int pf_set_env(pf_ctx* ctx, const float* E, const float* p_veg, const float* p_d
     if ((rc = copy_field(ctx, &ctx->E, E))) return rc;
     if ((rc = copy_field(ctx, &ctx->pveg, p_veg))) return rc;
     if ((rc = copy_field(ctx, &ctx->pden, p_den))) return rc;
-    for (size_t i = 1; i < ctx->winds.size(); ++i) {
-        dfree(ctx, ctx->winds[i].V);
-        dfree(ctx, ctx->winds[i].th);
-    }
-    ctx->winds.resize(1);
+    if ((rc = drop_epochs(ctx))) return rc;
     if ((rc = copy_field(ctx, &ctx->winds[0].V, V_w))) return rc;
     if ((rc = copy_field(ctx, &ctx->winds[0].th, theta_w_deg))) return rc;
     ctx->version++;
@@ -951,11 +1001,48 @@ int pf_set_wind(pf_ctx* ctx, const float* V_w, const float* theta_w_deg, int fro
     if (bad) return fail(ctx, PF_EINVAL, "pf_set_wind: NaN or infinite wind values");
     Epoch e{from_step, nullptr, nullptr};
     int rc;
+    if (V_w && (rc = wind_buffer(ctx, &e.V))) return rc;
+    if (theta_w_deg && (rc = wind_buffer(ctx, &e.th))) return rc;
     if ((rc = copy_field(ctx, &e.V, V_w))) return rc;
     if ((rc = copy_field(ctx, &e.th, theta_w_deg))) return rc;
     ctx->winds.push_back(e);
     if (ctx->tape_valid && from_step <= ctx->step) tape_reset(ctx);
     return PF_OK;
+}
+
+int pf_set_wind_async(pf_ctx* ctx, const float* V_w, const float* theta_w_deg, int from_step) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_set_wind_async: ctx is NULL");
+    if (from_step <= ctx->winds.back().from)
+        return fail(ctx, PF_EINVAL, "pf_set_wind_async: from_step %d must exceed the last epoch's start %d",
+                    from_step, ctx->winds.back().from);
+    if (!ctx->cst) CK(cudaStreamCreateWithFlags(&ctx->cst, cudaStreamNonBlocking));
+    Epoch e{from_step, nullptr, nullptr};
+    int rc;
+    if (V_w && (rc = wind_buffer(ctx, &e.V))) return rc;
+    if (theta_w_deg && (rc = wind_buffer(ctx, &e.th))) return rc;
+    CK(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
+    ctx->winds.push_back(e);  // from here on the event is owned (and destroyed) with the epoch
+    // the buffers may come from the pool: the copy waits for the work already queued on
+    // the context's stream, which may still read them
+    CK(cudaEventRecord(e.ready, ctx->st));
+    CK(cudaStreamWaitEvent(ctx->cst, e.ready, 0));
+    const size_t cells = (size_t)ctx->H * ctx->W;
+    if (V_w) CK(cudaMemcpyAsync(e.V, V_w, cells * sizeof(float), cudaMemcpyDefault, ctx->cst));
+    if (theta_w_deg) CK(cudaMemcpyAsync(e.th, theta_w_deg, cells * sizeof(float), cudaMemcpyDefault, ctx->cst));
+    // checked on the copy stream and reported by the next synchronising call (device_error);
+    // counted as misc launches, untimed (the profile's events are on the context's stream)
+    if (e.V) launch_validate_fields(e.V, cells, -INFINITY, 0, ctx->dflags + 3, ctx->cst);
+    if (e.th) launch_validate_fields(e.th, cells, -INFINITY, 1, ctx->dflags + 3, ctx->cst);
+    ctx->launches[K_MISC] += (e.V ? 1 : 0) + (e.th ? 1 : 0);
+    if ((rc = check_launch(ctx, "validate uploaded wind"))) return rc;
+    CK(cudaEventRecord(e.ready, ctx->cst));
+    if (ctx->tape_valid && from_step <= ctx->step) tape_reset(ctx);
+    return PF_OK;
+}
+
+int pf_wait(pf_ctx* ctx) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_wait: ctx is NULL");
+    return device_error(ctx);
 }
 
 int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t) {
