@@ -196,6 +196,16 @@ constexpr uint8_t kFrozen = 4;
 // for every step (its region is constant over the launch)
 constexpr int kTileFrozenBit = 1 << 30;
 
+// Adds a block's per-thread counts to a per-launch counter with one global atomic per
+// block (every tile of a launch would otherwise hit the same address). s: a __shared__
+// word zeroed before a __syncthreads that precedes the call; every thread of the block
+// calls this.
+__device__ __forceinline__ void block_count(unsigned long long* g, unsigned long long& s, unsigned long long v) {
+    if (v) atomicAdd(&s, v);
+    __syncthreads();
+    if (threadIdx.x == 0 && g && s) atomicAdd(g, s);
+}
+
 // temporal-blocked adjoint with TMEM working set: n <= adjoint_blocked_max_steps() steps
 // t = t1-1 .. t1-n per launch. tst: 3-D map over a buffer of consecutive states
 // (pitch, H, 2 * nstates), box {64, 64, 2}; the state at t1-1-m is state index zlast-m.

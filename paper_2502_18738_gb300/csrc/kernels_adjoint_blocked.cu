@@ -465,13 +465,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 // carries a factor b_i = 0. Such a tile's interior gets lambda = 0, sigma = kSigmaZero
 // here; the others are listed (in any order: each tile writes only its own interior and
 // adds to its own cells' dL/dq once) for k_adjoint_blocked.
-__global__ void __launch_bounds__(256) k_adjoint_tiles(const float* __restrict__ A, int H, int W, int pitch,
+__device__ __forceinline__ void adjoint_tile(const float* __restrict__ A, int H, int W, int pitch,
                                                        int tiles_x, int ntiles, int n, int* __restrict__ list,
                                                        int* __restrict__ count, float* __restrict__ lam_out,
                                                        uint8_t* __restrict__ sig_out,
-                                                       unsigned long long* __restrict__ skipped) {
-    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;  // one warp per tile
-    if (tile >= ntiles) return;
+                                                       unsigned long long* __restrict__ skipped, int tile, int lane, unsigned long long& sk) {
     int r0, c0;
     origin(tile, tiles_x, r0, c0);
     uint32_t any = 0u;
@@ -498,19 +496,33 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles(const float* __restrict__
         *reinterpret_cast<float4*>(lam_out + gplane + j) = z;
         *reinterpret_cast<uint32_t*>(sig_out + j) = 0x01010101u * (uint32_t)kSigmaZero;
     }
-    if (lane == 0 && skipped)
-        atomicAdd(skipped, (unsigned long long)(min(kIR, H - ir0) * min(kIC, W - ic0)) * (unsigned long long)n);
+    if (lane == 0) sk = (unsigned long long)(min(kIR, H - ir0) * min(kIC, W - ic0)) * (unsigned long long)n;
 }
 
-__global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __restrict__ act, int H, int W, int pitch,
+__global__ void __launch_bounds__(256) k_adjoint_tiles(const float* __restrict__ A, int H, int W, int pitch,
+                                                       int tiles_x, int ntiles, int n, int* __restrict__ list,
+                                                       int* __restrict__ count, float* __restrict__ lam_out,
+                                                       uint8_t* __restrict__ sig_out,
+                                                       unsigned long long* __restrict__ skipped) {
+    __shared__ unsigned long long s_sk;
+    if (threadIdx.x == 0) s_sk = 0ull;
+    __syncthreads();
+    unsigned long long sk = 0ull;
+    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
+    if (tile < ntiles)
+        adjoint_tile(A, H, W, pitch, tiles_x, ntiles, n, list, count, lam_out, sig_out, skipped, tile,
+                     threadIdx.x & 31, sk);
+    block_count(skipped, s_sk, sk);
+}
+
+__device__ __forceinline__ void adjoint_tile_flags(const uint8_t* __restrict__ act, int H, int W, int pitch,
                                                              int tiles_x, int tiles_y, int n, int* __restrict__ list,
                                                              int* __restrict__ count, float* __restrict__ lam_out,
                                                              uint8_t* __restrict__ sig_out,
                                                              uint8_t* __restrict__ deadcnt, int use_frozen,
                                                              unsigned long long* __restrict__ skipped,
-                                                             unsigned long long* __restrict__ frozen_steps) {
-    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;  // one warp per tile
-    if (tile >= tiles_x * tiles_y) return;
+                                                             unsigned long long* __restrict__ frozen_steps, int tile, int lane, unsigned long long& sk,
+                                                   unsigned long long& fz_steps) {
     const int ty = tile / tiles_x, tx = tile % tiles_x;
     uint32_t around = 0u;
     for (int dy = -1; dy <= 1; ++dy)
@@ -523,11 +535,11 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __re
             const bool fz = use_frozen && (act[tile] & kFrozen);
             list[atomicAdd(count, 1)] = tile | (fz ? kTileFrozenBit : 0);
             deadcnt[tile] = 0;
-            if (fz && frozen_steps) {
+            if (fz) {
                 int r0, c0;
                 origin(tile, tiles_x, r0, c0);
-                atomicAdd(frozen_steps, (unsigned long long)(min(kIR, H - r0 - kHalo) * min(kIC, W - c0 - kHalo)) *
-                                            (unsigned long long)n);
+                fz_steps = (unsigned long long)(min(kIR, H - r0 - kHalo) * min(kIC, W - c0 - kHalo)) *
+                           (unsigned long long)n;
             }
         }
         return;
@@ -551,9 +563,27 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __re
     __syncwarp();
     if (lane == 0) {
         if (dc < 2) deadcnt[tile] = (uint8_t)(dc + 1);
-        if (skipped)
-            atomicAdd(skipped, (unsigned long long)(min(kIR, H - ir0) * min(kIC, W - ic0)) * (unsigned long long)n);
+        sk = (unsigned long long)(min(kIR, H - ir0) * min(kIC, W - ic0)) * (unsigned long long)n;
     }
+}
+
+__global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __restrict__ act, int H, int W, int pitch,
+                                                             int tiles_x, int tiles_y, int n, int* __restrict__ list,
+                                                             int* __restrict__ count, float* __restrict__ lam_out,
+                                                             uint8_t* __restrict__ sig_out,
+                                                             uint8_t* __restrict__ deadcnt, int use_frozen,
+                                                             unsigned long long* __restrict__ skipped,
+                                                             unsigned long long* __restrict__ frozen_steps) {
+    __shared__ unsigned long long s_sk, s_fz;
+    if (threadIdx.x == 0) s_sk = s_fz = 0ull;
+    __syncthreads();
+    unsigned long long sk = 0ull, fz = 0ull;
+    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
+    if (tile < tiles_x * tiles_y)
+        adjoint_tile_flags(act, H, W, pitch, tiles_x, tiles_y, n, list, count, lam_out, sig_out, deadcnt, use_frozen,
+                           skipped, frozen_steps, tile, threadIdx.x & 31, sk, fz);
+    block_count(skipped, s_sk, sk);
+    block_count(frozen_steps, s_fz, fz);
 }
 
 }  // namespace

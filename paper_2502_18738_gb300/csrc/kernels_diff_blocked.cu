@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ 
 // the whole launch); its slots only have to hold zeros, which they already do unless the
 // tile is dirty, in which case all of them are zeroed once.
 template <int kHalo>
-__global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in, int H, int W, int pitch,
+__device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, int W, int pitch,
                                                    int tiles_x, int tiles_y, int n, const uint8_t* __restrict__ act_in,
                                                    uint8_t* __restrict__ act_out, uint8_t* __restrict__ wasdead,
                                                    int* __restrict__ list, int* __restrict__ count,
@@ -264,10 +264,8 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                                                    float* __restrict__ all_out, size_t all_stride,
                                                    uint8_t* __restrict__ seg_dirty, float* __restrict__ zero_base,
                                                    int zero_slots, int frozen,
-                                                   unsigned long long* __restrict__ skipped) {
+                                                   unsigned long long* __restrict__ skipped, int tile, int lane, unsigned long long& sk) {
     constexpr int kI = kRT - 2 * kHalo;
-    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (tile >= tiles_x * tiles_y) return;
     const int ty = tile / tiles_x, tx = tile % tiles_x;
     uint32_t around = 0u, around5 = 0u;
     for (int dy = -2; dy <= 2; ++dy)
@@ -336,9 +334,30 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
     if (lane == 0) {
         act_out[tile] = (uint8_t)((act_in[tile] & kActA) | (frozen ? kFrozen : 0));
         wasdead[tile] = 1;
-        if (skipped)
-            atomicAdd(skipped, (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)n);
+        sk = (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)n;
     }
+}
+
+template <int kHalo>
+__global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in, int H, int W, int pitch,
+                                                   int tiles_x, int tiles_y, int n, const uint8_t* __restrict__ act_in,
+                                                   uint8_t* __restrict__ act_out, uint8_t* __restrict__ wasdead,
+                                                   int* __restrict__ list, int* __restrict__ count,
+                                                   float* __restrict__ out, int out_is_prev_in,
+                                                   float* __restrict__ all_out, size_t all_stride,
+                                                   uint8_t* __restrict__ seg_dirty, float* __restrict__ zero_base,
+                                                   int zero_slots, int frozen,
+                                                   unsigned long long* __restrict__ skipped) {
+    __shared__ unsigned long long s_sk;
+    if (threadIdx.x == 0) s_sk = 0ull;
+    __syncthreads();
+    unsigned long long sk = 0ull;
+    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
+    if (tile < tiles_x * tiles_y)
+        fwd_tile<kHalo>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out, wasdead, list, count, out,
+                        out_is_prev_in, all_out, all_stride, seg_dirty, zero_base, zero_slots, frozen, skipped, tile,
+                        threadIdx.x & 31, sk);
+    block_count(skipped, s_sk, sk);
 }
 
 }  // namespace
