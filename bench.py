@@ -396,33 +396,61 @@ def main():
         hgpv = torch.empty((Hs, Ws), dtype=torch.float32).pin_memory()
         hgpd = torch.empty_like(hgpv)
         hout = torch.empty((2, Hs, Ws), dtype=torch.float32).pin_memory()
-        d2 = {k: torch.empty_like(v, device="cuda") for k, v in host.items() if k != "winds"}
-        dw0 = tuple(torch.empty_like(x, device="cuda") for x in host["winds"][0])
-        h2d = sum(v.numel() * v.element_size() for k, v in host.items() if k != "winds")
+        keys = ["E", "pv", "pd", "S0", "y"]
+        h2d = sum(host[k].numel() * host[k].element_size() for k in keys)
         h2d += sum(V.numel() * 4 + th.numel() * 4 for V, th in host["winds"])
         d2h = hgpv.numel() * 4 * 2 + hout.numel() * 4 + 4 * 8
+        # every input of a step lands in one of two device staging sets: a step's inputs
+        # are copied in on a side stream while the previous step's adjoint runs (the
+        # first step's before its forward, with its later wind epochs streamed by the
+        # library from the pinned host buffers: pf_set_wind_async). Every copy of every
+        # step is inside the timed region.
+        stage = [dict({k: torch.empty_like(host[k], device="cuda") for k in keys},
+                      winds=[(torch.empty_like(V, device="cuda"), torch.empty_like(th, device="cuda"))
+                             for V, th in host["winds"]]) for _ in range(2)]
+        side = torch.cuda.Stream()
+        ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_out = torch.cuda.Event()
 
-        def e2e_step():
-            # the fields and the first wind epoch are needed before the first step; the
-            # later epochs are uploaded by the library from the pinned host buffers on its
-            # copy stream while the run computes (pf_set_wind_async)
-            for k in d2:
-                d2[k].copy_(host[k], non_blocking=True)
-            for dx, x in zip(dw0, host["winds"][0]):
-                dx.copy_(x, non_blocking=True)
-            m.set_env(d2["E"], d2["pv"], d2["pd"], *dw0)
-            for e, (V, th) in enumerate(host["winds"][1:], start=1):
-                pf.pf_set_wind_async(m.h, Hs, Ws, V, th, e * EPOCH_STEPS)  # host buffers outlive the run
-            m.set_params(**PARAMS)
-            pf.pf_forward(m.h, d2["S0"], Ts, out)
-            pf.pf_loss_bce(out[0], d2["y"], g_a, want_loss=False)
-            g = pf.pf_backward(m.h, g_a, None, gpv, gpd)
-            hgpv.copy_(gpv, non_blocking=True)
-            hgpd.copy_(gpd, non_blocking=True)
-            hout.copy_(out, non_blocking=True)
-            return g
+        def upload(st, winds_from=0):
+            for k in keys:
+                st[k].copy_(host[k], non_blocking=True)
+            for (dV, dth), (V, th) in list(zip(st["winds"], host["winds"]))[winds_from:]:
+                dV.copy_(V, non_blocking=True)
+                dth.copy_(th, non_blocking=True)
 
-        ms_e2e = timed(e2e_step, max(1, args.steps))
+        def e2e_run(n):
+            for i in range(n):
+                st = stage[i % 2]
+                if i == 0:
+                    upload(st, winds_from=len(host["winds"]))
+                    st["winds"][0][0].copy_(host["winds"][0][0], non_blocking=True)
+                    st["winds"][0][1].copy_(host["winds"][0][1], non_blocking=True)
+                    m.set_env(st["E"], st["pv"], st["pd"], *st["winds"][0])
+                    for e, (V, th) in enumerate(host["winds"][1:], start=1):
+                        pf.pf_set_wind_async(m.h, Hs, Ws, V, th, e * EPOCH_STEPS)  # pinned host buffers
+                else:
+                    stream.wait_event(ev_in[i % 2])
+                    m.set_env(st["E"], st["pv"], st["pd"], *st["winds"][0])
+                    for e, (V, th) in enumerate(st["winds"][1:], start=1):
+                        pf.pf_set_wind_async(m.h, Hs, Ws, V, th, e * EPOCH_STEPS)
+                m.set_params(**PARAMS)
+                pf.pf_forward(m.h, st["S0"], Ts, out)
+                side.wait_stream(stream)  # out is final; the other staging set is free
+                with torch.cuda.stream(side):
+                    hout.copy_(out, non_blocking=True)
+                    ev_out.record(side)
+                    if i + 1 < n:
+                        upload(stage[(i + 1) % 2])
+                        ev_in[(i + 1) % 2].record(side)
+                pf.pf_loss_bce(out[0], st["y"], g_a, want_loss=False)
+                pf.pf_backward(m.h, g_a, None, gpv, gpd)
+                hgpv.copy_(gpv, non_blocking=True)
+                hgpd.copy_(gpd, non_blocking=True)
+                stream.wait_event(ev_out)
+
+        n_e2e = max(1, args.steps)
+        ms_e2e = timed(lambda: e2e_run(n_e2e), 1) / n_e2e
         e2e = {"value": cells * world / (ms_e2e / 1000.0), "unit": "cell-updates/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
 
