@@ -161,8 +161,11 @@ int diff_blocked_configure();
 // k_diff_blocked writes act_out for the tiles it runs. skipped (nullable) accumulates the
 // interior cell-steps of quiescent tiles.
 int diff_blocked_tiles(int halo, int H, int pitch);
-void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* act, uint8_t* wasdead,
+void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* act, uint8_t* qrun,
                          cudaStream_t s);
+// qrun: per tile, the number of consecutive launches of the chain it has been quiescent
+// in (saturating at 255); out_age > 0: out holds the input state of the launch out_age
+// launches back, so tiles with qrun >= out_age need no copy into it (0: out holds nothing).
 // seg_dirty (nullable): all_out lies in a segment buffer reused across segments, whose
 // slots zero_base + s * all_stride (s < zero_slots) hold zeros for tiles not dirty; void
 // tiles (a = b = 0 in the whole region) then write nothing there (see k_fwd_tiles).
@@ -171,8 +174,8 @@ void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* a
 // the launch's last slot (the next launch's input): every tile whose region reaches into
 // them is frozen too and reads its first slot instead of the intermediate ones.
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
-                      uint8_t* act_out, uint8_t* wasdead, int* tile_list, int* tile_count, float* out,
-                      bool out_is_prev_in, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
+                      uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
+                      int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
                       int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s);
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
                          int n, const int* tile_list, const int* tile_count, float* out, float* all_out,

@@ -469,7 +469,8 @@ __device__ __forceinline__ void adjoint_tile(const float* __restrict__ A, int H,
                                                        int tiles_x, int ntiles, int n, int* __restrict__ list,
                                                        int* __restrict__ count, float* __restrict__ lam_out,
                                                        uint8_t* __restrict__ sig_out,
-                                                       unsigned long long* __restrict__ skipped, int tile, int lane, unsigned long long& sk) {
+                                                       unsigned long long* __restrict__ skipped, int tile, int lane,
+                                                       unsigned long long& sk) {
     int r0, c0;
     origin(tile, tiles_x, r0, c0);
     uint32_t any = 0u;
@@ -521,15 +522,17 @@ __device__ __forceinline__ void adjoint_tile_flags(const uint8_t* __restrict__ a
                                                              uint8_t* __restrict__ sig_out,
                                                              uint8_t* __restrict__ deadcnt, int use_frozen,
                                                              unsigned long long* __restrict__ skipped,
-                                                             unsigned long long* __restrict__ frozen_steps, int tile, int lane, unsigned long long& sk,
-                                                   unsigned long long& fz_steps) {
+                                                             unsigned long long* __restrict__ frozen_steps, int tile,
+                                                             int lane, unsigned long long& sk,
+                                                             unsigned long long& fz_steps) {
     const int ty = tile / tiles_x, tx = tile % tiles_x;
-    uint32_t around = 0u;
-    for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int yy = ty + dy, xx = tx + dx;
-            if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) around |= act[yy * tiles_x + xx];
-        }
+    // the 3 x 3 flags around the tile, one per lane, OR-reduced
+    uint32_t f = 0u;
+    if (lane < 9) {
+        const int yy = ty + lane / 3 - 1, xx = tx + lane % 3 - 1;
+        if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) f = act[yy * tiles_x + xx];
+    }
+    const uint32_t around = __reduce_or_sync(0xffffffffu, f);
     if (around & kActA) {
         if (lane == 0) {
             const bool fz = use_frozen && (act[tile] & kFrozen);

@@ -209,12 +209,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Activity of a state at the start of a chain of launches; wasdead[tile] = 0 (nothing is
+// Activity of a state at the start of a chain of launches; qrun[tile] = 0 (nothing is
 // known about the other buffers). One warp per tile.
 template <int kHalo>
 __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ ab, int H, int pitch, int tiles_x,
                                                       int ntiles, uint8_t* __restrict__ act,
-                                                      uint8_t* __restrict__ wasdead) {
+                                                      uint8_t* __restrict__ qrun) {
     constexpr int kI = kRT - 2 * kHalo;
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (tile >= ntiles) return;
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ 
     const bool hasA = __any_sync(0xffffffffu, anyA != 0u), hasB = __any_sync(0xffffffffu, anyB != 0u);
     if (lane == 0) {
         act[tile] = (hasA ? kActA : 0) | (hasB ? kActB : 0);
-        wasdead[tile] = 0;
+        qrun[tile] = 0;
     }
 }
 
@@ -246,8 +246,9 @@ __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ 
 // tile that is not live has b = 0 in its whole region and its state does not change
 // during the launch. Live tiles are listed for k_diff_blocked, which writes their
 // act_out. A quiescent tile keeps its kActA flag; its interior is copied to the outputs,
-// except into `out` when out holds the previous launch's input and the tile was
-// quiescent then too (out already holds this state).
+// except into `out` when out already holds its state: out holds the input state of the
+// launch out_age launches back (out_age > 0) and the tile has been quiescent in every
+// launch since (qrun[tile], the tile's quiescent streak, saturating at 255).
 //
 // Segment buffers (seg_dirty != nullptr): all_out is a run of slots of a buffer that is
 // reused from segment to segment, and seg_dirty[tile] records whether the tile's interior
@@ -258,28 +259,31 @@ __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ 
 template <int kHalo>
 __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, int W, int pitch,
                                                    int tiles_x, int tiles_y, int n, const uint8_t* __restrict__ act_in,
-                                                   uint8_t* __restrict__ act_out, uint8_t* __restrict__ wasdead,
+                                                   uint8_t* __restrict__ act_out, uint8_t* __restrict__ qrun,
                                                    int* __restrict__ list, int* __restrict__ count,
-                                                   float* __restrict__ out, int out_is_prev_in,
+                                                   float* __restrict__ out, int out_age,
                                                    float* __restrict__ all_out, size_t all_stride,
                                                    uint8_t* __restrict__ seg_dirty, float* __restrict__ zero_base,
                                                    int zero_slots, int frozen,
-                                                   unsigned long long* __restrict__ skipped, int tile, int lane, unsigned long long& sk) {
+                                                   unsigned long long* __restrict__ skipped, int tile, int lane,
+                                                   unsigned long long& sk) {
     constexpr int kI = kRT - 2 * kHalo;
     const int ty = tile / tiles_x, tx = tile % tiles_x;
-    uint32_t around = 0u, around5 = 0u;
-    for (int dy = -2; dy <= 2; ++dy)
-        for (int dx = -2; dx <= 2; ++dx) {
-            const int yy = ty + dy, xx = tx + dx;
-            if (yy < 0 || yy >= tiles_y || xx < 0 || xx >= tiles_x) continue;
-            const uint32_t f = act_in[yy * tiles_x + xx];
-            around5 |= f;
-            if (dy >= -1 && dy <= 1 && dx >= -1 && dx <= 1) around |= f;
-        }
+    // the 5 x 5 flags around the tile, one per lane (25 independent loads), OR-reduced
+    uint32_t f = 0u;
+    bool inner3 = false;
+    if (lane < 25) {
+        const int dy = lane / 5 - 2, dx = lane % 5 - 2;
+        const int yy = ty + dy, xx = tx + dx;
+        if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) f = act_in[yy * tiles_x + xx];
+        inner3 = dy >= -1 && dy <= 1 && dx >= -1 && dx <= 1;
+    }
+    const uint32_t around5 = __reduce_or_sync(0xffffffffu, f);
+    const uint32_t around = __reduce_or_sync(0xffffffffu, inner3 ? f : 0u);
     if (around & kActB) {
         if (lane == 0) {
             list[atomicAdd(count, 1)] = tile;
-            wasdead[tile] = 0;
+            qrun[tile] = 0;
             if (seg_dirty) seg_dirty[tile] = 1;
         }
         return;
@@ -309,7 +313,8 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     }
     // far from anything burning: only the last slot (the next launch's input) is read
     const bool last_only = frozen && write_all && !(around5 & kActB);
-    const bool copy_out = out && !(out_is_prev_in && wasdead[tile]);
+    const int qr = qrun[tile];
+    const bool copy_out = out && !(out_age > 0 && qr >= out_age);
     if (copy_out || write_all) {
         // float4 columns: c0 and pitch are multiples of 4
         for (int i = lane; i < kI * (kI / 4); i += 32) {
@@ -330,10 +335,10 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
                 }
         }
     }
-    __syncwarp();  // wasdead[tile] read by every lane before it changes
+    __syncwarp();  // qrun[tile] read by every lane before it changes
     if (lane == 0) {
         act_out[tile] = (uint8_t)((act_in[tile] & kActA) | (frozen ? kFrozen : 0));
-        wasdead[tile] = 1;
+        qrun[tile] = (uint8_t)min(qr + 1, 255);
         sk = (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)n;
     }
 }
@@ -341,9 +346,9 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
 template <int kHalo>
 __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in, int H, int W, int pitch,
                                                    int tiles_x, int tiles_y, int n, const uint8_t* __restrict__ act_in,
-                                                   uint8_t* __restrict__ act_out, uint8_t* __restrict__ wasdead,
+                                                   uint8_t* __restrict__ act_out, uint8_t* __restrict__ qrun,
                                                    int* __restrict__ list, int* __restrict__ count,
-                                                   float* __restrict__ out, int out_is_prev_in,
+                                                   float* __restrict__ out, int out_age,
                                                    float* __restrict__ all_out, size_t all_stride,
                                                    uint8_t* __restrict__ seg_dirty, float* __restrict__ zero_base,
                                                    int zero_slots, int frozen,
@@ -354,8 +359,8 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
     unsigned long long sk = 0ull;
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
     if (tile < tiles_x * tiles_y)
-        fwd_tile<kHalo>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out, wasdead, list, count, out,
-                        out_is_prev_in, all_out, all_stride, seg_dirty, zero_base, zero_slots, frozen, skipped, tile,
+        fwd_tile<kHalo>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out, qrun, list, count, out,
+                        out_age, all_out, all_stride, seg_dirty, zero_base, zero_slots, frozen, skipped, tile,
                         threadIdx.x & 31, sk);
     block_count(skipped, s_sk, sk);
 }
@@ -386,21 +391,21 @@ int diff_blocked_tiles(int halo, int H, int pitch) {
     return ((pitch + inner - 1) / inner) * ((H + inner - 1) / inner);
 }
 
-void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* act, uint8_t* wasdead,
+void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* act, uint8_t* qrun,
                          cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int ntiles = diff_blocked_tiles(halo, H, pitch);
     const int blocks = (ntiles + 7) / 8;  // one warp per tile
     if (halo == 4)
-        k_fwd_act_init<4><<<blocks, 256, 0, s>>>(ab, H, pitch, tiles_x, ntiles, act, wasdead);
+        k_fwd_act_init<4><<<blocks, 256, 0, s>>>(ab, H, pitch, tiles_x, ntiles, act, qrun);
     else
-        k_fwd_act_init<8><<<blocks, 256, 0, s>>>(ab, H, pitch, tiles_x, ntiles, act, wasdead);
+        k_fwd_act_init<8><<<blocks, 256, 0, s>>>(ab, H, pitch, tiles_x, ntiles, act, qrun);
 }
 
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
-                      uint8_t* act_out, uint8_t* wasdead, int* tile_list, int* tile_count, float* out,
-                      bool out_is_prev_in, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
+                      uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
+                      int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
                       int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
@@ -408,12 +413,12 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
     cudaMemsetAsync(tile_count, 0, sizeof(int), s);
     if (halo == 4)
         k_fwd_tiles<4><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
-                                                         wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
+                                                         qrun, tile_list, tile_count, out, out_age,
                                                          all_out, all_stride, seg_dirty, zero_base, zero_slots,
                                                          frozen ? 1 : 0, skipped);
     else
         k_fwd_tiles<8><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
-                                                         wasdead, tile_list, tile_count, out, out_is_prev_in ? 1 : 0,
+                                                         qrun, tile_list, tile_count, out, out_age,
                                                          all_out, all_stride, seg_dirty, zero_base, zero_slots,
                                                          frozen ? 1 : 0, skipped);
 }

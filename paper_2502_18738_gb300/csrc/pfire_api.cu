@@ -133,10 +133,11 @@ struct pf_ctx {
     // tile activity of the blocked forward (b > 0 in a tile's interior), carried along a
     // chain of launches: act ping-pong, quiescent-last-launch flags, live list (count: dflags[9])
     uint8_t* fact[2] = {nullptr, nullptr};
-    uint8_t* fwasdead = nullptr;
+    uint8_t* fqrun = nullptr;  // per tile: quiescent streak along the chain (k_fwd_tiles)
     int* flist = nullptr;
     const float* fl_state = nullptr;    // the state fact[fl_par] describes (nullptr: none)
-    const float* fl_prev_in = nullptr;  // input of the chain's previous launch
+    int fl_launch = 0;                  // launches of the chain so far
+    int fl_in_at[2] = {-1, -1};         // launch whose input work[x] last was (-1: none)
     int fl_par = 0;
     int fl_halo = 0;
     // the tile activity at the end of every launch of a taped (K = 1) forward or of a
@@ -454,16 +455,22 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
     if (ctx->fl_state != in || ctx->fl_halo != halo) {
         {
             LaunchScope ls(ctx, K_FTILES);
-            launch_fwd_act_init(halo, in, ctx->H, ctx->P, ctx->fact[ctx->fl_par], ctx->fwasdead, ctx->st);
+            launch_fwd_act_init(halo, in, ctx->H, ctx->P, ctx->fact[ctx->fl_par], ctx->fqrun, ctx->st);
         }
         ctx->fl_halo = halo;
-        ctx->fl_prev_in = nullptr;
+        ctx->fl_launch = 0;
+        ctx->fl_in_at[0] = ctx->fl_in_at[1] = -1;
     }
     const size_t stride = 2 * plane_elems(ctx);
+    // out, if a work buffer, holds the input state of the launch it last was the input of
+    // (each launch's output becomes the next one's input, and is complete after it)
+    int out_age = 0;
+    for (int x = 0; x < 2; ++x)
+        if (out && out == ctx->work[x] && ctx->fl_in_at[x] >= 0) out_age = ctx->fl_launch - ctx->fl_in_at[x];
     {
         LaunchScope ls(ctx, K_FTILES);
         launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
-                         ctx->fwasdead, ctx->flist, ctx->dflags + 9, out, out && out == ctx->fl_prev_in, all_out,
+                         ctx->fqrun, ctx->flist, ctx->dflags + 9, out, out_age, all_out,
                          stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_buf + stride : nullptr,
                          ctx->seg_cap - 1, seg && frozen && halo == 8, ctx->dskip + K_FBLK, ctx->st);
     }
@@ -475,7 +482,9 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
     }
     ctx->fl_par ^= 1;
     ctx->fl_state = out ? out : all_out + (size_t)(n - 1) * stride;
-    ctx->fl_prev_in = in;
+    for (int x = 0; x < 2; ++x)
+        if (in == ctx->work[x]) ctx->fl_in_at[x] = ctx->fl_launch;
+    ctx->fl_launch++;
     if (ctx->actrec_on && end_step >= 0 && halo == 8) {
         int rc = actrec_push(ctx, end_step);
         if (rc) return rc;
@@ -628,8 +637,12 @@ int diff_steps(pf_ctx* ctx, int T) {
             if (rc) return rc;
             ctx->ckpts.push_back({t + n, s});
             out = slot_ptr(ctx, s);
-        } else {
+        } else if (ctx->cur_ab == ctx->work[0] || ctx->cur_ab == ctx->work[1]) {
             out = (ctx->cur_ab == ctx->work[0]) ? ctx->work[1] : ctx->work[0];
+        } else {
+            // the state is in a checkpoint slot: the work buffer that was an input most
+            // recently holds the most quiescent tiles' states already
+            out = ctx->fl_in_at[1] > ctx->fl_in_at[0] ? ctx->work[1] : ctx->work[0];
         }
         if (kern == 2) {
             if ((rc = diff_blocked_launch(ctx, ctx->cur_ab, ctx->pc, n, out, all_out, false,
@@ -815,7 +828,7 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
             const size_t nt = (size_t)std::max(diff_blocked_tiles(8, H, ctx->P), diff_blocked_tiles(4, H, ctx->P));
             ALLOC(ctx->fact[0], nt);
             ALLOC(ctx->fact[1], nt);
-            ALLOC(ctx->fwasdead, nt);
+            ALLOC(ctx->fqrun, nt);
             ALLOC(ctx->flist, nt * sizeof(int));
         }
         if (cudaMemsetAsync(ctx->work[0], 0, diff_state_bytes(ctx), ctx->st) != cudaSuccess) goto cuda_failed;
