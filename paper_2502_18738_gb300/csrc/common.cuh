@@ -102,6 +102,10 @@ struct PrepArgs {
     const uint8_t* burnable;                 // dense H*W, nullable
     const float* slope;                      // dense [H][W][3][3] degrees (replaces E), nullable
     float p_h, c1, c2, a, l;
+    // reach mask (nullable, prep only): q is computed in the 32 x 32 cell blocks whose
+    // byte reach[(r / 32) * reach_bw + c / 32] is set and left as it is elsewhere
+    const uint8_t* reach;
+    int reach_bw;
     // derived on the host in FP64 and split into hi + lo floats:
     // a * 180/pi, 1/l and 1/(sqrt(2) l)
     float adeg_hi, adeg_lo, ikl_e_hi, ikl_e_lo, ikl_d_hi, ikl_d_lo;
@@ -110,10 +114,17 @@ struct PrepArgs {
 void prep_derive(PrepArgs& g);
 
 void launch_prep(const PrepArgs& g, float* q, cudaStream_t s);
+// Reach mask of a differentiable state ab ([2][H][pitch], encoded a then b) over 32 x 32
+// cell blocks (ceil(H/32) x ceil(W/32) bytes, row-major): reach[B] = 1 iff a block within
+// Chebyshev block distance `radius` of B holds a cell with a > 0 or b > 0. tmp: scratch
+// of the same size.
+int prep_reach_bytes(int H, int W);
+void launch_prep_reach(const float* ab, int H, int W, int pitch, int radius, uint8_t* tmp, uint8_t* reach,
+                       cudaStream_t s);
 // dL/dq -> per-block FP64 partials of dL/d(p_h, c1, c2, a) (partials[nblk][4]) and
-// accumulation of per-cell gradients (dense H*W, nullable).
+// accumulation of per-cell gradients (dense H*W, nullable). Gq is left all zeros.
 int prep_adjoint_blocks(int H, int W);
-void launch_prep_adjoint(const PrepArgs& g, const float* Gq, double* partials, float* gpveg,
+void launch_prep_adjoint(const PrepArgs& g, float* Gq, double* partials, float* gpveg,
                          float* gpden, cudaStream_t s);
 // acc[0..3] += fixed-order FP64 sum of partials[nblk][4]
 void launch_reduce_partials(const double* partials, int nblk, double* acc, cudaStream_t s);

@@ -127,6 +127,9 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs g, float* __restrict__ q)
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
     if (r >= g.H || c >= g.pitch) return;
+    // outside the reach mask (and in the padding columns, which hold zeros) q is not read
+    // where it matters: keep what the buffer holds
+    if (g.reach && (c >= g.W || !g.reach[(r >> 5) * g.reach_bw + (c >> 5)])) return;
     const size_t plane = (size_t)g.H * g.pitch;
     float* qo = q + (size_t)r * g.pitch + c;
     if (c >= g.W || (g.burnable && g.burnable[(size_t)r * g.W + c] == 0)) {
@@ -143,6 +146,40 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs g, float* __restrict__ q)
     }
 }
 
+// One warp per 32 x 32 block, a lane per column: whether any a or b bit is set (b's sign
+// bit ignored, as -0 is no fire).
+__global__ void __launch_bounds__(256) k_reach_any(const float* __restrict__ ab, int H, int W, int pitch, int bw,
+                                                   int nblk, uint8_t* __restrict__ any) {
+    const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (b >= nblk) return;
+    const int r0 = (b / bw) * 32, c = (b % bw) * 32 + lane;
+    const int r1 = min(r0 + 32, H);
+    const size_t plane = (size_t)H * pitch;
+    uint32_t v = 0u;
+    if (c < W)
+        for (int r = r0; r < r1; ++r) {
+            v |= __float_as_uint(__ldg(ab + (size_t)r * pitch + c));
+            v |= __float_as_uint(__ldg(ab + plane + (size_t)r * pitch + c)) & 0x7fffffffu;
+        }
+    const bool hit = __any_sync(0xffffffffu, v != 0u);
+    if (lane == 0) any[b] = hit ? 1 : 0;
+}
+
+// One pass of a separable block dilation: out[B] = OR of in over the blocks within
+// `radius` of B along rows (horizontal) or columns.
+__global__ void __launch_bounds__(256) k_reach_dilate(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                                                      int bh, int bw, int radius, int horizontal) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= bh * bw) return;
+    const int by = i / bw, bx = i % bw;
+    uint8_t v = 0;
+    for (int k = -radius; k <= radius && !v; ++k) {
+        const int y = horizontal ? by : by + k, x = horizontal ? bx + k : bx;
+        if (y >= 0 && y < bh && x >= 0 && x < bw) v = in[y * bw + x];
+    }
+    out[i] = v;
+}
+
 constexpr int kAdjThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -155,7 +192,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // accumulated per thread in FP32 over the 8 directions of a cell and in FP64 across
 // cells, reduced by warp shuffles and then across the block, and written as one FP64
 // row per block. Per-cell gradients are accumulated into gpveg / gpden.
-__global__ void __launch_bounds__(kAdjThreads) k_prep_adjoint(PrepArgs g, const float* __restrict__ Gq,
+__global__ void __launch_bounds__(kAdjThreads) k_prep_adjoint(PrepArgs g, float* __restrict__ Gq,
                                                               double* __restrict__ partials,
                                                               float* __restrict__ gpveg,
                                                               float* __restrict__ gpden) {
@@ -164,10 +201,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_prep_adjoint(PrepArgs g, const 
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (size_t j = (size_t)blockIdx.x * kAdjThreads + threadIdx.x; j < HW; j += (size_t)gridDim.x * kAdjThreads) {
         const int r = (int)(j / g.W), c = (int)(j % g.W);
-        if (g.burnable && g.burnable[j] == 0) continue;
-        const float* gq = Gq + (size_t)r * g.pitch + c;
+        float* gq = Gq + (size_t)r * g.pitch + c;
         // cells no fire reached during the epoch have dL/dq = 0 in every direction and
-        // contribute nothing: skip their (transcendental-heavy) derivative evaluation
+        // contribute nothing: skip their (transcendental-heavy) derivative evaluation.
+        // The others are cleared for the next epoch here, so that Gq is all zeros again
+        // after the pass without a separate sweep over it.
         float gqv[8];
         bool any = false;
 #pragma unroll
@@ -176,6 +214,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_prep_adjoint(PrepArgs g, const 
             any |= gqv[d] != 0.0f;
         }
         if (!any) continue;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) gq[d * plane] = 0.0f;
+        if (g.burnable && g.burnable[j] == 0) continue;
         const CellFactors f = load_cell(g, r, c);
         float sh = 0.f, s1 = 0.f, s2 = 0.f, sa = 0.f, se = 0.f;
 #pragma unroll
@@ -250,6 +291,16 @@ void prep_derive(PrepArgs& g) {
     split(1.0 / (std::sqrt(2.0) * (double)g.l), g.ikl_d_hi, g.ikl_d_lo);
 }
 
+int prep_reach_bytes(int H, int W) { return ((H + 31) / 32) * ((W + 31) / 32); }
+
+void launch_prep_reach(const float* ab, int H, int W, int pitch, int radius, uint8_t* tmp, uint8_t* reach,
+                       cudaStream_t s) {
+    const int bh = (H + 31) / 32, bw = (W + 31) / 32, nb = bh * bw;
+    k_reach_any<<<(nb + 7) / 8, 256, 0, s>>>(ab, H, W, pitch, bw, nb, reach);
+    k_reach_dilate<<<(nb + 255) / 256, 256, 0, s>>>(reach, tmp, bh, bw, radius, 1);
+    k_reach_dilate<<<(nb + 255) / 256, 256, 0, s>>>(tmp, reach, bh, bw, radius, 0);
+}
+
 void launch_prep(const PrepArgs& g, float* q, cudaStream_t s) {
     dim3 blk(64, 4);
     dim3 grd((g.pitch + blk.x - 1) / blk.x, (g.H + blk.y - 1) / blk.y);
@@ -263,7 +314,7 @@ int prep_adjoint_blocks(int H, int W) {
     return (int)(want < cap ? (want ? want : 1) : cap);
 }
 
-void launch_prep_adjoint(const PrepArgs& g, const float* Gq, double* partials, float* gpveg, float* gpden,
+void launch_prep_adjoint(const PrepArgs& g, float* Gq, double* partials, float* gpveg, float* gpden,
                          cudaStream_t s) {
     const int nblk = prep_adjoint_blocks(g.H, g.W);
     k_prep_adjoint<<<nblk, kAdjThreads, 0, s>>>(g, Gq, partials, gpveg, gpden);

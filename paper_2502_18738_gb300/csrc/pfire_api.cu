@@ -91,6 +91,11 @@ struct pf_ctx {
     // the epochs fit in 30% of the free memory), with the version each was made at
     std::vector<float*> qcache;
     std::vector<long> qcache_ver;
+    // differentiable form: a q computed under a reach mask is valid for the steps before
+    // q_until (qcache_until[e] for the cached ones) of the trajectory it was made on
+    std::vector<int> qcache_until;
+    int q_until = 0x7fffffff;
+    uint8_t* qreach = nullptr;  // reach mask and its scratch (2 x prep_reach_bytes)
     bool qcache_on = false;
     long q_key_epoch = -1;
     long q_key_version = -1;
@@ -351,33 +356,67 @@ int use_q_buffer(pf_ctx* ctx, float* buf) {
     return PF_OK;
 }
 
-int ensure_q(pf_ctx* ctx, int e) {
+// q of wind epoch e, valid for the steps before `until` of the current trajectory. In the
+// differentiable form a bounded `until` lets prep skip the cells nothing reads before
+// then: the region a > 0 grows by at most one cell per step, and every kernel reads q
+// only within a few tiles (at most 128 cells) of a cell with a > 0 (the blocked kernels'
+// tile regions) or where a burning neighbour multiplies it (elsewhere it multiplies a
+// zero). So q is computed only in the 32 x 32 blocks within (until - step) + 160 cells
+// of the current a > 0 cells. The other cells keep the buffer's finite values: q buffers
+// are zeroed when allocated and only ever receive q values.
+int ensure_q(pf_ctx* ctx, int e, int until = 0x7fffffff) {
     int rc;
+    const bool masked = ctx->form == PF_DIFF && until != 0x7fffffff && ctx->cur_ab != nullptr;
+    if (!masked) until = 0x7fffffff;
     // a taped forward keeps every epoch's q for the adjoint when the cache is on
     const bool cache = ctx->qcache_on && ctx->tape_valid && e < (int)ctx->qcache.size();
-    if (cache && ctx->qcache[e] && ctx->qcache_ver[e] == ctx->version) {
+    if (cache && ctx->qcache[e] && ctx->qcache_ver[e] == ctx->version && until <= ctx->qcache_until[e]) {
         if ((rc = use_q_buffer(ctx, ctx->qcache[e]))) return rc;
         ctx->q_key_epoch = e;
         ctx->q_key_version = ctx->version;
+        ctx->q_until = ctx->qcache_until[e];
         return PF_OK;
     }
     if (cache && !ctx->qcache[e]) {
         void* p;
-        if (dalloc(ctx, &p, 8 * plane_elems(ctx) * sizeof(float)) == PF_OK) ctx->qcache[e] = (float*)p;
-        else cudaGetLastError();
+        if (dalloc(ctx, &p, 8 * plane_elems(ctx) * sizeof(float)) == PF_OK) {
+            ctx->qcache[e] = (float*)p;
+            CK(cudaMemsetAsync(p, 0, 8 * plane_elems(ctx) * sizeof(float), ctx->st));
+        } else {
+            cudaGetLastError();
+        }
     }
     float* dst = (cache && ctx->qcache[e]) ? ctx->qcache[e] : ctx->q_own;
-    if (ctx->q == dst && ctx->q_key_epoch == e && ctx->q_key_version == ctx->version) return PF_OK;
+    if (ctx->q == dst && ctx->q_key_epoch == e && ctx->q_key_version == ctx->version && until <= ctx->q_until)
+        return PF_OK;
     if ((rc = use_q_buffer(ctx, dst))) return rc;
+    PrepArgs g = prep_args(ctx, e, false);
     {
         LaunchScope ls(ctx, K_PREP);
-        launch_prep(prep_args(ctx, e, false), ctx->q, ctx->st);
+        if (masked) {
+            const int nb = prep_reach_bytes(ctx->H, ctx->W);
+            if (!ctx->qreach) {
+                void* p;
+                if ((rc = dalloc(ctx, &p, 2 * (size_t)nb))) return rc;
+                ctx->qreach = (uint8_t*)p;
+            }
+            const long reach = (long)(until - ctx->step) + 160;
+            const int radius = (int)std::min<long>((reach + 31) / 32 + 1, 1L << 20);
+            launch_prep_reach(ctx->cur_ab, ctx->H, ctx->W, ctx->P, radius, ctx->qreach + nb, ctx->qreach, ctx->st);
+            g.reach = ctx->qreach;
+            g.reach_bw = (ctx->W + 31) / 32;
+        }
+        launch_prep(g, ctx->q, ctx->st);
     }
     rc = check_launch(ctx, "prep");
     if (rc) return rc;
-    if (dst != ctx->q_own) ctx->qcache_ver[e] = ctx->version;
+    if (dst != ctx->q_own) {
+        ctx->qcache_ver[e] = ctx->version;
+        ctx->qcache_until[e] = until;
+    }
     ctx->q_key_epoch = e;
     ctx->q_key_version = ctx->version;
+    ctx->q_until = until;
     return PF_OK;
 }
 
@@ -594,6 +633,7 @@ int choose_K(pf_ctx* ctx, int T) {
     if ((int)ctx->qcache.size() < ne) {
         ctx->qcache.resize(ne, nullptr);
         ctx->qcache_ver.resize(ne, -1);
+        ctx->qcache_until.resize(ne, 0);
     }
     const double budget = 0.6 * (avail + (double)ctx->arena_cap * sb) - (ctx->qcache_on ? qbytes - cached : 0.0);
     if ((double)(T + 1 + ne) * sb <= budget) return 1;  // keep every state: no recomputation
@@ -618,7 +658,7 @@ int diff_steps(pf_ctx* ctx, int T) {
     const bool all_states = ctx->tape_valid && ctx->K == 1;
     while (ctx->step < end) {
         const int t = ctx->step;
-        int rc = ensure_q(ctx, epoch_of(ctx, t));
+        int rc = ensure_q(ctx, epoch_of(ctx, t), std::min(end, next_epoch_start(ctx, t)));
         if (rc) return rc;
         int n = 1;
         if (kern == 2) {
@@ -796,6 +836,7 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
     } while (0)
     ALLOC(ctx->q, 8 * pe * sizeof(float));
     ctx->q_own = ctx->q;
+    if (cudaMemsetAsync(ctx->q, 0, 8 * pe * sizeof(float), ctx->st) != cudaSuccess) goto cuda_failed;
     ALLOC(ctx->dflags, 16 * sizeof(int));
     ALLOC(ctx->dskip, K_NKINDS * sizeof(unsigned long long));
     if (cudaMallocHost((void**)&ctx->hflags, 16 * sizeof(int)) != cudaSuccess) {
@@ -1200,6 +1241,7 @@ int pf_set_state(pf_ctx* ctx, int step, const void* S) {
     if (!S || step < 0) return fail(ctx, PF_EINVAL, "pf_set_state: NULL state or negative step");
     tape_reset(ctx);
     ctx->dca_valid = false;
+    ctx->version++;  // a q computed under a reach mask holds for the trajectory it was made on
     if (ctx->form == PF_DISCRETE) {
         int rc = validate_states(ctx, (const uint8_t*)S, (size_t)ctx->R * ctx->H * ctx->W);
         if (rc) return rc;
@@ -1221,7 +1263,7 @@ int pf_set_state(pf_ctx* ctx, int step, const void* S) {
 
 int pf_ignition_map(pf_ctx* ctx, float* P_out) {
     if (!ctx || !P_out) return fail(ctx, PF_EINVAL, "pf_ignition_map: NULL argument");
-    int rc = ensure_q(ctx, epoch_of(ctx, ctx->step));
+    int rc = ensure_q(ctx, epoch_of(ctx, ctx->step), ctx->step + 1);
     if (rc) return rc;
     {
         LaunchScope ls(ctx, K_MISC);
@@ -1313,10 +1355,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             LaunchScope ls(ctx, K_RED);
             launch_reduce_partials(ctx->partials, nblk, ctx->gacc, ctx->st);
         }
-        if ((r = check_launch(ctx, "fp64 reduction"))) return r;
-        if (cudaMemsetAsync(ctx->Gq, 0, 8 * pe * sizeof(float), ctx->st) != cudaSuccess)
-            return fail(ctx, PF_ECUDA, "memset Gq failed");
-        return PF_OK;
+        return check_launch(ctx, "fp64 reduction");  // prep_adjoint left Gq zeroed
     };
     // switch q (and the dL/dq accumulator) to the epoch of step t
     auto enter_epoch = [&](int t) -> int {
@@ -1556,10 +1595,7 @@ int pf_backward_dca(pf_ctx* ctx, const float* dL_dacc, const uint8_t* step_mask,
             LaunchScope ls(ctx, K_RED);
             launch_reduce_partials(ctx->partials, nblk, ctx->gacc, ctx->st);
         }
-        if ((r = check_launch(ctx, "fp64 reduction"))) return r;
-        if (cudaMemsetAsync(ctx->Gq, 0, 8 * pe * sizeof(float), ctx->st) != cudaSuccess)
-            return fail(ctx, PF_ECUDA, "memset Gq failed");
-        return PF_OK;
+        return check_launch(ctx, "fp64 reduction");  // prep_adjoint left Gq zeroed
     };
     // replay the trajectory (same Philox counters) with the plain step; at every attached
     // step add the gradient of the cells that ignite in it
