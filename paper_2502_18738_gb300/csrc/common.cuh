@@ -106,6 +106,10 @@ struct PrepArgs {
     // byte reach[(r / 32) * reach_bw + c / 32] is set and left as it is elsewhere
     const uint8_t* reach;
     int reach_bw;
+    // dL/dq tiles (nullable, prep adjoint only): dL/dq can be nonzero only in the 48 x 48
+    // tiles whose byte gq_dirty[(r / 48) * gq_tiles_x + c / 48] is set
+    const uint8_t* gq_dirty;
+    int gq_tiles_x;
     // derived on the host in FP64 and split into hi + lo floats:
     // a * 180/pi, 1/l and 1/(sqrt(2) l)
     float adeg_hi, adeg_lo, ikl_e_hi, ikl_e_lo, ikl_d_hi, ikl_d_lo;
@@ -183,10 +187,14 @@ void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* a
 // frozen (segment buffers only, launches aligned with the adjoint's): quiescent tiles get
 // kFrozen in act_out, and those with b = 0 in the 5 x 5 interiors around them write only
 // the launch's last slot (the next launch's input): every tile whose region reaches into
-// them is frozen too and reads its first slot instead of the intermediate ones.
+// them is frozen too and reads its first slot instead of the intermediate ones. With
+// slot0 (the segment's first state, slot 0 of the buffer) as well, those with b = 0 in
+// the 7 x 7 interiors and no change since slot 0 in the 5 x 5 write nothing (kStale; see
+// k_fwd_tiles).
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
-                      int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
+                      int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, const float* slot0,
+                      float* zero_base,
                       int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s);
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
                          int n, const int* tile_list, const int* tile_count, float* out, float* all_out,
@@ -206,9 +214,17 @@ constexpr uint8_t kActB = 1, kActA = 2;
 // interiors around the tile at the launch's first state, so the tile's region is
 // constant over the launch's steps
 constexpr uint8_t kFrozen = 4;
+// Segment recompute (aligned launches): kQb: the tile was quiescent in every launch of the
+// segment before this one (its state at the launch's input is the segment's first state,
+// slot 0); kQt: ... and in this one too; kStale: the tile's state is not in this launch's
+// last slot (it skipped the write; see k_fwd_tiles).
+constexpr uint8_t kQb = 8, kQt = 16, kStale = 32;
 // an adjoint tile-list entry with this bit reads the state of its launch's first step
-// for every step (its region is constant over the launch)
+// for every step (its region is constant over the launch); with kTileCkptBit as well it
+// reads it from slot 0, the segment's first state (the 3 x 3 tiles around it are kQb)
 constexpr int kTileFrozenBit = 1 << 30;
+constexpr int kTileCkptBit = 1 << 29;
+constexpr int kTileIndexMask = kTileCkptBit - 1;
 
 // Adds a block's per-thread counts to a per-launch counter with one global atomic per
 // block (every tile of a launch would otherwise hit the same address). s: a __shared__
@@ -232,7 +248,8 @@ int adjoint_blocked_max_steps();
 int adjoint_blocked_configure();
 int adjoint_blocked_tiles(int H, int pitch);
 void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
-                          int* tile_list, int* tile_count, unsigned long long* skipped, cudaStream_t s);
+                          int* tile_list, int* tile_count, uint8_t* gq_dirty, unsigned long long* skipped,
+                          cudaStream_t s);
 // The same pre-pass from the forward's tile activity at a state s >= t1 - 1 (a never
 // decreases, so a tile with kActA in none of the 3 x 3 interiors around it has a = 0 in
 // its region at t1 - 1) instead of the state itself; a quiescent tile's lambda and sigma
@@ -240,9 +257,12 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
 // use_frozen: the flags come from a recompute launch aligned with this adjoint launch;
 // tiles recorded kFrozen are listed with kTileFrozenBit (their interior cell-steps are
 // added to frozen_steps, nullable).
+// Both pre-passes set gq_dirty[tile] (nullable) for every listed tile that may add to dL/dq
+// (the frozen ones add nothing).
 void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
                                 uint8_t* deadcnt, int* tile_list, int* tile_count, bool use_frozen,
-                                unsigned long long* skipped, unsigned long long* frozen_steps, cudaStream_t s);
+                                uint8_t* gq_dirty, unsigned long long* skipped, unsigned long long* frozen_steps,
+                                cudaStream_t s);
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
                             float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int l = i / n, m = i % n;
         int r0, c0;
         const int e = tiles[(int)blockIdx.x + l * (int)gridDim.x];
-        origin(e & ~kTileFrozenBit, tiles_x, r0, c0);
+        origin(e & kTileIndexMask, tiles_x, r0, c0);
         const int s = i & 1;
         if ((e & kTileFrozenBit) && m > 0) {
             // a frozen tile's region is constant over the launch: its steps read only the
@@ -102,12 +102,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_arrive_expect_tx(&sbar[s], 0u);
             return;
         }
+        // a frozen tile reads the launch's first state, from state 0 when its region has
+        // not changed since then (the recompute may have skipped writing it later)
+        const int z = (e & kTileFrozenBit) ? ((e & kTileCkptBit) ? 0 : zlast - (n - 1)) : zlast - m;
         mbar_arrive_expect_tx(&sbar[s], (uint32_t)(2 * kPlane * sizeof(float)));
-        tma_load_3d(sm.st[s], &tst, &sbar[s], c0, r0, 2 * (zlast - ((e & kTileFrozenBit) ? n - 1 : m)));
+        tma_load_3d(sm.st[s], &tst, &sbar[s], c0, r0, 2 * z);
     };
     auto issue_q = [&](int l) {
         int r0, c0;
-        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x] & ~kTileFrozenBit, tiles_x, r0, c0);
+        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x] & kTileIndexMask, tiles_x, r0, c0);
         mbar_arrive_expect_tx(&qbar, (uint32_t)(8 * kPlane * sizeof(float)));
         tma_load_3d(sm.q, &tq, &qbar, c0, r0, 0);
     };
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int r0, c0;
         const int ent = tiles[(int)blockIdx.x + l * (int)gridDim.x];
         const bool frz = (ent & kTileFrozenBit) != 0;  // uniform across the CTA
-        origin(ent & ~kTileFrozenBit, tiles_x, r0, c0);
+        origin(ent & kTileIndexMask, tiles_x, r0, c0);
         if (!__syncthreads_and(mbar_wait_bounded(&qbar, (uint32_t)(l & 1)))) {
             failed = true;
             break;
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 __device__ __forceinline__ void adjoint_tile(const float* __restrict__ A, int H, int W, int pitch,
                                                        int tiles_x, int ntiles, int n, int* __restrict__ list,
                                                        int* __restrict__ count, float* __restrict__ lam_out,
-                                                       uint8_t* __restrict__ sig_out,
+                                                       uint8_t* __restrict__ sig_out, uint8_t* __restrict__ gq_dirty,
                                                        unsigned long long* __restrict__ skipped, int tile, int lane,
                                                        unsigned long long& sk) {
     int r0, c0;
@@ -483,7 +486,10 @@ __device__ __forceinline__ void adjoint_tile(const float* __restrict__ A, int H,
         any |= v.x | v.y | v.z | v.w;
     }
     if (__any_sync(0xffffffffu, any != 0u)) {
-        if (lane == 0) list[atomicAdd(count, 1)] = tile;
+        if (lane == 0) {
+            list[atomicAdd(count, 1)] = tile;
+            if (gq_dirty) gq_dirty[tile] = 1;
+        }
         return;
     }
     const size_t gplane = (size_t)H * pitch;
@@ -503,7 +509,7 @@ __device__ __forceinline__ void adjoint_tile(const float* __restrict__ A, int H,
 __global__ void __launch_bounds__(256) k_adjoint_tiles(const float* __restrict__ A, int H, int W, int pitch,
                                                        int tiles_x, int ntiles, int n, int* __restrict__ list,
                                                        int* __restrict__ count, float* __restrict__ lam_out,
-                                                       uint8_t* __restrict__ sig_out,
+                                                       uint8_t* __restrict__ sig_out, uint8_t* __restrict__ gq_dirty,
                                                        unsigned long long* __restrict__ skipped) {
     __shared__ unsigned long long s_sk;
     if (threadIdx.x == 0) s_sk = 0ull;
@@ -511,7 +517,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles(const float* __restrict__
     unsigned long long sk = 0ull;
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
     if (tile < ntiles)
-        adjoint_tile(A, H, W, pitch, tiles_x, ntiles, n, list, count, lam_out, sig_out, skipped, tile,
+        adjoint_tile(A, H, W, pitch, tiles_x, ntiles, n, list, count, lam_out, sig_out, gq_dirty, skipped, tile,
                      threadIdx.x & 31, sk);
     block_count(skipped, s_sk, sk);
 }
@@ -521,23 +527,30 @@ __device__ __forceinline__ void adjoint_tile_flags(const uint8_t* __restrict__ a
                                                              int* __restrict__ count, float* __restrict__ lam_out,
                                                              uint8_t* __restrict__ sig_out,
                                                              uint8_t* __restrict__ deadcnt, int use_frozen,
+                                                             uint8_t* __restrict__ gq_dirty,
                                                              unsigned long long* __restrict__ skipped,
                                                              unsigned long long* __restrict__ frozen_steps, int tile,
                                                              int lane, unsigned long long& sk,
                                                              unsigned long long& fz_steps) {
     const int ty = tile / tiles_x, tx = tile % tiles_x;
-    // the 3 x 3 flags around the tile, one per lane, OR-reduced
-    uint32_t f = 0u;
+    // the 3 x 3 flags around the tile, one per lane: OR-reduced, and whether all of them
+    // are unchanged since the segment's first state (kQb; outside the grid: yes)
+    uint32_t f = 0u, qb = 1u;
     if (lane < 9) {
         const int yy = ty + lane / 3 - 1, xx = tx + lane % 3 - 1;
-        if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) f = act[yy * tiles_x + xx];
+        if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) {
+            f = act[yy * tiles_x + xx];
+            qb = (f & kQb) ? 1u : 0u;
+        }
     }
     const uint32_t around = __reduce_or_sync(0xffffffffu, f);
+    const bool all_qb = __reduce_and_sync(0xffffffffu, qb) != 0u;
     if (around & kActA) {
         if (lane == 0) {
             const bool fz = use_frozen && (act[tile] & kFrozen);
-            list[atomicAdd(count, 1)] = tile | (fz ? kTileFrozenBit : 0);
+            list[atomicAdd(count, 1)] = tile | (fz ? kTileFrozenBit : 0) | (fz && all_qb ? kTileCkptBit : 0);
             deadcnt[tile] = 0;
+            if (gq_dirty && !fz) gq_dirty[tile] = 1;
             if (fz) {
                 int r0, c0;
                 origin(tile, tiles_x, r0, c0);
@@ -575,6 +588,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __re
                                                              int* __restrict__ count, float* __restrict__ lam_out,
                                                              uint8_t* __restrict__ sig_out,
                                                              uint8_t* __restrict__ deadcnt, int use_frozen,
+                                                             uint8_t* __restrict__ gq_dirty,
                                                              unsigned long long* __restrict__ skipped,
                                                              unsigned long long* __restrict__ frozen_steps) {
     __shared__ unsigned long long s_sk, s_fz;
@@ -584,7 +598,7 @@ __global__ void __launch_bounds__(256) k_adjoint_tiles_flags(const uint8_t* __re
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
     if (tile < tiles_x * tiles_y)
         adjoint_tile_flags(act, H, W, pitch, tiles_x, tiles_y, n, list, count, lam_out, sig_out, deadcnt, use_frozen,
-                           skipped, frozen_steps, tile, threadIdx.x & 31, sk, fz);
+                           gq_dirty, skipped, frozen_steps, tile, threadIdx.x & 31, sk, fz);
     block_count(skipped, s_sk, sk);
     block_count(frozen_steps, s_fz, fz);
 }
@@ -609,23 +623,25 @@ int adjoint_blocked_configure() {
 int adjoint_blocked_tiles(int H, int pitch) { return ((pitch + kIC - 1) / kIC) * ((H + kIR - 1) / kIR); }
 
 void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
-                          int* tile_list, int* tile_count, unsigned long long* skipped, cudaStream_t s) {
+                          int* tile_list, int* tile_count, uint8_t* gq_dirty, unsigned long long* skipped,
+                          cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
     cudaMemsetAsync(tile_count, 0, sizeof(int), s);
     const int ntiles = adjoint_blocked_tiles(H, pitch);
     k_adjoint_tiles<<<(ntiles + 7) / 8, 256, 0, s>>>(A_latest, H, W, pitch, tiles_x, ntiles, n, tile_list, tile_count,
-                                                     lam_out, sig_out, skipped);
+                                                     lam_out, sig_out, gq_dirty, skipped);
 }
 
 void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int n, float* lam_out, uint8_t* sig_out,
                                 uint8_t* deadcnt, int* tile_list, int* tile_count, bool use_frozen,
-                                unsigned long long* skipped, unsigned long long* frozen_steps, cudaStream_t s) {
+                                uint8_t* gq_dirty, unsigned long long* skipped, unsigned long long* frozen_steps,
+                                cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC, tiles_y = (H + kIR - 1) / kIR;
     const int ntiles = tiles_x * tiles_y;
     cudaMemsetAsync(tile_count, 0, sizeof(int), s);
     k_adjoint_tiles_flags<<<(ntiles + 7) / 8, 256, 0, s>>>(act, H, W, pitch, tiles_x, tiles_y, n, tile_list, tile_count,
-                                                           lam_out, sig_out, deadcnt, use_frozen ? 1 : 0, skipped,
-                                                           frozen_steps);
+                                                           lam_out, sig_out, deadcnt, use_frozen ? 1 : 0, gq_dirty,
+                                                           skipped, frozen_steps);
 }
 
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         actB = __syncthreads_or(actB);
         actA = __syncthreads_or(actA);
-        if (tid == 0) act_out[tile] = (actA ? kActA : 0) | (actB ? kActB : 0);
+        if (tid == 0) act_out[tile] = (act_out[tile] & kQb) | (actA ? kActA : 0) | (actB ? kActB : 0);
     }
 }
 
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ 
     }
     const bool hasA = __any_sync(0xffffffffu, anyA != 0u), hasB = __any_sync(0xffffffffu, anyB != 0u);
     if (lane == 0) {
-        act[tile] = (hasA ? kActA : 0) | (hasB ? kActB : 0);
+        act[tile] = (hasA ? kActA : 0) | (hasB ? kActB : 0) | kQt;  // nothing happened yet
         qrun[tile] = 0;
     }
 }
@@ -256,6 +256,17 @@ __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ 
 // a = 0 in the 3 x 3 interiors around it is void (exactly zero in its whole region for
 // the whole launch); its slots only have to hold zeros, which they already do unless the
 // tile is dirty, in which case all of them are zeroed once.
+//
+// Aligned segment recompute (frozen != 0): quiescent tiles get kFrozen (their region is
+// constant over the launch). One with b = 0 in the 5 x 5 interiors around it writes only
+// the launch's last slot (the next launch's input): every tile whose region reaches into
+// it is frozen too and is read at its first slot only. One with b = 0 in the 7 x 7
+// interiors whose 5 x 5 tiles have all been quiescent since the segment's start (kQt)
+// writes nothing and is marked kStale. Then every tile whose region reaches into it is
+// quiescent in this launch and the next, and kQb (unchanged since slot 0) in the next.
+// So the adjoint reads those tiles' regions from slot0 (kTileCkptBit), which holds the
+// stale tile's state, and no live tile's region reaches it before it writes again. When
+// it does, it copies from slot0.
 template <int kHalo>
 __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, int W, int pitch,
                                                    int tiles_x, int tiles_y, int n, const uint8_t* __restrict__ act_in,
@@ -263,28 +274,40 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
                                                    int* __restrict__ list, int* __restrict__ count,
                                                    float* __restrict__ out, int out_age,
                                                    float* __restrict__ all_out, size_t all_stride,
-                                                   uint8_t* __restrict__ seg_dirty, float* __restrict__ zero_base,
-                                                   int zero_slots, int frozen,
+                                                   uint8_t* __restrict__ seg_dirty, const float* __restrict__ slot0,
+                                                   float* __restrict__ zero_base, int zero_slots, int frozen,
                                                    unsigned long long* __restrict__ skipped, int tile, int lane,
                                                    unsigned long long& sk) {
     constexpr int kI = kRT - 2 * kHalo;
     const int ty = tile / tiles_x, tx = tile % tiles_x;
-    // the 5 x 5 flags around the tile, one per lane (25 independent loads), OR-reduced
-    uint32_t f = 0u;
-    bool inner3 = false;
-    if (lane < 25) {
-        const int dy = lane / 5 - 2, dx = lane % 5 - 2;
+    // the 7 x 7 flags around the tile, two per lane (independent loads), reduced into the
+    // ORs over the 3 x 3, 5 x 5 and 7 x 7 tiles and the AND of kQt over the 5 x 5 (tiles
+    // outside the grid count as quiescent and empty)
+    uint32_t o3 = 0u, o5 = 0u, o7 = 0u, q5 = 1u;
+    for (int p = lane; p < 49; p += 32) {
+        const int dy = p / 7 - 3, dx = p % 7 - 3;
         const int yy = ty + dy, xx = tx + dx;
-        if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) f = act_in[yy * tiles_x + xx];
-        inner3 = dy >= -1 && dy <= 1 && dx >= -1 && dx <= 1;
+        const bool in_grid = yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x;
+        const uint32_t f = in_grid ? act_in[yy * tiles_x + xx] : 0u;
+        o7 |= f;
+        if (dy >= -2 && dy <= 2 && dx >= -2 && dx <= 2) {
+            o5 |= f;
+            if (in_grid && !(f & kQt)) q5 = 0u;
+        }
+        if (dy >= -1 && dy <= 1 && dx >= -1 && dx <= 1) o3 |= f;
     }
-    const uint32_t around5 = __reduce_or_sync(0xffffffffu, f);
-    const uint32_t around = __reduce_or_sync(0xffffffffu, inner3 ? f : 0u);
+    const uint32_t around = __reduce_or_sync(0xffffffffu, o3);
+    const uint32_t around5 = __reduce_or_sync(0xffffffffu, o5);
+    const uint32_t around7 = __reduce_or_sync(0xffffffffu, o7);
+    const bool qseg5 = __reduce_and_sync(0xffffffffu, q5) != 0u;
+    const uint32_t me = act_in[tile];
+    const uint8_t qb = (me & kQt) ? kQb : 0;  // quiescent in every earlier launch of the segment
     if (around & kActB) {
         if (lane == 0) {
             list[atomicAdd(count, 1)] = tile;
             qrun[tile] = 0;
             if (seg_dirty) seg_dirty[tile] = 1;
+            act_out[tile] = qb;  // k_diff_blocked adds the tile's activity
         }
         return;
     }
@@ -311,8 +334,13 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     } else if (seg_dirty && lane == 0) {
         seg_dirty[tile] = 1;
     }
-    // far from anything burning: only the last slot (the next launch's input) is read
+    // far from anything burning: only the last slot (the next launch's input) is read;
+    // farther still and unchanged since slot 0 around it: nothing is
     const bool last_only = frozen && write_all && !(around5 & kActB);
+    const bool stale = last_only && slot0 && !(around7 & kActB) && qseg5;
+    if (stale) write_all = false;
+    // a tile that skipped its last write takes its state from slot 0
+    const float* src = (frozen && slot0 && (me & kStale)) ? slot0 : in;
     const int qr = qrun[tile];
     const bool copy_out = out && !(out_age > 0 && qr >= out_age);
     if (copy_out || write_all) {
@@ -321,8 +349,8 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
             const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
             if (gr >= H || gc >= pitch) continue;
             const size_t j = (size_t)gr * pitch + gc;
-            const float4 a = __ldg(reinterpret_cast<const float4*>(in + j));
-            const float4 b = __ldg(reinterpret_cast<const float4*>(in + gplane + j));
+            const float4 a = __ldg(reinterpret_cast<const float4*>(src + j));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(src + gplane + j));
             if (copy_out) {
                 *reinterpret_cast<float4*>(out + j) = a;
                 *reinterpret_cast<float4*>(out + gplane + j) = b;
@@ -337,7 +365,7 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     }
     __syncwarp();  // qrun[tile] read by every lane before it changes
     if (lane == 0) {
-        act_out[tile] = (uint8_t)((act_in[tile] & kActA) | (frozen ? kFrozen : 0));
+        act_out[tile] = (uint8_t)((me & (kActA | kQt)) | qb | (frozen ? kFrozen : 0) | (stale ? kStale : 0));
         qrun[tile] = (uint8_t)min(qr + 1, 255);
         sk = (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)n;
     }
@@ -350,8 +378,8 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                                                    int* __restrict__ list, int* __restrict__ count,
                                                    float* __restrict__ out, int out_age,
                                                    float* __restrict__ all_out, size_t all_stride,
-                                                   uint8_t* __restrict__ seg_dirty, float* __restrict__ zero_base,
-                                                   int zero_slots, int frozen,
+                                                   uint8_t* __restrict__ seg_dirty, const float* __restrict__ slot0,
+                                                   float* __restrict__ zero_base, int zero_slots, int frozen,
                                                    unsigned long long* __restrict__ skipped) {
     __shared__ unsigned long long s_sk;
     if (threadIdx.x == 0) s_sk = 0ull;
@@ -360,7 +388,7 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
     if (tile < tiles_x * tiles_y)
         fwd_tile<kHalo>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out, qrun, list, count, out,
-                        out_age, all_out, all_stride, seg_dirty, zero_base, zero_slots, frozen, skipped, tile,
+                        out_age, all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots, frozen, skipped, tile,
                         threadIdx.x & 31, sk);
     block_count(skipped, s_sk, sk);
 }
@@ -405,8 +433,8 @@ void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* a
 
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
-                      int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, float* zero_base,
-                      int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s) {
+                      int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, const float* slot0,
+                      float* zero_base, int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int tiles_y = (H + inner - 1) / inner;
@@ -414,12 +442,12 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
     if (halo == 4)
         k_fwd_tiles<4><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          qrun, tile_list, tile_count, out, out_age,
-                                                         all_out, all_stride, seg_dirty, zero_base, zero_slots,
+                                                         all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots,
                                                          frozen ? 1 : 0, skipped);
     else
         k_fwd_tiles<8><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          qrun, tile_list, tile_count, out, out_age,
-                                                         all_out, all_stride, seg_dirty, zero_base, zero_slots,
+                                                         all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots,
                                                          frozen ? 1 : 0, skipped);
 }
 

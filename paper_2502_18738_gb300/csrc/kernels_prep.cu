@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_prep_adjoint(PrepArgs g, float*
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (size_t j = (size_t)blockIdx.x * kAdjThreads + threadIdx.x; j < HW; j += (size_t)gridDim.x * kAdjThreads) {
         const int r = (int)(j / g.W), c = (int)(j % g.W);
+        if (g.gq_dirty && !g.gq_dirty[(r / 48) * g.gq_tiles_x + c / 48]) continue;  // dL/dq = 0 here
         float* gq = Gq + (size_t)r * g.pitch + c;
         // cells no fire reached during the epoch have dL/dq = 0 in every direction and
         // contribute nothing: skip their (transcendental-heavy) derivative evaluation.

@@ -135,6 +135,7 @@ struct pf_ctx {
     int* hflags = nullptr;  // pinned mirror
     unsigned long long* dskip = nullptr;  // per kernel kind: cell-steps of skipped quiescent tiles
     int* tile_list = nullptr;             // live tiles of one blocked-adjoint launch (count: dflags[8])
+    uint8_t* gqdirty = nullptr;           // per adjoint tile: may hold nonzero dL/dq this epoch
     // tile activity of the blocked forward (b > 0 in a tile's interior), carried along a
     // chain of launches: act ping-pong, quiescent-last-launch flags, live list (count: dflags[9])
     uint8_t* fact[2] = {nullptr, nullptr};
@@ -510,7 +511,8 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
         LaunchScope ls(ctx, K_FTILES);
         launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
                          ctx->fqrun, ctx->flist, ctx->dflags + 9, out, out_age, all_out,
-                         stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_buf + stride : nullptr,
+                         stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_buf : nullptr,
+                         seg ? ctx->seg_buf + stride : nullptr,
                          ctx->seg_cap - 1, seg && frozen && halo == 8, ctx->dskip + K_FBLK, ctx->st);
     }
     {
@@ -865,6 +867,7 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
         ALLOC(ctx->burn, (size_t)H * W);
         ALLOC(ctx->tile_list, (size_t)adjoint_blocked_tiles(H, ctx->P) * sizeof(int));
         ALLOC(ctx->adeadcnt, (size_t)adjoint_blocked_tiles(H, ctx->P));
+        ALLOC(ctx->gqdirty, (size_t)adjoint_blocked_tiles(H, ctx->P));
         {
             const size_t nt = (size_t)std::max(diff_blocked_tiles(8, H, ctx->P), diff_blocked_tiles(4, H, ctx->P));
             ALLOC(ctx->fact[0], nt);
@@ -1339,18 +1342,30 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
     if (grad_pveg) CK(cudaMemsetAsync(grad_pveg, 0, cell_bytes, ctx->st));
     if (grad_pden) CK(cudaMemsetAsync(grad_pden, 0, cell_bytes, ctx->st));
     CK(cudaMemsetAsync(ctx->Gq, 0, 8 * pe * sizeof(float), ctx->st));
-    CK(cudaMemsetAsync(ctx->adeadcnt, 0, (size_t)adjoint_blocked_tiles(ctx->H, ctx->P), ctx->st));
+    const size_t ntiles_adj = (size_t)adjoint_blocked_tiles(ctx->H, ctx->P);
+    CK(cudaMemsetAsync(ctx->adeadcnt, 0, ntiles_adj, ctx->st));
+    CK(cudaMemsetAsync(ctx->gqdirty, 0, ntiles_adj, ctx->st));
 
     const int T_end = ctx->step;
     int lcur = 0;
     int cur_e = -1;
+    // the blocked adjoint's pre-passes mark the tiles that may add to dL/dq; a plain
+    // adjoint step may add anywhere
+    bool gq_anywhere = false;
     auto flush = [&](int e) -> int {
         {
             LaunchScope ls(ctx, K_PADJ);
-            launch_prep_adjoint(prep_args(ctx, e, true), ctx->Gq, ctx->partials, grad_pveg, grad_pden, ctx->st);
+            PrepArgs g = prep_args(ctx, e, true);
+            if (!gq_anywhere) {
+                g.gq_dirty = ctx->gqdirty;
+                g.gq_tiles_x = (ctx->P + 47) / 48;
+            }
+            launch_prep_adjoint(g, ctx->Gq, ctx->partials, grad_pveg, grad_pden, ctx->st);
         }
         int r = check_launch(ctx, "prep adjoint");
         if (r) return r;
+        CK(cudaMemsetAsync(ctx->gqdirty, 0, ntiles_adj, ctx->st));
+        gq_anywhere = false;
         {
             LaunchScope ls(ctx, K_RED);
             launch_reduce_partials(ctx->partials, nblk, ctx->gacc, ctx->st);
@@ -1403,12 +1418,12 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                                                    ctx->adeadcnt, ctx->tile_list, ctx->dflags + 8,
                                                    // aligned: the record is this launch's own recompute
                                                    // (a one-step launch reads one state anyway)
-                                                   align > 0,
+                                                   align > 0, ctx->gqdirty,
                                                    ctx->dskip + K_ABLK, ctx->dskip + K_ATILES, ctx->st);
                     else
                         launch_adjoint_tiles(buf + (size_t)(t1 - 1 - tbase) * selems, ctx->H, ctx->W, ctx->P, n,
                                              ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->tile_list, ctx->dflags + 8,
-                                             ctx->dskip + K_ABLK, ctx->st);
+                                             ctx->gqdirty, ctx->dskip + K_ABLK, ctx->st);
                 }
                 {
                     LaunchScope ls(ctx, K_ABLK, n);
@@ -1419,6 +1434,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                 if ((r = check_launch(ctx, "adjoint blocked"))) return r;
                 t1 -= n;
             } else {
+                gq_anywhere = true;
                 {
                     LaunchScope ls(ctx, K_ADJ);
                     launch_adjoint_step(ctx->H, ctx->W, ctx->P, pc, buf + (size_t)(t1 - 1 - tbase) * selems, ctx->q,
