@@ -238,7 +238,9 @@ __device__ __forceinline__ void block_count(unsigned long long* g, unsigned long
 
 // temporal-blocked adjoint with TMEM working set: n <= adjoint_blocked_max_steps() steps
 // t = t1-1 .. t1-n per launch. tst: 3-D map over a buffer of consecutive states
-// (pitch, H, 2 * nstates), box {64, 64, 2}; the state at t1-1-m is state index zlast-m.
+// (pitch, H, 2 * nstates), box {64, 64, 2}; the state at t1-1-m is state index zlast-m,
+// except state index 0, which is read through tst0 (a map of one state, the same box:
+// a checkpoint that is not copied into the buffer, or tst itself).
 // tq as for launch_diff_blocked. Gq is accumulated. Only the tiles listed by the
 // pre-pass launch_adjoint_tiles run: from A_latest, the encoded a plane of the state at
 // t1-1, it lists the tiles with a > 0 somewhere in their region (tile_list, capacity
@@ -263,7 +265,8 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
                                 uint8_t* deadcnt, int* tile_list, int* tile_count, bool use_frozen,
                                 uint8_t* gq_dirty, unsigned long long* skipped, unsigned long long* frozen_steps,
                                 cudaStream_t s);
-void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
+void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq, int H, int pitch,
+                            float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
                             float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,
                             cudaStream_t s);

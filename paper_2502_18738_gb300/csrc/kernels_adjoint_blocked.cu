@@ -55,7 +55,8 @@ __device__ __forceinline__ void origin(int tile, int tiles_x, int& r0, int& c0) 
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_adjoint_blocked(const __grid_constant__ CUtensorMap tst, const __grid_constant__ CUtensorMap tq, int H,
+    k_adjoint_blocked(const __grid_constant__ CUtensorMap tst, const __grid_constant__ CUtensorMap tst0,
+                      const __grid_constant__ CUtensorMap tq, int H,
                       int pitch, float pc, int zlast, int n, int tiles_x, const int* __restrict__ tiles,
                       const int* __restrict__ ntiles_live,
                       const float* __restrict__ lam_in, const uint8_t* __restrict__ sig_in,
@@ -106,7 +107,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // not changed since then (the recompute may have skipped writing it later)
         const int z = (e & kTileFrozenBit) ? ((e & kTileCkptBit) ? 0 : zlast - (n - 1)) : zlast - m;
         mbar_arrive_expect_tx(&sbar[s], (uint32_t)(2 * kPlane * sizeof(float)));
-        tma_load_3d(sm.st[s], &tst, &sbar[s], c0, r0, 2 * z);
+        if (z == 0)
+            tma_load_3d(sm.st[s], &tst0, &sbar[s], c0, r0, 0);
+        else
+            tma_load_3d(sm.st[s], &tst, &sbar[s], c0, r0, 2 * z);
     };
     auto issue_q = [&](int l) {
         int r0, c0;
@@ -644,14 +648,15 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
                                                            skipped, frozen_steps);
 }
 
-void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tq, int H, int pitch, float pc, int zlast,
+void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq, int H, int pitch,
+                            float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
                             float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,
                             cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
     const int ntiles = adjoint_blocked_tiles(H, pitch);
     const int grid = ntiles < nsm ? ntiles : nsm;
-    k_adjoint_blocked<<<grid, kThreads, adjoint_blocked_smem(), s>>>(*tst, *tq, H, pitch, pc, zlast, n, tiles_x,
+    k_adjoint_blocked<<<grid, kThreads, adjoint_blocked_smem(), s>>>(*tst, *tst0, *tq, H, pitch, pc, zlast, n, tiles_x,
                                                                      tile_list, tile_count, lam_in, sig_in, lam_out,
                                                                      sig_out, Gq, err);
 }

@@ -162,6 +162,7 @@ struct pf_ctx {
     float* seg_buf = nullptr;  // K-1 contiguous states (segment recompute)
     int seg_cap = 0;
     uint8_t* seg_dirty = nullptr;  // per forward tile: its interior may be nonzero in slots 1.. of seg_buf
+    const float* seg_slot0 = nullptr;  // the segment's first state (its checkpoint; slot 0 of seg_buf is unused)
     int seg_halo = 0;              // tile geometry seg_dirty refers to
     int TH = 64, KH = 16;
     pf_tuning tun{0, 0, 0, 0};
@@ -511,7 +512,7 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
         LaunchScope ls(ctx, K_FTILES);
         launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
                          ctx->fqrun, ctx->flist, ctx->dflags + 9, out, out_age, all_out,
-                         stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_buf : nullptr,
+                         stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_slot0 : nullptr,
                          seg ? ctx->seg_buf + stride : nullptr,
                          ctx->seg_cap - 1, seg && frozen && halo == 8, ctx->dskip + K_FBLK, ctx->st);
     }
@@ -1399,8 +1400,10 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
     // With `align` > 0 the launches are [t0 + align i, t0 + align (i + 1)) like the
     // segment's recompute launches, whose recorded tile flags then describe exactly the
     // states of each adjoint launch (kFrozen tiles read one state for all steps).
-    auto adjoint_run = [&](const float* buf, const CUtensorMap* tmap, int tbase, int t0, int t1,
-                           int align = 0) -> int {
+    // first / tmap0 (nullable): the state at tbase when it is not in buf (a checkpoint)
+    auto adjoint_run = [&](const float* buf, const CUtensorMap* tmap, int tbase, int t0, int t1, int align = 0,
+                           const float* first = nullptr, const CUtensorMap* tmap0 = nullptr) -> int {
+        auto state_at = [&](int t) { return (t == tbase && first) ? first : buf + (size_t)(t - tbase) * selems; };
         int r;
         while (t1 > t0) {
             if (tmap) {
@@ -1421,13 +1424,14 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                                                    align > 0, ctx->gqdirty,
                                                    ctx->dskip + K_ABLK, ctx->dskip + K_ATILES, ctx->st);
                     else
-                        launch_adjoint_tiles(buf + (size_t)(t1 - 1 - tbase) * selems, ctx->H, ctx->W, ctx->P, n,
+                        launch_adjoint_tiles(state_at(t1 - 1), ctx->H, ctx->W, ctx->P, n,
                                              ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->tile_list, ctx->dflags + 8,
                                              ctx->gqdirty, ctx->dskip + K_ABLK, ctx->st);
                 }
                 {
                     LaunchScope ls(ctx, K_ABLK, n);
-                    launch_adjoint_blocked(tmap, &ctx->tmapQ, ctx->H, ctx->P, pc, t1 - 1 - tbase, n, ctx->lam[lcur],
+                    launch_adjoint_blocked(tmap, tmap0 ? tmap0 : tmap, &ctx->tmapQ, ctx->H, ctx->P, pc, t1 - 1 - tbase,
+                                           n, ctx->lam[lcur],
                                            ctx->sig[lcur], ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->Gq,
                                            ctx->tile_list, ctx->dflags + 8, ctx->nsm, ctx->dflags, ctx->st);
                 }
@@ -1437,7 +1441,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                 gq_anywhere = true;
                 {
                     LaunchScope ls(ctx, K_ADJ);
-                    launch_adjoint_step(ctx->H, ctx->W, ctx->P, pc, buf + (size_t)(t1 - 1 - tbase) * selems, ctx->q,
+                    launch_adjoint_step(ctx->H, ctx->W, ctx->P, pc, state_at(t1 - 1), ctx->q,
                                         ctx->lam[lcur], ctx->sig[lcur], ctx->lam[1 - lcur], ctx->sig[1 - lcur],
                                         ctx->Gq, ctx->st);
                 }
@@ -1472,8 +1476,8 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             const int s1 = (si + 1 < (int)ctx->ckpts.size()) ? ctx->ckpts[si + 1].first : T_end;
             if (s1 <= s0) continue;
             if ((rc = enter_epoch(s0))) return rc;
-            // the segment's states s0 .. s1-1, consecutive in the segment buffer: the
-            // checkpoint copied to slot 0, the rest recomputed
+            // the segment's states s0 .. s1-1: the checkpoint itself, then the recomputed
+            // ones in slots 1.. of the segment buffer (slot 0 unused)
             float* seg = ctx->seg_buf;
             if (kern == 2) {
                 // blocked recompute: the slots hold zeros wherever seg_dirty is clear
@@ -1495,12 +1499,17 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             } else {
                 ctx->seg_halo = 0;  // the plain kernel writes every cell of the slots
             }
-            CK(cudaMemcpyAsync(seg, slot_ptr(ctx, ctx->ckpts[si].second), sbytes, cudaMemcpyDeviceToDevice, ctx->st));
+            const float* ck = slot_ptr(ctx, ctx->ckpts[si].second);
+            ctx->seg_slot0 = ck;
+            CUtensorMap tck;
+            if (adj_blocked && !encode_f32_3d(&tck, ck, ctx->P, ctx->H, 2, diff_blocked_box_cols(),
+                                              diff_blocked_box_rows(), 2))
+                return fail(ctx, PF_ECUDA, "tensor map encoding of a checkpoint failed");
             ctx->fl_state = nullptr;  // a new chain starts from the checkpoint
             ctx->actrec_end.clear();
             ctx->actrec_on = true;
             for (int t = s0; t < s1 - 1;) {
-                const float* in = seg + (size_t)(t - s0) * selems;
+                const float* in = t == s0 ? ck : seg + (size_t)(t - s0) * selems;
                 float* nxt = seg + (size_t)(t - s0 + 1) * selems;
                 if (kern == 2) {
                     // launches of `chunk` steps from s0, the adjoint's launches below
@@ -1516,7 +1525,9 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                     t += 1;
                 }
             }
-            if ((rc = adjoint_run(seg, adj_blocked ? &tseg : nullptr, s0, s0, s1, aligned ? chunk : 0))) return rc;
+            if ((rc = adjoint_run(seg, adj_blocked ? &tseg : nullptr, s0, s0, s1, aligned ? chunk : 0, ck,
+                                  adj_blocked ? &tck : nullptr)))
+                return rc;
         }
     }
     if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
