@@ -174,7 +174,8 @@ int diff_blocked_configure();
 // activity act_in (b > 0 in a tile's interior, from the previous launch's act_out or from
 // launch_fwd_act_init at the start of a chain) and handles the quiescent tiles itself.
 // k_diff_blocked writes act_out for the tiles it runs. skipped (nullable) accumulates the
-// interior cell-steps of quiescent tiles.
+// interior cell-steps of quiescent tiles. tile_count: two device ints, the count and the
+// kernel's work counter (its CTAs take tiles dynamically), both zeroed by the pre-pass.
 int diff_blocked_tiles(int halo, int H, int pitch);
 void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* act, uint8_t* qrun,
                          cudaStream_t s);
@@ -197,7 +198,7 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
                       float* zero_base,
                       int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s);
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
-                         int n, const int* tile_list, const int* tile_count, float* out, float* all_out,
+                         int n, const int* tile_list, int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
                          cudaStream_t s);
 // lam: scaled adjoint (mu_a, mu_b) [2][H][pitch]; sig: its exponents uint8 [H][pitch]
@@ -244,7 +245,8 @@ __device__ __forceinline__ void block_count(unsigned long long* g, unsigned long
 // tq as for launch_diff_blocked. Gq is accumulated. Only the tiles listed by the
 // pre-pass launch_adjoint_tiles run: from A_latest, the encoded a plane of the state at
 // t1-1, it lists the tiles with a > 0 somewhere in their region (tile_list, capacity
-// adjoint_blocked_tiles(); tile_count: one device int) and writes lambda = 0,
+// adjoint_blocked_tiles(); tile_count: two device ints, the count and the kernel's work
+// counter, both zeroed by the pre-pass) and writes lambda = 0,
 // sigma = kSigmaZero for the others, whose interior cell-steps it adds to skipped.
 int adjoint_blocked_max_steps();
 int adjoint_blocked_configure();
@@ -268,7 +270,7 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq, int H, int pitch,
                             float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
-                            float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,
+                            float* Gq, const int* tile_list, int* tile_count, int nsm, int* err,
                             cudaStream_t s);
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,
                                   cudaStream_t s);

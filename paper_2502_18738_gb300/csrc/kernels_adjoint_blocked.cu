@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_adjoint_blocked(const __grid_constant__ CUtensorMap tst, const __grid_constant__ CUtensorMap tst0,
                       const __grid_constant__ CUtensorMap tq, int H,
                       int pitch, float pc, int zlast, int n, int tiles_x, const int* __restrict__ tiles,
-                      const int* __restrict__ ntiles_live,
+                      const int* __restrict__ ntiles_live, int* __restrict__ next,
                       const float* __restrict__ lam_in, const uint8_t* __restrict__ sig_in,
                       float* __restrict__ lam_out, uint8_t* __restrict__ sig_out, float* __restrict__ Gq,
                       int* __restrict__ err) {
@@ -67,6 +67,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ __align__(8) uint64_t sbar[2];
     __shared__ __align__(8) uint64_t qbar;
     __shared__ uint32_t tslot;
+    // list entries of this CTA's tiles l = 0, 1, ... at tring[l & 3] (-1: no more). Tiles
+    // are handed out dynamically: the first is tiles[blockIdx.x], each next one comes from
+    // the work counter next (claimed by thread 0 one tile ahead of its use, two when a
+    // launch has fewer than 3 steps, so the TMA prefetch of its q and first states keeps
+    // its distance).
+    __shared__ int tring[4];
 
     const int tid = threadIdx.x;
     const int x = tid % kCT;
@@ -76,9 +82,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = tid >> 5;
     const size_t gplane = (size_t)H * pitch;
     const int ntiles = *ntiles_live;  // tiles not ahead of the fire (k_adjoint_tiles)
-    const int nloc = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-    if (nloc <= 0) return;
-    const int total = nloc * n;
+    if ((int)blockIdx.x >= ntiles) return;
+    // thread 0's queue state, in shared memory to keep it out of the hot loop's registers:
+    // entries of tiles 0 .. qstate[0]-1 are in tring; qstate[1]: no more tiles
+    __shared__ int qstate[2];
+    if (tid == 0) qstate[0] = qstate[1] = 0;
+    auto ensure = [&](int l) {  // thread 0: make the entry of tile l known
+        while (qstate[0] <= l) {
+            const int f = qstate[0];
+            int e = -1;
+            if (!qstate[1]) {
+                const int k = f == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(next, 1);
+                if (k < ntiles) e = tiles[k];
+                else qstate[1] = 1;
+            }
+            tring[f & 3] = e;
+            qstate[0] = f + 1;
+        }
+    };
 
     if (tid == 0) {
         mbar_init(&sbar[0], 1);
@@ -91,10 +112,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     // this thread's TMEM columns: lane quarter warp % 4, column block warp / 4
     const uint32_t tbase = tslot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * 128);
 
-    auto issue_state = [&](int i) {
+    auto issue_state = [&](int i) {  // thread 0: stage the state of local step i, if any
         const int l = i / n, m = i % n;
+        ensure(l);
+        const int e = tring[l & 3];
+        if (e < 0) return;
         int r0, c0;
-        const int e = tiles[(int)blockIdx.x + l * (int)gridDim.x];
         origin(e & kTileIndexMask, tiles_x, r0, c0);
         const int s = i & 1;
         if ((e & kTileFrozenBit) && m > 0) {
@@ -112,24 +135,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         else
             tma_load_3d(sm.st[s], &tst, &sbar[s], c0, r0, 2 * z);
     };
-    auto issue_q = [&](int l) {
+    auto issue_q = [&](int l) {  // thread 0: stage q of tile l, if any
+        ensure(l);
+        const int e = tring[l & 3];
+        if (e < 0) return;
         int r0, c0;
-        origin(tiles[(int)blockIdx.x + l * (int)gridDim.x] & kTileIndexMask, tiles_x, r0, c0);
+        origin(e & kTileIndexMask, tiles_x, r0, c0);
         mbar_arrive_expect_tx(&qbar, (uint32_t)(8 * kPlane * sizeof(float)));
         tma_load_3d(sm.q, &tq, &qbar, c0, r0, 0);
     };
     if (tid == 0) {
         issue_q(0);
         issue_state(0);
-        if (total > 1) issue_state(1);
+        issue_state(1);
     }
+    __syncthreads();  // tring[0]
 
     bool failed = false;
     float la[kM], lb[kM];     // scaled adjoint mu of this thread's cells (lambda = mu 2^sigma)
     uint32_t sgp[2];          // sigma at t + 1 of the 8 cells, 4 per word
-    for (int l = 0; l < nloc && !failed; ++l) {
+    for (int l = 0; !failed; ++l) {
+        // written by thread 0 before the barriers of the previous tile's steps
+        const int ent = tring[l & 3];
+        if (ent < 0) break;
         int r0, c0;
-        const int ent = tiles[(int)blockIdx.x + l * (int)gridDim.x];
         const bool frz = (ent & kTileFrozenBit) != 0;  // uniform across the CTA
         origin(ent & kTileIndexMask, tiles_x, r0, c0);
         if (!__syncthreads_and(mbar_wait_bounded(&qbar, (uint32_t)(l & 1)))) {
@@ -197,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_wait_st();
         fence_proxy_async();
         __syncthreads();  // q stage consumed
-        if (tid == 0 && l + 1 < nloc) issue_q(l + 1);
+        if (tid == 0) issue_q(l + 1);
 
         for (int m = 0; m < n; ++m) {
             const int i = l * n + m;
@@ -405,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 failed = true;
                 break;
             }
-            if (tid == 0 && i + 2 < total) issue_state(i + 2);
+            if (tid == 0) issue_state(i + 2);
             // gather: lambda_b at the sources of this strip
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
@@ -630,7 +659,7 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
                           int* tile_list, int* tile_count, uint8_t* gq_dirty, unsigned long long* skipped,
                           cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
-    cudaMemsetAsync(tile_count, 0, sizeof(int), s);
+    cudaMemsetAsync(tile_count, 0, 2 * sizeof(int), s);  // the count and the adjoint's work counter
     const int ntiles = adjoint_blocked_tiles(H, pitch);
     k_adjoint_tiles<<<(ntiles + 7) / 8, 256, 0, s>>>(A_latest, H, W, pitch, tiles_x, ntiles, n, tile_list, tile_count,
                                                      lam_out, sig_out, gq_dirty, skipped);
@@ -642,7 +671,7 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
                                 cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC, tiles_y = (H + kIR - 1) / kIR;
     const int ntiles = tiles_x * tiles_y;
-    cudaMemsetAsync(tile_count, 0, sizeof(int), s);
+    cudaMemsetAsync(tile_count, 0, 2 * sizeof(int), s);  // the count and the adjoint's work counter
     k_adjoint_tiles_flags<<<(ntiles + 7) / 8, 256, 0, s>>>(act, H, W, pitch, tiles_x, tiles_y, n, tile_list, tile_count,
                                                            lam_out, sig_out, deadcnt, use_frozen ? 1 : 0, gq_dirty,
                                                            skipped, frozen_steps);
@@ -651,13 +680,14 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq, int H, int pitch,
                             float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
-                            float* Gq, const int* tile_list, const int* tile_count, int nsm, int* err,
+                            float* Gq, const int* tile_list, int* tile_count, int nsm, int* err,
                             cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
     const int ntiles = adjoint_blocked_tiles(H, pitch);
     const int grid = ntiles < nsm ? ntiles : nsm;
     k_adjoint_blocked<<<grid, kThreads, adjoint_blocked_smem(), s>>>(*tst, *tst0, *tq, H, pitch, pc, zlast, n, tiles_x,
-                                                                     tile_list, tile_count, lam_in, sig_in, lam_out,
+                                                                     tile_list, tile_count, tile_count + 1, lam_in,
+                                                                     sig_in, lam_out,
                                                                      sig_out, Gq, err);
 }
 

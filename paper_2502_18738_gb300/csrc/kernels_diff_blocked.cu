@@ -48,12 +48,16 @@ template <int kHalo>
 __global__ void __launch_bounds__(kThreads, 1)
     k_diff_blocked(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap tq, int H, int pitch,
                    int W, float pc, int n, int tiles_x, const int* __restrict__ tiles,
-                   const int* __restrict__ ntiles_live, float* __restrict__ out, float* __restrict__ all_out,
+                   const int* __restrict__ ntiles_live, int* __restrict__ work, float* __restrict__ out,
+                   float* __restrict__ all_out,
                    size_t all_stride, uint8_t* __restrict__ act_out, unsigned long long* __restrict__ skipped,
                    int* __restrict__ err) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     __shared__ __align__(8) uint64_t bar;
+    // the list index of this CTA's next tile: tiles are handed out dynamically (the first
+    // is blockIdx.x, then work counter claims), one tile ahead for the TMA prefetch
+    __shared__ int s_next;
     const int tid = threadIdx.x;
     const int x = tid % kCT;             // region column
     const int ys = (tid / kCT) * kM;     // first region row of the strip
@@ -78,7 +82,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t parity = 0;
     float q[kM][8];
     float A[kM];
-    for (; li < ntiles; li += gridDim.x) {
+    for (;;) {
         const int tile = tiles[li];
         const bool ok = mbar_wait_bounded(&bar, parity);
         if (!__syncthreads_and(ok)) {
@@ -105,7 +109,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // b = 0 in the whole region: every P is 0 at every step of the launch, so the
         // region's state does not change and the steps are skipped (the stores remain)
         const bool live = __syncthreads_or(burning);  // also: stage fully consumed
-        const int next = li + gridDim.x;
+        int next = ntiles;
+        if (tid == 0) {
+            next = (int)gridDim.x + atomicAdd(work, 1);
+            s_next = next;  // read by every thread after this tile's last barrier
+        }
         if (tid == 0 && next < ntiles) {
             int r0, c0;
             tile_origin<kHalo>(tiles[next], tiles_x, r0, c0);
@@ -206,6 +214,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         actB = __syncthreads_or(actB);
         actA = __syncthreads_or(actA);
         if (tid == 0) act_out[tile] = (act_out[tile] & kQb) | (actA ? kActA : 0) | (actB ? kActB : 0);
+        li = s_next;
+        if (li >= ntiles) break;
     }
 }
 
@@ -438,7 +448,7 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int tiles_y = (H + inner - 1) / inner;
-    cudaMemsetAsync(tile_count, 0, sizeof(int), s);
+    cudaMemsetAsync(tile_count, 0, 2 * sizeof(int), s);  // the count and k_diff_blocked's work counter
     if (halo == 4)
         k_fwd_tiles<4><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          qrun, tile_list, tile_count, out, out_age,
@@ -452,7 +462,7 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
 }
 
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
-                         int n, const int* tile_list, const int* tile_count, float* out, float* all_out,
+                         int n, const int* tile_list, int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
                          cudaStream_t s) {
     const int inner = kRT - 2 * halo;
@@ -461,12 +471,12 @@ void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq
     const int grid = ntiles < nsm ? ntiles : nsm;
     if (halo == 4)
         k_diff_blocked<4><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, tile_list,
-                                                                      tile_count, out, all_out, all_stride, act_out,
-                                                                      skipped, err);
+                                                                      tile_count, tile_count + 1, out, all_out,
+                                                                      all_stride, act_out, skipped, err);
     else
         k_diff_blocked<8><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, tile_list,
-                                                                      tile_count, out, all_out, all_stride, act_out,
-                                                                      skipped, err);
+                                                                      tile_count, tile_count + 1, out, all_out,
+                                                                      all_stride, act_out, skipped, err);
 }
 
 }  // namespace pf

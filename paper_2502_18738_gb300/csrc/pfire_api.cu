@@ -134,10 +134,10 @@ struct pf_ctx {
     int* dflags = nullptr;  // [0] device error word, [1] validation, [3] async wind validation
     int* hflags = nullptr;  // pinned mirror
     unsigned long long* dskip = nullptr;  // per kernel kind: cell-steps of skipped quiescent tiles
-    int* tile_list = nullptr;             // live tiles of one blocked-adjoint launch (count: dflags[8])
+    int* tile_list = nullptr;             // live tiles of one blocked-adjoint launch (count: dflags[8], work: [9])
     uint8_t* gqdirty = nullptr;           // per adjoint tile: may hold nonzero dL/dq this epoch
     // tile activity of the blocked forward (b > 0 in a tile's interior), carried along a
-    // chain of launches: act ping-pong, quiescent-last-launch flags, live list (count: dflags[9])
+    // chain of launches: act ping-pong, quiescent-last-launch flags, live list (count: dflags[11])
     uint8_t* fact[2] = {nullptr, nullptr};
     uint8_t* fqrun = nullptr;  // per tile: quiescent streak along the chain (k_fwd_tiles)
     int* flist = nullptr;
@@ -511,14 +511,14 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
     {
         LaunchScope ls(ctx, K_FTILES);
         launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
-                         ctx->fqrun, ctx->flist, ctx->dflags + 9, out, out_age, all_out,
+                         ctx->fqrun, ctx->flist, ctx->dflags + 11, out, out_age, all_out,
                          stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_slot0 : nullptr,
                          seg ? ctx->seg_buf + stride : nullptr,
                          ctx->seg_cap - 1, seg && frozen && halo == 8, ctx->dskip + K_FBLK, ctx->st);
     }
     {
         LaunchScope ls(ctx, K_FBLK, n);
-        launch_diff_blocked(halo, &tab, &ctx->tmapQ, ctx->H, ctx->W, ctx->P, pc, n, ctx->flist, ctx->dflags + 9, out,
+        launch_diff_blocked(halo, &tab, &ctx->tmapQ, ctx->H, ctx->W, ctx->P, pc, n, ctx->flist, ctx->dflags + 11, out,
                             all_out, stride, ctx->fact[1 - ctx->fl_par], ctx->dskip + K_FBLK, ctx->nsm, ctx->dflags,
                             ctx->st);
     }
