@@ -179,6 +179,9 @@ int diff_blocked_configure();
 int diff_blocked_tiles(int halo, int H, int pitch);
 void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* act, uint8_t* qrun,
                          cudaStream_t s);
+// The same from the act_out an earlier chain recorded for the state (same halo).
+void launch_fwd_act_seed(int halo, const uint8_t* seed, int H, int pitch, uint8_t* act, uint8_t* qrun,
+                         cudaStream_t s);
 // qrun: per tile, the number of consecutive launches of the chain it has been quiescent
 // in (saturating at 255); out_age > 0: out holds the input state of the launch out_age
 // launches back, so tiles with qrun >= out_age need no copy into it (0: out holds nothing).

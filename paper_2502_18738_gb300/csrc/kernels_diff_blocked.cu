@@ -250,6 +250,16 @@ __global__ void __launch_bounds__(256) k_fwd_act_init(const float* __restrict__ 
     }
 }
 
+// The same from flags recorded for the state by an earlier chain (its launch's act_out):
+// their activity bits are exact, the segment bits start afresh.
+__global__ void __launch_bounds__(256) k_fwd_act_seed(const uint8_t* __restrict__ seed, int ntiles,
+                                                      uint8_t* __restrict__ act, uint8_t* __restrict__ qrun) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= ntiles) return;
+    act[i] = (uint8_t)((seed[i] & (kActA | kActB)) | kQt);
+    qrun[i] = 0;
+}
+
 // Pre-pass of one forward launch, one warp per tile. A tile is live if b > 0 anywhere in
 // the interiors of the 3 x 3 tiles around it (act_in, from the previous launch or
 // k_fwd_act_init): its region (interior + halo <= one interior) lies inside them, so a
@@ -439,6 +449,12 @@ void launch_fwd_act_init(int halo, const float* ab, int H, int pitch, uint8_t* a
         k_fwd_act_init<4><<<blocks, 256, 0, s>>>(ab, H, pitch, tiles_x, ntiles, act, qrun);
     else
         k_fwd_act_init<8><<<blocks, 256, 0, s>>>(ab, H, pitch, tiles_x, ntiles, act, qrun);
+}
+
+void launch_fwd_act_seed(int halo, const uint8_t* seed, int H, int pitch, uint8_t* act, uint8_t* qrun,
+                         cudaStream_t s) {
+    const int ntiles = diff_blocked_tiles(halo, H, pitch);
+    k_fwd_act_seed<<<(ntiles + 255) / 256, 256, 0, s>>>(seed, ntiles, act, qrun);
 }
 
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,

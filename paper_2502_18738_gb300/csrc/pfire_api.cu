@@ -143,6 +143,13 @@ struct pf_ctx {
     int* flist = nullptr;
     const float* fl_state = nullptr;    // the state fact[fl_par] describes (nullptr: none)
     int fl_launch = 0;                  // launches of the chain so far
+    const uint8_t* fl_seed = nullptr;   // flags recorded for the next chain's first state (or none)
+    int fl_seed_halo = 0;
+    // per arena slot: the tile flags the blocked forward recorded for the checkpoint it
+    // wrote there (ckact + slot * tiles), with their halo (0: none)
+    uint8_t* ckact = nullptr;
+    int ckact_cap = 0;
+    std::vector<int> ckact_halo;
     int fl_in_at[2] = {-1, -1};         // launch whose input work[x] last was (-1: none)
     int fl_par = 0;
     int fl_halo = 0;
@@ -496,8 +503,12 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
     if (ctx->fl_state != in || ctx->fl_halo != halo) {
         {
             LaunchScope ls(ctx, K_FTILES);
-            launch_fwd_act_init(halo, in, ctx->H, ctx->P, ctx->fact[ctx->fl_par], ctx->fqrun, ctx->st);
+            if (ctx->fl_seed && ctx->fl_seed_halo == halo)
+                launch_fwd_act_seed(halo, ctx->fl_seed, ctx->H, ctx->P, ctx->fact[ctx->fl_par], ctx->fqrun, ctx->st);
+            else
+                launch_fwd_act_init(halo, in, ctx->H, ctx->P, ctx->fact[ctx->fl_par], ctx->fqrun, ctx->st);
         }
+        ctx->fl_seed = nullptr;
         ctx->fl_halo = halo;
         ctx->fl_launch = 0;
         ctx->fl_in_at[0] = ctx->fl_in_at[1] = -1;
@@ -607,7 +618,29 @@ int take_slots(pf_ctx* ctx, int n, int* rc) {
     }
     const int s0 = ctx->arena_used;
     ctx->arena_used += n;
+    if ((int)ctx->ckact_halo.size() < ctx->arena_cap) ctx->ckact_halo.resize(ctx->arena_cap, 0);
+    for (int i = s0; i < s0 + n; ++i) ctx->ckact_halo[i] = 0;  // no flags recorded for the new contents
     return s0;
+}
+
+// Keep the tile flags of the blocked forward's last launch (its act_out, describing the
+// state it wrote into arena slot s) for the recompute that will start from that state.
+int save_ckpt_flags(pf_ctx* ctx, int s) {
+    const size_t nt = (size_t)std::max(diff_blocked_tiles(8, ctx->H, ctx->P), diff_blocked_tiles(4, ctx->H, ctx->P));
+    if (ctx->ckact_cap < ctx->arena_cap) {
+        void* p;
+        int rc = dalloc(ctx, &p, nt * (size_t)ctx->arena_cap);
+        if (rc) return rc;
+        if (ctx->ckact) {
+            CK(cudaMemcpyAsync(p, ctx->ckact, nt * (size_t)ctx->ckact_cap, cudaMemcpyDeviceToDevice, ctx->st));
+            dfree(ctx, ctx->ckact);
+        }
+        ctx->ckact = (uint8_t*)p;
+        ctx->ckact_cap = ctx->arena_cap;
+    }
+    CK(cudaMemcpyAsync(ctx->ckact + nt * s, ctx->fact[ctx->fl_par], nt, cudaMemcpyDeviceToDevice, ctx->st));
+    ctx->ckact_halo[s] = ctx->fl_halo;
+    return PF_OK;
 }
 
 bool is_ckpt_step(const pf_ctx* c, int t) {
@@ -656,6 +689,7 @@ int diff_steps(pf_ctx* ctx, int T) {
     const int end = ctx->step + T;
     const int kern = choose_kernel(ctx);
     ctx->fl_state = nullptr;  // the current state may have been set by other means
+    ctx->fl_seed = nullptr;
     // with K == 1 every state is saved: blocked launches write all of them into
     // consecutive tape slots
     const bool all_states = ctx->tape_valid && ctx->K == 1;
@@ -670,6 +704,7 @@ int diff_steps(pf_ctx* ctx, int T) {
         }
         float* out = nullptr;
         float* all_out = nullptr;
+        int ckpt_slot = -1;
         if (all_states) {
             const int s = take_slots(ctx, n, &rc);
             if (rc) return rc;
@@ -680,6 +715,7 @@ int diff_steps(pf_ctx* ctx, int T) {
             if (rc) return rc;
             ctx->ckpts.push_back({t + n, s});
             out = slot_ptr(ctx, s);
+            ckpt_slot = s;
         } else if (ctx->cur_ab == ctx->work[0] || ctx->cur_ab == ctx->work[1]) {
             out = (ctx->cur_ab == ctx->work[0]) ? ctx->work[1] : ctx->work[0];
         } else {
@@ -691,6 +727,7 @@ int diff_steps(pf_ctx* ctx, int T) {
             if ((rc = diff_blocked_launch(ctx, ctx->cur_ab, ctx->pc, n, out, all_out, false,
                                           all_states ? t + n : -1)))
                 return rc;
+            if (ckpt_slot >= 0 && (rc = save_ckpt_flags(ctx, ckpt_slot))) return rc;
         } else {
             float* dst = out ? out : all_out;
             {
@@ -1505,7 +1542,15 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             if (adj_blocked && !encode_f32_3d(&tck, ck, ctx->P, ctx->H, 2, diff_blocked_box_cols(),
                                               diff_blocked_box_rows(), 2))
                 return fail(ctx, PF_ECUDA, "tensor map encoding of a checkpoint failed");
-            ctx->fl_state = nullptr;  // a new chain starts from the checkpoint
+            ctx->fl_state = nullptr;  // a new chain starts from the checkpoint, with its recorded flags if any
+            {
+                const int cs = ctx->ckpts[si].second;
+                const bool rec = cs < (int)ctx->ckact_halo.size() && ctx->ckact_halo[cs] != 0;
+                const size_t nt = (size_t)std::max(diff_blocked_tiles(8, ctx->H, ctx->P),
+                                                   diff_blocked_tiles(4, ctx->H, ctx->P));
+                ctx->fl_seed = rec ? ctx->ckact + nt * cs : nullptr;
+                ctx->fl_seed_halo = rec ? ctx->ckact_halo[cs] : 0;
+            }
             ctx->actrec_end.clear();
             ctx->actrec_on = true;
             for (int t = s0; t < s1 - 1;) {
@@ -1530,6 +1575,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                 return rc;
         }
     }
+    ctx->fl_seed = nullptr;
     if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
     CK(cudaMemcpyAsync(ctx->hflags + 4, ctx->gacc, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     if ((rc = device_error(ctx))) return rc;  // synchronises the stream
@@ -1653,6 +1699,7 @@ int pf_backward_dca(pf_ctx* ctx, const float* dL_dacc, const uint8_t* step_mask,
         }
         cur = 1 - cur;
     }
+    ctx->fl_seed = nullptr;
     if (cur_e >= 0 && (rc = flush(cur_e))) return rc;
     CK(cudaMemcpyAsync(ctx->hflags + 4, ctx->gacc, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
