@@ -248,8 +248,9 @@ __device__ __forceinline__ void block_count(unsigned long long* g, unsigned long
 // tq as for launch_diff_blocked. Gq is accumulated. Only the tiles listed by the
 // pre-pass launch_adjoint_tiles run: from A_latest, the encoded a plane of the state at
 // t1-1, it lists the tiles with a > 0 somewhere in their region (tile_list, capacity
-// adjoint_blocked_tiles(); tile_count: two device ints, the count and the kernel's work
-// counter, both zeroed by the pre-pass) and writes lambda = 0,
+// adjoint_blocked_tiles(); tile_count: three device ints zeroed by the pre-pass: the
+// count listed from the front, the kernel's work counter, the count listed from the back
+// (frozen tiles)) and writes lambda = 0,
 // sigma = kSigmaZero for the others, whose interior cell-steps it adds to skipped.
 int adjoint_blocked_max_steps();
 int adjoint_blocked_configure();

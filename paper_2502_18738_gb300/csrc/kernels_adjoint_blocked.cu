@@ -81,19 +81,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const size_t gplane = (size_t)H * pitch;
-    const int ntiles = *ntiles_live;  // tiles not ahead of the fire (k_adjoint_tiles)
+    // tiles not ahead of the fire (k_adjoint_tiles): the others from the front of the
+    // list, then the frozen ones (about half the cost) stored from its back, so that the
+    // dynamic hand-out ends on cheap tiles
+    const int ntiles = ntiles_live[0] + ntiles_live[2];
     if ((int)blockIdx.x >= ntiles) return;
     // thread 0's queue state, in shared memory to keep it out of the hot loop's registers:
     // entries of tiles 0 .. qstate[0]-1 are in tring; qstate[1]: no more tiles
-    __shared__ int qstate[2];
-    if (tid == 0) qstate[0] = qstate[1] = 0;
+    // (and the list's front count and capacity)
+    __shared__ int qstate[4];
+    if (tid == 0) {
+        qstate[0] = qstate[1] = 0;
+        qstate[2] = ntiles_live[0];
+        qstate[3] = tiles_x * ((H + kIR - 1) / kIR);
+    }
     auto ensure = [&](int l) {  // thread 0: make the entry of tile l known
         while (qstate[0] <= l) {
             const int f = qstate[0];
             int e = -1;
             if (!qstate[1]) {
                 const int k = f == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(next, 1);
-                if (k < ntiles) e = tiles[k];
+                const int nfront = qstate[2];
+                if (k < ntiles_live[0] + ntiles_live[2]) e = tiles[k < nfront ? k : qstate[3] - 1 - (k - nfront)];
                 else qstate[1] = 1;
             }
             tring[f & 3] = e;
@@ -581,7 +590,11 @@ __device__ __forceinline__ void adjoint_tile_flags(const uint8_t* __restrict__ a
     if (around & kActA) {
         if (lane == 0) {
             const bool fz = use_frozen && (act[tile] & kFrozen);
-            list[atomicAdd(count, 1)] = tile | (fz ? kTileFrozenBit : 0) | (fz && all_qb ? kTileCkptBit : 0);
+            const int cap = tiles_x * tiles_y;  // the list's capacity
+            if (fz)  // from the back of the list (count[2] of them)
+                list[cap - 1 - atomicAdd(count + 2, 1)] = tile | kTileFrozenBit | (all_qb ? kTileCkptBit : 0);
+            else
+                list[atomicAdd(count, 1)] = tile;
             deadcnt[tile] = 0;
             if (gq_dirty && !fz) gq_dirty[tile] = 1;
             if (fz) {
@@ -659,7 +672,7 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
                           int* tile_list, int* tile_count, uint8_t* gq_dirty, unsigned long long* skipped,
                           cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
-    cudaMemsetAsync(tile_count, 0, 2 * sizeof(int), s);  // the count and the adjoint's work counter
+    cudaMemsetAsync(tile_count, 0, 3 * sizeof(int), s);  // the counts and the adjoint's work counter
     const int ntiles = adjoint_blocked_tiles(H, pitch);
     k_adjoint_tiles<<<(ntiles + 7) / 8, 256, 0, s>>>(A_latest, H, W, pitch, tiles_x, ntiles, n, tile_list, tile_count,
                                                      lam_out, sig_out, gq_dirty, skipped);
@@ -671,7 +684,7 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
                                 cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC, tiles_y = (H + kIR - 1) / kIR;
     const int ntiles = tiles_x * tiles_y;
-    cudaMemsetAsync(tile_count, 0, 2 * sizeof(int), s);  // the count and the adjoint's work counter
+    cudaMemsetAsync(tile_count, 0, 3 * sizeof(int), s);  // the counts and the adjoint's work counter
     k_adjoint_tiles_flags<<<(ntiles + 7) / 8, 256, 0, s>>>(act, H, W, pitch, tiles_x, tiles_y, n, tile_list, tile_count,
                                                            lam_out, sig_out, deadcnt, use_frozen ? 1 : 0, gq_dirty,
                                                            skipped, frozen_steps);
