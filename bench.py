@@ -458,6 +458,13 @@ def main():
         ms_e2e = timed(lambda: e2e_run(n_e2e), 1) / n_e2e
         e2e = {"value": cells * world / (ms_e2e / 1000.0), "unit": "cell-updates/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+        del stage, host
+
+    # the comparisons below need their own memory (the batch's adjoint keeps every state
+    # of its differentiable fires): release the workload's model and buffers first
+    m.close()
+    del dev, out, g_a, gpv, gpd
+    torch.cuda.empty_cache()
 
     extras = {}
     if not args.no_extras:
