@@ -46,14 +46,14 @@ B_FWD, B_ADJ = 16, 24  # algorithmic bytes per cell-step: (a, b) in + out; state
 
 
 # DRAM traffic of the blocked kernels measured by ncu over every launch of one timed step
-# of the default workload (dram__bytes_read.sum + dram__bytes_write.sum, summed; see
-# profiles/dram_traffic_fwd_adjoint_8192sq_T2000.md), per cell-step the kernel computed.
+# of the default workload (dram__bytes_read.sum + dram__bytes_write.sum, summed; the
+# capture is summarised under profiles/), per cell-step the kernel computed.
 # A figure is used only while the kernel's sources hash to the value it was taken on.
 NCU_TRAFFIC = {
     "adjoint_blocked": {"files": ["kernels_adjoint_blocked.cu", "common.cuh", "tma.cuh", "tmem.cuh"],
-                        "sha256_16": "82292be22e261880", "bytes_per_computed_cell_step": 22.00},
+                        "sha256_16": "f195ae8c783a2934", "bytes_per_computed_cell_step": 17.29},
     "diff_blocked": {"files": ["kernels_diff_blocked.cu", "common.cuh", "tma.cuh"],
-                     "sha256_16": "9786801aa90141a2", "bytes_per_computed_cell_step": 15.28},
+                     "sha256_16": "a87f59f2606e06ac", "bytes_per_computed_cell_step": 14.78},
 }
 
 
