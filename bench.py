@@ -270,6 +270,44 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_probe(kind, N=2048, T=14):
+    """Cost of the blocked adjoint per computed cell-step on one kind of tile: "frozen"
+    (a = 0.65, b = 0 on every burnable cell: nothing burns, every listed tile is frozen)
+    or "live" (b > 0 everywhere: every cell takes the full path). T steps taped in one
+    segment, so the recompute's flags mark the frozen tiles; the second backward is
+    profiled. Returns a dict for the JSON line."""
+    import torch
+    import paper_2502_18738_gb300 as pf
+    pf.build()
+    land = syn.make_landscape(N, N, 3)
+    burn = land.burnable != 0
+    c = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    rng = np.random.default_rng(1)
+    if kind == "frozen":
+        a, b = np.full((N, N), 0.65, np.float32), np.zeros((N, N), np.float32)
+    else:
+        a = (0.3 + 0.2 * rng.random((N, N))).astype(np.float32)
+        b = (0.05 + 0.1 * rng.random((N, N))).astype(np.float32)
+    ab = c(np.stack([np.where(burn, a, 0), np.where(burn, b, 0)]).astype(np.float32))
+    m = pf.FireModel(N, N, pf.PF_DIFF)
+    m.set_env(c(land.E), c(land.p_veg), c(land.p_den), c(np.full((N, N), 3.0, np.float32)),
+              c(np.zeros((N, N), np.float32)))
+    m.set_params(**PARAMS)
+    m.forward(c(np.where(burn, 1, 0).astype(np.uint8)), 0)  # the burnable mask
+    w = torch.full((N, N), 1e-3, device="cuda")
+    for prof in (0, 1):
+        pf.pf_set_tuning(m.h, K=T, profile=prof)
+        pf.pf_profile_read(m.h, reset=True)
+        m.set_state(0, ab)
+        m.advance(T)
+        m.backward(w, None, per_cell=False)
+        torch.cuda.synchronize()
+    p = pf.pf_profile_read(m.h, reset=True)
+    n, cs, ms, sk = p["adjoint_blocked"]
+    return {"probe": "adjoint_" + kind, "grid": N, "steps": T, "launches": n, "computed_cell_steps": cs - sk,
+            "frozen_cell_steps": p["adjoint_tiles"][3], "ms": ms, "ps_per_computed_cell_step": ms * 1e9 / max(1, cs - sk)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -285,12 +323,17 @@ def main():
                     help="skip the discrete-ensemble and batched-fires comparisons against the plain kernels")
     ap.add_argument("--K", type=int, default=0, help="checkpoint interval (0 = chosen by the library)")
     ap.add_argument("--k", type=int, default=0, help="steps per blocked forward launch (0 = library default)")
+    ap.add_argument("--probe", choices=["frozen", "live"],
+                    help="instead of the benchmark: the blocked adjoint's cost on one kind of tile")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.probe:
+        print(json.dumps(adjoint_probe(args.probe)), flush=True)
+        return 0
 
     import torch
     import paper_2502_18738_gb300 as pf
