@@ -444,27 +444,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             if (tid == 0) issue_state(i + 2);
-            // gather: lambda_b at the sources of this strip
+            // gather: lambda_b at the sources of this strip. The per-lane boundary terms are
+            // selected rather than branched on: every lane loads them (one address per warp,
+            // a broadcast) and keeps its own.
+            const int xp = x + 1 < kCT ? x + 1 : x, xm = x >= 1 ? x - 1 : x;
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 float v = fmaf(pc * scl[k], lb[k], own[k]);
-                if (lane == 31 && x == 31) v += sm.er2l[ex][strip][k];
-                if (lane == 0 && x == 32) v += sm.el2r[ex][strip][k];
-                if (k == 0 && strip > 0) {
-                    v += sm.vbot[ex][strip - 1][1][x];
-                    if (x + 1 < kCT) v += sm.vbot[ex][strip - 1][0][x + 1];
-                    if (x >= 1) v += sm.vbot[ex][strip - 1][2][x - 1];
+                const float from_r = sm.er2l[ex][strip][k], from_l = sm.el2r[ex][strip][k];
+                v += x == 31 ? from_r : (x == 32 ? from_l : 0.0f);
+                if (k == 0 && strip > 0) {  // uniform across the warp
+                    const float c = sm.vbot[ex][strip - 1][1][x];
+                    const float r = sm.vbot[ex][strip - 1][0][xp], lf = sm.vbot[ex][strip - 1][2][xm];
+                    v += c;
+                    v += x + 1 < kCT ? r : 0.0f;
+                    v += x >= 1 ? lf : 0.0f;
                 }
                 if (k == kM - 1 && strip < kStrips - 1) {
-                    v += sm.vtop[ex][strip + 1][1][x];
-                    if (x + 1 < kCT) v += sm.vtop[ex][strip + 1][0][x + 1];
-                    if (x >= 1) v += sm.vtop[ex][strip + 1][2][x - 1];
+                    const float c = sm.vtop[ex][strip + 1][1][x];
+                    const float r = sm.vtop[ex][strip + 1][0][xp], lf = sm.vtop[ex][strip + 1][2][xm];
+                    v += c;
+                    v += x + 1 < kCT ? r : 0.0f;
+                    v += x >= 1 ? lf : 0.0f;
                 }
-                lb[k] = v;
-                if (((sgc[k >> 2] >> (8 * (k & 3))) & 0xffu) == (uint32_t)kSigmaZero) {
-                    la[k] = 0.0f;  // a == 0 at t: lambda multiplies only zeros
-                    lb[k] = 0.0f;
-                }
+                // a == 0 at t: lambda multiplies only zeros
+                const bool dead = ((sgc[k >> 2] >> (8 * (k & 3))) & 0xffu) == (uint32_t)kSigmaZero;
+                lb[k] = dead ? 0.0f : v;
+                la[k] = dead ? 0.0f : la[k];
             }
             sgp[0] = sgc[0];
             sgp[1] = sgc[1];
