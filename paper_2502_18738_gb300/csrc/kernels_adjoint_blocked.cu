@@ -22,6 +22,8 @@
 // The halo shrinks by one cell per step, so the 48 x 48 interior is exact for n <= 7.
 #include <cuda.h>
 
+#include <cstddef>
+
 #include "common.cuh"
 #include "tma.cuh"
 #include "tmem.cuh"
@@ -47,6 +49,7 @@ struct Smem {
     float vbot[2][kStrips][3][kCT];      // C for row ys+8
     float el2r[2][kStrips][kM];          // x = 31 -> x = 32 (dc = +1), rows of the strip
     float er2l[2][kStrips][kM];          // x = 32 -> x = 31 (dc = -1)
+    float edump[kThreads];               // where the other threads' exchange stores go
 };
 
 __device__ __forceinline__ void origin(int tile, int tiles_x, int& r0, int& c0) {
@@ -160,6 +163,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();  // tring[0]
 
+    // the cross-warp exchange of a completed row: x = 31 passes its dc = +1 term to x = 32,
+    // x = 32 its dc = -1 term to x = 31; every other thread stores into its own scratch
+    // word, so the store is not branched on (float offsets into the shared-memory block)
+    const bool ex_on = x == 31 || x == 32;
+    const int ex_off = x == 31   ? (int)(offsetof(Smem, el2r) / sizeof(float)) + strip * kM
+                       : x == 32 ? (int)(offsetof(Smem, er2l) / sizeof(float)) + strip * kM
+                                 : (int)(offsetof(Smem, edump) / sizeof(float)) + tid;
+    auto exchange = [&](int ex, int row, float right, float left) {
+        reinterpret_cast<float*>(&sm)[ex_off + (ex_on ? ex * kStrips * kM + row : 0)] = x == 32 ? left : right;
+    };
     bool failed = false;
     float la[kM], lb[kM];     // scaled adjoint mu of this thread's cells (lambda = mu 2^sigma)
     uint32_t sgp[2];          // sigma at t + 1 of the 8 cells, 4 per word
@@ -289,8 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float fr = __shfl_down_sync(0xffffffffu, wu[0], 1);
                         const float fl = __shfl_up_sync(0xffffffffu, wu[2], 1);
                         own[k - 1] = wu[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
-                        if (x == 31) sm.el2r[ex][strip][k - 1] = wu[2];
-                        if (x == 32) sm.er2l[ex][strip][k - 1] = wu[0];
+                        exchange(ex, k - 1, wu[2], wu[0]);
                     }
 #pragma unroll
                     for (int j = 0; j < 3; ++j) wu[j] = 0.0f;
@@ -418,8 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float fr = __shfl_down_sync(0xffffffffu, wu[0], 1);  // from column x + 1
                     const float fl = __shfl_up_sync(0xffffffffu, wu[2], 1);    // from column x - 1
                     own[k - 1] = wu[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
-                    if (x == 31) sm.el2r[ex][strip][k - 1] = wu[2];
-                    if (x == 32) sm.er2l[ex][strip][k - 1] = wu[0];
+                    exchange(ex, k - 1, wu[2], wu[0]);
                 }
 #pragma unroll
                 for (int j = 0; j < 3; ++j) wu[j] = 0.0f;  // the slot becomes row R = k + 3
@@ -432,8 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float fr = __shfl_down_sync(0xffffffffu, w8[0], 1);
                 const float fl = __shfl_up_sync(0xffffffffu, w8[2], 1);
                 own[kM - 1] = w8[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
-                if (x == 31) sm.el2r[ex][strip][kM - 1] = w8[2];
-                if (x == 32) sm.er2l[ex][strip][kM - 1] = w8[0];
+                exchange(ex, kM - 1, w8[2], w8[0]);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) sm.vbot[ex][strip][j][x] = w9[j];
             }
