@@ -360,14 +360,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         qv[d] = __uint_as_float(tmv[d]);
                         gv[d] = __uint_as_float(tmv[8 + d]);
                     }
-                    if (xin && live) {
+                    if (live) {
+                        // The region's edge columns (!xin) contribute nothing: they take
+                        // the same path on their clamped (in-bounds) window with tg = 0 and
+                        // P = 0, which leaves only l_a <- l_a scl, instead of diverging.
                         // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
                         const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
                         const float nu[8] = {uu[0], uu[1], uu[2], um[0], um[2], ud[0], ud[1], ud[2]};
                         float av, ua;
                         a_decode(Aown, av, ua);
                         const float ln = la[k] + lb[k];
-                        const float tg = ln * ua;  // l_P_j in units 2^sigma'(j)
+                        const float tg = xin ? ln * ua : 0.0f;  // l_P_j in units 2^sigma'(j)
                         bool quiet = true;  // no neighbour burning (behind or ahead of the front)
 #pragma unroll
                         for (int d = 0; d < 8; ++d) quiet &= nb[d] == 0.0f;
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             // P = 0, every leave-one-out product is 1 and every dL/dq term
                             // carries b_i = 0: only the contributions t_d q_dj = tg q_dj remain
                             la[k] *= scl[k];
-                            if (tg != 0.0f) {  // 0 for cells burned out to a = 1 exactly
+                            {  // tg = 0 (edge columns; cells burned out to a = 1 exactly) adds zeros
 #pragma unroll
                                 for (int d = 0; d < 8; ++d) {
                                     const float tq = tg * qv[d];
@@ -396,9 +399,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float p03 = p01 * p23, p47 = p45 * p67;
                             // P enters only l_a = l_a' - l_n P here, where 1 - S's absolute
                             // error (a few 1e-8) is harmless; the forward keeps the recurrence
-                            const float P = 1.0f - p03 * p47;
+                            const float P = xin ? 1.0f - p03 * p47 : 0.0f;
                             la[k] = fmaf(-ln, P, la[k]) * scl[k];
-                            if (tg != 0.0f) {
+                            {  // as above: unconditional, tg = 0 adds zeros
                                 const float g03 = tg * p47, g47 = tg * p03;
                                 const float r01 = g03 * p23, r23 = g03 * p01, r45 = g47 * p67, r67 = g47 * p45;
                                 const float t[8] = {f[1] * r01, f[0] * r01, f[3] * r23, f[2] * r23,

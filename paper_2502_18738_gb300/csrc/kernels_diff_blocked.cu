@@ -148,23 +148,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int yn = y + 1 < kRT ? y + 1 : y;
                     bd[0] = src[yn * kCT + xl]; bd[1] = src[yn * kCT + x]; bd[2] = src[yn * kCT + xr];
                     if (y >= 1 && y < kRT - 1) {  // the region's edge rows are never updated
-                        float bnew = bm[1];
-                        if (xin) {
-                            // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
-                            const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
-                            float P = 0.0f, S = 1.0f;
+                        // the edge columns are never updated either: they compute on their
+                        // clamped (in-bounds) window like the others and keep their old
+                        // values, a select rather than a divergent branch
+                        // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
+                        const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
+                        float P = 0.0f, S = 1.0f;
 #pragma unroll
-                            for (int d = 0; d < 8; ++d) {
-                                const float xx = nb[d] * q[m][d];
-                                ign_acc(xx, P, S);
-                            }
-                            float a, ua;
-                            a_decode(A[m], a, ua);
-                            const float nn = ua * P;
-                            A[m] = a_encode(a + nn, ua * S);
-                            bnew = fmaf(pc, bm[1], nn);
+                        for (int d = 0; d < 8; ++d) {
+                            const float xx = nb[d] * q[m][d];
+                            ign_acc(xx, P, S);
                         }
-                        dst[y * kCT + x] = bnew;
+                        float a, ua;
+                        a_decode(A[m], a, ua);
+                        const float nn = ua * P;
+                        const float An = a_encode(a + nn, ua * S);
+                        A[m] = xin ? An : A[m];
+                        dst[y * kCT + x] = xin ? fmaf(pc, bm[1], nn) : bm[1];
                     }
                 }
                 __syncthreads();
