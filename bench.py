@@ -430,6 +430,8 @@ def main():
             # computed cell-steps per launch); null if the kernel changed since
             "traffic": None if tb is None else tb * (cs_l - sk_l) / n_l,
             "traffic_bytes_per_computed_cell_step": tb,
+            # DRAM utilisation: the measured bytes per launch over the launch's time
+            "dram_frac": None if tb is None else tb * (cs_l - sk_l) / (t_l / 1000.0) / 1e9 / hbm,
             "launches": n_l, "ms_per_launch": t_l / n_l, "cell_steps_per_launch": (cs_l - sk_l) / n_l,
             "skipped_frac": sk_l / max(1, cs_l),
             "alg_bytes_per_cell_step": alg,
