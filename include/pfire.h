@@ -149,7 +149,8 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                 float* grad_pveg, float* grad_pden);
 
 /* Current state and its global step number. S: discrete uint8 [R][H][W]; differentiable
- * FP32 [2][H][W] (a then b). step may be NULL. */
+ * FP32 [2][H][W] (a then b; the library keeps a and b down to about 1e-327, and values
+ * below FP32's range are returned as their FP32 rounding, down to 0). step may be NULL. */
 int pf_get_state(pf_ctx* ctx, int* step, void* S);
 
 /* Overwrite the current state and set the global step counter (resume, and the
@@ -157,6 +158,30 @@ int pf_get_state(pf_ctx* ctx, int* step, void* S);
  * 0-3. Differentiable: FP32 [2][H][W] with 0 <= b <= a <= 1 (not validated); cells with
  * a == b == 0 remain burnable. Discards the recorded run. */
 int pf_set_state(pf_ctx* ctx, int step, const void* S);
+
+/* Counts of the current state, and the near-ties of the discrete draws (Sec. 2.2: the
+ * transition compares p_ignite and p_continue with two random matrices; a cell whose
+ * draw lies within 1e-6 of the probability it is compared with is a near-tie, the only
+ * kind of cell whose transition may legitimately differ from the FP64 oracle's).
+ *   step                 the current global step.
+ *   cells[4]             discrete: cells in state 0, 1, 2, 3 over all realisations.
+ *                        Differentiable: non-burnable cells, the expected unburned
+ *                        cells (sum of 1 - a over burnable cells), the expected burning
+ *                        cells (sum of b) and the expected burned cells (sum of a - b),
+ *                        summed in FP64 in no fixed order.
+ *   near_ties_ignite     discrete: unburned cells with a burning neighbour whose
+ *                        ignition draw u satisfied |u - p_ignite| < 1e-6 (FP32 values),
+ *                        over every step and realisation since the last pf_forward
+ *                        (pf_advance adds to it). 0 in the differentiable form.
+ *   near_ties_continue   the same for burning cells and |u - p_continue| < 1e-6.
+ * Synchronous (reads the counts back); out is a host struct. */
+typedef struct pf_stats_t {
+    int step;
+    double cells[4];
+    long long near_ties_ignite;
+    long long near_ties_continue;
+} pf_stats_t;
+int pf_stats(pf_ctx* ctx, pf_stats_t* out);
 
 /* Ignition probability map p_ignite (Eq. 9) of the current state: FP32 [R][H][W]
  * (discrete: over burning neighbours, for every cell; differentiable: with burning
@@ -179,8 +204,9 @@ int pf_loss_bce(const float* a, const float* y, int64_t n, float* dL_da, double*
  * statically allocated device array of 16385 doubles (128 KB, held by every GPU that
  * loads the library until the process exits), which bounds n to
  * PF_NOALLOC_BCE_MAX_N elements (larger n: PF_EINVAL, message via pf_last_error(NULL)).
- * The first call on a device looks up the array's device address (once per device, with
- * that device current); make that first call before any stream capture. All calls share
+ * The first call on a device looks up the array's device address (once per device and
+ * context, with that device current); make that first call before any stream capture.
+ * After cudaDeviceReset the next call looks the address up again in the new context. All calls share
  * the array: calls whose work overlaps on the GPU (different streams, or concurrent host
  * threads) race on it and must be serialised by the caller. Each call overwrites every
  * entry it reads, so no clearing is needed. The paper has no counterpart: this is a

@@ -27,7 +27,7 @@ __all__ = [
     "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
     "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10", "pf_arrival_probability",
     "pf_affected_count", "pf_jaccard", "manhattan", "pf_set_slope", "simulate", "WildfireModel",
-    "EXPORTED_SYMBOLS",
+    "pf_stats", "PfStats", "EXPORTED_SYMBOLS",
 ]
 
 PF_DISCRETE, PF_DIFF = 0, 1
@@ -39,7 +39,7 @@ LIB_PATH = _build.LIB
 
 # every extern "C" entry point declared in include/pfire.h
 EXPORTED_SYMBOLS = [
-    "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
+    "pf_stats", "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
     "pf_loss_bce_noalloc", "pf_autotune", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
@@ -56,6 +56,11 @@ class PFireError(RuntimeError):
 
 class PfTuning(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("k", ctypes.c_int), ("K", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class PfStats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int), ("cells", ctypes.c_double * 4), ("near_ties_ignite", ctypes.c_longlong),
+                ("near_ties_continue", ctypes.c_longlong)]
 
 
 class PfJob(ctypes.Structure):
@@ -103,6 +108,7 @@ def load():
             "pf_get_state": ([vp, ctypes.POINTER(i), vp], i),
             "pf_set_state": ([vp, i, vp], i),
             "pf_ignition_map": ([vp, vp], i),
+            "pf_stats": ([vp, ctypes.POINTER(PfStats)], i),
             "pf_loss_bce": ([vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double), vp], i),
             "pf_loss_bce_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double), vp], i),
             "pf_set_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
@@ -257,6 +263,14 @@ def pf_set_state(h, step, S):
     _check(load().pf_set_state(h, int(step), _ptr(S, None, None, "S")), h)
 
 
+def pf_stats(h) -> dict:
+    """State counts and discrete near-tie counts of a context (see include/pfire.h)."""
+    st = PfStats()
+    _check(load().pf_stats(h, ctypes.byref(st)), h)
+    return dict(step=st.step, cells=[st.cells[i] for i in range(4)], near_ties_ignite=st.near_ties_ignite,
+                near_ties_continue=st.near_ties_continue)
+
+
 def pf_ignition_map(h, P_out):
     _check(load().pf_ignition_map(h, _ptr(P_out, torch.float32, None, "P_out")), h)
     return P_out
@@ -271,14 +285,12 @@ def pf_loss_bce(a, y, dL_da=None, want_loss=True, stream=None):
     return loss.value if want_loss else None
 
 
-def pf_loss_bce_noalloc(a, y, dL_da=None, want_loss=True, stream=None, n=None):
-    """pf_loss_bce with its scratch in a static device array (no device allocation);
-    n defaults to a.numel() (an explicit n is passed through unchecked, for tests of the
-    size limit)."""
-    n = a.numel() if n is None else int(n)
+def pf_loss_bce_noalloc(a, y, dL_da=None, want_loss=True, stream=None):
+    """pf_loss_bce with its scratch in a static device array (no device allocation)."""
+    n = a.numel()
     loss = ctypes.c_double()
-    _check(load().pf_loss_bce_noalloc(_ptr(a, torch.float32, None, "a"), _ptr(y, torch.float32, None, "y"), n,
-                                      _ptr(dL_da, torch.float32, None, "dL_da"),
+    _check(load().pf_loss_bce_noalloc(_ptr(a, torch.float32, n, "a"), _ptr(y, torch.float32, n, "y"), n,
+                                      _ptr(dL_da, torch.float32, n, "dL_da"),
                                       ctypes.byref(loss) if want_loss else None, _stream(stream)))
     return loss.value if want_loss else None
 
@@ -513,6 +525,9 @@ class FireModel:
         P = torch.empty((self.R if self.form == PF_DISCRETE else 1, self.H, self.W), dtype=torch.float32,
                         device="cuda")
         return pf_ignition_map(self.h, P)
+
+    def stats(self) -> dict:
+        return pf_stats(self.h)
 
 
 class DiffFire(torch.autograd.Function):

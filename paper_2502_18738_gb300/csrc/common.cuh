@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tma.cuh"
+
 namespace pf {
 
 // f_p(x) = tanh(C x) (Eq. 5/8), the paper's constant rounded to FP32.
@@ -62,6 +64,147 @@ __device__ __forceinline__ void a_decode(float A, float& a, float& ua) {
 }
 __device__ __forceinline__ float a_encode(float a, float ua) { return a < 0.5f ? a : -ua; }
 
+// ------------------------------------------------------ extended-range (tiered) state
+// Ahead of a fire the mean-field state falls far below FP32's range (2^-149): values of
+// a and b decay by a roughly constant factor per cell towards the light cone, and the
+// front, a pulled front, moves at a speed set by how deep that leading edge is carried.
+// Truncating it at FP32's floor slows the front measurably within a few hundred steps;
+// carrying it to FP64's floor (2^-1074) does not. Cells with a < 2^-64 are therefore
+// held in tiers k = 1 .. kKMax with a = A 2^(-64 k), b = B 2^(-64 k), A in [2^-64, 1):
+// an FP32 mantissa with an 11-bit exponent range, below 2^-1088 the cell is 0.
+// Storage keeps 8 bytes per cell. A cell of tier 0 is stored as before (A complement-
+// aware, B >= +0). A tiered cell stores -B (B's sign bit marks the tier) and its A
+// rounded to 19 mantissa bits with k in the low 5 bits.
+constexpr int kKMax = 16;
+constexpr int kKNone = 31;  // tier of "no burning neighbour": every tier difference >= 3
+constexpr float kTierUp = 0x1p64f, kTierDown = 0x1p-64f;
+
+// 2^(-64 d) for a tier difference d >= 0 (0 from d = 3 on, where a term is below 2^-192
+// of the largest); d < 0 gives 0 and is only used on zero terms
+__device__ __forceinline__ float tier_scale(int d) {
+    return d == 0 ? 1.0f : (d == 1 ? 0x1p-64f : (d == 2 ? 0x1p-128f : 0.0f));
+}
+
+// stored (As, Bs) -> tier k and the magnitudes A, B in that tier
+__device__ __forceinline__ void x_decode(float As, float Bs, float& A, float& B, int& k) {
+    const uint32_t ua = __float_as_uint(As), ub = __float_as_uint(Bs);
+    const bool tiered = (int32_t)ub < 0;
+    k = tiered ? (int)(ua & 31u) : 0;
+    A = tiered ? __uint_as_float(ua & ~31u) : As;
+    B = __uint_as_float(ub & 0x7fffffffu);
+}
+// the tier of a stored cell (0 for tier 0 and for a = 0)
+__device__ __forceinline__ int x_tier(float As, float Bs) {
+    return (int32_t)__float_as_uint(Bs) < 0 ? (int)(__float_as_uint(As) & 31u) : 0;
+}
+// A of a tiered cell as it is kept: 19 mantissa bits (round to nearest)
+__device__ __forceinline__ float x_round19(float A) { return __uint_as_float((__float_as_uint(A) + 0x10u) & ~31u); }
+__device__ __forceinline__ void x_encode(float A, float B, int k, float& As, float& Bs) {
+    if (k == 0) {
+        As = A;
+        Bs = B;
+    } else {
+        As = __uint_as_float((__float_as_uint(A) & ~31u) | (uint32_t)k);  // A already rounded
+        Bs = __uint_as_float(__float_as_uint(B) | 0x80000000u);
+    }
+}
+// Keep a non-complement cell normalised after its update: A in [2^-64, 1) for k >= 1
+// (A rounded to 19 bits there), and a cell below the deepest tier becomes 0. A cell that
+// is already normalised is left exactly as it is, so a cell whose inputs do not change
+// does not change either (which makes skipping quiescent tiles exact).
+__device__ __forceinline__ void x_renorm(float& A, float& B, int& k) {
+    if (!(A > 0.0f)) {  // complement-encoded (a >= 1/2, tier 0) or exactly 0
+        if (__float_as_uint(A) == 0u) { B = 0.0f; k = 0; }
+        return;
+    }
+    if (A >= 1.0f && k >= 1) { A *= kTierDown; B *= kTierDown; --k; }
+    while (A < kTierDown) {
+        if (k == kKMax) { A = 0.0f; B = 0.0f; k = 0; return; }
+        A *= kTierUp; B *= kTierUp; ++k;
+    }
+    if (k > 0) {
+        A = x_round19(A);
+        if (A >= 1.0f) { A *= kTierDown; B *= kTierDown; --k; }  // rounded up to 1: exact 2^-64 a tier up
+    }
+}
+
+// One cell's differentiable step in the tiered arithmetic (the definition every kernel
+// follows; on tier-0 inputs it is the plain FP32 update below, bit for bit).
+//   nb[d], nk[d]: the neighbours' B magnitudes and tiers (B = 0 outside the grid);
+//   q[d]: the folded factors into this cell; A, B, k: the cell's own (A complement-
+//   encoded when k = 0 and a >= 1/2); returns A', B', k' (A' rounded when tiered).
+// P is accumulated at the tier kP of the largest contributions (terms more than two
+// tiers down vanish); when kP >= 1 every true term is below 2^-61, so the survival
+// product stays 1 and P is a plain sum.
+__device__ __forceinline__ void x_update(const float (&nb)[8], const int (&nk)[8], const float (&q)[8], float A,
+                                         float B, int k, float pc, float& An, float& Bn, int& kn) {
+    int kP = kKNone;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) kP = nb[d] != 0.0f ? min(kP, nk[d]) : kP;
+    const bool kP0 = kP == 0;
+    float P = 0.0f, S = 1.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const float x = __fmul_rn(__fmul_rn(nb[d], q[d]), tier_scale(nk[d] - kP));
+        P = fmaf(x, S, P);
+        S = kP0 ? fmaf(-x, S, S) : S;
+    }
+    if (signbit(A)) {  // a >= 1/2, tier 0
+        const float a = __fadd_rn(1.0f, A), ua = -A;
+        const float n = __fmul_rn(__fmul_rn(ua, P), tier_scale(kP));
+        An = a_encode(__fadd_rn(a, n), __fmul_rn(ua, S));
+        Bn = fmaf(pc, B, n);
+        kn = 0;
+        return;
+    }
+    const int s = __float_as_uint(A) == 0u ? kP : min(k, kP);
+    const float h = tier_scale(k - s);
+    const float as = __fmul_rn(A, h), bs = __fmul_rn(B, h);
+    const float ua = k == 0 ? __fsub_rn(1.0f, A) : 1.0f;
+    const float n = __fmul_rn(ua, __fmul_rn(P, tier_scale(kP - s)));
+    const float an = __fadd_rn(as, n);
+    Bn = fmaf(pc, bs, n);
+    An = s == 0 ? a_encode(an, __fmul_rn(ua, S)) : an;
+    kn = s;
+    x_renorm(An, Bn, kn);
+}
+
+// The same update when the cell and every neighbour are in tier 0, from the P and S that
+// ign_acc accumulated over x_d = b_i q_dj (rounded products): the same roundings as
+// x_update on such inputs (every tier factor there is an exact 1).
+__device__ __forceinline__ void x_update_t0(float P, float S, float A, float B, float pc, float& An, float& Bn,
+                                            int& kn) {
+    float a, ua;
+    if (signbit(A)) {
+        a = __fadd_rn(1.0f, A);
+        ua = -A;
+    } else {
+        a = A;
+        ua = __fsub_rn(1.0f, A);
+    }
+    const float n = __fmul_rn(ua, P);
+    An = a_encode(__fadd_rn(a, n), __fmul_rn(ua, S));
+    Bn = fmaf(pc, B, n);
+    kn = 0;
+    if (!signbit(A)) x_renorm(An, Bn, kn);
+}
+
+// Scaled adjoint exponents for the tiered state (see the scaled adjoint below): sigma in
+// units of 8 bits, sigma = 8 k + min(-floor(log2 A), 63) / 8 (0 for a >= 1/2).
+__device__ __forceinline__ int x_sigma(float As, float Bs) {
+    const uint32_t ua = __float_as_uint(As);
+    if (ua == 0u) return 255;  // a == 0 (kSigmaZero)
+    if ((int32_t)ua < 0) return 0;
+    const int k = x_tier(As, Bs);
+    const int e = min(127 - (int)((ua >> 23) & 0xffu), 63);
+    return 8 * k + (e >> 3);
+}
+// 2^e for an integer exponent, 0 below 2^-126 (terms scaled that far down are dropped)
+__device__ __forceinline__ float exp2i(int e) {
+    e = min(e, 127);
+    return e < -126 ? 0.0f : __int_as_float((e + 127) << 23);
+}
+
 // Eq. 9 over the factors x_d = b_i q_dj of a differentiable step: S = prod_d (1 - x_d)
 // and P = 1 - S, accumulated as P += x_d S (the term x_d prod_{e<d} (1 - x_e)). Both are
 // sums / products of non-negative terms, so P keeps its relative accuracy when it is
@@ -74,26 +217,14 @@ __device__ __forceinline__ void ign_acc(float x, float& P, float& S) {
 // Scaled adjoint. Ahead of the fire the exact lambda grows about 4x per step backwards
 // in time while the states it multiplies shrink as fast; their products, which carry
 // the (pulled) front's sensitivity, stay O(1), but lambda itself overflows FP32 within
-// ~60 steps. The adjoint therefore stores mu_j = lambda_j * 2^-sigma_j with the per-cell
-// exponent sigma_j = -floor(log2 a_j) of the cell's own state, clamped to [0, 100]
-// (0 for a >= 1/2), and rescales every transfer between cells by exact powers of two.
-// sigma = kSigmaZero marks a == 0 exactly (outside the light cone, or non-burnable):
-// there lambda multiplies only exact zeros and is held at 0.
-constexpr int kSigmaMax = 100;
+// ~60 steps (and FP64 within a few hundred). The adjoint therefore stores
+// mu_j = lambda_j 2^(-8 sigma_j) with a per-cell exponent sigma_j (units of 8 bits) taken
+// from the cell's own state (x_sigma above: about -log2(a_j) / 8, 0 for a >= 1/2, up to
+// 8 kKMax + 7 in the deepest tier), and rescales every transfer between cells by the
+// exact power of two 2^(8 (sigma_j - sigma_i)). sigma = kSigmaZero marks a == 0 exactly
+// (outside the light cone, or non-burnable): there lambda multiplies only exact zeros
+// and is held at 0.
 constexpr int kSigmaZero = 255;
-
-// 2^-sigma of a cell from its encoded state A (1 for a >= 1/2, >= 2^-100 otherwise)
-__device__ __forceinline__ float adj_unit_inv(float A) {
-    if (signbit(A)) return 1.0f;
-    return fmaxf(__int_as_float(__float_as_int(A) & 0x7f800000), 7.8886090522101181e-31f);  // 2^-100
-}
-__device__ __forceinline__ int adj_sigma(float A) {
-    if (__float_as_int(A) == 0) return kSigmaZero;
-    return 127 - (__float_as_int(adj_unit_inv(A)) >> 23);
-}
-// 2^sigma and 2^-sigma for sigma in [0, 100] (exact powers of two)
-__device__ __forceinline__ float adj_unit(int sigma) { return __int_as_float((sigma + 127) << 23); }
-__device__ __forceinline__ float adj_unit_inv_of(int sigma) { return __int_as_float((127 - sigma) << 23); }
 
 // ---------------------------------------------------------------- launchers
 struct PrepArgs {
@@ -142,7 +273,12 @@ struct DiscreteArgs {
     // [acc_c0, acc_c1) of the grid they compute exactly once (the launcher sets these).
     float* acc;
     int acc_r0, acc_r1, acc_c0, acc_c1;
+    // near-tie counters (nullable): [0] cells whose ignition draw lies within kNearTie of
+    // p_ignite, [1] burning cells whose continue draw lies within kNearTie of p_continue;
+    // counted for the cells in the same rows / columns as the accumulator
+    unsigned long long* ties;
 };
+constexpr float kNearTie = 1e-6f;
 void launch_discrete_step(const DiscreteArgs& g, const uint8_t* S, uint8_t* Sn, const float* q,
                           uint32_t step, cudaStream_t s);
 // DCA gradient of one step (the paper's accumulator path): for each cell j that ignites
@@ -156,7 +292,7 @@ void launch_dca_step(const DiscreteArgs& g, const uint8_t* S, const uint8_t* Sn,
 int discrete_blocked_tile_rows();
 size_t discrete_blocked_smem(int TH, int KH);
 void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin, int TH, int KH, uint8_t* Sn,
-                                  const float* q, uint32_t step, int k, int* err, cudaStream_t s);
+                                  const float* q, uint32_t step, int k, int* err, TmaHook hk, cudaStream_t s);
 
 void launch_diff_step(int H, int W, int pitch, float p_continue, const float* ab, float* ab_next,
                       const float* q, cudaStream_t s);
@@ -203,7 +339,7 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
                          int n, const int* tile_list, int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
-                         cudaStream_t s);
+                         TmaHook hk, cudaStream_t s);
 // lam: scaled adjoint (mu_a, mu_b) [2][H][pitch]; sig: its exponents uint8 [H][pitch]
 void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float* ab, const float* q,
                          const float* lam1, const uint8_t* sig1, float* lam0, uint8_t* sig0, float* Gq,
@@ -274,7 +410,7 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq, int H, int pitch,
                             float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
-                            float* Gq, const int* tile_list, int* tile_count, int nsm, int* err,
+                            float* Gq, const int* tile_list, int* tile_count, int nsm, int* err, TmaHook hk,
                             cudaStream_t s);
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,
                                   cudaStream_t s);

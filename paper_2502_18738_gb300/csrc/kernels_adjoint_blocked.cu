@@ -23,6 +23,7 @@
 #include <cuda.h>
 
 #include <cstddef>
+#include <type_traits>
 
 #include "common.cuh"
 #include "tma.cuh"
@@ -52,6 +53,16 @@ struct Smem {
     float edump[kThreads];               // where the other threads' exchange stores go
 };
 
+// 2^(-8 sigma) of a cell known to be in tier 0 (1 for a >= 1/2 and for a = 0, where it
+// is never used), and 2^(8 s) for s in [0, 15]
+__device__ __forceinline__ float unit_inv_t0(float As) {
+    const uint32_t u = __float_as_uint(As);
+    if ((int32_t)u <= 0) return 1.0f;
+    const int e = min(127 - (int)(u >> 23), 63);
+    return __int_as_float((127 - 8 * (e >> 3)) << 23);
+}
+__device__ __forceinline__ float unit8(int s) { return __int_as_float((8 * s + 127) << 23); }
+
 __device__ __forceinline__ void origin(int tile, int tiles_x, int& r0, int& c0) {
     r0 = (tile / tiles_x) * kIR - kHalo;
     c0 = (tile % tiles_x) * kIC - kHalo;
@@ -64,7 +75,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const int* __restrict__ ntiles_live, int* __restrict__ next,
                       const float* __restrict__ lam_in, const uint8_t* __restrict__ sig_in,
                       float* __restrict__ lam_out, uint8_t* __restrict__ sig_out, float* __restrict__ Gq,
-                      int* __restrict__ err) {
+                      int* __restrict__ err, TmaHook hk) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     __shared__ __align__(8) uint64_t sbar[2];
@@ -142,6 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // not changed since then (the recompute may have skipped writing it later)
         const int z = (e & kTileFrozenBit) ? ((e & kTileCkptBit) ? 0 : zlast - (n - 1)) : zlast - m;
         mbar_arrive_expect_tx(&sbar[s], (uint32_t)(2 * kPlane * sizeof(float)));
+        if (hk.withhold) return;
         if (z == 0)
             tma_load_3d(sm.st[s], &tst0, &sbar[s], c0, r0, 0);
         else
@@ -154,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int r0, c0;
         origin(e & kTileIndexMask, tiles_x, r0, c0);
         mbar_arrive_expect_tx(&qbar, (uint32_t)(8 * kPlane * sizeof(float)));
-        tma_load_3d(sm.q, &tq, &qbar, c0, r0, 0);
+        if (!hk.withhold) tma_load_3d(sm.q, &tq, &qbar, c0, r0, 0);
     };
     if (tid == 0) {
         issue_q(0);
@@ -183,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int r0, c0;
         const bool frz = (ent & kTileFrozenBit) != 0;  // uniform across the CTA
         origin(ent & kTileIndexMask, tiles_x, r0, c0);
-        if (!__syncthreads_and(mbar_wait_bounded(&qbar, (uint32_t)(l & 1)))) {
+        if (!__syncthreads_and(mbar_wait_bounded(&qbar, (uint32_t)(l & 1), hk.spin))) {
             failed = true;
             break;
         }
@@ -207,27 +219,28 @@ __global__ void __launch_bounds__(kThreads, 1)
             // K_dj = (1 - a_j) q_dj 2^(sigma_j - sigma_i) kept in TMEM (64 consecutive
             // columns, read with two loads and one wait per step).
             const int i0 = l * n;
-            if (!__syncthreads_and(mbar_wait_bounded(&sbar[i0 & 1], (uint32_t)((i0 >> 1) & 1)))) {
+            if (!__syncthreads_and(mbar_wait_bounded(&sbar[i0 & 1], (uint32_t)((i0 >> 1) & 1), hk.spin))) {
                 failed = true;
                 break;
             }
             const float* stA = sm.st[i0 & 1];
             const bool xin = x >= 1 && x < kCT - 1;
+            const float* stB = stA + kPlane;
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 const int y = ys + k;
                 float kv[8];
-                const float Aj = stA[y * kCT + x];
-                const int sj = adj_sigma(Aj);
+                const float Aj = stA[y * kCT + x], Bj = stB[y * kCT + x];
+                const int sj = x_sigma(Aj, Bj);
                 // as in the general path: edge rows and columns of the region contribute nothing
                 const bool use = xin && y >= 1 && y < kRT - 1 && sj != kSigmaZero;
-                float aj, uaj;
-                a_decode(Aj, aj, uaj);
-                const float Uj = use ? adj_unit(sj) : 0.0f;
+                // 1 - a (1 in the tiers below 2^-64)
+                const float uaj = signbit(Aj) ? -Aj : ((int32_t)__float_as_uint(Bj) < 0 ? 1.0f : 1.0f - Aj);
 #pragma unroll
                 for (int d = 0; d < 8; ++d) {
                     const int yy = use ? y + dir_dr(d) : y, xx = use ? x + dir_dc(d) : x;
-                    kv[d] = (uaj * sm.q[d * kPlane + y * kCT + x]) * (Uj * adj_unit_inv(stA[yy * kCT + xx]));
+                    const int si = x_sigma(stA[yy * kCT + xx], stB[yy * kCT + xx]);
+                    kv[d] = use ? (uaj * sm.q[d * kPlane + y * kCT + x]) * exp2i(8 * (sj - si)) : 0.0f;
                 }
                 tmem_st8_nc(tbase + 8 * k, kv);  // frozen layout: cell k in columns 8k .. 8k + 7
             }
@@ -255,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int s = i & 1, ex = i & 1;
             // each thread waits for the stage itself; a wait that ran out is agreed on at
             // the step's barrier below (one barrier per step)
-            const bool stage_ok = mbar_wait_bounded(&sbar[s], (uint32_t)((i >> 1) & 1));
+            const bool stage_ok = mbar_wait_bounded(&sbar[s], (uint32_t)((i >> 1) & 1), hk.spin);
             const float* stA = sm.st[s];
             const float* stB = sm.st[s] + kPlane;
             // every row but the region's edges is processed: skipping the rows the shrinking
@@ -310,134 +323,188 @@ __global__ void __launch_bounds__(kThreads, 1)
                 sgc[0] = sgp[0];
                 sgc[1] = sgp[1];
             } else {
-            float bw[3][3], uw[3][3];
-            {
-                const int y0 = ys > 0 ? ys - 1 : 0;
-                const int cols[3] = {xl, x, xr};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    bw[0][c] = stB[y0 * kCT + cols[c]];
-                    uw[0][c] = adj_unit_inv(stA[y0 * kCT + cols[c]]);
-                    bw[1][c] = stB[ys * kCT + cols[c]];
-                    uw[1][c] = adj_unit_inv(stA[ys * kCT + cols[c]]);
-                }
-            }
+            // Cells in the tiers below 2^-64 at t (staged state) or t + 1 (sigma' >= 8)
+            // anywhere in the region take the general arithmetic: unit ratios
+            // 2^(8 (sigma' - sigma)) from integer exponents, b of tiered sources 0 in the
+            // factors 1 - b q and their exact b 2^(8 sigma') in dL/dq. Otherwise every
+            // exponent is below 8 and the ratios are products of per-cell powers of two,
+            // the same values.
+            bool tq = false;
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
-                const int y = ys + k;
-                float(&bu)[3] = bw[k % 3];
-                float(&bm)[3] = bw[(k + 1) % 3];
-                float(&bd)[3] = bw[(k + 2) % 3];
-                float(&uu)[3] = uw[k % 3];
-                float(&um)[3] = uw[(k + 1) % 3];
-                float(&ud)[3] = uw[(k + 2) % 3];
+                const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
+                tq |= (int32_t)__float_as_uint(stB[(ys + k) * kCT + x]) < 0 || (sp >= 8 && sp != kSigmaZero);
+            }
+            const bool slow = __syncthreads_or(tq);
+            auto cells = [&](auto tag) {
+                constexpr bool kSlow = decltype(tag)::value;
+                // stored b and (general path) sigma or (tier 0) 2^-sigma of rows y-1, y, y+1 in
+                // columns x-1, x, x+1: ring slot (row - ys + 1) % 3
+                float bw[3][3], uw[3][3];
+                int sw[3][3];
+                auto src = [&](int row, int c, float& bv, float& uv, int& sv) {
+                    const int o = row * kCT + c;
+                    bv = stB[o];
+                    if constexpr (kSlow) sv = x_sigma(stA[o], bv);
+                    else uv = unit_inv_t0(stA[o]);
+                };
                 {
-                    const int yd = y + 1 < kRT ? y + 1 : y;
+                    const int y0 = ys > 0 ? ys - 1 : 0;
                     const int cols[3] = {xl, x, xr};
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        bd[c] = stB[yd * kCT + cols[c]];
-                        ud[c] = adj_unit_inv(stA[yd * kCT + cols[c]]);
+                        src(y0, cols[c], bw[0][c], uw[0][c], sw[0][c]);
+                        src(ys, cols[c], bw[1][c], uw[1][c], sw[1][c]);
                     }
                 }
-                float(&wu)[3] = w[k % 3];        // source row y - 1 (R = k)
-                float(&wm)[3] = w[(k + 1) % 3];  // source row y
-                float(&wd)[3] = w[(k + 2) % 3];  // source row y + 1
-                const float Aown = stA[y * kCT + x];
-                const int sg = adj_sigma(Aown);
-                sgc[k >> 2] |= (uint32_t)sg << (8 * (k & 3));
-                const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
-                const bool live = sp != kSigmaZero;  // a > 0 at t + 1
-                const float Up = live ? adj_unit(sp) : 0.0f;
-                scl[k] = (sg == kSigmaZero) ? 0.0f : Up * um[1];
-                uint32_t tmv[16];
-                tmem_ld16_async(tbase + 16 * k, tmv);
-                tmem_wait_ld16(tmv);
-                if (y >= ylo && y < yhi) {  // uniform across the warp
-                    float qv[8], gv[8];
 #pragma unroll
-                    for (int d = 0; d < 8; ++d) {
-                        qv[d] = __uint_as_float(tmv[d]);
-                        gv[d] = __uint_as_float(tmv[8 + d]);
+                for (int k = 0; k < kM; ++k) {
+                    const int y = ys + k;
+                    float(&bu)[3] = bw[k % 3];
+                    float(&bm)[3] = bw[(k + 1) % 3];
+                    float(&bd)[3] = bw[(k + 2) % 3];
+                    float(&uu)[3] = uw[k % 3];
+                    float(&um)[3] = uw[(k + 1) % 3];
+                    float(&ud)[3] = uw[(k + 2) % 3];
+                    int(&su)[3] = sw[k % 3];
+                    int(&sm3)[3] = sw[(k + 1) % 3];
+                    int(&sd)[3] = sw[(k + 2) % 3];
+                    {
+                        const int yd = y + 1 < kRT ? y + 1 : y;
+                        const int cols[3] = {xl, x, xr};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) src(yd, cols[c], bd[c], ud[c], sd[c]);
                     }
-                    if (live) {
-                        // The region's edge columns (!xin) contribute nothing: they take
-                        // the same path on their clamped (in-bounds) window with tg = 0 and
-                        // P = 0, which leaves only l_a <- l_a scl, instead of diverging.
-                        // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
-                        const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
-                        const float nu[8] = {uu[0], uu[1], uu[2], um[0], um[2], ud[0], ud[1], ud[2]};
-                        float av, ua;
-                        a_decode(Aown, av, ua);
-                        const float ln = la[k] + lb[k];
-                        const float tg = xin ? ln * ua : 0.0f;  // l_P_j in units 2^sigma'(j)
-                        bool quiet = true;  // no neighbour burning (behind or ahead of the front)
+                    float(&wu)[3] = w[k % 3];        // source row y - 1 (R = k)
+                    float(&wm)[3] = w[(k + 1) % 3];  // source row y
+                    float(&wd)[3] = w[(k + 2) % 3];  // source row y + 1
+                    const float Aown = stA[y * kCT + x];
+                    int sg;
+                    if constexpr (kSlow) sg = sm3[1];
+                    else sg = x_sigma(Aown, 0.0f);
+                    sgc[k >> 2] |= (uint32_t)sg << (8 * (k & 3));
+                    const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
+                    const bool live = sp != kSigmaZero;  // a > 0 at t + 1
+                    float Up = 0.0f;
+                    if constexpr (kSlow) {
+                        scl[k] = (sg == kSigmaZero || !live) ? 0.0f : exp2i(8 * (sp - sg));
+                    } else {
+                        Up = live ? unit8(sp) : 0.0f;
+                        scl[k] = (sg == kSigmaZero) ? 0.0f : Up * um[1];
+                    }
+                    uint32_t tmv[16];
+                    tmem_ld16_async(tbase + 16 * k, tmv);
+                    tmem_wait_ld16(tmv);
+                    if (y >= ylo && y < yhi) {  // uniform across the warp
+                        float qv[8], gv[8];
 #pragma unroll
-                        for (int d = 0; d < 8; ++d) quiet &= nb[d] == 0.0f;
-                        if (quiet) {
-                            // P = 0, every leave-one-out product is 1 and every dL/dq term
-                            // carries b_i = 0: only the contributions t_d q_dj = tg q_dj remain
-                            la[k] *= scl[k];
-                            {  // tg = 0 (edge columns; cells burned out to a = 1 exactly) adds zeros
+                        for (int d = 0; d < 8; ++d) {
+                            qv[d] = __uint_as_float(tmv[d]);
+                            gv[d] = __uint_as_float(tmv[8 + d]);
+                        }
+                        if (live) {
+                            // The region's edge columns (!xin) contribute nothing: they take
+                            // the same path on their clamped (in-bounds) window with tg = 0 and
+                            // P = 0, which leaves only l_a <- l_a scl, instead of diverging.
+                            // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
+                            const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
+                            float r[8];  // 2^(8 (sigma'(j) - sigma(i))): to the units of source i
+                            if constexpr (kSlow) {
+                                const int ns[8] = {su[0], su[1], su[2], sm3[0], sm3[2], sd[0], sd[1], sd[2]};
 #pragma unroll
-                                for (int d = 0; d < 8; ++d) {
-                                    const float tq = tg * qv[d];
-                                    const float r = Up * nu[d];
-                                    const int j = dir_dc(d) + 1;
-                                    if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
-                                    else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
-                                    else wd[j] = fmaf(tq, r, wd[j]);
+                                for (int d = 0; d < 8; ++d) r[d] = exp2i(8 * (sp - ns[d]));
+                            } else {
+                                const float nu[8] = {uu[0], uu[1], uu[2], um[0], um[2], ud[0], ud[1], ud[2]};
+#pragma unroll
+                                for (int d = 0; d < 8; ++d) r[d] = Up * nu[d];
+                            }
+                            // 1 - a of this cell (1 in the tiers below 2^-64)
+                            float ua;
+                            if constexpr (kSlow)
+                                ua = signbit(Aown) ? -Aown : ((int32_t)__float_as_uint(bm[1]) < 0 ? 1.0f : 1.0f - Aown);
+                            else
+                                ua = signbit(Aown) ? -Aown : 1.0f - Aown;
+                            const float ln = la[k] + lb[k];
+                            const float tg = xin ? ln * ua : 0.0f;  // l_P_j in units 2^(8 sigma'(j))
+                            bool quiet = true;  // no neighbour burning (behind or ahead of the front)
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) quiet &= nb[d] == 0.0f;
+                            if (quiet) {
+                                // P = 0, every leave-one-out product is 1 and every dL/dq term
+                                // carries b_i = 0: only the contributions t_d q_dj = tg q_dj remain
+                                la[k] *= scl[k];
+                                {  // tg = 0 (edge columns; cells burned out to a = 1 exactly) adds zeros
+#pragma unroll
+                                    for (int d = 0; d < 8; ++d) {
+                                        const float tqv = tg * qv[d];
+                                        const int j = dir_dc(d) + 1;
+                                        if (dir_dr(d) < 0) wu[j] = fmaf(tqv, r[d], wu[j]);
+                                        else if (dir_dr(d) == 0) wm[j] = fmaf(tqv, r[d], wm[j]);
+                                        else wd[j] = fmaf(tqv, r[d], wd[j]);
+                                    }
+                                }
+                            } else {
+                                float f[8];
+                                // b of a tiered source is below 2^-64: its factor is exactly 1
+#pragma unroll
+                                for (int d = 0; d < 8; ++d) f[d] = fmaf(kSlow ? -fmaxf(nb[d], 0.0f) : -nb[d], qv[d], 1.0f);
+                                // t_d = tg prod_{e != d} f_e by a product tree over pairs and
+                                // halves (no division: a factor can be exactly 0)
+                                const float p01 = f[0] * f[1], p23 = f[2] * f[3], p45 = f[4] * f[5], p67 = f[6] * f[7];
+                                const float p03 = p01 * p23, p47 = p45 * p67;
+                                // P enters only l_a = l_a' - l_n P here, where 1 - S's absolute
+                                // error (a few 1e-8) is harmless; the forward keeps the recurrence
+                                const float P = xin ? 1.0f - p03 * p47 : 0.0f;
+                                la[k] = fmaf(-ln, P, la[k]) * scl[k];
+                                {  // as above: unconditional, tg = 0 adds zeros
+                                    const float g03 = tg * p47, g47 = tg * p03;
+                                    const float r01 = g03 * p23, r23 = g03 * p01, r45 = g47 * p67, r67 = g47 * p45;
+                                    const float t[8] = {f[1] * r01, f[0] * r01, f[3] * r23, f[2] * r23,
+                                                        f[5] * r45, f[4] * r45, f[7] * r67, f[6] * r67};
+                                    float g[8];  // b_i 2^(8 sigma'(j))
+                                    if constexpr (kSlow) {
+                                        const int ns[8] = {su[0], su[1], su[2], sm3[0], sm3[2], sd[0], sd[1], sd[2]};
+#pragma unroll
+                                        for (int d = 0; d < 8; ++d)
+                                            g[d] = (fabsf(nb[d]) * exp2i(8 * (ns[d] & 7))) * r[d];
+                                    } else {
+#pragma unroll
+                                        for (int d = 0; d < 8; ++d) g[d] = nb[d] * Up;
+                                    }
+#pragma unroll
+                                    for (int d = 0; d < 8; ++d) {
+                                        gv[d] = fmaf(t[d], g[d], gv[d]);
+                                        const float tqv = t[d] * qv[d];
+                                        const int j = dir_dc(d) + 1;
+                                        if (dir_dr(d) < 0) wu[j] = fmaf(tqv, r[d], wu[j]);
+                                        else if (dir_dr(d) == 0) wm[j] = fmaf(tqv, r[d], wm[j]);
+                                        else wd[j] = fmaf(tqv, r[d], wd[j]);
+                                    }
                                 }
                             }
                         } else {
-                            float f[8];
-#pragma unroll
-                            for (int d = 0; d < 8; ++d) f[d] = fmaf(-nb[d], qv[d], 1.0f);
-                            // t_d = tg prod_{e != d} f_e by a product tree over pairs and
-                            // halves (no division: a factor can be exactly 0)
-                            const float p01 = f[0] * f[1], p23 = f[2] * f[3], p45 = f[4] * f[5], p67 = f[6] * f[7];
-                            const float p03 = p01 * p23, p47 = p45 * p67;
-                            // P enters only l_a = l_a' - l_n P here, where 1 - S's absolute
-                            // error (a few 1e-8) is harmless; the forward keeps the recurrence
-                            const float P = xin ? 1.0f - p03 * p47 : 0.0f;
-                            la[k] = fmaf(-ln, P, la[k]) * scl[k];
-                            {  // as above: unconditional, tg = 0 adds zeros
-                                const float g03 = tg * p47, g47 = tg * p03;
-                                const float r01 = g03 * p23, r23 = g03 * p01, r45 = g47 * p67, r67 = g47 * p45;
-                                const float t[8] = {f[1] * r01, f[0] * r01, f[3] * r23, f[2] * r23,
-                                                    f[5] * r45, f[4] * r45, f[7] * r67, f[6] * r67};
-#pragma unroll
-                                for (int d = 0; d < 8; ++d) {
-                                    gv[d] = fmaf(t[d], nb[d] * Up, gv[d]);
-                                    const float tq = t[d] * qv[d];
-                                    const float r = Up * nu[d];  // 2^(sigma'(j) - sigma(i)): to the units of source i
-                                    const int j = dir_dc(d) + 1;
-                                    if (dir_dr(d) < 0) wu[j] = fmaf(tq, r, wu[j]);
-                                    else if (dir_dr(d) == 0) wm[j] = fmaf(tq, r, wm[j]);
-                                    else wd[j] = fmaf(tq, r, wd[j]);
-                                }
-                            }
+                            la[k] *= scl[k];
                         }
+                        tmem_st8_nc(tbase + 16 * k + 8, gv);
                     } else {
                         la[k] *= scl[k];
                     }
-                    tmem_st8_nc(tbase + 16 * k + 8, gv);
-                } else {
-                    la[k] *= scl[k];
-                }
-                // row R = k (source row ys + k - 1) is complete
-                if (k == 0) {
+                    // row R = k (source row ys + k - 1) is complete
+                    if (k == 0) {
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) sm.vtop[ex][strip][j][x] = wu[j];
-                } else {
-                    const float fr = __shfl_down_sync(0xffffffffu, wu[0], 1);  // from column x + 1
-                    const float fl = __shfl_up_sync(0xffffffffu, wu[2], 1);    // from column x - 1
-                    own[k - 1] = wu[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
-                    exchange(ex, k - 1, wu[2], wu[0]);
-                }
+                        for (int j = 0; j < 3; ++j) sm.vtop[ex][strip][j][x] = wu[j];
+                    } else {
+                        const float fr = __shfl_down_sync(0xffffffffu, wu[0], 1);  // from column x + 1
+                        const float fl = __shfl_up_sync(0xffffffffu, wu[2], 1);    // from column x - 1
+                        own[k - 1] = wu[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
+                        exchange(ex, k - 1, wu[2], wu[0]);
+                    }
 #pragma unroll
-                for (int j = 0; j < 3; ++j) wu[j] = 0.0f;  // the slot becomes row R = k + 3
-            }
+                    for (int j = 0; j < 3; ++j) wu[j] = 0.0f;  // the slot becomes row R = k + 3
+                }
+            };
+            if (slow) cells(std::true_type{});
+            else cells(std::false_type{});
             }
             // rows R = 8 (source row ys + 7, slot 8 % 3) and R = 9 (the next strip's first row)
             {
@@ -514,9 +581,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (failed && tid == 0) {
         atomicExch(err, kErrTmaTimeout);
         // give the copies in flight one more bounded wait before the CTA exits
-        mbar_wait_bounded(&qbar, 0);
-        mbar_wait_bounded(&sbar[0], 0);
-        mbar_wait_bounded(&sbar[1], 0);
+        mbar_wait_bounded(&qbar, 0, hk.spin);
+        mbar_wait_bounded(&sbar[0], 0, hk.spin);
+        mbar_wait_bounded(&sbar[1], 0, hk.spin);
     }
     tmem_sync_threads();
     if (warp == 0) tmem_dealloc(tslot, kTmemCols);
@@ -712,7 +779,7 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
 void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq, int H, int pitch,
                             float pc, int zlast,
                             int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
-                            float* Gq, const int* tile_list, int* tile_count, int nsm, int* err,
+                            float* Gq, const int* tile_list, int* tile_count, int nsm, int* err, TmaHook hk,
                             cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
     const int ntiles = adjoint_blocked_tiles(H, pitch);
@@ -720,7 +787,7 @@ void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, con
     k_adjoint_blocked<<<grid, kThreads, adjoint_blocked_smem(), s>>>(*tst, *tst0, *tq, H, pitch, pc, zlast, n, tiles_x,
                                                                      tile_list, tile_count, tile_count + 1, lam_in,
                                                                      sig_in, lam_out,
-                                                                     sig_out, Gq, err);
+                                                                     sig_out, Gq, err, hk);
 }
 
 }  // namespace pf

@@ -154,16 +154,23 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
                 else ((uint8_t*)J.st[(b + 1) & 1])[(size_t)gr * J.P + gc] = v;
             }
         } else {
+            // differentiable: A (decoded, own cell only) in sA[0], b and its tier in
+            // ping-pong buffers (the tiers in the otherwise unused second half of sA)
+            uint8_t(&sK)[2][kRR][kRC] = *reinterpret_cast<uint8_t(*)[2][kRR][kRC]>(&sA[1]);
             const float* in = (const float*)J.st[b & 1];
             bool burning = false;
             for (int i = tid; i < kRR * kRC; i += kBThreads) {
                 const int y = i / kRC, x = i % kRC, gr = r0 + y, gc = c0 + x;
                 const bool inside = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
                 const size_t g = (size_t)gr * J.P + gc;
-                sA[0][y][x] = inside ? __ldcg(in + g) : 0.0f;
-                const float bv = inside ? __ldcg(in + plane + g) : 0.0f;
+                float Av = 0.0f, bv = 0.0f;
+                int kv = 0;
+                if (inside) x_decode(__ldcg(in + g), __ldcg(in + plane + g), Av, bv, kv);
+                sA[0][y][x] = Av;
                 sB[0][y][x] = bv;
                 sB[1][y][x] = bv;
+                sK[0][y][x] = (uint8_t)kv;
+                sK[1][y][x] = (uint8_t)kv;
                 burning |= bv != 0.0f;
             }
             // b = 0 in the whole region: every P is 0, the state does not change
@@ -174,21 +181,23 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
                     for (int i = tid; i < (kRR - 2) * (kRC - 2); i += kBThreads) {
                         const int y = 1 + i / (kRC - 2), x = 1 + i % (kRC - 2), gr = r0 + y, gc = c0 + x;
                         float bnew = sB[cur][y][x];
+                        int knew = sK[cur][y][x];
                         if (gr >= 0 && gr < J.H && gc >= 0 && gc < J.W) {
                             const size_t qoff = (size_t)gr * J.P + gc;
-                            float P = 0.0f, S = 1.0f;
+                            float nb[8], qv[8];
+                            int nk[8];
 #pragma unroll
                             for (int d = 0; d < 8; ++d) {
-                                const float xx = sB[cur][y + dir_dr(d)][x + dir_dc(d)] * __ldg(J.q + d * plane + qoff);
-                                ign_acc(xx, P, S);
+                                nb[d] = sB[cur][y + dir_dr(d)][x + dir_dc(d)];
+                                nk[d] = sK[cur][y + dir_dr(d)][x + dir_dc(d)];
+                                qv[d] = __ldg(J.q + d * plane + qoff);
                             }
-                            float a, ua;
-                            a_decode(sA[0][y][x], a, ua);
-                            const float n = ua * P;
-                            sA[0][y][x] = a_encode(a + n, ua * S);  // own cell only: in place
-                            bnew = fmaf(J.pc, sB[cur][y][x], n);
+                            float An;
+                            x_update(nb, nk, qv, sA[0][y][x], sB[cur][y][x], knew, J.pc, An, bnew, knew);
+                            sA[0][y][x] = An;  // own cell only: in place
                         }
                         sB[cur ^ 1][y][x] = bnew;
+                        sK[cur ^ 1][y][x] = (uint8_t)knew;
                     }
                     __syncthreads();
                     cur ^= 1;
@@ -198,8 +207,8 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
                     for (int i = tid; i < kTR * kTC; i += kBThreads) {
                         const int y = kB + i / kTC, x = kB + i % kTC, gr = r0 + y, gc = c0 + x;
                         if (gr >= J.H || gc >= J.W) continue;
-                        o[(size_t)gr * J.P + gc] = sA[0][y][x];
-                        o[plane + (size_t)gr * J.P + gc] = sB[cur][y][x];
+                        x_encode(sA[0][y][x], sB[cur][y][x], sK[cur][y][x], o[(size_t)gr * J.P + gc],
+                                 o[plane + (size_t)gr * J.P + gc]);
                     }
                 }
             }
@@ -207,16 +216,15 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
                 const int y = kB + i / kTC, x = kB + i % kTC, gr = r0 + y, gc = c0 + x;
                 if (gr >= J.H || gc >= J.W) continue;
                 const float Av = sA[0][y][x], bv = sB[cur][y][x];
+                const int kv = sK[cur][y][x];
                 if (last) {
-                    float a, ua;
-                    a_decode(Av, a, ua);
+                    // the output in plain FP32 (a tier's values read as 0 below FP32's range)
                     float* o = (float*)J.out;
-                    o[(size_t)gr * J.W + gc] = a;
-                    o[(size_t)J.H * J.W + (size_t)gr * J.W + gc] = bv;
+                    o[(size_t)gr * J.W + gc] = signbit(Av) ? 1.0f + Av : Av * tier_scale(kv);
+                    o[(size_t)J.H * J.W + (size_t)gr * J.W + gc] = bv * tier_scale(kv);
                 } else {
                     float* o = (float*)J.st[(b + 1) & 1];
-                    o[(size_t)gr * J.P + gc] = Av;
-                    o[plane + (size_t)gr * J.P + gc] = bv;
+                    x_encode(Av, bv, kv, o[(size_t)gr * J.P + gc], o[plane + (size_t)gr * J.P + gc]);
                 }
             }
         }
@@ -245,8 +253,10 @@ constexpr int kAThreads = 256;
 
 struct AdjSmem {
     float mua[kARR][kARC], mub[kARR][kARC];  // scaled lambda (mu) at t + 1, then at t
-    float sa[kARR][kARC], sb[kARR][kARC];    // state (A, b) at t
-    float su[kARR][kARC];                    // 2^-sigma(t)
+    float sa[kARR][kARC];                    // stored A at t
+    float sb[kARR][kARC];                    // b at t in tier 0, 0 in the tiers (their 1 - b q is 1)
+    float sbs[kARR][kARC];                   // b at t in the cell's own adjoint units, b 2^(8 sigma)
+    int ss[kARR][kARC];                      // sigma(t)
     float sc[8][kARR][kARC];                 // contributions of targets, in source units
     float gq[8][kAR][kAC];                   // the item's dL/dq of the interior
     uint8_t sg[kARR][kARC];                  // sigma at t + 1, then at t
@@ -346,10 +356,13 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                 const int y = i / kARC, x = i % kARC, gr = r0 + y, gc = c0 + x;
                 const bool in = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
                 const size_t g = (size_t)gr * J.P + gc;
-                const float A = in ? __ldcg(st + g) : 0.0f;
-                sm.sa[y][x] = A;
-                sm.sb[y][x] = in ? __ldcg(st + plane + g) : 0.0f;
-                sm.su[y][x] = in ? adj_unit_inv(A) : 1.0f;
+                const float As = in ? __ldcg(st + g) : 0.0f;
+                const float Bs = in ? __ldcg(st + plane + g) : 0.0f;
+                const int sg = in ? x_sigma(As, Bs) : kSigmaZero;
+                sm.sa[y][x] = As;
+                sm.sb[y][x] = fmaxf(Bs, 0.0f);
+                sm.sbs[y][x] = fabsf(Bs) * exp2i(8 * (sg & 7));
+                sm.ss[y][x] = sg;
             }
             __syncthreads();
             // targets j: contributions to their sources and, in the interior, dL/dq
@@ -362,16 +375,11 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                     continue;
                 }
                 const size_t g = (size_t)gr * J.P + gc;
-                const float Up = adj_unit(sgp);
-                float qd[8], bi[8], f[8];
-                float P = 0.0f, S = 1.0f;
+                float qd[8], f[8];
 #pragma unroll
                 for (int d = 0; d < 8; ++d) {
                     qd[d] = __ldg(J.q + d * plane + g);
-                    bi[d] = sm.sb[y + dir_dr(d)][x + dir_dc(d)];
-                    const float xx = bi[d] * qd[d];
-                    f[d] = 1.0f - xx;
-                    ign_acc(xx, P, S);
+                    f[d] = fmaf(-sm.sb[y + dir_dr(d)][x + dir_dc(d)], qd[d], 1.0f);
                 }
                 float pre[8], suf[8];
                 pre[0] = 1.0f;
@@ -380,20 +388,25 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                 suf[7] = 1.0f;
 #pragma unroll
                 for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
+                const float P = 1.0f - pre[7] * f[7];
                 const float la = sm.mua[y][x], lb = sm.mub[y][x];
                 const float ln = la + lb;
-                float av, ua;
-                a_decode(sm.sa[y][x], av, ua);
+                const float As = sm.sa[y][x];
+                const int sj = sm.ss[y][x];
+                // 1 - a (1 in the tiers below 2^-64, whose sigma is >= 8)
+                const float ua = signbit(As) ? -As : (sj >= 8 ? 1.0f : 1.0f - As);
                 const float tg = ln * ua;
                 const bool interior = y >= kAH && y < kAH + kAR && x >= kAH && x < kAH + kAC;
 #pragma unroll
                 for (int d = 0; d < 8; ++d) {
+                    const int yy = y + dir_dr(d), xx = x + dir_dc(d);
                     const float tt = tg * (pre[d] * suf[d]);
-                    const float r_d = Up * sm.su[y + dir_dr(d)][x + dir_dc(d)];
+                    const float r_d = exp2i(8 * (sgp - sm.ss[yy][xx]));
                     sm.sc[d][y][x] = tt * qd[d] * r_d;
-                    if (interior) sm.gq[d][y - kAH][x - kAH] = fmaf(tt, bi[d] * Up, sm.gq[d][y - kAH][x - kAH]);
+                    if (interior)
+                        sm.gq[d][y - kAH][x - kAH] = fmaf(tt, sm.sbs[yy][xx] * r_d, sm.gq[d][y - kAH][x - kAH]);
                 }
-                sm.mua[y][x] = (la - ln * P) * (Up * sm.su[y][x]);  // own cell: in place
+                sm.mua[y][x] = fmaf(-ln, P, la) * exp2i(8 * (sgp - sj));  // own cell: in place
             }
             __syncthreads();
             // sources i: lambda_b at t, and the masks of cells with a = 0
@@ -401,9 +414,9 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                 const int y = 2 + i / (kARC - 4), x = 2 + i % (kARC - 4), gr = r0 + y, gc = c0 + x;
                 const bool in = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
                 const int sgp = sm.sg[y][x];
-                const int sgt = in ? adj_sigma(sm.sa[y][x]) : kSigmaZero;
+                const int sgt = in ? sm.ss[y][x] : kSigmaZero;
                 float acc = 0.0f;
-                if (sgp != kSigmaZero) acc = J.pc * sm.mub[y][x] * (adj_unit(sgp) * sm.su[y][x]);
+                if (sgp != kSigmaZero) acc = J.pc * sm.mub[y][x] * exp2i(8 * (sgp - sgt));
 #pragma unroll
                 for (int d = 0; d < 8; ++d) acc += sm.sc[d][y - dir_dr(d)][x - dir_dc(d)];
                 if (sgt == kSigmaZero || sgp == kSigmaZero) {

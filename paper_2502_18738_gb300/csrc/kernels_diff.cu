@@ -24,22 +24,26 @@ __global__ void __launch_bounds__(256) k_diff_step(int H, int W, int pitch, floa
         abn[plane + j] = 0.0f;
         return;
     }
-    const float* b = ab + plane;
-    float P = 0.0f, S = 1.0f;
+    float nb[8], qv[8];
+    int nk[8];
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const int ri = r + dir_dr(d), ci = c + dir_dc(d);
-        if (ri < 0 || ri >= H || ci < 0 || ci >= W) continue;
-        const float x = __ldg(b + (size_t)ri * pitch + ci) * __ldg(q + d * plane + j);
-        ign_acc(x, P, S);
+        const bool in = ri >= 0 && ri < H && ci >= 0 && ci < W;
+        const size_t i = in ? (size_t)ri * pitch + ci : j;
+        float Ai, Bi;
+        x_decode(__ldg(ab + i), __ldg(ab + plane + i), Ai, Bi, nk[d]);
+        nb[d] = in ? Bi : 0.0f;
+        qv[d] = __ldg(q + d * plane + j);
     }
-    float a, ua;
-    a_decode(ab[j], a, ua);
-    const float n = ua * P;
-    abn[j] = a_encode(a + n, ua * S);
-    abn[plane + j] = fmaf(pc, b[j], n);
+    float A, B, An, Bn;
+    int k, kn;
+    x_decode(ab[j], ab[plane + j], A, B, k);
+    x_update(nb, nk, qv, A, B, k, pc, An, Bn, kn);
+    x_encode(An, Bn, kn, abn[j], abn[plane + j]);
 }
 
+// p_ignite of every cell (FP32; values below FP32's range read as 0)
 __global__ void k_ignition_map_diff(int H, int W, int pitch, const float* __restrict__ ab,
                                     const float* __restrict__ q, float* __restrict__ Pout) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,15 +51,25 @@ __global__ void k_ignition_map_diff(int H, int W, int pitch, const float* __rest
     const int r = (int)(idx / W), c = (int)(idx % W);
     const size_t plane = (size_t)H * pitch;
     const size_t j = (size_t)r * pitch + c;
-    const float* b = ab + plane;
-    float P = 0.0f, S = 1.0f;
+    float nb[8];
+    int nk[8];
+    int kP = kKNone;
     for (int d = 0; d < 8; ++d) {
         const int ri = r + dir_dr(d), ci = c + dir_dc(d);
-        if (ri < 0 || ri >= H || ci < 0 || ci >= W) continue;
-        const float x = b[(size_t)ri * pitch + ci] * q[d * plane + j];
-        ign_acc(x, P, S);
+        const bool in = ri >= 0 && ri < H && ci >= 0 && ci < W;
+        const size_t i = in ? (size_t)ri * pitch + ci : j;
+        float Ai;
+        x_decode(ab[i], ab[plane + i], Ai, nb[d], nk[d]);
+        nb[d] = in ? nb[d] : 0.0f;
+        kP = nb[d] != 0.0f ? min(kP, nk[d]) : kP;
     }
-    Pout[idx] = P;
+    float P = 0.0f, S = 1.0f;
+    for (int d = 0; d < 8; ++d) {
+        const float x = (nb[d] * q[d * plane + j]) * tier_scale(nk[d] - kP);
+        P = fmaf(x, S, P);
+        S = kP == 0 ? fmaf(-x, S, S) : S;
+    }
+    Pout[idx] = P * tier_scale(kP);
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -76,8 +90,9 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
                                                             const uint8_t* __restrict__ sig1,
                                                             float* __restrict__ lam0, uint8_t* __restrict__ sig0,
                                                             float* __restrict__ Gq) {
-    __shared__ float sb[kAY + 4][kAX + 4];          // b at t, rows r0-2 .. r0+kAY+1
-    __shared__ float su[kAY + 4][kAX + 4];          // 2^-sigma(t) of the same cells
+    __shared__ float sbt[kAY + 4][kAX + 4];         // true b at t (FP32, tiers flushed), rows r0-2 .. r0+kAY+1
+    __shared__ float sbs[kAY + 4][kAX + 4];         // b at t in the cell's own adjoint units, b 2^(8 sigma)
+    __shared__ int ssg[kAY + 4][kAX + 4];           // sigma(t) of the same cells
     __shared__ float sc[8][kAY + 2][kAX + 2];       // contributions of targets j, in source units
     const int c0 = blockIdx.x * kAX, r0 = blockIdx.y * kAY;
     const int tid = threadIdx.y * kAX + threadIdx.x;
@@ -90,8 +105,20 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
         const int y = i / (kAX + 4), x = i % (kAX + 4);
         const int r = r0 - 2 + y, c = c0 - 2 + x;
         const bool in = r >= 0 && r < H && c >= 0 && c < W;
-        sb[y][x] = in ? b[(size_t)r * pitch + c] : 0.0f;
-        su[y][x] = in ? adj_unit_inv(a[(size_t)r * pitch + c]) : 1.0f;
+        float bt = 0.0f, bs = 0.0f;
+        int sg = kSigmaZero;
+        if (in) {
+            const float As = a[(size_t)r * pitch + c], Bs = b[(size_t)r * pitch + c];
+            float A, B;
+            int k;
+            x_decode(As, Bs, A, B, k);
+            sg = x_sigma(As, Bs);
+            bt = B * tier_scale(k);
+            bs = sg == kSigmaZero ? 0.0f : B * exp2i(8 * sg - 64 * k);
+        }
+        sbt[y][x] = bt;
+        sbs[y][x] = bs;
+        ssg[y][x] = sg;
     }
     __syncthreads();
     for (int i = tid; i < (kAY + 2) * (kAX + 2); i += kAX * kAY) {
@@ -104,16 +131,11 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
             for (int d = 0; d < 8; ++d) sc[d][y][x] = 0.0f;
             continue;
         }
-        const float Up = adj_unit(sgp);  // 2^sigma'(j)
-        float qd[8], bi[8], f[8];
-        float P = 0.0f, S = 1.0f;
+        float qd[8], f[8];
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             qd[d] = __ldg(q + d * plane + j);
-            bi[d] = sb[y + 1 + dir_dr(d)][x + 1 + dir_dc(d)];
-            const float xx = bi[d] * qd[d];
-            f[d] = 1.0f - xx;
-            ign_acc(xx, P, S);
+            f[d] = fmaf(-sbt[y + 1 + dir_dr(d)][x + 1 + dir_dc(d)], qd[d], 1.0f);
         }
         float pre[8], suf[8];
         pre[0] = 1.0f;
@@ -122,20 +144,23 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
         suf[7] = 1.0f;
 #pragma unroll
         for (int d = 6; d >= 0; --d) suf[d] = suf[d + 1] * f[d + 1];
+        const float P = 1.0f - pre[7] * f[7];
         const float la = __ldg(la1 + j), lb = __ldg(lb1 + j);
         const float ln = la + lb;
-        float av, ua;
-        a_decode(__ldg(a + j), av, ua);
-        const float tg = ln * ua;  // l_P_j in units 2^sigma'(j)
+        const float As = __ldg(a + j);
+        // 1 - a: 1 for a tiered cell (a < 2^-64)
+        const float ua = signbit(As) ? -As : (x_tier(As, __ldg(b + j)) == 0 ? 1.0f - As : 1.0f);
+        const float tg = ln * ua;  // l_P_j in units 2^(8 sigma'(j))
         const bool interior = (y >= 1 && y <= kAY && x >= 1 && x <= kAX);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
+            const int yy = y + 1 + dir_dr(d), xx = x + 1 + dir_dc(d);
             const float t = tg * (pre[d] * suf[d]);
-            const float r_d = Up * su[y + 1 + dir_dr(d)][x + 1 + dir_dc(d)];  // 2^(sigma'(j) - sigma(i))
+            const float r_d = exp2i(8 * (sgp - ssg[yy][xx]));  // 2^(8 (sigma'(j) - sigma(i)))
             sc[d][y][x] = t * qd[d] * r_d;
-            if (interior) Gq[d * plane + j] = fmaf(t, bi[d] * Up, Gq[d * plane + j]);
+            if (interior) Gq[d * plane + j] = fmaf(t, sbs[yy][xx] * r_d, Gq[d * plane + j]);
         }
-        if (interior) lam0[j] = (la - ln * P) * (Up * su[y + 1][x + 1]);
+        if (interior) lam0[j] = fmaf(-ln, P, la) * exp2i(8 * (sgp - ssg[y + 1][x + 1]));
     }
     __syncthreads();
     const int x = threadIdx.x, y = threadIdx.y;
@@ -143,9 +168,9 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
     if (r >= H || c >= W) return;
     const size_t j = (size_t)r * pitch + c;
     const int sgp = __ldg(sig1 + j);
-    const int sg = adj_sigma(__ldg(a + j));
+    const int sg = ssg[y + 2][x + 2];
     float acc = 0.0f;
-    if (sgp != kSigmaZero) acc = pc * __ldg(lb1 + j) * (adj_unit(sgp) * su[y + 2][x + 2]);
+    if (sgp != kSigmaZero) acc = pc * __ldg(lb1 + j) * exp2i(8 * (sgp - sg));
 #pragma unroll
     for (int d = 0; d < 8; ++d) acc += sc[d][y + 1 - dir_dr(d)][x + 1 - dir_dc(d)];  // target j = i - offset
     if (sg == kSigmaZero || sgp == kSigmaZero) {  // a == 0 at t: lambda multiplies only zeros
@@ -167,9 +192,9 @@ __global__ void k_adjoint_init(const float* __restrict__ dLda, const float* __re
     float la = 0.0f, lb = 0.0f;
     int sg = kSigmaZero;
     if (c < W) {
-        sg = adj_sigma(ab[j]);
+        sg = x_sigma(ab[j], ab[plane + j]);
         if (sg != kSigmaZero) {
-            const float ui = adj_unit_inv_of(sg);
+            const float ui = exp2i(-8 * sg);
             if (dLda) la = dLda[(size_t)r * W + c] * ui;
             if (dLdb) lb = dLdb[(size_t)r * W + c] * ui;
         }

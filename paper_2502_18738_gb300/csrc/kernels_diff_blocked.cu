@@ -31,7 +31,8 @@ constexpr int kPlane = kRT * kCT;      // floats per staged plane
 struct Smem {
     float q[8 * kPlane];     // staged q planes of the next tile (TMA destination)
     float st[2 * kPlane];    // staged (A, b) of the next tile (TMA destination)
-    float b[2][kPlane];      // b ping-pong of the current tile
+    float b[2][kPlane];      // b ping-pong of the current tile (magnitude in its tier)
+    uint8_t k[2][kPlane];    // tier ping-pong of the current tile
 };
 
 // Tile activity flags (kActB, kActA: common.cuh); kActA tests the encoded A != +0.
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const int* __restrict__ ntiles_live, int* __restrict__ work, float* __restrict__ out,
                    float* __restrict__ all_out,
                    size_t all_stride, uint8_t* __restrict__ act_out, unsigned long long* __restrict__ skipped,
-                   int* __restrict__ err) {
+                   int* __restrict__ err, TmaHook hk) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     __shared__ __align__(8) uint64_t bar;
@@ -76,39 +77,46 @@ __global__ void __launch_bounds__(kThreads, 1)
         int r0, c0;
         tile_origin<kHalo>(tiles[li], tiles_x, r0, c0);
         mbar_arrive_expect_tx(&bar, bytes);
-        tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
-        tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
+        if (!hk.withhold) {
+            tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
+            tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
+        }
     }
     uint32_t parity = 0;
     float q[kM][8];
     float A[kM];
     for (;;) {
         const int tile = tiles[li];
-        const bool ok = mbar_wait_bounded(&bar, parity);
+        const bool ok = mbar_wait_bounded(&bar, parity, hk.spin);
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
                 atomicExch(err, kErrTmaTimeout);
-                mbar_wait_bounded(&bar, parity);
+                mbar_wait_bounded(&bar, parity, hk.spin);
             }
             return;
         }
         parity ^= 1u;
-        // stage -> registers (q, A) and -> ping-pong buffer 0 (b)
-        bool burning = false;
+        // stage -> registers (q, A) and -> ping-pong buffer 0 (b and its tier)
+        bool burning = false, tiered = false;
 #pragma unroll
         for (int m = 0; m < kM; ++m) {
             const int y = ys + m;
 #pragma unroll
             for (int d = 0; d < 8; ++d) q[m][d] = sm.q[d * kPlane + y * kCT + x];
-            A[m] = sm.st[y * kCT + x];
-            const float bv = sm.st[kPlane + y * kCT + x];
+            float bv;
+            int kv;
+            x_decode(sm.st[y * kCT + x], sm.st[kPlane + y * kCT + x], A[m], bv, kv);
             sm.b[0][y * kCT + x] = bv;
+            sm.k[0][y * kCT + x] = (uint8_t)kv;
             burning |= bv != 0.0f;
+            tiered |= kv != 0;
         }
         fence_proxy_async();  // these generic reads of the stage precede the next TMA writes
         // b = 0 in the whole region: every P is 0 at every step of the launch, so the
         // region's state does not change and the steps are skipped (the stores remain)
         const bool live = __syncthreads_or(burning);  // also: stage fully consumed
+        // a tiered cell in the region: its steps take the general (tiered) update
+        tiered = __syncthreads_or(tiered);
         int next = ntiles;
         if (tid == 0) {
             next = (int)gridDim.x + atomicAdd(work, 1);
@@ -118,8 +126,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             int r0, c0;
             tile_origin<kHalo>(tiles[next], tiles_x, r0, c0);
             mbar_arrive_expect_tx(&bar, bytes);
-            tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
-            tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
+            if (!hk.withhold) {
+                tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
+                tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
+            }
         }
         int r0, c0;
         tile_origin<kHalo>(tile, tiles_x, r0, c0);
@@ -133,41 +143,76 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (live) {
                 const float* src = sm.b[cur];
                 float* dst = sm.b[cur ^ 1];
-                // ring of b rows ys-1 .. ys+kM (slot (row - ys + 1) % 3) in columns x-1, x, x+1
-                float bw[3][3];
+                const uint8_t* ksrc = sm.k[cur];
+                uint8_t* kdst = sm.k[cur ^ 1];
                 const int xl = xin ? x - 1 : x, xr = xin ? x + 1 : x;
-                const int y_first = ys > 0 ? ys - 1 : 0;
-                bw[0][0] = src[y_first * kCT + xl]; bw[0][1] = src[y_first * kCT + x]; bw[0][2] = src[y_first * kCT + xr];
-                bw[1][0] = src[ys * kCT + xl];      bw[1][1] = src[ys * kCT + x];      bw[1][2] = src[ys * kCT + xr];
+                bool now_tiered = false;
+                if (!tiered) {
+                    // every cell of the region in tier 0: the FP32 update, which is the
+                    // tiered one on such inputs, plus the move of cells that fall below
+                    // 2^-64 into tier 1
+                    // ring of b rows ys-1 .. ys+kM (slot (row - ys + 1) % 3) in columns x-1, x, x+1
+                    float bw[3][3];
+                    const int y_first = ys > 0 ? ys - 1 : 0;
+                    bw[0][0] = src[y_first * kCT + xl]; bw[0][1] = src[y_first * kCT + x]; bw[0][2] = src[y_first * kCT + xr];
+                    bw[1][0] = src[ys * kCT + xl];      bw[1][1] = src[ys * kCT + x];      bw[1][2] = src[ys * kCT + xr];
 #pragma unroll
-                for (int m = 0; m < kM; ++m) {
-                    const int y = ys + m;
-                    float(&bu)[3] = bw[m % 3];
-                    float(&bm)[3] = bw[(m + 1) % 3];
-                    float(&bd)[3] = bw[(m + 2) % 3];
-                    const int yn = y + 1 < kRT ? y + 1 : y;
-                    bd[0] = src[yn * kCT + xl]; bd[1] = src[yn * kCT + x]; bd[2] = src[yn * kCT + xr];
-                    if (y >= 1 && y < kRT - 1) {  // the region's edge rows are never updated
-                        // the edge columns are never updated either: they compute on their
-                        // clamped (in-bounds) window like the others and keep their old
-                        // values, a select rather than a divergent branch
-                        // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
-                        const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
-                        float P = 0.0f, S = 1.0f;
+                    for (int m = 0; m < kM; ++m) {
+                        const int y = ys + m;
+                        float(&bu)[3] = bw[m % 3];
+                        float(&bm)[3] = bw[(m + 1) % 3];
+                        float(&bd)[3] = bw[(m + 2) % 3];
+                        const int yn = y + 1 < kRT ? y + 1 : y;
+                        bd[0] = src[yn * kCT + xl]; bd[1] = src[yn * kCT + x]; bd[2] = src[yn * kCT + xr];
+                        if (y >= 1 && y < kRT - 1) {  // the region's edge rows are never updated
+                            // the edge columns are never updated either: they compute on their
+                            // clamped (in-bounds) window like the others and keep their old
+                            // values, a select rather than a divergent branch
+                            // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
+                            const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
+                            float P = 0.0f, S = 1.0f;
 #pragma unroll
-                        for (int d = 0; d < 8; ++d) {
-                            const float xx = nb[d] * q[m][d];
-                            ign_acc(xx, P, S);
+                            for (int d = 0; d < 8; ++d) ign_acc(__fmul_rn(nb[d], q[m][d]), P, S);
+                            float An, Bn;
+                            int kn;
+                            x_update_t0(P, S, A[m], bm[1], pc, An, Bn, kn);
+                            A[m] = xin ? An : A[m];
+                            dst[y * kCT + x] = xin ? Bn : bm[1];
+                            kdst[y * kCT + x] = (uint8_t)(xin ? kn : 0);
+                            now_tiered |= xin && kn != 0;
                         }
-                        float a, ua;
-                        a_decode(A[m], a, ua);
-                        const float nn = ua * P;
-                        const float An = a_encode(a + nn, ua * S);
-                        A[m] = xin ? An : A[m];
-                        dst[y * kCT + x] = xin ? fmaf(pc, bm[1], nn) : bm[1];
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < kM; ++m) {
+                        const int y = ys + m;
+                        if (y >= 1 && y < kRT - 1) {
+                            // the edge columns compute on their clamped window and keep
+                            // their old values, as in the tier-0 path
+                            float nb[8];
+                            int nk[8];
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) {
+                                const int dc = dir_dc(d);
+                                const int xx = dc < 0 ? xl : (dc > 0 ? xr : x);
+                                const int o = (y + dir_dr(d)) * kCT + xx;
+                                nb[d] = src[o];
+                                nk[d] = ksrc[o];
+                            }
+                            const float Bo = src[y * kCT + x];
+                            const int ko = ksrc[y * kCT + x];
+                            float An, Bn;
+                            int kn;
+                            x_update(nb, nk, q[m], A[m], Bo, ko, pc, An, Bn, kn);
+                            A[m] = xin ? An : A[m];
+                            dst[y * kCT + x] = xin ? Bn : Bo;
+                            const int kw = xin ? kn : ko;
+                            kdst[y * kCT + x] = (uint8_t)kw;
+                            now_tiered |= kw != 0;
+                        }
                     }
                 }
-                __syncthreads();
+                tiered = __syncthreads_or(now_tiered);
                 cur ^= 1;
             }
             if (all_out) {  // every intermediate state (segment recompute for the adjoint)
@@ -178,8 +223,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int m = 0; m < kM; ++m) {
                         const int y = ys + m, gr = r0 + y;
                         if (y >= kHalo && y < kRT - kHalo && gr < H) {
-                            o[(size_t)gr * pitch + gc] = A[m];
-                            o[gplane + (size_t)gr * pitch + gc] = sm.b[cur][y * kCT + x];
+                            float As, Bs;
+                            x_encode(A[m], sm.b[cur][y * kCT + x], sm.k[cur][y * kCT + x], As, Bs);
+                            o[(size_t)gr * pitch + gc] = As;
+                            o[gplane + (size_t)gr * pitch + gc] = Bs;
                         }
                     }
                 }
@@ -192,8 +239,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int m = 0; m < kM; ++m) {
                     const int y = ys + m, gr = r0 + y;
                     if (y >= kHalo && y < kRT - kHalo && gr < H) {
-                        out[(size_t)gr * pitch + gc] = A[m];
-                        out[gplane + (size_t)gr * pitch + gc] = sm.b[cur][y * kCT + x];
+                        float As, Bs;
+                        x_encode(A[m], sm.b[cur][y * kCT + x], sm.k[cur][y * kCT + x], As, Bs);
+                        out[(size_t)gr * pitch + gc] = As;
+                        out[gplane + (size_t)gr * pitch + gc] = Bs;
                     }
                 }
             }
@@ -480,7 +529,7 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
                          int n, const int* tile_list, int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
-                         cudaStream_t s) {
+                         TmaHook hk, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int ntiles = diff_blocked_tiles(halo, H, pitch);
@@ -488,11 +537,11 @@ void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq
     if (halo == 4)
         k_diff_blocked<4><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, tile_list,
                                                                       tile_count, tile_count + 1, out, all_out,
-                                                                      all_stride, act_out, skipped, err);
+                                                                      all_stride, act_out, skipped, err, hk);
     else
         k_diff_blocked<8><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, tile_list,
                                                                       tile_count, tile_count + 1, out, all_out,
-                                                                      all_stride, act_out, skipped, err);
+                                                                      all_stride, act_out, skipped, err, hk);
 }
 
 }  // namespace pf

@@ -21,9 +21,12 @@ __device__ __forceinline__ uint64_t row_burning(uint32_t left, uint32_t mid, uin
 
 // New value of the 4 cells of word `mid` (row r, columns col0..col0+3 of the grid).
 // U/C/D are the burning flags of the rows above / at / below (row_burning layout).
+// ties: near-tie counts of this call's owned cells (ignition in the low 16 bits,
+// continue in the high 16 bits), added to.
 __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64_t C, uint64_t D, int r,
                                                 int col0, size_t qoff, size_t qplane, const float* __restrict__ q,
-                                                const DiscreteArgs& g, uint32_t run, uint32_t step, int rr) {
+                                                const DiscreteArgs& g, uint32_t run, uint32_t step, int rr,
+                                                uint32_t& ties) {
     const uint64_t all3 = U | C | D;
     const uint64_t nb64 = (all3 << 8) | (all3 >> 8) | U | D;  // neighbours of byte positions 1..4
     const uint32_t nb = (uint32_t)(nb64 >> 8) & 0x01010101u;
@@ -50,16 +53,34 @@ __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64
                 }
             }
             const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
-            ns = (u24(x.x) < P) ? 2u : 1u;
-            if (ns == 2u && g.acc && r >= g.acc_r0 && r < g.acc_r1 && col >= g.acc_c0 && col < g.acc_c1)
+            const float u = u24(x.x);
+            ns = (u < P) ? 2u : 1u;
+            const bool owned = r >= g.acc_r0 && r < g.acc_r1 && col >= g.acc_c0 && col < g.acc_c1;
+            if (ns == 2u && g.acc && owned)
                 g.acc[((size_t)rr * g.H + r) * g.W + col] = P;  // the accumulator (Sec. 2.2 data flow)
+            ties += (owned && fabsf(u - P) < kNearTie) ? 1u : 0u;
         } else {
             const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
-            ns = (u24(x.y) < g.p_continue) ? 2u : 3u;
+            const float u = u24(x.y);
+            ns = (u < g.p_continue) ? 2u : 3u;
+            const bool owned = r >= g.acc_r0 && r < g.acc_r1 && col >= g.acc_c0 && col < g.acc_c1;
+            ties += (owned && fabsf(u - g.p_continue) < kNearTie) ? 0x10000u : 0u;
         }
         out = (out & ~(0xffu << (8 * k))) | (ns << (8 * k));
     }
     return out;
+}
+
+// Adds a thread's near-tie counts to the global counters: one reduction per warp, and
+// atomics only from warps that saw a tie (they are rare). Every lane of the warp calls this.
+__device__ __forceinline__ void flush_ties(const DiscreteArgs& g, uint32_t ties) {
+    if (!g.ties || !__any_sync(0xffffffffu, ties != 0u)) return;
+    const uint32_t ign = __reduce_add_sync(0xffffffffu, ties & 0xffffu);
+    const uint32_t con = __reduce_add_sync(0xffffffffu, ties >> 16);
+    if ((threadIdx.x & 31) == 0) {
+        if (ign) atomicAdd(g.ties, (unsigned long long)ign);
+        if (con) atomicAdd(g.ties + 1, (unsigned long long)con);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_discrete_step(DiscreteArgs g, const uint8_t* __restrict__ S,
@@ -68,22 +89,25 @@ __global__ void __launch_bounds__(256) k_discrete_step(DiscreteArgs g, const uin
     const int wpr = g.pitch >> 2;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t total = (size_t)g.R * g.H * wpr;
-    if (idx >= total) return;
-    const int w = (int)(idx % wpr);
-    const size_t rowid = idx / wpr;
-    const int r = (int)(rowid % g.H);
-    const int rr = (int)(rowid / g.H);
-    const uint32_t* base = reinterpret_cast<const uint32_t*>(S + (size_t)rr * g.H * g.pitch);
-    auto ld = [&](int y, int x) -> uint32_t {
-        return (y >= 0 && y < g.H && x >= 0 && x < wpr) ? __ldg(base + (size_t)y * wpr + x) : 0u;
-    };
-    const uint32_t mid = ld(r, w);
-    const uint64_t U = row_burning(ld(r - 1, w - 1), ld(r - 1, w), ld(r - 1, w + 1));
-    const uint64_t C = row_burning(ld(r, w - 1), mid, ld(r, w + 1));
-    const uint64_t D = row_burning(ld(r + 1, w - 1), ld(r + 1, w), ld(r + 1, w + 1));
-    const uint32_t out = update_word(mid, U, C, D, r, 4 * w, (size_t)r * g.pitch + 4 * w, (size_t)g.H * g.pitch,
-                                     q, g, g.run0 + (uint32_t)rr, step, rr);
-    reinterpret_cast<uint32_t*>(Sn + (size_t)rr * g.H * g.pitch)[(size_t)r * wpr + w] = out;
+    uint32_t ties = 0u;
+    if (idx < total) {
+        const int w = (int)(idx % wpr);
+        const size_t rowid = idx / wpr;
+        const int r = (int)(rowid % g.H);
+        const int rr = (int)(rowid / g.H);
+        const uint32_t* base = reinterpret_cast<const uint32_t*>(S + (size_t)rr * g.H * g.pitch);
+        auto ld = [&](int y, int x) -> uint32_t {
+            return (y >= 0 && y < g.H && x >= 0 && x < wpr) ? __ldg(base + (size_t)y * wpr + x) : 0u;
+        };
+        const uint32_t mid = ld(r, w);
+        const uint64_t U = row_burning(ld(r - 1, w - 1), ld(r - 1, w), ld(r - 1, w + 1));
+        const uint64_t C = row_burning(ld(r, w - 1), mid, ld(r, w + 1));
+        const uint64_t D = row_burning(ld(r + 1, w - 1), ld(r + 1, w), ld(r + 1, w + 1));
+        const uint32_t out = update_word(mid, U, C, D, r, 4 * w, (size_t)r * g.pitch + 4 * w,
+                                         (size_t)g.H * g.pitch, q, g, g.run0 + (uint32_t)rr, step, rr, ties);
+        reinterpret_cast<uint32_t*>(Sn + (size_t)rr * g.H * g.pitch)[(size_t)r * wpr + w] = out;
+    }
+    flush_ties(g, ties);  // every lane of the warp, converged
 }
 
 // ------------------------------------------------------------ temporal-blocked
@@ -99,7 +123,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
                                                                   DiscreteArgs g, int TH, int KH,
                                                                   uint8_t* __restrict__ Sn,
                                                                   const float* __restrict__ q, uint32_t step0,
-                                                                  int k, int* __restrict__ err) {
+                                                                  int k, int* __restrict__ err, TmaHook hk) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // TMA destinations: round the dynamic shared-memory base up to 128 bytes (the
@@ -121,13 +145,13 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(&bar, (uint32_t)tile_bytes);
-        tma_load_3d(A, &tin, &bar, c0 - kXH, r0 - KH, rr);
+        if (!hk.withhold) tma_load_3d(A, &tin, &bar, c0 - kXH, r0 - KH, rr);
     }
-    const bool ok = mbar_wait_bounded(&bar, 0);
+    const bool ok = mbar_wait_bounded(&bar, 0, hk.spin);
     if (!__syncthreads_and(ok)) {
         if (threadIdx.x == 0) {
             atomicExch(err, kErrTmaTimeout);
-            mbar_wait_bounded(&bar, 0);  // give the copy in flight one more budget
+            mbar_wait_bounded(&bar, 0, hk.spin);  // give the copy in flight one more budget
         }
         return;
     }
@@ -151,6 +175,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
     ga.acc_r1 = r0 + TH;
     ga.acc_c0 = c0;
     ga.acc_c1 = c0 + kTW < g.W ? c0 + kTW : g.W;
+    uint32_t ties = 0u;
     if (any_burning) {
         const int y_off = r0 - KH, x_off = c0 - kXH;
         for (int s = 0; s < k; ++s) {
@@ -176,12 +201,13 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
                 // cell is active; the q offset is formed but only read for such cells
                 const size_t qoff = (size_t)gr * g.pitch + gc;
                 dst[y * kCW + m] = update_word(mid, U, C, D, gr, gc, qoff, qplane, q, ga, g.run0 + (uint32_t)rr, step,
-                                               rr);
+                                               rr, ties);
             }
             __syncthreads();
             uint32_t* t = src; src = dst; dst = t;
         }
     }
+    flush_ties(g, ties);
     // store the interior rows [KH, KH + TH), bytes [16, 144) with 16-byte vectors
     uint8_t* out = Sn + (size_t)rr * g.H * g.pitch;
     const int vec_per_row = kTW / 16;
@@ -281,7 +307,7 @@ size_t discrete_blocked_smem(int TH, int KH) {
 }
 
 void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin, int TH, int KH, uint8_t* Sn,
-                                  const float* q, uint32_t step, int k, int* err, cudaStream_t s) {
+                                  const float* q, uint32_t step, int k, int* err, TmaHook hk, cudaStream_t s) {
     const size_t smem = discrete_blocked_smem(TH, KH);
     static bool attr_set = false;
     if (!attr_set) {
@@ -289,7 +315,7 @@ void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin,
         attr_set = true;
     }
     dim3 grd((g.pitch + kTW - 1) / kTW, (g.H + TH - 1) / TH, g.R);
-    k_discrete_blocked<<<grd, kBlkThreads, smem, s>>>(*tin, g, TH, KH, Sn, q, step, k, err);
+    k_discrete_blocked<<<grd, kBlkThreads, smem, s>>>(*tin, g, TH, KH, Sn, q, step, k, err, hk);
 }
 
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,

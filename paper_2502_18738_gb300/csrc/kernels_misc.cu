@@ -1,5 +1,8 @@
 // Small helper kernels: input validation, continuous-state initialisation, and the
 // binary cross-entropy loss of a burn-probability map.
+#include <algorithm>
+#include <cstring>
+
 #include "common.cuh"
 
 namespace pf {
@@ -41,9 +44,75 @@ __global__ void k_diff_pack(const float* __restrict__ dense, int H, int W, int p
     if (idx >= HW) return;
     const int r = (int)(idx / W), c = (int)(idx % W);
     const size_t j = (size_t)r * pitch + c;
-    const float a = dense[idx];
-    ab[j] = a_encode(a, 1.0f - a);
-    ab[(size_t)H * pitch + j] = dense[HW + idx];
+    const float a = dense[idx], b = dense[HW + idx];
+    // values below 2^-64 go to their tier; b = -0 is stored as +0 (the sign marks a tier)
+    float A = a_encode(a, 1.0f - a), B = b <= 0.0f ? 0.0f : b;
+    int k = 0;
+    x_renorm(A, B, k);
+    x_encode(A, B, k, ab[j], ab[(size_t)H * pitch + j]);
+}
+
+// Cells in each state 0..3 over all realisations (grid-stride; one atomic per block and state).
+__global__ void __launch_bounds__(256) k_state_counts(const uint8_t* __restrict__ S, int R, int H, int W, int pitch,
+                                                      unsigned long long* __restrict__ counts) {
+    __shared__ unsigned long long sc[4];
+    if (threadIdx.x < 4) sc[threadIdx.x] = 0ull;
+    __syncthreads();
+    unsigned long long c[4] = {0ull, 0ull, 0ull, 0ull};
+    const size_t n = (size_t)R * H * W;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t rr = i / ((size_t)H * W), j = i % ((size_t)H * W);
+        const uint8_t v = S[(rr * H + j / W) * pitch + j % W];
+        c[v & 3u] += 1ull;
+    }
+    for (int k = 0; k < 4; ++k)
+        if (c[k]) atomicAdd(&sc[k], c[k]);
+    __syncthreads();
+    if (threadIdx.x < 4 && sc[threadIdx.x]) atomicAdd(counts + threadIdx.x, sc[threadIdx.x]);
+}
+
+// Burnable cells, and FP64 sums of a and b over the grid (tiers below FP32's range add 0).
+__global__ void __launch_bounds__(256) k_diff_sums(const float* __restrict__ ab, const uint8_t* __restrict__ burn,
+                                                   int H, int W, int pitch, unsigned long long* __restrict__ nburn,
+                                                   double* __restrict__ sums) {
+    __shared__ double s2[2][8];
+    __shared__ unsigned long long sn[8];
+    double sa = 0.0, sb = 0.0;
+    unsigned long long nb = 0ull;
+    const size_t n = (size_t)H * W, plane = (size_t)H * pitch;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t j = (i / W) * pitch + i % W;
+        float A, B;
+        int k;
+        x_decode(ab[j], ab[plane + j], A, B, k);
+        sa += signbit(A) ? 1.0 + (double)A : (double)(A * tier_scale(k));
+        sb += (double)(B * tier_scale(k));
+        nb += burn && burn[i] ? 1ull : 0ull;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sb += __shfl_down_sync(0xffffffffu, sb, o);
+        nb += __shfl_down_sync(0xffffffffu, nb, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s2[0][w] = sa;
+        s2[1][w] = sb;
+        sn[w] = nb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        unsigned long long tn = 0ull;
+        for (int k = 0; k < 8; ++k) {
+            ta += s2[0][k];
+            tb += s2[1][k];
+            tn += sn[k];
+        }
+        atomicAdd(sums, ta);
+        atomicAdd(sums + 1, tb);
+        atomicAdd(nburn, tn);
+    }
 }
 
 __global__ void k_diff_unpack(const float* __restrict__ ab, int H, int W, int pitch, float* __restrict__ dense) {
@@ -52,10 +121,12 @@ __global__ void k_diff_unpack(const float* __restrict__ ab, int H, int W, int pi
     if (idx >= HW) return;
     const int r = (int)(idx / W), c = (int)(idx % W);
     const size_t j = (size_t)r * pitch + c;
-    float a, ua;
-    a_decode(ab[j], a, ua);
-    dense[idx] = a;
-    dense[HW + idx] = ab[(size_t)H * pitch + j];
+    float A, B;
+    int k;
+    x_decode(ab[j], ab[(size_t)H * pitch + j], A, B, k);
+    // plain FP32: values of the tiers below FP32's range read as 0
+    dense[idx] = signbit(A) ? 1.0f + A : A * tier_scale(k);
+    dense[HW + idx] = B * tier_scale(k);
 }
 
 constexpr int kBceThreads = 256;
@@ -331,6 +402,20 @@ void launch_validate_states(const uint8_t* S, size_t n, int* flags, cudaStream_t
 void launch_diff_init(const uint8_t* S, int H, int W, int pitch, float* ab, uint8_t* burn, cudaStream_t s) {
     const size_t n = (size_t)H * W;
     k_diff_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(S, H, W, pitch, ab, burn);
+}
+
+void launch_state_counts(const uint8_t* S, int R, int H, int W, int pitch, unsigned long long* counts,
+                         cudaStream_t s) {
+    const size_t n = (size_t)R * H * W;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+    k_state_counts<<<blocks, 256, 0, s>>>(S, R, H, W, pitch, counts);
+}
+
+void launch_diff_sums(const float* ab, const uint8_t* burn, int H, int W, int pitch, unsigned long long* nburn,
+                      double* sums, cudaStream_t s) {
+    const size_t n = (size_t)H * W;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+    k_diff_sums<<<blocks, 256, 0, s>>>(ab, burn, H, W, pitch, nburn, sums);
 }
 
 void launch_diff_pack(const float* dense, int H, int W, int pitch, float* ab, cudaStream_t s) {

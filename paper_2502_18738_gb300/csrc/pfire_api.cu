@@ -19,6 +19,9 @@ namespace pf {
 void launch_validate_fields(const float* x, size_t n, float lo, int bit, int* flags, cudaStream_t s);
 void launch_validate_states(const uint8_t* S, size_t n, int* flags, cudaStream_t s);
 void launch_diff_init(const uint8_t* S, int H, int W, int pitch, float* ab, uint8_t* burn, cudaStream_t s);
+void launch_state_counts(const uint8_t* S, int R, int H, int W, int pitch, unsigned long long* counts, cudaStream_t s);
+void launch_diff_sums(const float* ab, const uint8_t* burn, int H, int W, int pitch, unsigned long long* nburn,
+                      double* sums, cudaStream_t s);
 void launch_bce(const float* a, const float* y, int64_t n, float* g, double* partials, int nblk, cudaStream_t s);
 void launch_arrival(const uint8_t* S, int R, int64_t HW, float* P, cudaStream_t s);
 void launch_count(const uint8_t* A, const uint8_t* B, int64_t n, int R, unsigned long long* out, cudaStream_t s);
@@ -67,6 +70,20 @@ long fault_alloc_at() {
         at = s ? atol(s) : -1;
     }
     return at;
+}
+
+// The TMA kernels' test hook from the environment: PF_TMA_TEST_WITHHOLD=1 makes them arm
+// their barriers without issuing the copies, PF_TMA_SPIN_LIMIT=n bounds each wait to n
+// polls (default kSpinLimit). Read at each call that launches them, so a test can turn
+// it on and off between calls.
+pf::TmaHook read_tma_hook() {
+    pf::TmaHook h{pf::kSpinLimit, 0};
+    if (const char* w = getenv("PF_TMA_TEST_WITHHOLD")) h.withhold = atoi(w) != 0;
+    if (const char* l = getenv("PF_TMA_SPIN_LIMIT")) {
+        const long v = atol(l);
+        if (v > 0) h.spin = (uint32_t)v;
+    }
+    return h;
 }
 
 }  // namespace
@@ -134,6 +151,12 @@ struct pf_ctx {
     int* dflags = nullptr;  // [0] device error word, [1] validation, [3] async wind validation
     int* hflags = nullptr;  // pinned mirror
     unsigned long long* dskip = nullptr;  // per kernel kind: cell-steps of skipped quiescent tiles
+    // discrete near-tie counters ([0] ignition, [1] continue, since the last pf_forward)
+    // and pf_stats scratch ([2..5] state counts, [6..7] FP64 sums of a and b)
+    unsigned long long* dties = nullptr;
+    // test hook of the TMA kernels, read from the environment at each forward / backward
+    // (PF_TMA_TEST_WITHHOLD, PF_TMA_SPIN_LIMIT)
+    TmaHook hook{kSpinLimit, 0};
     int* tile_list = nullptr;             // live tiles of one blocked-adjoint launch (count: dflags[8], work: [9])
     uint8_t* gqdirty = nullptr;           // per adjoint tile: may hold nonzero dL/dq this epoch
     // tile activity of the blocked forward (b > 0 in a tile's interior), carried along a
@@ -531,7 +554,7 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
         LaunchScope ls(ctx, K_FBLK, n);
         launch_diff_blocked(halo, &tab, &ctx->tmapQ, ctx->H, ctx->W, ctx->P, pc, n, ctx->flist, ctx->dflags + 11, out,
                             all_out, stride, ctx->fact[1 - ctx->fl_par], ctx->dskip + K_FBLK, ctx->nsm, ctx->dflags,
-                            ctx->st);
+                            ctx->hook, ctx->st);
     }
     ctx->fl_par ^= 1;
     ctx->fl_state = out ? out : all_out + (size_t)(n - 1) * stride;
@@ -554,6 +577,7 @@ DiscreteArgs dargs(const pf_ctx* c) {
     g.fire = 0; g.run0 = 0;
     g.acc = c->acc;
     g.acc_r0 = 0; g.acc_r1 = c->H; g.acc_c0 = 0; g.acc_c1 = c->W;
+    g.ties = c->dties;
     return g;
 }
 
@@ -572,7 +596,7 @@ int run_discrete(pf_ctx* ctx, int T) {
             n = std::min(n, blocked_k(ctx));
             LaunchScope ls(ctx, K_DBLK, n);
             launch_discrete_blocked_impl(g, &ctx->tmapS[src], ctx->TH, ctx->KH, ctx->S[dst], ctx->q, (uint32_t)t, n,
-                                         ctx->dflags, ctx->st);
+                                         ctx->dflags, ctx->hook, ctx->st);
         } else {
             n = 1;
             LaunchScope ls(ctx, K_DSTEP);
@@ -879,6 +903,8 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
     if (cudaMemsetAsync(ctx->q, 0, 8 * pe * sizeof(float), ctx->st) != cudaSuccess) goto cuda_failed;
     ALLOC(ctx->dflags, 16 * sizeof(int));
     ALLOC(ctx->dskip, K_NKINDS * sizeof(unsigned long long));
+    ALLOC(ctx->dties, 8 * sizeof(unsigned long long));
+    if (cudaMemsetAsync(ctx->dties, 0, 8 * sizeof(unsigned long long), ctx->st) != cudaSuccess) goto cuda_failed;
     if (cudaMallocHost((void**)&ctx->hflags, 16 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         rc = fail(ctx, PF_ENOMEM, "pinned flag allocation failed");
@@ -1233,11 +1259,13 @@ int pf_forward(pf_ctx* ctx, const uint8_t* S_init, int T, void* S_out) {
     const size_t n = (size_t)ctx->R * ctx->H * ctx->W;
     int rc = validate_states(ctx, S_init, n);
     if (rc) return rc;
+    ctx->hook = read_tma_hook();
     ctx->step = 0;
     if (ctx->form == PF_DISCRETE) {
         ctx->scur = 0;
         CK(cudaMemcpy2DAsync(ctx->S[0], ctx->P, S_init, ctx->W, ctx->W, (size_t)ctx->R * ctx->H,
                              cudaMemcpyDeviceToDevice, ctx->st));
+        CK(cudaMemsetAsync(ctx->dties, 0, 2 * sizeof(unsigned long long), ctx->st));
         if (ctx->acc && (rc = dca_record(ctx))) return rc;
         rc = run_discrete(ctx, T);
         if (rc) return rc;
@@ -1258,6 +1286,7 @@ int pf_forward(pf_ctx* ctx, const uint8_t* S_init, int T, void* S_out) {
 int pf_advance(pf_ctx* ctx, int T, void* S_out) {
     if (!ctx) return fail(nullptr, PF_EINVAL, "pf_advance: ctx is NULL");
     if (T < 0) return fail(ctx, PF_EINVAL, "pf_advance: T must be >= 0");
+    ctx->hook = read_tma_hook();
     int rc;
     if (ctx->form == PF_DISCRETE) {
         if ((rc = run_discrete(ctx, T))) return rc;
@@ -1302,6 +1331,41 @@ int pf_set_state(pf_ctx* ctx, int step, const void* S) {
     return PF_OK;
 }
 
+int pf_stats(pf_ctx* ctx, pf_stats_t* out) {
+    if (!ctx || !out) return fail(ctx, PF_EINVAL, "pf_stats: NULL argument");
+    CK(cudaMemsetAsync(ctx->dties + 2, 0, 6 * sizeof(unsigned long long), ctx->st));
+    {
+        LaunchScope ls(ctx, K_MISC);
+        if (ctx->form == PF_DISCRETE)
+            launch_state_counts(ctx->S[ctx->scur], ctx->R, ctx->H, ctx->W, ctx->P, ctx->dties + 2, ctx->st);
+        else
+            launch_diff_sums(ctx->cur_ab, ctx->burn, ctx->H, ctx->W, ctx->P, ctx->dties + 2,
+                             reinterpret_cast<double*>(ctx->dties + 6), ctx->st);
+    }
+    int rc = check_launch(ctx, "state statistics");
+    if (rc) return rc;
+    unsigned long long h[8];
+    CK(cudaMemcpyAsync(h, ctx->dties, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    out->step = ctx->step;
+    if (ctx->form == PF_DISCRETE) {
+        for (int i = 0; i < 4; ++i) out->cells[i] = (double)h[2 + i];
+        out->near_ties_ignite = (long long)h[0];
+        out->near_ties_continue = (long long)h[1];
+    } else {
+        double sa, sb;
+        memcpy(&sa, h + 6, sizeof(double));
+        memcpy(&sb, h + 7, sizeof(double));
+        const double nburn = (double)h[2];
+        out->cells[0] = (double)ctx->H * ctx->W - nburn;
+        out->cells[1] = nburn - sa;
+        out->cells[2] = sb;
+        out->cells[3] = sa - sb;
+        out->near_ties_ignite = out->near_ties_continue = 0;  // the differentiable form draws nothing
+    }
+    return PF_OK;
+}
+
 int pf_ignition_map(pf_ctx* ctx, float* P_out) {
     if (!ctx || !P_out) return fail(ctx, PF_EINVAL, "pf_ignition_map: NULL argument");
     int rc = ensure_q(ctx, epoch_of(ctx, ctx->step), ctx->step + 1);
@@ -1326,6 +1390,7 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
     const size_t pe = plane_elems(ctx);
     const size_t sbytes = diff_state_bytes(ctx);
     int rc;
+    ctx->hook = read_tma_hook();
     // lazily allocated adjoint buffers
     for (int i = 0; i < 2; ++i) {
         if (!ctx->lam[i]) {
@@ -1470,7 +1535,8 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                     launch_adjoint_blocked(tmap, tmap0 ? tmap0 : tmap, &ctx->tmapQ, ctx->H, ctx->P, pc, t1 - 1 - tbase,
                                            n, ctx->lam[lcur],
                                            ctx->sig[lcur], ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->Gq,
-                                           ctx->tile_list, ctx->dflags + 8, ctx->nsm, ctx->dflags, ctx->st);
+                                           ctx->tile_list, ctx->dflags + 8, ctx->nsm, ctx->dflags, ctx->hook,
+                                           ctx->st);
                 }
                 if ((r = check_launch(ctx, "adjoint blocked"))) return r;
                 t1 -= n;
@@ -1657,6 +1723,7 @@ int pf_backward_dca(pf_ctx* ctx, const float* dL_dacc, const uint8_t* step_mask,
     DiscreteArgs g = dargs(ctx);
     g.p_continue = ctx->t_pc;
     g.acc = nullptr;
+    g.ties = nullptr;  // a replay: its draws were counted when the trajectory was made
     auto flush = [&](int e) -> int {
         {
             LaunchScope ls(ctx, K_PADJ);

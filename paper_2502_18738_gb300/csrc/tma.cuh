@@ -50,11 +50,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for phase `parity` of bar; false if the spin budget ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit) {
+    for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+
+// Test hook of the TMA kernels (TmaHook::withhold): arm the barrier for the bytes of a
+// copy but issue no copy, so that its waits run out and the timeout path is exercised
+// without any copy in flight.
+struct TmaHook {
+    uint32_t spin;  // polls per wait
+    int withhold;
+};
 
 // 3-D tiled load into shared memory, completion signalled on bar (transaction bytes).
 // x (innermost) must be a multiple of 16 bytes' worth of elements; callers guarantee it.

@@ -92,7 +92,9 @@ def smooth_field(H: int, W: int, sigma: float, seed: int, stream: int = 0) -> np
         g = _gauss_filter_fft(noise, sigma / f)
         g = _bilinear_upsample(g.astype(np.float32), H, W, f)
     else:
-        noise = rng.standard_normal((H, W), dtype=np.float32)
+        # FP64 noise and transform: their FP32 rounding comes out the same on x86 and Arm
+        # hosts (an FP32 transform does not), so both build identical fields
+        noise = rng.standard_normal((H, W))
         g = _gauss_filter_fft(noise, sigma)
     return np.ascontiguousarray(g, dtype=np.float32)
 

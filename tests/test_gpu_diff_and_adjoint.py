@@ -60,6 +60,34 @@ def test_single_step_random_states(pf, orc, H, W, kernel):
     _close(Pg, P, STEP_RTOL, STEP_ATOL)
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_single_step_states_below_the_first_tier_boundary(pf, orc, kernel):
+    """States in 8 x 8 blocks scaled by 1e-30 (below 2^-64, so held in the first tier)
+    next to ordinary ones: one step against the oracle at the per-step relative tolerance
+    with no absolute floor, so the tiny values are checked as closely as the others."""
+    H, W = 96, 112
+    land = syn.make_landscape(H, W, 12)
+    V, th = syn.smooth_wind(H, W, 12, 0, sigma=6.0)
+    m, prm = _model(pf, orc, land, V, th, H, W)
+    m.set_tuning(kernel=kernel)
+    S0 = np.where(land.burnable != 0, 1, 0).astype(np.uint8)
+    m.forward(cuda(S0), 0)
+    q = orc.prep(H, W, land.E, land.p_veg, land.p_den, V, th, prm, burnable=land.burnable)
+    a, b = syn.random_diff_state(H, W, 9, land.burnable)
+    rr, cc = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    tiny = ((rr // 8 + cc // 8) % 3) == 0
+    a = np.where(tiny, a * np.float32(1e-30), a).astype(np.float32)
+    b = np.where(tiny, b * np.float32(1e-30), b).astype(np.float32)
+    m.set_state(0, cuda(np.stack([a, b])))
+    Pg = m.ignition_map()[0].cpu().numpy()
+    out = m.advance(1).cpu().numpy()
+    a1, b1, P = orc.step_diff(a, b, q, prm.p_continue, return_P=True)
+    _close(out[0], a1, STEP_RTOL, 1e-40)
+    _close(out[1], b1, STEP_RTOL, 1e-40)
+    _close(Pg, P, STEP_RTOL, 1e-40)
+    assert ((a1 > 0) & (a1 < 2.0 ** -64)).sum() > 100  # some cells stay in the tier
+
+
 def _problem(H, W, T, seed, n_epochs=2):
     land = syn.make_landscape(H, W, seed)
     winds = [syn.smooth_wind(H, W, seed, e, sigma=8.0) for e in range(n_epochs)]

@@ -5,6 +5,9 @@ configuration bench.py times (automatic kernel choice and checkpoint interval):
   finite differences on a 64 x 64 crop of the same problem;
 * 1024 x 1024 ensemble of 64 realisations, T = 1000: temporal-blocked == plain kernel
   for every realisation, and two realisations against the oracle's trajectory;
+* five fires under the bench's per-cell winds at 1024 x 1024 (T = 300) and 2048 x 2048
+  (T = 600 and 1000): the whole state against the oracle, and gradients at 1024 x 1024,
+  T = 600 against the oracle's finite differences;
 * 8192 x 8192, T = 2000: sampled outputs the oracle can compute exactly (the light cone
   of an ignition after 20 steps, forward and per-cell gradients), and properties that
   hold at any size for the full run (bounds, light cone, determinism, and the adjoint
@@ -230,8 +233,7 @@ def test_8192_t2000_properties(pf, orc):
 
 def test_1024_t900_adjoint_against_finite_difference(pf, orc):
     """Long run on a grid the fire fills: the adjoint against a central difference of
-    the forward in p_h for a smooth loss (on open grids the FP32 forward's leading-edge
-    truncation makes the difference quotient itself non-smooth; see the design notes)."""
+    the GPU forward in p_h for a smooth loss."""
     import torch
     N, T = 1024, 900
     land = syn.make_landscape(N, N, 5)
@@ -290,20 +292,59 @@ def test_1024_t300_five_fires_blocked_equals_plain(pf):
     assert np.array_equal(_run(pf, land, winds, starts, S0, 300, 2), _run(pf, land, winds, starts, S0, 300, 1))
 
 
-def test_1024_t300_five_fires_uniform_wind_matches_oracle(pf, orc):
-    """Five fires at 1024 x 1024 under a uniform 5 m/s wind, T = 300, blocked kernels:
-    a_T and b_T against the FP64 oracle within the after-T tolerance. (Under the per-cell
-    winds of the bench, up to 12 m/s, the upwind fronts are slow, pulled fronts whose
-    leading edge falls below FP32's range within this horizon, and the FP32 state drifts
-    from the FP64 oracle by up to 5e-3 in a by T = 300; see the design notes' reading of
-    the FP32 leading edge.)"""
-    land, winds, starts, S0 = _five_fires(1024, 1024, 300, 5, uniform_wind=True)
-    out = _run(pf, land, winds, starts, S0, 300, 2).astype(np.float64)
-    a, b, _ = orc.diff_forward(land, winds, starts, orc.Params(**PRM), S0, 300, keep_states=False)
+@pytest.mark.parametrize("N,T", [(1024, 300), (2048, 600), (2048, 1000)])
+def test_bench_winds_five_fires_match_oracle(pf, orc, N, T):
+    """The bench workload's structure (five ignitions, per-cell winds up to 12 m/s
+    resampled every 100 steps) at N x N for T steps, blocked kernels: a_T and b_T against
+    the FP64 oracle element by element within the after-T tolerance. The upwind fronts
+    are slow, pulled fronts whose leading edge reaches far below FP32's range; the tiered
+    state carries it down to FP64's, and the count of such cells is printed."""
+    land, winds, starts, S0 = _five_fires(N, N, T, 5, uniform_wind=False)
+    out = _run(pf, land, winds, starts, S0, T, 2).astype(np.float64)
+    a, b, _ = orc.diff_forward(land, winds, starts, orc.Params(**PRM), S0, T, keep_states=False)
     for got, want in ((out[0], a), (out[1], b)):
         err = np.abs(got - want) - (1e-4 * want + 1e-6)
         assert err.max() <= 0, (float(err.max()), np.unravel_index(err.argmax(), err.shape))
-    assert (a > 0.5).sum() > 50000  # the fires did spread
+    floor32 = 2.0 ** -126
+    deep_a = int(((a > 0) & (a < floor32)).sum())
+    print(f"\n{N}x{N} T={T}: cells with 0 < a_T < 2^-126 in the oracle: {deep_a}, "
+          f"0 < b_T < 2^-126: {int(((b > 0) & (b < floor32)).sum())}, a_T > 0.5: {int((a > 0.5).sum())}")
+    assert (a > 0.5).sum() > 0.3 * N * N  # the fires did spread
+    assert deep_a > 0  # the leading edge does reach below FP32's range
+
+
+def test_bench_winds_gradients_match_oracle_fd_1024_t600(pf, orc):
+    """Parameter gradients of the bench structure at 1024 x 1024, T = 600, per-cell winds:
+    the GPU adjoint (blocked kernels, automatic checkpointing) against central finite
+    differences of the FP64 oracle's forward, for a mean-square loss against a target
+    map, within 1e-3 relative."""
+    N, T = 1024, 600
+    land, winds, starts, S0 = _five_fires(N, N, T, 5, uniform_wind=False)
+    rr, cc = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    y = ((np.hypot(rr - N / 2, cc - N / 2) < 0.3 * T) * (S0 != 0)).astype(np.float64)
+    m = pf.FireModel(N, N, pf.PF_DIFF)
+    set_landscape(m, land, *winds[0])
+    for (V, th), s0 in list(zip(winds, starts))[1:]:
+        m.set_wind(cuda(V), cuda(th), s0)
+    m.set_params(**PRM)
+    o = m.forward(cuda(S0), T)
+    import torch
+    gm = (2.0 * (o[0].double() - cuda(y)) / (N * N)).float()
+    g4, _, _ = m.backward(gm, None, per_cell=False)
+    m.close()
+    base = orc.Params(**PRM)
+    names = ("p_h", "c1", "c2", "a")
+    for k, name in enumerate(names):
+        v = getattr(base, name)
+        h = 1e-4 * v
+        ls = []
+        for sgn in (+1, -1):
+            prm = orc.Params(**{**{n: getattr(base, n) for n in names}, name: v + sgn * h,
+                                "p_continue": base.p_continue, "l": base.l}, exact=True)
+            a, _, _ = orc.diff_forward(land, winds, starts, prm, S0, T, keep_states=False)
+            ls.append(float(((a - y) ** 2).mean()))
+        fd = (ls[0] - ls[1]) / (2 * h)
+        assert g4[k] == pytest.approx(fd, rel=GRAD_RTOL), (name, g4[k], fd)
 
 
 def test_uneven_batch_of_config4_distribution_matches_per_fire_contexts(pf):

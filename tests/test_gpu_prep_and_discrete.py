@@ -193,3 +193,81 @@ def test_slope_tensor_input_matches_oracle(pf, orc):
     d = lattice_direction(H, W, 0, 0)
     rr, cc = np.nonzero(~on)
     assert np.all(np.abs(P[rr, cc] - q_E[d[rr, cc], rr, cc]) <= 2e-6 * q_E[d[rr, cc], rr, cc] + 1e-7)
+
+
+def _has_burning_neighbour(S):
+    """Per realisation: whether any Moore neighbour (inside the grid) is burning."""
+    H, W = S.shape[-2:]
+    b = np.pad(S == 2, [(0, 0)] * (S.ndim - 2) + [(1, 1), (1, 1)])
+    out = np.zeros(S.shape, bool)
+    for dr in (-1, 0, 1):
+        for dc in (-1, 0, 1):
+            if dr or dc:
+                out |= b[..., 1 + dr:1 + dr + H, 1 + dc:1 + dc + W]
+    return out
+
+
+@pytest.mark.parametrize("kernel,k", [(1, 1), (2, 1), (2, 4)])
+def test_near_ties_and_state_counts_are_reported(pf, orc, kernel, k):
+    """pf_stats after steps of 4 realisations on random states: the state counts equal
+    the oracle's; the near-tie counts equal those recounted from the oracle's draws
+    against the library's own FP32 p_ignite (the ignition map) and p_continue, and
+    agree with the count against the oracle's FP64 p_ignite up to the draws that lie
+    within FP32 rounding of the 1e-6 boundary."""
+    H, W, R = 384, 512, 4
+    seed = 0xC0FFEE1234
+    m, land, V, th, prm, q = _setup(pf, orc, H, W, seed=17, R=R, rng_seed=seed)
+    m.set_tuning(kernel=kernel, k=k)
+    pc32 = np.float32(prm.p_continue)
+    want_gpu_p, want_orc, got = [0, 0], [0, 0], [0, 0]
+    for step in (0, 9, 77, 1000, 4321, 65536):
+        S = syn.random_state(H, W, seed=step + 5, R=R)
+        m.set_state(step, cuda(S))
+        before = m.stats()
+        Pg = m.ignition_map().cpu().numpy()
+        nxt = m.advance(k).cpu().numpy()
+        after = m.stats()
+        got[0] += after["near_ties_ignite"] - before["near_ties_ignite"]
+        got[1] += after["near_ties_continue"] - before["near_ties_continue"]
+        # the oracle's first of the k steps: its decisive draws and FP64 p_ignite
+        ora, P, u = orc.step_discrete(S, q, prm.p_continue, seed=seed, step=step, return_P=True)
+        act = (S == 1) & _has_burning_neighbour(S)
+        u32 = u.astype(np.float32)
+        want_gpu_p[0] += int((act & (np.abs(u32 - Pg) < np.float32(NEAR))).sum())
+        want_orc[0] += int((act & (np.abs(u - P) < NEAR)).sum())
+        n_cont = int(((S == 2) & (np.abs(u32 - pc32) < np.float32(NEAR))).sum())
+        want_gpu_p[1] += n_cont
+        want_orc[1] += int(((S == 2) & (np.abs(u - prm.p_continue) < NEAR)).sum())
+        if k == 1:
+            assert np.array_equal(nxt, ora) or _compare_step(S, nxt, ora, P, u) is not None
+            counts = np.bincount(nxt.reshape(-1), minlength=4)
+            assert after["cells"] == [float(c) for c in counts], (after["cells"], counts)
+    if k == 1:  # one step per call: the counts cover exactly the oracle's step
+        assert got == want_gpu_p, (got, want_gpu_p)
+        assert abs(got[0] - want_orc[0]) <= 3 + 0.25 * want_orc[0], (got, want_orc)
+        assert got[1] == want_orc[1]
+        assert got[0] > 0 and got[1] > 0  # ties do occur at this size
+    else:  # k steps per call: at least the first step's ties
+        assert got[0] >= want_gpu_p[0] and got[1] >= want_gpu_p[1]
+
+
+def test_diff_state_counts_are_reported(pf, orc):
+    """pf_stats of the differentiable form: the expected counts of unburned, burning and
+    burned cells against FP64 sums of the oracle's state."""
+    H, W, T = 200, 240, 50
+    land = syn.make_landscape(H, W, 23)
+    V, th = syn.smooth_wind(H, W, 23, 0, sigma=8.0)
+    S0 = syn.initial_state(land, [(100, 120), (30, 40)])
+    m = pf.FireModel(H, W, pf.PF_DIFF)
+    set_landscape(m, land, V, th)
+    m.set_params(**PRM)
+    m.forward(cuda(S0), T)
+    st = m.stats()
+    a, b, _ = orc.diff_forward(land, [(V, th)], [0], orc.Params(**PRM), S0, T, keep_states=False)
+    burn = S0 != 0
+    want = [float((~burn).sum()), float((1 - a)[burn].sum()), float(b.sum()), float((a - b).sum())]
+    assert st["step"] == T
+    assert st["cells"][0] == want[0]
+    for g, w in zip(st["cells"][1:], want[1:]):
+        assert g == pytest.approx(w, rel=1e-5, abs=1e-3)
+    assert st["near_ties_ignite"] == 0 and st["near_ties_continue"] == 0
