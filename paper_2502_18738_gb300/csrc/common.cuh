@@ -71,19 +71,17 @@ __device__ __forceinline__ float a_encode(float a, float ua) { return a < 0.5f ?
 // Truncating it at FP32's floor slows the front measurably within a few hundred steps;
 // carrying it to FP64's floor (2^-1074) does not. Cells with a < 2^-64 are therefore
 // held in tiers k = 1 .. kKMax with a = A 2^(-64 k), b = B 2^(-64 k), A in [2^-64, 1):
-// an FP32 mantissa with an 11-bit exponent range, below 2^-1088 the cell is 0.
+// an FP32 mantissa with an 11-bit exponent range, below 2^-960 the cell is 0.
 // Storage keeps 8 bytes per cell. A cell of tier 0 is stored as before (A complement-
 // aware, B >= +0). A tiered cell stores -B (B's sign bit marks the tier) and its A
 // rounded to 19 mantissa bits with k in the low 5 bits.
-constexpr int kKMax = 16;
-constexpr int kKNone = 31;  // tier of "no burning neighbour": every tier difference >= 3
+constexpr int kKMax = 14;  // below 2^-960 a cell is 0 (4-bit tier fields keep 15 for "a = 0")
+constexpr int kKNone = 15;  // b-tier of a cell with b = 0 (and kP of a cell with no burning neighbour)
 constexpr float kTierUp = 0x1p64f, kTierDown = 0x1p-64f;
 
-// 2^(-64 d) for a tier difference d >= 0 (0 from d = 3 on, where a term is below 2^-192
-// of the largest); d < 0 gives 0 and is only used on zero terms
-__device__ __forceinline__ float tier_scale(int d) {
-    return d == 0 ? 1.0f : (d == 1 ? 0x1p-64f : (d == 2 ? 0x1p-128f : 0.0f));
-}
+// 2^(-64 d) for a tier difference 0 <= d <= 15: 1, 2^-64, and 0 from d = 2 on (a term two
+// tiers down is below 2^-128 of the largest)
+__device__ __forceinline__ float tier_scale(int d) { return __int_as_float(max(127 - 64 * d, 0) << 23); }
 
 // stored (As, Bs) -> tier k and the magnitudes A, B in that tier
 __device__ __forceinline__ void x_decode(float As, float Bs, float& A, float& B, int& k) {
@@ -93,6 +91,51 @@ __device__ __forceinline__ void x_decode(float As, float Bs, float& A, float& B,
     A = tiered ? __uint_as_float(ua & ~31u) : As;
     B = __uint_as_float(ub & 0x7fffffffu);
 }
+// Per-thread tier summaries of a 4-bit-per-cell tier word (a = 0 cells hold 15, which
+// belongs to no tier: such a cell computes the same under any tier's arithmetic). Fields
+// of 4 bits: [0] the least tier of the word's cells (15: none), [1] the greatest (0:
+// none), [2] / [3] the same for its first cell, [4] / [5] for its last cell.
+__device__ __forceinline__ uint32_t tier_summary(uint32_t w) {
+    uint32_t lo = 15u, hi = 0u;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const uint32_t t = (w >> (4 * m)) & 15u;
+        lo = min(lo, t);
+        hi = max(hi, t == 15u ? 0u : t);
+    }
+    const uint32_t f = w & 15u, l = w >> 28;
+    return lo | (hi << 4) | (f << 8) | ((f == 15u ? 0u : f) << 12) | (l << 16) | ((l == 15u ? 0u : l) << 20);
+}
+__device__ __forceinline__ uint32_t ts_lo(uint32_t s) { return s & 15u; }
+__device__ __forceinline__ uint32_t ts_hi(uint32_t s) { return (s >> 4) & 15u; }
+__device__ __forceinline__ uint32_t ts_first_lo(uint32_t s) { return (s >> 8) & 15u; }
+__device__ __forceinline__ uint32_t ts_first_hi(uint32_t s) { return (s >> 12) & 15u; }
+__device__ __forceinline__ uint32_t ts_last_lo(uint32_t s) { return (s >> 16) & 15u; }
+__device__ __forceinline__ uint32_t ts_last_hi(uint32_t s) { return (s >> 20) & 15u; }
+
+// The window of a thread owning the 8-cell column strip at (strip, x) of a 64 x 64 region
+// (rows ys-1 .. ys+8, columns x-1 .. x+1) from the summaries of its own strip (c), the
+// neighbouring columns (at -dl / +dr) and the strips above and below: whether its cells
+// that are not 0 are all in one tier, and that tier (k0 = 0 when all are 0).
+__device__ __forceinline__ bool window_one_tier(const uint32_t* sum, int tid, int dl, int dr, bool above,
+                                                bool below, int row_stride, uint32_t c, uint32_t& k0) {
+    const uint32_t l = sum[tid - dl], r = sum[tid + dr];
+    uint32_t lo = min(min(ts_lo(c), ts_lo(l)), ts_lo(r));
+    uint32_t hi = max(max(ts_hi(c), ts_hi(l)), ts_hi(r));
+    if (above) {
+        const uint32_t* a = sum + tid - row_stride;
+        lo = min(min(lo, ts_last_lo(a[0])), min(ts_last_lo(a[-dl]), ts_last_lo(a[dr])));
+        hi = max(max(hi, ts_last_hi(a[0])), max(ts_last_hi(a[-dl]), ts_last_hi(a[dr])));
+    }
+    if (below) {
+        const uint32_t* b = sum + tid + row_stride;
+        lo = min(min(lo, ts_first_lo(b[0])), min(ts_first_lo(b[-dl]), ts_first_lo(b[dr])));
+        hi = max(max(hi, ts_first_hi(b[0])), max(ts_first_hi(b[-dl]), ts_first_hi(b[dr])));
+    }
+    k0 = lo == 15u ? 0u : lo;
+    return lo >= hi;
+}
+
 // the tier of a stored cell (0 for tier 0 and for a = 0)
 __device__ __forceinline__ int x_tier(float As, float Bs) {
     return (int32_t)__float_as_uint(Bs) < 0 ? (int)(__float_as_uint(As) & 31u) : 0;
@@ -128,27 +171,12 @@ __device__ __forceinline__ void x_renorm(float& A, float& B, int& k) {
     }
 }
 
-// One cell's differentiable step in the tiered arithmetic (the definition every kernel
-// follows; on tier-0 inputs it is the plain FP32 update below, bit for bit).
-//   nb[d], nk[d]: the neighbours' B magnitudes and tiers (B = 0 outside the grid);
-//   q[d]: the folded factors into this cell; A, B, k: the cell's own (A complement-
-//   encoded when k = 0 and a >= 1/2); returns A', B', k' (A' rounded when tiered).
-// P is accumulated at the tier kP of the largest contributions (terms more than two
-// tiers down vanish); when kP >= 1 every true term is below 2^-61, so the survival
-// product stays 1 and P is a plain sum.
-__device__ __forceinline__ void x_update(const float (&nb)[8], const int (&nk)[8], const float (&q)[8], float A,
-                                         float B, int k, float pc, float& An, float& Bn, int& kn) {
-    int kP = kKNone;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) kP = nb[d] != 0.0f ? min(kP, nk[d]) : kP;
-    const bool kP0 = kP == 0;
-    float P = 0.0f, S = 1.0f;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        const float x = __fmul_rn(__fmul_rn(nb[d], q[d]), tier_scale(nk[d] - kP));
-        P = fmaf(x, S, P);
-        S = kP0 ? fmaf(-x, S, S) : S;
-    }
+// The cell's own part of a differentiable step in the tiered arithmetic, from the P and S
+// accumulated over its neighbours at tier kP (kKNone: no burning neighbour): A, B, k are
+// the cell's own (A complement-encoded when k = 0 and a >= 1/2); returns A', B', k' (A'
+// rounded when tiered). The update runs at tier min(k, kP) and renormalises.
+__device__ __forceinline__ void x_own(float P, float S, int kP, float A, float B, int k, float pc, float& An,
+                                      float& Bn, int& kn) {
     if (signbit(A)) {  // a >= 1/2, tier 0
         const float a = __fadd_rn(1.0f, A), ua = -A;
         const float n = __fmul_rn(__fmul_rn(ua, P), tier_scale(kP));
@@ -158,7 +186,7 @@ __device__ __forceinline__ void x_update(const float (&nb)[8], const int (&nk)[8
         return;
     }
     const int s = __float_as_uint(A) == 0u ? kP : min(k, kP);
-    const float h = tier_scale(k - s);
+    const float h = tier_scale(max(k - s, 0));  // a = 0 (s = kP may exceed k): A = B = 0, h unused
     const float as = __fmul_rn(A, h), bs = __fmul_rn(B, h);
     const float ua = k == 0 ? __fsub_rn(1.0f, A) : 1.0f;
     const float n = __fmul_rn(ua, __fmul_rn(P, tier_scale(kP - s)));
@@ -167,6 +195,29 @@ __device__ __forceinline__ void x_update(const float (&nb)[8], const int (&nk)[8
     An = s == 0 ? a_encode(an, __fmul_rn(ua, S)) : an;
     kn = s;
     x_renorm(An, Bn, kn);
+}
+
+// One cell's differentiable step in the tiered arithmetic (the definition every kernel
+// follows; on tier-0 inputs it is the plain FP32 update below, bit for bit).
+//   nb[d], nk[d]: the neighbours' B magnitudes and tiers (B = 0 outside the grid);
+//   q[d]: the folded factors into this cell; A, B, k: the cell's own.
+// P is accumulated at the tier kP of the largest contributions, the least tier of the
+// neighbours with b > 0 (terms two or more tiers down vanish); when kP >= 1 every true
+// term is below 2^-61, so the survival product stays 1 and P is a plain sum.
+__device__ __forceinline__ void x_update(const float (&nb)[8], const int (&nk)[8], const float (&q)[8], float A,
+                                         float B, int k, float pc, float& An, float& Bn, int& kn) {
+    int kP = kKNone;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) kP = min(kP, nb[d] != 0.0f ? nk[d] : kKNone);
+    const bool kP0 = kP == 0;
+    float P = 0.0f, S = 1.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const float x = __fmul_rn(__fmul_rn(nb[d], q[d]), tier_scale((nb[d] != 0.0f ? nk[d] : kKNone) - kP));
+        P = fmaf(x, S, P);
+        S = kP0 ? fmaf(-x, S, S) : S;
+    }
+    x_own(P, S, kP, A, B, k, pc, An, Bn, kn);
 }
 
 // The same update when the cell and every neighbour are in tier 0, from the P and S that

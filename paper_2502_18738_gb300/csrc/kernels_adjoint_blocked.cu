@@ -51,6 +51,7 @@ struct Smem {
     float el2r[2][kStrips][kM];          // x = 31 -> x = 32 (dc = +1), rows of the strip
     float er2l[2][kStrips][kM];          // x = 32 -> x = 31 (dc = -1)
     float edump[kThreads];               // where the other threads' exchange stores go
+    uint32_t ks[kThreads];               // tier summaries at t of each thread's 8 cells (tier_summary)
 };
 
 // 2^(-8 sigma) of a cell known to be in tier 0 (1 for a >= 1/2 and for a = 0, where it
@@ -329,13 +330,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             // factors 1 - b q and their exact b 2^(8 sigma') in dL/dq. Otherwise every
             // exponent is below 8 and the ratios are products of per-cell powers of two,
             // the same values.
-            bool tq = false;
+            // The tiers at t of this thread's cells, packed, for its neighbours' choice of
+            // path below (written after the previous step's barrier, read before this
+            // step's end barrier).
+            uint32_t kword = 0u;
+#pragma unroll
+            for (int k = 0; k < kM; ++k) {
+                const float As = stA[(ys + k) * kCT + x];
+                kword |= (__float_as_uint(As) == 0u ? 15u : (uint32_t)x_tier(As, stB[(ys + k) * kCT + x])) << (4 * k);
+            }
+            const uint32_t ksum = tier_summary(kword);
+            sm.ks[tid] = ksum;
+            __syncthreads();
+            // A warp whose windows (rows ys-1 .. ys+8, columns x-1 .. x+1) hold, at t, cells
+            // of one tier k0 besides cells with a = 0, and whose cells' exponents at t + 1 lie
+            // within 15 of 8 k0, measures every exponent from 8 k0: its unit ratios are then
+            // products of per-cell powers of two, the values the general arithmetic forms
+            // from integer exponents. Other warps take the general arithmetic.
+            uint32_t k0;
+            bool uni = window_one_tier(sm.ks, tid, x - xl, xr - x, strip > 0, strip < kStrips - 1, kCT, ksum, k0);
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
-                tq |= (int32_t)__float_as_uint(stB[(ys + k) * kCT + x]) < 0 || (sp >= 8 && sp != kSigmaZero);
+                const int rel = sp - 8 * (int)k0;
+                uni = uni && (sp == kSigmaZero || (rel >= -15 && rel <= 15));
             }
-            const bool slow = __syncthreads_or(tq);
+            const bool slow = !__all_sync(0xffffffffu, uni);
             auto cells = [&](auto tag) {
                 constexpr bool kSlow = decltype(tag)::value;
                 // stored b and (general path) sigma or (tier 0) 2^-sigma of rows y-1, y, y+1 in
@@ -380,8 +400,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float(&wd)[3] = w[(k + 2) % 3];  // source row y + 1
                     const float Aown = stA[y * kCT + x];
                     int sg;
-                    if constexpr (kSlow) sg = sm3[1];
-                    else sg = x_sigma(Aown, 0.0f);
+                    if constexpr (kSlow) {
+                        sg = sm3[1];
+                    } else {
+                        sg = x_sigma(Aown, 0.0f);  // 8 k0 below this one
+                        sg = sg == kSigmaZero ? sg : sg + 8 * (int)k0;
+                    }
                     sgc[k >> 2] |= (uint32_t)sg << (8 * (k & 3));
                     const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
                     const bool live = sp != kSigmaZero;  // a > 0 at t + 1
@@ -389,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if constexpr (kSlow) {
                         scl[k] = (sg == kSigmaZero || !live) ? 0.0f : exp2i(8 * (sp - sg));
                     } else {
-                        Up = live ? unit8(sp) : 0.0f;
+                        Up = live ? unit8(sp - 8 * (int)k0) : 0.0f;  // 2^(8 (sigma' - 8 k0))
                         scl[k] = (sg == kSigmaZero) ? 0.0f : Up * um[1];
                     }
                     uint32_t tmv[16];
@@ -423,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if constexpr (kSlow)
                                 ua = signbit(Aown) ? -Aown : ((int32_t)__float_as_uint(bm[1]) < 0 ? 1.0f : 1.0f - Aown);
                             else
-                                ua = signbit(Aown) ? -Aown : 1.0f - Aown;
+                                ua = signbit(Aown) ? -Aown : (k0 != 0u ? 1.0f : 1.0f - Aown);
                             const float ln = la[k] + lb[k];
                             const float tg = xin ? ln * ua : 0.0f;  // l_P_j in units 2^(8 sigma'(j))
                             bool quiet = true;  // no neighbour burning (behind or ahead of the front)
@@ -447,7 +471,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 float f[8];
                                 // b of a tiered source is below 2^-64: its factor is exactly 1
 #pragma unroll
-                                for (int d = 0; d < 8; ++d) f[d] = fmaf(kSlow ? -fmaxf(nb[d], 0.0f) : -nb[d], qv[d], 1.0f);
+                                for (int d = 0; d < 8; ++d)
+                                    f[d] = fmaf((kSlow || k0 != 0u) ? -fmaxf(nb[d], 0.0f) : -nb[d], qv[d], 1.0f);
                                 // t_d = tg prod_{e != d} f_e by a product tree over pairs and
                                 // halves (no division: a factor can be exactly 0)
                                 const float p01 = f[0] * f[1], p23 = f[2] * f[3], p45 = f[4] * f[5], p67 = f[6] * f[7];
@@ -469,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                             g[d] = (fabsf(nb[d]) * exp2i(8 * (ns[d] & 7))) * r[d];
                                     } else {
 #pragma unroll
-                                        for (int d = 0; d < 8; ++d) g[d] = nb[d] * Up;
+                                        for (int d = 0; d < 8; ++d) g[d] = fabsf(nb[d]) * Up;
                                     }
 #pragma unroll
                                     for (int d = 0; d < 8; ++d) {

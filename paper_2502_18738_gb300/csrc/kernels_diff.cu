@@ -61,11 +61,12 @@ __global__ void k_ignition_map_diff(int H, int W, int pitch, const float* __rest
         float Ai;
         x_decode(ab[i], ab[plane + i], Ai, nb[d], nk[d]);
         nb[d] = in ? nb[d] : 0.0f;
-        kP = nb[d] != 0.0f ? min(kP, nk[d]) : kP;
+        nk[d] = nb[d] != 0.0f ? nk[d] : kKNone;  // the b-tier
+        kP = min(kP, nk[d]);
     }
     float P = 0.0f, S = 1.0f;
     for (int d = 0; d < 8; ++d) {
-        const float x = (nb[d] * q[d * plane + j]) * tier_scale(nk[d] - kP);
+        const float x = __fmul_rn(__fmul_rn(nb[d], q[d * plane + j]), tier_scale(nk[d] - kP));
         P = fmaf(x, S, P);
         S = kP == 0 ? fmaf(-x, S, S) : S;
     }

@@ -32,7 +32,8 @@ struct Smem {
     float q[8 * kPlane];     // staged q planes of the next tile (TMA destination)
     float st[2 * kPlane];    // staged (A, b) of the next tile (TMA destination)
     float b[2][kPlane];      // b ping-pong of the current tile (magnitude in its tier)
-    uint8_t k[2][kPlane];    // tier ping-pong of the current tile
+    uint8_t k[2][kPlane];    // b-tier ping-pong of the current tile (the tier where b > 0, else kKNone)
+    uint32_t ks[2][kThreads];  // per thread: the tier summary of its 8 cells (tier_summary)
 };
 
 // Tile activity flags (kActB, kActA: common.cuh); kActA tests the encoded A != +0.
@@ -61,7 +62,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ int s_next;
     const int tid = threadIdx.x;
     const int x = tid % kCT;             // region column
-    const int ys = (tid / kCT) * kM;     // first region row of the strip
+    const int strip = tid / kCT;
+    const int ys = strip * kM;           // first region row of the strip
     const uint32_t bytes = (uint32_t)((8 + 2) * kPlane * sizeof(float));
     const size_t gplane = (size_t)H * pitch;
 
@@ -97,7 +99,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         parity ^= 1u;
         // stage -> registers (q, A) and -> ping-pong buffer 0 (b and its tier)
-        bool burning = false, tiered = false;
+        bool burning = false;
+        uint32_t kword = 0u;  // this thread's tiers, packed
 #pragma unroll
         for (int m = 0; m < kM; ++m) {
             const int y = ys + m;
@@ -107,16 +110,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             int kv;
             x_decode(sm.st[y * kCT + x], sm.st[kPlane + y * kCT + x], A[m], bv, kv);
             sm.b[0][y * kCT + x] = bv;
-            sm.k[0][y * kCT + x] = (uint8_t)kv;
+            sm.k[0][y * kCT + x] = (uint8_t)(bv != 0.0f ? kv : kKNone);
+            kword |= (__float_as_uint(A[m]) == 0u ? 15u : (uint32_t)kv) << (4 * m);
             burning |= bv != 0.0f;
-            tiered |= kv != 0;
         }
+        uint32_t ksum = tier_summary(kword);
+        sm.ks[0][tid] = ksum;
         fence_proxy_async();  // these generic reads of the stage precede the next TMA writes
         // b = 0 in the whole region: every P is 0 at every step of the launch, so the
         // region's state does not change and the steps are skipped (the stores remain)
         const bool live = __syncthreads_or(burning);  // also: stage fully consumed
-        // a tiered cell in the region: its steps take the general (tiered) update
-        tiered = __syncthreads_or(tiered);
         int next = ntiles;
         if (tid == 0) {
             next = (int)gridDim.x + atomicAdd(work, 1);
@@ -146,11 +149,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint8_t* ksrc = sm.k[cur];
                 uint8_t* kdst = sm.k[cur ^ 1];
                 const int xl = xin ? x - 1 : x, xr = xin ? x + 1 : x;
-                bool now_tiered = false;
-                if (!tiered) {
-                    // every cell of the region in tier 0: the FP32 update, which is the
-                    // tiered one on such inputs, plus the move of cells that fall below
-                    // 2^-64 into tier 1
+                // Whether the cells of this thread's windows (rows ys-1 .. ys+8, columns
+                // x-1 .. x+1) that are not 0 are all in one tier k0 (from the per-thread tier
+                // summaries); when it holds for every lane of the warp, the warp takes the
+                // update specialised to one tier (the general one on such inputs, bit for
+                // bit), otherwise the general update with per-neighbour tiers.
+                uint32_t k0;
+                const bool uni = window_one_tier(sm.ks[cur], tid, x - xl, xr - x, strip > 0, strip < kRT / kM - 1,
+                                                 kCT, ksum, k0);
+                uint32_t knew = kword;
+                if (__all_sync(0xffffffffu, uni)) {
+                    // one tier k0 for the whole warp (adjacent lanes share window columns)
                     // ring of b rows ys-1 .. ys+kM (slot (row - ys + 1) % 3) in columns x-1, x, x+1
                     float bw[3][3];
                     const int y_first = ys > 0 ? ys - 1 : 0;
@@ -170,49 +179,103 @@ __global__ void __launch_bounds__(kThreads, 1)
                             // values, a select rather than a divergent branch
                             // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
                             const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
-                            float P = 0.0f, S = 1.0f;
-#pragma unroll
-                            for (int d = 0; d < 8; ++d) ign_acc(__fmul_rn(nb[d], q[m][d]), P, S);
                             float An, Bn;
                             int kn;
-                            x_update_t0(P, S, A[m], bm[1], pc, An, Bn, kn);
-                            A[m] = xin ? An : A[m];
-                            dst[y * kCT + x] = xin ? Bn : bm[1];
-                            kdst[y * kCT + x] = (uint8_t)(xin ? kn : 0);
-                            now_tiered |= xin && kn != 0;
+                            if (k0 == 0u) {
+                                // tier 0: Eq. 9 with the survival product
+                                float P = 0.0f, S = 1.0f;
+#pragma unroll
+                                for (int d = 0; d < 8; ++d) ign_acc(__fmul_rn(nb[d], q[m][d]), P, S);
+                                x_update_t0(P, S, A[m], bm[1], pc, An, Bn, kn);
+                            } else {
+                                // one tier below 2^-64: every true term is below 2^-61, so the
+                                // survival product is 1, 1 - a is 1 and P is a plain sum
+                                float P = 0.0f;
+#pragma unroll
+                                for (int d = 0; d < 8; ++d) P = fmaf(__fmul_rn(nb[d], q[m][d]), 1.0f, P);
+                                An = __fadd_rn(A[m], P);
+                                Bn = fmaf(pc, bm[1], P);
+                                kn = (int)k0;
+                                x_renorm(An, Bn, kn);
+                            }
+                            if (xin) {  // an edge column keeps its cell
+                                A[m] = An;
+                                dst[y * kCT + x] = Bn;
+                                kdst[y * kCT + x] = (uint8_t)(Bn != 0.0f ? kn : kKNone);
+                                const uint32_t nib = __float_as_uint(An) == 0u ? 15u : (uint32_t)kn;
+                                knew = (knew & ~(15u << (4 * m))) | (nib << (4 * m));
+                            } else {
+                                dst[y * kCT + x] = bm[1];
+                                kdst[y * kCT + x] = ksrc[y * kCT + x];
+                            }
                         }
                     }
                 } else {
+                    // General: per-neighbour tiers. Rolling windows of b and of 64 x the
+                    // b-tier over rows ys-1 .. ys+kM in columns x-1, x, x+1 (slot (row - ys + 1)
+                    // % 3), and each window row's least b-tier; kP of a cell is the least over
+                    // the rows above and below and its own row's left and right cells.
+                    float bw[3][3];
+                    int tw[3][3], rmin[3];
+                    const int cols[3] = {xl, x, xr};
+                    const int y_first = ys > 0 ? ys - 1 : 0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        bw[0][c] = src[y_first * kCT + cols[c]];
+                        tw[0][c] = 64 * (int)ksrc[y_first * kCT + cols[c]];
+                        bw[1][c] = src[ys * kCT + cols[c]];
+                        tw[1][c] = 64 * (int)ksrc[ys * kCT + cols[c]];
+                    }
+                    rmin[0] = min(min(tw[0][0], tw[0][1]), tw[0][2]);
+                    rmin[1] = min(min(tw[1][0], tw[1][1]), tw[1][2]);
 #pragma unroll
                     for (int m = 0; m < kM; ++m) {
                         const int y = ys + m;
+                        const int su = m % 3, sc = (m + 1) % 3, sd = (m + 2) % 3;
+                        const int yn = y + 1 < kRT ? y + 1 : y;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            bw[sd][c] = src[yn * kCT + cols[c]];
+                            tw[sd][c] = 64 * (int)ksrc[yn * kCT + cols[c]];
+                        }
+                        rmin[sd] = min(min(tw[sd][0], tw[sd][1]), tw[sd][2]);
                         if (y >= 1 && y < kRT - 1) {
-                            // the edge columns compute on their clamped window and keep
-                            // their old values, as in the tier-0 path
-                            float nb[8];
-                            int nk[8];
+                            // the edge columns compute on their clamped window and keep their
+                            // old values, as in the path above
+                            const int kP64 = min(min(rmin[su], rmin[sd]), min(tw[sc][0], tw[sc][2]));
+                            const int e0 = 127 + kP64;  // tier_scale(t - kP) = 2^(e0 - 64 t - 127) or 0
+                            const bool kP0 = kP64 == 0;
+                            const float nb[8] = {bw[su][0], bw[su][1], bw[su][2], bw[sc][0], bw[sc][2], bw[sd][0], bw[sd][1], bw[sd][2]};
+                            const int nt[8] = {tw[su][0], tw[su][1], tw[su][2], tw[sc][0], tw[sc][2], tw[sd][0], tw[sd][1], tw[sd][2]};
+                            float P = 0.0f, S = 1.0f;
 #pragma unroll
                             for (int d = 0; d < 8; ++d) {
-                                const int dc = dir_dc(d);
-                                const int xx = dc < 0 ? xl : (dc > 0 ? xr : x);
-                                const int o = (y + dir_dr(d)) * kCT + xx;
-                                nb[d] = src[o];
-                                nk[d] = ksrc[o];
+                                const float f = __int_as_float(max(e0 - nt[d], 0) << 23);
+                                const float xx = __fmul_rn(__fmul_rn(nb[d], q[m][d]), f);
+                                P = fmaf(xx, S, P);
+                                S = kP0 ? fmaf(-xx, S, S) : S;
                             }
-                            const float Bo = src[y * kCT + x];
-                            const int ko = ksrc[y * kCT + x];
+                            const uint32_t nib = (kword >> (4 * m)) & 15u;
                             float An, Bn;
                             int kn;
-                            x_update(nb, nk, q[m], A[m], Bo, ko, pc, An, Bn, kn);
-                            A[m] = xin ? An : A[m];
-                            dst[y * kCT + x] = xin ? Bn : Bo;
-                            const int kw = xin ? kn : ko;
-                            kdst[y * kCT + x] = (uint8_t)kw;
-                            now_tiered |= kw != 0;
+                            x_own(P, S, kP64 >> 6, A[m], bw[sc][1], nib == 15u ? 0 : (int)nib, pc, An, Bn, kn);
+                            if (xin) {
+                                A[m] = An;
+                                dst[y * kCT + x] = Bn;
+                                kdst[y * kCT + x] = (uint8_t)(Bn != 0.0f ? kn : kKNone);
+                                const uint32_t nn = __float_as_uint(An) == 0u ? 15u : (uint32_t)kn;
+                                knew = (knew & ~(15u << (4 * m))) | (nn << (4 * m));
+                            } else {
+                                dst[y * kCT + x] = bw[sc][1];
+                                kdst[y * kCT + x] = ksrc[y * kCT + x];
+                            }
                         }
                     }
                 }
-                tiered = __syncthreads_or(now_tiered);
+                kword = knew;
+                ksum = tier_summary(kword);
+                sm.ks[cur ^ 1][tid] = ksum;
+                __syncthreads();
                 cur ^= 1;
             }
             if (all_out) {  // every intermediate state (segment recompute for the adjoint)
@@ -224,7 +287,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int y = ys + m, gr = r0 + y;
                         if (y >= kHalo && y < kRT - kHalo && gr < H) {
                             float As, Bs;
-                            x_encode(A[m], sm.b[cur][y * kCT + x], sm.k[cur][y * kCT + x], As, Bs);
+                            const uint32_t nib = (kword >> (4 * m)) & 15u;
+                            x_encode(A[m], sm.b[cur][y * kCT + x], nib == 15u ? 0 : (int)nib, As, Bs);
                             o[(size_t)gr * pitch + gc] = As;
                             o[gplane + (size_t)gr * pitch + gc] = Bs;
                         }
@@ -240,7 +304,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int y = ys + m, gr = r0 + y;
                     if (y >= kHalo && y < kRT - kHalo && gr < H) {
                         float As, Bs;
-                        x_encode(A[m], sm.b[cur][y * kCT + x], sm.k[cur][y * kCT + x], As, Bs);
+                        const uint32_t nib = (kword >> (4 * m)) & 15u;
+                        x_encode(A[m], sm.b[cur][y * kCT + x], nib == 15u ? 0 : (int)nib, As, Bs);
                         out[(size_t)gr * pitch + gc] = As;
                         out[gplane + (size_t)gr * pitch + gc] = Bs;
                     }
