@@ -240,15 +240,12 @@ __device__ __forceinline__ void x_update_t0(float P, float S, float A, float B, 
     if (!signbit(A)) x_renorm(An, Bn, kn);
 }
 
-// Scaled adjoint exponents for the tiered state (see the scaled adjoint below): sigma in
-// units of 8 bits, sigma = 8 k + min(-floor(log2 A), 63) / 8 (0 for a >= 1/2).
+// Scaled-adjoint exponent of a cell (see the scaled adjoint below): its tier, 0 for
+// a >= 1/2, and 255 (kSigmaZero) for a == 0.
 __device__ __forceinline__ int x_sigma(float As, float Bs) {
     const uint32_t ua = __float_as_uint(As);
     if (ua == 0u) return 255;  // a == 0 (kSigmaZero)
-    if ((int32_t)ua < 0) return 0;
-    const int k = x_tier(As, Bs);
-    const int e = min(127 - (int)((ua >> 23) & 0xffu), 63);
-    return 8 * k + (e >> 3);
+    return x_tier(As, Bs);
 }
 // 2^e for an integer exponent, 0 below 2^-126 (terms scaled that far down are dropped)
 __device__ __forceinline__ float exp2i(int e) {
@@ -269,12 +266,12 @@ __device__ __forceinline__ void ign_acc(float x, float& P, float& S) {
 // in time while the states it multiplies shrink as fast; their products, which carry
 // the (pulled) front's sensitivity, stay O(1), but lambda itself overflows FP32 within
 // ~60 steps (and FP64 within a few hundred). The adjoint therefore stores
-// mu_j = lambda_j 2^(-8 sigma_j) with a per-cell exponent sigma_j (units of 8 bits) taken
-// from the cell's own state (x_sigma above: about -log2(a_j) / 8, 0 for a >= 1/2, up to
-// 8 kKMax + 7 in the deepest tier), and rescales every transfer between cells by the
-// exact power of two 2^(8 (sigma_j - sigma_i)). sigma = kSigmaZero marks a == 0 exactly
-// (outside the light cone, or non-burnable): there lambda multiplies only exact zeros
-// and is held at 0.
+// mu_j = lambda_j 2^(-64 sigma_j) with sigma_j the tier of the cell's own state (x_sigma;
+// lambda ~ 1 / a spans 2^64 within a tier, well inside FP32), and rescales a transfer
+// between cells of different tiers by the exact power of two 2^(64 (sigma_j - sigma_i)).
+// Within one tier nothing is rescaled. sigma = kSigmaZero marks a == 0 exactly (outside
+// the light cone, or non-burnable): there lambda multiplies only exact zeros and is held
+// at 0.
 constexpr int kSigmaZero = 255;
 
 // ---------------------------------------------------------------- launchers

@@ -54,16 +54,6 @@ struct Smem {
     uint32_t ks[kThreads];               // tier summaries at t of each thread's 8 cells (tier_summary)
 };
 
-// 2^(-8 sigma) of a cell known to be in tier 0 (1 for a >= 1/2 and for a = 0, where it
-// is never used), and 2^(8 s) for s in [0, 15]
-__device__ __forceinline__ float unit_inv_t0(float As) {
-    const uint32_t u = __float_as_uint(As);
-    if ((int32_t)u <= 0) return 1.0f;
-    const int e = min(127 - (int)(u >> 23), 63);
-    return __int_as_float((127 - 8 * (e >> 3)) << 23);
-}
-__device__ __forceinline__ float unit8(int s) { return __int_as_float((8 * s + 127) << 23); }
-
 __device__ __forceinline__ void origin(int tile, int tiles_x, int& r0, int& c0) {
     r0 = (tile / tiles_x) * kIR - kHalo;
     c0 = (tile % tiles_x) * kIC - kHalo;
@@ -241,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int d = 0; d < 8; ++d) {
                     const int yy = use ? y + dir_dr(d) : y, xx = use ? x + dir_dc(d) : x;
                     const int si = x_sigma(stA[yy * kCT + xx], stB[yy * kCT + xx]);
-                    kv[d] = use ? (uaj * sm.q[d * kPlane + y * kCT + x]) * exp2i(8 * (sj - si)) : 0.0f;
+                    kv[d] = use ? (uaj * sm.q[d * kPlane + y * kCT + x]) * exp2i(64 * (sj - si)) : 0.0f;
                 }
                 tmem_st8_nc(tbase + 8 * k, kv);  // frozen layout: cell k in columns 8k .. 8k + 7
             }
@@ -324,15 +314,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 sgc[0] = sgp[0];
                 sgc[1] = sgp[1];
             } else {
-            // Cells in the tiers below 2^-64 at t (staged state) or t + 1 (sigma' >= 8)
-            // anywhere in the region take the general arithmetic: unit ratios
-            // 2^(8 (sigma' - sigma)) from integer exponents, b of tiered sources 0 in the
-            // factors 1 - b q and their exact b 2^(8 sigma') in dL/dq. Otherwise every
-            // exponent is below 8 and the ratios are products of per-cell powers of two,
-            // the same values.
-            // The tiers at t of this thread's cells, packed, for its neighbours' choice of
-            // path below (written after the previous step's barrier, read before this
-            // step's end barrier).
+            // The tiers at t of this thread's cells, packed (15: a = 0), and their summary for
+            // the neighbours' choice of path below (written after the previous step's
+            // barrier, read before this step's end barrier).
             uint32_t kword = 0u;
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
@@ -342,39 +326,37 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t ksum = tier_summary(kword);
             sm.ks[tid] = ksum;
             __syncthreads();
-            // A warp whose windows (rows ys-1 .. ys+8, columns x-1 .. x+1) hold, at t, cells
-            // of one tier k0 besides cells with a = 0, and whose cells' exponents at t + 1 lie
-            // within 15 of 8 k0, measures every exponent from 8 k0: its unit ratios are then
-            // products of per-cell powers of two, the values the general arithmetic forms
-            // from integer exponents. Other warps take the general arithmetic.
+            // A warp whose windows (rows ys-1 .. ys+8, columns x-1 .. x+1) hold, at t, cells of
+            // one tier k0 besides cells with a = 0, and whose cells are at t + 1 in tier k0 or
+            // k0 - 1 (or have a = 0), needs no unit ratios between sources: every transfer of
+            // a target j is rescaled by 2^(64 (sigma'(j) - k0)), folded into its l_P once.
+            // Other warps take the general arithmetic, a ratio per transfer.
             uint32_t k0;
             bool uni = window_one_tier(sm.ks, tid, x - xl, xr - x, strip > 0, strip < kStrips - 1, kCT, ksum, k0);
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
-                const int rel = sp - 8 * (int)k0;
-                uni = uni && (sp == kSigmaZero || (rel >= -15 && rel <= 15));
+                uni = uni && (sp == kSigmaZero || sp == (int)k0 || sp + 1 == (int)k0);
             }
             const bool slow = !__all_sync(0xffffffffu, uni);
             auto cells = [&](auto tag) {
                 constexpr bool kSlow = decltype(tag)::value;
-                // stored b and (general path) sigma or (tier 0) 2^-sigma of rows y-1, y, y+1 in
-                // columns x-1, x, x+1: ring slot (row - ys + 1) % 3
-                float bw[3][3], uw[3][3];
+                // stored b and (general path) the tier of rows y-1, y, y+1 in columns x-1, x,
+                // x+1: ring slot (row - ys + 1) % 3
+                float bw[3][3];
                 int sw[3][3];
-                auto src = [&](int row, int c, float& bv, float& uv, int& sv) {
+                auto src = [&](int row, int c, float& bv, int& sv) {
                     const int o = row * kCT + c;
                     bv = stB[o];
                     if constexpr (kSlow) sv = x_sigma(stA[o], bv);
-                    else uv = unit_inv_t0(stA[o]);
                 };
                 {
                     const int y0 = ys > 0 ? ys - 1 : 0;
                     const int cols[3] = {xl, x, xr};
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        src(y0, cols[c], bw[0][c], uw[0][c], sw[0][c]);
-                        src(ys, cols[c], bw[1][c], uw[1][c], sw[1][c]);
+                        src(y0, cols[c], bw[0][c], sw[0][c]);
+                        src(ys, cols[c], bw[1][c], sw[1][c]);
                     }
                 }
 #pragma unroll
@@ -383,9 +365,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float(&bu)[3] = bw[k % 3];
                     float(&bm)[3] = bw[(k + 1) % 3];
                     float(&bd)[3] = bw[(k + 2) % 3];
-                    float(&uu)[3] = uw[k % 3];
-                    float(&um)[3] = uw[(k + 1) % 3];
-                    float(&ud)[3] = uw[(k + 2) % 3];
                     int(&su)[3] = sw[k % 3];
                     int(&sm3)[3] = sw[(k + 1) % 3];
                     int(&sd)[3] = sw[(k + 2) % 3];
@@ -393,29 +372,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int yd = y + 1 < kRT ? y + 1 : y;
                         const int cols[3] = {xl, x, xr};
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) src(yd, cols[c], bd[c], ud[c], sd[c]);
+                        for (int c = 0; c < 3; ++c) src(yd, cols[c], bd[c], sd[c]);
                     }
                     float(&wu)[3] = w[k % 3];        // source row y - 1 (R = k)
                     float(&wm)[3] = w[(k + 1) % 3];  // source row y
                     float(&wd)[3] = w[(k + 2) % 3];  // source row y + 1
                     const float Aown = stA[y * kCT + x];
+                    // sigma(t) of this cell: the tier (k0 on the single-tier path), kSigmaZero for a = 0
                     int sg;
-                    if constexpr (kSlow) {
-                        sg = sm3[1];
-                    } else {
-                        sg = x_sigma(Aown, 0.0f);  // 8 k0 below this one
-                        sg = sg == kSigmaZero ? sg : sg + 8 * (int)k0;
-                    }
+                    if constexpr (kSlow) sg = sm3[1];
+                    else sg = __float_as_uint(Aown) == 0u ? kSigmaZero : (int)k0;
                     sgc[k >> 2] |= (uint32_t)sg << (8 * (k & 3));
                     const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
                     const bool live = sp != kSigmaZero;  // a > 0 at t + 1
-                    float Up = 0.0f;
-                    if constexpr (kSlow) {
-                        scl[k] = (sg == kSigmaZero || !live) ? 0.0f : exp2i(8 * (sp - sg));
-                    } else {
-                        Up = live ? unit8(sp - 8 * (int)k0) : 0.0f;  // 2^(8 (sigma' - 8 k0))
-                        scl[k] = (sg == kSigmaZero) ? 0.0f : Up * um[1];
-                    }
+                    // single tier: 2^(64 (sigma'(j) - k0)), the ratio of every transfer of j and,
+                    // for this cell's own l_a, the ratio 2^(64 (sigma'(j) - sigma(j)))
+                    const float Up = (kSlow || !live) ? 0.0f : (sp == (int)k0 ? 1.0f : 0x1p-64f);
+                    scl[k] = (sg == kSigmaZero || !live) ? 0.0f : (kSlow ? exp2i(64 * (sp - sg)) : Up);
                     uint32_t tmv[16];
                     tmem_ld16_async(tbase + 16 * k, tmv);
                     tmem_wait_ld16(tmv);
@@ -432,24 +405,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                             // P = 0, which leaves only l_a <- l_a scl, instead of diverging.
                             // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
                             const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
-                            float r[8];  // 2^(8 (sigma'(j) - sigma(i))): to the units of source i
+                            float r[8];  // 2^(64 (sigma'(j) - sigma(i))): to the units of source i
                             if constexpr (kSlow) {
                                 const int ns[8] = {su[0], su[1], su[2], sm3[0], sm3[2], sd[0], sd[1], sd[2]};
 #pragma unroll
-                                for (int d = 0; d < 8; ++d) r[d] = exp2i(8 * (sp - ns[d]));
-                            } else {
-                                const float nu[8] = {uu[0], uu[1], uu[2], um[0], um[2], ud[0], ud[1], ud[2]};
-#pragma unroll
-                                for (int d = 0; d < 8; ++d) r[d] = Up * nu[d];
+                                for (int d = 0; d < 8; ++d) r[d] = exp2i(64 * (sp - ns[d]));
                             }
                             // 1 - a of this cell (1 in the tiers below 2^-64)
-                            float ua;
-                            if constexpr (kSlow)
-                                ua = signbit(Aown) ? -Aown : ((int32_t)__float_as_uint(bm[1]) < 0 ? 1.0f : 1.0f - Aown);
-                            else
-                                ua = signbit(Aown) ? -Aown : (k0 != 0u ? 1.0f : 1.0f - Aown);
+                            const bool own_tiered = kSlow ? (int32_t)__float_as_uint(bm[1]) < 0 : k0 != 0u;
+                            const float ua = signbit(Aown) ? -Aown : (own_tiered ? 1.0f : 1.0f - Aown);
                             const float ln = la[k] + lb[k];
-                            const float tg = xin ? ln * ua : 0.0f;  // l_P_j in units 2^(8 sigma'(j))
+                            // l_P_j in units 2^(64 sigma'(j)); on the single-tier path already in
+                            // the sources' units
+                            const float tg = xin ? (kSlow ? ln * ua : (ln * ua) * Up) : 0.0f;
                             bool quiet = true;  // no neighbour burning (behind or ahead of the front)
 #pragma unroll
                             for (int d = 0; d < 8; ++d) quiet &= nb[d] == 0.0f;
@@ -461,18 +429,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                                     for (int d = 0; d < 8; ++d) {
                                         const float tqv = tg * qv[d];
+                                        const float c = kSlow ? tqv * r[d] : tqv;
                                         const int j = dir_dc(d) + 1;
-                                        if (dir_dr(d) < 0) wu[j] = fmaf(tqv, r[d], wu[j]);
-                                        else if (dir_dr(d) == 0) wm[j] = fmaf(tqv, r[d], wm[j]);
-                                        else wd[j] = fmaf(tqv, r[d], wd[j]);
+                                        if (dir_dr(d) < 0) wu[j] += c;
+                                        else if (dir_dr(d) == 0) wm[j] += c;
+                                        else wd[j] += c;
                                     }
                                 }
                             } else {
                                 float f[8];
                                 // b of a tiered source is below 2^-64: its factor is exactly 1
 #pragma unroll
-                                for (int d = 0; d < 8; ++d)
-                                    f[d] = fmaf((kSlow || k0 != 0u) ? -fmaxf(nb[d], 0.0f) : -nb[d], qv[d], 1.0f);
+                                for (int d = 0; d < 8; ++d) f[d] = fmaf(-fmaxf(nb[d], 0.0f), qv[d], 1.0f);
                                 // t_d = tg prod_{e != d} f_e by a product tree over pairs and
                                 // halves (no division: a factor can be exactly 0)
                                 const float p01 = f[0] * f[1], p23 = f[2] * f[3], p45 = f[4] * f[5], p67 = f[6] * f[7];
@@ -486,24 +454,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     const float r01 = g03 * p23, r23 = g03 * p01, r45 = g47 * p67, r67 = g47 * p45;
                                     const float t[8] = {f[1] * r01, f[0] * r01, f[3] * r23, f[2] * r23,
                                                         f[5] * r45, f[4] * r45, f[7] * r67, f[6] * r67};
-                                    float g[8];  // b_i 2^(8 sigma'(j))
-                                    if constexpr (kSlow) {
-                                        const int ns[8] = {su[0], su[1], su[2], sm3[0], sm3[2], sd[0], sd[1], sd[2]};
-#pragma unroll
-                                        for (int d = 0; d < 8; ++d)
-                                            g[d] = (fabsf(nb[d]) * exp2i(8 * (ns[d] & 7))) * r[d];
-                                    } else {
-#pragma unroll
-                                        for (int d = 0; d < 8; ++d) g[d] = fabsf(nb[d]) * Up;
-                                    }
 #pragma unroll
                                     for (int d = 0; d < 8; ++d) {
-                                        gv[d] = fmaf(t[d], g[d], gv[d]);
+                                        // dL/dq_dj += l_P_j b_i prod_{e != d} f_e, b_i = |B_i| 2^(-64 sigma(i))
+                                        const float g = kSlow ? fabsf(nb[d]) * r[d] : fabsf(nb[d]);
+                                        gv[d] = fmaf(t[d], g, gv[d]);
                                         const float tqv = t[d] * qv[d];
+                                        const float c = kSlow ? tqv * r[d] : tqv;
                                         const int j = dir_dc(d) + 1;
-                                        if (dir_dr(d) < 0) wu[j] = fmaf(tqv, r[d], wu[j]);
-                                        else if (dir_dr(d) == 0) wm[j] = fmaf(tqv, r[d], wm[j]);
-                                        else wd[j] = fmaf(tqv, r[d], wd[j]);
+                                        if (dir_dr(d) < 0) wu[j] += c;
+                                        else if (dir_dr(d) == 0) wm[j] += c;
+                                        else wd[j] += c;
                                     }
                                 }
                             }

@@ -255,8 +255,8 @@ struct AdjSmem {
     float mua[kARR][kARC], mub[kARR][kARC];  // scaled lambda (mu) at t + 1, then at t
     float sa[kARR][kARC];                    // stored A at t
     float sb[kARR][kARC];                    // b at t in tier 0, 0 in the tiers (their 1 - b q is 1)
-    float sbs[kARR][kARC];                   // b at t in the cell's own adjoint units, b 2^(8 sigma)
-    int ss[kARR][kARC];                      // sigma(t)
+    float sbs[kARR][kARC];                   // b at t in its tier's units, b 2^(64 sigma)
+    int ss[kARR][kARC];                      // sigma(t) (the tier)
     float sc[8][kARR][kARC];                 // contributions of targets, in source units
     float gq[8][kAR][kAC];                   // the item's dL/dq of the interior
     uint8_t sg[kARR][kARC];                  // sigma at t + 1, then at t
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                 const int sg = in ? x_sigma(As, Bs) : kSigmaZero;
                 sm.sa[y][x] = As;
                 sm.sb[y][x] = fmaxf(Bs, 0.0f);
-                sm.sbs[y][x] = fabsf(Bs) * exp2i(8 * (sg & 7));
+                sm.sbs[y][x] = fabsf(Bs);
                 sm.ss[y][x] = sg;
             }
             __syncthreads();
@@ -393,20 +393,20 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                 const float ln = la + lb;
                 const float As = sm.sa[y][x];
                 const int sj = sm.ss[y][x];
-                // 1 - a (1 in the tiers below 2^-64, whose sigma is >= 8)
-                const float ua = signbit(As) ? -As : (sj >= 8 ? 1.0f : 1.0f - As);
+                // 1 - a (1 in the tiers below 2^-64)
+                const float ua = signbit(As) ? -As : (sj >= 1 && sj != kSigmaZero ? 1.0f : 1.0f - As);
                 const float tg = ln * ua;
                 const bool interior = y >= kAH && y < kAH + kAR && x >= kAH && x < kAH + kAC;
 #pragma unroll
                 for (int d = 0; d < 8; ++d) {
                     const int yy = y + dir_dr(d), xx = x + dir_dc(d);
                     const float tt = tg * (pre[d] * suf[d]);
-                    const float r_d = exp2i(8 * (sgp - sm.ss[yy][xx]));
+                    const float r_d = exp2i(64 * (sgp - sm.ss[yy][xx]));
                     sm.sc[d][y][x] = tt * qd[d] * r_d;
                     if (interior)
                         sm.gq[d][y - kAH][x - kAH] = fmaf(tt, sm.sbs[yy][xx] * r_d, sm.gq[d][y - kAH][x - kAH]);
                 }
-                sm.mua[y][x] = fmaf(-ln, P, la) * exp2i(8 * (sgp - sj));  // own cell: in place
+                sm.mua[y][x] = fmaf(-ln, P, la) * exp2i(64 * (sgp - sj));  // own cell: in place
             }
             __syncthreads();
             // sources i: lambda_b at t, and the masks of cells with a = 0
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                 const int sgp = sm.sg[y][x];
                 const int sgt = in ? sm.ss[y][x] : kSigmaZero;
                 float acc = 0.0f;
-                if (sgp != kSigmaZero) acc = J.pc * sm.mub[y][x] * exp2i(8 * (sgp - sgt));
+                if (sgp != kSigmaZero) acc = J.pc * sm.mub[y][x] * exp2i(64 * (sgp - sgt));
 #pragma unroll
                 for (int d = 0; d < 8; ++d) acc += sm.sc[d][y - dir_dr(d)][x - dir_dc(d)];
                 if (sgt == kSigmaZero || sgp == kSigmaZero) {

@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
                                                             float* __restrict__ lam0, uint8_t* __restrict__ sig0,
                                                             float* __restrict__ Gq) {
     __shared__ float sbt[kAY + 4][kAX + 4];         // true b at t (FP32, tiers flushed), rows r0-2 .. r0+kAY+1
-    __shared__ float sbs[kAY + 4][kAX + 4];         // b at t in the cell's own adjoint units, b 2^(8 sigma)
-    __shared__ int ssg[kAY + 4][kAX + 4];           // sigma(t) of the same cells
+    __shared__ float sbs[kAY + 4][kAX + 4];         // b at t in its tier's units, b 2^(64 sigma)
+    __shared__ int ssg[kAY + 4][kAX + 4];           // sigma(t) of the same cells (the tier)
     __shared__ float sc[8][kAY + 2][kAX + 2];       // contributions of targets j, in source units
     const int c0 = blockIdx.x * kAX, r0 = blockIdx.y * kAY;
     const int tid = threadIdx.y * kAX + threadIdx.x;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
             x_decode(As, Bs, A, B, k);
             sg = x_sigma(As, Bs);
             bt = B * tier_scale(k);
-            bs = sg == kSigmaZero ? 0.0f : B * exp2i(8 * sg - 64 * k);
+            bs = B;
         }
         sbt[y][x] = bt;
         sbs[y][x] = bs;
@@ -151,17 +151,17 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
         const float As = __ldg(a + j);
         // 1 - a: 1 for a tiered cell (a < 2^-64)
         const float ua = signbit(As) ? -As : (x_tier(As, __ldg(b + j)) == 0 ? 1.0f - As : 1.0f);
-        const float tg = ln * ua;  // l_P_j in units 2^(8 sigma'(j))
+        const float tg = ln * ua;  // l_P_j in units 2^(64 sigma'(j))
         const bool interior = (y >= 1 && y <= kAY && x >= 1 && x <= kAX);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
             const int yy = y + 1 + dir_dr(d), xx = x + 1 + dir_dc(d);
             const float t = tg * (pre[d] * suf[d]);
-            const float r_d = exp2i(8 * (sgp - ssg[yy][xx]));  // 2^(8 (sigma'(j) - sigma(i)))
+            const float r_d = exp2i(64 * (sgp - ssg[yy][xx]));  // 2^(64 (sigma'(j) - sigma(i)))
             sc[d][y][x] = t * qd[d] * r_d;
             if (interior) Gq[d * plane + j] = fmaf(t, sbs[yy][xx] * r_d, Gq[d * plane + j]);
         }
-        if (interior) lam0[j] = fmaf(-ln, P, la) * exp2i(8 * (sgp - ssg[y + 1][x + 1]));
+        if (interior) lam0[j] = fmaf(-ln, P, la) * exp2i(64 * (sgp - ssg[y + 1][x + 1]));
     }
     __syncthreads();
     const int x = threadIdx.x, y = threadIdx.y;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kAX * kAY) k_adjoint_step(int H, int W, int pi
     const int sgp = __ldg(sig1 + j);
     const int sg = ssg[y + 2][x + 2];
     float acc = 0.0f;
-    if (sgp != kSigmaZero) acc = pc * __ldg(lb1 + j) * exp2i(8 * (sgp - sg));
+    if (sgp != kSigmaZero) acc = pc * __ldg(lb1 + j) * exp2i(64 * (sgp - sg));
 #pragma unroll
     for (int d = 0; d < 8; ++d) acc += sc[d][y + 1 - dir_dr(d)][x + 1 - dir_dc(d)];  // target j = i - offset
     if (sg == kSigmaZero || sgp == kSigmaZero) {  // a == 0 at t: lambda multiplies only zeros
@@ -195,7 +195,7 @@ __global__ void k_adjoint_init(const float* __restrict__ dLda, const float* __re
     if (c < W) {
         sg = x_sigma(ab[j], ab[plane + j]);
         if (sg != kSigmaZero) {
-            const float ui = exp2i(-8 * sg);
+            const float ui = exp2i(-64 * sg);
             if (dLda) la = dLda[(size_t)r * W + c] * ui;
             if (dLdb) lb = dLdb[(size_t)r * W + c] * ui;
         }
