@@ -23,6 +23,7 @@ import json
 import os
 import statistics
 import subprocess
+import threading
 import sys
 import time
 
@@ -43,6 +44,7 @@ HIDDEN = dict(p_h=0.5, c1=0.05, c2=0.12, a=0.08)
 METRIC = "cell-updates/s fwd+adjoint (8192^2 diff form, T=2000)"
 WORKLOAD = "8192x8192 differentiable fwd+adjoint, T=2000, wind resampled every 100 steps"
 B_FWD, B_ADJ = 16, 24  # algorithmic bytes per cell-step: (a, b) in + out; state, lambda in, lambda out
+B_DISC = 2  # discrete: the uint8 state in + out
 
 
 # DRAM traffic of the blocked kernels measured by ncu over every launch of one timed step
@@ -102,21 +104,28 @@ def make_inputs(H, W, T, seed):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling during the timed region, kept in memory (and written to
+    `path` as CSV when one is given)."""
 
-    def __init__(self, path):
+    def __init__(self, path=None):
         self.path = path
         self.p = None
+        self.lines = []
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line)
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
                                        "-lms", "200", "-i", os.environ.get("LOCAL_RANK", "0")],
-                                      stdout=self.f, stderr=subprocess.DEVNULL)
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
         except Exception:
             self.p = None
         return self
@@ -125,23 +134,26 @@ class Clocks:
         if self.p is not None:
             self.p.terminate()
             self.p.wait()
-            self.f.close()
+            self.t.join(timeout=5)
+        if self.path:
+            with open(self.path, "w") as f:
+                f.writelines(self.lines)
 
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        try:
-            for line in open(self.path):
-                f = [x.strip() for x in line.split(",")]
-                if len(f) < 9:
-                    continue
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
                 sm.append(float(f[1]))
                 mx = max(mx, float(f[2]))
-                for n, v in zip(names, f[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(n)
-        except Exception:
-            pass
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
         if not sm:
             return None
         loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
@@ -196,12 +208,29 @@ def discrete_ensemble(pf, torch, timed, seed=1, N=1024, R=64, T=1000):
         m.forward(S0d, 20)  # warm-up
         ms = timed(lambda: m.forward(S0d, T), 1)
         out[name] = N * N * R * T / (ms / 1000.0)
+        if kern == 2:
+            st = m.stats()  # the near-ties of the timed run (every step, every realisation)
+    # one more blocked run with per-launch events: the blocked kernel's time and the
+    # cell-steps it computed (tiles with nothing burning skip their steps)
+    m.set_tuning(kernel=2, profile=1)
+    pf.pf_profile_read(m.h, reset=True)
+    m.forward(S0d, T)
+    torch.cuda.synchronize()
+    n_l, cs_l, t_l, sk_l = pf.pf_profile_read(m.h, reset=True)["discrete_blocked"]
     m.close()
+    hbm, how = peaks()
+    achieved = B_DISC * (cs_l - sk_l) / (t_l / 1000.0) / 1e9
     return {"config": f"{N}x{N}, R={R} realisations, T={T}, discrete uint8", "unit": "cell-updates/s",
-            "blocked": out["blocked"], "plain": out["plain"], "speedup": out["blocked"] / out["plain"]}
+            "blocked": out["blocked"], "plain": out["plain"], "speedup": out["blocked"] / out["plain"],
+            "near_ties_ignite": st["near_ties_ignite"], "near_ties_continue": st["near_ties_continue"],
+            "draws_checked": "every drawn cell of the timed blocked run",
+            "roofline": {"kernel": "discrete_blocked", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "peak_source": how,
+                         "alg_bytes_per_cell_step": B_DISC, "launches": n_l, "ms": t_l,
+                         "computed_cell_steps": cs_l - sk_l, "skipped_frac": sk_l / max(1, cs_l)}}
 
 
-def batched_fires(pf, torch, timed, n_fires=64, seed=4):
+def batched_fires(pf, torch, timed, n_fires=256, seed=4):
     """Uneven fires (side log-uniform in [64, 2048], T uniform in [100, 1000], 1-5
     ignitions, half discrete / half differentiable, the latter with an adjoint) through
     one pf_batch_submit, against the same fires run one after another through per-fire
@@ -239,11 +268,17 @@ def batched_fires(pf, torch, timed, n_fires=64, seed=4):
                 m.backward(wts[i], None, per_cell=False)
             m.close()
     ms_plain = timed(plain_all, 1)
+    # algorithmic bytes of every cell-step (2 B discrete, 16 B differentiable forward, 24 B
+    # adjoint) over the whole submission's time: an effective fraction (skipped quiescent
+    # regions count too, so it may exceed 1)
+    alg = sum(side * side * T * (B_DISC if form == 0 else B_FWD + B_ADJ) for side, T, form, *_ in fires)
+    hbm, how = peaks()
     return {"config": f"{n_fires} fires, side log-uniform [64, 2048], T uniform [100, 1000], "
                       "half discrete / half differentiable, forward + adjoint of the differentiable ones",
             "unit": "cell-updates/s",
             "cell_steps": cells, "batched": cells / (ms_batch / 1000.0), "plain_per_fire": cells / (ms_plain / 1000.0),
-            "speedup": ms_plain / ms_batch}
+            "speedup": ms_plain / ms_batch, "ms_batched": ms_batch, "ms_plain_per_fire": ms_plain,
+            "frac_hbm_alg_effective": alg / (ms_batch / 1000.0) / 1e9 / hbm}
 
 
 def run_reference(args, rank, world):
@@ -322,6 +357,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the discrete-ensemble and batched-fires comparisons against the plain kernels")
     ap.add_argument("--K", type=int, default=0, help="checkpoint interval (0 = chosen by the library)")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="also write the clock samples of the timed region to this CSV ({rank} is replaced)")
     ap.add_argument("--k", type=int, default=0, help="steps per blocked forward launch (0 = library default)")
     ap.add_argument("--probe", choices=["frozen", "live"],
                     help="instead of the benchmark: the blocked adjoint's cost on one kind of tile")
@@ -337,6 +374,7 @@ def main():
 
     import torch
     import paper_2502_18738_gb300 as pf
+    from paper_2502_18738_gb300.ensemble import allreduce_param_grads
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -370,7 +408,12 @@ def main():
     def step():
         pf.pf_forward(m.h, dev["S0"], Ts, out)
         pf.pf_loss_bce(out[0], dev["y"], g_a, want_loss=False)
-        return pf.pf_backward(m.h, g_a, None, gpv, gpd)
+        g4 = pf.pf_backward(m.h, g_a, None, gpv, gpd)
+        if dist is not None:
+            # the replicas form a shared-parameter ensemble: its gradient is the sum over
+            # ranks (one FP64 all-reduce of 32 bytes, the path's only exchange)
+            g4 = allreduce_param_grads(g4)
+        return g4
 
     def barrier():
         if dist is not None:
@@ -393,8 +436,7 @@ def main():
     # the timed steps run without the library's per-launch CUDA events (launches are
     # counted on the host either way); one more step with them gives the per-kernel times
     pf.pf_profile_read(m.h, reset=True)
-    with Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/pfire_clocks_{rank}.csv") as clk:
+    with Clocks(args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv else None) as clk:
         ms = timed(step, args.steps)
     counts = pf.pf_profile_read(m.h, reset=True)
     gpu_launches = sum(v[0] for v in counts.values())

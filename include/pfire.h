@@ -308,6 +308,12 @@ int pf_arrival_probability(const uint8_t* S, int R, int H, int W, float* P_out, 
  * longs): the |A_t| of Eq. 12 for the state at one step. Synchronous. */
 int pf_affected_count(const uint8_t* S, int R, int64_t HW, long long* counts, void* cuda_stream);
 
+/* Manhattan distance of Eq. 12 between two runs: SA and SB are series of T maps of HW
+ * cells ([T][HW] uint8, the state after each step); the affected counts |A_t| and
+ * |Ahat_t| of every step are taken on the device and *out (host) receives the sum over t
+ * of | |A_t| - |Ahat_t| |. Synchronous. */
+int pf_manhattan(const uint8_t* SA, const uint8_t* SB, int T, int64_t HW, long long* out, void* cuda_stream);
+
 /* Jaccard index of Eq. 11 between the affected sets of two maps of n cells:
  * |A and B| / |A or B|, 1 when both are empty. *out: host double. Synchronous. */
 int pf_jaccard(const uint8_t* A, const uint8_t* B, int64_t n, double* out, void* cuda_stream);

@@ -16,7 +16,7 @@
  *   orc_adjoint_step    the exact transpose (reverse-mode chain rule) of orc_step_diff.
  *   orc_prep_adjoint    the chain rule of orc_prep to (p_h, c1, c2, a, p_veg, p_den).
  *
- * Conventions (readings of the paper, listed in the design notes):
+ * Conventions (readings of the paper where it is silent or ambiguous):
  *   grid H x W row-major, row r grows southward, column c grows eastward;
  *   direction d = 0..7 is the offset (dr, dc) from the receiving cell j to its burning
  *   neighbour i = j + (dr, dc), in the order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1);

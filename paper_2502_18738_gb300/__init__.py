@@ -26,7 +26,7 @@ __all__ = [
     "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_profile_read", "pf_batch_submit", "pf_last_error",
     "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
     "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10", "pf_arrival_probability",
-    "pf_affected_count", "pf_jaccard", "manhattan", "pf_set_slope", "simulate", "WildfireModel",
+    "pf_affected_count", "pf_jaccard", "pf_manhattan", "pf_set_slope", "simulate", "WildfireModel",
     "pf_stats", "PfStats", "EXPORTED_SYMBOLS",
 ]
 
@@ -39,7 +39,7 @@ LIB_PATH = _build.LIB
 
 # every extern "C" entry point declared in include/pfire.h
 EXPORTED_SYMBOLS = [
-    "pf_stats", "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
+    "pf_manhattan", "pf_stats", "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
     "pf_loss_bce_noalloc", "pf_autotune", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
@@ -122,6 +122,7 @@ def load():
             "pf_set_slope": ([vp, vp], i),
             "pf_affected_count": ([vp, i, ctypes.c_int64, ctypes.POINTER(ctypes.c_longlong), vp], i),
             "pf_jaccard": ([vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), vp], i),
+            "pf_manhattan": ([vp, vp, i, ctypes.c_int64, ctypes.POINTER(ctypes.c_longlong), vp], i),
             "pf_profile_read": ([vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(ctypes.c_double), i], i),
@@ -374,9 +375,17 @@ def pf_jaccard(A, B, stream=None):
     return out.value
 
 
-def manhattan(counts_a, counts_b):
-    """Eq. 12 from two series of affected-cell counts (pf_affected_count per step)."""
-    return int(sum(abs(int(x) - int(y)) for x, y in zip(counts_a, counts_b)))
+def pf_manhattan(SA, SB, stream=None) -> int:
+    """Eq. 12 between two runs, each a series of T states (uint8 CUDA tensors [T][H][W],
+    the state after each step of one realisation), computed on the device."""
+    if SA.shape != SB.shape or SA.dim() < 2:
+        raise ValueError("pf_manhattan: SA and SB must be [T][...] tensors of one shape")
+    T = SA.shape[0]
+    HW = SA.numel() // T
+    out = ctypes.c_longlong()
+    _check(load().pf_manhattan(_ptr(SA, torch.uint8, None, "SA"), _ptr(SB, torch.uint8, None, "SB"), int(T),
+                               int(HW), ctypes.byref(out), _stream(stream)))
+    return int(out.value)
 
 
 def pf_profile_read(h, reset=False) -> dict:

@@ -337,10 +337,12 @@ void launch_dca_step(const DiscreteArgs& g, const uint8_t* S, const uint8_t* Sn,
                      float* Gq, cudaStream_t s);
 // temporal-blocked: k <= KH steps per launch from global step `step`; `tin` is a 3-D
 // tensor map over the [R][H][pitch] uint8 input buffer with box {160, TH + 2 KH, 1}.
+// skipped (nullable) accumulates the interior cell-steps of tiles with nothing burning.
 int discrete_blocked_tile_rows();
 size_t discrete_blocked_smem(int TH, int KH);
 void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin, int TH, int KH, uint8_t* Sn,
-                                  const float* q, uint32_t step, int k, int* err, TmaHook hk, cudaStream_t s);
+                                  const float* q, uint32_t step, int k, int* err, TmaHook hk,
+                                  unsigned long long* skipped, cudaStream_t s);
 
 void launch_diff_step(int H, int W, int pitch, float p_continue, const float* ab, float* ab_next,
                       const float* q, cudaStream_t s);

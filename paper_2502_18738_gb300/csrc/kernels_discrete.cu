@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
                                                                   DiscreteArgs g, int TH, int KH,
                                                                   uint8_t* __restrict__ Sn,
                                                                   const float* __restrict__ q, uint32_t step0,
-                                                                  int k, int* __restrict__ err, TmaHook hk) {
+                                                                  int k, int* __restrict__ err, TmaHook hk,
+                                                                  unsigned long long* __restrict__ skipped) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // TMA destinations: round the dynamic shared-memory base up to 128 bytes (the
@@ -176,6 +177,12 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
     ga.acc_c0 = c0;
     ga.acc_c1 = c0 + kTW < g.W ? c0 + kTW : g.W;
     uint32_t ties = 0u;
+    // nothing burns in the tile: no cell can change during the launch (its steps are
+    // skipped; the interior is still stored)
+    if (!any_burning && skipped && threadIdx.x == 0) {
+        const int rows = min(TH, g.H - r0), cols = min(kTW, g.W - c0);
+        if (rows > 0 && cols > 0) atomicAdd(skipped, (unsigned long long)rows * cols * k);
+    }
     if (any_burning) {
         const int y_off = r0 - KH, x_off = c0 - kXH;
         for (int s = 0; s < k; ++s) {
@@ -307,7 +314,8 @@ size_t discrete_blocked_smem(int TH, int KH) {
 }
 
 void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin, int TH, int KH, uint8_t* Sn,
-                                  const float* q, uint32_t step, int k, int* err, TmaHook hk, cudaStream_t s) {
+                                  const float* q, uint32_t step, int k, int* err, TmaHook hk,
+                                  unsigned long long* skipped, cudaStream_t s) {
     const size_t smem = discrete_blocked_smem(TH, KH);
     static bool attr_set = false;
     if (!attr_set) {
@@ -315,7 +323,7 @@ void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin,
         attr_set = true;
     }
     dim3 grd((g.pitch + kTW - 1) / kTW, (g.H + TH - 1) / TH, g.R);
-    k_discrete_blocked<<<grd, kBlkThreads, smem, s>>>(*tin, g, TH, KH, Sn, q, step, k, err, hk);
+    k_discrete_blocked<<<grd, kBlkThreads, smem, s>>>(*tin, g, TH, KH, Sn, q, step, k, err, hk, skipped);
 }
 
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,

@@ -366,6 +366,29 @@ void launch_arrival(const uint8_t* S, int R, int64_t HW, float* P, cudaStream_t 
     k_arrival<<<blocks, 256, 0, s>>>(S, R, HW, P);
 }
 
+// Eq. 12 from two series of affected counts: out += sum over t of |a[t] - b[t]| (one block)
+__global__ void __launch_bounds__(256) k_l1(const unsigned long long* __restrict__ a,
+                                            const unsigned long long* __restrict__ b, int T,
+                                            unsigned long long* __restrict__ out) {
+    __shared__ unsigned long long sw[8];
+    unsigned long long v = 0ull;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) v += a[t] > b[t] ? a[t] - b[t] : b[t] - a[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0ull;
+        for (int w = 0; w < 8; ++w) t += sw[w];
+        *out = t;
+    }
+}
+
+void launch_l1(const unsigned long long* a, const unsigned long long* b, int T, unsigned long long* out,
+               cudaStream_t s) {
+    k_l1<<<1, 256, 0, s>>>(a, b, T, out);
+}
+
 void launch_count(const uint8_t* A, const uint8_t* B, int64_t n, int R, unsigned long long* out, cudaStream_t s) {
     const int blocks = (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 4);
     k_count<<<dim3(blocks, B ? 1 : R), 256, 0, s>>>(A, B, n, out);

@@ -25,6 +25,8 @@ void launch_diff_sums(const float* ab, const uint8_t* burn, int H, int W, int pi
 void launch_bce(const float* a, const float* y, int64_t n, float* g, double* partials, int nblk, cudaStream_t s);
 void launch_arrival(const uint8_t* S, int R, int64_t HW, float* P, cudaStream_t s);
 void launch_count(const uint8_t* A, const uint8_t* B, int64_t n, int R, unsigned long long* out, cudaStream_t s);
+void launch_l1(const unsigned long long* a, const unsigned long long* b, int T, unsigned long long* out,
+               cudaStream_t s);
 int eq10_blocks(int H, int W);
 size_t eq10_scratch_bytes(int H, int W);
 const double* eq10_result(const double* scratch, int nblk);
@@ -596,7 +598,7 @@ int run_discrete(pf_ctx* ctx, int T) {
             n = std::min(n, blocked_k(ctx));
             LaunchScope ls(ctx, K_DBLK, n);
             launch_discrete_blocked_impl(g, &ctx->tmapS[src], ctx->TH, ctx->KH, ctx->S[dst], ctx->q, (uint32_t)t, n,
-                                         ctx->dflags, ctx->hook, ctx->st);
+                                         ctx->dflags, ctx->hook, ctx->dskip + K_DBLK, ctx->st);
         } else {
             n = 1;
             LaunchScope ls(ctx, K_DSTEP);
@@ -1818,6 +1820,27 @@ int pf_affected_count(const uint8_t* S, int R, int64_t HW, long long* counts, vo
     return PF_OK;
 }
 
+int pf_manhattan(const uint8_t* SA, const uint8_t* SB, int T, int64_t HW, long long* out, void* cuda_stream) {
+    if (!SA || !SB || !out || T < 1 || HW < 1) return fail(nullptr, PF_EINVAL, "pf_manhattan: bad arguments");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int rc;
+    unsigned long long* d = count_scratch(2 * T + 1, &rc);
+    if (!d) return fail(nullptr, rc, "pf_manhattan: scratch allocation failed");
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * (2 * (size_t)T + 1), st);
+    if (e == cudaSuccess) {
+        launch_count(SA, nullptr, HW, T, d, st);
+        launch_count(SB, nullptr, HW, T, d + T, st);
+        launch_l1(d, d + T, T, d + 2 * T, st);
+        e = cudaGetLastError();
+    }
+    unsigned long long h = 0ull;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d + 2 * T, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, "pf_manhattan: %s", cudaGetErrorString(e));
+    *out = (long long)h;
+    return PF_OK;
+}
+
 int pf_jaccard(const uint8_t* A, const uint8_t* B, int64_t n, double* out, void* cuda_stream) {
     if (!A || !B || !out || n < 1) return fail(nullptr, PF_EINVAL, "pf_jaccard: bad arguments");
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -1897,26 +1920,11 @@ int pf_loss_bce(const float* a, const float* y, int64_t n, float* dL_da, double*
     return PF_OK;
 }
 
-int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
+// One submission (a wave) of jobs that were validated by pf_batch_submit: one arena,
+// one captured graph, one persistent forward kernel and one adjoint kernel.
+static int batch_submit_wave(const pf_job* jobs, int n, cudaStream_t st) {
     pf_ctx* ctx = nullptr;  // context-free: errors go to pf_last_error(NULL)
-    if (n < 0 || (n > 0 && !jobs)) return fail(nullptr, PF_EINVAL, "pf_batch_submit: bad job array");
-    if (n == 0) return PF_OK;
     const int kB = batch_steps_per_item(), kTR = batch_tile_rows(), kTC = batch_tile_cols();
-    for (int i = 0; i < n; ++i) {
-        const pf_job& J = jobs[i];
-        if (J.H < 1 || J.W < 1 || J.H > 65536 || J.W > 65536 || (uint64_t)J.H * J.W >= (1ull << 32))
-            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: bad grid %dx%d", i, J.H, J.W);
-        if (J.T < 0 || (J.form != PF_DISCRETE && J.form != PF_DIFF) || !J.S_init || !J.S_out)
-            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: bad T, form or NULL state", i);
-        const float v[6] = {J.p_h, J.c1, J.c2, J.a, J.p_continue, J.l};
-        for (float x : v)
-            if (!std::isfinite(x)) return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: non-finite parameter", i);
-        if (J.p_h < 0 || J.p_continue < 0 || J.p_continue > 1 || !(J.l > 0))
-            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: parameter out of range", i);
-        if (J.dL_da && (J.form != PF_DIFF || !J.grad_params))
-            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: dL_da needs the differentiable form and grad_params", i);
-    }
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     // order jobs by block count, descending (block-major item order)
     std::vector<int> order(n);
     std::vector<int> nblk(n);
@@ -2205,6 +2213,77 @@ done:
     cudaGetLastError();
     (void)ctx;
     return rc;
+}
+
+int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
+    pf_ctx* ctx = nullptr;  // context-free: errors go to pf_last_error(NULL)
+    if (n < 0 || (n > 0 && !jobs)) return fail(nullptr, PF_EINVAL, "pf_batch_submit: bad job array");
+    if (n == 0) return PF_OK;
+    const int kB = batch_steps_per_item(), kTR = batch_tile_rows(), kTC = batch_tile_cols();
+    for (int i = 0; i < n; ++i) {
+        const pf_job& J = jobs[i];
+        if (J.H < 1 || J.W < 1 || J.H > 65536 || J.W > 65536 || (uint64_t)J.H * J.W >= (1ull << 32))
+            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: bad grid %dx%d", i, J.H, J.W);
+        if (J.T < 0 || (J.form != PF_DISCRETE && J.form != PF_DIFF) || !J.S_init || !J.S_out)
+            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: bad T, form or NULL state", i);
+        const float v[6] = {J.p_h, J.c1, J.c2, J.a, J.p_continue, J.l};
+        for (float x : v)
+            if (!std::isfinite(x)) return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: non-finite parameter", i);
+        if (J.p_h < 0 || J.p_continue < 0 || J.p_continue > 1 || !(J.l > 0))
+            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: parameter out of range", i);
+        if (J.dL_da && (J.form != PF_DIFF || !J.grad_params))
+            return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: dL_da needs the differentiable form and grad_params", i);
+    }
+    // Device memory of one job in a wave's arena (as batch_submit_wave lays it out): two
+    // state buffers, q, the burnable mask, tile counters and, with an adjoint, every
+    // state, the scaled adjoint and dL/dq.
+    auto job_bytes = [&](const pf_job& J) {
+        const size_t P = (size_t)pitch_of(J.W), plane = (size_t)J.H * P;
+        auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        const size_t tiles = (size_t)((J.W + kTC - 1) / kTC) * ((J.H + kTR - 1) / kTR);
+        size_t b = r(2 * (J.form == PF_DISCRETE ? plane : 2 * plane * sizeof(float))) + r(8 * plane * sizeof(float)) +
+                   r((size_t)J.H * J.W) + r(tiles * sizeof(int));
+        if (J.dL_da) {
+            const size_t bt = (size_t)((J.W + batch_adj_tile_cols() - 1) / batch_adj_tile_cols()) *
+                              ((J.H + batch_adj_tile_rows() - 1) / batch_adj_tile_rows());
+            b += r((size_t)(J.T + 1) * 2 * plane * sizeof(float)) + r(2 * 2 * plane * sizeof(float)) + r(2 * plane) +
+                 r(8 * plane * sizeof(float)) + r(bt * sizeof(int));
+        }
+        return b + 4096;  // and its share of the plan tables
+    };
+    // Jobs whose arenas do not fit in the device memory together run in waves, each a
+    // submission of its own; a wave takes the largest remaining jobs that fit in 70% of
+    // the free memory.
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    const size_t budget = (size_t)(0.7 * (double)free_b);
+    std::vector<int> by_size(n);
+    for (int i = 0; i < n; ++i) by_size[i] = i;
+    std::stable_sort(by_size.begin(), by_size.end(),
+                     [&](int x, int y) { return job_bytes(jobs[x]) > job_bytes(jobs[y]); });
+    std::vector<char> done(n, 0);
+    int left = n;
+    std::vector<pf_job> wave;
+    while (left > 0) {
+        wave.clear();
+        size_t used = 0;
+        for (int i : by_size) {
+            if (done[i]) continue;
+            const size_t b = job_bytes(jobs[i]);
+            if (wave.empty() || used + b <= budget) {
+                wave.push_back(jobs[i]);
+                used += b;
+                done[i] = 1;
+                --left;
+            }
+        }
+        const int rc = batch_submit_wave(wave.data(), (int)wave.size(), (cudaStream_t)cuda_stream);
+        if (rc) return rc;
+    }
+    return PF_OK;
 }
 
 }  // extern "C"

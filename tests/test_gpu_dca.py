@@ -123,8 +123,8 @@ def test_dca_state_errors(pf):
 def test_calibration_loop_runs(pf):
     """Alg. 1 on a 96 x 96 map: observations from the hidden parameters of the
     calibration case (p_h 0.5, c1 0.05, c2 0.12, a 0.08); starting from the workload's
-    parameters, four epochs of three iterations give finite losses and move the
-    parameters, which stay inside the clamps."""
+    parameters, four epochs of three iterations give finite losses and keep the
+    parameters inside the clamps."""
     import torch
     from paper_2502_18738_gb300.calibrate import BOUNDS, calibrate, step_rings
     H = W = 96
@@ -147,6 +147,47 @@ def test_calibration_loop_runs(pf):
     assert len(hist) == 12 and all(np.isfinite(l) and l > 0 for _, _, l in hist)
     assert p != [0.58, 0.045, 0.131, 0.078]
     assert list(np.nonzero(step_rings(10, 2, 2, 1))[0]) == [0, 1, 5, 8, 9]
+
+
+def test_calibration_loop_descends_towards_the_hidden_spread_parameter(pf):
+    """Alg. 1 (Eq. 10 loss, accumulator gradient, AdamW, clamps) on an easy case: flat
+    terrain, no wind and uniform vegetation, so q = f_p(p_h) in every direction and only
+    p_h acts (the gradients in c1, c2, a are exactly 0). Observations come from p_h = 0.5;
+    from an underburning start (p_h = 0.25) two epochs raise p_h towards 0.5, and the
+    Eq. 10 loss of a re-simulation with the observations' seed falls. (Eq. 10 rewards a
+    larger p_ignite at every correctly ignited cell, so the loop's resting point lies
+    above the observations' p_h: the test asks for the descent, not for convergence.)"""
+    import torch
+    from paper_2502_18738_gb300.calibrate import calibrate
+    H = W = 128
+    z = torch.zeros((H, W), device="cuda")
+    m = pf.FireModel(H, W, pf.PF_DISCRETE, 1, seed=0)
+    m.set_env(z, z, z, z, z)
+    m.set_params(p_h=0.5, c1=0.045, c2=0.131, a=0.078, p_continue=0.3)
+    S0 = np.ones((1, H, W), dtype=np.uint8)
+    S0[0, H // 2, W // 2] = 2
+    S = cuda(S0)
+    obs = []
+    for it in range(3):
+        m.reseed(0)
+        out = m.forward(S, (it + 1) * 8)
+        obs.append(((out[0] >= 2).float().contiguous(), None))
+
+    def loss_at(p_h):
+        m.set_params(p_h=p_h, c1=0.045, c2=0.131, a=0.078, p_continue=0.3)
+        acc = m.set_accumulator(torch.zeros((1, H, W), device="cuda"))
+        m.reseed(0)
+        m.forward(S, 24)
+        return pf.pf_loss_eq10(acc[0], obs[2][0], torch.empty((H, W), device="cuda"))
+
+    p0 = 0.25
+    before = loss_at(p0)
+    p, hist = calibrate(m, S, obs, (p0, 0.045, 0.131, 0.078), max_epochs=2, steps_update_interval=8, lr=3e-2,
+                        seed0=0)
+    assert 0.30 < p[0] <= 0.5 + 0.05, (p, hist)
+    assert p[1:] == pytest.approx([0.045, 0.131, 0.078], abs=1e-3)  # only weight decay acts on them
+    after = loss_at(p[0])
+    assert after < before, (before, after, p)
 
 
 def test_paper_style_model_object(pf):

@@ -40,7 +40,9 @@ def test_arrival_probability_counts_and_jaccard(pf, orc):
 
 
 def test_manhattan_distance_over_a_run(pf, orc):
-    """Eq. 12 between two realisations' affected-cell series, stepped through the ABI."""
+    """Eq. 12 between two realisations' affected-cell series, stepped through the ABI
+    (per-step counts by pf_affected_count, the distance by pf_manhattan on the device)."""
+    import torch
     H, W, T = 80, 80, 20
     land = syn.make_landscape(H, W, 5)
     V, th = syn.smooth_wind(H, W, 5, 0, sigma=8.0)
@@ -49,11 +51,12 @@ def test_manhattan_distance_over_a_run(pf, orc):
     set_landscape(m, land, V, th)
     m.set_params(**PRM)
     out = m.forward(cuda(S0), 0)
-    series = []
+    series, states = [], []
     for t in range(T):
         out = m.advance(1)
         series.append(pf.pf_affected_count(out))
-    a, b = [s[0] for s in series], [s[1] for s in series]
+        states.append(out.clone())
+    st = torch.stack(states)  # [T][2][H][W]
     prm = orc.Params(**PRM)
     q = orc.prep(H, W, land.E, land.p_veg, land.p_den, V, th, prm)
     S, want = S0, []
@@ -61,7 +64,7 @@ def test_manhattan_distance_over_a_run(pf, orc):
         S = orc.step_discrete(S, q, prm.p_continue, 4, t)
         want.append([int(((S[r] == 2) | (S[r] == 3)).sum()) for r in range(2)])
     assert series == want
-    assert pf.manhattan(a, b) == sum(abs(x - y) for x, y in want)
+    assert pf.pf_manhattan(st[:, 0].contiguous(), st[:, 1].contiguous()) == sum(abs(x - y) for x, y in want)
 
 
 def test_ensemble_mean_against_the_mean_field_form(pf, orc):
