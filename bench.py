@@ -37,6 +37,8 @@ import synthetic as syn  # noqa: E402
 H = W = 8192
 T = 2000
 EPOCH_STEPS = 100
+T_PROBE = 400   # forward steps of the autotuner's launch search
+PREP_T = 500    # forward steps of the prep-variant comparison
 FIELD_SEED = 5
 PHILOX_SEED = 5
 PARAMS = dict(p_h=0.58, c1=0.045, c2=0.131, a=0.078, p_continue=0.3, l=30.0)
@@ -190,6 +192,18 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
+def prep_variants(pf, m, S0, out, timed, T):
+    """Forward ms of T steps with q materialised per wind epoch (prep 1) or recomputed
+    inside the step kernels (prep 2), for the plain kernel and the blocked one at k = 4, 8."""
+    res = {}
+    for kernel, k in ((1, 1), (2, 4), (2, 8)):
+        for prep in (1, 2):
+            pf.pf_set_tuning(m.h, kernel=kernel, k=k, prep=prep)
+            pf.pf_forward(m.h, S0, T, out)  # warm-up
+            res[f"kernel{kernel}_k{k}_prep{prep}"] = timed(lambda: pf.pf_forward(m.h, S0, T, out), 1)
+    return res
+
+
 def discrete_ensemble(pf, torch, timed, seed=1, N=1024, R=64, T=1000):
     """The discrete forward ensemble (N^2 grid, R realisations in one context, smooth
     per-cell wind, T steps): temporal-blocked kernel against the plain per-step kernel
@@ -256,6 +270,7 @@ def batched_fires(pf, torch, timed, n_fires=256, seed=4):
                         dL_da=wts[i], **PARAMS)[0] for i, (side, T, form, E, pv, pd, V, th, S0) in enumerate(dev)]
     pf.pf_batch_submit(jobs)  # warm-up
     ms_batch = timed(lambda: pf.pf_batch_submit(jobs), 1)
+    bst = pf.pf_batch_last_stats()
 
     def plain_all():
         for i, (side, T, form, E, pv, pd, V, th, S0) in enumerate(dev):
@@ -268,6 +283,17 @@ def batched_fires(pf, torch, timed, n_fires=256, seed=4):
                 m.backward(wts[i], None, per_cell=False)
             m.close()
     ms_plain = timed(plain_all, 1)
+
+    def blocked_all():  # the same with the library's default (temporal-blocked) kernels
+        for i, (side, T, form, E, pv, pd, V, th, S0) in enumerate(dev):
+            m = pf.FireModel(side, side, form, 1, seed=seed)
+            m.set_env(E, pv, pd, V, th)
+            m.set_params(**PARAMS)
+            m.forward(S0, T)
+            if form == 1:
+                m.backward(wts[i], None, per_cell=False)
+            m.close()
+    ms_blocked = timed(blocked_all, 1)
     # algorithmic bytes of every cell-step (2 B discrete, 16 B differentiable forward, 24 B
     # adjoint) over the whole submission's time: an effective fraction (skipped quiescent
     # regions count too, so it may exceed 1)
@@ -278,7 +304,25 @@ def batched_fires(pf, torch, timed, n_fires=256, seed=4):
             "unit": "cell-updates/s",
             "cell_steps": cells, "batched": cells / (ms_batch / 1000.0), "plain_per_fire": cells / (ms_plain / 1000.0),
             "speedup": ms_plain / ms_batch, "ms_batched": ms_batch, "ms_plain_per_fire": ms_plain,
-            "frac_hbm_alg_effective": alg / (ms_batch / 1000.0) / 1e9 / hbm}
+            "blocked_per_fire": cells / (ms_blocked / 1000.0), "ms_blocked_per_fire": ms_blocked,
+            "frac_hbm_alg_effective": alg / (ms_batch / 1000.0) / 1e9 / hbm,
+            "kernels": bst, "roofline": batch_roofline(bst, hbm, how)}
+
+
+def batch_roofline(bst, hbm, how):
+    """Roofline of the batch's two persistent kernels on the cell-steps they computed
+    (items with nothing to do are skipped and not counted): 2 B per discrete and 16 B per
+    differentiable forward cell-step over the forward kernel's time, 24 B per adjoint
+    cell-step over the adjoint kernel's; the dominant one (more device time) first."""
+    out = []
+    for kernel, b, ms in (("k_batch", B_DISC * bst["disc_cell_steps"] + B_FWD * bst["diff_cell_steps"],
+                           bst["ms_forward"]),
+                          ("k_batch_adj", B_ADJ * bst["adj_cell_steps"], bst["ms_adjoint"])):
+        ach = b / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
+        out.append({"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "peak_source": how, "ms": ms, "alg_bytes": b})
+    out.sort(key=lambda r: -r["ms"])
+    return out
 
 
 def run_reference(args, rank, world):
@@ -360,6 +404,11 @@ def main():
     ap.add_argument("--clocks-csv", default=None,
                     help="also write the clock samples of the timed region to this CSV ({rank} is replaced)")
     ap.add_argument("--k", type=int, default=0, help="steps per blocked forward launch (0 = library default)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (launch search and checkpoint-interval search)")
+    ap.add_argument("--only", choices=["discrete", "batch"],
+                    help="instead of the benchmark: only the discrete ensemble or the batched fires")
+    ap.add_argument("--fires", type=int, default=256, help="fires of the batched workload (with --only batch)")
     ap.add_argument("--probe", choices=["frozen", "live"],
                     help="instead of the benchmark: the blocked adjoint's cost on one kind of tile")
     args = ap.parse_args()
@@ -370,6 +419,25 @@ def main():
         return run_reference(args, rank, world)
     if args.probe:
         print(json.dumps(adjoint_probe(args.probe)), flush=True)
+        return 0
+    if args.only:
+        # one secondary workload alone (for profiling it): no workload line is printed
+        import torch
+        import paper_2502_18738_gb300 as pf
+        pf.build()
+
+        def timed1(fn, n):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(n):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / n
+        res = (discrete_ensemble(pf, torch, timed1, T=args.T if args.T != T else 1000) if args.only == "discrete"
+               else batched_fires(pf, torch, timed1, n_fires=args.fires))
+        print(json.dumps({"only": args.only, **res}), flush=True)
         return 0
 
     import torch
@@ -399,7 +467,21 @@ def main():
 
     m = pf.FireModel(Hs, Ws, pf.PF_DIFF, seed=PHILOX_SEED + rank)
     setup(m)
-    pf.pf_set_tuning(m.h, K=args.K, k=args.k)
+    # the autotuner picks the launch configuration (kernel, k, materialised or recomputed
+    # q) on a forward probe and then the checkpoint interval on forward + adjoint of the
+    # workload itself; its answers are cached on disk, keyed by GPU, grid and T
+    base = dict(K=args.K, k=args.k)
+    tuning = {"source": "fixed by --k / --K" if (args.k or args.K) else "library defaults (--no-tune)"}
+    if not args.no_tune and args.k == 0 and args.K == 0:
+        t0 = time.time()
+        chosen = m.autotune(dev["S0"], T_PROBE)
+        t1 = time.time()
+        Kc = m.autotune_ckpt(dev["S0"], Ts)
+        t2 = time.time()
+        base = dict(kernel=chosen["kernel"], k=chosen["k"], prep=chosen["prep"], tile_rows=chosen["tile_rows"], K=Kc)
+        tuning = {"source": "pf_autotune + pf_autotune_ckpt", "T_probe": T_PROBE, "launch_search_s": t1 - t0,
+                  "ckpt_search_s": t2 - t1, "chosen": dict(base)}
+    pf.pf_set_tuning(m.h, **base)
     g_a = torch.empty((Hs, Ws), dtype=torch.float32, device="cuda")
     gpv = torch.empty_like(g_a)
     gpd = torch.empty_like(g_a)
@@ -440,11 +522,11 @@ def main():
         ms = timed(step, args.steps)
     counts = pf.pf_profile_read(m.h, reset=True)
     gpu_launches = sum(v[0] for v in counts.values())
-    pf.pf_set_tuning(m.h, K=args.K, k=args.k, profile=1)
+    pf.pf_set_tuning(m.h, **base, profile=1)
     step()
     torch.cuda.synchronize()
     prof = pf.pf_profile_read(m.h, reset=True)  # one profiled step
-    pf.pf_set_tuning(m.h, K=args.K, k=args.k, profile=0)
+    pf.pf_set_tuning(m.h, **base)
     tun = pf.pf_get_tuning(m.h)
     cells = Hs * Ws * Ts
     value = cells * world / (ms / 1000.0)
@@ -453,9 +535,9 @@ def main():
     # plain one-launch-per-step comparator (forward)
     ms_fwd_plain = None
     if not args.no_plain:
-        pf.pf_set_tuning(m.h, kernel=1, K=tun["K"], k=args.k)
+        pf.pf_set_tuning(m.h, **{**base, "kernel": 1, "prep": 1, "K": tun["K"]})
         ms_fwd_plain = timed(lambda: pf.pf_forward(m.h, dev["S0"], Ts, out), 1)
-        pf.pf_set_tuning(m.h, kernel=0, K=args.K, k=args.k)
+        pf.pf_set_tuning(m.h, **base)
 
     # roofline of the dominant kernel (largest share of device time in the timed region):
     # algorithmic bytes = per-cell-step bytes x the cell-steps its launches processed
@@ -547,14 +629,32 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
         del stage, host
 
+    extras = {}
+    if not args.no_extras:
+        extras["prep_variants"] = {f"{Hs}x{Ws}": prep_variants(pf, m, dev["S0"], out, timed, PREP_T)}
+        pf.pf_set_tuning(m.h, **base)
+
     # the comparisons below need their own memory (the batch's adjoint keeps every state
     # of its differentiable fires): release the workload's model and buffers first
     m.close()
     del dev, out, g_a, gpv, gpd
     torch.cuda.empty_cache()
 
-    extras = {}
     if not args.no_extras:
+        land_s, winds_s, S0_s, _ = make_inputs(1024, 1024, PREP_T, FIELD_SEED + 7 + rank)
+        ms_ = pf.FireModel(1024, 1024, pf.PF_DIFF, seed=PHILOX_SEED + rank)
+        ms_.set_env(c(land_s.E), c(land_s.p_veg), c(land_s.p_den), *[c(x) for x in winds_s[0]])
+        keep = [(c(V), c(th)) for V, th in winds_s[1:]]
+        for e, (V, th) in enumerate(keep, start=1):
+            ms_.set_wind(V, th, e * EPOCH_STEPS)
+        ms_.set_params(**PARAMS)
+        out_s = torch.empty((2, 1024, 1024), dtype=torch.float32, device="cuda")
+        extras["prep_variants"]["1024x1024"] = prep_variants(pf, ms_, c(S0_s), out_s, timed, PREP_T)
+        ms_.close()
+        del keep, out_s
+        extras["prep_variants"]["note"] = (f"forward only, T={PREP_T} from the workload's ignition, ms per "
+                                           "forward; prep 1 = q materialised per wind epoch (its prep "
+                                           "launches included), 2 = q recomputed inside the step kernels")
         extras["discrete_ensemble"] = discrete_ensemble(pf, torch, timed)
         extras["batched_fires"] = batched_fires(pf, torch, timed)
 
@@ -570,7 +670,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD if (Hs == H and Ts == T) else f"{Hs}x{Ws} diff fwd+adjoint T={Ts}",
                            "H": Hs, "W": Ws, "T": Ts, "wind_epochs": len(winds),
-                           "checkpoint_K": tun["K"], "kernel": tun["kernel"], "k": tun["k"],
+                           "checkpoint_K": tun["K"], "kernel": tun["kernel"], "k": tun["k"], "prep": tun["prep"],
+                           "tuning": tuning,
                            "l2": "inputs larger than L2 (state 0.5 GB, q 2.1 GB per epoch)"},
                 "fwd": {"value": cells * world / (ms_fwd / 1000.0), "unit": "cell-updates/s", "ms": ms_fwd,
                         "frac_hbm_alg_effective": B_FWD * cells / (ms_fwd / 1000.0) / 1e9 / hbm},

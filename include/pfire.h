@@ -216,16 +216,28 @@ int pf_loss_bce(const float* a, const float* y, int64_t n, float* dL_da, double*
 int pf_loss_bce_noalloc(const float* a, const float* y, int64_t n, float* dL_da, double* loss, void* cuda_stream);
 
 /* Kernel selection and checkpoint interval. Zero fields mean "choose automatically".
- *   kernel  1 = plain one-launch-per-step kernels, 2 = temporal-blocked TMA kernels.
- *   k       steps per launch of the temporal-blocked kernels (1..16).
- *   K       checkpoint interval of the differentiable form (>= 1; 1 keeps every state).
- *   profile 1 = time every kernel launch with CUDA events on the context's stream
- *           (read with pf_profile_read). */
+ *   kernel    1 = plain one-launch-per-step kernels, 2 = temporal-blocked TMA kernels.
+ *   k         steps per launch of the temporal-blocked kernels (1..16; the differentiable
+ *             kernels take at most 8, the discrete one at most 12).
+ *   K         checkpoint interval of the differentiable form (>= 1; 1 keeps every state).
+ *   profile   1 = time every kernel launch with CUDA events on the context's stream
+ *             (read with pf_profile_read).
+ *   prep      where the forward's ignition factors q (Eq. 1-5) come from: 1 = materialised
+ *             once per wind epoch into eight FP32 planes that the step kernels read, 2 =
+ *             recomputed inside the step kernels from the fields (the same arithmetic:
+ *             results are identical). The adjoint always materialises q. 0 = 1.
+ *   tile_rows interior rows per tile of the discrete blocked kernel (16, 32, 64 or 128; 0
+ *             = 64); its halo is k rows (16 when k = 0). Ignored by the differentiable
+ *             form, whose 64 x 64 regions take a 4-cell halo for k <= 4, else 8.
+ * Results do not depend on any of these (the same arithmetic in every variant), except
+ * through K's effect on memory. PF_EINVAL for values out of range. */
 typedef struct pf_tuning {
     int kernel;
     int k;
     int K;
     int profile;
+    int prep;
+    int tile_rows;
 } pf_tuning;
 
 int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t);
@@ -234,14 +246,30 @@ int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t);
 /* Autotuner (no counterpart in the paper, which has one PyTorch code path). Times, on
  * this context's grid, fields and parameters, a forward of T_probe steps from S_init
  * (device, uint8 [R][H][W] as for pf_forward) with each candidate launch configuration:
- * the plain per-step kernels and the temporal-blocked kernels at several depths k (for
- * the differentiable form k <= 4 also selects the 4-cell-halo tile geometry). Keeps
- * the fastest as the context's kernel and k (the checkpoint interval K stays chosen by
- * memory), and writes the resulting tuning to *chosen (nullable, host). Results do not
- * depend on the choice: the kernels compute the same arithmetic. The probe runs leave
- * no tape: call pf_forward before pf_backward. Synchronous. PF_EINVAL for NULL
- * arguments, T_probe < 1 or invalid state codes. */
+ * q materialised or recomputed (prep 1 / 2), each with the plain per-step kernels and
+ * the temporal-blocked kernels at several depths k (differentiable: k in {2, 4, 6, 8};
+ * discrete: k in {4, 8, 12} x tile_rows in {32, 64, 128}). Keeps the fastest as the
+ * context's tuning (K and profile are left as they were) and writes the resulting
+ * tuning to *chosen (nullable, host). The probe runs leave no tape: call pf_forward
+ * before pf_backward.
+ * On-disk cache: the choice is appended to a text file, one line per key (GPU model,
+ * compute capability and SM count; form, H, W, R, T_probe), and a later call with the
+ * same key applies the cached choice without timing. The file is $PF_TUNE_CACHE, else
+ * $XDG_CACHE_HOME/pfire/tuning.tsv, else $HOME/.cache/pfire/tuning.tsv; PF_TUNE_CACHE
+ * set to "" or "off" disables it. A file that cannot be read or written is skipped.
+ * Synchronous. PF_EINVAL for NULL arguments, T_probe < 1 or invalid state codes. */
 int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chosen);
+
+/* Checkpoint-interval search of the differentiable form (PF_DIFF only, else PF_ESTATE).
+ * Times pf_forward of T steps from S_init plus pf_backward (zero loss gradients) for
+ * the memory rule of pf_tuning.K = 0 and for intervals that are multiples of the
+ * blocked kernels' k around the one it picks (launches are then never cut short at a
+ * checkpoint), with the context's other tuning; keeps the fastest as pf_tuning.K (0 =
+ * the memory rule) and writes it to *K_chosen (nullable, host). Uses the same on-disk
+ * cache as pf_autotune (key: form, H, W, R, T). The probe runs leave no tape.
+ * Synchronous; a candidate that does not fit in memory ends the search with PF_ENOMEM
+ * and the tuning unchanged. */
+int pf_autotune_ckpt(pf_ctx* ctx, const uint8_t* S_init, int T, int* K_chosen);
 
 /* Per-kernel-kind launch counts, cell-steps processed (cells x automaton steps the
  * launches advanced or reversed), the part of those cell-steps the temporal-blocked
@@ -352,6 +380,24 @@ typedef struct pf_job {
  * Synchronous. PF_ETIMEOUT if a bounded device-side wait ran out, PF_ENOMEM if the
  * states of the differentiable jobs with an adjoint do not fit. */
 int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream);
+
+/* Work and device time of this thread's last pf_batch_submit, summed over the waves it
+ * ran in (jobs are grouped into waves that fit in free memory). Cell-steps count each
+ * job's interior cells times the steps of the work items that computed them; the
+ * skipped ones are those of items whose region had nothing burning (discrete), b = 0
+ * (differentiable forward) or a = 0 (adjoint), which change nothing and are not
+ * computed. ms_forward / ms_adjoint: device time of the persistent forward / adjoint
+ * kernels (CUDA events in the submission's graph); ms_kernels_from_start: from the
+ * start of the graph to the end of the last of them (initial states, prep, both
+ * kernels). The paper has no counterpart: reporting for the batch's roofline. */
+typedef struct pf_batch_stats_t {
+    long long disc_cell_steps, disc_skipped;
+    long long diff_cell_steps, diff_skipped;
+    long long adj_cell_steps, adj_skipped;
+    double ms_forward, ms_adjoint, ms_kernels_from_start;
+    int waves;
+} pf_batch_stats_t;
+int pf_batch_last_stats(pf_batch_stats_t* out);
 
 /* Message of the last failure on ctx (or of the last context-free call when ctx is
  * NULL). Never NULL; valid until the next call on the same context. */

@@ -23,7 +23,7 @@ __all__ = [
     "PFireError", "build", "load", "PF_DISCRETE", "PF_DIFF",
     "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_wind_async", "pf_wait", "pf_set_params",
     "pf_forward", "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
-    "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_profile_read", "pf_batch_submit", "pf_last_error",
+    "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_profile_read", "pf_batch_submit", "pf_last_error",
     "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
     "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10", "pf_arrival_probability",
     "pf_affected_count", "pf_jaccard", "pf_manhattan", "pf_set_slope", "simulate", "WildfireModel",
@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = [
     "pf_manhattan", "pf_stats", "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
-    "pf_loss_bce_noalloc", "pf_autotune", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
+    "pf_loss_bce_noalloc", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
     "pf_arrival_probability", "pf_affected_count", "pf_jaccard", "pf_set_slope", "pf_set_wind_async", "pf_wait",
 ]
 PF_NOALLOC_BCE_MAX_N = 67108864
@@ -55,12 +55,24 @@ class PFireError(RuntimeError):
 
 
 class PfTuning(ctypes.Structure):
-    _fields_ = [("kernel", ctypes.c_int), ("k", ctypes.c_int), ("K", ctypes.c_int), ("profile", ctypes.c_int)]
+    _fields_ = [("kernel", ctypes.c_int), ("k", ctypes.c_int), ("K", ctypes.c_int), ("profile", ctypes.c_int),
+                ("prep", ctypes.c_int), ("tile_rows", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class PfStats(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int), ("cells", ctypes.c_double * 4), ("near_ties_ignite", ctypes.c_longlong),
                 ("near_ties_continue", ctypes.c_longlong)]
+
+
+class PfBatchStats(ctypes.Structure):
+    _fields_ = [("disc_cell_steps", ctypes.c_longlong), ("disc_skipped", ctypes.c_longlong),
+                ("diff_cell_steps", ctypes.c_longlong), ("diff_skipped", ctypes.c_longlong),
+                ("adj_cell_steps", ctypes.c_longlong), ("adj_skipped", ctypes.c_longlong),
+                ("ms_forward", ctypes.c_double), ("ms_adjoint", ctypes.c_double),
+                ("ms_kernels_from_start", ctypes.c_double), ("waves", ctypes.c_int)]
 
 
 class PfJob(ctypes.Structure):
@@ -114,6 +126,8 @@ def load():
             "pf_set_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_get_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_autotune": ([vp, vp, i, ctypes.POINTER(PfTuning)], i),
+            "pf_autotune_ckpt": ([vp, vp, i, ctypes.POINTER(ctypes.c_int)], i),
+            "pf_batch_last_stats": ([ctypes.POINTER(PfBatchStats)], i),
             "pf_set_accumulator": ([vp, vp], i),
             "pf_reseed": ([vp, ctypes.c_uint64], i),
             "pf_backward_dca": ([vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp], i),
@@ -296,15 +310,18 @@ def pf_loss_bce_noalloc(a, y, dL_da=None, want_loss=True, stream=None):
     return loss.value if want_loss else None
 
 
-def pf_set_tuning(h, kernel=0, k=0, K=0, profile=0):
-    t = PfTuning(kernel, k, K, profile)
+def pf_set_tuning(h, kernel=0, k=0, K=0, profile=0, prep=0, tile_rows=0):
+    """kernel 1 plain / 2 blocked, k steps per blocked launch, K checkpoint interval,
+    profile, prep 1 materialised q / 2 q recomputed in the step kernels, tile_rows of the
+    discrete blocked kernel; 0 = automatic."""
+    t = PfTuning(kernel, k, K, profile, prep, tile_rows)
     _check(load().pf_set_tuning(h, ctypes.byref(t)), h)
 
 
 def pf_get_tuning(h) -> dict:
     t = PfTuning()
     _check(load().pf_get_tuning(h, ctypes.byref(t)), h)
-    return dict(kernel=t.kernel, k=t.k, K=t.K, profile=t.profile)
+    return t.as_dict()
 
 
 def pf_autotune(h, S_init, T_probe) -> dict:
@@ -312,7 +329,15 @@ def pf_autotune(h, S_init, T_probe) -> dict:
     and keep the fastest; returns the resulting tuning."""
     t = PfTuning()
     _check(load().pf_autotune(h, _ptr(S_init, torch.uint8, None, "S_init"), int(T_probe), ctypes.byref(t)), h)
-    return dict(kernel=t.kernel, k=t.k, K=t.K, profile=t.profile)
+    return t.as_dict()
+
+
+def pf_autotune_ckpt(h, S_init, T) -> int:
+    """Time forward + adjoint of T steps for the candidate checkpoint intervals and keep
+    the fastest (0 = the memory rule); returns it."""
+    K = ctypes.c_int(0)
+    _check(load().pf_autotune_ckpt(h, _ptr(S_init, torch.uint8, None, "S_init"), int(T), ctypes.byref(K)), h)
+    return K.value
 
 
 def pf_set_accumulator(h, acc):
@@ -440,6 +465,13 @@ def pf_batch_submit(jobs, stream=None):
     _check(load().pf_batch_submit(arr, len(jobs), _stream(stream)))
 
 
+def pf_batch_last_stats() -> dict:
+    """Cell-steps computed / skipped and device ms of this thread's last pf_batch_submit."""
+    st = PfBatchStats()
+    _check(load().pf_batch_last_stats(ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
 # ------------------------------------------------------------- conveniences
 
 class FireModel:
@@ -482,6 +514,9 @@ class FireModel:
 
     def autotune(self, S_init, T_probe=64):
         return pf_autotune(self.h, S_init, T_probe)
+
+    def autotune_ckpt(self, S_init, T):
+        return pf_autotune_ckpt(self.h, S_init, T)
 
     def set_accumulator(self, acc=None):
         """Attach (or, with None, detach) an FP32 [R][H][W] accumulator tensor; returns it."""

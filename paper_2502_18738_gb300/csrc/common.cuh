@@ -339,13 +339,20 @@ void launch_dca_step(const DiscreteArgs& g, const uint8_t* S, const uint8_t* Sn,
 // tensor map over the [R][H][pitch] uint8 input buffer with box {160, TH + 2 KH, 1}.
 // skipped (nullable) accumulates the interior cell-steps of tiles with nothing burning.
 int discrete_blocked_tile_rows();
+int discrete_blocked_max_k();  // steps per launch the column halo supports
 size_t discrete_blocked_smem(int TH, int KH);
+// pa: NULL = q read from q; else q recomputed in the kernel from pa's fields (q unused)
 void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin, int TH, int KH, uint8_t* Sn,
-                                  const float* q, uint32_t step, int k, int* err, TmaHook hk,
+                                  const float* q, const PrepArgs* pa, uint32_t step, int k, int* err, TmaHook hk,
                                   unsigned long long* skipped, cudaStream_t s);
 
 void launch_diff_step(int H, int W, int pitch, float p_continue, const float* ab, float* ab_next,
                       const float* q, cudaStream_t s);
+// the same steps with q recomputed in the kernel from the fields of PrepArgs (prep's
+// arithmetic) instead of read from materialised planes
+void launch_diff_step_rc(const PrepArgs& g, float p_continue, const float* ab, float* ab_next, cudaStream_t s);
+void launch_discrete_step_rc(const DiscreteArgs& g, const uint8_t* S, uint8_t* Sn, const PrepArgs& pa, uint32_t step,
+                             cudaStream_t s);
 // temporal-blocked differentiable forward: n <= diff_blocked_halo() steps per launch.
 // tab: 3-D map over the input (A, b) buffer (pitch, H, 2), box {64, 64, 2};
 // tq: 3-D map over q (pitch, H, 8), box {64, 64, 8}. out (nullable) receives the state
@@ -381,13 +388,17 @@ void launch_fwd_act_seed(int halo, const uint8_t* seed, int H, int pitch, uint8_
 // slot0 (the segment's first state, slot 0 of the buffer) as well, those with b = 0 in
 // the 7 x 7 interiors and no change since slot 0 in the 5 x 5 write nothing (kStale; see
 // k_fwd_tiles).
+// out_dirty (nullable, with out a checkpoint slot): per tile of this geometry, whether the
+// slot's interior may hold nonzeros; all-zero tiles (a = 0) are written only where it is
+// set (all tiles if dirty_unknown), and it is updated to the state written.
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
                       int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, const float* slot0,
-                      float* zero_base,
-                      int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s);
-void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
-                         int n, const int* tile_list, int* tile_count, float* out, float* all_out,
+                      float* zero_base, int zero_slots, bool frozen, uint8_t* out_dirty, bool dirty_unknown,
+                      unsigned long long* skipped, cudaStream_t s);
+// pa: NULL = q staged from the planes of tq; else q recomputed in the kernel from pa's fields
+void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, const PrepArgs* pa, int H, int W,
+                         int pitch, float pc, int n, const int* tile_list, int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
                          TmaHook hk, cudaStream_t s);
 // lam: scaled adjoint (mu_a, mu_b) [2][H][pitch]; sig: its exponents uint8 [H][pitch]
@@ -499,7 +510,11 @@ struct BatchPlan {
     int* err;
     long long wait_limit_ns;  // bound on one wait for a neighbouring tile
     int withhold;
+    // nullable: interior cell-steps of the items that were stepped / skipped (nothing
+    // burning, or a = 0 for the adjoint, in the item's region), indexed by BatchStat
+    unsigned long long* stats;
 };
+enum BatchStat { kStatDisc, kStatDiscSkip, kStatDiff, kStatDiffSkip, kStatAdj, kStatAdjSkip, kStatCount };
 int batch_tile_rows();
 int batch_tile_cols();
 int batch_steps_per_item();

@@ -418,16 +418,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                             // l_P_j in units 2^(64 sigma'(j)); on the single-tier path already in
                             // the sources' units
                             const float tg = xin ? (kSlow ? ln * ua : (ln * ua) * Up) : 0.0f;
-                            bool quiet = true;  // no neighbour burning (behind or ahead of the front)
+                            // no neighbour with b in tier 0 (b = 0, or a tiered b below 2^-64,
+                            // stored negative): every factor 1 - b_i q_dj is exactly 1
+                            bool quiet = true;
 #pragma unroll
-                            for (int d = 0; d < 8; ++d) quiet &= nb[d] == 0.0f;
+                            for (int d = 0; d < 8; ++d) quiet &= nb[d] <= 0.0f;
                             if (quiet) {
-                                // P = 0, every leave-one-out product is 1 and every dL/dq term
-                                // carries b_i = 0: only the contributions t_d q_dj = tg q_dj remain
+                                // P = 0 and every leave-one-out product is exactly 1, so t_d = tg:
+                                // the general arithmetic below with its factors folded (the same
+                                // bits); the dL/dq terms carry the tiered b_i (0 for b_i = 0)
                                 la[k] *= scl[k];
                                 {  // tg = 0 (edge columns; cells burned out to a = 1 exactly) adds zeros
 #pragma unroll
                                     for (int d = 0; d < 8; ++d) {
+                                        const float g = kSlow ? fabsf(nb[d]) * r[d] : fabsf(nb[d]);
+                                        gv[d] = fmaf(tg, g, gv[d]);
                                         const float tqv = tg * qv[d];
                                         const float c = kSlow ? tqv * r[d] : tqv;
                                         const int j = dir_dc(d) + 1;

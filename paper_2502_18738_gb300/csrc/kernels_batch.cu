@@ -128,6 +128,11 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
             }
             // nothing burns in the region: no cell can change during the item's steps
             const int nsteps = __syncthreads_or(burning) ? steps : 0;
+            if (tid == 0 && plan.stats) {
+                const unsigned long long ic =
+                    (unsigned long long)(min(kTR, J.H - ty * kTR) * min(kTC, J.W - tx * kTC)) * (unsigned long long)steps;
+                atomicAdd(plan.stats + (nsteps ? kStatDisc : kStatDiscSkip), ic);
+            }
             int cur = 0;
             for (int s = 0; s < nsteps; ++s) {
                 for (int i = tid; i < (kRR - 2) * (kRC - 2); i += kBThreads) {
@@ -175,6 +180,11 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
             }
             // b = 0 in the whole region: every P is 0, the state does not change
             const bool live = __syncthreads_or(burning);
+            if (tid == 0 && plan.stats) {
+                const unsigned long long ic =
+                    (unsigned long long)(min(kTR, J.H - ty * kTR) * min(kTC, J.W - tx * kTC)) * (unsigned long long)steps;
+                atomicAdd(plan.stats + (live ? kStatDiff : kStatDiffSkip), ic);
+            }
             int cur = 0;
             for (int s = 0; s < steps; ++s) {
                 if (live) {
@@ -319,7 +329,13 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                         any |= __float_as_uint(__ldcg(st + (size_t)gr * J.P + gc)) != 0u;
                 }
             }
-            if (!__syncthreads_or(any)) {
+            const bool live_item = __syncthreads_or(any);
+            if (tid == 0 && plan.stats) {
+                const unsigned long long ic = (unsigned long long)(min(kAR, J.H - ty * kAR) * min(kAC, J.W - tx * kAC)) *
+                                              (unsigned long long)max(0, t1 - t0);
+                atomicAdd(plan.stats + (live_item ? kStatAdj : kStatAdjSkip), ic);
+            }
+            if (!live_item) {
                 float* lo = J.lam[b & 1];
                 uint8_t* so = J.sig[b & 1];
                 for (int i = tid; i < kAR * kAC; i += kAThreads) {

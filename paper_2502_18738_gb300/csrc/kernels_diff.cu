@@ -7,6 +7,7 @@
 // FP32, and the survival product S = prod_d (1 - x_d) alongside it, so that
 // 1 - a' = (1 - a) S is formed without cancellation.
 #include "common.cuh"
+#include "prep_math.cuh"
 
 namespace pf {
 
@@ -36,6 +37,40 @@ __global__ void __launch_bounds__(256) k_diff_step(int H, int W, int pitch, floa
         nb[d] = in ? Bi : 0.0f;
         qv[d] = __ldg(q + d * plane + j);
     }
+    float A, B, An, Bn;
+    int k, kn;
+    x_decode(ab[j], ab[plane + j], A, B, k);
+    x_update(nb, nk, qv, A, B, k, pc, An, Bn, kn);
+    x_encode(An, Bn, kn, abn[j], abn[plane + j]);
+}
+
+// The same step with q recomputed from the fields in every cell and step (prep's
+// arithmetic, q_cell) instead of read from the materialised planes: the same bits.
+__global__ void __launch_bounds__(256) k_diff_step_rc(PrepArgs g, float pc, const float* __restrict__ ab,
+                                                      float* __restrict__ abn) {
+    const int H = g.H, W = g.W, pitch = g.pitch;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (r >= H || c >= pitch) return;
+    const size_t plane = (size_t)H * pitch;
+    const size_t j = (size_t)r * pitch + c;
+    if (c >= W) {
+        abn[j] = 0.0f;
+        abn[plane + j] = 0.0f;
+        return;
+    }
+    float nb[8], qv[8];
+    int nk[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int ri = r + dir_dr(d), ci = c + dir_dc(d);
+        const bool in = ri >= 0 && ri < H && ci >= 0 && ci < W;
+        const size_t i = in ? (size_t)ri * pitch + ci : j;
+        float Ai, Bi;
+        x_decode(__ldg(ab + i), __ldg(ab + plane + i), Ai, Bi, nk[d]);
+        nb[d] = in ? Bi : 0.0f;
+    }
+    q_cell(g, r, c, qv);
     float A, B, An, Bn;
     int k, kn;
     x_decode(ab[j], ab[plane + j], A, B, k);
@@ -212,6 +247,12 @@ void launch_diff_step(int H, int W, int pitch, float pc, const float* ab, float*
     dim3 blk(64, 4);
     dim3 grd((pitch + 63) / 64, (H + 3) / 4);
     k_diff_step<<<grd, blk, 0, s>>>(H, W, pitch, pc, ab, abn, q);
+}
+
+void launch_diff_step_rc(const PrepArgs& g, float pc, const float* ab, float* abn, cudaStream_t s) {
+    dim3 blk(64, 4);
+    dim3 grd((g.pitch + 63) / 64, (g.H + 3) / 4);
+    k_diff_step_rc<<<grd, blk, 0, s>>>(g, pc, ab, abn);
 }
 
 void launch_ignition_map_diff(int H, int W, int pitch, const float* ab, const float* q, float* P, cudaStream_t s) {

@@ -13,6 +13,7 @@
 #include <cuda.h>
 
 #include "common.cuh"
+#include "prep_math.cuh"
 #include "tma.cuh"
 
 namespace pf {
@@ -46,9 +47,12 @@ __device__ __forceinline__ void tile_origin(int tile, int tiles_x, int& r0, int&
     c0 = tx * kIC - kHalo;
 }
 
-template <int kHalo>
+// kRc: q recomputed from the fields of pa (prep's arithmetic, q_cell) for every live
+// tile instead of staged from the materialised planes by TMA; the same bits either way.
+template <int kHalo, bool kRc>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_diff_blocked(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap tq, int H, int pitch,
+    k_diff_blocked(const __grid_constant__ CUtensorMap tab, const __grid_constant__ CUtensorMap tq,
+                   const __grid_constant__ PrepArgs pa, int H, int pitch,
                    int W, float pc, int n, int tiles_x, const int* __restrict__ tiles,
                    const int* __restrict__ ntiles_live, int* __restrict__ work, float* __restrict__ out,
                    float* __restrict__ all_out,
@@ -64,7 +68,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int x = tid % kCT;             // region column
     const int strip = tid / kCT;
     const int ys = strip * kM;           // first region row of the strip
-    const uint32_t bytes = (uint32_t)((8 + 2) * kPlane * sizeof(float));
+    const uint32_t bytes = (uint32_t)(((kRc ? 0 : 8) + 2) * kPlane * sizeof(float));
     const size_t gplane = (size_t)H * pitch;
 
     const int ntiles = *ntiles_live;  // tiles listed by k_fwd_tiles
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tile_origin<kHalo>(tiles[li], tiles_x, r0, c0);
         mbar_arrive_expect_tx(&bar, bytes);
         if (!hk.withhold) {
-            tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
+            if (!kRc) tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
             tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
         }
     }
@@ -104,8 +108,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int m = 0; m < kM; ++m) {
             const int y = ys + m;
+            if (!kRc)
 #pragma unroll
-            for (int d = 0; d < 8; ++d) q[m][d] = sm.q[d * kPlane + y * kCT + x];
+                for (int d = 0; d < 8; ++d) q[m][d] = sm.q[d * kPlane + y * kCT + x];
             float bv;
             int kv;
             x_decode(sm.st[y * kCT + x], sm.st[kPlane + y * kCT + x], A[m], bv, kv);
@@ -130,12 +135,28 @@ __global__ void __launch_bounds__(kThreads, 1)
             tile_origin<kHalo>(tiles[next], tiles_x, r0, c0);
             mbar_arrive_expect_tx(&bar, bytes);
             if (!hk.withhold) {
-                tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
+                if (!kRc) tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
                 tma_load_3d(sm.st, &tab, &bar, c0, r0, 0);
             }
         }
         int r0, c0;
         tile_origin<kHalo>(tile, tiles_x, r0, c0);
+        if (kRc && live) {
+            // q of this thread's cells (0 outside the grid, as the TMA fill and the zero
+            // padding columns give), through this thread's own slots of sm.q, which no
+            // copy writes in this variant
+            for (int m = 0; m < kM; ++m) {
+                const int y = ys + m, gr = r0 + y, gc = c0 + x;
+                float qv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                if (gr >= 0 && gr < H && gc >= 0 && gc < W) q_cell(pa, gr, gc, qv);
+#pragma unroll
+                for (int d = 0; d < 8; ++d) sm.q[d * kPlane + y * kCT + x] = qv[d];
+            }
+#pragma unroll
+            for (int m = 0; m < kM; ++m)
+#pragma unroll
+                for (int d = 0; d < 8; ++d) q[m][d] = sm.q[d * kPlane + (ys + m) * kCT + x];
+        }
         const bool xin = (x >= 1 && x < kCT - 1);
         if (!live && tid == 0 && skipped)
             atomicAdd(skipped, (unsigned long long)(min(kRT - 2 * kHalo, H - (r0 + kHalo)) *
@@ -410,6 +431,7 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
                                                    float* __restrict__ all_out, size_t all_stride,
                                                    uint8_t* __restrict__ seg_dirty, const float* __restrict__ slot0,
                                                    float* __restrict__ zero_base, int zero_slots, int frozen,
+                                                   uint8_t* __restrict__ out_dirty, int dirty_unknown,
                                                    unsigned long long* __restrict__ skipped, int tile, int lane,
                                                    unsigned long long& sk) {
     constexpr int kI = kRT - 2 * kHalo;
@@ -441,6 +463,7 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
             list[atomicAdd(count, 1)] = tile;
             qrun[tile] = 0;
             if (seg_dirty) seg_dirty[tile] = 1;
+            if (out_dirty) out_dirty[tile] = 1;
             act_out[tile] = qb;  // k_diff_blocked adds the tile's activity
         }
         return;
@@ -476,7 +499,24 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     // a tile that skipped its last write takes its state from slot 0
     const float* src = (frozen && slot0 && (me & kStale)) ? slot0 : in;
     const int qr = qrun[tile];
-    const bool copy_out = out && !(out_age > 0 && qr >= out_age);
+    bool copy_out = out && !(out_age > 0 && qr >= out_age);
+    // a checkpoint slot with dirty bits (out_dirty): an all-zero tile (a = 0 in the
+    // interior, so b = 0 too) is written only if the slot's tile may hold nonzeros
+    bool zero_out = false;
+    if (copy_out && out_dirty && !(me & kActA)) {
+        zero_out = dirty_unknown || out_dirty[tile];
+        copy_out = false;
+    }
+    if (zero_out) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = lane; i < kI * (kI / 4); i += 32) {
+            const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
+            if (gr >= H || gc >= pitch) continue;
+            const size_t j = (size_t)gr * pitch + gc;
+            *reinterpret_cast<float4*>(out + j) = z;
+            *reinterpret_cast<float4*>(out + gplane + j) = z;
+        }
+    }
     if (copy_out || write_all) {
         // float4 columns: c0 and pitch are multiples of 4
         for (int i = lane; i < kI * (kI / 4); i += 32) {
@@ -499,6 +539,7 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     }
     __syncwarp();  // qrun[tile] read by every lane before it changes
     if (lane == 0) {
+        if (out_dirty && out) out_dirty[tile] = (me & kActA) ? 1 : 0;
         act_out[tile] = (uint8_t)((me & (kActA | kQt)) | qb | (frozen ? kFrozen : 0) | (stale ? kStale : 0));
         qrun[tile] = (uint8_t)min(qr + 1, 255);
         sk = (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)n;
@@ -514,6 +555,7 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                                                    float* __restrict__ all_out, size_t all_stride,
                                                    uint8_t* __restrict__ seg_dirty, const float* __restrict__ slot0,
                                                    float* __restrict__ zero_base, int zero_slots, int frozen,
+                                                   uint8_t* __restrict__ out_dirty, int dirty_unknown,
                                                    unsigned long long* __restrict__ skipped) {
     __shared__ unsigned long long s_sk;
     if (threadIdx.x == 0) s_sk = 0ull;
@@ -522,8 +564,8 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
     if (tile < tiles_x * tiles_y)
         fwd_tile<kHalo>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out, qrun, list, count, out,
-                        out_age, all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots, frozen, skipped, tile,
-                        threadIdx.x & 31, sk);
+                        out_age, all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots, frozen, out_dirty,
+                        dirty_unknown, skipped, tile, threadIdx.x & 31, sk);
     block_count(skipped, s_sk, sk);
 }
 
@@ -538,9 +580,13 @@ size_t diff_blocked_smem() { return sizeof(Smem) + 128; }
 int diff_blocked_configure() {
     static int done = 0;
     if (!done) {
-        if (cudaFuncSetAttribute(k_diff_blocked<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_diff_blocked<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)diff_blocked_smem()) != cudaSuccess ||
-            cudaFuncSetAttribute(k_diff_blocked<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_diff_blocked<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)diff_blocked_smem()) != cudaSuccess ||
+            cudaFuncSetAttribute(k_diff_blocked<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)diff_blocked_smem()) != cudaSuccess ||
+            cudaFuncSetAttribute(k_diff_blocked<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)diff_blocked_smem()) != cudaSuccess)
             return -1;
         done = 1;
@@ -574,7 +620,8 @@ void launch_fwd_act_seed(int halo, const uint8_t* seed, int H, int pitch, uint8_
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
                       int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, const float* slot0,
-                      float* zero_base, int zero_slots, bool frozen, unsigned long long* skipped, cudaStream_t s) {
+                      float* zero_base, int zero_slots, bool frozen, uint8_t* out_dirty, bool dirty_unknown,
+                      unsigned long long* skipped, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int tiles_y = (H + inner - 1) / inner;
@@ -583,30 +630,33 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
         k_fwd_tiles<4><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          qrun, tile_list, tile_count, out, out_age,
                                                          all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots,
-                                                         frozen ? 1 : 0, skipped);
+                                                         frozen ? 1 : 0, out_dirty, dirty_unknown ? 1 : 0, skipped);
     else
         k_fwd_tiles<8><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          qrun, tile_list, tile_count, out, out_age,
                                                          all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots,
-                                                         frozen ? 1 : 0, skipped);
+                                                         frozen ? 1 : 0, out_dirty, dirty_unknown ? 1 : 0, skipped);
 }
 
-void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, int H, int W, int pitch, float pc,
-                         int n, const int* tile_list, int* tile_count, float* out, float* all_out,
+void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, const PrepArgs* pa, int H, int W,
+                         int pitch, float pc, int n, const int* tile_list, int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
                          TmaHook hk, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int ntiles = diff_blocked_tiles(halo, H, pitch);
     const int grid = ntiles < nsm ? ntiles : nsm;
-    if (halo == 4)
-        k_diff_blocked<4><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, tile_list,
-                                                                      tile_count, tile_count + 1, out, all_out,
-                                                                      all_stride, act_out, skipped, err, hk);
-    else
-        k_diff_blocked<8><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, H, pitch, W, pc, n, tiles_x, tile_list,
-                                                                      tile_count, tile_count + 1, out, all_out,
-                                                                      all_stride, act_out, skipped, err, hk);
+    const PrepArgs g = pa ? *pa : PrepArgs{};
+#define PF_DIFF_BLOCKED(HALO, RC)                                                                                   \
+    k_diff_blocked<HALO, RC><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, g, H, pitch, W, pc, n, tiles_x, \
+                                                                          tile_list, tile_count, tile_count + 1, out, \
+                                                                          all_out, all_stride, act_out, skipped, err, hk)
+    if (halo == 4) {
+        if (pa) PF_DIFF_BLOCKED(4, true); else PF_DIFF_BLOCKED(4, false);
+    } else {
+        if (pa) PF_DIFF_BLOCKED(8, true); else PF_DIFF_BLOCKED(8, false);
+    }
+#undef PF_DIFF_BLOCKED
 }
 
 }  // namespace pf

@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "tma.cuh"
+#include "prep_math.cuh"
 
 namespace pf {
 
@@ -26,7 +27,7 @@ __device__ __forceinline__ uint64_t row_burning(uint32_t left, uint32_t mid, uin
 __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64_t C, uint64_t D, int r,
                                                 int col0, size_t qoff, size_t qplane, const float* __restrict__ q,
                                                 const DiscreteArgs& g, uint32_t run, uint32_t step, int rr,
-                                                uint32_t& ties) {
+                                                uint32_t& ties, const PrepArgs* pa = nullptr) {
     const uint64_t all3 = U | C | D;
     const uint64_t nb64 = (all3 << 8) | (all3 >> 8) | U | D;  // neighbours of byte positions 1..4
     const uint32_t nb = (uint32_t)(nb64 >> 8) & 0x01010101u;
@@ -42,13 +43,16 @@ __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64
         const uint32_t cell = (uint32_t)r * (uint32_t)g.W + (uint32_t)col;
         uint32_t ns;
         if (s == 1u) {
-            // Eq. 9 over the burning neighbours, as P <- P + x (1 - P)
+            // Eq. 9 over the burning neighbours, as P <- P + x (1 - P); q read from the
+            // materialised planes, or (pa) recomputed from the fields with prep's arithmetic
+            float qv[8];
+            if (pa) q_cell(*pa, r, col, qv);
             float P = 0.0f;
 #pragma unroll
             for (int d = 0; d < 8; ++d) {
                 const uint64_t row = dir_dr(d) < 0 ? U : (dir_dr(d) == 0 ? C : D);
                 if ((row >> (8 * (k + 1 + dir_dc(d)))) & 1ull) {
-                    const float x = __ldg(q + (size_t)d * qplane + qoff + k);
+                    const float x = pa ? qv[d] : __ldg(q + (size_t)d * qplane + qoff + k);
                     P = fmaf(x, 1.0f - P, P);
                 }
             }
@@ -83,9 +87,11 @@ __device__ __forceinline__ void flush_ties(const DiscreteArgs& g, uint32_t ties)
     }
 }
 
+// rc: q recomputed from the fields (prep's arithmetic) instead of read from q
+template <bool rc>
 __global__ void __launch_bounds__(256) k_discrete_step(DiscreteArgs g, const uint8_t* __restrict__ S,
                                                        uint8_t* __restrict__ Sn, const float* __restrict__ q,
-                                                       uint32_t step) {
+                                                       uint32_t step, const __grid_constant__ PrepArgs pa) {
     const int wpr = g.pitch >> 2;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t total = (size_t)g.R * g.H * wpr;
@@ -104,7 +110,8 @@ __global__ void __launch_bounds__(256) k_discrete_step(DiscreteArgs g, const uin
         const uint64_t C = row_burning(ld(r, w - 1), mid, ld(r, w + 1));
         const uint64_t D = row_burning(ld(r + 1, w - 1), ld(r + 1, w), ld(r + 1, w + 1));
         const uint32_t out = update_word(mid, U, C, D, r, 4 * w, (size_t)r * g.pitch + 4 * w,
-                                         (size_t)g.H * g.pitch, q, g, g.run0 + (uint32_t)rr, step, rr, ties);
+                                         (size_t)g.H * g.pitch, q, g, g.run0 + (uint32_t)rr, step, rr, ties,
+                                         rc ? &pa : nullptr);
         reinterpret_cast<uint32_t*>(Sn + (size_t)rr * g.H * g.pitch)[(size_t)r * wpr + w] = out;
     }
     flush_ties(g, ties);  // every lane of the warp, converged
@@ -119,7 +126,10 @@ constexpr int kCT = kTW + 2 * kXH;  // 160 bytes per tile row
 constexpr int kCW = kCT / 4;        // 40 words per tile row
 constexpr int kBlkThreads = 256;
 
+// kRc: q recomputed from the fields of pa (prep's arithmetic) instead of read from q
+template <bool kRc>
 __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_constant__ CUtensorMap tin,
+                                                                  const __grid_constant__ PrepArgs pa,
                                                                   DiscreteArgs g, int TH, int KH,
                                                                   uint8_t* __restrict__ Sn,
                                                                   const float* __restrict__ q, uint32_t step0,
@@ -208,7 +218,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
                 // cell is active; the q offset is formed but only read for such cells
                 const size_t qoff = (size_t)gr * g.pitch + gc;
                 dst[y * kCW + m] = update_word(mid, U, C, D, gr, gc, qoff, qplane, q, ga, g.run0 + (uint32_t)rr, step,
-                                               rr, ties);
+                                               rr, ties, kRc ? &pa : nullptr);
             }
             __syncthreads();
             uint32_t* t = src; src = dst; dst = t;
@@ -297,7 +307,14 @@ void launch_discrete_step(const DiscreteArgs& g, const uint8_t* S, uint8_t* Sn, 
                           cudaStream_t s) {
     const size_t total = (size_t)g.R * g.H * (g.pitch >> 2);
     const unsigned blocks = (unsigned)((total + 255) / 256);
-    k_discrete_step<<<blocks, 256, 0, s>>>(g, S, Sn, q, step);
+    k_discrete_step<false><<<blocks, 256, 0, s>>>(g, S, Sn, q, step, PrepArgs{});
+}
+
+void launch_discrete_step_rc(const DiscreteArgs& g, const uint8_t* S, uint8_t* Sn, const PrepArgs& pa, uint32_t step,
+                             cudaStream_t s) {
+    const size_t total = (size_t)g.R * g.H * (g.pitch >> 2);
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    k_discrete_step<true><<<blocks, 256, 0, s>>>(g, S, Sn, nullptr, step, pa);
 }
 
 void launch_dca_step(const DiscreteArgs& g, const uint8_t* S, const uint8_t* Sn, const float* q, const float* w,
@@ -307,6 +324,10 @@ void launch_dca_step(const DiscreteArgs& g, const uint8_t* S, const uint8_t* Sn,
 }
 
 int discrete_blocked_tile_rows() { return 64; }
+// The first and last 4-byte words of a staged row are never updated (their outer
+// neighbour word is not staged), so the kXH-byte column halo supports kXH - 3 steps per
+// launch; a multiple of 4 below that.
+int discrete_blocked_max_k() { return kXH - 4; }
 
 size_t discrete_blocked_smem(int TH, int KH) {
     const int tile_bytes = (TH + 2 * KH) * kCT;
@@ -314,16 +335,22 @@ size_t discrete_blocked_smem(int TH, int KH) {
 }
 
 void launch_discrete_blocked_impl(const DiscreteArgs& g, const CUtensorMap* tin, int TH, int KH, uint8_t* Sn,
-                                  const float* q, uint32_t step, int k, int* err, TmaHook hk,
+                                  const float* q, const PrepArgs* pa, uint32_t step, int k, int* err, TmaHook hk,
                                   unsigned long long* skipped, cudaStream_t s) {
     const size_t smem = discrete_blocked_smem(TH, KH);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_discrete_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_discrete_blocked<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        cudaFuncSetAttribute(k_discrete_blocked<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
         attr_set = true;
     }
     dim3 grd((g.pitch + kTW - 1) / kTW, (g.H + TH - 1) / TH, g.R);
-    k_discrete_blocked<<<grd, kBlkThreads, smem, s>>>(*tin, g, TH, KH, Sn, q, step, k, err, hk, skipped);
+    if (pa)
+        k_discrete_blocked<true><<<grd, kBlkThreads, smem, s>>>(*tin, *pa, g, TH, KH, Sn, nullptr, step, k, err, hk,
+                                                                skipped);
+    else
+        k_discrete_blocked<false><<<grd, kBlkThreads, smem, s>>>(*tin, PrepArgs{}, g, TH, KH, Sn, q, step, k, err, hk,
+                                                                 skipped);
 }
 
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,

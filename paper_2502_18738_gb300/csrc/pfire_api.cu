@@ -1,12 +1,16 @@
 // libpfire C ABI: context, buffers, wind epochs, checkpointed reverse sweep, dispatch.
 #include <cudaTypedefs.h>
+#include <sys/stat.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -42,13 +46,13 @@ thread_local std::string g_last_error = "no error";
 
 enum Kind {
     K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_ATILES, K_FTILES, K_DCA,
-    K_NKINDS
+    K_STILES, K_NKINDS
 };
 const char* kKindNames[K_NKINDS] = {"prep",         "discrete_step",    "discrete_blocked",
                                     "diff_step",    "diff_blocked",     "adjoint_step",
                                     "adjoint_blocked", "prep_adjoint",  "reduce_fp64",
                                     "misc",         "adjoint_tiles",    "diff_tiles",
-                                    "dca_step"};
+                                    "dca_step",     "segment_tiles"};
 
 struct Epoch {
     int from;
@@ -175,6 +179,11 @@ struct pf_ctx {
     uint8_t* ckact = nullptr;
     int ckact_cap = 0;
     std::vector<int> ckact_halo;
+    // per arena slot and forward tile: whether the slot's tile may hold nonzeros, valid
+    // for the tile geometry (halo) ckdirty_halo[slot] (0: unknown, every tile is written)
+    uint8_t* ckdirty = nullptr;
+    int ckdirty_cap = 0;
+    std::vector<int> ckdirty_halo;
     int fl_in_at[2] = {-1, -1};         // launch whose input work[x] last was (-1: none)
     int fl_par = 0;
     int fl_halo = 0;
@@ -197,7 +206,7 @@ struct pf_ctx {
     const float* seg_slot0 = nullptr;  // the segment's first state (its checkpoint; slot 0 of seg_buf is unused)
     int seg_halo = 0;              // tile geometry seg_dirty refers to
     int TH = 64, KH = 16;
-    pf_tuning tun{0, 0, 0, 0};
+    pf_tuning tun{0, 0, 0, 0, 0, 0};
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
     long long launches[K_NKINDS] = {0};
@@ -262,7 +271,7 @@ struct LaunchScope {
     LaunchScope(pf_ctx* c_, int k, int steps = 1) : c(c_), kind(k) {
         c->launches[k] += 1;
         if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED && k != K_ATILES && k != K_FTILES &&
-            k != K_DCA)
+            k != K_DCA && k != K_STILES)
             c->cell_steps[k] += (long long)steps * c->H * c->W * (k == K_DSTEP || k == K_DBLK ? c->R : 1);
         if (!c->tun.profile) return;
         cudaEvent_t e0 = take();
@@ -491,7 +500,7 @@ int choose_kernel(const pf_ctx* c) {
 
 int blocked_k(const pf_ctx* c) {
     int k = c->tun.k > 0 ? c->tun.k : 8;
-    return std::min(k, c->form == PF_DISCRETE ? c->KH : diff_blocked_halo());
+    return std::min(k, c->form == PF_DISCRETE ? std::min(c->KH, discrete_blocked_max_k()) : diff_blocked_halo());
 }
 
 // One launch of the blocked diff kernel from `in`; out / all_out as in launch_diff_blocked.
@@ -519,8 +528,24 @@ int actrec_push(pf_ctx* ctx, int end_step) {
     return PF_OK;
 }
 
+// Dirty bits of arena slot s for tile geometry `halo` (allocated on first use).
+uint8_t* ckpt_dirty_bits(pf_ctx* ctx, int s, int* rc) {
+    const size_t nt = (size_t)std::max(diff_blocked_tiles(8, ctx->H, ctx->P), diff_blocked_tiles(4, ctx->H, ctx->P));
+    *rc = PF_OK;
+    if (ctx->ckdirty_cap < ctx->arena_cap) {
+        void* p;
+        if ((*rc = dalloc(ctx, &p, nt * (size_t)ctx->arena_cap))) return nullptr;
+        if (ctx->ckdirty) dfree(ctx, ctx->ckdirty);
+        ctx->ckdirty = (uint8_t*)p;
+        ctx->ckdirty_cap = ctx->arena_cap;
+        std::fill(ctx->ckdirty_halo.begin(), ctx->ckdirty_halo.end(), 0);
+    }
+    return ctx->ckdirty + nt * (size_t)s;
+}
+
 int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* out, float* all_out,
-                        bool seg = false, int end_step = -1, bool frozen = false) {
+                        bool seg = false, int end_step = -1, bool frozen = false, const PrepArgs* pa = nullptr,
+                        int ckpt_slot = -1) {
     CUtensorMap tab;
     if (!encode_f32_3d(&tab, in, ctx->P, ctx->H, 2, diff_blocked_box_cols(), diff_blocked_box_rows(), 2))
         return fail(ctx, PF_ECUDA, "tensor map encoding of the state buffer failed");
@@ -539,22 +564,33 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
         ctx->fl_in_at[0] = ctx->fl_in_at[1] = -1;
     }
     const size_t stride = 2 * plane_elems(ctx);
+    uint8_t* dirty = nullptr;
+    bool dirty_unknown = true;
+    if (ckpt_slot >= 0) {
+        int rc;
+        dirty = ckpt_dirty_bits(ctx, ckpt_slot, &rc);
+        if (rc) return rc;
+        dirty_unknown = ctx->ckdirty_halo[ckpt_slot] != halo;
+        ctx->ckdirty_halo[ckpt_slot] = halo;
+    }
     // out, if a work buffer, holds the input state of the launch it last was the input of
     // (each launch's output becomes the next one's input, and is complete after it)
     int out_age = 0;
     for (int x = 0; x < 2; ++x)
         if (out && out == ctx->work[x] && ctx->fl_in_at[x] >= 0) out_age = ctx->fl_launch - ctx->fl_in_at[x];
     {
-        LaunchScope ls(ctx, K_FTILES);
+        // the pre-pass of a forward launch, or of one recomputing a segment for the adjoint
+        LaunchScope ls(ctx, seg ? K_STILES : K_FTILES);
         launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
                          ctx->fqrun, ctx->flist, ctx->dflags + 11, out, out_age, all_out,
                          stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_slot0 : nullptr,
                          seg ? ctx->seg_buf + stride : nullptr,
-                         ctx->seg_cap - 1, seg && frozen && halo == 8, ctx->dskip + K_FBLK, ctx->st);
+                         ctx->seg_cap - 1, seg && frozen && halo == 8, dirty, dirty_unknown, ctx->dskip + K_FBLK,
+                         ctx->st);
     }
     {
         LaunchScope ls(ctx, K_FBLK, n);
-        launch_diff_blocked(halo, &tab, &ctx->tmapQ, ctx->H, ctx->W, ctx->P, pc, n, ctx->flist, ctx->dflags + 11, out,
+        launch_diff_blocked(halo, &tab, &ctx->tmapQ, pa, ctx->H, ctx->W, ctx->P, pc, n, ctx->flist, ctx->dflags + 11, out,
                             all_out, stride, ctx->fact[1 - ctx->fl_par], ctx->dskip + K_FBLK, ctx->nsm, ctx->dflags,
                             ctx->hook, ctx->st);
     }
@@ -586,23 +622,35 @@ DiscreteArgs dargs(const pf_ctx* c) {
 int run_discrete(pf_ctx* ctx, int T) {
     const DiscreteArgs g = dargs(ctx);
     const int kern = choose_kernel(ctx);
+    const bool rcq = ctx->tun.prep == 2;  // q recomputed inside the step kernels
     int t = ctx->step;
     const int end = ctx->step + T;
+    int pa_epoch = -1;
+    PrepArgs pa{};
     while (t < end) {
         const int e = epoch_of(ctx, t);
-        int rc = ensure_q(ctx, e);
-        if (rc) return rc;
+        int rc;
+        if (rcq) {
+            if (e != pa_epoch) pa = prep_args(ctx, e, false);
+            pa_epoch = e;
+        } else if ((rc = ensure_q(ctx, e))) {
+            return rc;
+        }
         int n = std::min(end - t, next_epoch_start(ctx, t) - t);
         const int src = ctx->scur, dst = 1 - ctx->scur;
         if (kern == 2) {
             n = std::min(n, blocked_k(ctx));
             LaunchScope ls(ctx, K_DBLK, n);
-            launch_discrete_blocked_impl(g, &ctx->tmapS[src], ctx->TH, ctx->KH, ctx->S[dst], ctx->q, (uint32_t)t, n,
-                                         ctx->dflags, ctx->hook, ctx->dskip + K_DBLK, ctx->st);
+            launch_discrete_blocked_impl(g, &ctx->tmapS[src], ctx->TH, ctx->KH, ctx->S[dst], ctx->q,
+                                         rcq ? &pa : nullptr, (uint32_t)t, n, ctx->dflags, ctx->hook,
+                                         ctx->dskip + K_DBLK, ctx->st);
         } else {
             n = 1;
             LaunchScope ls(ctx, K_DSTEP);
-            launch_discrete_step(g, ctx->S[src], ctx->S[dst], ctx->q, (uint32_t)t, ctx->st);
+            if (rcq)
+                launch_discrete_step_rc(g, ctx->S[src], ctx->S[dst], pa, (uint32_t)t, ctx->st);
+            else
+                launch_discrete_step(g, ctx->S[src], ctx->S[dst], ctx->q, (uint32_t)t, ctx->st);
         }
         rc = check_launch(ctx, "discrete step");
         if (rc) return rc;
@@ -632,6 +680,7 @@ int arena_reserve(pf_ctx* ctx, int need) {
     if (old) dfree(ctx, old);
     ctx->arena = (float*)p;
     ctx->arena_cap = need;
+    ctx->ckdirty_halo.assign(need, 0);  // new memory: nothing known about any slot's tiles
     return PF_OK;
 }
 
@@ -646,6 +695,7 @@ int take_slots(pf_ctx* ctx, int n, int* rc) {
     ctx->arena_used += n;
     if ((int)ctx->ckact_halo.size() < ctx->arena_cap) ctx->ckact_halo.resize(ctx->arena_cap, 0);
     for (int i = s0; i < s0 + n; ++i) ctx->ckact_halo[i] = 0;  // no flags recorded for the new contents
+    if ((int)ctx->ckdirty_halo.size() < ctx->arena_cap) ctx->ckdirty_halo.resize(ctx->arena_cap, 0);
     return s0;
 }
 
@@ -719,10 +769,19 @@ int diff_steps(pf_ctx* ctx, int T) {
     // with K == 1 every state is saved: blocked launches write all of them into
     // consecutive tape slots
     const bool all_states = ctx->tape_valid && ctx->K == 1;
+    const bool rcq = ctx->tun.prep == 2;  // q recomputed inside the step kernels
+    int pa_epoch = -1;
+    PrepArgs pa{};
     while (ctx->step < end) {
         const int t = ctx->step;
-        int rc = ensure_q(ctx, epoch_of(ctx, t), std::min(end, next_epoch_start(ctx, t)));
-        if (rc) return rc;
+        int rc;
+        if (rcq) {
+            const int e = epoch_of(ctx, t);
+            if (e != pa_epoch) pa = prep_args(ctx, e, false);
+            pa_epoch = e;
+        } else if ((rc = ensure_q(ctx, epoch_of(ctx, t), std::min(end, next_epoch_start(ctx, t))))) {
+            return rc;
+        }
         int n = 1;
         if (kern == 2) {
             n = std::min({blocked_k(ctx), end - t, next_epoch_start(ctx, t) - t});
@@ -734,7 +793,10 @@ int diff_steps(pf_ctx* ctx, int T) {
         if (all_states) {
             const int s = take_slots(ctx, n, &rc);
             if (rc) return rc;
-            for (int i = 0; i < n; ++i) ctx->ckpts.push_back({t + 1 + i, s + i});
+            for (int i = 0; i < n; ++i) {
+                ctx->ckpts.push_back({t + 1 + i, s + i});
+                ctx->ckdirty_halo[s + i] = 0;  // written whole: no dirty bits kept
+            }
             all_out = slot_ptr(ctx, s);
         } else if (ctx->tape_valid && is_ckpt_step(ctx, t + n)) {
             const int s = take_slots(ctx, 1, &rc);
@@ -751,14 +813,18 @@ int diff_steps(pf_ctx* ctx, int T) {
         }
         if (kern == 2) {
             if ((rc = diff_blocked_launch(ctx, ctx->cur_ab, ctx->pc, n, out, all_out, false,
-                                          all_states ? t + n : -1)))
+                                          all_states ? t + n : -1, false, rcq ? &pa : nullptr, ckpt_slot)))
                 return rc;
             if (ckpt_slot >= 0 && (rc = save_ckpt_flags(ctx, ckpt_slot))) return rc;
         } else {
             float* dst = out ? out : all_out;
+            if (ckpt_slot >= 0) ctx->ckdirty_halo[ckpt_slot] = 0;  // written whole
             {
                 LaunchScope ls(ctx, K_FSTEP);
-                launch_diff_step(ctx->H, ctx->W, ctx->P, ctx->pc, ctx->cur_ab, dst, ctx->q, ctx->st);
+                if (rcq)
+                    launch_diff_step_rc(pa, ctx->pc, ctx->cur_ab, dst, ctx->st);
+                else
+                    launch_diff_step(ctx->H, ctx->W, ctx->P, ctx->pc, ctx->cur_ab, dst, ctx->q, ctx->st);
             }
             if ((rc = check_launch(ctx, "diff step"))) return rc;
         }
@@ -803,6 +869,7 @@ int tape_begin(pf_ctx* ctx, int T) {
     if (rc) return rc;
     float* s0 = slot_ptr(ctx, s);
     CK(cudaMemcpyAsync(s0, ctx->cur_ab, diff_state_bytes(ctx), cudaMemcpyDeviceToDevice, ctx->st));
+    ctx->ckdirty_halo[s] = 0;  // written whole
     ctx->cur_ab = s0;
     ctx->ckpts.push_back({ctx->step, s});
     ctx->tape_valid = true;
@@ -1168,13 +1235,129 @@ int pf_wait(pf_ctx* ctx) {
     return device_error(ctx);
 }
 
-int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t) {
-    if (!ctx || !t) return fail(ctx, PF_EINVAL, "pf_set_tuning: NULL argument");
+namespace {
+
+// Tile geometry of the blocked discrete kernel: TH interior rows, KH halo rows (>= the
+// steps of one launch). Re-encodes both state tensor maps for the new box.
+int set_discrete_tiles(pf_ctx* ctx, int TH, int KH) {
+    if (ctx->form != PF_DISCRETE || (ctx->TH == TH && ctx->KH == KH)) return PF_OK;
+    const int oTH = ctx->TH, oKH = ctx->KH;
+    ctx->TH = TH;
+    ctx->KH = KH;
+    if (!encode_state_map(ctx, &ctx->tmapS[0], ctx->S[0]) || !encode_state_map(ctx, &ctx->tmapS[1], ctx->S[1])) {
+        ctx->TH = oTH;
+        ctx->KH = oKH;
+        ctx->tmap_ok = encode_state_map(ctx, &ctx->tmapS[0], ctx->S[0]) &&
+                       encode_state_map(ctx, &ctx->tmapS[1], ctx->S[1]);
+        return fail(ctx, PF_ECUDA, "tensor map encoding for %d-row tiles failed", TH);
+    }
+    return PF_OK;
+}
+
+int apply_tuning(pf_ctx* ctx, const pf_tuning* t) {
     if (t->kernel < 0 || t->kernel > 2) return fail(ctx, PF_EINVAL, "pf_set_tuning: kernel must be 0, 1 or 2");
     if (t->k < 0 || t->k > 16) return fail(ctx, PF_EINVAL, "pf_set_tuning: k must be in 0..16");
     if (t->K < 0) return fail(ctx, PF_EINVAL, "pf_set_tuning: K must be >= 0");
+    if (t->prep < 0 || t->prep > 2) return fail(ctx, PF_EINVAL, "pf_set_tuning: prep must be 0, 1 or 2");
+    if (t->tile_rows != 0 && t->tile_rows != 16 && t->tile_rows != 32 && t->tile_rows != 64 && t->tile_rows != 128)
+        return fail(ctx, PF_EINVAL, "pf_set_tuning: tile_rows must be 0, 16, 32, 64 or 128");
+    if (ctx->form == PF_DISCRETE) {
+        const int rc = set_discrete_tiles(ctx, t->tile_rows ? t->tile_rows : 64,
+                                          t->k ? std::min(t->k, discrete_blocked_max_k()) : 16);
+        if (rc) return rc;
+    }
     ctx->tun = *t;
     return PF_OK;
+}
+
+// ------------------------------------------------------------- tuning cache
+// One line per tuned configuration: "<key>\t<kernel> <k> <prep> <tile_rows> <K>". The
+// newest line of a key wins; a file that cannot be read or written is skipped.
+std::string tune_cache_path() {
+    const char* e = getenv("PF_TUNE_CACHE");
+    if (e) return (e[0] == '\0' || strcmp(e, "off") == 0) ? std::string() : std::string(e);
+    std::string dir;
+    const char* x = getenv("XDG_CACHE_HOME");
+    const char* h = getenv("HOME");
+    if (x && x[0])
+        dir = x;
+    else if (h && h[0])
+        dir = std::string(h) + "/.cache";
+    else
+        return std::string();
+    return dir + "/pfire/tuning.tsv";
+}
+
+// (GPU model, compute capability, SM count, search, form, H, W, R, T)
+std::string tune_key(const pf_ctx* ctx, const char* what, int T) {
+    cudaDeviceProp prop;
+    int dev = 0;
+    std::string gpu = "unknown";
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+        char b[320];
+        snprintf(b, sizeof b, "%s sm_%d%d x%d", prop.name, prop.major, prop.minor, prop.multiProcessorCount);
+        gpu = b;
+    } else {
+        cudaGetLastError();
+    }
+    for (char& ch : gpu)
+        if (ch == '\t' || ch == '\n' || ch == '|') ch = ' ';
+    char b[160];
+    snprintf(b, sizeof b, "|%s|%s|H=%d|W=%d|R=%d|T=%d", what, ctx->form == PF_DIFF ? "diff" : "discrete", ctx->H,
+             ctx->W, ctx->R, T);
+    return gpu + b;
+}
+
+bool tune_cache_get(const std::string& key, pf_tuning* t) {
+    const std::string path = tune_cache_path();
+    if (path.empty()) return false;
+    std::ifstream f(path);
+    if (!f) return false;
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {
+        const size_t tab = line.find('\t');
+        if (tab != key.size() || line.compare(0, tab, key) != 0) continue;
+        std::istringstream v(line.substr(tab + 1));
+        pf_tuning x{};
+        if (v >> x.kernel >> x.k >> x.prep >> x.tile_rows >> x.K) {
+            *t = x;
+            found = true;
+        }
+    }
+    return found;
+}
+
+void tune_cache_put(const std::string& key, const pf_tuning& t) {
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    for (size_t i = 1; i < path.size(); ++i)  // parent directories, mode 0755
+        if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
+    std::ofstream f(path, std::ios::app);
+    if (f) f << key << '\t' << t.kernel << ' ' << t.k << ' ' << t.prep << ' ' << t.tile_rows << ' ' << t.K << '\n';
+}
+
+// state of a probe run: S_init copied (discrete) or initialised (differentiable)
+int probe_start(pf_ctx* ctx, const uint8_t* S_init) {
+    ctx->step = 0;
+    if (ctx->form == PF_DISCRETE) {
+        ctx->scur = 0;
+        if (cudaMemcpy2DAsync(ctx->S[0], ctx->P, S_init, ctx->W, ctx->W, (size_t)ctx->R * ctx->H,
+                              cudaMemcpyDeviceToDevice, ctx->st) != cudaSuccess)
+            return fail(ctx, PF_ECUDA, "pf_autotune: state copy failed");
+    } else {
+        launch_diff_init(S_init, ctx->H, ctx->W, ctx->P, ctx->work[0], ctx->burn, ctx->st);
+        ctx->cur_ab = ctx->work[0];
+        ctx->version++;  // every materialising candidate pays for its own prep
+    }
+    return PF_OK;
+}
+
+}  // namespace
+
+int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t) {
+    if (!ctx || !t) return fail(ctx, PF_EINVAL, "pf_set_tuning: NULL argument");
+    return apply_tuning(ctx, t);
 }
 
 int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t) {
@@ -1183,6 +1366,8 @@ int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t) {
     t->kernel = choose_kernel(ctx);
     if (t->k == 0) t->k = blocked_k(ctx);
     if (t->K == 0) t->K = ctx->K;
+    if (t->prep == 0) t->prep = 1;
+    t->tile_rows = ctx->form == PF_DISCRETE ? ctx->TH : 0;
     return PF_OK;
 }
 
@@ -1192,17 +1377,33 @@ int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chos
     if (T_probe < 1) return fail(ctx, PF_EINVAL, "pf_autotune: T_probe must be >= 1");
     int rc = validate_states(ctx, S_init, (size_t)ctx->R * ctx->H * ctx->W);
     if (rc) return rc;
-    // candidates (kernel, k): the plain per-step kernels and the temporal-blocked ones at
-    // several depths (the differentiable blocked kernel switches to its 4-cell halo for k <= 4)
-    std::vector<std::pair<int, int>> cand = {{1, 1}};
-    if (ctx->form == PF_DISCRETE) {
-        if (ctx->tmap_ok)
-            for (int k : {4, 8, 16})
-                if (k <= ctx->KH) cand.push_back({2, k});
-    } else if (ctx->tmapQ_ok) {
-        for (int k : {2, 4, 6, 8}) cand.push_back({2, k});
-    }
     const pf_tuning saved = ctx->tun;
+    const std::string key = tune_key(ctx, "launch", T_probe);
+    pf_tuning hit;
+    if (tune_cache_get(key, &hit) && hit.kernel >= 1) {
+        hit.K = saved.K;  // this search leaves K alone
+        hit.profile = saved.profile;
+        if (apply_tuning(ctx, &hit) == PF_OK) {
+            if (chosen) pf_get_tuning(ctx, chosen);
+            return PF_OK;
+        }
+        ctx->tun = saved;
+    }
+    // candidates: q materialised per wind epoch (prep 1) or recomputed inside the step
+    // kernels (prep 2), each with the plain per-step kernels and the temporal-blocked ones
+    // at several depths k (the differentiable blocked kernel switches to its 4-cell halo
+    // for k <= 4; the discrete one also takes 32, 64 or 128 interior rows per tile)
+    std::vector<pf_tuning> cand;
+    for (int prep : {1, 2}) {
+        cand.push_back({1, 1, saved.K, saved.profile, prep, 0});
+        if (ctx->form == PF_DISCRETE) {
+            if (ctx->tmap_ok)
+                for (int k : {4, 8, 12})
+                    for (int rows : {32, 64, 128}) cand.push_back({2, k, saved.K, saved.profile, prep, rows});
+        } else if (ctx->tmapQ_ok) {
+            for (int k : {2, 4, 6, 8}) cand.push_back({2, k, saved.K, saved.profile, prep, 0});
+        }
+    }
     tape_reset(ctx);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1213,21 +1414,7 @@ int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chos
     int best = -1;
     for (int rep = 0; rep < 2 && rc == PF_OK; ++rep)  // first pass warms every variant up
         for (size_t c = 0; c < cand.size() && rc == PF_OK; ++c) {
-            ctx->tun.kernel = cand[c].first;
-            ctx->tun.k = cand[c].second;
-            ctx->step = 0;
-            if (ctx->form == PF_DISCRETE) {
-                ctx->scur = 0;
-                if (cudaMemcpy2DAsync(ctx->S[0], ctx->P, S_init, ctx->W, ctx->W, (size_t)ctx->R * ctx->H,
-                                      cudaMemcpyDeviceToDevice, ctx->st) != cudaSuccess) {
-                    rc = fail(ctx, PF_ECUDA, "pf_autotune: state copy failed");
-                    break;
-                }
-            } else {
-                launch_diff_init(S_init, ctx->H, ctx->W, ctx->P, ctx->work[0], ctx->burn, ctx->st);
-                ctx->cur_ab = ctx->work[0];
-                ctx->version++;
-            }
+            if ((rc = apply_tuning(ctx, &cand[c])) || (rc = probe_start(ctx, S_init))) break;
             cudaEventRecord(e0, ctx->st);
             rc = ctx->form == PF_DISCRETE ? run_discrete(ctx, T_probe) : diff_steps(ctx, T_probe);
             cudaEventRecord(e1, ctx->st);
@@ -1245,12 +1432,67 @@ int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chos
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->tun = saved;
     ctx->step = 0;
-    if (rc) return rc;
-    ctx->tun.kernel = cand[best].first;
-    ctx->tun.k = cand[best].second;
+    if (rc) {
+        apply_tuning(ctx, &saved);
+        return rc;
+    }
+    if ((rc = apply_tuning(ctx, &cand[best]))) return rc;
+    tune_cache_put(key, cand[best]);
     if (chosen) pf_get_tuning(ctx, chosen);
+    return PF_OK;
+}
+
+int pf_autotune_ckpt(pf_ctx* ctx, const uint8_t* S_init, int T, int* K_chosen) {
+    if (!ctx) return fail(nullptr, PF_EINVAL, "pf_autotune_ckpt: ctx is NULL");
+    if (!S_init) return fail(ctx, PF_EINVAL, "pf_autotune_ckpt: S_init is NULL");
+    if (ctx->form != PF_DIFF) return fail(ctx, PF_ESTATE, "pf_autotune_ckpt: only the differentiable form is taped");
+    if (T < 1) return fail(ctx, PF_EINVAL, "pf_autotune_ckpt: T must be >= 1");
+    int rc = validate_states(ctx, S_init, (size_t)ctx->H * ctx->W);
+    if (rc) return rc;
+    const pf_tuning saved = ctx->tun;
+    const std::string key = tune_key(ctx, "K", T);
+    pf_tuning hit;
+    if (tune_cache_get(key, &hit) && hit.K >= 0) {
+        ctx->tun.K = hit.K;
+        if (K_chosen) *K_chosen = hit.K;
+        return PF_OK;
+    }
+    // the memory rule (0), and intervals that are multiples of the blocked kernel's depth
+    // (no launch is cut short at a checkpoint) around the interval it picks
+    ctx->tun.K = 0;
+    tape_reset(ctx);
+    const int K0 = choose_K(ctx, T);
+    std::vector<int> cand = {0};
+    if (K0 > 1) {
+        const int k = choose_kernel(ctx) == 2 ? blocked_k(ctx) : 1;
+        for (int K : {k * ((K0 + k - 1) / k), k * (K0 / k), k * ((2 * K0 + k - 1) / k)})
+            if (K >= 2 && K != K0 && std::find(cand.begin(), cand.end(), K) == cand.end()) cand.push_back(K);
+    }
+    std::vector<double> t_ms(cand.size(), 0.0);
+    double grads[4];
+    for (int rep = 0; rep < 2 && rc == PF_OK && cand.size() > 1; ++rep)  // first pass warms up
+        for (size_t c = 0; c < cand.size() && rc == PF_OK; ++c) {
+            ctx->tun.K = cand[c];
+            if (cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+                rc = fail(ctx, PF_ECUDA, "pf_autotune_ckpt: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            const auto t0 = std::chrono::steady_clock::now();
+            if ((rc = pf_forward(ctx, S_init, T, nullptr))) break;
+            if ((rc = pf_backward(ctx, nullptr, nullptr, grads, nullptr, nullptr))) break;
+            const auto t1 = std::chrono::steady_clock::now();
+            if (rep == 1) t_ms[c] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        }
+    ctx->tun = saved;
+    tape_reset(ctx);
+    if (rc) return rc;
+    size_t best = 0;
+    for (size_t c = 1; c < cand.size(); ++c)
+        if (t_ms[c] < t_ms[best]) best = c;
+    ctx->tun.K = cand[best];
+    tune_cache_put(key, ctx->tun);
+    if (K_chosen) *K_chosen = cand[best];
     return PF_OK;
 }
 
@@ -1922,6 +2164,9 @@ int pf_loss_bce(const float* a, const float* y, int64_t n, float* dL_da, double*
 
 // One submission (a wave) of jobs that were validated by pf_batch_submit: one arena,
 // one captured graph, one persistent forward kernel and one adjoint kernel.
+// statistics of this thread's last pf_batch_submit, summed over its waves
+thread_local pf_batch_stats_t g_batch_stats{};
+
 static int batch_submit_wave(const pf_job* jobs, int n, cudaStream_t st) {
     pf_ctx* ctx = nullptr;  // context-free: errors go to pf_last_error(NULL)
     const int kB = batch_steps_per_item(), kTR = batch_tile_rows(), kTC = batch_tile_cols();
@@ -2007,6 +2252,7 @@ static int batch_submit_wave(const pf_job* jobs, int n, cudaStream_t st) {
     const size_t o_jb_b = take(sizeof(int) * std::max(1, max_blk_b));
     const size_t o_ctl_b = take(sizeof(unsigned long long));
     const size_t o_part = take(sizeof(double) * 4 * (size_t)nblk_prep);
+    const size_t o_stats = take(sizeof(unsigned long long) * kStatCount);
     char* arena = nullptr;
     if (cudaMalloc((void**)&arena, off) != cudaSuccess) {
         cudaGetLastError();
@@ -2067,6 +2313,7 @@ static int batch_submit_wave(const pf_job* jobs, int n, cudaStream_t st) {
     plan.err = derr;
     plan.wait_limit_ns = sl ? std::max(1000ll, atoll(sl)) : 4000000000ll;  // 4 s
     plan.withhold = wh ? atoi(wh) : 0;
+    plan.stats = (unsigned long long*)(arena + o_stats);
     BatchPlan plan_b = plan;
     plan_b.jobs = (const BatchJobDev*)(arena + o_jobs_b);
     plan_b.blk_start = (const long long*)(arena + o_bs_b);
@@ -2081,6 +2328,9 @@ static int batch_submit_wave(const pf_job* jobs, int n, cudaStream_t st) {
     const int grid = nsm * batch_blocks_per_sm();
     int herr = 0;
     std::vector<int> hvf(n, 0);
+    unsigned long long hstats[kStatCount] = {0};
+    // graph start; forward kernel start / end; adjoint kernel start / end
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     // inputs: state codes 0..3, finite fields, p_veg / p_den >= -1 (as pf_forward / pf_set_env)
     e = cudaMemsetAsync(arena + o_vf, 0, sizeof(int) * n, st);
     if (e != cudaSuccess) goto cuda_fail;
@@ -2124,9 +2374,14 @@ static int batch_submit_wave(const pf_job* jobs, int n, cudaStream_t st) {
     // which cannot capture; the graph is then launched on the caller's stream)
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) goto cuda_fail;
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    if (e != cudaSuccess) goto cuda_fail;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) goto cuda_fail;
+    cudaEventRecordWithFlags(ev[0], cs, cudaEventRecordExternal);  // timing nodes of the graph
     cudaMemsetAsync(arena + o_ctl, 0, sizeof(unsigned long long) + sizeof(int) * 4, cs);
+    cudaMemsetAsync(arena + o_stats, 0, sizeof(unsigned long long) * kStatCount, cs);
     for (int k = 0; k < n; ++k) {
         const pf_job& J = jobs[order[k]];
         const Lay& L = lay[k];
@@ -2152,7 +2407,9 @@ static int batch_submit_wave(const pf_job* jobs, int n, cudaStream_t st) {
             cudaMemsetAsync(arena + L.genb, 0, (size_t)L.btx * L.bty * sizeof(int), cs);
         }
     }
+    cudaEventRecordWithFlags(ev[1], cs, cudaEventRecordExternal);
     launch_batch(plan, grid, cs);
+    cudaEventRecordWithFlags(ev[2], cs, cudaEventRecordExternal);
     if (nb) {
         // terminal adjoint of each job from dL/da_T and its state at T, then the
         // backward work queue, then each job's chain rule of prep and FP64 reduction
@@ -2165,7 +2422,9 @@ static int batch_submit_wave(const pf_job* jobs, int n, cudaStream_t st) {
             launch_adjoint_init(J.dL_da, nullptr, D.tape + (size_t)J.T * 2 * plane, J.H, J.W, lay[k].P, D.lam[z],
                                 D.sig[z], cs);
         }
+        cudaEventRecordWithFlags(ev[3], cs, cudaEventRecordExternal);
         launch_batch_adj(plan_b, nsm * batch_adj_blocks_per_sm(), cs);
+        cudaEventRecordWithFlags(ev[4], cs, cudaEventRecordExternal);
         for (int k : ab) {
             const pf_job& J = jobs[order[k]];
             const Lay& L = lay[k];
@@ -2190,9 +2449,26 @@ static int batch_submit_wave(const pf_job* jobs, int n, cudaStream_t st) {
     e = cudaGraphLaunch(exec, st);
     if (e != cudaSuccess) goto cuda_fail;
     e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hstats, arena + o_stats, sizeof(hstats), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) goto cuda_fail;
     if (herr) rc = fail(nullptr, PF_ETIMEOUT, "pf_batch_submit: a bounded wait for a neighbouring tile ran out");
+    {
+        pf_batch_stats_t& B = g_batch_stats;
+        B.disc_cell_steps += (long long)hstats[kStatDisc];
+        B.disc_skipped += (long long)hstats[kStatDiscSkip];
+        B.diff_cell_steps += (long long)hstats[kStatDiff];
+        B.diff_skipped += (long long)hstats[kStatDiffSkip];
+        B.adj_cell_steps += (long long)hstats[kStatAdj];
+        B.adj_skipped += (long long)hstats[kStatAdjSkip];
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[1], ev[2]) == cudaSuccess) B.ms_forward += ms;
+        if (nb && cudaEventElapsedTime(&ms, ev[3], ev[4]) == cudaSuccess) B.ms_adjoint += ms;
+        if (cudaEventElapsedTime(&ms, ev[0], nb ? ev[4] : ev[2]) == cudaSuccess) B.ms_kernels_from_start += ms;
+        cudaGetLastError();
+        B.waves += 1;
+    }
     goto done;
 cuda_fail:
     rc = fail(nullptr, PF_ECUDA, "pf_batch_submit: %s", cudaGetErrorString(e));
@@ -2209,6 +2485,8 @@ done:
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     cudaStreamSynchronize(st);
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
     cudaFree(arena);
     cudaGetLastError();
     (void)ctx;
@@ -2216,6 +2494,7 @@ done:
 }
 
 int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
+    g_batch_stats = pf_batch_stats_t{};
     pf_ctx* ctx = nullptr;  // context-free: errors go to pf_last_error(NULL)
     if (n < 0 || (n > 0 && !jobs)) return fail(nullptr, PF_EINVAL, "pf_batch_submit: bad job array");
     if (n == 0) return PF_OK;
@@ -2283,6 +2562,12 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
         const int rc = batch_submit_wave(wave.data(), (int)wave.size(), (cudaStream_t)cuda_stream);
         if (rc) return rc;
     }
+    return PF_OK;
+}
+
+int pf_batch_last_stats(pf_batch_stats_t* out) {
+    if (!out) return fail(nullptr, PF_EINVAL, "pf_batch_last_stats: out is NULL");
+    *out = g_batch_stats;
     return PF_OK;
 }
 

@@ -34,3 +34,11 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _tuning_cache(tmp_path_factory):
+    # the autotuner's on-disk cache goes to a per-session file, not the user's cache
+    if "PF_TUNE_CACHE" not in os.environ:
+        os.environ["PF_TUNE_CACHE"] = str(tmp_path_factory.mktemp("tune") / "tuning.tsv")
+    yield

@@ -271,3 +271,30 @@ def test_degenerate_shapes_and_steps(pf, orc, H, W, T, kernel):
         assert not any(g4) and not gpv.any()
     for k in range(4):
         assert g4[k] == pytest.approx(want4[k], rel=GRAD_RTOL, abs=1e-12)
+
+
+def test_checkpoint_slots_reused_by_a_different_run(pf, orc):
+    """A context keeps its checkpoint slots from run to run and writes an all-zero tile
+    into a slot only where that slot may hold nonzeros: a second run whose fires lie
+    elsewhere (tiles burned in the first run are zero now, and the reverse) gives the
+    gradients and states of the same run on a fresh context, bit for bit."""
+    import torch
+    H, W, T, K = 300, 340, 70, 9
+    land = syn.make_landscape(H, W, 41)
+    V, th = syn.smooth_wind(H, W, 41, 0, sigma=8.0)
+    S_a = syn.initial_state(land, [(60, 60), (240, 280)])
+    S_b = syn.initial_state(land, [(150, 170), (60, 280)])
+    w = cuda(np.random.default_rng(3).standard_normal((H, W)).astype(np.float32) * 1e-3)
+    m, _ = _model(pf, orc, land, V, th, H, W)
+    m.set_tuning(kernel=2, k=8, K=K)
+    m.forward(cuda(S_a), T)
+    m.backward(w, None)
+    out = m.forward(cuda(S_b), T).cpu().numpy()
+    g4, gpv, _ = m.backward(w, None)
+    f, _ = _model(pf, orc, land, V, th, H, W)
+    f.set_tuning(kernel=2, k=8, K=K)
+    out_f = f.forward(cuda(S_b), T).cpu().numpy()
+    g4_f, gpv_f, _ = f.backward(w, None)
+    assert np.array_equal(out, out_f)
+    assert list(g4) == list(g4_f)
+    assert torch.equal(gpv, gpv_f)
