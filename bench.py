@@ -248,8 +248,10 @@ def batched_fires(pf, torch, timed, n_fires=256, seed=4):
     """Uneven fires (side log-uniform in [64, 2048], T uniform in [100, 1000], 1-5
     ignitions, half discrete / half differentiable, the latter with an adjoint) through
     one pf_batch_submit, against the same fires run one after another through per-fire
-    contexts with the plain per-step kernels; cell-updates/s over sum(side^2 T), the
-    differentiable fires counted twice (forward and adjoint)."""
+    contexts with the plain per-step kernels and with the default (blocked) ones;
+    cell-updates/s over sum(side^2 T), the differentiable fires counted twice (forward
+    and adjoint). The submission is also timed at several routing thresholds (jobs above
+    it through contexts of their own, the rest through the persistent queue)."""
     rng = np.random.default_rng(seed)
     fires = []
     for i in range(n_fires):
@@ -269,8 +271,16 @@ def batched_fires(pf, torch, timed, n_fires=256, seed=4):
     jobs = [pf.make_job(S0, T, form=form, seed=seed, fire_id=i, E=E, p_veg=pv, p_den=pd, V_w=V, theta_w=th,
                         dL_da=wts[i], **PARAMS)[0] for i, (side, T, form, E, pv, pd, V, th, S0) in enumerate(dev)]
     pf.pf_batch_submit(jobs)  # warm-up
-    ms_batch = timed(lambda: pf.pf_batch_submit(jobs), 1)
+    ms_batch = timed(lambda: pf.pf_batch_submit(jobs), 1)  # the library's default routing
     bst = pf.pf_batch_last_stats()
+    # the routing threshold: jobs of at least `cells` cells through contexts of their own
+    routing = {}
+    for name, cells_min in (("queue_only", 1 << 40), ("direct_from_2^20", 1 << 20), ("direct_from_2^18", 1 << 18),
+                            ("direct_from_2^16", 1 << 16), ("all_direct", 0)):
+        pf.pf_batch_set_direct_cells(cells_min)
+        routing[name] = {"ms": timed(lambda: pf.pf_batch_submit(jobs), 1), **pf.pf_batch_last_stats()}
+    pf.pf_batch_set_direct_cells(1 << 18)
+    q_only = routing["queue_only"]
 
     def plain_all():
         for i, (side, T, form, E, pv, pd, V, th, S0) in enumerate(dev):
@@ -306,7 +316,9 @@ def batched_fires(pf, torch, timed, n_fires=256, seed=4):
             "speedup": ms_plain / ms_batch, "ms_batched": ms_batch, "ms_plain_per_fire": ms_plain,
             "blocked_per_fire": cells / (ms_blocked / 1000.0), "ms_blocked_per_fire": ms_blocked,
             "frac_hbm_alg_effective": alg / (ms_batch / 1000.0) / 1e9 / hbm,
-            "kernels": bst, "roofline": batch_roofline(bst, hbm, how)}
+            "default_stats": bst, "routing_ms": {k: v["ms"] for k, v in routing.items()},
+            # the persistent kernels' roofline from the run with every job in the queue
+            "kernels_queue_only": q_only, "roofline": batch_roofline(q_only, hbm, how)}
 
 
 def batch_roofline(bst, hbm, how):
@@ -382,9 +394,12 @@ def adjoint_probe(kind, N=2048, T=14):
         m.backward(w, None, per_cell=False)
         torch.cuda.synchronize()
     p = pf.pf_profile_read(m.h, reset=True)
+    # a launch of the blocked adjoint: the live-tile kernel and the frozen-tile kernel
     n, cs, ms, sk = p["adjoint_blocked"]
+    ms_f = p.get("adjoint_frozen", (0, 0, 0.0, 0))[2]
     return {"probe": "adjoint_" + kind, "grid": N, "steps": T, "launches": n, "computed_cell_steps": cs - sk,
-            "frozen_cell_steps": p["adjoint_tiles"][3], "ms": ms, "ps_per_computed_cell_step": ms * 1e9 / max(1, cs - sk)}
+            "frozen_cell_steps": p["adjoint_tiles"][3], "ms_live_kernel": ms, "ms_frozen_kernel": ms_f,
+            "ps_per_computed_cell_step": (ms + ms_f) * 1e9 / max(1, cs - sk)}
 
 
 def main():
@@ -540,26 +555,53 @@ def main():
         pf.pf_set_tuning(m.h, **base)
 
     # roofline of the dominant kernel (largest share of device time in the timed region):
-    # algorithmic bytes = per-cell-step bytes x the cell-steps its launches processed
+    # algorithmic bytes = per-cell-step bytes x the cell-steps its launches computed.
+    # Cell-steps of quiescent tiles, which the kernels skip, are not counted (no state
+    # bytes move for them). The blocked adjoint runs its frozen tiles in a kernel of its
+    # own: those cell-steps (counted by its pre-pass) are the frozen kernel's, the rest of
+    # its computed ones the live kernel's.
     hbm, how = peaks()
-    # (cell-steps of quiescent tiles, which the kernel skips, are not counted: the kernel
-    # moves no state bytes for them)
-    kind, (n_l, cs_l, t_l, sk_l) = max(prof.items(), key=lambda kv: kv[1][2])
-    alg = {"adjoint_step": B_ADJ, "adjoint_blocked": B_ADJ, "diff_step": B_FWD, "diff_blocked": B_FWD}.get(kind, B_FWD)
-    achieved = alg * (cs_l - sk_l) / (t_l / 1000.0) / 1e9
-    tb = ncu_traffic(kind)
-    roof = {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "peak_source": how,
-            # measured DRAM bytes per launch (ncu, per computed cell-step x this run's
-            # computed cell-steps per launch); null if the kernel changed since
-            "traffic": None if tb is None else tb * (cs_l - sk_l) / n_l,
-            "traffic_bytes_per_computed_cell_step": tb,
-            # DRAM utilisation: the measured bytes per launch over the launch's time
-            "dram_frac": None if tb is None else tb * (cs_l - sk_l) / (t_l / 1000.0) / 1e9 / hbm,
-            "launches": n_l, "ms_per_launch": t_l / n_l, "cell_steps_per_launch": (cs_l - sk_l) / n_l,
-            "skipped_frac": sk_l / max(1, cs_l),
-            "alg_bytes_per_cell_step": alg,
-            "share": t_l / max(1e-9, sum(v[2] for v in prof.values()))}
+    total_ms = sum(v[2] for v in prof.values())
+    frozen_cs = prof.get("adjoint_tiles", (0, 0, 0.0, 0))[3]
+    computed = {}
+    for kname, (n_l, cs_l, t_l, sk_l) in prof.items():
+        if n_l == 0 or t_l <= 0.0:
+            continue
+        if kname == "adjoint_frozen":
+            computed[kname] = (frozen_cs, B_ADJ)
+        elif kname == "adjoint_blocked":
+            computed[kname] = (cs_l - sk_l - (frozen_cs if prof.get("adjoint_frozen", (0,))[0] else 0), B_ADJ)
+        elif kname in ("adjoint_step",):
+            computed[kname] = (cs_l - sk_l, B_ADJ)
+        elif kname in ("diff_step", "diff_blocked"):
+            computed[kname] = (cs_l - sk_l, B_FWD)
+
+    def roofline_of(kname):
+        n_l, cs_l, t_l, sk_l = prof[kname]
+        comp, alg = computed[kname]
+        achieved = alg * comp / (t_l / 1000.0) / 1e9
+        tb = ncu_traffic(kname)
+        return {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": how,
+                # measured DRAM bytes per launch (ncu on a small case, per computed cell-step,
+                # x this run's computed cell-steps per launch); null if the kernel changed since
+                "traffic": None if tb is None else tb * comp / n_l,
+                "traffic_bytes_per_computed_cell_step": tb,
+                # DRAM utilisation: the measured bytes per launch over the launch's time
+                "dram_frac": None if tb is None else tb * comp / (t_l / 1000.0) / 1e9 / hbm,
+                "launches": n_l, "ms_per_launch": t_l / n_l, "cell_steps_per_launch": comp / n_l,
+                "skipped_frac": None if kname == "adjoint_frozen" else sk_l / max(1, cs_l),
+                "alg_bytes_per_cell_step": alg, "share": t_l / max(1e-9, total_ms)}
+
+    kind = max(computed, key=lambda k: prof[k][2])
+    roof = roofline_of(kind)
+    roof["others"] = [roofline_of(k) for k in sorted(computed, key=lambda k: -prof[k][2]) if k != kind]
+    if "adjoint_frozen" in computed and "adjoint_blocked" in computed:
+        # the blocked adjoint as a whole (both kernels of each launch)
+        comp_adj = computed["adjoint_blocked"][0] + frozen_cs
+        t_adj = prof["adjoint_blocked"][2] + prof["adjoint_frozen"][2]
+        roof["adjoint_both_kernels"] = {"achieved": B_ADJ * comp_adj / (t_adj / 1000.0) / 1e9,
+                                        "frac": B_ADJ * comp_adj / (t_adj / 1000.0) / 1e9 / hbm, "ms": t_adj}
 
     # end to end through the C ABI with host buffers: inputs H2D, gradients D2H each step
     e2e = None

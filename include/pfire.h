@@ -276,7 +276,12 @@ int pf_autotune_ckpt(pf_ctx* ctx, const uint8_t* S_init, int T, int* K_chosen);
  * kernels skipped because their tile was quiescent (forward: b = 0 in the whole tile
  * region, so nothing changes; adjoint: a = 0 in the whole region, so lambda is 0; the
  * results are exact either way; for the kind "adjoint_tiles" it counts the cell-steps the
- * blocked adjoint ran on frozen tiles, whose region is constant over the launch) and, if
+ * blocked adjoint ran on frozen tiles, whose region is constant over the launch; for
+ * "diff_tiles" and "segment_tiles", the pre-passes of the blocked forward and of the
+ * adjoint's segment recomputes, the cells they copied or zero-filled). The blocked
+ * adjoint's frozen tiles run in a kernel of their own ("adjoint_frozen": its launches and
+ * time; its cell-steps are those "adjoint_tiles" counts; "adjoint_blocked" counts every
+ * cell-step of a launch, skipped = the void tiles') and, if
  * profiling, summed device milliseconds since the last reset. kinds[i] is a static name string; any output array may be NULL.
  * Synchronous. Returns the number of kinds written (<= max_kinds) or a negative pf_status. */
 int pf_profile_read(pf_ctx* ctx, int max_kinds, const char** kinds, long long* launches, long long* cell_steps,
@@ -373,13 +378,21 @@ typedef struct pf_job {
 } pf_job;
 
 /* Run n independent fires of uneven sizes and step counts (each as pf_forward would,
- * bit-identically for the discrete form) from one device work queue in a persistent
- * kernel, then, for the differentiable jobs that carry dL_da, their reverse-time adjoint
- * from a second work queue (block by block from each job's last step), and the
- * parameter and per-cell gradients; the whole submission is one captured CUDA graph.
- * Synchronous. PF_ETIMEOUT if a bounded device-side wait ran out, PF_ENOMEM if the
- * states of the differentiable jobs with an adjoint do not fit. */
+ * bit-identically for the discrete form and the differentiable forward), with, for the
+ * differentiable jobs that carry dL_da, their reverse-time adjoint and the parameter and
+ * per-cell gradients. Jobs of at least pf_batch_set_direct_cells cells (default 2^18)
+ * run one after another through a context of their own (the temporal-blocked kernels
+ * and the context's automatic tuning, with the job's fire_id and run); the others from
+ * one device work queue in a persistent kernel, then their adjoints from a second work
+ * queue (block by block from each job's last step), in one captured CUDA graph per wave
+ * of jobs that fits in memory. Synchronous. PF_ETIMEOUT if a bounded device-side wait
+ * ran out, PF_ENOMEM if the states of the differentiable jobs with an adjoint do not fit. */
 int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream);
+
+/* Jobs of pf_batch_submit with H * W >= min_cells run through contexts of their own
+ * (0: all of them; a value above every job's size: none). Process-wide; PF_EINVAL for
+ * min_cells < 0. No counterpart in the paper (a scheduling choice of the batch). */
+int pf_batch_set_direct_cells(long long min_cells);
 
 /* Work and device time of this thread's last pf_batch_submit, summed over the waves it
  * ran in (jobs are grouped into waves that fit in free memory). Cell-steps count each
@@ -389,13 +402,19 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream);
  * computed. ms_forward / ms_adjoint: device time of the persistent forward / adjoint
  * kernels (CUDA events in the submission's graph); ms_kernels_from_start: from the
  * start of the graph to the end of the last of them (initial states, prep, both
- * kernels). The paper has no counterpart: reporting for the batch's roofline. */
+ * kernels). These count the queued jobs only; direct_jobs ran through contexts of their
+ * own, with direct_cell_steps (H W T, twice for an adjoint) in ms_direct (CUDA events
+ * around them, context set-up included). The paper has no counterpart: reporting for
+ * the batch's roofline. */
 typedef struct pf_batch_stats_t {
     long long disc_cell_steps, disc_skipped;
     long long diff_cell_steps, diff_skipped;
     long long adj_cell_steps, adj_skipped;
     double ms_forward, ms_adjoint, ms_kernels_from_start;
     int waves;
+    int direct_jobs;
+    long long direct_cell_steps;
+    double ms_direct;
 } pf_batch_stats_t;
 int pf_batch_last_stats(pf_batch_stats_t* out);
 

@@ -23,7 +23,7 @@ __all__ = [
     "PFireError", "build", "load", "PF_DISCRETE", "PF_DIFF",
     "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_wind_async", "pf_wait", "pf_set_params",
     "pf_forward", "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
-    "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_profile_read", "pf_batch_submit", "pf_last_error",
+    "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_batch_set_direct_cells", "pf_profile_read", "pf_batch_submit", "pf_last_error",
     "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
     "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10", "pf_arrival_probability",
     "pf_affected_count", "pf_jaccard", "pf_manhattan", "pf_set_slope", "simulate", "WildfireModel",
@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = [
     "pf_manhattan", "pf_stats", "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
-    "pf_loss_bce_noalloc", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
+    "pf_loss_bce_noalloc", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_batch_set_direct_cells", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
     "pf_arrival_probability", "pf_affected_count", "pf_jaccard", "pf_set_slope", "pf_set_wind_async", "pf_wait",
 ]
 PF_NOALLOC_BCE_MAX_N = 67108864
@@ -72,7 +72,8 @@ class PfBatchStats(ctypes.Structure):
                 ("diff_cell_steps", ctypes.c_longlong), ("diff_skipped", ctypes.c_longlong),
                 ("adj_cell_steps", ctypes.c_longlong), ("adj_skipped", ctypes.c_longlong),
                 ("ms_forward", ctypes.c_double), ("ms_adjoint", ctypes.c_double),
-                ("ms_kernels_from_start", ctypes.c_double), ("waves", ctypes.c_int)]
+                ("ms_kernels_from_start", ctypes.c_double), ("waves", ctypes.c_int), ("direct_jobs", ctypes.c_int),
+                ("direct_cell_steps", ctypes.c_longlong), ("ms_direct", ctypes.c_double)]
 
 
 class PfJob(ctypes.Structure):
@@ -128,6 +129,7 @@ def load():
             "pf_autotune": ([vp, vp, i, ctypes.POINTER(PfTuning)], i),
             "pf_autotune_ckpt": ([vp, vp, i, ctypes.POINTER(ctypes.c_int)], i),
             "pf_batch_last_stats": ([ctypes.POINTER(PfBatchStats)], i),
+            "pf_batch_set_direct_cells": ([ctypes.c_longlong], i),
             "pf_set_accumulator": ([vp, vp], i),
             "pf_reseed": ([vp, ctypes.c_uint64], i),
             "pf_backward_dca": ([vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp], i),
@@ -463,6 +465,11 @@ def make_job(S_init, T, S_out=None, form=PF_DISCRETE, seed=0, run=0, fire_id=0, 
 def pf_batch_submit(jobs, stream=None):
     arr = (PfJob * len(jobs))(*jobs)
     _check(load().pf_batch_submit(arr, len(jobs), _stream(stream)))
+
+
+def pf_batch_set_direct_cells(min_cells: int):
+    """Jobs of pf_batch_submit with H * W >= min_cells run through contexts of their own."""
+    _check(load().pf_batch_set_direct_cells(int(min_cells)))
 
 
 def pf_batch_last_stats() -> dict:

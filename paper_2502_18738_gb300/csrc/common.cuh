@@ -391,11 +391,12 @@ void launch_fwd_act_seed(int halo, const uint8_t* seed, int H, int pitch, uint8_
 // out_dirty (nullable, with out a checkpoint slot): per tile of this geometry, whether the
 // slot's interior may hold nonzeros; all-zero tiles (a = 0) are written only where it is
 // set (all tiles if dirty_unknown), and it is updated to the state written.
+// written (nullable) accumulates the cells the pre-pass copied or zero-filled.
 void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
                       int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, const float* slot0,
                       float* zero_base, int zero_slots, bool frozen, uint8_t* out_dirty, bool dirty_unknown,
-                      unsigned long long* skipped, cudaStream_t s);
+                      unsigned long long* skipped, unsigned long long* written, cudaStream_t s);
 // pa: NULL = q staged from the planes of tq; else q recomputed in the kernel from pa's fields
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, const PrepArgs* pa, int H, int W,
                          int pitch, float pc, int n, const int* tile_list, int* tile_count, float* out, float* all_out,
@@ -468,10 +469,15 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
                                 uint8_t* deadcnt, int* tile_list, int* tile_count, bool use_frozen,
                                 uint8_t* gq_dirty, unsigned long long* skipped, unsigned long long* frozen_steps,
                                 cudaStream_t s);
-void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq, int H, int pitch,
-                            float pc, int zlast,
-                            int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
-                            float* Gq, const int* tile_list, int* tile_count, int nsm, int* err, TmaHook hk,
+// The listed non-frozen tiles run in k_adjoint_blocked (frozen_only false); the frozen ones
+// (listed from the back) in k_adjoint_frozen (frozen_only true), which stages q, the state
+// and lambda_in (tlam: a map of lam_in's two planes, the same box) by TMA. A launch of the
+// blocked adjoint is both calls. tile_count: [0] front count, [1] k_adjoint_blocked's work
+// counter, [2] frozen count, [3] k_adjoint_frozen's work counter (zeroed by the pre-passes).
+void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq,
+                            const CUtensorMap* tlam, int H, int pitch, float pc, int zlast, int n,
+                            const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out, float* Gq,
+                            const int* tile_list, int* tile_count, int nsm, int* err, TmaHook hk, bool frozen_only,
                             cudaStream_t s);
 void launch_ignition_map_discrete(const DiscreteArgs& g, const uint8_t* S, const float* q, float* P,
                                   cudaStream_t s);

@@ -20,6 +20,7 @@
 //     from the cell's own state, so it stays finite ahead of the fire);
 //   * writes lambda at t0 for the interior and adds the tile's dL/dq into global memory.
 // The halo shrinks by one cell per step, so the 48 x 48 interior is exact for n <= 7.
+// Tiles whose region is constant over the launch (frozen) run in k_adjoint_frozen below.
 #include <cuda.h>
 
 #include <cstddef>
@@ -51,7 +52,7 @@ struct Smem {
     float el2r[2][kStrips][kM];          // x = 31 -> x = 32 (dc = +1), rows of the strip
     float er2l[2][kStrips][kM];          // x = 32 -> x = 31 (dc = -1)
     float edump[kThreads];               // where the other threads' exchange stores go
-    uint32_t ks[kThreads];               // tier summaries at t of each thread's 8 cells (tier_summary)
+    uint32_t ks[2][kThreads];            // tier summaries at t of each thread's 8 cells, by step parity
 };
 
 __device__ __forceinline__ void origin(int tile, int tiles_x, int& r0, int& c0) {
@@ -86,10 +87,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int lane = tid & 31;
     const int warp = tid >> 5;
     const size_t gplane = (size_t)H * pitch;
-    // tiles not ahead of the fire (k_adjoint_tiles): the others from the front of the
-    // list, then the frozen ones (about half the cost) stored from its back, so that the
-    // dynamic hand-out ends on cheap tiles
-    const int ntiles = ntiles_live[0] + ntiles_live[2];
+    // the live tiles of the pre-pass's list, from its front (the frozen ones, stored from
+    // its back and counted in ntiles_live[2], run in k_adjoint_frozen)
+    const int ntiles = ntiles_live[0];
     if ((int)blockIdx.x >= ntiles) return;
     // thread 0's queue state, in shared memory to keep it out of the hot loop's registers:
     // entries of tiles 0 .. qstate[0]-1 are in tring; qstate[1]: no more tiles
@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int e = -1;
             if (!qstate[1]) {
                 const int k = f == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(next, 1);
-                const int nfront = qstate[2];
-                if (k < ntiles_live[0] + ntiles_live[2]) e = tiles[k < nfront ? k : qstate[3] - 1 - (k - nfront)];
+                if (k < qstate[2]) e = tiles[k];
                 else qstate[1] = 1;
             }
             tring[f & 3] = e;
@@ -134,15 +133,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int r0, c0;
         origin(e & kTileIndexMask, tiles_x, r0, c0);
         const int s = i & 1;
-        if ((e & kTileFrozenBit) && m > 0) {
-            // a frozen tile's region is constant over the launch: its steps read only the
-            // first state (staged for m = 0); the later stages complete without a copy
-            mbar_arrive_expect_tx(&sbar[s], 0u);
-            return;
-        }
-        // a frozen tile reads the launch's first state, from state 0 when its region has
-        // not changed since then (the recompute may have skipped writing it later)
-        const int z = (e & kTileFrozenBit) ? ((e & kTileCkptBit) ? 0 : zlast - (n - 1)) : zlast - m;
+        const int z = zlast - m;
         mbar_arrive_expect_tx(&sbar[s], (uint32_t)(2 * kPlane * sizeof(float)));
         if (hk.withhold) return;
         if (z == 0)
@@ -176,7 +167,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto exchange = [&](int ex, int row, float right, float left) {
         reinterpret_cast<float*>(&sm)[ex_off + (ex_on ? ex * kStrips * kM + row : 0)] = x == 32 ? left : right;
     };
+    // The tier summary (tier_summary) of this thread's cells in a staged state: computed
+    // for step i + 1 during step i (its stage was issued a step earlier), so the
+    // neighbours read it after step i's end barrier without a barrier of its own.
+    auto tier_sum = [&](const float* A_, const float* B_) {
+        uint32_t kword = 0u;
+#pragma unroll
+        for (int k = 0; k < kM; ++k) {
+            const float As = A_[(ys + k) * kCT + x];
+            kword |= (__float_as_uint(As) == 0u ? 15u : (uint32_t)x_tier(As, B_[(ys + k) * kCT + x])) << (4 * k);
+        }
+        return tier_summary(kword);
+    };
     bool failed = false;
+    uint32_t ksum = 0u;       // this thread's tier summary at the current step
     float la[kM], lb[kM];     // scaled adjoint mu of this thread's cells (lambda = mu 2^sigma)
     uint32_t sgp[2];          // sigma at t + 1 of the 8 cells, 4 per word
     for (int l = 0; !failed; ++l) {
@@ -184,7 +188,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ent = tring[l & 3];
         if (ent < 0) break;
         int r0, c0;
-        const bool frz = (ent & kTileFrozenBit) != 0;  // uniform across the CTA
         origin(ent & kTileIndexMask, tiles_x, r0, c0);
         if (!__syncthreads_and(mbar_wait_bounded(&qbar, (uint32_t)(l & 1), hk.spin))) {
             failed = true;
@@ -202,56 +205,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sv = in ? (uint32_t)__ldg(sig_in + (size_t)gr * pitch + gc) : (uint32_t)kSigmaZero;
             sgp[k >> 2] |= sv << (8 * (k & 3));
         }
-        if (frz) {
-            // Frozen tile: the region's state is constant over the launch and b = 0 in
-            // it, so sigma(t) = sigma(t + 1), P = 0, every leave-one-out product is 1 and no
-            // dL/dq term survives; each step reduces to l_b,i <- p_c l_b,i + sum over the
-            // targets j = i - d of (l_a + l_b)_j K_dj, with the constants
-            // K_dj = (1 - a_j) q_dj 2^(sigma_j - sigma_i) kept in TMEM (64 consecutive
-            // columns, read with two loads and one wait per step).
+#pragma unroll
+        for (int k = 0; k < kM; ++k) {
+            const int y = ys + k;
+            float qv[8], z[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                qv[d] = sm.q[d * kPlane + y * kCT + x];
+                z[d] = 0.0f;
+            }
+            tmem_st8_nc(tbase + 16 * k, qv);
+            tmem_st8_nc(tbase + 16 * k + 8, z);
+        }
+        // the tier summary of the tile's first step (the barrier below publishes it)
+        bool pro_ok;
+        {
             const int i0 = l * n;
-            if (!__syncthreads_and(mbar_wait_bounded(&sbar[i0 & 1], (uint32_t)((i0 >> 1) & 1), hk.spin))) {
-                failed = true;
-                break;
-            }
-            const float* stA = sm.st[i0 & 1];
-            const bool xin = x >= 1 && x < kCT - 1;
-            const float* stB = stA + kPlane;
-#pragma unroll
-            for (int k = 0; k < kM; ++k) {
-                const int y = ys + k;
-                float kv[8];
-                const float Aj = stA[y * kCT + x], Bj = stB[y * kCT + x];
-                const int sj = x_sigma(Aj, Bj);
-                // as in the general path: edge rows and columns of the region contribute nothing
-                const bool use = xin && y >= 1 && y < kRT - 1 && sj != kSigmaZero;
-                // 1 - a (1 in the tiers below 2^-64)
-                const float uaj = signbit(Aj) ? -Aj : ((int32_t)__float_as_uint(Bj) < 0 ? 1.0f : 1.0f - Aj);
-#pragma unroll
-                for (int d = 0; d < 8; ++d) {
-                    const int yy = use ? y + dir_dr(d) : y, xx = use ? x + dir_dc(d) : x;
-                    const int si = x_sigma(stA[yy * kCT + xx], stB[yy * kCT + xx]);
-                    kv[d] = use ? (uaj * sm.q[d * kPlane + y * kCT + x]) * exp2i(64 * (sj - si)) : 0.0f;
-                }
-                tmem_st8_nc(tbase + 8 * k, kv);  // frozen layout: cell k in columns 8k .. 8k + 7
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < kM; ++k) {
-                const int y = ys + k;
-                float qv[8], z[8];
-#pragma unroll
-                for (int d = 0; d < 8; ++d) {
-                    qv[d] = sm.q[d * kPlane + y * kCT + x];
-                    z[d] = 0.0f;
-                }
-                tmem_st8_nc(tbase + 16 * k, qv);
-                tmem_st8_nc(tbase + 16 * k + 8, z);
-            }
+            pro_ok = mbar_wait_bounded(&sbar[i0 & 1], (uint32_t)((i0 >> 1) & 1), hk.spin);
+            ksum = tier_sum(sm.st[i0 & 1], sm.st[i0 & 1] + kPlane);
+            sm.ks[i0 & 1][tid] = ksum;
         }
         tmem_wait_st();
         fence_proxy_async();
-        __syncthreads();  // q stage consumed
+        if (!__syncthreads_and(pro_ok)) {  // q stage consumed; the first step's summaries
+            failed = true;
+            break;
+        }
         if (tid == 0) issue_q(l + 1);
 
         for (int m = 0; m < n; ++m) {
@@ -275,64 +254,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             float w[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
             float own[kM];  // this thread's column, rows ys .. ys+7, before cross-warp / strip terms
             // b and 2^-sigma(t) of rows y-1, y, y+1 in columns x-1, x, x+1: ring slot (row - ys + 1) % 3
-            if (frz) {
-                uint32_t ka[32], kb[32];
-                tmem_ld32_async(tbase, ka);
-                tmem_ld32_async(tbase + 32, kb);
-                tmem_wait_ld64(ka, kb);
-#pragma unroll
-                for (int k = 0; k < kM; ++k) {
-                    const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
-                    scl[k] = (sp == kSigmaZero) ? 0.0f : 1.0f;  // sigma(t) = sigma(t + 1)
-                    float kv[8];
-#pragma unroll
-                    for (int d = 0; d < 8; ++d) kv[d] = __uint_as_float(k < 4 ? ka[8 * k + d] : kb[8 * (k - 4) + d]);
-                    float(&wu)[3] = w[k % 3];
-                    float(&wm)[3] = w[(k + 1) % 3];
-                    float(&wd)[3] = w[(k + 2) % 3];
-                    const float ln = la[k] + lb[k];  // l_a is unchanged (P = 0, no rescaling)
-#pragma unroll
-                    for (int d = 0; d < 8; ++d) {
-                        const int j = dir_dc(d) + 1;
-                        if (dir_dr(d) < 0) wu[j] = fmaf(ln, kv[d], wu[j]);
-                        else if (dir_dr(d) == 0) wm[j] = fmaf(ln, kv[d], wm[j]);
-                        else wd[j] = fmaf(ln, kv[d], wd[j]);
-                    }
-                    // row R = k (source row ys + k - 1) is complete
-                    if (k == 0) {
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) sm.vtop[ex][strip][j][x] = wu[j];
-                    } else {
-                        const float fr = __shfl_down_sync(0xffffffffu, wu[0], 1);
-                        const float fl = __shfl_up_sync(0xffffffffu, wu[2], 1);
-                        own[k - 1] = wu[1] + (lane < 31 ? fr : 0.0f) + (lane > 0 ? fl : 0.0f);
-                        exchange(ex, k - 1, wu[2], wu[0]);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) wu[j] = 0.0f;
-                }
-                sgc[0] = sgp[0];
-                sgc[1] = sgp[1];
-            } else {
-            // The tiers at t of this thread's cells, packed (15: a = 0), and their summary for
-            // the neighbours' choice of path below (written after the previous step's
-            // barrier, read before this step's end barrier).
-            uint32_t kword = 0u;
-#pragma unroll
-            for (int k = 0; k < kM; ++k) {
-                const float As = stA[(ys + k) * kCT + x];
-                kword |= (__float_as_uint(As) == 0u ? 15u : (uint32_t)x_tier(As, stB[(ys + k) * kCT + x])) << (4 * k);
-            }
-            const uint32_t ksum = tier_summary(kword);
-            sm.ks[tid] = ksum;
-            __syncthreads();
             // A warp whose windows (rows ys-1 .. ys+8, columns x-1 .. x+1) hold, at t, cells of
             // one tier k0 besides cells with a = 0, and whose cells are at t + 1 in tier k0 or
             // k0 - 1 (or have a = 0), needs no unit ratios between sources: every transfer of
             // a target j is rescaled by 2^(64 (sigma'(j) - k0)), folded into its l_P once.
             // Other warps take the general arithmetic, a ratio per transfer.
             uint32_t k0;
-            bool uni = window_one_tier(sm.ks, tid, x - xl, xr - x, strip > 0, strip < kStrips - 1, kCT, ksum, k0);
+            bool uni = window_one_tier(sm.ks[s], tid, x - xl, xr - x, strip > 0, strip < kStrips - 1, kCT, ksum, k0);
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
@@ -496,7 +424,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             };
             if (slow) cells(std::true_type{});
             else cells(std::false_type{});
-            }
             // rows R = 8 (source row ys + 7, slot 8 % 3) and R = 9 (the next strip's first row)
             {
                 float(&w8)[3] = w[kM % 3];
@@ -508,9 +435,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) sm.vbot[ex][strip][j][x] = w9[j];
             }
+            // the next step's tier summary, published by this step's end barrier
+            bool next_ok = true;
+            if (m + 1 < n) {
+                const int s1 = (i + 1) & 1;
+                next_ok = mbar_wait_bounded(&sbar[s1], (uint32_t)(((i + 1) >> 1) & 1), hk.spin);
+                ksum = tier_sum(sm.st[s1], sm.st[s1] + kPlane);
+                sm.ks[s1][tid] = ksum;
+            }
             tmem_wait_st();
             fence_proxy_async();  // stage s fully read before it is refilled by TMA
-            if (!__syncthreads_and(stage_ok)) {
+            if (!__syncthreads_and(stage_ok && next_ok)) {
                 failed = true;
                 break;
             }
@@ -553,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < kM; ++k) {
             const int y = ys + k;
             float gv[8];
-            if (!frz) tmem_ld8(tbase + 16 * k + 8, gv);  // a frozen tile adds nothing to dL/dq
+            tmem_ld8(tbase + 16 * k + 8, gv);
             const int gr = r0 + y, gc = c0 + x;
             if (xint && y >= kHalo && y < kRT - kHalo && gr < H && gc < pitch) {
                 const size_t j = (size_t)gr * pitch + gc;
@@ -562,10 +497,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 sig_out[j] = (uint8_t)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
                 // fire-and-forget reductions (no load round trip); each cell receives
                 // exactly one add per launch, so the result does not depend on timing
-                if (!frz) {
 #pragma unroll
-                    for (int d = 0; d < 8; ++d) atomicAdd(Gq + d * gplane + j, gv[d]);
-                }
+                for (int d = 0; d < 8; ++d) atomicAdd(Gq + d * gplane + j, gv[d]);
             }
         }
     }
@@ -578,6 +511,159 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tmem_sync_threads();
     if (warp == 0) tmem_dealloc(tslot, kTmemCols);
+}
+
+// ---------------------------------------------------------------- frozen tiles
+// The tiles the pre-pass lists from the back of the tile list (kTileFrozenBit): the
+// region's state is constant over the launch and b = 0 in it, so sigma(t) = sigma(t + 1),
+// P = 0, every leave-one-out product is 1 and no dL/dq term survives. A step reduces to
+//   l_b,i <- p_c l_b,i + sum_d G_di (l_a + l_b)_(i - dir d),   l_a unchanged,
+// over the sources i, with the targets j = i - dir(d) and the constant coefficients
+// G_di = (1 - a_j) q_dj 2^(64 (sigma_j - sigma_i)) (0 for targets on the region's edge,
+// with a = 0, or outside the grid). This kernel runs them apart from the live tiles: no
+// tensor memory and no cross-lane exchange. The region's q, state and lambda are staged
+// by TMA during the previous tile's steps; G stays in registers and l_a + l_b goes
+// through a zero-bordered shared-memory plane.
+constexpr int kFM = 8;                              // rows per thread
+constexpr int kFThreads = kCT * (kRT / kFM);        // 512
+struct FrozenSmem {
+    float q[8 * kPlane];            // q stage (TMA)
+    float st[2 * kPlane];           // state stage (TMA); then 1 - a and sigma (as int bits) in place
+    float lam[2 * kPlane];          // lambda stage (TMA)
+    float ln[kRT + 2][kCT + 2];     // l_a + l_b of the region; the border stays 0
+};
+
+__global__ void __launch_bounds__(kFThreads, 1)
+    k_adjoint_frozen(const __grid_constant__ CUtensorMap tst, const __grid_constant__ CUtensorMap tst0,
+                     const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tlam, int H,
+                     int pitch, float pc, int zlast, int n, int tiles_x, const int* __restrict__ tiles,
+                     const int* __restrict__ counts, int* __restrict__ work, float* __restrict__ lam_out,
+                     uint8_t* __restrict__ sig_out, int* __restrict__ err, TmaHook hk) {
+    extern __shared__ __align__(128) uint8_t fraw[];
+    FrozenSmem& sm = *reinterpret_cast<FrozenSmem*>(fraw + ((128u - (smem_u32(fraw) & 127u)) & 127u));
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_next;
+    const int nfz = counts[2];
+    int k = blockIdx.x;
+    if (k >= nfz) return;
+    const int tid = threadIdx.x;
+    const int x = tid % kCT;
+    const int ys = (tid / kCT) * kFM;
+    const size_t plane = (size_t)H * pitch;
+    const int cap = tiles_x * ((H + kIR - 1) / kIR);  // the list's capacity
+    const uint32_t bytes = (uint32_t)((8 + 2 + 2) * kPlane * sizeof(float));
+    // thread 0: stage tile list entry k (q, the launch's first state, lambda at t + 1)
+    auto issue = [&](int kk) {
+        const int e = tiles[cap - 1 - kk];
+        int r0, c0;
+        origin(e & kTileIndexMask, tiles_x, r0, c0);
+        // the launch's first state; state 0 when the region has not changed since then
+        const int z = (e & kTileCkptBit) ? 0 : zlast - (n - 1);
+        mbar_arrive_expect_tx(&bar, bytes);
+        if (hk.withhold) return;
+        tma_load_3d(sm.q, &tq, &bar, c0, r0, 0);
+        if (z == 0) tma_load_3d(sm.st, &tst0, &bar, c0, r0, 0);
+        else tma_load_3d(sm.st, &tst, &bar, c0, r0, 2 * z);
+        tma_load_3d(sm.lam, &tlam, &bar, c0, r0, 0);
+    };
+    for (int i = tid; i < (kRT + 2) * (kCT + 2); i += kFThreads) (&sm.ln[0][0])[i] = 0.0f;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        issue(k);
+        s_next = (int)gridDim.x + atomicAdd(work, 1);
+    }
+    __syncthreads();
+    uint32_t parity = 0u;
+    float* stA = sm.st;
+    float* stB = sm.st + kPlane;
+    while (k < nfz) {
+        const int next = s_next;  // written before the previous barrier
+        int r0, c0;
+        origin(tiles[cap - 1 - k] & kTileIndexMask, tiles_x, r0, c0);
+        if (!__syncthreads_and(mbar_wait_bounded(&bar, parity, hk.spin))) {
+            if (tid == 0) {
+                atomicExch(err, kErrTmaTimeout);
+                mbar_wait_bounded(&bar, parity, hk.spin);  // the copies in flight get one more budget
+            }
+            return;
+        }
+        parity ^= 1u;
+        // stage -> registers and planes: lambda (0 where a = 0), 1 - a and sigma in place
+        float la[kFM], lb[kFM];
+        uint32_t sgp[kFM / 4] = {};  // sigma of the cells (at t and t + 1 alike), a byte each
+#pragma unroll
+        for (int m = 0; m < kFM; ++m) {
+            const int o = (ys + m) * kCT + x;
+            const float A = stA[o], B = stB[o];
+            const int sg = x_sigma(A, B);
+            const bool lv = sg != kSigmaZero;
+            la[m] = lv ? sm.lam[o] : 0.0f;
+            lb[m] = lv ? sm.lam[kPlane + o] : 0.0f;
+            sgp[m >> 2] |= (uint32_t)sg << (8 * (m & 3));
+            sm.ln[ys + m + 1][x + 1] = la[m] + lb[m];
+            stA[o] = signbit(A) ? -A : ((int32_t)__float_as_uint(B) < 0 ? 1.0f : 1.0f - A);
+            stB[o] = __int_as_float(sg);
+        }
+        __syncthreads();
+        // the coefficients of this thread's sources
+        float G[kFM][8];
+#pragma unroll
+        for (int m = 0; m < kFM; ++m) {
+            const int y = ys + m;
+            const int si = (int)((sgp[m >> 2] >> (8 * (m & 3))) & 0xffu);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const int jy = y - dir_dr(d), jx = x - dir_dc(d);
+                // targets on the region's edge rows and columns contribute nothing
+                const bool inr = jy >= 1 && jy < kRT - 1 && jx >= 1 && jx < kCT - 1;
+                const int oj = inr ? jy * kCT + jx : 0;
+                const int sj = inr ? __float_as_int(stB[oj]) : kSigmaZero;
+                const bool use = si != kSigmaZero && sj != kSigmaZero;
+                G[m][d] = use ? (stA[oj] * sm.q[d * kPlane + oj]) * exp2i(64 * (sj - si)) : 0.0f;
+            }
+        }
+        fence_proxy_async();  // these generic reads of the stages precede the next TMA writes
+        __syncthreads();      // every stage fully read
+        if (tid == 0 && next < nfz) issue(next);
+        // the steps: rows ys-1 .. ys+kFM of l_a + l_b in columns x-1, x, x+1, read, then written
+        for (int s = 0; s < n; ++s) {
+            float w[kFM + 2][3];
+#pragma unroll
+            for (int r = 0; r < kFM + 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) w[r][c] = sm.ln[ys + r][x + c];
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < kFM; ++m) {
+                // target i - dir(d) of source (ys + m, x) sits at window (m + 1 - dr, 1 - dc)
+                float own = 0.0f;
+#pragma unroll
+                for (int d = 0; d < 8; ++d) own = fmaf(G[m][d], w[m + 1 - dir_dr(d)][1 - dir_dc(d)], own);
+                const bool lv = ((sgp[m >> 2] >> (8 * (m & 3))) & 0xffu) != (uint32_t)kSigmaZero;
+                lb[m] = lv ? fmaf(pc, lb[m], own) : 0.0f;
+                sm.ln[ys + m + 1][x + 1] = la[m] + lb[m];
+            }
+            __syncthreads();
+        }
+        // lambda at t0 of the interior (sigma unchanged); a frozen tile adds no dL/dq
+        const int gc = c0 + x;
+        if (x >= kHalo && x < kCT - kHalo && gc < pitch) {
+#pragma unroll
+            for (int m = 0; m < kFM; ++m) {
+                const int y = ys + m, gr = r0 + y;
+                if (y >= kHalo && y < kRT - kHalo && gr < H) {
+                    const size_t j = (size_t)gr * pitch + gc;
+                    lam_out[j] = la[m];
+                    lam_out[plane + j] = lb[m];
+                    sig_out[j] = (uint8_t)((sgp[m >> 2] >> (8 * (m & 3))) & 0xffu);
+                }
+            }
+        }
+        if (tid == 0 && next < nfz) s_next = (int)gridDim.x + atomicAdd(work, 1);
+        __syncthreads();  // s_next
+        k = next;
+    }
 }
 
 // Pre-pass of one adjoint launch: for each tile, whether any cell of its 64 x 64 region
@@ -736,7 +822,9 @@ int adjoint_blocked_configure() {
     static int done = 0;
     if (!done) {
         if (cudaFuncSetAttribute(k_adjoint_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)adjoint_blocked_smem()) != cudaSuccess)
+                                 (int)adjoint_blocked_smem()) != cudaSuccess ||
+            cudaFuncSetAttribute(k_adjoint_frozen, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(FrozenSmem) + 128) != cudaSuccess)
             return -1;
         done = 1;
     }
@@ -749,7 +837,8 @@ void launch_adjoint_tiles(const float* A_latest, int H, int W, int pitch, int n,
                           int* tile_list, int* tile_count, uint8_t* gq_dirty, unsigned long long* skipped,
                           cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
-    cudaMemsetAsync(tile_count, 0, 3 * sizeof(int), s);  // the counts and the adjoint's work counter
+    // the counts and both adjoint kernels' work counters
+    cudaMemsetAsync(tile_count, 0, 4 * sizeof(int), s);
     const int ntiles = adjoint_blocked_tiles(H, pitch);
     k_adjoint_tiles<<<(ntiles + 7) / 8, 256, 0, s>>>(A_latest, H, W, pitch, tiles_x, ntiles, n, tile_list, tile_count,
                                                      lam_out, sig_out, gq_dirty, skipped);
@@ -761,24 +850,29 @@ void launch_adjoint_tiles_flags(const uint8_t* act, int H, int W, int pitch, int
                                 cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC, tiles_y = (H + kIR - 1) / kIR;
     const int ntiles = tiles_x * tiles_y;
-    cudaMemsetAsync(tile_count, 0, 3 * sizeof(int), s);  // the counts and the adjoint's work counter
+    cudaMemsetAsync(tile_count, 0, 4 * sizeof(int), s);  // the counts and both adjoint kernels' work counters
     k_adjoint_tiles_flags<<<(ntiles + 7) / 8, 256, 0, s>>>(act, H, W, pitch, tiles_x, tiles_y, n, tile_list, tile_count,
                                                            lam_out, sig_out, deadcnt, use_frozen ? 1 : 0, gq_dirty,
                                                            skipped, frozen_steps);
 }
 
-void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq, int H, int pitch,
-                            float pc, int zlast,
-                            int n, const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out,
-                            float* Gq, const int* tile_list, int* tile_count, int nsm, int* err, TmaHook hk,
+void launch_adjoint_blocked(const CUtensorMap* tst, const CUtensorMap* tst0, const CUtensorMap* tq,
+                            const CUtensorMap* tlam, int H, int pitch, float pc, int zlast, int n,
+                            const float* lam_in, const uint8_t* sig_in, float* lam_out, uint8_t* sig_out, float* Gq,
+                            const int* tile_list, int* tile_count, int nsm, int* err, TmaHook hk, bool frozen_only,
                             cudaStream_t s) {
     const int tiles_x = (pitch + kIC - 1) / kIC;
     const int ntiles = adjoint_blocked_tiles(H, pitch);
     const int grid = ntiles < nsm ? ntiles : nsm;
-    k_adjoint_blocked<<<grid, kThreads, adjoint_blocked_smem(), s>>>(*tst, *tst0, *tq, H, pitch, pc, zlast, n, tiles_x,
-                                                                     tile_list, tile_count, tile_count + 1, lam_in,
-                                                                     sig_in, lam_out,
-                                                                     sig_out, Gq, err, hk);
+    if (!frozen_only)
+        k_adjoint_blocked<<<grid, kThreads, adjoint_blocked_smem(), s>>>(*tst, *tst0, *tq, H, pitch, pc, zlast, n,
+                                                                         tiles_x, tile_list, tile_count,
+                                                                         tile_count + 1, lam_in, sig_in, lam_out,
+                                                                         sig_out, Gq, err, hk);
+    else
+        k_adjoint_frozen<<<grid, kFThreads, sizeof(FrozenSmem) + 128, s>>>(*tst, *tst0, *tq, *tlam, H, pitch, pc,
+                                                                           zlast, n, tiles_x, tile_list, tile_count,
+                                                                           tile_count + 3, lam_out, sig_out, err, hk);
 }
 
 }  // namespace pf

@@ -433,7 +433,7 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
                                                    float* __restrict__ zero_base, int zero_slots, int frozen,
                                                    uint8_t* __restrict__ out_dirty, int dirty_unknown,
                                                    unsigned long long* __restrict__ skipped, int tile, int lane,
-                                                   unsigned long long& sk) {
+                                                   unsigned long long& sk, unsigned long long& wr) {
     constexpr int kI = kRT - 2 * kHalo;
     const int ty = tile / tiles_x, tx = tile % tiles_x;
     // the 7 x 7 flags around the tile, two per lane (independent loads), reduced into the
@@ -486,7 +486,10 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
                 }
             }
             __syncwarp();
-            if (lane == 0) seg_dirty[tile] = 0;
+            if (lane == 0) {
+                seg_dirty[tile] = 0;
+                wr += (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)zero_slots;
+            }
         }
     } else if (seg_dirty && lane == 0) {
         seg_dirty[tile] = 1;
@@ -517,10 +520,17 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
             *reinterpret_cast<float4*>(out + gplane + j) = z;
         }
     }
+    // In an aligned recompute the tile is frozen in the matching adjoint launch, which
+    // reads its region from the launch's first state only; the other tiles' regions reach
+    // 8 cells into its interior. So slots before the last need only that 8-cell band, and
+    // the last slot (the next launch's input) the whole interior.
+    const bool band_only = frozen && seg_dirty;
+    uint32_t nw = 0u;  // float4 pairs this lane wrote
     if (copy_out || write_all) {
-        // float4 columns: c0 and pitch are multiples of 4
+        // float4 columns: c0 and pitch are multiples of 4 (and 8, kI - 8 are too)
         for (int i = lane; i < kI * (kI / 4); i += 32) {
-            const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
+            const int ir = i / (kI / 4), ic = 4 * (i % (kI / 4));
+            const int gr = r0 + ir, gc = c0 + ic;
             if (gr >= H || gc >= pitch) continue;
             const size_t j = (size_t)gr * pitch + gc;
             const float4 a = __ldg(reinterpret_cast<const float4*>(src + j));
@@ -528,21 +538,29 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
             if (copy_out) {
                 *reinterpret_cast<float4*>(out + j) = a;
                 *reinterpret_cast<float4*>(out + gplane + j) = b;
+                ++nw;
             }
-            if (write_all)
+            if (write_all) {
+                const bool band = ir < 8 || ir >= kI - 8 || ic < 8 || ic >= kI - 8;
                 for (int s = last_only ? n - 1 : 0; s < n; ++s) {
+                    if (band_only && s < n - 1 && !band) continue;
                     float* o = all_out + (size_t)s * all_stride;
                     *reinterpret_cast<float4*>(o + j) = a;
                     *reinterpret_cast<float4*>(o + gplane + j) = b;
+                    ++nw;
                 }
+            }
         }
     }
+    nw = __reduce_add_sync(0xffffffffu, nw);
     __syncwarp();  // qrun[tile] read by every lane before it changes
     if (lane == 0) {
         if (out_dirty && out) out_dirty[tile] = (me & kActA) ? 1 : 0;
         act_out[tile] = (uint8_t)((me & (kActA | kQt)) | qb | (frozen ? kFrozen : 0) | (stale ? kStale : 0));
         qrun[tile] = (uint8_t)min(qr + 1, 255);
         sk = (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)n;
+        // cells this pre-pass wrote into its output buffers (copies and zero fills)
+        wr += 4ull * nw + (zero_out ? (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) : 0ull);
     }
 }
 
@@ -556,17 +574,19 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                                                    uint8_t* __restrict__ seg_dirty, const float* __restrict__ slot0,
                                                    float* __restrict__ zero_base, int zero_slots, int frozen,
                                                    uint8_t* __restrict__ out_dirty, int dirty_unknown,
-                                                   unsigned long long* __restrict__ skipped) {
-    __shared__ unsigned long long s_sk;
-    if (threadIdx.x == 0) s_sk = 0ull;
+                                                   unsigned long long* __restrict__ skipped,
+                                                   unsigned long long* __restrict__ written) {
+    __shared__ unsigned long long s_sk, s_wr;
+    if (threadIdx.x == 0) s_sk = s_wr = 0ull;
     __syncthreads();
-    unsigned long long sk = 0ull;
+    unsigned long long sk = 0ull, wr = 0ull;
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
     if (tile < tiles_x * tiles_y)
         fwd_tile<kHalo>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out, qrun, list, count, out,
                         out_age, all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots, frozen, out_dirty,
-                        dirty_unknown, skipped, tile, threadIdx.x & 31, sk);
+                        dirty_unknown, skipped, tile, threadIdx.x & 31, sk, wr);
     block_count(skipped, s_sk, sk);
+    block_count(written, s_wr, wr);
 }
 
 }  // namespace
@@ -621,7 +641,7 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
                       uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
                       int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, const float* slot0,
                       float* zero_base, int zero_slots, bool frozen, uint8_t* out_dirty, bool dirty_unknown,
-                      unsigned long long* skipped, cudaStream_t s) {
+                      unsigned long long* skipped, unsigned long long* written, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int tiles_y = (H + inner - 1) / inner;
@@ -630,12 +650,14 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
         k_fwd_tiles<4><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          qrun, tile_list, tile_count, out, out_age,
                                                          all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots,
-                                                         frozen ? 1 : 0, out_dirty, dirty_unknown ? 1 : 0, skipped);
+                                                         frozen ? 1 : 0, out_dirty, dirty_unknown ? 1 : 0, skipped,
+                                                         written);
     else
         k_fwd_tiles<8><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          qrun, tile_list, tile_count, out, out_age,
                                                          all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots,
-                                                         frozen ? 1 : 0, out_dirty, dirty_unknown ? 1 : 0, skipped);
+                                                         frozen ? 1 : 0, out_dirty, dirty_unknown ? 1 : 0, skipped,
+                                                         written);
 }
 
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, const PrepArgs* pa, int H, int W,

@@ -34,42 +34,46 @@ __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64
     const uint32_t burning = lanes_eq2(mid);
     const uint32_t active = burning | (nb & lanes_eq1(mid));
     if (active == 0u) return mid;
-    uint32_t out = mid;
+    // 1. per cell that draws: the probability its uniform is compared with (Eq. 9 over
+    //    the burning neighbours for an unburned cell, as P <- P + x (1 - P); p_continue
+    //    for a burning one), q read from the materialised planes or (pa) recomputed from
+    //    the fields with prep's arithmetic
+    float thr[4];
+    uint32_t ign = 0u;  // bytes of the unburned cells among them
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (((active >> (8 * k)) & 1u) == 0u) continue;
-        const uint32_t s = (mid >> (8 * k)) & 0xffu;
+        thr[k] = g.p_continue;
+        if (((active >> (8 * k)) & 1u) == 0u || ((mid >> (8 * k)) & 0xffu) != 1u) continue;
+        ign |= 1u << (8 * k);
+        float qv[8];
+        if (pa) q_cell(*pa, r, col0 + k, qv);
+        float P = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const uint64_t row = dir_dr(d) < 0 ? U : (dir_dr(d) == 0 ? C : D);
+            if ((row >> (8 * (k + 1 + dir_dc(d)))) & 1ull) {
+                const float x = pa ? qv[d] : __ldg(q + (size_t)d * qplane + qoff + k);
+                P = fmaf(x, 1.0f - P, P);
+            }
+        }
+        thr[k] = P;
+    }
+    // 2. the draws, one cell at a time per lane: every lane of a warp with a draw left
+    //    runs the same Philox code together, whichever of its 4 cells it is for
+    uint32_t out = mid;
+    for (uint32_t pend = active; pend != 0u; pend &= pend - 1u) {
+        const int k = (__ffs((int)pend) - 1) >> 3;
         const int col = col0 + k;
         const uint32_t cell = (uint32_t)r * (uint32_t)g.W + (uint32_t)col;
-        uint32_t ns;
-        if (s == 1u) {
-            // Eq. 9 over the burning neighbours, as P <- P + x (1 - P); q read from the
-            // materialised planes, or (pa) recomputed from the fields with prep's arithmetic
-            float qv[8];
-            if (pa) q_cell(*pa, r, col, qv);
-            float P = 0.0f;
-#pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const uint64_t row = dir_dr(d) < 0 ? U : (dir_dr(d) == 0 ? C : D);
-                if ((row >> (8 * (k + 1 + dir_dc(d)))) & 1ull) {
-                    const float x = pa ? qv[d] : __ldg(q + (size_t)d * qplane + qoff + k);
-                    P = fmaf(x, 1.0f - P, P);
-                }
-            }
-            const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
-            const float u = u24(x.x);
-            ns = (u < P) ? 2u : 1u;
-            const bool owned = r >= g.acc_r0 && r < g.acc_r1 && col >= g.acc_c0 && col < g.acc_c1;
-            if (ns == 2u && g.acc && owned)
-                g.acc[((size_t)rr * g.H + r) * g.W + col] = P;  // the accumulator (Sec. 2.2 data flow)
-            ties += (owned && fabsf(u - P) < kNearTie) ? 1u : 0u;
-        } else {
-            const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
-            const float u = u24(x.y);
-            ns = (u < g.p_continue) ? 2u : 3u;
-            const bool owned = r >= g.acc_r0 && r < g.acc_r1 && col >= g.acc_c0 && col < g.acc_c1;
-            ties += (owned && fabsf(u - g.p_continue) < kNearTie) ? 0x10000u : 0u;
-        }
+        const bool unburned = (ign >> (8 * k)) & 1u;
+        const float t = k == 0 ? thr[0] : (k == 1 ? thr[1] : (k == 2 ? thr[2] : thr[3]));
+        const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
+        const float u = u24(unburned ? x.x : x.y);
+        const uint32_t ns = (u < t) ? 2u : (unburned ? 1u : 3u);
+        const bool owned = r >= g.acc_r0 && r < g.acc_r1 && col >= g.acc_c0 && col < g.acc_c1;
+        if (unburned && ns == 2u && g.acc && owned)
+            g.acc[((size_t)rr * g.H + r) * g.W + col] = t;  // the accumulator (Sec. 2.2 data flow)
+        ties += (owned && fabsf(u - t) < kNearTie) ? (unburned ? 1u : 0x10000u) : 0u;
         out = (out & ~(0xffu << (8 * k))) | (ns << (8 * k));
     }
     return out;

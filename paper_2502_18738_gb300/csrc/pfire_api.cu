@@ -3,6 +3,7 @@
 #include <sys/stat.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -46,13 +47,13 @@ thread_local std::string g_last_error = "no error";
 
 enum Kind {
     K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_ATILES, K_FTILES, K_DCA,
-    K_STILES, K_NKINDS
+    K_STILES, K_AFRZ, K_NKINDS
 };
 const char* kKindNames[K_NKINDS] = {"prep",         "discrete_step",    "discrete_blocked",
                                     "diff_step",    "diff_blocked",     "adjoint_step",
                                     "adjoint_blocked", "prep_adjoint",  "reduce_fp64",
                                     "misc",         "adjoint_tiles",    "diff_tiles",
-                                    "dca_step",     "segment_tiles"};
+                                    "dca_step",     "segment_tiles",    "adjoint_frozen"};
 
 struct Epoch {
     int from;
@@ -163,10 +164,10 @@ struct pf_ctx {
     // test hook of the TMA kernels, read from the environment at each forward / backward
     // (PF_TMA_TEST_WITHHOLD, PF_TMA_SPIN_LIMIT)
     TmaHook hook{kSpinLimit, 0};
-    int* tile_list = nullptr;             // live tiles of one blocked-adjoint launch (count: dflags[8], work: [9])
+    int* tile_list = nullptr;             // tiles of one blocked-adjoint launch (counts: dflags[8], [10]; work: [9], [11])
     uint8_t* gqdirty = nullptr;           // per adjoint tile: may hold nonzero dL/dq this epoch
     // tile activity of the blocked forward (b > 0 in a tile's interior), carried along a
-    // chain of launches: act ping-pong, quiescent-last-launch flags, live list (count: dflags[11])
+    // chain of launches: act ping-pong, quiescent-last-launch flags, live list (count: dflags[12])
     uint8_t* fact[2] = {nullptr, nullptr};
     uint8_t* fqrun = nullptr;  // per tile: quiescent streak along the chain (k_fwd_tiles)
     int* flist = nullptr;
@@ -206,6 +207,9 @@ struct pf_ctx {
     const float* seg_slot0 = nullptr;  // the segment's first state (its checkpoint; slot 0 of seg_buf is unused)
     int seg_halo = 0;              // tile geometry seg_dirty refers to
     int TH = 64, KH = 16;
+    // Philox counter words 3 and 1 (base) of the discrete draws: 0 for contexts made by
+    // pf_create; a batch job run through a context of its own uses its fire_id and run
+    uint32_t fire_id = 0, run0 = 0;
     pf_tuning tun{0, 0, 0, 0, 0, 0};
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
@@ -271,7 +275,7 @@ struct LaunchScope {
     LaunchScope(pf_ctx* c_, int k, int steps = 1) : c(c_), kind(k) {
         c->launches[k] += 1;
         if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED && k != K_ATILES && k != K_FTILES &&
-            k != K_DCA && k != K_STILES)
+            k != K_DCA && k != K_STILES && k != K_AFRZ)
             c->cell_steps[k] += (long long)steps * c->H * c->W * (k == K_DSTEP || k == K_DBLK ? c->R : 1);
         if (!c->tun.profile) return;
         cudaEvent_t e0 = take();
@@ -582,15 +586,15 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
         // the pre-pass of a forward launch, or of one recomputing a segment for the adjoint
         LaunchScope ls(ctx, seg ? K_STILES : K_FTILES);
         launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
-                         ctx->fqrun, ctx->flist, ctx->dflags + 11, out, out_age, all_out,
+                         ctx->fqrun, ctx->flist, ctx->dflags + 12, out, out_age, all_out,
                          stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_slot0 : nullptr,
                          seg ? ctx->seg_buf + stride : nullptr,
                          ctx->seg_cap - 1, seg && frozen && halo == 8, dirty, dirty_unknown, ctx->dskip + K_FBLK,
-                         ctx->st);
+                         ctx->dskip + (seg ? K_STILES : K_FTILES), ctx->st);
     }
     {
         LaunchScope ls(ctx, K_FBLK, n);
-        launch_diff_blocked(halo, &tab, &ctx->tmapQ, pa, ctx->H, ctx->W, ctx->P, pc, n, ctx->flist, ctx->dflags + 11, out,
+        launch_diff_blocked(halo, &tab, &ctx->tmapQ, pa, ctx->H, ctx->W, ctx->P, pc, n, ctx->flist, ctx->dflags + 12, out,
                             all_out, stride, ctx->fact[1 - ctx->fl_par], ctx->dskip + K_FBLK, ctx->nsm, ctx->dflags,
                             ctx->hook, ctx->st);
     }
@@ -612,7 +616,7 @@ DiscreteArgs dargs(const pf_ctx* c) {
     g.H = c->H; g.W = c->W; g.pitch = c->P; g.R = c->R;
     g.p_continue = c->pc;
     g.key0 = (uint32_t)c->seed; g.key1 = (uint32_t)(c->seed >> 32);
-    g.fire = 0; g.run0 = 0;
+    g.fire = c->fire_id; g.run0 = c->run0;
     g.acc = c->acc;
     g.acc_r0 = 0; g.acc_r1 = c->H; g.acc_c0 = 0; g.acc_c1 = c->W;
     g.ties = c->dties;
@@ -1774,13 +1778,17 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
                                              ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->tile_list, ctx->dflags + 8,
                                              ctx->gqdirty, ctx->dskip + K_ABLK, ctx->st);
                 }
-                {
-                    LaunchScope ls(ctx, K_ABLK, n);
-                    launch_adjoint_blocked(tmap, tmap0 ? tmap0 : tmap, &ctx->tmapQ, ctx->H, ctx->P, pc, t1 - 1 - tbase,
-                                           n, ctx->lam[lcur],
-                                           ctx->sig[lcur], ctx->lam[1 - lcur], ctx->sig[1 - lcur], ctx->Gq,
-                                           ctx->tile_list, ctx->dflags + 8, ctx->nsm, ctx->dflags, ctx->hook,
-                                           ctx->st);
+                // the live tiles, then the frozen ones (a kernel of their own)
+                CUtensorMap tlam;
+                if (!encode_f32_3d(&tlam, ctx->lam[lcur], ctx->P, ctx->H, 2, diff_blocked_box_cols(),
+                                   diff_blocked_box_rows(), 2))
+                    return fail(ctx, PF_ECUDA, "tensor map encoding of lambda failed");
+                for (int fz = 0; fz < 2; ++fz) {
+                    LaunchScope ls(ctx, fz ? K_AFRZ : K_ABLK, n);
+                    launch_adjoint_blocked(tmap, tmap0 ? tmap0 : tmap, &ctx->tmapQ, &tlam, ctx->H, ctx->P, pc,
+                                           t1 - 1 - tbase, n, ctx->lam[lcur], ctx->sig[lcur], ctx->lam[1 - lcur],
+                                           ctx->sig[1 - lcur], ctx->Gq, ctx->tile_list, ctx->dflags + 8, ctx->nsm,
+                                           ctx->dflags, ctx->hook, fz != 0, ctx->st);
                 }
                 if ((r = check_launch(ctx, "adjoint blocked"))) return r;
                 t1 -= n;
@@ -2493,6 +2501,46 @@ done:
     return rc;
 }
 
+// jobs of at least this many cells run through a context of their own (temporal-blocked
+// kernels) instead of the persistent queue; set by pf_batch_set_direct_cells
+constexpr long long kBatchDirectCellsDefault = 1ll << 18;
+std::atomic<long long> g_batch_direct_cells{kBatchDirectCellsDefault};
+
+// One batch job as a context of its own would run it: the same results as the queue's
+// (the discrete draws use the job's fire_id and run; the differentiable forward uses the
+// same update), with the blocked kernels and the context's automatic tuning.
+static int batch_run_direct(const pf_job& J, int index, cudaStream_t st, std::vector<double>& host_grads) {
+    pf_ctx* c = nullptr;
+    int rc = pf_create(&c, J.H, J.W, J.form, 1, J.seed, st);
+    if (rc) return fail(nullptr, rc, "pf_batch_submit: job %d: %s", index, pf_last_error(nullptr));
+    c->fire_id = J.fire_id;
+    c->run0 = J.run;
+    auto done = [&](int r) {
+        if (r) fail(nullptr, r, "pf_batch_submit: job %d: %s", index, c->err.c_str());
+        pf_destroy(c);
+        return r;
+    };
+    if ((rc = pf_set_env(c, J.E, J.p_veg, J.p_den, J.V_w, J.theta_w))) return done(rc);
+    if ((rc = pf_set_params(c, J.p_h, J.c1, J.c2, J.a, J.p_continue, J.l))) return done(rc);
+    if ((rc = pf_forward(c, J.S_init, J.T, J.S_out))) return done(rc);
+    if (J.dL_da) {
+        double* g = host_grads.data() + 4 * (size_t)index;
+        if ((rc = pf_backward(c, J.dL_da, nullptr, g, J.grad_pveg, J.grad_pden))) return done(rc);
+        if (cudaMemcpyAsync(J.grad_params, g, 4 * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            return done(PF_ECUDA);
+        }
+    }
+    if ((rc = pf_wait(c))) return done(rc);
+    return done(PF_OK);
+}
+
+int pf_batch_set_direct_cells(long long min_cells) {
+    if (min_cells < 0) return fail(nullptr, PF_EINVAL, "pf_batch_set_direct_cells: min_cells must be >= 0");
+    g_batch_direct_cells.store(min_cells);
+    return PF_OK;
+}
+
 int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
     g_batch_stats = pf_batch_stats_t{};
     pf_ctx* ctx = nullptr;  // context-free: errors go to pf_last_error(NULL)
@@ -2512,6 +2560,44 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
             return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: parameter out of range", i);
         if (J.dL_da && (J.form != PF_DIFF || !J.grad_params))
             return fail(nullptr, PF_EINVAL, "pf_batch_submit: job %d: dL_da needs the differentiable form and grad_params", i);
+    }
+    // large jobs through contexts of their own, the rest through the persistent queue
+    const long long direct_cells = g_batch_direct_cells.load();
+    std::vector<pf_job> queued;
+    std::vector<int> direct;
+    for (int i = 0; i < n; ++i) {
+        if ((long long)jobs[i].H * jobs[i].W >= direct_cells) direct.push_back(i);
+        else queued.push_back(jobs[i]);
+    }
+    if (!direct.empty()) {
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        std::vector<double> host_grads(4 * (size_t)n, 0.0);
+        cudaEvent_t d0 = nullptr, d1 = nullptr;
+        const bool timing = cudaEventCreate(&d0) == cudaSuccess && cudaEventCreate(&d1) == cudaSuccess;
+        if (timing) cudaEventRecord(d0, st);
+        int rc = PF_OK;
+        for (int i : direct) {
+            if ((rc = batch_run_direct(jobs[i], i, st, host_grads))) break;
+            pf_batch_stats_t& B = g_batch_stats;
+            const long long cs = (long long)jobs[i].H * jobs[i].W * jobs[i].T;
+            B.direct_jobs += 1;
+            B.direct_cell_steps += cs * (jobs[i].dL_da ? 2 : 1);
+        }
+        if (timing) {
+            cudaEventRecord(d1, st);
+            float ms = 0.f;
+            if (cudaEventSynchronize(d1) == cudaSuccess && cudaEventElapsedTime(&ms, d0, d1) == cudaSuccess)
+                g_batch_stats.ms_direct += ms;
+        }
+        if (d0) cudaEventDestroy(d0);
+        if (d1) cudaEventDestroy(d1);
+        cudaGetLastError();
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == PF_OK)
+            rc = fail(nullptr, PF_ECUDA, "pf_batch_submit: %s", cudaGetErrorString(cudaGetLastError()));
+        if (rc) return rc;
+        if (queued.empty()) return PF_OK;
+        jobs = queued.data();
+        n = (int)queued.size();
     }
     // Device memory of one job in a wave's arena (as batch_submit_wave lays it out): two
     // state buffers, q, the burnable mask, tile counters and, with an adjoint, every

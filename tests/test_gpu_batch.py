@@ -231,3 +231,59 @@ def test_batched_adjoint_matches_per_fire_backward_and_oracle(pf, orc):
                                           np.zeros((H, W)))
         for k in range(4):
             assert g4[k] == pytest.approx(want4[k], rel=1e-3, abs=1e-9)
+
+
+@pytest.mark.parametrize("direct_cells", [0, 5000, 1 << 40])
+def test_direct_and_queued_jobs_give_the_same_results(pf, orc, direct_cells):
+    """pf_batch_submit runs jobs of at least pf_batch_set_direct_cells cells through
+    contexts of their own and the rest through the persistent queue: with every job
+    direct (0), a split (5000 cells) or none (2^40), the discrete fires equal the
+    oracle's (their own fire_id and run words), the differentiable forwards equal the
+    oracle's within the trajectory tolerance and one another bit for bit, and the
+    gradients equal the oracle's (1e-3)."""
+    import torch
+    prm = orc.Params(**PRM)
+    shapes = [(45, 77, 37), (100, 70, 23), (33, 40, 9), (90, 130, 30)]
+    jobs, disc, diff = [], [], []
+    for i, (H, W, T) in enumerate(shapes):
+        land, V, th, S0 = _fire(H, W, 500 + i)
+        q = orc.prep(H, W, land.E, land.p_veg, land.p_den, V, th, prm)
+        jd, od = _job(pf, land, V, th, S0, T, 0, seed=13, run=2 + i, fire_id=40 + i)
+        jobs.append(jd)
+        disc.append((od, orc.forward_discrete(S0, q, prm.p_continue, seed=13, T=T, run0=2 + i, fire=40 + i)))
+        w = torch.from_numpy(np.random.default_rng(i).standard_normal((H, W)).astype(np.float32) * 1e-2).cuda()
+        jc, oc = _job(pf, land, V, th, S0, T, 1, dL_da=w)
+        jobs.append(jc)
+        diff.append((oc, jc, land, V, th, S0, T, w))
+    try:
+        pf.pf_batch_set_direct_cells(direct_cells)
+        pf.pf_batch_submit(jobs)
+        st = pf.pf_batch_last_stats()
+    finally:
+        pf.pf_batch_set_direct_cells(1 << 18)
+    n_direct = sum(1 for H, W, _ in shapes if H * W >= direct_cells) * 2
+    assert st["direct_jobs"] == n_direct
+    for od, ref in disc:
+        assert np.array_equal(od.cpu().numpy(), ref)
+    for oc, jc, land, V, th, S0, T, w in diff:
+        H, W = S0.shape
+        m = pf.FireModel(H, W, 1, 1)
+        set_landscape(m, land, V, th)
+        m.set_params(**PRM)
+        m.set_tuning(kernel=1)
+        assert np.array_equal(oc.cpu().numpy(), m.forward(cuda(S0), T).cpu().numpy())
+        m.close()
+        a, b, tape = orc.diff_forward(land, [(V, th)], [0], prm, S0, T)
+        got = oc.cpu().numpy()
+        assert np.max(np.abs(got[0] - a)) < 1e-4 and np.max(np.abs(got[1] - b)) < 1e-4
+        want4, _, _ = orc.diff_backward(land, [(V, th)], [0], prm, S0, tape, w.cpu().numpy().astype(np.float64),
+                                        np.zeros((H, W)))
+        g4 = jc.grads.cpu().numpy()
+        for k in range(4):
+            assert g4[k] == pytest.approx(want4[k], rel=1e-3, abs=1e-9)
+
+
+def test_direct_cells_is_validated(pf):
+    with pytest.raises(pf.PFireError) as e:
+        pf.pf_batch_set_direct_cells(-1)
+    assert e.value.code == pf.PF_EINVAL

@@ -351,7 +351,11 @@ def test_uneven_batch_of_config4_distribution_matches_per_fire_contexts(pf):
     """Twenty fires drawn like the uneven-batch workload (side log-uniform in [64, 2048],
     T uniform in [100, 1000], 1-5 ignitions, half discrete / half differentiable with an
     adjoint) through one pf_batch_submit: discrete final states equal per-fire contexts
-    bit for bit; differentiable states and gradients equal the plain-kernel contexts'."""
+    bit for bit; differentiable states equal the plain-kernel contexts' bit for bit and
+    their gradients to 2e-5 of the largest component (jobs of 2^18 cells or more run
+    through contexts of their own with the blocked adjoint, whose FP32 sums of dL/dq run in
+    another order than the plain kernel's, as in the blocked-against-plain gradient tests;
+    a small component inherits the rounding of the large terms it is summed from)."""
     import torch
     rng = np.random.default_rng(4)
     jobs, keep = [], []
@@ -380,5 +384,5 @@ def test_uneven_batch_of_config4_distribution_matches_per_fire_contexts(pf):
             ref = m.forward(cuda(S0), T)
             r4, _, _ = m.backward(w, None, per_cell=False)
             assert np.array_equal(out.cpu().numpy(), ref.cpu().numpy())
-            assert np.allclose(j.grads.cpu().numpy(), r4, rtol=1e-6, atol=1e-12)
+            assert np.allclose(j.grads.cpu().numpy(), r4, rtol=2e-5, atol=2e-5 * np.abs(r4).max())
         m.close()

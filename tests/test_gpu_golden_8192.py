@@ -54,9 +54,9 @@ def test_8192_t2000_against_stored_oracle_values(pf):
     # the generators still produce the inputs the values were computed from (sums in
     # FP64 of FP32 fields; a relative slack for the host's libm)
     assert " ".join(f"{r},{c}" for r, c in ign) == " ".join(g["ignitions"])
-    assert float(land.E.astype(np.float64).sum()) == pytest.approx(float(g["E_sum"][0]), rel=1e-9)
-    assert float(winds[0][0].astype(np.float64).sum()) == pytest.approx(float(g["V0_sum"][0]), rel=1e-9)
-    assert float(winds[-1][1].astype(np.float64).sum()) == pytest.approx(float(g["th19_sum"][0]), rel=1e-9)
+    assert float(land.E.astype(np.float64).sum()) == pytest.approx(float(g["E_sum"][0]), rel=1e-6)
+    assert float(winds[0][0].astype(np.float64).sum()) == pytest.approx(float(g["V0_sum"][0]), rel=1e-6)
+    assert float(winds[-1][1].astype(np.float64).sum()) == pytest.approx(float(g["th19_sum"][0]), rel=1e-6)
     S0 = syn.initial_state(land, ign)
     m = pf.FireModel(N, N, pf.PF_DIFF)
     set_landscape(m, land, *winds[0])
