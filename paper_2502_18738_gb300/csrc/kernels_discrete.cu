@@ -24,6 +24,11 @@ __device__ __forceinline__ uint64_t row_burning(uint32_t left, uint32_t mid, uin
 // U/C/D are the burning flags of the rows above / at / below (row_burning layout).
 // ties: near-tie counts of this call's owned cells (ignition in the low 16 bits,
 // continue in the high 16 bits), added to.
+// kLoop: the draws of the word's cells in one loop over its drawing cells, so that every
+// lane of a warp with a draw left runs the same Philox code together, whichever of its 4
+// cells it is for (faster in the plain kernel); else a branch per cell (faster in the
+// blocked kernel, whose words are denser in drawing cells). The same arithmetic either way.
+template <bool kLoop>
 __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64_t C, uint64_t D, int r,
                                                 int col0, size_t qoff, size_t qplane, const float* __restrict__ q,
                                                 const DiscreteArgs& g, uint32_t run, uint32_t step, int rr,
@@ -34,17 +39,11 @@ __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64
     const uint32_t burning = lanes_eq2(mid);
     const uint32_t active = burning | (nb & lanes_eq1(mid));
     if (active == 0u) return mid;
-    // 1. per cell that draws: the probability its uniform is compared with (Eq. 9 over
-    //    the burning neighbours for an unburned cell, as P <- P + x (1 - P); p_continue
-    //    for a burning one), q read from the materialised planes or (pa) recomputed from
-    //    the fields with prep's arithmetic
-    float thr[4];
-    uint32_t ign = 0u;  // bytes of the unburned cells among them
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        thr[k] = g.p_continue;
-        if (((active >> (8 * k)) & 1u) == 0u || ((mid >> (8 * k)) & 0xffu) != 1u) continue;
-        ign |= 1u << (8 * k);
+    // the probability a drawing cell's uniform is compared with: Eq. 9 over the burning
+    // neighbours for an unburned cell, as P <- P + x (1 - P), with q read from the
+    // materialised planes or (pa) recomputed from the fields with prep's arithmetic;
+    // p_continue for a burning one
+    auto threshold = [&](int k) {
         float qv[8];
         if (pa) q_cell(*pa, r, col0 + k, qv);
         float P = 0.0f;
@@ -56,17 +55,12 @@ __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64
                 P = fmaf(x, 1.0f - P, P);
             }
         }
-        thr[k] = P;
-    }
-    // 2. the draws, one cell at a time per lane: every lane of a warp with a draw left
-    //    runs the same Philox code together, whichever of its 4 cells it is for
-    uint32_t out = mid;
-    for (uint32_t pend = active; pend != 0u; pend &= pend - 1u) {
-        const int k = (__ffs((int)pend) - 1) >> 3;
+        return P;
+    };
+    // the draw of cell k against t: its new state, the accumulator and the near-ties
+    auto draw = [&](int k, bool unburned, float t) {
         const int col = col0 + k;
         const uint32_t cell = (uint32_t)r * (uint32_t)g.W + (uint32_t)col;
-        const bool unburned = (ign >> (8 * k)) & 1u;
-        const float t = k == 0 ? thr[0] : (k == 1 ? thr[1] : (k == 2 ? thr[2] : thr[3]));
         const U4 x = philox10(cell, run, step, g.fire, g.key0, g.key1);
         const float u = u24(unburned ? x.x : x.y);
         const uint32_t ns = (u < t) ? 2u : (unburned ? 1u : 3u);
@@ -74,7 +68,33 @@ __device__ __forceinline__ uint32_t update_word(uint32_t mid, uint64_t U, uint64
         if (unburned && ns == 2u && g.acc && owned)
             g.acc[((size_t)rr * g.H + r) * g.W + col] = t;  // the accumulator (Sec. 2.2 data flow)
         ties += (owned && fabsf(u - t) < kNearTie) ? (unburned ? 1u : 0x10000u) : 0u;
-        out = (out & ~(0xffu << (8 * k))) | (ns << (8 * k));
+        return ns;
+    };
+    uint32_t out = mid;
+    if constexpr (kLoop) {
+        float thr[4];
+        uint32_t ign = 0u;  // bytes of the unburned drawing cells
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            thr[k] = g.p_continue;
+            if (((active >> (8 * k)) & 1u) == 0u || ((mid >> (8 * k)) & 0xffu) != 1u) continue;
+            ign |= 1u << (8 * k);
+            thr[k] = threshold(k);
+        }
+        for (uint32_t pend = active; pend != 0u; pend &= pend - 1u) {
+            const int k = (__ffs((int)pend) - 1) >> 3;
+            const float t = k == 0 ? thr[0] : (k == 1 ? thr[1] : (k == 2 ? thr[2] : thr[3]));
+            const uint32_t ns = draw(k, (ign >> (8 * k)) & 1u, t);
+            out = (out & ~(0xffu << (8 * k))) | (ns << (8 * k));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (((active >> (8 * k)) & 1u) == 0u) continue;
+            const bool unburned = ((mid >> (8 * k)) & 0xffu) == 1u;
+            const uint32_t ns = draw(k, unburned, unburned ? threshold(k) : g.p_continue);
+            out = (out & ~(0xffu << (8 * k))) | (ns << (8 * k));
+        }
     }
     return out;
 }
@@ -113,7 +133,7 @@ __global__ void __launch_bounds__(256) k_discrete_step(DiscreteArgs g, const uin
         const uint64_t U = row_burning(ld(r - 1, w - 1), ld(r - 1, w), ld(r - 1, w + 1));
         const uint64_t C = row_burning(ld(r, w - 1), mid, ld(r, w + 1));
         const uint64_t D = row_burning(ld(r + 1, w - 1), ld(r + 1, w), ld(r + 1, w + 1));
-        const uint32_t out = update_word(mid, U, C, D, r, 4 * w, (size_t)r * g.pitch + 4 * w,
+        const uint32_t out = update_word<true>(mid, U, C, D, r, 4 * w, (size_t)r * g.pitch + 4 * w,
                                          (size_t)g.H * g.pitch, q, g, g.run0 + (uint32_t)rr, step, rr, ties,
                                          rc ? &pa : nullptr);
         reinterpret_cast<uint32_t*>(Sn + (size_t)rr * g.H * g.pitch)[(size_t)r * wpr + w] = out;
@@ -221,7 +241,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_discrete_blocked(const __grid_c
                 // states 1/2 exist only inside the grid, so gr/gc are valid whenever a
                 // cell is active; the q offset is formed but only read for such cells
                 const size_t qoff = (size_t)gr * g.pitch + gc;
-                dst[y * kCW + m] = update_word(mid, U, C, D, gr, gc, qoff, qplane, q, ga, g.run0 + (uint32_t)rr, step,
+                dst[y * kCW + m] = update_word<false>(mid, U, C, D, gr, gc, qoff, qplane, q, ga, g.run0 + (uint32_t)rr, step,
                                                rr, ties, kRc ? &pa : nullptr);
             }
             __syncthreads();
