@@ -210,6 +210,9 @@ struct pf_ctx {
     // Philox counter words 3 and 1 (base) of the discrete draws: 0 for contexts made by
     // pf_create; a batch job run through a context of its own uses its fire_id and run
     uint32_t fire_id = 0, run0 = 0;
+    // device memory from this stream-ordered pool (allocations and frees ordered on st,
+    // no device-wide synchronisation), or from cudaMalloc when null
+    cudaMemPool_t pool = nullptr;
     pf_tuning tun{0, 0, 0, 0, 0, 0};
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
@@ -240,13 +243,17 @@ int fail(pf_ctx* c, int code, const char* fmt, ...) {
             return fail(ctx, PF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
     } while (0)
 
+// the pool of the contexts pf_create makes on this thread (the batch's direct jobs)
+thread_local cudaMemPool_t g_ctx_pool = nullptr;
+
 int dalloc(pf_ctx* ctx, void** p, size_t bytes) {
     *p = nullptr;
     ++g_alloc_count;
     const long at = fault_alloc_at();
     if (at > 0 && g_alloc_count == at)
         return fail(ctx, PF_ENOMEM, "injected allocation failure (PF_FAULT_ALLOC=%ld)", at);
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(p, bytes ? bytes : 16, ctx->pool, ctx->st)
+                              : cudaMalloc(p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -260,7 +267,8 @@ void dfree(pf_ctx* ctx, void* p) {
     if (!p) return;
     auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
     if (it != ctx->allocs.end()) ctx->allocs.erase(it);
-    cudaFree(p);
+    if (ctx->pool) cudaFreeAsync(p, ctx->st);
+    else cudaFree(p);
 }
 
 size_t plane_elems(const pf_ctx* c) { return (size_t)c->H * c->P; }
@@ -951,6 +959,7 @@ int pf_create(pf_ctx** out, int H, int W, int form, int realisations, uint64_t s
     if ((uint64_t)H * (uint64_t)W * (uint64_t)realisations >= (1ull << 32))
         return fail(nullptr, PF_EINVAL, "pf_create: H*W*R must be below 2^32");
     pf_ctx* ctx = new pf_ctx();
+    ctx->pool = g_ctx_pool;
     ctx->H = H; ctx->W = W; ctx->P = pitch_of(W); ctx->form = form; ctx->R = realisations;
     ctx->seed = seed;
     ctx->st = (cudaStream_t)cuda_stream;
@@ -1045,7 +1054,10 @@ void pf_destroy(pf_ctx* ctx) {
         cudaEventDestroy(r.e1);
     }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
-    for (void* p : ctx->allocs) cudaFree(p);
+    for (void* p : ctx->allocs) {
+        if (ctx->pool) cudaFreeAsync(p, ctx->st);
+        else cudaFree(p);
+    }
     if (ctx->hflags) cudaFreeHost(ctx->hflags);
     cudaGetLastError();
     delete ctx;
@@ -2572,6 +2584,27 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
     if (!direct.empty()) {
         cudaStream_t st = (cudaStream_t)cuda_stream;
         std::vector<double> host_grads(4 * (size_t)n, 0.0);
+        // the direct jobs' contexts allocate from one stream-ordered pool that keeps what
+        // they free until the last job ends: a job reuses the memory of those before it
+        // instead of allocating and freeing (and synchronising the device) every time
+        cudaMemPool_t pool = nullptr;
+        {
+            int dev = 0;
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            if (cudaGetDevice(&dev) == cudaSuccess) {
+                props.location.id = dev;
+                if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+                    uint64_t keep = ~0ull;
+                    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+                } else {
+                    pool = nullptr;
+                }
+            }
+            cudaGetLastError();
+        }
+        g_ctx_pool = pool;
         cudaEvent_t d0 = nullptr, d1 = nullptr;
         const bool timing = cudaEventCreate(&d0) == cudaSuccess && cudaEventCreate(&d1) == cudaSuccess;
         if (timing) cudaEventRecord(d0, st);
@@ -2592,8 +2625,11 @@ int pf_batch_submit(const pf_job* jobs, int n, void* cuda_stream) {
         if (d0) cudaEventDestroy(d0);
         if (d1) cudaEventDestroy(d1);
         cudaGetLastError();
+        g_ctx_pool = nullptr;
         if (cudaStreamSynchronize(st) != cudaSuccess && rc == PF_OK)
             rc = fail(nullptr, PF_ECUDA, "pf_batch_submit: %s", cudaGetErrorString(cudaGetLastError()));
+        if (pool) cudaMemPoolDestroy(pool);  // every context freed its memory into it
+        cudaGetLastError();
         if (rc) return rc;
         if (queued.empty()) return PF_OK;
         jobs = queued.data();
