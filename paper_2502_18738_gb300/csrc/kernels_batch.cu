@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
         if (J.form == 0) {  // discrete
             const uint8_t* in = (const uint8_t*)J.st[b & 1];
             bool burning = false;
+#pragma unroll 4  // the loads of several iterations in flight together
             for (int i = tid; i < kRR * kRC; i += kBThreads) {
                 const int y = i / kRC, x = i % kRC, gr = r0 + y, gc = c0 + x;
                 const uint8_t v = (gr >= 0 && gr < J.H && gc >= 0 && gc < J.W) ? __ldcg(in + (size_t)gr * J.P + gc) : 0;
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
             uint8_t(&sK)[2][kRR][kRC] = *reinterpret_cast<uint8_t(*)[2][kRR][kRC]>(&sA[1]);
             const float* in = (const float*)J.st[b & 1];
             bool burning = false;
+#pragma unroll 4  // the loads of several iterations in flight together
             for (int i = tid; i < kRR * kRC; i += kBThreads) {
                 const int y = i / kRC, x = i % kRC, gr = r0 + y, gc = c0 + x;
                 const bool inside = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
@@ -260,6 +262,9 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchPlan plan) {
 constexpr int kAR = 16, kAC = 32, kAH = kB + 1;
 constexpr int kARR = kAR + 2 * kAH, kARC = kAC + 2 * kAH;  // 26 x 42
 constexpr int kAThreads = 256;
+constexpr int kTargets = (kARR - 2) * (kARC - 2);                 // targets of a step
+constexpr int kTPT = (kTargets + kAThreads - 1) / kAThreads;       // targets per thread
+constexpr int kSPT = (kARR * kARC + kAThreads - 1) / kAThreads;    // staged cells per thread
 
 struct AdjSmem {
     float mua[kARR][kARC], mub[kARR][kARC];  // scaled lambda (mu) at t + 1, then at t
@@ -366,23 +371,48 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                 sm.sg[y][x] = in ? __ldcg(sin_ + g) : (uint8_t)kSigmaZero;
             }
         }
+        // q of this thread's targets (at most kTPT of them), read once for the item's steps
+        float qt[kTPT][8];
+#pragma unroll
+        for (int u = 0; u < kTPT; ++u) {
+            const int i = tid + u * kAThreads;
+            const int y = 1 + i / (kARC - 2), x = 1 + i % (kARC - 2), gr = r0 + y, gc = c0 + x;
+            const bool ok = i < kTargets && gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
+            const size_t g = ok ? (size_t)gr * J.P + gc : 0;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) qt[u][d] = ok ? __ldg(J.q + d * plane + g) : 0.0f;
+        }
         for (int t = t1 - 1; t >= t0; --t) {
             const float* st = J.tape + (size_t)t * 2 * plane;
-            for (int i = tid; i < kARR * kARC; i += kAThreads) {
+            // the region's state at t (every load of the thread issued before any store)
+            float As_[kSPT], Bs_[kSPT];
+#pragma unroll
+            for (int u = 0; u < kSPT; ++u) {
+                const int i = tid + u * kAThreads;
+                const int y = i / kARC, x = i % kARC, gr = r0 + y, gc = c0 + x;
+                const bool in = i < kARR * kARC && gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
+                const size_t g = in ? (size_t)gr * J.P + gc : 0;
+                As_[u] = in ? __ldcg(st + g) : 0.0f;
+                Bs_[u] = in ? __ldcg(st + plane + g) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < kSPT; ++u) {
+                const int i = tid + u * kAThreads;
+                if (i >= kARR * kARC) continue;
                 const int y = i / kARC, x = i % kARC, gr = r0 + y, gc = c0 + x;
                 const bool in = gr >= 0 && gr < J.H && gc >= 0 && gc < J.W;
-                const size_t g = (size_t)gr * J.P + gc;
-                const float As = in ? __ldcg(st + g) : 0.0f;
-                const float Bs = in ? __ldcg(st + plane + g) : 0.0f;
-                const int sg = in ? x_sigma(As, Bs) : kSigmaZero;
+                const float As = As_[u], Bs = Bs_[u];
                 sm.sa[y][x] = As;
                 sm.sb[y][x] = fmaxf(Bs, 0.0f);
                 sm.sbs[y][x] = fabsf(Bs);
-                sm.ss[y][x] = sg;
+                sm.ss[y][x] = in ? x_sigma(As, Bs) : kSigmaZero;
             }
             __syncthreads();
             // targets j: contributions to their sources and, in the interior, dL/dq
-            for (int i = tid; i < (kARR - 2) * (kARC - 2); i += kAThreads) {
+#pragma unroll
+            for (int u = 0; u < kTPT; ++u) {
+                const int i = tid + u * kAThreads;
+                if (i >= kTargets) continue;
                 const int y = 1 + i / (kARC - 2), x = 1 + i % (kARC - 2), gr = r0 + y, gc = c0 + x;
                 const int sgp = sm.sg[y][x];
                 if (sgp == kSigmaZero || gr < 0 || gr >= J.H || gc < 0 || gc >= J.W) {
@@ -390,11 +420,10 @@ __global__ void __launch_bounds__(kAThreads) k_batch_adj(BatchPlan plan) {
                     for (int d = 0; d < 8; ++d) sm.sc[d][y][x] = 0.0f;
                     continue;
                 }
-                const size_t g = (size_t)gr * J.P + gc;
                 float qd[8], f[8];
 #pragma unroll
                 for (int d = 0; d < 8; ++d) {
-                    qd[d] = __ldg(J.q + d * plane + g);
+                    qd[d] = qt[u][d];
                     f[d] = fmaf(-sm.sb[y + dir_dr(d)][x + dir_dc(d)], qd[d], 1.0f);
                 }
                 float pre[8], suf[8];
