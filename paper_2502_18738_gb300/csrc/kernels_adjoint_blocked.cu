@@ -261,10 +261,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             // Other warps take the general arithmetic, a ratio per transfer.
             uint32_t k0;
             bool uni = window_one_tier(sm.ks[s], tid, x - xl, xr - x, strip > 0, strip < kStrips - 1, kCT, ksum, k0);
+            {
+                // every byte of sigma' in {kSigmaZero, k0, k0 - 1}, four bytes a compare
+                const uint32_t k4 = k0 * 0x01010101u, km4 = ((k0 - 1u) & 0xffu) * 0x01010101u;
 #pragma unroll
-            for (int k = 0; k < kM; ++k) {
-                const int sp = (int)((sgp[k >> 2] >> (8 * (k & 3))) & 0xffu);
-                uni = uni && (sp == kSigmaZero || sp == (int)k0 || sp + 1 == (int)k0);
+                for (int w2 = 0; w2 < 2; ++w2) {
+                    const uint32_t ok = __vcmpeq4(sgp[w2], 0xffffffffu) | __vcmpeq4(sgp[w2], k4) |
+                                        __vcmpeq4(sgp[w2], km4);
+                    uni = uni && ok == 0xffffffffu;
+                }
             }
             const bool slow = !__all_sync(0xffffffffu, uni);
             auto cells = [&](auto tag) {
@@ -348,9 +353,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const float tg = xin ? (kSlow ? ln * ua : (ln * ua) * Up) : 0.0f;
                             // no neighbour with b in tier 0 (b = 0, or a tiered b below 2^-64,
                             // stored negative): every factor 1 - b_i q_dj is exactly 1
-                            bool quiet = true;
+                            float nbmax = nb[0];
 #pragma unroll
-                            for (int d = 0; d < 8; ++d) quiet &= nb[d] <= 0.0f;
+                            for (int d = 1; d < 8; ++d) nbmax = fmaxf(nbmax, nb[d]);
+                            const bool quiet = nbmax <= 0.0f;
                             if (quiet) {
                                 // P = 0 and every leave-one-out product is exactly 1, so t_d = tg:
                                 // the general arithmetic below with its factors folded (the same
@@ -454,6 +460,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // selected rather than branched on: every lane loads them (one address per warp,
             // a broadcast) and keeps its own.
             const int xp = x + 1 < kCT ? x + 1 : x, xm = x >= 1 ? x - 1 : x;
+            // bytes of sigma(t) equal to kSigmaZero (a = 0), as 0xff masks
+            const uint32_t dmask[2] = {__vcmpeq4(sgc[0], 0xffffffffu), __vcmpeq4(sgc[1], 0xffffffffu)};
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 float v = fmaf(pc * scl[k], lb[k], own[k]);
@@ -474,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     v += x >= 1 ? lf : 0.0f;
                 }
                 // a == 0 at t: lambda multiplies only zeros
-                const bool dead = ((sgc[k >> 2] >> (8 * (k & 3))) & 0xffu) == (uint32_t)kSigmaZero;
+                const bool dead = (dmask[k >> 2] >> (8 * (k & 3))) & 1u;
                 lb[k] = dead ? 0.0f : v;
                 la[k] = dead ? 0.0f : la[k];
             }
