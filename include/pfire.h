@@ -229,6 +229,14 @@ int pf_loss_bce_noalloc(const float* a, const float* y, int64_t n, float* dL_da,
  *   tile_rows interior rows per tile of the discrete blocked kernel (16, 32, 64 or 128; 0
  *             = 64); its halo is k rows (16 when k = 0). Ignored by the differentiable
  *             form, whose 64 x 64 regions take a 4-cell halo for k <= 4, else 8.
+ *   tape      differentiable form with checkpoints (K > 1) and the blocked kernels:
+ *             0 = keep a tile tape (every live tile's states of every forward launch)
+ *             so that the backward copies each segment's states instead of recomputing
+ *             them; a segment the tape does not cover is recomputed. The tape takes the
+ *             device memory the backward does not need, less an eighth of the device
+ *             (at least 16 GB) left free, and is kept by the context until pf_destroy;
+ *             the per-epoch q the adjoint would otherwise reuse is not kept then (the
+ *             backward prepares it again). 1 = no tape: always recompute.
  * Results do not depend on any of these (the same arithmetic in every variant), except
  * through K's effect on memory. PF_EINVAL for values out of range. */
 typedef struct pf_tuning {
@@ -238,6 +246,7 @@ typedef struct pf_tuning {
     int profile;
     int prep;
     int tile_rows;
+    int tape;
 } pf_tuning;
 
 int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t);

@@ -56,7 +56,7 @@ class PFireError(RuntimeError):
 
 class PfTuning(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("k", ctypes.c_int), ("K", ctypes.c_int), ("profile", ctypes.c_int),
-                ("prep", ctypes.c_int), ("tile_rows", ctypes.c_int)]
+                ("prep", ctypes.c_int), ("tile_rows", ctypes.c_int), ("tape", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -312,11 +312,11 @@ def pf_loss_bce_noalloc(a, y, dL_da=None, want_loss=True, stream=None):
     return loss.value if want_loss else None
 
 
-def pf_set_tuning(h, kernel=0, k=0, K=0, profile=0, prep=0, tile_rows=0):
+def pf_set_tuning(h, kernel=0, k=0, K=0, profile=0, prep=0, tile_rows=0, tape=0):
     """kernel 1 plain / 2 blocked, k steps per blocked launch, K checkpoint interval,
     profile, prep 1 materialised q / 2 q recomputed in the step kernels, tile_rows of the
-    discrete blocked kernel; 0 = automatic."""
-    t = PfTuning(kernel, k, K, profile, prep, tile_rows)
+    discrete blocked kernel, tape 1 to recompute every segment; 0 = automatic."""
+    t = PfTuning(kernel, k, K, profile, prep, tile_rows, tape)
     _check(load().pf_set_tuning(h, ctypes.byref(t)), h)
 
 

@@ -304,6 +304,8 @@ void launch_prep(const PrepArgs& g, float* q, cudaStream_t s);
 int prep_reach_bytes(int H, int W);
 void launch_prep_reach(const float* ab, int H, int W, int pitch, int radius, uint8_t* tmp, uint8_t* reach,
                        cudaStream_t s);
+// acc |= in over nb mask bytes (the union of two reach masks)
+void launch_reach_or(uint8_t* acc, const uint8_t* in, int nb, cudaStream_t s);
 // dL/dq -> per-block FP64 partials of dL/d(p_h, c1, c2, a) (partials[nblk][4]) and
 // accumulation of per-cell gradients (dense H*W, nullable). Gq is left all zeros.
 int prep_adjoint_blocks(int H, int W);
@@ -397,11 +399,36 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
                       int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, const float* slot0,
                       float* zero_base, int zero_slots, bool frozen, uint8_t* out_dirty, bool dirty_unknown,
                       unsigned long long* skipped, unsigned long long* written, cudaStream_t s);
+// Tile tape of a taped forward: the interior states of every listed (live) tile of a
+// blocked launch, kept so that the adjoint's segment recompute can copy them instead of
+// computing them again. A block is one state of one tile's interior, [2][kI][kI] FP32
+// (kI = the interior side), stored as the launch writes its slots (x_encode form). The
+// blocks of a launch are base + li * n + s (li: the tile's index in the launch's list,
+// s: its step); `used` (device) is the number of blocks taken so far.
+struct TileTape {
+    float* data;                        // NULL: no tape
+    unsigned long long* used;
+    unsigned long long cap;             // blocks
+};
 // pa: NULL = q staged from the planes of tq; else q recomputed in the kernel from pa's fields
+// tape (data NULL: none): the launch's live tiles' states are also written as blocks
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, const PrepArgs* pa, int H, int W,
                          int pitch, float pc, int n, const int* tile_list, int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
-                         TmaHook hk, cudaStream_t s);
+                         TmaHook hk, TileTape tape, cudaStream_t s);
+// After a taped launch: meta[4 L ..] = {base, n, count, ok} of launch record L (ok: every
+// block fitted), the list copied to lists + L * list_cap, and tape.used advanced.
+void launch_tape_record(TileTape tape, const int* tile_count, const int* tile_list, int n, int L,
+                        unsigned long long* meta, int* lists, int list_cap, cudaStream_t s);
+// A segment recompute launch of n steps from the tape instead of k_diff_blocked: for every
+// tile of the recompute's list, its n states from the blocks of record {base, n_rec,
+// count} (inv: tile -> index in the record's list, built here from rec_list) into
+// all_out's slots, and its activity after the launch into act_out (kQb kept), as
+// k_diff_blocked writes them. A listed tile missing from the record adds to *missing.
+void launch_tape_unpack(int halo, const float* tape_data, unsigned long long base, int n_rec, int rec_count,
+                        const int* rec_list, int* inv, int ntiles, const int* tile_list, const int* tile_count,
+                        int n, int H, int pitch, float* all_out, size_t all_stride, uint8_t* act_out, int* missing,
+                        cudaStream_t s);
 // lam: scaled adjoint (mu_a, mu_b) [2][H][pitch]; sig: its exponents uint8 [H][pitch]
 void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float* ab, const float* q,
                          const float* lam1, const uint8_t* sig1, float* lam0, uint8_t* sig0, float* Gq,

@@ -57,9 +57,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const int* __restrict__ ntiles_live, int* __restrict__ work, float* __restrict__ out,
                    float* __restrict__ all_out,
                    size_t all_stride, uint8_t* __restrict__ act_out, unsigned long long* __restrict__ skipped,
-                   int* __restrict__ err, TmaHook hk) {
+                   int* __restrict__ err, TmaHook hk, TileTape tape) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    constexpr int kI = kRT - 2 * kHalo;  // interior side (a tape block is [2][kI][kI])
+    const unsigned long long tbase = tape.data ? *tape.used : 0ull;
     __shared__ __align__(8) uint64_t bar;
     // the list index of this CTA's next tile: tiles are handed out dynamically (the first
     // is blockIdx.x, then work counter claims), one tile ahead for the TMA prefetch
@@ -312,6 +314,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                             x_encode(A[m], sm.b[cur][y * kCT + x], nib == 15u ? 0 : (int)nib, As, Bs);
                             o[(size_t)gr * pitch + gc] = As;
                             o[gplane + (size_t)gr * pitch + gc] = Bs;
+                        }
+                    }
+                }
+            }
+            if (tape.data) {  // the tile tape: this state of a live tile as a block
+                const unsigned long long blk = tbase + (unsigned long long)li * n + s;
+                const int gc = c0 + x;
+                if (blk < tape.cap && x >= kHalo && x < kCT - kHalo && gc < pitch) {
+                    float* o = tape.data + blk * (2ull * kI * kI);
+#pragma unroll
+                    for (int m = 0; m < kM; ++m) {
+                        const int y = ys + m, gr = r0 + y;
+                        if (y >= kHalo && y < kRT - kHalo && gr < H) {
+                            float As, Bs;
+                            const uint32_t nib = (kword >> (4 * m)) & 15u;
+                            x_encode(A[m], sm.b[cur][y * kCT + x], nib == 15u ? 0 : (int)nib, As, Bs);
+                            const int o_ = (y - kHalo) * kI + (x - kHalo);
+                            o[o_] = As;
+                            o[kI * kI + o_] = Bs;
                         }
                     }
                 }
@@ -589,6 +610,83 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
     block_count(written, s_wr, wr);
 }
 
+// After a taped launch (one block of 256 threads): the launch's record and list.
+__global__ void __launch_bounds__(256) k_tape_record(TileTape tape, const int* __restrict__ tile_count,
+                                                     const int* __restrict__ tile_list, int n, int L,
+                                                     unsigned long long* __restrict__ meta, int* __restrict__ lists,
+                                                     int list_cap) {
+    const unsigned long long count = (unsigned long long)*tile_count;
+    const unsigned long long base = *tape.used;
+    const bool ok = base + count * (unsigned long long)n <= tape.cap;
+    __syncthreads();  // every thread has read tape.used before thread 0 advances it
+    if (threadIdx.x == 0) {
+        meta[4 * L + 0] = base;
+        meta[4 * L + 1] = (unsigned long long)n;
+        meta[4 * L + 2] = count;
+        meta[4 * L + 3] = ok ? 1ull : 0ull;
+        if (ok) *tape.used = base + count * (unsigned long long)n;
+    }
+    if (ok)
+        for (unsigned long long i = threadIdx.x; i < count; i += 256) lists[(size_t)L * list_cap + i] = tile_list[i];
+}
+
+// inv[tile] = its index in a record's list (inv holds -1 elsewhere)
+__global__ void __launch_bounds__(256) k_tape_inv(const int* __restrict__ rec_list, int rec_count,
+                                                  int* __restrict__ inv) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i < rec_count) inv[rec_list[i]] = i;
+}
+
+// One block per entry of the recompute's list: the tile's n states from the tape into
+// the segment slots, and its activity after the launch (as k_diff_blocked writes it).
+template <int kHalo>
+__global__ void __launch_bounds__(256) k_tape_unpack(const float* __restrict__ tape_data, unsigned long long base,
+                                                     int n_rec, const int* __restrict__ inv,
+                                                     const int* __restrict__ tile_list,
+                                                     const int* __restrict__ tile_count, int n, int H, int pitch,
+                                                     int tiles_x, float* __restrict__ all_out, size_t all_stride,
+                                                     uint8_t* __restrict__ act_out, int* __restrict__ missing) {
+    constexpr int kI = kRT - 2 * kHalo;
+    __shared__ int s_any[2];
+    if ((int)blockIdx.x >= *tile_count) return;
+    const int tile = tile_list[blockIdx.x];
+    const int li = inv[tile];
+    if (li < 0) {  // not in the record: the caller recomputes the segment
+        if (threadIdx.x == 0) atomicAdd(missing, 1);
+        return;
+    }
+    if (threadIdx.x == 0) s_any[0] = s_any[1] = 0;
+    __syncthreads();
+    const int ty = tile / tiles_x, tx = tile % tiles_x;
+    const int r0 = ty * kI, c0 = tx * kI;
+    const size_t gplane = (size_t)H * pitch;
+    int anyA = 0, anyB = 0;
+    for (int st = 0; st < n; ++st) {
+        const float* src = tape_data + (base + (unsigned long long)li * n_rec + st) * (2ull * kI * kI);
+        float* o = all_out + (size_t)st * all_stride;
+        // float4 columns: c0 and pitch are multiples of 4
+        for (int i = threadIdx.x; i < kI * (kI / 4); i += 256) {
+            const int ir = i / (kI / 4), ic = 4 * (i % (kI / 4));
+            const int gr = r0 + ir, gc = c0 + ic;
+            if (gr >= H || gc >= pitch) continue;
+            const float4 a = *reinterpret_cast<const float4*>(src + ir * kI + ic);
+            const float4 b = *reinterpret_cast<const float4*>(src + kI * kI + ir * kI + ic);
+            const size_t j = (size_t)gr * pitch + gc;
+            *reinterpret_cast<float4*>(o + j) = a;
+            *reinterpret_cast<float4*>(o + gplane + j) = b;
+            if (st == n - 1) {
+                anyA |= (__float_as_uint(a.x) | __float_as_uint(a.y) | __float_as_uint(a.z) | __float_as_uint(a.w)) != 0u;
+                anyB |= b.x != 0.0f || b.y != 0.0f || b.z != 0.0f || b.w != 0.0f;
+            }
+        }
+    }
+    if (anyA) s_any[0] = 1;
+    if (anyB) s_any[1] = 1;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        act_out[tile] = (uint8_t)((act_out[tile] & kQb) | (s_any[0] ? kActA : 0) | (s_any[1] ? kActB : 0));
+}
+
 }  // namespace
 
 int diff_blocked_halo() { return kHaloMax; }
@@ -663,7 +761,7 @@ void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n,
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, const PrepArgs* pa, int H, int W,
                          int pitch, float pc, int n, const int* tile_list, int* tile_count, float* out, float* all_out,
                          size_t all_stride, uint8_t* act_out, unsigned long long* skipped, int nsm, int* err,
-                         TmaHook hk, cudaStream_t s) {
+                         TmaHook hk, TileTape tape, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     const int ntiles = diff_blocked_tiles(halo, H, pitch);
@@ -672,13 +770,39 @@ void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq
 #define PF_DIFF_BLOCKED(HALO, RC)                                                                                   \
     k_diff_blocked<HALO, RC><<<grid, kThreads, diff_blocked_smem(), s>>>(*tab, *tq, g, H, pitch, W, pc, n, tiles_x, \
                                                                           tile_list, tile_count, tile_count + 1, out, \
-                                                                          all_out, all_stride, act_out, skipped, err, hk)
+                                                                          all_out, all_stride, act_out, skipped, err, hk, \
+                                                                          tape)
     if (halo == 4) {
         if (pa) PF_DIFF_BLOCKED(4, true); else PF_DIFF_BLOCKED(4, false);
     } else {
         if (pa) PF_DIFF_BLOCKED(8, true); else PF_DIFF_BLOCKED(8, false);
     }
 #undef PF_DIFF_BLOCKED
+}
+
+}  // namespace pf
+
+namespace pf {
+
+void launch_tape_record(TileTape tape, const int* tile_count, const int* tile_list, int n, int L,
+                        unsigned long long* meta, int* lists, int list_cap, cudaStream_t s) {
+    k_tape_record<<<1, 256, 0, s>>>(tape, tile_count, tile_list, n, L, meta, lists, list_cap);
+}
+
+void launch_tape_unpack(int halo, const float* tape_data, unsigned long long base, int n_rec, int rec_count,
+                        const int* rec_list, int* inv, int ntiles, const int* tile_list, const int* tile_count,
+                        int n, int H, int pitch, float* all_out, size_t all_stride, uint8_t* act_out, int* missing,
+                        cudaStream_t s) {
+    const int inner = kRT - 2 * halo;
+    const int tiles_x = (pitch + inner - 1) / inner;
+    cudaMemsetAsync(inv, 0xff, sizeof(int) * (size_t)ntiles, s);
+    if (rec_count > 0) k_tape_inv<<<(rec_count + 255) / 256, 256, 0, s>>>(rec_list, rec_count, inv);
+    if (halo == 4)
+        k_tape_unpack<4><<<ntiles, 256, 0, s>>>(tape_data, base, n_rec, inv, tile_list, tile_count, n, H, pitch,
+                                                tiles_x, all_out, all_stride, act_out, missing);
+    else
+        k_tape_unpack<8><<<ntiles, 256, 0, s>>>(tape_data, base, n_rec, inv, tile_list, tile_count, n, H, pitch,
+                                                tiles_x, all_out, all_stride, act_out, missing);
 }
 
 }  // namespace pf

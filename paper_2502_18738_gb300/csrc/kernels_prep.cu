@@ -59,6 +59,12 @@ __global__ void __launch_bounds__(256) k_reach_dilate(const uint8_t* __restrict_
     out[i] = v;
 }
 
+// acc[B] |= in[B] over nb bytes
+__global__ void __launch_bounds__(256) k_reach_or(uint8_t* __restrict__ acc, const uint8_t* __restrict__ in, int nb) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i < nb) acc[i] |= in[i];
+}
+
 constexpr int kAdjThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -179,6 +185,10 @@ void launch_prep_reach(const float* ab, int H, int W, int pitch, int radius, uin
     k_reach_any<<<(nb + 7) / 8, 256, 0, s>>>(ab, H, W, pitch, bw, nb, reach);
     k_reach_dilate<<<(nb + 255) / 256, 256, 0, s>>>(reach, tmp, bh, bw, radius, 1);
     k_reach_dilate<<<(nb + 255) / 256, 256, 0, s>>>(tmp, reach, bh, bw, radius, 0);
+}
+
+void launch_reach_or(uint8_t* acc, const uint8_t* in, int nb, cudaStream_t s) {
+    if (nb > 0) k_reach_or<<<(nb + 255) / 256, 256, 0, s>>>(acc, in, nb);
 }
 
 void launch_prep(const PrepArgs& g, float* q, cudaStream_t s) {

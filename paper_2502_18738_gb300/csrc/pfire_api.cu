@@ -47,13 +47,14 @@ thread_local std::string g_last_error = "no error";
 
 enum Kind {
     K_PREP, K_DSTEP, K_DBLK, K_FSTEP, K_FBLK, K_ADJ, K_ABLK, K_PADJ, K_RED, K_MISC, K_ATILES, K_FTILES, K_DCA,
-    K_STILES, K_AFRZ, K_NKINDS
+    K_STILES, K_AFRZ, K_TUNPACK, K_NKINDS
 };
 const char* kKindNames[K_NKINDS] = {"prep",         "discrete_step",    "discrete_blocked",
                                     "diff_step",    "diff_blocked",     "adjoint_step",
                                     "adjoint_blocked", "prep_adjoint",  "reduce_fp64",
                                     "misc",         "adjoint_tiles",    "diff_tiles",
-                                    "dca_step",     "segment_tiles",    "adjoint_frozen"};
+                                    "dca_step",     "segment_tiles",    "adjoint_frozen",
+                                    "segment_from_tape"};
 
 struct Epoch {
     int from;
@@ -120,6 +121,12 @@ struct pf_ctx {
     std::vector<int> qcache_until;
     int q_until = 0x7fffffff;
     uint8_t* qreach = nullptr;  // reach mask and its scratch (2 x prep_reach_bytes)
+    // a taped forward without the q cache: the union of the reach masks each epoch's q
+    // was computed under (qmasks[e * prep_reach_bytes ..]), so that the adjoint recomputes
+    // q in the same blocks; qmask_state[e] 0 none, 1 masked, 2 every cell
+    uint8_t* qmasks = nullptr;
+    int qmasks_cap = 0;  // epochs
+    std::vector<int> qmask_state;
     bool qcache_on = false;
     long q_key_epoch = -1;
     long q_key_version = -1;
@@ -206,6 +213,20 @@ struct pf_ctx {
     uint8_t* seg_dirty = nullptr;  // per forward tile: its interior may be nonzero in slots 1.. of seg_buf
     const float* seg_slot0 = nullptr;  // the segment's first state (its checkpoint; slot 0 of seg_buf is unused)
     int seg_halo = 0;              // tile geometry seg_dirty refers to
+    // tile tape of a checkpointed taped forward (TileTape in common.cuh): the live tiles'
+    // states of every blocked launch, so that the backward copies a segment's states
+    // instead of recomputing them; records (t0, n) of this tape's launches, their device
+    // records {base, n, count, ok} and lists
+    float* ttape = nullptr;
+    unsigned long long ttape_cap = 0;      // blocks
+    unsigned long long* ttape_used = nullptr;
+    unsigned long long* ttape_meta = nullptr;
+    int* ttape_lists = nullptr;
+    int* ttape_inv = nullptr;
+    int ttape_rec_cap = 0;
+    std::vector<std::pair<int, int>> ttape_rec;
+    std::vector<unsigned long long> ttape_meta_h;  // host copy of the records (backward)
+    bool ttape_on = false;
     int TH = 64, KH = 16;
     // Philox counter words 3 and 1 (base) of the discrete draws: 0 for contexts made by
     // pf_create; a batch job run through a context of its own uses its fire_id and run
@@ -213,7 +234,7 @@ struct pf_ctx {
     // device memory from this stream-ordered pool (allocations and frees ordered on st,
     // no device-wide synchronisation), or from cudaMalloc when null
     cudaMemPool_t pool = nullptr;
-    pf_tuning tun{0, 0, 0, 0, 0, 0};
+    pf_tuning tun{0, 0, 0, 0, 0, 0, 0};
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
     long long launches[K_NKINDS] = {0};
@@ -283,7 +304,7 @@ struct LaunchScope {
     LaunchScope(pf_ctx* c_, int k, int steps = 1) : c(c_), kind(k) {
         c->launches[k] += 1;
         if (k != K_MISC && k != K_PREP && k != K_PADJ && k != K_RED && k != K_ATILES && k != K_FTILES &&
-            k != K_DCA && k != K_STILES && k != K_AFRZ)
+            k != K_DCA && k != K_STILES && k != K_AFRZ && k != K_TUNPACK)
             c->cell_steps[k] += (long long)steps * c->H * c->W * (k == K_DSTEP || k == K_DBLK ? c->R : 1);
         if (!c->tun.profile) return;
         cudaEvent_t e0 = take();
@@ -411,6 +432,43 @@ int use_q_buffer(pf_ctx* ctx, float* buf) {
     return PF_OK;
 }
 
+// Record, for the adjoint of a taped forward that keeps no q cache, which blocks the prep
+// of epoch e just computed: the reach mask in ctx->qreach (masked) or every cell.
+int qmask_record(pf_ctx* ctx, int e, bool masked) {
+    if (!ctx->tape_valid || ctx->qcache_on || ctx->version != ctx->t_version || e < 0) return PF_OK;
+    const int ne = (int)ctx->winds.size();
+    if (e >= ne) return PF_OK;
+    if ((int)ctx->qmask_state.size() < ne) ctx->qmask_state.resize(ne, 0);
+    int& st = ctx->qmask_state[e];
+    if (!masked || st == 2) {
+        st = 2;
+        return PF_OK;
+    }
+    const int nb = prep_reach_bytes(ctx->H, ctx->W);
+    if (ctx->qmasks_cap < ne) {
+        if (ctx->qmasks) dfree(ctx, ctx->qmasks);
+        ctx->qmasks = nullptr;
+        ctx->qmasks_cap = 0;
+        void* p;
+        if (dalloc(ctx, &p, (size_t)nb * ne) != PF_OK) {
+            cudaGetLastError();
+            st = 2;  // no record: the adjoint computes every cell
+            return PF_OK;
+        }
+        ctx->qmasks = (uint8_t*)p;
+        ctx->qmasks_cap = ne;
+        for (int k = 0; k < ne; ++k)  // the old records went with the old buffer
+            if (ctx->qmask_state[k] == 1 && k != e) ctx->qmask_state[k] = 2;
+    }
+    uint8_t* m = ctx->qmasks + (size_t)e * nb;
+    if (st == 0)
+        CK(cudaMemcpyAsync(m, ctx->qreach, (size_t)nb, cudaMemcpyDeviceToDevice, ctx->st));
+    else
+        launch_reach_or(m, ctx->qreach, nb, ctx->st);
+    st = 1;
+    return check_launch(ctx, "reach mask record");
+}
+
 // q of wind epoch e, valid for the steps before `until` of the current trajectory. In the
 // differentiable form a bounded `until` lets prep skip the cells nothing reads before
 // then: the region a > 0 grows by at most one cell per step, and every kernel reads q
@@ -465,6 +523,7 @@ int ensure_q(pf_ctx* ctx, int e, int until = 0x7fffffff) {
     }
     rc = check_launch(ctx, "prep");
     if (rc) return rc;
+    if ((rc = qmask_record(ctx, e, masked))) return rc;
     if (dst != ctx->q_own) {
         ctx->qcache_ver[e] = ctx->version;
         ctx->qcache_until[e] = until;
@@ -555,9 +614,13 @@ uint8_t* ckpt_dirty_bits(pf_ctx* ctx, int s, int* rc) {
     return ctx->ckdirty + nt * (size_t)s;
 }
 
+// A launch of the blocked forward from `in` (n steps). rec >= 0 (a segment recompute):
+// the states of the listed tiles come from tile-tape record rec instead of the kernel.
+// record (a taped forward with the tile tape on): the listed tiles' states are also
+// written into the tape, as a new record.
 int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* out, float* all_out,
                         bool seg = false, int end_step = -1, bool frozen = false, const PrepArgs* pa = nullptr,
-                        int ckpt_slot = -1) {
+                        int ckpt_slot = -1, int rec = -1, bool record = false) {
     CUtensorMap tab;
     if (!encode_f32_3d(&tab, in, ctx->P, ctx->H, 2, diff_blocked_box_cols(), diff_blocked_box_rows(), 2))
         return fail(ctx, PF_ECUDA, "tensor map encoding of the state buffer failed");
@@ -597,14 +660,31 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
                          ctx->fqrun, ctx->flist, ctx->dflags + 12, out, out_age, all_out,
                          stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_slot0 : nullptr,
                          seg ? ctx->seg_buf + stride : nullptr,
-                         ctx->seg_cap - 1, seg && frozen && halo == 8, dirty, dirty_unknown, ctx->dskip + K_FBLK,
-                         ctx->dskip + (seg ? K_STILES : K_FTILES), ctx->st);
+                         ctx->seg_cap - 1, seg && frozen && halo == 8, dirty, dirty_unknown,
+                         ctx->dskip + (rec >= 0 ? K_TUNPACK : K_FBLK), ctx->dskip + (seg ? K_STILES : K_FTILES),
+                         ctx->st);
     }
-    {
+    if (rec >= 0) {
+        LaunchScope ls(ctx, K_TUNPACK);
+        const unsigned long long* m = &ctx->ttape_meta_h[4 * (size_t)rec];
+        const size_t nt = (size_t)diff_blocked_tiles(halo, ctx->H, ctx->P);
+        launch_tape_unpack(halo, ctx->ttape, m[0], (int)m[1], (int)m[2], ctx->ttape_lists + nt * (size_t)rec,
+                           ctx->ttape_inv, (int)nt, ctx->flist, ctx->dflags + 12, n, ctx->H, ctx->P, all_out, stride,
+                           ctx->fact[1 - ctx->fl_par], ctx->dflags + 14, ctx->st);
+    } else {
         LaunchScope ls(ctx, K_FBLK, n);
+        const TileTape tape{record ? ctx->ttape : nullptr, ctx->ttape_used, ctx->ttape_cap};
         launch_diff_blocked(halo, &tab, &ctx->tmapQ, pa, ctx->H, ctx->W, ctx->P, pc, n, ctx->flist, ctx->dflags + 12, out,
                             all_out, stride, ctx->fact[1 - ctx->fl_par], ctx->dskip + K_FBLK, ctx->nsm, ctx->dflags,
-                            ctx->hook, ctx->st);
+                            ctx->hook, tape, ctx->st);
+    }
+    if (record) {
+        LaunchScope ls(ctx, K_MISC);
+        const int L = (int)ctx->ttape_rec.size();
+        const int nt = diff_blocked_tiles(halo, ctx->H, ctx->P);
+        launch_tape_record(TileTape{ctx->ttape, ctx->ttape_used, ctx->ttape_cap}, ctx->dflags + 12, ctx->flist, n, L,
+                           ctx->ttape_meta, ctx->ttape_lists, nt, ctx->st);
+        ctx->ttape_rec.push_back({ctx->step, n});
     }
     ctx->fl_par ^= 1;
     ctx->fl_state = out ? out : all_out + (size_t)(n - 1) * stride;
@@ -795,8 +875,13 @@ int diff_steps(pf_ctx* ctx, int T) {
             return rc;
         }
         int n = 1;
+        // with the tile tape, launches of the adjoint's chunk from every checkpoint, as the
+        // backward's recompute launches them (so that a record covers a recompute launch)
+        const bool record = ctx->ttape_on && ctx->tape_valid && !all_states &&
+                            (int)ctx->ttape_rec.size() < ctx->ttape_rec_cap;
         if (kern == 2) {
-            n = std::min({blocked_k(ctx), end - t, next_epoch_start(ctx, t) - t});
+            n = std::min({record ? std::min(blocked_k(ctx), adjoint_blocked_max_steps()) : blocked_k(ctx), end - t,
+                          next_epoch_start(ctx, t) - t});
             if (!all_states) n = std::min(n, steps_to_ckpt(ctx, t));
         }
         float* out = nullptr;
@@ -825,7 +910,8 @@ int diff_steps(pf_ctx* ctx, int T) {
         }
         if (kern == 2) {
             if ((rc = diff_blocked_launch(ctx, ctx->cur_ab, ctx->pc, n, out, all_out, false,
-                                          all_states ? t + n : -1, false, rcq ? &pa : nullptr, ckpt_slot)))
+                                          all_states ? t + n : -1, false, rcq ? &pa : nullptr, ckpt_slot, -1,
+                                          record)))
                 return rc;
             if (ckpt_slot >= 0 && (rc = save_ckpt_flags(ctx, ckpt_slot))) return rc;
         } else {
@@ -848,6 +934,8 @@ int diff_steps(pf_ctx* ctx, int T) {
 
 void tape_reset(pf_ctx* ctx) {
     ctx->tape_valid = false;
+    ctx->ttape_on = false;
+    ctx->ttape_rec.clear();
     ctx->actrec_on = false;
     ctx->actrec_end.clear();
     ctx->ckpts.clear();
@@ -861,11 +949,95 @@ void tape_reset(pf_ctx* ctx) {
     ctx->arena_used = 0;
 }
 
+// The tile tape of a checkpointed blocked run (pf_tuning.tape 0): blocks for the live
+// tiles' states in the memory the backward does not need (its segment buffer, lambda,
+// sigma and dL/dq are counted out) less an eighth of the device (at least 16 GB) left
+// to the caller, records for up to T launches. The per-epoch q cache gives way to it. Without room, or for a
+// run that keeps every state or runs the plain kernels, there is no tape and the backward
+// recomputes its segments.
+int ttape_begin(pf_ctx* ctx, int T) {
+    ctx->ttape_on = false;
+    ctx->ttape_rec.clear();
+    if (ctx->tun.tape == 1 || ctx->K <= 1 || choose_kernel(ctx) != 2 || ctx->tun.prep == 2) return PF_OK;
+    // the tape saves the backward a whole recompute of the forward; the per-epoch q cache
+    // only one prep per epoch: the memory goes to the tape
+    ctx->qcache_on = false;
+    for (float*& b : ctx->qcache)
+        if (b) {
+            if (ctx->q == b) use_q_buffer(ctx, ctx->q_own);
+            dfree(ctx, b);
+            b = nullptr;
+        }
+    for (long& v : ctx->qcache_ver) v = -1;
+    const int halo = blocked_k(ctx) <= 4 ? 4 : 8;
+    const size_t ki = (size_t)(diff_blocked_box_rows() - 2 * halo);
+    const size_t blk = 2 * ki * ki * sizeof(float);
+    const size_t nt = (size_t)diff_blocked_tiles(halo, ctx->H, ctx->P);
+    if (ctx->ttape_rec_cap < T) {
+        for (void* p : {(void*)ctx->ttape_meta, (void*)ctx->ttape_lists})
+            if (p) dfree(ctx, p);
+        ctx->ttape_meta = nullptr;
+        ctx->ttape_lists = nullptr;
+        ctx->ttape_rec_cap = 0;
+        void *pm, *pl;
+        if (dalloc(ctx, &pm, 4 * sizeof(unsigned long long) * (size_t)T) != PF_OK) { cudaGetLastError(); return PF_OK; }
+        ctx->ttape_meta = (unsigned long long*)pm;
+        if (dalloc(ctx, &pl, sizeof(int) * nt * (size_t)T) != PF_OK) { cudaGetLastError(); return PF_OK; }
+        ctx->ttape_lists = (int*)pl;
+        ctx->ttape_rec_cap = T;
+    }
+    if (!ctx->ttape_used) {
+        void *pu, *pi;
+        if (dalloc(ctx, &pu, sizeof(unsigned long long)) != PF_OK) { cudaGetLastError(); return PF_OK; }
+        ctx->ttape_used = (unsigned long long*)pu;
+        if (dalloc(ctx, &pi, sizeof(int) * (size_t)std::max(diff_blocked_tiles(4, ctx->H, ctx->P),
+                                                              diff_blocked_tiles(8, ctx->H, ctx->P))) != PF_OK)
+            { cudaGetLastError(); return PF_OK; }
+        ctx->ttape_inv = (int*)pi;
+    }
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            return PF_OK;
+        }
+        const size_t sb = diff_state_bytes(ctx), pe = plane_elems(ctx);
+        // what the backward allocates later: the segment buffer, lambda and sigma
+        // ping-pong, dL/dq, and a margin; and an eighth of the device (at least 16 GB)
+        // left to the caller. The tape's own memory counts as available.
+        size_t later = (ctx->seg_cap < ctx->K ? (size_t)ctx->K * sb : 0) + 2 * sb + 2 * pe + 8 * pe * sizeof(float) +
+                       ((size_t)2 << 30);
+        if (ctx->lam[0]) later -= std::min(later, 2 * sb + 2 * pe + 8 * pe * sizeof(float));
+        const size_t keep = std::max((size_t)16 << 30, total_b / 8);
+        const size_t avail = free_b + (size_t)ctx->ttape_cap * blk;
+        const size_t cap = avail > later + keep ? (avail - later - keep) / blk : 0;
+        if (ctx->ttape && cap < ctx->ttape_cap) {  // the run needs the memory elsewhere now
+            dfree(ctx, ctx->ttape);
+            ctx->ttape = nullptr;
+            ctx->ttape_cap = 0;
+        }
+        if (cap < nt) return PF_OK;
+        if (!ctx->ttape) {
+            void* p;
+            if (dalloc(ctx, &p, cap * blk) != PF_OK) {
+                cudaGetLastError();
+                return PF_OK;
+            }
+            ctx->ttape = (float*)p;
+            ctx->ttape_cap = cap;
+        }
+    }
+    CK(cudaMemsetAsync(ctx->ttape_used, 0, sizeof(unsigned long long), ctx->st));
+    ctx->ttape_on = true;
+    return PF_OK;
+}
+
 // Start a fresh tape at the current step with the current state as checkpoint 0.
 // The per-epoch q kept for the adjoint belongs to one tape: a new forward recomputes it.
 int tape_begin(pf_ctx* ctx, int T) {
     tape_reset(ctx);
     for (long& v : ctx->qcache_ver) v = -1;
+    for (int& v : ctx->qmask_state) v = 0;
     ctx->q_key_epoch = -1;
     ctx->actrec_end.clear();
     ctx->actrec_on = true;
@@ -885,6 +1057,7 @@ int tape_begin(pf_ctx* ctx, int T) {
     ctx->cur_ab = s0;
     ctx->ckpts.push_back({ctx->step, s});
     ctx->tape_valid = true;
+    if ((rc = ttape_begin(ctx, T))) return rc;
     return PF_OK;
 }
 
@@ -1275,6 +1448,7 @@ int apply_tuning(pf_ctx* ctx, const pf_tuning* t) {
     if (t->k < 0 || t->k > 16) return fail(ctx, PF_EINVAL, "pf_set_tuning: k must be in 0..16");
     if (t->K < 0) return fail(ctx, PF_EINVAL, "pf_set_tuning: K must be >= 0");
     if (t->prep < 0 || t->prep > 2) return fail(ctx, PF_EINVAL, "pf_set_tuning: prep must be 0, 1 or 2");
+    if (t->tape < 0 || t->tape > 1) return fail(ctx, PF_EINVAL, "pf_set_tuning: tape must be 0 or 1");
     if (t->tile_rows != 0 && t->tile_rows != 16 && t->tile_rows != 32 && t->tile_rows != 64 && t->tile_rows != 128)
         return fail(ctx, PF_EINVAL, "pf_set_tuning: tile_rows must be 0, 16, 32, 64 or 128");
     if (ctx->form == PF_DISCRETE) {
@@ -1399,6 +1573,7 @@ int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chos
     if (tune_cache_get(key, &hit) && hit.kernel >= 1) {
         hit.K = saved.K;  // this search leaves K alone
         hit.profile = saved.profile;
+        hit.tape = saved.tape;
         if (apply_tuning(ctx, &hit) == PF_OK) {
             if (chosen) pf_get_tuning(ctx, chosen);
             return PF_OK;
@@ -1411,13 +1586,13 @@ int pf_autotune(pf_ctx* ctx, const uint8_t* S_init, int T_probe, pf_tuning* chos
     // for k <= 4; the discrete one also takes 32, 64 or 128 interior rows per tile)
     std::vector<pf_tuning> cand;
     for (int prep : {1, 2}) {
-        cand.push_back({1, 1, saved.K, saved.profile, prep, 0});
+        cand.push_back({1, 1, saved.K, saved.profile, prep, 0, saved.tape});
         if (ctx->form == PF_DISCRETE) {
             if (ctx->tmap_ok)
                 for (int k : {4, 8, 12})
-                    for (int rows : {32, 64, 128}) cand.push_back({2, k, saved.K, saved.profile, prep, rows});
+                    for (int rows : {32, 64, 128}) cand.push_back({2, k, saved.K, saved.profile, prep, rows, saved.tape});
         } else if (ctx->tmapQ_ok) {
-            for (int k : {2, 4, 6, 8}) cand.push_back({2, k, saved.K, saved.profile, prep, 0});
+            for (int k : {2, 4, 6, 8}) cand.push_back({2, k, saved.K, saved.profile, prep, 0, saved.tape});
         }
     }
     tape_reset(ctx);
@@ -1749,7 +1924,14 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             if ((r = use_q_buffer(ctx, ctx->q_own))) return r;
             {
                 LaunchScope ls(ctx, K_PREP);
-                launch_prep(prep_args(ctx, e, true), ctx->q, ctx->st);
+                PrepArgs g = prep_args(ctx, e, true);
+                // the blocks the taped forward computed (the rest of the buffer keeps
+                // finite q values nothing reads), else every cell
+                if (e < (int)ctx->qmask_state.size() && ctx->qmask_state[e] == 1 && ctx->qmasks) {
+                    g.reach = ctx->qmasks + (size_t)e * prep_reach_bytes(ctx->H, ctx->W);
+                    g.reach_bw = (ctx->W + 31) / 32;
+                }
+                launch_prep(g, ctx->q, ctx->st);
             }
             if ((r = check_launch(ctx, "prep"))) return r;
         }
@@ -1838,6 +2020,21 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
         // the recorded flags of a recompute launch describe an adjoint launch's states
         const int chunk = std::min(blocked_k(ctx), adjoint_blocked_max_steps());
         const bool aligned = kern == 2 && adj_blocked && blocked_k(ctx) > 4;
+        // the tile tape's records, by first step (only complete ones: every block fitted)
+        std::vector<int> rec_at;
+        if (kern == 2 && ctx->ttape_on && !ctx->ttape_rec.empty()) {
+            const size_t nr = ctx->ttape_rec.size();
+            ctx->ttape_meta_h.assign(4 * nr, 0ull);
+            CK(cudaMemcpyAsync(ctx->ttape_meta_h.data(), ctx->ttape_meta, 4 * nr * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaMemsetAsync(ctx->dflags + 14, 0, sizeof(int), ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            rec_at.assign((size_t)(T_end - ctx->tape_start + 1), -1);
+            for (size_t L = 0; L < nr; ++L) {
+                const int t0 = ctx->ttape_rec[L].first - ctx->tape_start;
+                if (ctx->ttape_meta_h[4 * L + 3] && t0 >= 0 && t0 < (int)rec_at.size()) rec_at[t0] = (int)L;
+            }
+        }
         for (int si = (int)ctx->ckpts.size() - 1; si >= 0; --si) {
             const int s0 = ctx->ckpts[si].first;
             const int s1 = (si + 1 < (int)ctx->ckpts.size()) ? ctx->ckpts[si + 1].first : T_end;
@@ -1872,32 +2069,59 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             if (adj_blocked && !encode_f32_3d(&tck, ck, ctx->P, ctx->H, 2, diff_blocked_box_cols(),
                                               diff_blocked_box_rows(), 2))
                 return fail(ctx, PF_ECUDA, "tensor map encoding of a checkpoint failed");
-            ctx->fl_state = nullptr;  // a new chain starts from the checkpoint, with its recorded flags if any
-            {
-                const int cs = ctx->ckpts[si].second;
-                const bool rec = cs < (int)ctx->ckact_halo.size() && ctx->ckact_halo[cs] != 0;
-                const size_t nt = (size_t)std::max(diff_blocked_tiles(8, ctx->H, ctx->P),
-                                                   diff_blocked_tiles(4, ctx->H, ctx->P));
-                ctx->fl_seed = rec ? ctx->ckact + nt * cs : nullptr;
-                ctx->fl_seed_halo = rec ? ctx->ckact_halo[cs] : 0;
-            }
-            ctx->actrec_end.clear();
-            ctx->actrec_on = true;
-            for (int t = s0; t < s1 - 1;) {
-                const float* in = t == s0 ? ck : seg + (size_t)(t - s0) * selems;
-                float* nxt = seg + (size_t)(t - s0 + 1) * selems;
-                if (kern == 2) {
-                    // launches of `chunk` steps from s0, the adjoint's launches below
-                    const int n = std::min(chunk, s1 - 1 - t);
-                    if ((rc = diff_blocked_launch(ctx, in, pc, n, nullptr, nxt, true, t + n, aligned))) return rc;
-                    t += n;
-                } else {
-                    {
-                        LaunchScope ls(ctx, K_FSTEP);
-                        launch_diff_step(ctx->H, ctx->W, ctx->P, pc, in, nxt, ctx->q, ctx->st);
+            // the segment's states, recomputed or (use_tape) copied from the tile tape where
+            // a complete record covers a launch; returns whether any launch used the tape
+            auto run_segment = [&](bool use_tape, bool* used_tape) -> int {
+                *used_tape = false;
+                ctx->fl_state = nullptr;  // a new chain starts from the checkpoint, with its recorded flags if any
+                {
+                    const int cs = ctx->ckpts[si].second;
+                    const bool rec = cs < (int)ctx->ckact_halo.size() && ctx->ckact_halo[cs] != 0;
+                    const size_t nt = (size_t)std::max(diff_blocked_tiles(8, ctx->H, ctx->P),
+                                                       diff_blocked_tiles(4, ctx->H, ctx->P));
+                    ctx->fl_seed = rec ? ctx->ckact + nt * cs : nullptr;
+                    ctx->fl_seed_halo = rec ? ctx->ckact_halo[cs] : 0;
+                }
+                ctx->actrec_end.clear();
+                ctx->actrec_on = true;
+                int r;
+                for (int t = s0; t < s1 - 1;) {
+                    const float* in = t == s0 ? ck : seg + (size_t)(t - s0) * selems;
+                    float* nxt = seg + (size_t)(t - s0 + 1) * selems;
+                    if (kern == 2) {
+                        // launches of `chunk` steps from s0, the adjoint's launches below
+                        const int n = std::min(chunk, s1 - 1 - t);
+                        int L = -1;
+                        if (use_tape && t - ctx->tape_start < (int)rec_at.size()) {
+                            L = rec_at[(size_t)(t - ctx->tape_start)];
+                            if (L >= 0 && (int)ctx->ttape_meta_h[4 * (size_t)L + 1] < n) L = -1;
+                        }
+                        if (L >= 0) *used_tape = true;
+                        if ((r = diff_blocked_launch(ctx, in, pc, n, nullptr, nxt, true, t + n, aligned, nullptr, -1,
+                                                     L)))
+                            return r;
+                        t += n;
+                    } else {
+                        {
+                            LaunchScope ls(ctx, K_FSTEP);
+                            launch_diff_step(ctx->H, ctx->W, ctx->P, pc, in, nxt, ctx->q, ctx->st);
+                        }
+                        if ((r = check_launch(ctx, "diff step (recompute)"))) return r;
+                        t += 1;
                     }
-                    if ((rc = check_launch(ctx, "diff step (recompute)"))) return rc;
-                    t += 1;
+                }
+                return PF_OK;
+            };
+            bool used_tape = false;
+            if ((rc = run_segment(!rec_at.empty(), &used_tape))) return rc;
+            if (used_tape) {
+                // a listed tile the tape's record lacks (its launch was listed differently):
+                // recompute the segment
+                CK(cudaMemcpyAsync(ctx->hflags + 14, ctx->dflags + 14, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+                CK(cudaStreamSynchronize(ctx->st));
+                if (ctx->hflags[14] != 0) {
+                    CK(cudaMemsetAsync(ctx->dflags + 14, 0, sizeof(int), ctx->st));
+                    if ((rc = run_segment(false, &used_tape))) return rc;
                 }
             }
             if ((rc = adjoint_run(seg, adj_blocked ? &tseg : nullptr, s0, s0, s1, aligned ? chunk : 0, ck,

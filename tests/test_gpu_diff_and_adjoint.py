@@ -298,3 +298,31 @@ def test_checkpoint_slots_reused_by_a_different_run(pf, orc):
     assert np.array_equal(out, out_f)
     assert list(g4) == list(g4_f)
     assert torch.equal(gpv, gpv_f)
+
+
+@pytest.mark.parametrize("K,k", [(7, 8), (13, 8), (22, 6)])
+def test_tile_tape_gives_the_recomputed_gradients(pf, orc, K, k):
+    """With checkpoints, the backward copies each segment's states from the tile tape the
+    forward kept (pf_tuning.tape 0) instead of recomputing them (tape 1): the states are
+    the same bits, so the gradients are identical; the tape was used."""
+    H, W, T = 300, 340, 90
+    land = syn.make_landscape(H, W, 43)
+    winds = [syn.smooth_wind(H, W, 43, e, sigma=8.0) for e in range(2)]
+    starts = [0, 41]
+    S0 = syn.initial_state(land, [(70, 80), (220, 250)])
+    w = cuda(np.random.default_rng(7).standard_normal((H, W)).astype(np.float32) * 1e-3)
+    res = {}
+    for tape in (0, 1):
+        m, _ = _model(pf, orc, land, *winds[0], H, W)
+        _set_winds(m, winds, starts)
+        m.set_tuning(kernel=2, k=k, K=K, tape=tape, profile=1)
+        pf.pf_profile_read(m.h, reset=True)
+        out = m.forward(cuda(S0), T).cpu().numpy()
+        g4, gpv, _ = m.backward(w, None)
+        prof = pf.pf_profile_read(m.h, reset=True)
+        res[tape] = (out, list(g4), gpv.cpu().numpy(), prof.get("segment_from_tape", (0,))[0])
+        m.close()
+    assert res[0][3] > 0 and res[1][3] == 0
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1]
+    assert np.array_equal(res[0][2], res[1][2])
