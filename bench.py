@@ -546,6 +546,7 @@ def main():
     step()
     torch.cuda.synchronize()
     prof = pf.pf_profile_read(m.h, reset=True)  # one profiled step
+    memst = pf.pf_memory_stats(m.h)  # the gradient path's memory and the tape's use, after it
     pf.pf_set_tuning(m.h, **base)
     tun = pf.pf_get_tuning(m.h)
     cells = Hs * Ws * Ts
@@ -671,6 +672,7 @@ def main():
                 stream.wait_event(ev_out)
 
         n_e2e = max(1, args.steps)
+        e2e_run(1)  # warm-up: the staging buffers are new, the library adapts its memory to them
         ms_e2e = timed(lambda: e2e_run(n_e2e), 1) / n_e2e
         e2e = {"value": cells * world / (ms_e2e / 1000.0), "unit": "cell-updates/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
@@ -719,6 +721,7 @@ def main():
                            "H": Hs, "W": Ws, "T": Ts, "wind_epochs": len(winds),
                            "checkpoint_K": tun["K"], "kernel": tun["kernel"], "k": tun["k"], "prep": tun["prep"],
                            "tuning": tuning,
+                           "gradient_memory_gb": {k: (v / 1e9 if k.endswith("_bytes") else v) for k, v in memst.items()},
                            "l2": "inputs larger than L2 (state 0.5 GB, q 2.1 GB per epoch)"},
                 "fwd": {"value": cells * world / (ms_fwd / 1000.0), "unit": "cell-updates/s", "ms": ms_fwd,
                         "frac_hbm_alg_effective": B_FWD * cells / (ms_fwd / 1000.0) / 1e9 / hbm},

@@ -233,10 +233,12 @@ int pf_loss_bce_noalloc(const float* a, const float* y, int64_t n, float* dL_da,
  *             0 = keep a tile tape (every live tile's states of every forward launch)
  *             so that the backward copies each segment's states instead of recomputing
  *             them; a segment the tape does not cover is recomputed. The tape takes the
- *             device memory the backward does not need, less an eighth of the device
- *             (at least 16 GB) left free, and is kept by the context until pf_destroy;
- *             the per-epoch q the adjoint would otherwise reuse is not kept then (the
- *             backward prepares it again). 1 = no tape: always recompute.
+ *             device memory the backward does not need, less a sixteenth of the
+ *             device (at least 16 GB) left free; once a backward has seen how much the tape
+ *             needs, it holds that and an eighth more. It is kept by the context until
+ *             pf_destroy. The per-epoch q cache (the forward's q of every wind epoch
+ *             kept for the adjoint) is kept beside it only where both fit; otherwise
+ *             the backward prepares q again. 1 = no tape: always recompute.
  * Results do not depend on any of these (the same arithmetic in every variant), except
  * through K's effect on memory. PF_EINVAL for values out of range. */
 typedef struct pf_tuning {
@@ -251,6 +253,27 @@ typedef struct pf_tuning {
 
 int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t);
 int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t);
+
+/* Device memory the differentiable form's gradient path holds, and how the last taped
+ * forward used it (no counterpart in the paper: memory planning for the checkpointed
+ * backward). Bytes: checkpoint states (the arena), the backward's segment buffer, the
+ * per-epoch q cache, the tile tape and the part of it the last taped forward wrote.
+ * tape_launches: blocked launches of that forward the tape tried to record;
+ * tape_recorded: those it had room for (the others are recomputed by the backward).
+ * K: that forward's checkpoint interval; tape_short: the tape of the last backward
+ * ran short (some of its launches were recomputed). Synchronises the context's stream. */
+typedef struct pf_memory_stats_t {
+    long long checkpoint_bytes;
+    long long segment_bytes;
+    long long qcache_bytes;
+    long long tape_bytes;
+    long long tape_used_bytes;
+    int tape_launches;
+    int tape_recorded;
+    int K;
+    int tape_short;
+} pf_memory_stats_t;
+int pf_memory_stats(pf_ctx* ctx, pf_memory_stats_t* out);
 
 /* Autotuner (no counterpart in the paper, which has one PyTorch code path). Times, on
  * this context's grid, fields and parameters, a forward of T_probe steps from S_init

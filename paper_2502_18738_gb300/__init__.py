@@ -23,7 +23,7 @@ __all__ = [
     "PFireError", "build", "load", "PF_DISCRETE", "PF_DIFF",
     "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_wind_async", "pf_wait", "pf_set_params",
     "pf_forward", "pf_advance", "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce",
-    "pf_set_tuning", "pf_get_tuning", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_batch_set_direct_cells", "pf_profile_read", "pf_batch_submit", "pf_last_error",
+    "pf_set_tuning", "pf_get_tuning", "pf_memory_stats", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_batch_set_direct_cells", "pf_profile_read", "pf_batch_submit", "pf_last_error",
     "pf_version", "pf_loss_bce_noalloc", "PF_NOALLOC_BCE_MAX_N", "FireModel", "DiffFire", "PfJob", "make_job",
     "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10", "pf_arrival_probability",
     "pf_affected_count", "pf_jaccard", "pf_manhattan", "pf_set_slope", "simulate", "WildfireModel",
@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = [
     "pf_manhattan", "pf_stats", "pf_create", "pf_destroy", "pf_set_env", "pf_set_wind", "pf_set_params", "pf_forward", "pf_advance",
     "pf_backward", "pf_get_state", "pf_set_state", "pf_ignition_map", "pf_loss_bce", "pf_set_tuning",
     "pf_get_tuning", "pf_profile_read", "pf_batch_submit", "pf_last_error", "pf_version",
-    "pf_loss_bce_noalloc", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_batch_set_direct_cells", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
+    "pf_loss_bce_noalloc", "pf_memory_stats", "pf_autotune", "pf_autotune_ckpt", "pf_batch_last_stats", "pf_batch_set_direct_cells", "pf_set_accumulator", "pf_reseed", "pf_backward_dca", "pf_loss_eq10",
     "pf_arrival_probability", "pf_affected_count", "pf_jaccard", "pf_set_slope", "pf_set_wind_async", "pf_wait",
 ]
 PF_NOALLOC_BCE_MAX_N = 67108864
@@ -74,6 +74,13 @@ class PfBatchStats(ctypes.Structure):
                 ("ms_forward", ctypes.c_double), ("ms_adjoint", ctypes.c_double),
                 ("ms_kernels_from_start", ctypes.c_double), ("waves", ctypes.c_int), ("direct_jobs", ctypes.c_int),
                 ("direct_cell_steps", ctypes.c_longlong), ("ms_direct", ctypes.c_double)]
+
+
+class PfMemoryStats(ctypes.Structure):
+    _fields_ = [("checkpoint_bytes", ctypes.c_longlong), ("segment_bytes", ctypes.c_longlong),
+                ("qcache_bytes", ctypes.c_longlong), ("tape_bytes", ctypes.c_longlong),
+                ("tape_used_bytes", ctypes.c_longlong), ("tape_launches", ctypes.c_int),
+                ("tape_recorded", ctypes.c_int), ("K", ctypes.c_int), ("tape_short", ctypes.c_int)]
 
 
 class PfJob(ctypes.Structure):
@@ -126,6 +133,7 @@ def load():
             "pf_loss_bce_noalloc": ([vp, vp, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_double), vp], i),
             "pf_set_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
             "pf_get_tuning": ([vp, ctypes.POINTER(PfTuning)], i),
+            "pf_memory_stats": ([vp, ctypes.POINTER(PfMemoryStats)], i),
             "pf_autotune": ([vp, vp, i, ctypes.POINTER(PfTuning)], i),
             "pf_autotune_ckpt": ([vp, vp, i, ctypes.POINTER(ctypes.c_int)], i),
             "pf_batch_last_stats": ([ctypes.POINTER(PfBatchStats)], i),
@@ -324,6 +332,14 @@ def pf_get_tuning(h) -> dict:
     t = PfTuning()
     _check(load().pf_get_tuning(h, ctypes.byref(t)), h)
     return t.as_dict()
+
+
+def pf_memory_stats(h) -> dict:
+    """Device memory of the gradient path (checkpoints, segment buffer, q cache, tile
+    tape) and how much of the tape the last taped forward used."""
+    st = PfMemoryStats()
+    _check(load().pf_memory_stats(h, ctypes.byref(st)), h)
+    return {name: getattr(st, name) for name, _ in st._fields_}
 
 
 def pf_autotune(h, S_init, T_probe) -> dict:

@@ -380,9 +380,11 @@ void launch_fwd_act_seed(int halo, const uint8_t* seed, int H, int pitch, uint8_
 // qrun: per tile, the number of consecutive launches of the chain it has been quiescent
 // in (saturating at 255); out_age > 0: out holds the input state of the launch out_age
 // launches back, so tiles with qrun >= out_age need no copy into it (0: out holds nothing).
-// seg_dirty (nullable): all_out lies in a segment buffer reused across segments, whose
-// slots zero_base + s * all_stride (s < zero_slots) hold zeros for tiles not dirty; void
-// tiles (a = b = 0 in the whole region) then write nothing there (see k_fwd_tiles).
+// seg_rng (nullable): all_out lies in a segment buffer reused across segments, whose
+// slots zero_base + s * all_stride (s < zero_slots) hold zeros for each tile outside its
+// dirty slot range seg_rng[tile] = lo | hi << 16 ([lo, hi), empty when lo >= hi); void
+// tiles (a = b = 0 in the whole region) write nothing but zeros into the launch's own
+// slots where they are dirty (see k_fwd_tiles).
 // frozen (segment buffers only, launches aligned with the adjoint's): quiescent tiles get
 // kFrozen in act_out, and those with b = 0 in the 5 x 5 interiors around them write only
 // the launch's last slot (the next launch's input): every tile whose region reaches into
@@ -394,9 +396,10 @@ void launch_fwd_act_seed(int halo, const uint8_t* seed, int H, int pitch, uint8_
 // slot's interior may hold nonzeros; all-zero tiles (a = 0) are written only where it is
 // set (all tiles if dirty_unknown), and it is updated to the state written.
 // written (nullable) accumulates the cells the pre-pass copied or zero-filled.
-void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
+// Returns false (nothing launched) when all_out's slots fall outside the segment buffer.
+bool launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
-                      int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, const float* slot0,
+                      int out_age, float* all_out, size_t all_stride, uint32_t* seg_rng, const float* slot0,
                       float* zero_base, int zero_slots, bool frozen, uint8_t* out_dirty, bool dirty_unknown,
                       unsigned long long* skipped, unsigned long long* written, cudaStream_t s);
 // Tile tape of a taped forward: the interior states of every listed (live) tile of a
@@ -425,10 +428,11 @@ void launch_tape_record(TileTape tape, const int* tile_count, const int* tile_li
 // count} (inv: tile -> index in the record's list, built here from rec_list) into
 // all_out's slots, and its activity after the launch into act_out (kQb kept), as
 // k_diff_blocked writes them. A listed tile missing from the record adds to *missing.
+// nsm: the device's SM count (the grid is eight blocks an SM).
 void launch_tape_unpack(int halo, const float* tape_data, unsigned long long base, int n_rec, int rec_count,
                         const int* rec_list, int* inv, int ntiles, const int* tile_list, const int* tile_count,
                         int n, int H, int pitch, float* all_out, size_t all_stride, uint8_t* act_out, int* missing,
-                        cudaStream_t s);
+                        int nsm, cudaStream_t s);
 // lam: scaled adjoint (mu_a, mu_b) [2][H][pitch]; sig: its exponents uint8 [H][pitch]
 void launch_adjoint_step(int H, int W, int pitch, float p_continue, const float* ab, const float* q,
                          const float* lam1, const uint8_t* sig1, float* lam0, uint8_t* sig0, float* Gq,

@@ -426,12 +426,15 @@ __global__ void __launch_bounds__(256) k_fwd_act_seed(const uint8_t* __restrict_
 // launch out_age launches back (out_age > 0) and the tile has been quiescent in every
 // launch since (qrun[tile], the tile's quiescent streak, saturating at 255).
 //
-// Segment buffers (seg_dirty != nullptr): all_out is a run of slots of a buffer that is
-// reused from segment to segment, and seg_dirty[tile] records whether the tile's interior
-// may be nonzero in any of its zero_slots slots from zero_base on. A quiescent tile with
-// a = 0 in the 3 x 3 interiors around it is void (exactly zero in its whole region for
-// the whole launch); its slots only have to hold zeros, which they already do unless the
-// tile is dirty, in which case all of them are zeroed once.
+// Segment buffers (seg_rng != nullptr): all_out is a run of slots of a buffer that is
+// reused from segment to segment (slot_a .. slot_a + n - 1 counted from zero_base), and
+// seg_rng[tile] = lo | hi << 16 bounds the slots [lo, hi) where the tile's interior may
+// be nonzero. A quiescent tile with a = 0 in the 3 x 3 interiors around it is void
+// (exactly zero in its whole region for the whole launch); the launch's slots only have
+// to hold zeros there, which they already do outside the range. The launch zeroes its
+// own slots inside it, and the range loses them when they are its front: the launches of
+// a segment run in slot order, so a tile that turns live within a segment zeroes only the
+// slots before, and in the segment after (earlier in time) only the rest.
 //
 // Aligned segment recompute (frozen != 0): quiescent tiles get kFrozen (their region is
 // constant over the launch). One with b = 0 in the 5 x 5 interiors around it writes only
@@ -450,8 +453,8 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
                                                    int* __restrict__ list, int* __restrict__ count,
                                                    float* __restrict__ out, int out_age,
                                                    float* __restrict__ all_out, size_t all_stride,
-                                                   uint8_t* __restrict__ seg_dirty, const float* __restrict__ slot0,
-                                                   float* __restrict__ zero_base, int zero_slots, int frozen,
+                                                   uint32_t* __restrict__ seg_rng, const float* __restrict__ slot0,
+                                                   float* __restrict__ zero_base, int slot_a, int frozen,
                                                    uint8_t* __restrict__ out_dirty, int dirty_unknown,
                                                    unsigned long long* __restrict__ skipped, int tile, int lane,
                                                    unsigned long long& sk, unsigned long long& wr) {
@@ -479,11 +482,19 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     const bool qseg5 = __reduce_and_sync(0xffffffffu, q5) != 0u;
     const uint32_t me = act_in[tile];
     const uint8_t qb = (me & kQt) ? kQb : 0;  // quiescent in every earlier launch of the segment
+    // the tile's dirty slot range grows by [w0, slot_a + n) (lane 0)
+    auto rng_add = [&](int w0) {
+        const uint32_t r = seg_rng[tile];
+        int lo = (int)(r & 0xffffu), hi = (int)(r >> 16);
+        if (lo >= hi) lo = w0, hi = slot_a + n;
+        else lo = min(lo, w0), hi = max(hi, slot_a + n);
+        seg_rng[tile] = (uint32_t)lo | ((uint32_t)hi << 16);
+    };
     if (around & kActB) {
         if (lane == 0) {
             list[atomicAdd(count, 1)] = tile;
             qrun[tile] = 0;
-            if (seg_dirty) seg_dirty[tile] = 1;
+            if (seg_rng) rng_add(slot_a);
             if (out_dirty) out_dirty[tile] = 1;
             act_out[tile] = qb;  // k_diff_blocked adds the tile's activity
         }
@@ -492,15 +503,19 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     const int r0 = ty * kI, c0 = tx * kI;
     const size_t gplane = (size_t)H * pitch;
     bool write_all = all_out != nullptr;
-    if (seg_dirty && !(around & kActA)) {
+    const bool void_tile = seg_rng && !(around & kActA);
+    if (void_tile) {
         write_all = false;
-        if (seg_dirty[tile]) {
+        const uint32_t r = seg_rng[tile];  // read by every lane before lane 0 changes it
+        const int lo = (int)(r & 0xffffu), hi = (int)(r >> 16);
+        const int z0 = max(lo, slot_a), z1 = min(hi, slot_a + n);
+        if (z0 < z1) {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int i = lane; i < kI * (kI / 4); i += 32) {
                 const int gr = r0 + i / (kI / 4), gc = c0 + 4 * (i % (kI / 4));
                 if (gr >= H || gc >= pitch) continue;
                 const size_t j = (size_t)gr * pitch + gc;
-                for (int s = 0; s < zero_slots; ++s) {
+                for (int s = z0; s < z1; ++s) {
                     float* o = zero_base + (size_t)s * all_stride;
                     *reinterpret_cast<float4*>(o + j) = z;
                     *reinterpret_cast<float4*>(o + gplane + j) = z;
@@ -508,12 +523,10 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
             }
             __syncwarp();
             if (lane == 0) {
-                seg_dirty[tile] = 0;
-                wr += (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)zero_slots;
+                if (z0 == lo) seg_rng[tile] = z1 >= hi ? 0u : ((uint32_t)z1 | ((uint32_t)hi << 16));
+                wr += (unsigned long long)(min(kI, H - r0) * min(kI, W - c0)) * (unsigned long long)(z1 - z0);
             }
         }
-    } else if (seg_dirty && lane == 0) {
-        seg_dirty[tile] = 1;
     }
     // far from anything burning: only the last slot (the next launch's input) is read;
     // farther still and unchanged since slot 0 around it: nothing is
@@ -545,7 +558,8 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     // reads its region from the launch's first state only; the other tiles' regions reach
     // 8 cells into its interior. So slots before the last need only that 8-cell band, and
     // the last slot (the next launch's input) the whole interior.
-    const bool band_only = frozen && seg_dirty;
+    const bool band_only = frozen && seg_rng;
+    if (seg_rng && write_all && lane == 0) rng_add(last_only ? slot_a + n - 1 : slot_a);
     uint32_t nw = 0u;  // float4 pairs this lane wrote
     if (copy_out || write_all) {
         // float4 columns: c0 and pitch are multiples of 4 (and 8, kI - 8 are too)
@@ -592,8 +606,8 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
                                                    int* __restrict__ list, int* __restrict__ count,
                                                    float* __restrict__ out, int out_age,
                                                    float* __restrict__ all_out, size_t all_stride,
-                                                   uint8_t* __restrict__ seg_dirty, const float* __restrict__ slot0,
-                                                   float* __restrict__ zero_base, int zero_slots, int frozen,
+                                                   uint32_t* __restrict__ seg_rng, const float* __restrict__ slot0,
+                                                   float* __restrict__ zero_base, int slot_a, int frozen,
                                                    uint8_t* __restrict__ out_dirty, int dirty_unknown,
                                                    unsigned long long* __restrict__ skipped,
                                                    unsigned long long* __restrict__ written) {
@@ -604,7 +618,7 @@ __global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in,
     const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);  // one warp per tile
     if (tile < tiles_x * tiles_y)
         fwd_tile<kHalo>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out, qrun, list, count, out,
-                        out_age, all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots, frozen, out_dirty,
+                        out_age, all_out, all_stride, seg_rng, slot0, zero_base, slot_a, frozen, out_dirty,
                         dirty_unknown, skipped, tile, threadIdx.x & 31, sk, wr);
     block_count(skipped, s_sk, sk);
     block_count(written, s_wr, wr);
@@ -637,8 +651,10 @@ __global__ void __launch_bounds__(256) k_tape_inv(const int* __restrict__ rec_li
     if (i < rec_count) inv[rec_list[i]] = i;
 }
 
-// One block per entry of the recompute's list: the tile's n states from the tape into
-// the segment slots, and its activity after the launch (as k_diff_blocked writes it).
+// Work item w = (entry w / n of the recompute's list, step w % n), taken by the blocks
+// in turn (grid-stride): the tile's state at that step from the tape into its segment
+// slot; the last step's item also writes the tile's activity after the launch (as
+// k_diff_blocked writes it).
 template <int kHalo>
 __global__ void __launch_bounds__(256) k_tape_unpack(const float* __restrict__ tape_data, unsigned long long base,
                                                      int n_rec, const int* __restrict__ inv,
@@ -647,44 +663,60 @@ __global__ void __launch_bounds__(256) k_tape_unpack(const float* __restrict__ t
                                                      int tiles_x, float* __restrict__ all_out, size_t all_stride,
                                                      uint8_t* __restrict__ act_out, int* __restrict__ missing) {
     constexpr int kI = kRT - 2 * kHalo;
+    constexpr int kPer = kI * (kI / 4);             // float4 of a plane
+    constexpr int kU = (kPer + 255) / 256;          // of them a thread
     __shared__ int s_any[2];
-    if ((int)blockIdx.x >= *tile_count) return;
-    const int tile = tile_list[blockIdx.x];
-    const int li = inv[tile];
-    if (li < 0) {  // not in the record: the caller recomputes the segment
-        if (threadIdx.x == 0) atomicAdd(missing, 1);
-        return;
-    }
-    if (threadIdx.x == 0) s_any[0] = s_any[1] = 0;
-    __syncthreads();
-    const int ty = tile / tiles_x, tx = tile % tiles_x;
-    const int r0 = ty * kI, c0 = tx * kI;
+    const int items = *tile_count * n;
     const size_t gplane = (size_t)H * pitch;
-    int anyA = 0, anyB = 0;
-    for (int st = 0; st < n; ++st) {
+    for (int w = blockIdx.x; w < items; w += gridDim.x) {  // uniform across the block
+        const int st = w % n;
+        const int tile = tile_list[w / n];
+        const int li = inv[tile];
+        if (li < 0) {  // not in the record: the caller recomputes the segment
+            if (threadIdx.x == 0 && st == 0) atomicAdd(missing, 1);
+            continue;
+        }
+        const bool last = st == n - 1;
+        if (last && threadIdx.x == 0) s_any[0] = s_any[1] = 0;
+        const int ty = tile / tiles_x, tx = tile % tiles_x;
+        const int r0 = ty * kI, c0 = tx * kI;
         const float* src = tape_data + (base + (unsigned long long)li * n_rec + st) * (2ull * kI * kI);
         float* o = all_out + (size_t)st * all_stride;
-        // float4 columns: c0 and pitch are multiples of 4
-        for (int i = threadIdx.x; i < kI * (kI / 4); i += 256) {
+        // every load of the thread before any store; float4 columns (c0 and pitch are
+        // multiples of 4)
+        float4 a[kU], b[kU];
+        size_t jo[kU];
+        bool ok[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = threadIdx.x + 256 * u;
             const int ir = i / (kI / 4), ic = 4 * (i % (kI / 4));
             const int gr = r0 + ir, gc = c0 + ic;
-            if (gr >= H || gc >= pitch) continue;
-            const float4 a = *reinterpret_cast<const float4*>(src + ir * kI + ic);
-            const float4 b = *reinterpret_cast<const float4*>(src + kI * kI + ir * kI + ic);
-            const size_t j = (size_t)gr * pitch + gc;
-            *reinterpret_cast<float4*>(o + j) = a;
-            *reinterpret_cast<float4*>(o + gplane + j) = b;
-            if (st == n - 1) {
-                anyA |= (__float_as_uint(a.x) | __float_as_uint(a.y) | __float_as_uint(a.z) | __float_as_uint(a.w)) != 0u;
-                anyB |= b.x != 0.0f || b.y != 0.0f || b.z != 0.0f || b.w != 0.0f;
+            ok[u] = i < kPer && gr < H && gc < pitch;
+            jo[u] = (size_t)gr * pitch + gc;
+            if (ok[u]) {
+                a[u] = *reinterpret_cast<const float4*>(src + ir * kI + ic);
+                b[u] = *reinterpret_cast<const float4*>(src + kI * kI + ir * kI + ic);
             }
         }
+        int anyA = 0, anyB = 0;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (!ok[u]) continue;
+            *reinterpret_cast<float4*>(o + jo[u]) = a[u];
+            *reinterpret_cast<float4*>(o + gplane + jo[u]) = b[u];
+            anyA |= (__float_as_uint(a[u].x) | __float_as_uint(a[u].y) | __float_as_uint(a[u].z) |
+                     __float_as_uint(a[u].w)) != 0u;
+            anyB |= b[u].x != 0.0f || b[u].y != 0.0f || b[u].z != 0.0f || b[u].w != 0.0f;
+        }
+        if (!last) continue;
+        __syncthreads();  // s_any cleared
+        if (anyA) s_any[0] = 1;
+        if (anyB) s_any[1] = 1;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            act_out[tile] = (uint8_t)((act_out[tile] & kQb) | (s_any[0] ? kActA : 0) | (s_any[1] ? kActB : 0));
     }
-    if (anyA) s_any[0] = 1;
-    if (anyB) s_any[1] = 1;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        act_out[tile] = (uint8_t)((act_out[tile] & kQb) | (s_any[0] ? kActA : 0) | (s_any[1] ? kActB : 0));
 }
 
 }  // namespace
@@ -735,27 +767,34 @@ void launch_fwd_act_seed(int halo, const uint8_t* seed, int H, int pitch, uint8_
     k_fwd_act_seed<<<(ntiles + 255) / 256, 256, 0, s>>>(seed, ntiles, act, qrun);
 }
 
-void launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
+bool launch_fwd_tiles(int halo, const float* in, int H, int W, int pitch, int n, const uint8_t* act_in,
                       uint8_t* act_out, uint8_t* qrun, int* tile_list, int* tile_count, float* out,
-                      int out_age, float* all_out, size_t all_stride, uint8_t* seg_dirty, const float* slot0,
+                      int out_age, float* all_out, size_t all_stride, uint32_t* seg_rng, const float* slot0,
                       float* zero_base, int zero_slots, bool frozen, uint8_t* out_dirty, bool dirty_unknown,
                       unsigned long long* skipped, unsigned long long* written, cudaStream_t s) {
     const int inner = kRT - 2 * halo;
+    // the launch's first slot, counted from zero_base (slots zero_base .. + zero_slots - 1)
+    int slot_a = 0;
+    if (seg_rng) {
+        slot_a = (int)((all_out - zero_base) / (ptrdiff_t)all_stride);
+        if (all_out < zero_base || slot_a + n > zero_slots || slot_a + n > 0xffff) return false;
+    }
     const int tiles_x = (pitch + inner - 1) / inner;
     const int tiles_y = (H + inner - 1) / inner;
     cudaMemsetAsync(tile_count, 0, 2 * sizeof(int), s);  // the count and k_diff_blocked's work counter
     if (halo == 4)
         k_fwd_tiles<4><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          qrun, tile_list, tile_count, out, out_age,
-                                                         all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots,
+                                                         all_out, all_stride, seg_rng, slot0, zero_base, slot_a,
                                                          frozen ? 1 : 0, out_dirty, dirty_unknown ? 1 : 0, skipped,
                                                          written);
     else
         k_fwd_tiles<8><<<(tiles_x * tiles_y + 7) / 8, 256, 0, s>>>(in, H, W, pitch, tiles_x, tiles_y, n, act_in, act_out,
                                                          qrun, tile_list, tile_count, out, out_age,
-                                                         all_out, all_stride, seg_dirty, slot0, zero_base, zero_slots,
+                                                         all_out, all_stride, seg_rng, slot0, zero_base, slot_a,
                                                          frozen ? 1 : 0, out_dirty, dirty_unknown ? 1 : 0, skipped,
                                                          written);
+    return true;
 }
 
 void launch_diff_blocked(int halo, const CUtensorMap* tab, const CUtensorMap* tq, const PrepArgs* pa, int H, int W,
@@ -792,16 +831,19 @@ void launch_tape_record(TileTape tape, const int* tile_count, const int* tile_li
 void launch_tape_unpack(int halo, const float* tape_data, unsigned long long base, int n_rec, int rec_count,
                         const int* rec_list, int* inv, int ntiles, const int* tile_list, const int* tile_count,
                         int n, int H, int pitch, float* all_out, size_t all_stride, uint8_t* act_out, int* missing,
-                        cudaStream_t s) {
+                        int nsm, cudaStream_t s) {
+    if (n <= 0 || ntiles <= 0) return;
     const int inner = kRT - 2 * halo;
     const int tiles_x = (pitch + inner - 1) / inner;
     cudaMemsetAsync(inv, 0xff, sizeof(int) * (size_t)ntiles, s);
     if (rec_count > 0) k_tape_inv<<<(rec_count + 255) / 256, 256, 0, s>>>(rec_list, rec_count, inv);
+    // eight blocks an SM (their resident limit) take the items in turn
+    const int grid = std::max(1, std::min(ntiles * n, 8 * std::max(nsm, 1)));
     if (halo == 4)
-        k_tape_unpack<4><<<ntiles, 256, 0, s>>>(tape_data, base, n_rec, inv, tile_list, tile_count, n, H, pitch,
+        k_tape_unpack<4><<<grid, 256, 0, s>>>(tape_data, base, n_rec, inv, tile_list, tile_count, n, H, pitch,
                                                 tiles_x, all_out, all_stride, act_out, missing);
     else
-        k_tape_unpack<8><<<ntiles, 256, 0, s>>>(tape_data, base, n_rec, inv, tile_list, tile_count, n, H, pitch,
+        k_tape_unpack<8><<<grid, 256, 0, s>>>(tape_data, base, n_rec, inv, tile_list, tile_count, n, H, pitch,
                                                 tiles_x, all_out, all_stride, act_out, missing);
 }
 

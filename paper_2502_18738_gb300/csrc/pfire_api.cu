@@ -210,7 +210,7 @@ struct pf_ctx {
     int nsm = 152;
     float* seg_buf = nullptr;  // K-1 contiguous states (segment recompute)
     int seg_cap = 0;
-    uint8_t* seg_dirty = nullptr;  // per forward tile: its interior may be nonzero in slots 1.. of seg_buf
+    uint32_t* seg_rng = nullptr;  // per forward tile: slots [lo, hi) of seg_buf (from slot 1) where its interior may be nonzero
     const float* seg_slot0 = nullptr;  // the segment's first state (its checkpoint; slot 0 of seg_buf is unused)
     int seg_halo = 0;              // tile geometry seg_dirty refers to
     // tile tape of a checkpointed taped forward (TileTape in common.cuh): the live tiles'
@@ -219,6 +219,7 @@ struct pf_ctx {
     // records {base, n, count, ok} and lists
     float* ttape = nullptr;
     unsigned long long ttape_cap = 0;      // blocks
+    size_t ttape_blk = 0;                  // bytes a block
     unsigned long long* ttape_used = nullptr;
     unsigned long long* ttape_meta = nullptr;
     int* ttape_lists = nullptr;
@@ -227,6 +228,11 @@ struct pf_ctx {
     std::vector<std::pair<int, int>> ttape_rec;
     std::vector<unsigned long long> ttape_meta_h;  // host copy of the records (backward)
     bool ttape_on = false;
+    // the last tape ran out of blocks (some launches were left out and recomputed)
+    bool ttape_short = false;
+    // blocks the last taped forward asked for (recorded or not), at block size ttape_need_blk
+    unsigned long long ttape_need = 0;
+    size_t ttape_need_blk = 0;
     int TH = 64, KH = 16;
     // Philox counter words 3 and 1 (base) of the discrete draws: 0 for contexts made by
     // pf_create; a batch job run through a context of its own uses its fire_id and run
@@ -656,13 +662,14 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
     {
         // the pre-pass of a forward launch, or of one recomputing a segment for the adjoint
         LaunchScope ls(ctx, seg ? K_STILES : K_FTILES);
-        launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
+        if (!launch_fwd_tiles(halo, in, ctx->H, ctx->W, ctx->P, n, ctx->fact[ctx->fl_par], ctx->fact[1 - ctx->fl_par],
                          ctx->fqrun, ctx->flist, ctx->dflags + 12, out, out_age, all_out,
-                         stride, seg ? ctx->seg_dirty : nullptr, seg ? ctx->seg_slot0 : nullptr,
+                         stride, seg ? ctx->seg_rng : nullptr, seg ? ctx->seg_slot0 : nullptr,
                          seg ? ctx->seg_buf + stride : nullptr,
                          ctx->seg_cap - 1, seg && frozen && halo == 8, dirty, dirty_unknown,
                          ctx->dskip + (rec >= 0 ? K_TUNPACK : K_FBLK), ctx->dskip + (seg ? K_STILES : K_FTILES),
-                         ctx->st);
+                         ctx->st))
+            return fail(ctx, PF_EINVAL, "segment launch outside the segment buffer");
     }
     if (rec >= 0) {
         LaunchScope ls(ctx, K_TUNPACK);
@@ -670,7 +677,7 @@ int diff_blocked_launch(pf_ctx* ctx, const float* in, float pc, int n, float* ou
         const size_t nt = (size_t)diff_blocked_tiles(halo, ctx->H, ctx->P);
         launch_tape_unpack(halo, ctx->ttape, m[0], (int)m[1], (int)m[2], ctx->ttape_lists + nt * (size_t)rec,
                            ctx->ttape_inv, (int)nt, ctx->flist, ctx->dflags + 12, n, ctx->H, ctx->P, all_out, stride,
-                           ctx->fact[1 - ctx->fl_par], ctx->dflags + 14, ctx->st);
+                           ctx->fact[1 - ctx->fl_par], ctx->dflags + 14, ctx->nsm, ctx->st);
     } else {
         LaunchScope ls(ctx, K_FBLK, n);
         const TileTape tape{record ? ctx->ttape : nullptr, ctx->ttape_used, ctx->ttape_cap};
@@ -827,22 +834,59 @@ int choose_K(pf_ctx* ctx, int T) {
     }
     const double sb = (double)diff_state_bytes(ctx);
     const int ne = (int)ctx->winds.size();
-    // keep every epoch's q for the adjoint (saves one prep per epoch) when they take at
-    // most 30% of the free memory; the tape gets the rest of the budget
+    // the per-epoch q cache (qcache_decide) is counted out of the tape's budget
     double cached = 0.0;
     for (float* b : ctx->qcache) cached += b ? 8.0 * (double)plane_elems(ctx) * sizeof(float) : 0.0;
     const double qbytes = 8.0 * (double)plane_elems(ctx) * sizeof(float) * ne;
     const double avail = (double)free_b + cached;
-    ctx->qcache_on = qbytes <= 0.3 * avail;
+    const double budget = 0.6 * (avail + (double)ctx->arena_cap * sb) - (ctx->qcache_on ? qbytes - cached : 0.0);
+    if ((double)(T + 1 + ne) * sb <= budget) return 1;  // keep every state: no recomputation
+    int K = std::max(2, (int)std::ceil(std::sqrt((double)T)));
+    return K;
+}
+
+// Device memory the tile tape and the q cache leave free for the caller: a sixteenth of
+// the device, at least 16 GB.
+size_t tape_keep_bytes(size_t total_b) { return std::max((size_t)16 << 30, total_b / 16); }
+
+// Whether a taped forward keeps every epoch's q for the adjoint (saves the adjoint one
+// prep per epoch): when they take at most 30% of the free memory, and, where a tile tape
+// will be kept and the last one's need is known, when the tape's need (an eighth more)
+// fits beside them with tape_keep_bytes left free. The tape
+// saves a whole recompute, the cache one prep per epoch: the tape comes first. Buffers
+// of a cache that is off are freed.
+void qcache_decide(pf_ctx* ctx) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    const int ne = (int)ctx->winds.size();
+    const double qb = 8.0 * (double)plane_elems(ctx) * sizeof(float);
+    double cached = 0.0;
+    for (float* b : ctx->qcache) cached += b ? qb : 0.0;
+    // a tile tape's memory counts as free: ttape_begin sizes the tape after this
+    const double held = ctx->ttape ? (double)ctx->ttape_cap * (double)ctx->ttape_blk : 0.0;
+    bool on = qb * ne <= 0.3 * ((double)free_b + cached + held);
+    const bool tape = ctx->form == PF_DIFF && ctx->tun.tape != 1 && ctx->tun.prep != 2 && choose_kernel(ctx) == 2;
+    if (on && tape && ctx->ttape_need > 0) {
+        const double need = (double)ctx->ttape_need * 1.125 * (double)ctx->ttape_need_blk;
+        const double keep = (double)tape_keep_bytes(total_b);
+        on = qb * ne - cached + need + keep + 2.0 * (1 << 30) <= (double)free_b + held;
+    }
+    ctx->qcache_on = on;
     if ((int)ctx->qcache.size() < ne) {
         ctx->qcache.resize(ne, nullptr);
         ctx->qcache_ver.resize(ne, -1);
         ctx->qcache_until.resize(ne, 0);
     }
-    const double budget = 0.6 * (avail + (double)ctx->arena_cap * sb) - (ctx->qcache_on ? qbytes - cached : 0.0);
-    if ((double)(T + 1 + ne) * sb <= budget) return 1;  // keep every state: no recomputation
-    int K = std::max(2, (int)std::ceil(std::sqrt((double)T)));
-    return K;
+    if (!ctx->qcache_on)
+        for (float*& b : ctx->qcache)
+            if (b) {
+                if (ctx->q == b) use_q_buffer(ctx, ctx->q_own);
+                dfree(ctx, b);
+                b = nullptr;
+            }
 }
 
 // steps from t until the next checkpoint step (exclusive bound t + result)
@@ -951,24 +995,15 @@ void tape_reset(pf_ctx* ctx) {
 
 // The tile tape of a checkpointed blocked run (pf_tuning.tape 0): blocks for the live
 // tiles' states in the memory the backward does not need (its segment buffer, lambda,
-// sigma and dL/dq are counted out) less an eighth of the device (at least 16 GB) left
-// to the caller, records for up to T launches. The per-epoch q cache gives way to it. Without room, or for a
-// run that keeps every state or runs the plain kernels, there is no tape and the backward
-// recomputes its segments.
+// sigma and dL/dq, and the per-epoch q cache's buffers still to come are counted out)
+// less tape_keep_bytes left to the caller, records for up to T
+// launches. Without room, or for a run that keeps every state or runs the plain kernels,
+// there is no tape and the backward recomputes its segments; launches the tape has no
+// room for are recomputed too.
 int ttape_begin(pf_ctx* ctx, int T) {
     ctx->ttape_on = false;
     ctx->ttape_rec.clear();
     if (ctx->tun.tape == 1 || ctx->K <= 1 || choose_kernel(ctx) != 2 || ctx->tun.prep == 2) return PF_OK;
-    // the tape saves the backward a whole recompute of the forward; the per-epoch q cache
-    // only one prep per epoch: the memory goes to the tape
-    ctx->qcache_on = false;
-    for (float*& b : ctx->qcache)
-        if (b) {
-            if (ctx->q == b) use_q_buffer(ctx, ctx->q_own);
-            dfree(ctx, b);
-            b = nullptr;
-        }
-    for (long& v : ctx->qcache_ver) v = -1;
     const int halo = blocked_k(ctx) <= 4 ? 4 : 8;
     const size_t ki = (size_t)(diff_blocked_box_rows() - 2 * halo);
     const size_t blk = 2 * ki * ki * sizeof(float);
@@ -1003,28 +1038,42 @@ int ttape_begin(pf_ctx* ctx, int T) {
         }
         const size_t sb = diff_state_bytes(ctx), pe = plane_elems(ctx);
         // what the backward allocates later: the segment buffer, lambda and sigma
-        // ping-pong, dL/dq, and a margin; and an eighth of the device (at least 16 GB)
+        // ping-pong, dL/dq, and a margin; and tape_keep_bytes
         // left to the caller. The tape's own memory counts as available.
         size_t later = (ctx->seg_cap < ctx->K ? (size_t)ctx->K * sb : 0) + 2 * sb + 2 * pe + 8 * pe * sizeof(float) +
                        ((size_t)2 << 30);
         if (ctx->lam[0]) later -= std::min(later, 2 * sb + 2 * pe + 8 * pe * sizeof(float));
-        const size_t keep = std::max((size_t)16 << 30, total_b / 8);
-        const size_t avail = free_b + (size_t)ctx->ttape_cap * blk;
+        if (ctx->qcache_on)
+            for (size_t e = 0; e < ctx->winds.size(); ++e)
+                if (e >= ctx->qcache.size() || !ctx->qcache[e]) later += 8 * pe * sizeof(float);
+        const size_t keep = tape_keep_bytes(total_b);
+        const size_t avail = free_b + (ctx->ttape ? (size_t)ctx->ttape_cap * ctx->ttape_blk : 0);
         const size_t cap = avail > later + keep ? (avail - later - keep) / blk : 0;
-        if (ctx->ttape && cap < ctx->ttape_cap) {  // the run needs the memory elsewhere now
+        // the blocks to hold: what the last taped forward of this geometry needed and an
+        // eighth more, or, before any is known, all the room there is
+        const bool known = ctx->ttape_need > 0 && ctx->ttape_need_blk == blk;
+        const size_t need = known ? (size_t)ctx->ttape_need : 0;
+        const size_t want = known ? std::min(cap, need + need / 8 + nt) : cap;
+        // the tape is allocated again when it has another block size, when the run needs
+        // its memory elsewhere now, when it is short of a known need that now fits, or
+        // when it holds well over what is wanted (the rest is left to the caller)
+        if (ctx->ttape && (ctx->ttape_blk != blk || cap < ctx->ttape_cap ||
+                           (known && ctx->ttape_cap < need && want > ctx->ttape_cap) ||
+                           ctx->ttape_cap > want + want / 4)) {
             dfree(ctx, ctx->ttape);
             ctx->ttape = nullptr;
             ctx->ttape_cap = 0;
         }
-        if (cap < nt) return PF_OK;
         if (!ctx->ttape) {
+            if (want < nt) return PF_OK;
             void* p;
-            if (dalloc(ctx, &p, cap * blk) != PF_OK) {
+            if (dalloc(ctx, &p, want * blk) != PF_OK) {
                 cudaGetLastError();
                 return PF_OK;
             }
             ctx->ttape = (float*)p;
-            ctx->ttape_cap = cap;
+            ctx->ttape_cap = want;
+            ctx->ttape_blk = blk;
         }
     }
     CK(cudaMemsetAsync(ctx->ttape_used, 0, sizeof(unsigned long long), ctx->st));
@@ -1038,6 +1087,7 @@ int tape_begin(pf_ctx* ctx, int T) {
     tape_reset(ctx);
     for (long& v : ctx->qcache_ver) v = -1;
     for (int& v : ctx->qmask_state) v = 0;
+    qcache_decide(ctx);
     ctx->q_key_epoch = -1;
     ctx->actrec_end.clear();
     ctx->actrec_on = true;
@@ -1550,6 +1600,32 @@ int pf_set_tuning(pf_ctx* ctx, const pf_tuning* t) {
     return apply_tuning(ctx, t);
 }
 
+int pf_memory_stats(pf_ctx* ctx, pf_memory_stats_t* out) {
+    if (!ctx || !out) return fail(ctx, PF_EINVAL, "pf_memory_stats: NULL argument");
+    *out = pf_memory_stats_t{};
+    const size_t sb = ctx->form == PF_DIFF ? diff_state_bytes(ctx) : 0;
+    out->checkpoint_bytes = (long long)ctx->arena_cap * (long long)sb;
+    out->segment_bytes = (long long)ctx->seg_cap * (long long)sb;
+    for (float* b : ctx->qcache)
+        if (b) out->qcache_bytes += 8LL * (long long)plane_elems(ctx) * (long long)sizeof(float);
+    out->tape_bytes = ctx->ttape ? (long long)(ctx->ttape_cap * ctx->ttape_blk) : 0;
+    out->K = ctx->K;
+    out->tape_short = ctx->ttape_short ? 1 : 0;
+    const size_t nr = ctx->ttape_rec.size();
+    out->tape_launches = (int)nr;
+    if (ctx->ttape_used && nr > 0) {
+        unsigned long long used = 0;
+        std::vector<unsigned long long> meta(4 * nr);
+        CK(cudaMemcpyAsync(&used, ctx->ttape_used, sizeof(used), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(meta.data(), ctx->ttape_meta, meta.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        out->tape_used_bytes = (long long)(std::min<unsigned long long>(used, ctx->ttape_cap) * ctx->ttape_blk);
+        for (size_t L = 0; L < nr; ++L) out->tape_recorded += meta[4 * L + 3] ? 1 : 0;
+    }
+    return PF_OK;
+}
+
 int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t) {
     if (!ctx || !t) return fail(nullptr, PF_EINVAL, "pf_get_tuning: NULL argument");
     *t = ctx->tun;
@@ -1653,6 +1729,7 @@ int pf_autotune_ckpt(pf_ctx* ctx, const uint8_t* S_init, int T, int* K_chosen) {
     // (no launch is cut short at a checkpoint) around the interval it picks
     ctx->tun.K = 0;
     tape_reset(ctx);
+    qcache_decide(ctx);
     const int K0 = choose_K(ctx, T);
     std::vector<int> cand = {0};
     if (K0 > 1) {
@@ -1682,6 +1759,14 @@ int pf_autotune_ckpt(pf_ctx* ctx, const uint8_t* S_init, int T, int* K_chosen) {
     for (size_t c = 1; c < cand.size(); ++c)
         if (t_ms[c] < t_ms[best]) best = c;
     ctx->tun.K = cand[best];
+    // a segment buffer sized for a larger candidate is given back: the next backward
+    // allocates the chosen interval's
+    if (ctx->seg_buf && ctx->seg_cap > std::max(cand[best], 2)) {
+        dfree(ctx, ctx->seg_buf);
+        ctx->seg_buf = nullptr;
+        ctx->seg_cap = 0;
+        ctx->seg_halo = 0;
+    }
     tune_cache_put(key, ctx->tun);
     if (K_chosen) *K_chosen = cand[best];
     return PF_OK;
@@ -2030,8 +2115,13 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             CK(cudaMemsetAsync(ctx->dflags + 14, 0, sizeof(int), ctx->st));
             CK(cudaStreamSynchronize(ctx->st));
             rec_at.assign((size_t)(T_end - ctx->tape_start + 1), -1);
+            ctx->ttape_need = 0;
+            ctx->ttape_need_blk = ctx->ttape_blk;
+            ctx->ttape_short = false;
             for (size_t L = 0; L < nr; ++L) {
                 const int t0 = ctx->ttape_rec[L].first - ctx->tape_start;
+                ctx->ttape_need += ctx->ttape_meta_h[4 * L + 1] * ctx->ttape_meta_h[4 * L + 2];
+                if (!ctx->ttape_meta_h[4 * L + 3]) ctx->ttape_short = true;
                 if (ctx->ttape_meta_h[4 * L + 3] && t0 >= 0 && t0 < (int)rec_at.size()) rec_at[t0] = (int)L;
             }
         }
@@ -2044,20 +2134,18 @@ int pf_backward(pf_ctx* ctx, const float* dL_da_T, const float* dL_db_T, double 
             // ones in slots 1.. of the segment buffer (slot 0 unused)
             float* seg = ctx->seg_buf;
             if (kern == 2) {
-                // blocked recompute: the slots hold zeros wherever seg_dirty is clear
+                // blocked recompute: the slots hold zeros outside each tile's seg_rng range
                 const int halo = blocked_k(ctx) <= 4 ? 4 : 8;
                 if (ctx->seg_halo != halo) {
-                    if (!ctx->seg_dirty) {
+                    const size_t nt = (size_t)std::max(diff_blocked_tiles(8, ctx->H, ctx->P),
+                                                       diff_blocked_tiles(4, ctx->H, ctx->P));
+                    if (!ctx->seg_rng) {
                         void* p;
-                        const int nt = std::max(diff_blocked_tiles(8, ctx->H, ctx->P), diff_blocked_tiles(4, ctx->H, ctx->P));
-                        if ((rc = dalloc(ctx, &p, (size_t)nt))) return rc;
-                        ctx->seg_dirty = (uint8_t*)p;
+                        if ((rc = dalloc(ctx, &p, nt * sizeof(uint32_t)))) return rc;
+                        ctx->seg_rng = (uint32_t*)p;
                     }
                     CK(cudaMemsetAsync(seg, 0, sbytes * (size_t)ctx->seg_cap, ctx->st));
-                    CK(cudaMemsetAsync(ctx->seg_dirty, 0,
-                                       (size_t)std::max(diff_blocked_tiles(8, ctx->H, ctx->P),
-                                                        diff_blocked_tiles(4, ctx->H, ctx->P)),
-                                       ctx->st));
+                    CK(cudaMemsetAsync(ctx->seg_rng, 0, nt * sizeof(uint32_t), ctx->st));
                     ctx->seg_halo = halo;
                 }
             } else {

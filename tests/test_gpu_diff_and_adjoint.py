@@ -320,9 +320,16 @@ def test_tile_tape_gives_the_recomputed_gradients(pf, orc, K, k):
         out = m.forward(cuda(S0), T).cpu().numpy()
         g4, gpv, _ = m.backward(w, None)
         prof = pf.pf_profile_read(m.h, reset=True)
-        res[tape] = (out, list(g4), gpv.cpu().numpy(), prof.get("segment_from_tape", (0,))[0])
+        mem = pf.pf_memory_stats(m.h)
+        res[tape] = (out, list(g4), gpv.cpu().numpy(), prof.get("segment_from_tape", (0,))[0], mem)
         m.close()
     assert res[0][3] > 0 and res[1][3] == 0
+    # the tape held every launch of the forward (a few MB at this size); none without it
+    mem0, mem1 = res[0][4], res[1][4]
+    assert mem0["tape_launches"] > 0 and mem0["tape_recorded"] == mem0["tape_launches"]
+    assert 0 < mem0["tape_used_bytes"] <= mem0["tape_bytes"] and mem0["tape_short"] == 0
+    assert mem1["tape_bytes"] == 0 and mem1["tape_launches"] == 0
+    assert mem0["K"] == mem1["K"] == K and mem0["segment_bytes"] >= (K - 1) * 2 * H * W * 4
     assert np.array_equal(res[0][0], res[1][0])
     assert res[0][1] == res[1][1]
     assert np.array_equal(res[0][2], res[1][2])
