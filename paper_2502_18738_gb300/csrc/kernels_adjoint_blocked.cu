@@ -531,15 +531,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 // with a = 0, or outside the grid). This kernel runs them apart from the live tiles: no
 // tensor memory and no cross-lane exchange. The region's q, state and lambda are staged
 // by TMA during the previous tile's steps; G stays in registers and l_a + l_b goes
-// through a zero-bordered shared-memory plane.
+// through two zero-bordered shared-memory planes (a step reads one and writes the other,
+// one barrier a step).
 constexpr int kFM = 8;                              // rows per thread
 constexpr int kFThreads = kCT * (kRT / kFM);        // 512
 struct FrozenSmem {
     float q[8 * kPlane];            // q stage (TMA)
     float st[2 * kPlane];           // state stage (TMA); then 1 - a and sigma (as int bits) in place
     float lam[2 * kPlane];          // lambda stage (TMA)
-    float ln[kRT + 2][kCT + 2];     // l_a + l_b of the region; the border stays 0
+    float ln[2][kRT + 2][kCT + 2];  // l_a + l_b of the region, by step parity; the borders stay 0
 };
+static_assert(sizeof(FrozenSmem) + 128 <= 227 * 1024, "k_adjoint_frozen's shared memory");
 
 __global__ void __launch_bounds__(kFThreads, 1)
     k_adjoint_frozen(const __grid_constant__ CUtensorMap tst, const __grid_constant__ CUtensorMap tst0,
@@ -574,7 +576,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
         else tma_load_3d(sm.st, &tst, &bar, c0, r0, 2 * z);
         tma_load_3d(sm.lam, &tlam, &bar, c0, r0, 0);
     };
-    for (int i = tid; i < (kRT + 2) * (kCT + 2); i += kFThreads) (&sm.ln[0][0])[i] = 0.0f;
+    for (int i = tid; i < 2 * (kRT + 2) * (kCT + 2); i += kFThreads) (&sm.ln[0][0][0])[i] = 0.0f;
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -609,7 +611,7 @@ __global__ void __launch_bounds__(kFThreads, 1)
             la[m] = lv ? sm.lam[o] : 0.0f;
             lb[m] = lv ? sm.lam[kPlane + o] : 0.0f;
             sgp[m >> 2] |= (uint32_t)sg << (8 * (m & 3));
-            sm.ln[ys + m + 1][x + 1] = la[m] + lb[m];
+            sm.ln[0][ys + m + 1][x + 1] = la[m] + lb[m];
             stA[o] = signbit(A) ? -A : ((int32_t)__float_as_uint(B) < 0 ? 1.0f : 1.0f - A);
             stB[o] = __int_as_float(sg);
         }
@@ -634,14 +636,15 @@ __global__ void __launch_bounds__(kFThreads, 1)
         fence_proxy_async();  // these generic reads of the stages precede the next TMA writes
         __syncthreads();      // every stage fully read
         if (tid == 0 && next < nfz) issue(next);
-        // the steps: rows ys-1 .. ys+kFM of l_a + l_b in columns x-1, x, x+1, read, then written
+        // the steps: rows ys-1 .. ys+kFM of l_a + l_b in columns x-1, x, x+1 read from one
+        // plane, the new values written into the other
         for (int s = 0; s < n; ++s) {
+            const int p = s & 1;
             float w[kFM + 2][3];
 #pragma unroll
             for (int r = 0; r < kFM + 2; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) w[r][c] = sm.ln[ys + r][x + c];
-            __syncthreads();
+                for (int c = 0; c < 3; ++c) w[r][c] = sm.ln[p][ys + r][x + c];
 #pragma unroll
             for (int m = 0; m < kFM; ++m) {
                 // target i - dir(d) of source (ys + m, x) sits at window (m + 1 - dr, 1 - dc)
@@ -650,9 +653,9 @@ __global__ void __launch_bounds__(kFThreads, 1)
                 for (int d = 0; d < 8; ++d) own = fmaf(G[m][d], w[m + 1 - dir_dr(d)][1 - dir_dc(d)], own);
                 const bool lv = ((sgp[m >> 2] >> (8 * (m & 3))) & 0xffu) != (uint32_t)kSigmaZero;
                 lb[m] = lv ? fmaf(pc, lb[m], own) : 0.0f;
-                sm.ln[ys + m + 1][x + 1] = la[m] + lb[m];
+                sm.ln[p ^ 1][ys + m + 1][x + 1] = la[m] + lb[m];
             }
-            __syncthreads();
+            __syncthreads();  // the new plane complete, the old one read by every thread
         }
         // lambda at t0 of the interior (sigma unchanged); a frozen tile adds no dL/dq
         const int gc = c0 + x;
