@@ -46,6 +46,9 @@ HIDDEN = dict(p_h=0.5, c1=0.05, c2=0.12, a=0.08)
 METRIC = "cell-updates/s fwd+adjoint (8192^2 diff form, T=2000)"
 WORKLOAD = "8192x8192 differentiable fwd+adjoint, T=2000, wind resampled every 100 steps"
 B_FWD, B_ADJ = 16, 24  # algorithmic bytes per cell-step: (a, b) in + out; state, lambda in, lambda out
+# a frozen tile's region is constant over its adjoint launch: per cell and launch it reads
+# q (32 B), the state once (8 B) and lambda (8 B), and writes lambda (8 B) and sigma (1 B)
+B_FROZEN_LAUNCH = 57
 B_DISC = 2  # discrete: the uint8 state in + out
 
 
@@ -538,15 +541,20 @@ def main():
     # the timed steps run without the library's per-launch CUDA events (launches are
     # counted on the host either way); one more step with them gives the per-kernel times
     pf.pf_profile_read(m.h, reset=True)
+    mem0 = pf.pf_memory_stats(m.h)
     with Clocks(args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv else None) as clk:
         ms = timed(step, args.steps)
     counts = pf.pf_profile_read(m.h, reset=True)
+    mem1 = pf.pf_memory_stats(m.h)
     gpu_launches = sum(v[0] for v in counts.values())
     pf.pf_set_tuning(m.h, **base, profile=1)
     step()
     torch.cuda.synchronize()
     prof = pf.pf_profile_read(m.h, reset=True)  # one profiled step
     memst = pf.pf_memory_stats(m.h)  # the gradient path's memory and the tape's use, after it
+    # device allocations and frees the library made during the timed steps (0 when steady)
+    memst["allocations_in_timed_steps"] = mem1["allocations"] - mem0["allocations"]
+    memst["frees_in_timed_steps"] = mem1["frees"] - mem0["frees"]
     pf.pf_set_tuning(m.h, **base)
     tun = pf.pf_get_tuning(m.h)
     cells = Hs * Ws * Ts
@@ -574,7 +582,8 @@ def main():
         if n_l == 0 or t_l <= 0.0:
             continue
         if kname == "adjoint_frozen":
-            computed[kname] = (frozen_cs, B_ADJ)
+            # its own bytes: B_FROZEN_LAUNCH per cell over the launch's steps (T / launches)
+            computed[kname] = (frozen_cs, B_FROZEN_LAUNCH * n_l / Ts)
         elif kname == "adjoint_blocked":
             computed[kname] = (cs_l - sk_l - (frozen_cs if prof.get("adjoint_frozen", (0,))[0] else 0), B_ADJ)
         elif kname in ("adjoint_step",):
@@ -606,8 +615,12 @@ def main():
         # the blocked adjoint as a whole (both kernels of each launch)
         comp_adj = computed["adjoint_blocked"][0] + frozen_cs
         t_adj = prof["adjoint_blocked"][2] + prof["adjoint_frozen"][2]
+        # frac: the adjoint's 24 B per computed cell-step; frac_own_bytes: each kernel's
+        # own bytes (a frozen tile reads its state once a launch, not once a step)
+        own = computed["adjoint_blocked"][0] * B_ADJ + frozen_cs * computed["adjoint_frozen"][1]
         roof["adjoint_both_kernels"] = {"achieved": B_ADJ * comp_adj / (t_adj / 1000.0) / 1e9,
-                                        "frac": B_ADJ * comp_adj / (t_adj / 1000.0) / 1e9 / hbm, "ms": t_adj}
+                                        "frac": B_ADJ * comp_adj / (t_adj / 1000.0) / 1e9 / hbm, "ms": t_adj,
+                                        "frac_own_bytes": own / (t_adj / 1000.0) / 1e9 / hbm}
 
     # end to end through the C ABI with host buffers: inputs H2D, gradients D2H each step
     e2e = None

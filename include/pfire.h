@@ -261,7 +261,9 @@ int pf_get_tuning(const pf_ctx* ctx, pf_tuning* t);
  * tape_launches: blocked launches of that forward the tape tried to record;
  * tape_recorded: those it had room for (the others are recomputed by the backward).
  * K: that forward's checkpoint interval; tape_short: the tape of the last backward
- * ran short (some of its launches were recomputed). Synchronises the context's stream. */
+ * ran short (some of its launches were recomputed). allocations / frees: the device
+ * allocations and frees the context has made so far (steady runs make none).
+ * Synchronises the context's stream. */
 typedef struct pf_memory_stats_t {
     long long checkpoint_bytes;
     long long segment_bytes;
@@ -272,6 +274,8 @@ typedef struct pf_memory_stats_t {
     int tape_recorded;
     int K;
     int tape_short;
+    long long allocations;
+    long long frees;
 } pf_memory_stats_t;
 int pf_memory_stats(pf_ctx* ctx, pf_memory_stats_t* out);
 

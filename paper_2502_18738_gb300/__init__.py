@@ -80,7 +80,8 @@ class PfMemoryStats(ctypes.Structure):
     _fields_ = [("checkpoint_bytes", ctypes.c_longlong), ("segment_bytes", ctypes.c_longlong),
                 ("qcache_bytes", ctypes.c_longlong), ("tape_bytes", ctypes.c_longlong),
                 ("tape_used_bytes", ctypes.c_longlong), ("tape_launches", ctypes.c_int),
-                ("tape_recorded", ctypes.c_int), ("K", ctypes.c_int), ("tape_short", ctypes.c_int)]
+                ("tape_recorded", ctypes.c_int), ("K", ctypes.c_int), ("tape_short", ctypes.c_int),
+                ("allocations", ctypes.c_longlong), ("frees", ctypes.c_longlong)]
 
 
 class PfJob(ctypes.Structure):

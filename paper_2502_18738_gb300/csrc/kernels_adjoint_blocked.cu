@@ -553,10 +553,13 @@ __global__ void __launch_bounds__(kFThreads, 1)
     FrozenSmem& sm = *reinterpret_cast<FrozenSmem*>(fraw + ((128u - (smem_u32(fraw) & 127u)) & 127u));
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_next;
+    // least and greatest sigma of the region's cells with a > 0 (reset for every tile)
+    __shared__ unsigned s_tlo, s_thi;
     const int nfz = counts[2];
     int k = blockIdx.x;
     if (k >= nfz) return;
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int x = tid % kCT;
     const int ys = (tid / kCT) * kFM;
     const size_t plane = (size_t)H * pitch;
@@ -582,6 +585,8 @@ __global__ void __launch_bounds__(kFThreads, 1)
         fence_mbar_init();
         issue(k);
         s_next = (int)gridDim.x + atomicAdd(work, 1);
+        s_tlo = 255u;
+        s_thi = 0u;
     }
     __syncthreads();
     uint32_t parity = 0u;
@@ -599,9 +604,11 @@ __global__ void __launch_bounds__(kFThreads, 1)
             return;
         }
         parity ^= 1u;
-        // stage -> registers and planes: lambda (0 where a = 0), 1 - a and sigma in place
+        // stage -> registers and planes: lambda (0 where a = 0), 1 - a (0 where a = 0) and
+        // sigma in place
         float la[kFM], lb[kFM];
         uint32_t sgp[kFM / 4] = {};  // sigma of the cells (at t and t + 1 alike), a byte each
+        unsigned tlo = 255u, thi = 0u;
 #pragma unroll
         for (int m = 0; m < kFM; ++m) {
             const int o = (ys + m) * kCT + x;
@@ -612,25 +619,51 @@ __global__ void __launch_bounds__(kFThreads, 1)
             lb[m] = lv ? sm.lam[kPlane + o] : 0.0f;
             sgp[m >> 2] |= (uint32_t)sg << (8 * (m & 3));
             sm.ln[0][ys + m + 1][x + 1] = la[m] + lb[m];
-            stA[o] = signbit(A) ? -A : ((int32_t)__float_as_uint(B) < 0 ? 1.0f : 1.0f - A);
+            stA[o] = !lv ? 0.0f : (signbit(A) ? -A : ((int32_t)__float_as_uint(B) < 0 ? 1.0f : 1.0f - A));
             stB[o] = __int_as_float(sg);
+            tlo = min(tlo, (unsigned)sg);            // kSigmaZero is the greatest value
+            thi = max(thi, lv ? (unsigned)sg : 0u);
+        }
+        tlo = __reduce_min_sync(0xffffffffu, tlo);
+        thi = __reduce_max_sync(0xffffffffu, thi);
+        if (lane == 0) {
+            atomicMin(&s_tlo, tlo);
+            atomicMax(&s_thi, thi);
         }
         __syncthreads();
+        // one sigma for every cell with a > 0 in the region (or none): every transfer's
+        // unit ratio is 1 and a target with a = 0 has 1 - a stored as 0, so G needs no sigma
+        const bool one_tier = s_tlo >= s_thi;
         // the coefficients of this thread's sources
         float G[kFM][8];
+        if (one_tier) {
 #pragma unroll
-        for (int m = 0; m < kFM; ++m) {
-            const int y = ys + m;
-            const int si = (int)((sgp[m >> 2] >> (8 * (m & 3))) & 0xffu);
+            for (int m = 0; m < kFM; ++m) {
+                const int y = ys + m;
+                const bool si_live = ((sgp[m >> 2] >> (8 * (m & 3))) & 0xffu) != (uint32_t)kSigmaZero;
 #pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const int jy = y - dir_dr(d), jx = x - dir_dc(d);
-                // targets on the region's edge rows and columns contribute nothing
-                const bool inr = jy >= 1 && jy < kRT - 1 && jx >= 1 && jx < kCT - 1;
-                const int oj = inr ? jy * kCT + jx : 0;
-                const int sj = inr ? __float_as_int(stB[oj]) : kSigmaZero;
-                const bool use = si != kSigmaZero && sj != kSigmaZero;
-                G[m][d] = use ? (stA[oj] * sm.q[d * kPlane + oj]) * exp2i(64 * (sj - si)) : 0.0f;
+                for (int d = 0; d < 8; ++d) {
+                    const int jy = y - dir_dr(d), jx = x - dir_dc(d);
+                    const bool inr = jy >= 1 && jy < kRT - 1 && jx >= 1 && jx < kCT - 1;
+                    const int oj = inr ? jy * kCT + jx : 0;
+                    G[m][d] = (si_live && inr) ? stA[oj] * sm.q[d * kPlane + oj] : 0.0f;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < kFM; ++m) {
+                const int y = ys + m;
+                const int si = (int)((sgp[m >> 2] >> (8 * (m & 3))) & 0xffu);
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    const int jy = y - dir_dr(d), jx = x - dir_dc(d);
+                    // targets on the region's edge rows and columns contribute nothing
+                    const bool inr = jy >= 1 && jy < kRT - 1 && jx >= 1 && jx < kCT - 1;
+                    const int oj = inr ? jy * kCT + jx : 0;
+                    const int sj = inr ? __float_as_int(stB[oj]) : kSigmaZero;
+                    const bool use = si != kSigmaZero && sj != kSigmaZero;
+                    G[m][d] = use ? (stA[oj] * sm.q[d * kPlane + oj]) * exp2i(64 * (sj - si)) : 0.0f;
+                }
             }
         }
         fence_proxy_async();  // these generic reads of the stages precede the next TMA writes
@@ -641,10 +674,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
         for (int s = 0; s < n; ++s) {
             const int p = s & 1;
             float w[kFM + 2][3];
+            // the thread's own column (rows ys .. ys+7) is what it wrote last: la + lb
 #pragma unroll
             for (int r = 0; r < kFM + 2; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) w[r][c] = sm.ln[p][ys + r][x + c];
+                for (int c = 0; c < 3; ++c)
+                    w[r][c] = (c == 1 && r >= 1 && r <= kFM) ? la[r - 1] + lb[r - 1] : sm.ln[p][ys + r][x + c];
 #pragma unroll
             for (int m = 0; m < kFM; ++m) {
                 // target i - dir(d) of source (ys + m, x) sits at window (m + 1 - dr, 1 - dc)
@@ -671,8 +706,12 @@ __global__ void __launch_bounds__(kFThreads, 1)
                 }
             }
         }
-        if (tid == 0 && next < nfz) s_next = (int)gridDim.x + atomicAdd(work, 1);
-        __syncthreads();  // s_next
+        if (tid == 0) {
+            if (next < nfz) s_next = (int)gridDim.x + atomicAdd(work, 1);
+            s_tlo = 255u;
+            s_thi = 0u;
+        }
+        __syncthreads();  // s_next, the sigma bounds reset
         k = next;
     }
 }

@@ -247,6 +247,7 @@ struct pf_ctx {
     long long cell_steps[K_NKINDS] = {0};
     double prof_ms[K_NKINDS] = {0};
     std::vector<void*> allocs;
+    long long n_allocs = 0, n_frees = 0;  // device allocations and frees made so far
     std::string err = "no error";
 };
 
@@ -287,11 +288,13 @@ int dalloc(pf_ctx* ctx, void** p, size_t bytes) {
         return fail(ctx, PF_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     }
     ctx->allocs.push_back(*p);
+    ++ctx->n_allocs;
     return PF_OK;
 }
 
 void dfree(pf_ctx* ctx, void* p) {
     if (!p) return;
+    ++ctx->n_frees;
     auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
     if (it != ctx->allocs.end()) ctx->allocs.erase(it);
     if (ctx->pool) cudaFreeAsync(p, ctx->st);
@@ -1611,6 +1614,8 @@ int pf_memory_stats(pf_ctx* ctx, pf_memory_stats_t* out) {
     out->tape_bytes = ctx->ttape ? (long long)(ctx->ttape_cap * ctx->ttape_blk) : 0;
     out->K = ctx->K;
     out->tape_short = ctx->ttape_short ? 1 : 0;
+    out->allocations = ctx->n_allocs;
+    out->frees = ctx->n_frees;
     const size_t nr = ctx->ttape_rec.size();
     out->tape_launches = (int)nr;
     if (ctx->ttape_used && nr > 0) {
