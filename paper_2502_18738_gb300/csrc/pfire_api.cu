@@ -1053,10 +1053,11 @@ int ttape_begin(pf_ctx* ctx, int T) {
         const size_t avail = free_b + (ctx->ttape ? (size_t)ctx->ttape_cap * ctx->ttape_blk : 0);
         const size_t cap = avail > later + keep ? (avail - later - keep) / blk : 0;
         // the blocks to hold: what the last taped forward of this geometry needed and an
-        // eighth more, or, before any is known, all the room there is
+        // eighth more, or, before any is known, the room there is up to what T steps of
+        // every tile would take
         const bool known = ctx->ttape_need > 0 && ctx->ttape_need_blk == blk;
         const size_t need = known ? (size_t)ctx->ttape_need : 0;
-        const size_t want = known ? std::min(cap, need + need / 8 + nt) : cap;
+        const size_t want = known ? std::min(cap, need + need / 8 + nt) : std::min(cap, (size_t)T * nt);
         // the tape is allocated again when it has another block size, when the run needs
         // its memory elsewhere now, when it is short of a known need that now fits, or
         // when it holds well over what is wanted (the rest is left to the caller)
