@@ -332,12 +332,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                             qv[d] = __uint_as_float(tmv[d]);
                             gv[d] = __uint_as_float(tmv[8 + d]);
                         }
+                        // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
+                        const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
+                        // no neighbour with b in tier 0 (b = 0, or a tiered b below 2^-64,
+                        // stored negative): every factor 1 - b_i q_dj is exactly 1. The short
+                        // path below is taken when that holds for every cell of the warp's row
+                        // that has a > 0 at t + 1; otherwise the whole row takes the general
+                        // arithmetic, which gives the short path's bits on such cells (so a row
+                        // of both kinds does not run both paths one after the other).
+                        float nbmax = nb[0];
+#pragma unroll
+                        for (int d = 1; d < 8; ++d) nbmax = fmaxf(nbmax, nb[d]);
+                        const bool quiet = __all_sync(0xffffffffu, nbmax <= 0.0f || !live);
                         if (live) {
                             // The region's edge columns (!xin) contribute nothing: they take
                             // the same path on their clamped (in-bounds) window with tg = 0 and
                             // P = 0, which leaves only l_a <- l_a scl, instead of diverging.
-                            // neighbours in direction order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1) (1,-1) (1,0) (1,1)
-                            const float nb[8] = {bu[0], bu[1], bu[2], bm[0], bm[2], bd[0], bd[1], bd[2]};
                             float r[8];  // 2^(64 (sigma'(j) - sigma(i))): to the units of source i
                             if constexpr (kSlow) {
                                 const int ns[8] = {su[0], su[1], su[2], sm3[0], sm3[2], sd[0], sd[1], sd[2]};
@@ -351,12 +361,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                             // l_P_j in units 2^(64 sigma'(j)); on the single-tier path already in
                             // the sources' units
                             const float tg = xin ? (kSlow ? ln * ua : (ln * ua) * Up) : 0.0f;
-                            // no neighbour with b in tier 0 (b = 0, or a tiered b below 2^-64,
-                            // stored negative): every factor 1 - b_i q_dj is exactly 1
-                            float nbmax = nb[0];
-#pragma unroll
-                            for (int d = 1; d < 8; ++d) nbmax = fmaxf(nbmax, nb[d]);
-                            const bool quiet = nbmax <= 0.0f;
                             if (quiet) {
                                 // P = 0 and every leave-one-out product is exactly 1, so t_d = tg:
                                 // the general arithmetic below with its factors folded (the same
