@@ -136,6 +136,11 @@ class Clocks:
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi's start-up (NVML over every GPU of the node) is kept out of the
+            # timed region: the region starts once the first sample has arrived
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0 and self.p.poll() is None:
+                time.sleep(0.02)
         except Exception:
             self.p = None
         return self
