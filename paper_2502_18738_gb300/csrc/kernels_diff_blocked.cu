@@ -460,6 +460,12 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
                                                    unsigned long long& sk, unsigned long long& wr) {
     constexpr int kI = kRT - 2 * kHalo;
     const int ty = tile / tiles_x, tx = tile % tiles_x;
+    // the tile's own entries, loaded with the flags below so that their latencies overlap
+    // (each is read before this warp writes it, and no other warp touches them)
+    const uint32_t me = act_in[tile];
+    const int qr = qrun[tile];
+    const uint32_t rng = seg_rng ? seg_rng[tile] : 0u;
+    const bool od = out_dirty ? out_dirty[tile] != 0 : false;
     // the 7 x 7 flags around the tile, two per lane (independent loads), reduced into the
     // ORs over the 3 x 3, 5 x 5 and 7 x 7 tiles and the AND of kQt over the 5 x 5 (tiles
     // outside the grid count as quiescent and empty)
@@ -480,11 +486,10 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     const uint32_t around5 = __reduce_or_sync(0xffffffffu, o5);
     const uint32_t around7 = __reduce_or_sync(0xffffffffu, o7);
     const bool qseg5 = __reduce_and_sync(0xffffffffu, q5) != 0u;
-    const uint32_t me = act_in[tile];
     const uint8_t qb = (me & kQt) ? kQb : 0;  // quiescent in every earlier launch of the segment
     // the tile's dirty slot range grows by [w0, slot_a + n) (lane 0)
     auto rng_add = [&](int w0) {
-        const uint32_t r = seg_rng[tile];
+        const uint32_t r = rng;
         int lo = (int)(r & 0xffffu), hi = (int)(r >> 16);
         if (lo >= hi) lo = w0, hi = slot_a + n;
         else lo = min(lo, w0), hi = max(hi, slot_a + n);
@@ -506,8 +511,7 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     const bool void_tile = seg_rng && !(around & kActA);
     if (void_tile) {
         write_all = false;
-        const uint32_t r = seg_rng[tile];  // read by every lane before lane 0 changes it
-        const int lo = (int)(r & 0xffffu), hi = (int)(r >> 16);
+        const int lo = (int)(rng & 0xffffu), hi = (int)(rng >> 16);
         const int z0 = max(lo, slot_a), z1 = min(hi, slot_a + n);
         if (z0 < z1) {
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -535,13 +539,12 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     if (stale) write_all = false;
     // a tile that skipped its last write takes its state from slot 0
     const float* src = (frozen && slot0 && (me & kStale)) ? slot0 : in;
-    const int qr = qrun[tile];
     bool copy_out = out && !(out_age > 0 && qr >= out_age);
     // a checkpoint slot with dirty bits (out_dirty): an all-zero tile (a = 0 in the
     // interior, so b = 0 too) is written only if the slot's tile may hold nonzeros
     bool zero_out = false;
     if (copy_out && out_dirty && !(me & kActA)) {
-        zero_out = dirty_unknown || out_dirty[tile];
+        zero_out = dirty_unknown || od;
         copy_out = false;
     }
     if (zero_out) {
