@@ -232,11 +232,12 @@ int pf_loss_bce_noalloc(const float* a, const float* y, int64_t n, float* dL_da,
  *   tape      differentiable form with checkpoints (K > 1) and the blocked kernels:
  *             0 = keep a tile tape (every live tile's states of every forward launch)
  *             so that the backward copies each segment's states instead of recomputing
- *             them; a segment the tape does not cover is recomputed. The tape takes the
- *             device memory the backward does not need, less a sixteenth of the
- *             device (at least 16 GB) left free; once a backward has seen how much the tape
- *             needs, it holds that and an eighth more. It is kept by the context until
- *             pf_destroy. The per-epoch q cache (the forward's q of every wind epoch
+ *             them; a segment the tape does not cover is recomputed. The first tape
+ *             takes the device memory the backward does not need, less a sixteenth of
+ *             the device (at least 16 GB) left free, up to what T steps of every tile
+ *             would take (18 KB a tile and step at the 8-cell halo); once a backward has
+ *             seen how much the tape needs, it holds that and an eighth more. It is
+ *             kept by the context until pf_destroy. The per-epoch q cache (the forward's q of every wind epoch
  *             kept for the adjoint) is kept beside it only where both fit; otherwise
  *             the backward prepares q again. 1 = no tape: always recompute.
  * Results do not depend on any of these (the same arithmetic in every variant), except
