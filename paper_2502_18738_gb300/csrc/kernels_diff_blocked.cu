@@ -565,27 +565,44 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
     if (seg_rng && write_all && lane == 0) rng_add(last_only ? slot_a + n - 1 : slot_a);
     uint32_t nw = 0u;  // float4 pairs this lane wrote
     if (copy_out || write_all) {
-        // float4 columns: c0 and pitch are multiples of 4 (and 8, kI - 8 are too)
-        for (int i = lane; i < kI * (kI / 4); i += 32) {
-            const int ir = i / (kI / 4), ic = 4 * (i % (kI / 4));
-            const int gr = r0 + ir, gc = c0 + ic;
-            if (gr >= H || gc >= pitch) continue;
-            const size_t j = (size_t)gr * pitch + gc;
-            const float4 a = __ldg(reinterpret_cast<const float4*>(src + j));
-            const float4 b = __ldg(reinterpret_cast<const float4*>(src + gplane + j));
-            if (copy_out) {
-                *reinterpret_cast<float4*>(out + j) = a;
-                *reinterpret_cast<float4*>(out + gplane + j) = b;
-                ++nw;
+        // float4 columns: c0 and pitch are multiples of 4 (and 8, kI - 8 are too). Each
+        // lane loads kU float4 pairs before it stores any, so their latencies overlap.
+        constexpr int kPer = kI * (kI / 4);
+        constexpr int kU = 2;
+        for (int i0 = lane; i0 < kPer; i0 += 32 * kU) {
+            float4 a[kU], b[kU];
+            size_t jj[kU];
+            bool ok[kU], band[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int i = i0 + 32 * u;
+                const int ir = i / (kI / 4), ic = 4 * (i % (kI / 4));
+                const int gr = r0 + ir, gc = c0 + ic;
+                ok[u] = i < kPer && gr < H && gc < pitch;
+                band[u] = ir < 8 || ir >= kI - 8 || ic < 8 || ic >= kI - 8;
+                jj[u] = (size_t)gr * pitch + gc;
+                if (ok[u]) {
+                    a[u] = __ldg(reinterpret_cast<const float4*>(src + jj[u]));
+                    b[u] = __ldg(reinterpret_cast<const float4*>(src + gplane + jj[u]));
+                }
             }
-            if (write_all) {
-                const bool band = ir < 8 || ir >= kI - 8 || ic < 8 || ic >= kI - 8;
-                for (int s = last_only ? n - 1 : 0; s < n; ++s) {
-                    if (band_only && s < n - 1 && !band) continue;
-                    float* o = all_out + (size_t)s * all_stride;
-                    *reinterpret_cast<float4*>(o + j) = a;
-                    *reinterpret_cast<float4*>(o + gplane + j) = b;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                if (!ok[u]) continue;
+                const size_t j = jj[u];
+                if (copy_out) {
+                    *reinterpret_cast<float4*>(out + j) = a[u];
+                    *reinterpret_cast<float4*>(out + gplane + j) = b[u];
                     ++nw;
+                }
+                if (write_all) {
+                    for (int s = last_only ? n - 1 : 0; s < n; ++s) {
+                        if (band_only && s < n - 1 && !band[u]) continue;
+                        float* o = all_out + (size_t)s * all_stride;
+                        *reinterpret_cast<float4*>(o + j) = a[u];
+                        *reinterpret_cast<float4*>(o + gplane + j) = b[u];
+                        ++nw;
+                    }
                 }
             }
         }
@@ -603,7 +620,7 @@ __device__ __forceinline__ void fwd_tile(const float* __restrict__ in, int H, in
 }
 
 template <int kHalo>
-__global__ void __launch_bounds__(256) k_fwd_tiles(const float* __restrict__ in, int H, int W, int pitch,
+__global__ void __launch_bounds__(256, 5) k_fwd_tiles(const float* __restrict__ in, int H, int W, int pitch,
                                                    int tiles_x, int tiles_y, int n, const uint8_t* __restrict__ act_in,
                                                    uint8_t* __restrict__ act_out, uint8_t* __restrict__ qrun,
                                                    int* __restrict__ list, int* __restrict__ count,
