@@ -54,6 +54,7 @@ struct Smem {
     float edump[kThreads];               // where the other threads' exchange stores go
     uint32_t ks[2][kThreads];            // tier summaries at t of each thread's 8 cells, by step parity
 };
+static_assert(offsetof(Smem, el2r) % 16 == 0 && offsetof(Smem, er2l) % 16 == 0, "16-byte loads of the exchange rows");
 
 __device__ __forceinline__ void origin(int tile, int tiles_x, int& r0, int& c0) {
     r0 = (tile / tiles_x) * kIR - kHalo;
@@ -466,11 +467,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int xp = x + 1 < kCT ? x + 1 : x, xm = x >= 1 ? x - 1 : x;
             // bytes of sigma(t) equal to kSigmaZero (a = 0), as 0xff masks
             const uint32_t dmask[2] = {__vcmpeq4(sgc[0], 0xffffffffu), __vcmpeq4(sgc[1], 0xffffffffu)};
+            // the cross-warp terms of this strip's 8 rows: x = 31 takes those from x = 32, x =
+            // 32 those from x = 31, the others add zeros (two 16-byte loads a thread)
+            const bool edge = x == 31 || x == 32;
+            const float4* ep = reinterpret_cast<const float4*>(x == 31 ? sm.er2l[ex][strip] : sm.el2r[ex][strip]);
+            const float4 e0 = ep[0], e1 = ep[1];
+            const float ev[kM] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
                 float v = fmaf(pc * scl[k], lb[k], own[k]);
-                const float from_r = sm.er2l[ex][strip][k], from_l = sm.el2r[ex][strip][k];
-                v += x == 31 ? from_r : (x == 32 ? from_l : 0.0f);
+                v += edge ? ev[k] : 0.0f;
                 if (k == 0 && strip > 0) {  // uniform across the warp
                     const float c = sm.vbot[ex][strip - 1][1][x];
                     const float r = sm.vbot[ex][strip - 1][0][xp], lf = sm.vbot[ex][strip - 1][2][xm];
@@ -792,6 +798,8 @@ __device__ __forceinline__ void adjoint_tile_flags(const uint8_t* __restrict__ a
                                                              int lane, unsigned long long& sk,
                                                              unsigned long long& fz_steps) {
     const int ty = tile / tiles_x, tx = tile % tiles_x;
+    // the tile's quiescent count, loaded with the flags below so that the latencies overlap
+    const int dc = deadcnt[tile];
     // the 3 x 3 flags around the tile, one per lane: OR-reduced, and whether all of them
     // are unchanged since the segment's first state (kQb; outside the grid: yes)
     uint32_t f = 0u, qb = 1u;
@@ -802,11 +810,12 @@ __device__ __forceinline__ void adjoint_tile_flags(const uint8_t* __restrict__ a
             qb = (f & kQb) ? 1u : 0u;
         }
     }
+    const uint32_t me = __shfl_sync(0xffffffffu, f, 4);  // lane 4 holds the tile's own flags
     const uint32_t around = __reduce_or_sync(0xffffffffu, f);
     const bool all_qb = __reduce_and_sync(0xffffffffu, qb) != 0u;
     if (around & kActA) {
         if (lane == 0) {
-            const bool fz = use_frozen && (act[tile] & kFrozen);
+            const bool fz = use_frozen && (me & kFrozen);
             const int cap = tiles_x * tiles_y;  // the list's capacity
             if (fz)  // from the back of the list (count[2] of them)
                 list[cap - 1 - atomicAdd(count + 2, 1)] = tile | kTileFrozenBit | (all_qb ? kTileCkptBit : 0);
@@ -826,7 +835,6 @@ __device__ __forceinline__ void adjoint_tile_flags(const uint8_t* __restrict__ a
     int r0, c0;
     origin(tile, tiles_x, r0, c0);
     const int ir0 = r0 + kHalo, ic0 = c0 + kHalo;
-    const int dc = deadcnt[tile];
     if (dc < 2) {  // the first two quiescent launches fill both ping-pong buffers
         const size_t gplane = (size_t)H * pitch;
         for (int i = lane; i < kIR * (kIC / 4); i += 32) {
