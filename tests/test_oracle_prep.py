@@ -25,7 +25,7 @@ def test_flat_calm_is_tanh_c_ph(orc):
     q, prm = _prep3(orc)
     want = math.tanh(C * prm.p_h)
     assert np.allclose(q[:, 1, 1], want, rtol=0, atol=1e-15)
-    # the value the survey derived by hand from Eq. 2-5 for p_h = 0.58
+    # the value derived by hand from Eq. 2-5 for p_h = 0.58: tanh(c p_h) with c of Eq. 8
     assert abs(q[0, 1, 1] - 0.5824793373) < 1e-9
 
 
@@ -62,7 +62,7 @@ def test_wind_direction_conventions(orc, theta_w, src, cos_theta):
     assert abs(q[D[src], 1, 1] - math.tanh(C * prm.p_h * pw)) < 1e-14
 
 
-def test_wind_factor_survey_values(orc):
+def test_wind_factor_hand_derived_values(orc):
     # p_w at V = 5, c1 = 0.045, c2 = 0.131 for theta = 0, 45, 90, 180 deg (hand-derived)
     q, prm = _prep3(orc, V=5.0, th=0.0, p_h=1.0)
     got = {}
