@@ -1057,13 +1057,23 @@ int ttape_begin(pf_ctx* ctx, int T) {
         // every tile would take
         const bool known = ctx->ttape_need > 0 && ctx->ttape_need_blk == blk;
         const size_t need = known ? (size_t)ctx->ttape_need : 0;
-        const size_t want = known ? std::min(cap, need + need / 8 + nt) : std::min(cap, (size_t)T * nt);
+        size_t want = known ? std::min(cap, need + need / 8 + nt) : std::min(cap, (size_t)T * nt);
+        // test hook: PF_TAPE_MAX_BLOCKS=n caps the tape at n blocks (read at every tape),
+        // so that a run can be made to outgrow it and recompute its later launches
+        bool capped = false;
+        if (const char* e = getenv("PF_TAPE_MAX_BLOCKS")) {
+            const long long m = atoll(e);
+            if (m > 0 && (size_t)m < want) {
+                want = (size_t)m;
+                capped = true;
+            }
+        }
         // the tape is allocated again when it has another block size, when the run needs
         // its memory elsewhere now, when it is short of a known need that now fits, or
         // when it holds well over what is wanted (the rest is left to the caller)
         if (ctx->ttape && (ctx->ttape_blk != blk || cap < ctx->ttape_cap ||
                            (known && ctx->ttape_cap < need && want > ctx->ttape_cap) ||
-                           ctx->ttape_cap > want + want / 4)) {
+                           ctx->ttape_cap > want + want / 4 || (capped && ctx->ttape_cap > want))) {
             dfree(ctx, ctx->ttape);
             ctx->ttape = nullptr;
             ctx->ttape_cap = 0;

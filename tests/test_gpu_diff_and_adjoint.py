@@ -333,3 +333,51 @@ def test_tile_tape_gives_the_recomputed_gradients(pf, orc, K, k):
     assert np.array_equal(res[0][0], res[1][0])
     assert res[0][1] == res[1][1]
     assert np.array_equal(res[0][2], res[1][2])
+
+
+def test_tile_tape_that_runs_short_gives_the_recomputed_gradients(pf, orc, monkeypatch):
+    """A tile tape too small for the whole forward (capped with PF_TAPE_MAX_BLOCKS)
+    records the launches that fit; the backward copies those from it and recomputes
+    the others, some segments mixing both, with the same bits as a run without a tape."""
+    H, W, T, K, k = 300, 340, 90, 13, 8
+    land = syn.make_landscape(H, W, 43)
+    winds = [syn.smooth_wind(H, W, 43, e, sigma=8.0) for e in range(2)]
+    starts = [0, 41]
+    S0 = syn.initial_state(land, [(70, 80), (220, 250)])
+    w = cuda(np.random.default_rng(7).standard_normal((H, W)).astype(np.float32) * 1e-3)
+
+    def run(tape, cap=None):
+        if cap is None:
+            monkeypatch.delenv("PF_TAPE_MAX_BLOCKS", raising=False)
+        else:
+            monkeypatch.setenv("PF_TAPE_MAX_BLOCKS", str(cap))
+        m, _ = _model(pf, orc, land, *winds[0], H, W)
+        _set_winds(m, winds, starts)
+        m.set_tuning(kernel=2, k=k, K=K, tape=tape, profile=1)
+        pf.pf_profile_read(m.h, reset=True)
+        out = m.forward(cuda(S0), T).cpu().numpy()
+        g4, gpv, _ = m.backward(w, None)
+        prof = pf.pf_profile_read(m.h, reset=True)
+        mem = pf.pf_memory_stats(m.h)
+        m.close()
+        return out, list(g4), gpv.cpu().numpy(), prof, mem
+
+    full = run(0)
+    blk = 2 * 48 * 48 * 4
+    need = full[4]["tape_used_bytes"] // blk
+    tiles = ((340 + 15) // 16 * 16 + 47) // 48 * ((H + 47) // 48)
+    cap = max(tiles, need // 2)
+    assert cap < need
+    short = run(0, cap)
+    ref = run(1)
+    monkeypatch.delenv("PF_TAPE_MAX_BLOCKS", raising=False)
+    mem = short[4]
+    assert mem["tape_short"] == 1 and 0 < mem["tape_recorded"] < mem["tape_launches"]
+    assert mem["tape_used_bytes"] <= cap * blk
+    # both kinds of segment launch ran: copies from the tape and recomputes
+    assert short[3].get("segment_from_tape", (0,))[0] > 0
+    assert short[3]["diff_blocked"][0] > full[3]["diff_blocked"][0]
+    for got in (short, full):
+        assert np.array_equal(got[0], ref[0])
+        assert got[1] == ref[1]
+        assert np.array_equal(got[2], ref[2])
